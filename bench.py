@@ -1,0 +1,349 @@
+"""Benchmark: directional H^2 compression of a dense Helmholtz collocation matrix.
+
+Workload (default): n = 32768 Fibonacci-sphere points, kappa = 32, leaf 64,
+eps = 1e-4, dense complex64 G (8 GiB) resident in HBM, FP32 mode; the reported
+relative error is measured against the complex128 matrix.  One step = one call
+of dh2_compress: block norms + nearfield copy, the leaf factorisations of both
+bases, the non-leaf level steps, the basis expansion and the projection.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead on
+a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except OSError:
+        return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(args):
+    return {"workload": f"helmholtz-collocation fibonacci-sphere n={args.n} kappa={args.kappa:g} leaf={args.leaf} "
+                        f"eps={args.eps:g} {'FP32 complex64' if args.mode == 'fp32' else 'FP64 complex128'}",
+            "n": args.n, "kappa": args.kappa, "leaf": args.leaf, "eps": args.eps, "eta1": args.eta1,
+            "eta2": args.eta2, "zeta": 2.0 / 3.0, "mode": args.mode,
+            "nearfield": "copy" if args.nearfield == 0 else "view",
+            "l2": "inputs larger than L2 (G is 8 GiB at n=32768)"}
+
+
+# --------------------------------------------------------------------------- oracle baseline
+
+def oracle_sample(args, budget_s: float, seed: int = 0):
+    """Time the FP64 oracle's leaf step on a seeded sample of leaf pairs of the
+    workload and scale by work (m_t^2 * #F_tc summed over all leaf pairs of
+    both bases) to a whole-compression time.  Returns (seconds_total_est,
+    sample description, threads)."""
+    from oracle import dh2_oracle as O
+    from synth import fibonacci_sphere, mean_nn_distance
+
+    pts = fibonacci_sphere(args.n)
+    tp = O.TreeParams(leaf_size=args.leaf, kappa=args.kappa, eta1=args.eta1, eta2=args.eta2)
+    cp = O.CompressParams(eps=args.eps)
+    tr = O.build_tree(pts, tp)
+    h = mean_nn_distance(pts)
+    P = pts[tr.perm]
+    F = O.column_sets(tr, "row")
+    eps_l = [O.eps_hat(cp) * cp.zeta ** l for l in range(tr.depth + 1)]
+    leaf_pairs = [(t, c) for t in range(tr.nclusters()) if tr.is_leaf(t) for c in F[t]]
+    work = {}
+    for (t, c) in leaf_pairs:
+        N = sum(tr.size[tr.blocks[b][1]] for b in F[t][c])
+        work[(t, c)] = tr.size[t] ** 2 * N
+    total_work = 2.0 * sum(work.values())  # both bases
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(leaf_pairs))
+
+    def G_block(r0, r1, c0, c1):
+        d = P[r0:r1, None, :] - P[None, c0:c1, :]
+        r = np.sqrt((d * d).sum(-1))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = np.exp(1j * args.kappa * r) / (4.0 * math.pi * r)
+        ii, jj = np.nonzero(r == 0.0)
+        g[ii, jj] = 1.0 / (4.0 * math.pi * h)
+        return g
+
+    done_work, t_used, npairs = 0.0, 0.0, 0
+    for idx in order:
+        t, c = leaf_pairs[idx]
+        t0 = time.perf_counter()
+        parts = []
+        for b in F[t][c]:
+            bt, bs, _, _ = tr.blocks[b]
+            Gb = G_block(tr.start[bt], tr.start[bt] + tr.size[bt], tr.start[bs], tr.start[bs] + tr.size[bs])
+            w = math.sqrt(float(np.sum(np.abs(Gb) ** 2))) * cp.zeta ** (-tr.level[bt])
+            off = tr.start[t] - tr.start[bt]
+            parts.append(Gb[off:off + tr.size[t]] / w)
+        A = np.concatenate(parts, axis=1)
+        Q, sig, k = O.leaf_pair_basis(A, eps_l[tr.level[t]])
+        _ = Q.conj().T @ A
+        t_used += time.perf_counter() - t0
+        done_work += work[(t, c)]
+        npairs += 1
+        if t_used >= budget_s:
+            break
+    est = t_used * total_work / done_work
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:  # pragma: no cover
+        threads = os.cpu_count() or 1
+    desc = (f"oracle leaf step (numpy SVD + R, complex128, weights from block norms) on {npairs} of "
+            f"{len(leaf_pairs)} row-basis leaf pairs (seeded), {t_used:.1f} s, scaled by m^2*#F work to "
+            f"both bases of the whole compression")
+    return est, desc, threads
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+
+    import paper_1510_07087_gb300 as D
+    from synth import fibonacci_sphere, mean_nn_distance
+    from synth.inputs import helmholtz_matrix_torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pts = fibonacci_sphere(args.n)
+    h = mean_nn_distance(pts)
+    T = D.dh2_tree_build(pts, args.leaf, args.kappa, args.eta1, args.eta2)
+    perm = T.perm()
+    st = T.stats()
+    P = pts[perm]
+    cdt = torch.complex64 if args.mode == "fp32" else torch.complex128
+    mode = D.MODE_FP32 if args.mode == "fp32" else D.MODE_FP64
+    G = helmholtz_matrix_torch(P, args.kappa, h, cdt, dev)  # symmetric: row-major == column-major
+    Gd = G.t()
+    stream = torch.cuda.current_stream()
+    elem = 8 if args.mode == "fp32" else 16
+    in_bytes = elem * args.n * args.n
+
+    def step():
+        M = D.dh2_compress(T, Gd, eps=args.eps, mode=mode, nearfield=args.nearfield)
+        return M
+
+    for _ in range(args.warmup):
+        M = step()
+        del M
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phases = np.zeros(5)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            M = step()
+            phases += M.phase_ms()
+            del M
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    phases /= args.steps
+    M = step()
+    ranks = [M.ranks(0), M.ranks(1)]
+    storage = M.storage()
+    # error against the FP64 matrix (complex128, built the same way)
+    del G
+    rel_err = None
+    if args.mode == "fp32" and not args.skip_error:
+        G128 = helmholtz_matrix_torch(P, args.kappa, h, torch.complex128, dev)
+        rel_err = D.dh2_error(M, G128.t())
+        del G128
+    elif not args.skip_error:
+        rel_err = D.dh2_error(M, Gd)
+    # end to end through the C ABI from pinned host memory: H2D of G, compress, D2H of the ranks
+    e2e = None
+    if not args.skip_e2e:
+        Gh = torch.empty((args.n, args.n), dtype=cdt, pin_memory=True)
+        Gh.copy_(Gd.t(), non_blocking=False)
+        Gdev = torch.empty_like(Gh, device=dev)
+        rk_h = [torch.empty(len(r), dtype=torch.int32, pin_memory=True) for r in ranks]
+        Me = None
+        for it in range(args.warmup + args.steps):
+            if it == args.warmup:
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            Gdev.copy_(Gh, non_blocking=True)
+            Me = D.dh2_compress(T, Gdev.t(), eps=args.eps, mode=mode, nearfield=args.nearfield)
+            for sd in (0, 1):
+                rk_h[sd].numpy()[:] = Me.ranks(sd)
+            del Me
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / args.steps
+        d2h = sum(4 * len(r) for r in ranks)
+        e2e = {"value": in_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h}
+        del Gh, Gdev
+    peaks, src = _peaks()
+    adm_bytes = elem * st.adm_fraction * args.n * args.n
+    leaf_ms = float(phases[1])
+    # dominant kernel: the leaf factorisation launch; algorithmic bytes = one
+    # read of every admissible entry of G (each feeds one row and one column pair)
+    roof = {"bound": "hbm", "kernel": "pair_kernel (leaf launch)", "achieved": adm_bytes / (leaf_ms * 1e-3) / 1e9,
+            "peak": peaks["hbm_gbs"], "peak_source": src, "unit": "GB/s",
+            "frac": adm_bytes / (leaf_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+            "alg_bytes_per_launch": adm_bytes}
+    # kernels per compress: norms/nearfield, leaf factors, one non-leaf launch
+    # per level with non-leaf pairs, one expansion launch per level with
+    # non-leaf column pairs, projection
+    lv = T.clusters()["level"]
+    nl_levels = set()
+    col_nl_levels = set()
+    for sd in (0, 1):
+        pr = T.pairs(sd)
+        for c, lf in zip(pr["cluster"], pr["leaf"]):
+            if not lf:
+                nl_levels.add(int(lv[c]))
+                if sd == 1:
+                    col_nl_levels.add(int(lv[c]))
+    launches = 3 + len(nl_levels) + len(col_nl_levels)
+    line = {
+        "metric": "compression wall time & input GB/s at n=32768, kappa=32, eps=1e-4; rel. error vs FP64",
+        "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "replicas only",
+        "vs_baseline": None, "dtype": "c64/f32 (f64 tail sums)" if args.mode == "fp32" else "c128/f64",
+        "data": "synthetic (Fibonacci sphere, Helmholtz collocation)", "config": workload(args),
+        "rel_err_vs_fp64": rel_err, "phases_ms": {k: float(v) for k, v in zip(
+            ["norms_nearfield", "leaf_factors", "level_steps", "expansion", "projection"], phases)},
+        "k_max": int(max(ranks[0].max(initial=0), ranks[1].max(initial=0))),
+        "mem_per_n_kib_c128": storage["total"] * 16 / 1024 / args.n,
+        "adm_fraction": st.adm_fraction, "roofline": roof, "e2e": e2e,
+        "clocks": clk.summary(), "gpu_launches": launches * args.steps, "launches_per_step": launches,
+    }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--kappa", type=float, default=32.0)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--eta1", type=float, default=2.0 * math.sqrt(2.0))
+    ap.add_argument("--eta2", type=float, default=1.0)
+    ap.add_argument("--mode", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--nearfield", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-error", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    elem = 8 if args.mode == "fp32" else 16
+    in_bytes = elem * args.n * args.n
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        desc, thr = "", 1
+        for _ in range(args.warmup):
+            oracle_sample(args, budget_s=max(1.0, args.cpu_budget / 5))
+        for s in range(args.steps):
+            est, desc, thr = oracle_sample(args, budget_s=args.cpu_budget, seed=s)
+            vals.append(in_bytes / est / 1e9)
+        v = statistics.median(vals)
+        line = {"impl": "reference", "metric": "compression wall time & input GB/s at n=32768, kappa=32, "
+                "eps=1e-4; rel. error vs FP64", "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": in_bytes / v / 1e6,
+                "higher_is_better": True, "scaling": "replicas only", "vs_baseline": None, "dtype": "c128/f64",
+                "data": "synthetic", "config": workload(args),
+                "cpu_baseline": {"value": v, "unit": "GB/s", "cores": thr, "kind": "oracle", "sample": desc},
+                "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    line = run_gpu(args)
+    line["n_gpus"] = world
+    if not args.skip_cpu and rank == 0:
+        est, desc, thr = oracle_sample(args, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": in_bytes / est / 1e9, "unit": "GB/s", "cores": thr, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

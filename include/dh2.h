@@ -1,0 +1,199 @@
+/*
+ * dh2.h - C ABI of the GB300 directional H^2-matrix compression library.
+ *
+ * The library approximates a dense complex matrix G in C^{I x I} by a
+ * directional H^2 (DH^2) matrix: orthonormal directional row and column
+ * cluster bases V, W given by leaf matrices and transfer matrices E
+ * (Def. "Directional cluster basis", Eq. nested), coupling matrices
+ * S_b = V_tc^* G|_{t x s} W_sc for admissible leaves b = (t, s) with block
+ * direction c = c_b (Def. "Directional H^2-matrix", Section 6), and the
+ * nearfield blocks G|_b of the inadmissible leaves.  The bases are built
+ * bottom-up by the compression procedure of Section 6 (procedure basis()
+ * of the figure "Construction of an orthogonal directional cluster basis")
+ * applied to G for V and to G^* for W.
+ *
+ * Conventions for every entry point:
+ *  - Return value: a dh2_status; no exception crosses the ABI.  On failure an
+ *    output handle is set to NULL and nothing is leaked.
+ *  - Index order: every device vector and matrix is in the tree's PERMUTED
+ *    order, in which each cluster is a contiguous index range; dh2_tree_perm
+ *    gives the map back to the caller's order.
+ *  - Complex data are interleaved (re, im) pairs: DH2_C64 = 2 x float,
+ *    DH2_C128 = 2 x double.  Matrices are column-major with a leading
+ *    dimension `ld` >= n (in elements).
+ *  - Streams: calls that take a cudaStream_t (passed as void*) enqueue their
+ *    GPU work on it; dh2_compress synchronises that stream once at its end to
+ *    read the device status word (NULL = the legacy default stream).
+ *  - Ownership: the caller owns G, x, y and the points; the library owns
+ *    everything behind a handle and frees it in dh2_*_free.  In nearfield VIEW
+ *    mode the matrix handle keeps a pointer to G, which must outlive it.
+ *  - Host-only calls (tree build, tree queries) never touch a GPU.
+ */
+#ifndef DH2_H
+#define DH2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dh2_tree dh2_tree;     /* cluster tree, directions, block tree, work lists */
+typedef struct dh2_matrix dh2_matrix; /* device-resident DH^2 representation             */
+
+typedef enum {
+  DH2_OK = 0,
+  DH2_EINVAL = 1,       /* bad argument (null pointer, size, parameter range)       */
+  DH2_ENOMEM = 2,       /* host or device allocation failed                         */
+  DH2_ECUDA = 3,        /* a CUDA runtime call failed                               */
+  DH2_ETIMEOUT = 4,     /* a bounded device-side wait ran out                        */
+  DH2_ENOCONV = 5,      /* a Jacobi SVD hit its sweep cap before converging          */
+  DH2_EUNSUPPORTED = 6  /* size beyond a compiled limit (e.g. rows of a factor)      */
+} dh2_status;
+
+typedef enum { DH2_C64 = 0, DH2_C128 = 1 } dh2_dtype;
+
+/* Arithmetic of the compression.  FP64: complex128 input and FP64 everywhere
+ * (the plain form).  FP32: complex64 input, FP32 factorisations on the
+ * non-squared factors, FP64 tail sums for the rank decisions. */
+typedef enum { DH2_MODE_FP64 = 0, DH2_MODE_FP32 = 1 } dh2_mode;
+
+/* Tree parameters (Section 3; Section 7 for the paper's values).
+ *  leaf_size : a cluster with more indices is bisected (Def. 1).
+ *  kappa     : wave number of Eq. (helmholtz) and Eq. (adm_parabolic).
+ *  eta1      : direction parameter of Eq. (adm_directional): D_l covers the
+ *              sphere with radius eta1 / (kappa * delta_l).
+ *  eta2      : parameter of Eqs. (adm_parabolic) and (adm_standard).
+ *  dir_rule  : 0 = cube-surface directions on every level, 1 = {0} on levels
+ *              with kappa * delta_l <= eta1 (Def. 3 allows c = 0). */
+typedef struct {
+  int32_t leaf_size;
+  int32_t dir_rule;
+  double kappa;
+  double eta1;
+  double eta2;
+} dh2_tree_params;
+
+/* Compression parameters (Remark "Error control").
+ *  eps       : requested accuracy.
+ *  zeta      : level factor of eps_r = eps_hat * zeta^level(r), zeta < 1/sqrt 2.
+ *  err_mode  : 0 = eps_hat = eps*sqrt(1-2 zeta^2)/sqrt 2, which bounds
+ *              |G - G~|_F <= eps |G|_F; 1 = eps_hat = eps.
+ *  mode      : dh2_mode; must match the dtype of G (FP64 <-> C128, FP32 <-> C64).
+ *  nearfield : 0 = copy the inadmissible blocks into the matrix handle,
+ *              1 = keep a view of G.
+ *  max_sweeps: cap on Jacobi sweeps per factor (0 = default 30). */
+typedef struct {
+  double eps;
+  double zeta;
+  int32_t err_mode;
+  int32_t mode;
+  int32_t nearfield;
+  int32_t max_sweeps;
+} dh2_compress_params;
+
+typedef struct {
+  int64_t n;
+  int32_t depth;           /* p_I of Def. 1                                  */
+  int32_t nclusters;
+  int64_t nblocks;         /* leaves of the block tree                        */
+  int64_t nadmissible;     /* admissible leaves                               */
+  double adm_fraction;     /* admissible entries / n^2                        */
+  int64_t npairs[2];       /* used (t, c) pairs, [0] row side, [1] column side */
+  int64_t nleafpairs[2];
+  int64_t ncolumns[2];     /* sum over pairs of #F_tc                          */
+  int64_t nleafcolumns[2]; /* sum over leaf pairs of #F_tc                     */
+  int32_t max_leaf;        /* largest leaf cluster                            */
+  int32_t ndirs_max;       /* largest |D_l|                                    */
+} dh2_tree_stats;
+
+/* ---------------------------------------------------------------- tree (host) */
+
+/* Build the cluster tree (Def. 1, bisection of tight bounding boxes at the
+ * midpoint of the longest side), the direction families D_l and son maps
+ * sd_l (Def. 3, Section 3), the block tree (Def. 2 with Eqs. adm_parabolic and
+ * adm_standard), the block directions c_b and, for both sides, the used
+ * (cluster, direction) pairs with their column sets F_tc (Section 6).
+ * pts_xyz: host, n x 3 row-major doubles, read only during the call. */
+dh2_status dh2_tree_build(const double* pts_xyz, int64_t n, const dh2_tree_params* params,
+                          dh2_tree** out);
+void dh2_tree_free(dh2_tree* tree);
+dh2_status dh2_tree_stats_get(const dh2_tree* tree, dh2_tree_stats* out);
+/* perm[i] = caller index of permuted index i (host, n entries). */
+dh2_status dh2_tree_perm(const dh2_tree* tree, int64_t* perm);
+/* Per-cluster arrays (host, nclusters entries each; lo/hi 3 per cluster;
+ * son0/son1 = -1 for leaves).  Any pointer may be NULL. */
+dh2_status dh2_tree_clusters(const dh2_tree* tree, int32_t* start, int32_t* size, int32_t* level,
+                             int32_t* parent, int32_t* son0, int32_t* son1, double* lo, double* hi);
+/* Number of directions on a level, then the directions (3 doubles each) and
+ * the son map into level+1 (-1 on the deepest level).  Either pointer may be NULL. */
+dh2_status dh2_tree_ndirs(const dh2_tree* tree, int32_t level, int32_t* ndirs);
+dh2_status dh2_tree_directions(const dh2_tree* tree, int32_t level, double* dirs, int32_t* sd);
+/* Leaves of the block tree in construction order (host, nblocks entries each):
+ * row cluster, column cluster, admissible flag, block direction (-1 if not admissible). */
+dh2_status dh2_tree_blocks(const dh2_tree* tree, int32_t* t, int32_t* s, int32_t* adm, int32_t* cb);
+/* Used pairs of one side (0 row, 1 column): cluster, direction, #F_tc columns,
+ * leaf flag; and the blocks of F_tc in the library's column order as CSR
+ * (offsets: npairs+1 entries; block ids: offsets[npairs] entries).  A NULL
+ * `block_ids` with non-NULL `offsets` returns only the offsets. */
+dh2_status dh2_tree_pairs(const dh2_tree* tree, int32_t side, int32_t* cluster, int32_t* dir,
+                          int64_t* ncols, int32_t* is_leaf);
+dh2_status dh2_tree_pair_blocks(const dh2_tree* tree, int32_t side, int64_t* offsets, int32_t* block_ids);
+
+/* ---------------------------------------------------------------- compression (GPU) */
+
+/* Compress G (device, n x n column-major, permuted order, leading dimension
+ * ld) into a DH^2 matrix.  Realises procedure basis() of Section 6 for the row
+ * basis and for the column basis (the same procedure on G^*), with the
+ * weighted error control of Remark "Error control" (omega_b = |G_b|_F *
+ * zeta^-level(t)), followed by the projection S_b = V_tc^* G_b W_sc.
+ * Errors: DH2_EINVAL for bad sizes/params or a dtype/mode mismatch,
+ * DH2_ENOCONV / DH2_EUNSUPPORTED from the device status word, DH2_ECUDA. */
+dh2_status dh2_compress(const dh2_tree* tree, const void* G, dh2_dtype dtype, int64_t ld,
+                        const dh2_compress_params* params, void* stream, dh2_matrix** out);
+void dh2_matrix_free(dh2_matrix* M);
+
+/* y = G~ x for the compressed matrix (Section 4: forward transformation,
+ * coupling, backward transformation, plus the nearfield).  x, y: device,
+ * n x nrhs column-major (leading dimension n), permuted order, dtype of the
+ * matrix.  y is overwritten. */
+dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream);
+
+/* Relative Frobenius error |G_ref - G~|_F / |G_ref|_F, block by block, with
+ * G_ref a device matrix of dtype ref_dtype (n x n column-major, permuted
+ * order, leading dimension ld).  Synchronises the stream. */
+dh2_status dh2_error(const dh2_matrix* M, const void* G_ref, dh2_dtype ref_dtype, int64_t ld,
+                     void* stream, double* rel_err);
+
+/* Ranks of the used pairs of one side (host, npairs entries). */
+dh2_status dh2_matrix_ranks(const dh2_matrix* M, int32_t side, int32_t* ranks);
+/* Singular values computed for one pair (host, up to `cap` doubles, sorted
+ * descending); *count receives the number of values (rows of the factor). */
+dh2_status dh2_matrix_sigma(const dh2_matrix* M, int32_t side, int64_t pair, double* out, int32_t cap,
+                            int32_t* count);
+/* Stored matrix of one pair, copied to the host as complex128: a leaf pair's
+ * basis Q_tc (rows = cluster size) or a non-leaf pair's [E_t1c; E_t2c]
+ * (rows = k_t1c' + k_t2c').  out: rows x k column-major, ld = rows. */
+dh2_status dh2_matrix_pair_basis(const dh2_matrix* M, int32_t side, int64_t pair, double* out,
+                                 int64_t cap_elems, int32_t* rows, int32_t* k);
+/* Coupling matrix S_b of an admissible block, copied to the host as complex128
+ * (k_t x k_s column-major). */
+dh2_status dh2_matrix_coupling(const dh2_matrix* M, int64_t block, double* out, int64_t cap_elems,
+                               int32_t* kt, int32_t* ks);
+/* Storage in stored entries (Def. "DH^2-matrix representation"):
+ * parts[0..5] = V leaves, W leaves, E of V, E of W, S, nearfield; *total = sum. */
+dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts);
+/* Time of the last dh2_compress per phase in ms measured with CUDA events:
+ * [0] norms+nearfield, [1] leaf factors, [2] level steps, [3] expansion, [4] projection. */
+dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms5);
+
+const char* dh2_status_string(dh2_status s);
+/* Library version string. */
+const char* dh2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DH2_H */

@@ -439,6 +439,15 @@ def compress(tr: OracleTree, G: np.ndarray, cp: CompressParams, side: str = "row
     return out
 
 
+def leaf_pair_basis(A: np.ndarray, eps_l: float):
+    """Leaf step for one explicit matrix A = G^omega_tc (Section 6): the
+    singular values, the rank by the truncation rule and Q = leading left
+    singular vectors.  Used to check sampled pairs of large problems."""
+    U, sig, _ = np.linalg.svd(A, full_matrices=False)
+    k = _truncation_rank(sig, eps_l)
+    return U[:, :k], sig, k
+
+
 def expand_basis(tr: OracleTree, B: Basis, t: int, c: int, cache: dict | None = None) -> np.ndarray:
     """Explicit Q_tc from leaf matrices and transfer matrices by Eq. (nested)."""
     if cache is not None and (t, c) in cache:

@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) directional H^2-matrix compression.
+
+The compute path is the C-ABI CUDA library `libdh2.so` (include/dh2.h); this
+package is its Python binding (argument marshalling only).
+"""
+from ._binding import (  # noqa: F401
+    DH2_C64, DH2_C128, MODE_FP32, MODE_FP64, SIDE_COL, SIDE_ROW,
+    DH2Error, Matrix, Tree,
+    dh2_compress, dh2_error, dh2_matvec, dh2_tree_build, dh2_version, exported_symbols,
+)

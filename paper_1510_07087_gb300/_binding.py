@@ -1,0 +1,304 @@
+"""ctypes binding of the C ABI in include/dh2.h (argument marshalling only).
+
+Every compute step runs in the CUDA library `libdh2.so`; this module only
+converts numpy arrays / torch tensors into pointers, sizes and the current
+CUDA stream, and turns status codes into exceptions.  There is no fallback:
+if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_float, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdh2.so")
+
+DH2_C64 = 0
+DH2_C128 = 1
+MODE_FP64 = 0
+MODE_FP32 = 1
+SIDE_ROW = 0
+SIDE_COL = 1
+
+
+class TreeParams(ctypes.Structure):
+    _fields_ = [("leaf_size", c_int32), ("dir_rule", c_int32), ("kappa", c_double),
+                ("eta1", c_double), ("eta2", c_double)]
+
+
+class CompressParams(ctypes.Structure):
+    _fields_ = [("eps", c_double), ("zeta", c_double), ("err_mode", c_int32), ("mode", c_int32),
+                ("nearfield", c_int32), ("max_sweeps", c_int32)]
+
+
+class TreeStats(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("depth", c_int32), ("nclusters", c_int32), ("nblocks", c_int64),
+                ("nadmissible", c_int64), ("adm_fraction", c_double), ("npairs", c_int64 * 2),
+                ("nleafpairs", c_int64 * 2), ("ncolumns", c_int64 * 2), ("nleafcolumns", c_int64 * 2),
+                ("max_leaf", c_int32), ("ndirs_max", c_int32)]
+
+
+class DH2Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib().dh2_status_string(status).decode()} (status {status})")
+
+
+_LIB = None
+
+# (name, restype, argtypes) of every entry point declared in include/dh2.h
+SIGNATURES = [
+    ("dh2_tree_build", c_int32, [c_void_p, c_int64, POINTER(TreeParams), POINTER(c_void_p)]),
+    ("dh2_tree_free", None, [c_void_p]),
+    ("dh2_tree_stats_get", c_int32, [c_void_p, POINTER(TreeStats)]),
+    ("dh2_tree_perm", c_int32, [c_void_p, c_void_p]),
+    ("dh2_tree_clusters", c_int32, [c_void_p] + [c_void_p] * 8),
+    ("dh2_tree_ndirs", c_int32, [c_void_p, c_int32, POINTER(c_int32)]),
+    ("dh2_tree_directions", c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+    ("dh2_tree_blocks", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("dh2_tree_pairs", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    ("dh2_tree_pair_blocks", c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+    ("dh2_compress", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p,
+                               POINTER(c_void_p)]),
+    ("dh2_matrix_free", None, [c_void_p]),
+    ("dh2_matvec", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    ("dh2_error", c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_void_p, POINTER(c_double)]),
+    ("dh2_matrix_ranks", c_int32, [c_void_p, c_int32, c_void_p]),
+    ("dh2_matrix_sigma", c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int32, POINTER(c_int32)]),
+    ("dh2_matrix_pair_basis", c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int64, POINTER(c_int32),
+                                        POINTER(c_int32)]),
+    ("dh2_matrix_coupling", c_int32, [c_void_p, c_int64, c_void_p, c_int64, POINTER(c_int32), POINTER(c_int32)]),
+    ("dh2_storage", c_int32, [c_void_p, POINTER(c_double), c_void_p]),
+    ("dh2_matrix_phase_ms", c_int32, [c_void_p, c_void_p]),
+    ("dh2_status_string", ctypes.c_char_p, [c_int32]),
+    ("dh2_version", ctypes.c_char_p, []),
+]
+
+
+def _lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libdh2.so is not built ({LIB_PATH}); run `python -m paper_1510_07087_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int, what: str) -> None:
+    if status != 0:
+        raise DH2Error(status, what)
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ------------------------------------------------------------------ tree
+
+class Tree:
+    """Owner of a dh2_tree handle."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = c_void_p(handle)
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib().dh2_tree_free(self.handle)
+            self.handle = c_void_p()
+
+    # queries
+    def stats(self) -> TreeStats:
+        st = TreeStats()
+        _check(_lib().dh2_tree_stats_get(self.handle, byref(st)), "dh2_tree_stats_get")
+        return st
+
+    def perm(self) -> np.ndarray:
+        out = np.empty(self.n, dtype=np.int64)
+        _check(_lib().dh2_tree_perm(self.handle, _ptr(out)), "dh2_tree_perm")
+        return out
+
+    def clusters(self) -> dict:
+        nc = self.stats().nclusters
+        d = {k: np.empty(nc, dtype=np.int32) for k in ("start", "size", "level", "parent", "son0", "son1")}
+        lo = np.empty((nc, 3))
+        hi = np.empty((nc, 3))
+        _check(_lib().dh2_tree_clusters(self.handle, *[_ptr(d[k]) for k in ("start", "size", "level", "parent",
+                                                                             "son0", "son1")], _ptr(lo), _ptr(hi)),
+               "dh2_tree_clusters")
+        d["lo"], d["hi"] = lo, hi
+        return d
+
+    def directions(self, level: int):
+        nd = c_int32()
+        _check(_lib().dh2_tree_ndirs(self.handle, level, byref(nd)), "dh2_tree_ndirs")
+        D = np.empty((nd.value, 3))
+        sd = np.empty(nd.value, dtype=np.int32)
+        _check(_lib().dh2_tree_directions(self.handle, level, _ptr(D), _ptr(sd)), "dh2_tree_directions")
+        return D, sd
+
+    def blocks(self) -> np.ndarray:
+        nb = self.stats().nblocks
+        arr = [np.empty(nb, dtype=np.int32) for _ in range(4)]
+        _check(_lib().dh2_tree_blocks(self.handle, *[_ptr(a) for a in arr]), "dh2_tree_blocks")
+        return np.stack(arr, axis=1)
+
+    def pairs(self, side: int) -> dict:
+        np_ = self.stats().npairs[side]
+        cl = np.empty(np_, dtype=np.int32)
+        di = np.empty(np_, dtype=np.int32)
+        nc = np.empty(np_, dtype=np.int64)
+        lf = np.empty(np_, dtype=np.int32)
+        _check(_lib().dh2_tree_pairs(self.handle, side, _ptr(cl), _ptr(di), _ptr(nc), _ptr(lf)), "dh2_tree_pairs")
+        return {"cluster": cl, "dir": di, "ncols": nc, "leaf": lf}
+
+    def pair_blocks(self, side: int):
+        np_ = self.stats().npairs[side]
+        off = np.empty(np_ + 1, dtype=np.int64)
+        _check(_lib().dh2_tree_pair_blocks(self.handle, side, _ptr(off), None), "dh2_tree_pair_blocks")
+        ids = np.empty(max(1, int(off[-1])), dtype=np.int32)
+        _check(_lib().dh2_tree_pair_blocks(self.handle, side, _ptr(off), _ptr(ids)), "dh2_tree_pair_blocks")
+        return off, ids[:int(off[-1])]
+
+
+def dh2_tree_build(points: np.ndarray, leaf_size: int = 32, kappa: float = 4.0,
+                   eta1: float = 2.0 * np.sqrt(2.0), eta2: float = 1.0, dir_rule: int = 0) -> Tree:
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    if pts.ndim != 2 or pts.shape[1] != 3:
+        raise ValueError("points must be (n, 3)")
+    p = TreeParams(int(leaf_size), int(dir_rule), float(kappa), float(eta1), float(eta2))
+    h = c_void_p()
+    _check(_lib().dh2_tree_build(_ptr(pts), pts.shape[0], byref(p), byref(h)), "dh2_tree_build")
+    return Tree(h.value, pts.shape[0])
+
+
+# ------------------------------------------------------------------ matrix
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+
+    if t.dtype == torch.complex64:
+        return DH2_C64
+    if t.dtype == torch.complex128:
+        return DH2_C128
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _colmajor_ld(G) -> int:
+    if G.dim() != 2 or G.stride(0) != 1 or G.stride(1) < G.shape[0]:
+        raise ValueError("G must be a column-major (n, n) view: stride (1, ld) with ld >= n")
+    return int(G.stride(1))
+
+
+class Matrix:
+    """Owner of a dh2_matrix handle (device-resident DH^2 representation)."""
+
+    def __init__(self, handle: int, tree: Tree, mode: int, G):
+        self.handle = c_void_p(handle)
+        self.tree = tree
+        self.mode = mode
+        self._G = G  # keeps a viewed nearfield alive
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib().dh2_matrix_free(self.handle)
+            self.handle = c_void_p()
+
+    def ranks(self, side: int) -> np.ndarray:
+        out = np.empty(self.tree.stats().npairs[side], dtype=np.int32)
+        _check(_lib().dh2_matrix_ranks(self.handle, side, _ptr(out)), "dh2_matrix_ranks")
+        return out
+
+    def sigma(self, side: int, pair: int) -> np.ndarray:
+        out = np.empty(128)
+        cnt = c_int32()
+        _check(_lib().dh2_matrix_sigma(self.handle, side, pair, _ptr(out), 128, byref(cnt)), "dh2_matrix_sigma")
+        return out[:min(cnt.value, 128)].copy()
+
+    def pair_basis(self, side: int, pair: int) -> np.ndarray:
+        cap = 128 * 128
+        out = np.empty(2 * cap)
+        rows, k = c_int32(), c_int32()
+        _check(_lib().dh2_matrix_pair_basis(self.handle, side, pair, _ptr(out), cap, byref(rows), byref(k)),
+               "dh2_matrix_pair_basis")
+        r, kk = rows.value, k.value
+        return out[:2 * r * kk].view(np.complex128).reshape(kk, r).T.copy()
+
+    def coupling(self, block: int) -> np.ndarray:
+        cap = 128 * 128
+        out = np.empty(2 * cap)
+        kt, ks = c_int32(), c_int32()
+        _check(_lib().dh2_matrix_coupling(self.handle, block, _ptr(out), cap, byref(kt), byref(ks)),
+               "dh2_matrix_coupling")
+        a, b = kt.value, ks.value
+        return out[:2 * a * b].view(np.complex128).reshape(b, a).T.copy()
+
+    def storage(self) -> dict:
+        tot = c_double()
+        parts = np.zeros(6)
+        _check(_lib().dh2_storage(self.handle, byref(tot), _ptr(parts)), "dh2_storage")
+        keys = ["V", "W", "E_V", "E_W", "S", "near"]
+        d = {k: float(v) for k, v in zip(keys, parts)}
+        d["total"] = float(tot.value)
+        return d
+
+    def phase_ms(self) -> np.ndarray:
+        out = np.zeros(5, dtype=np.float32)
+        _check(_lib().dh2_matrix_phase_ms(self.handle, _ptr(out)), "dh2_matrix_phase_ms")
+        return out
+
+
+def dh2_compress(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,
+                 mode: int | None = None, nearfield: int = 0, max_sweeps: int = 0, stream=None) -> Matrix:
+    """Compress a device matrix G (torch, column-major view, tree's permuted order)."""
+    dt = _dtype_code(G)
+    if mode is None:
+        mode = MODE_FP32 if dt == DH2_C64 else MODE_FP64
+    ld = _colmajor_ld(G)
+    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), int(nearfield), int(max_sweeps))
+    h = c_void_p()
+    _check(_lib().dh2_compress(tree.handle, c_void_p(G.data_ptr()), dt, ld, byref(p),
+                               c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress")
+    return Matrix(h.value, tree, mode, G)
+
+
+def dh2_matvec(M: Matrix, x, y, stream=None) -> None:
+    """y = G~ x; x, y torch device tensors (n,) or (n, nrhs) column-major, matrix dtype."""
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    for v in (x, y):
+        if v.dim() == 2 and (v.stride(0) != 1 or v.stride(1) != v.shape[0]):
+            raise ValueError("x, y must be column-major (n, nrhs)")
+        if v.dim() == 1 and v.stride(0) != 1:
+            raise ValueError("x, y must be contiguous")
+    _check(_lib().dh2_matvec(M.handle, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), nrhs,
+                             c_void_p(_stream_handle(stream))), "dh2_matvec")
+
+
+def dh2_error(M: Matrix, Gref, stream=None) -> float:
+    out = c_double()
+    _check(_lib().dh2_error(M.handle, c_void_p(Gref.data_ptr()), _dtype_code(Gref), _colmajor_ld(Gref),
+                            c_void_p(_stream_handle(stream)), byref(out)), "dh2_error")
+    return float(out.value)
+
+
+def dh2_version() -> str:
+    return _lib().dh2_version().decode()
+
+
+def exported_symbols() -> list:
+    return [name for name, _, _ in SIGNATURES]

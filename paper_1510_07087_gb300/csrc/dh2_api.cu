@@ -1,0 +1,992 @@
+// C ABI of the library: tree queries, device upload of the work lists, the
+// level schedule of the compression, matrix-vector product, error, export.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <new>
+#include <vector>
+
+#include "dh2_internal.h"
+#include "dh2_kernels.cuh"
+#include "dh2_ops.cuh"
+
+using namespace dh2;
+
+#define DH2_CUDA_TRY(x)                   \
+  do {                                    \
+    if ((x) != cudaSuccess) {             \
+      cudaGetLastError();                 \
+      return DH2_ECUDA;                   \
+    }                                     \
+  } while (0)
+
+namespace dh2 {
+
+// Device copy of a tree's work lists (one arena, uploaded on first use).
+struct Tree::Dev {
+  void* arena = nullptr;
+  // clusters
+  int32_t *cstart, *csize, *clevel;
+  // per side, per pair
+  int32_t *cluster[2], *leaf[2], *start[2], *m[2], *ncols[2], *son[2], *sonoff[2], *level[2], *kcap[2],
+      *rowcap[2];
+  int64_t *cmoff[2], *Roff[2], *Qoff[2], *Xoff[2], *hoff[2];
+  int32_t *gcol[2], *gblk[2];
+  int32_t* iota[2];        // 0..npairs-1
+  int32_t* leaf_list[2];   // leaf pair ids
+  // blocks
+  int32_t *bt, *bs, *badm, *bpair[2], *boff_row;
+  int64_t *near_off, *Soff;
+  int32_t *adm_list, *inadm_list;
+  // matvec lists (row side)
+  int64_t *own_ptr, *par_ptr;
+  int32_t *own_blk, *par_pair, *par_son;
+  // launch orders: leaf launch (both sides) then non-leaf per level
+  int32_t* codes;
+  // host-side sizes
+  int64_t npairs[2] = {0, 0}, nleaf[2] = {0, 0};
+  int64_t R_elems[2] = {0, 0}, Q_elems[2] = {0, 0}, X_elems[2] = {0, 0}, h_elems[2] = {0, 0};
+  int64_t S_elems = 0, near_elems = 0;
+  int64_t nadm = 0, ninadm = 0;
+  int64_t nleaf_codes = 0;
+  std::vector<int64_t> nl_code_begin, nl_code_count;    // per level
+  std::vector<int32_t> nl_rowcap_max;                   // per level
+  std::vector<int64_t> lvl_begin[2], lvl_nl_begin[2], lvl_end[2];
+  int32_t max_leaf = 0;
+  std::vector<int32_t> kcap_h[2], rowcap_h[2];
+  std::vector<int64_t> Qoff_h[2], Soff_h;
+};
+
+}  // namespace dh2
+
+struct dh2_matrix {
+  dh2_tree* tree = nullptr;
+  int device = 0;
+  int mode = 0;
+  dh2_dtype dtype = DH2_C64;
+  size_t es = 8;  // bytes per complex element
+  cudaStream_t stream = nullptr;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  void* R[2] = {nullptr, nullptr};
+  void* Q[2] = {nullptr, nullptr};
+  void* X[2] = {nullptr, nullptr};
+  double* sig[2] = {nullptr, nullptr};
+  int32_t* rank[2] = {nullptr, nullptr};
+  void* S = nullptr;
+  void* near = nullptr;
+  double* invw = nullptr;
+  double* eps2 = nullptr;
+  double* zpow = nullptr;
+  uint32_t* status = nullptr;
+  double* acc = nullptr;
+  const void* G = nullptr;
+  int64_t ld = 0;
+  int nearfield_copy = 1;
+  bool v_expanded = false;
+  std::vector<double> eps2_h, zpow_h;
+  float phase_ms[5] = {0, 0, 0, 0, 0};
+};
+
+namespace {
+
+template <typename V>
+size_t bytes_of(const std::vector<V>& v) {
+  return v.size() * sizeof(V);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Capacities: leaf rank <= min(rows, #F); non-leaf rank <= min(k_cap(t1c') +
+// k_cap(t2c'), #F, 128).  Offsets of R (k_cap x #F), Q ([E1;E2] rowcap x k_cap)
+// and of the expanded non-leaf bases (#t x k_cap) follow.
+dh2_status upload_tree(Tree& tr) {
+  Tree::Dev* D = new (std::nothrow) Tree::Dev();
+  if (!D) return DH2_ENOMEM;
+  const int32_t nc = tr.nclusters();
+  struct Buf {
+    const void* src;
+    size_t bytes;
+    void** dst;
+  };
+  std::vector<Buf> bufs;
+  // keep host arrays alive until the copy
+  std::vector<std::vector<int32_t>> i32;
+  std::vector<std::vector<int64_t>> i64;
+  i32.reserve(64);
+  i64.reserve(32);
+  auto add32 = [&](std::vector<int32_t>&& v, int32_t** dst) {
+    i32.push_back(std::move(v));
+    bufs.push_back({i32.back().data(), bytes_of(i32.back()), (void**)dst});
+  };
+  auto add64 = [&](std::vector<int64_t>&& v, int64_t** dst) {
+    i64.push_back(std::move(v));
+    bufs.push_back({i64.back().data(), bytes_of(i64.back()), (void**)dst});
+  };
+  add32(std::vector<int32_t>(tr.start), &D->cstart);
+  add32(std::vector<int32_t>(tr.size), &D->csize);
+  add32(std::vector<int32_t>(tr.level), &D->clevel);
+  D->max_leaf = tr.max_leaf;
+
+  for (int sd = 0; sd < 2; ++sd) {
+    Side& S = tr.side[sd];
+    const int64_t np = (int64_t)S.pairs.size();
+    D->npairs[sd] = np;
+    std::vector<int32_t> cl(np), lf(np), st(np), mm(np), nco(np), son(2 * np, -1), soff(2 * np, 0), lv(np),
+        kc(np), rc(np), io(np);
+    std::vector<int64_t> cmo(np), ro(np), qo(np), xo(np, 0), ho(np);
+    int64_t R_e = 0, Q_e = 0, X_e = 0, h_e = 0;
+    for (int64_t p = 0; p < np; ++p) {  // sons before fathers (level descending)
+      const Pair& P = S.pairs[p];
+      cl[p] = P.cluster;
+      lf[p] = P.leaf;
+      st[p] = tr.start[P.cluster];
+      mm[p] = tr.size[P.cluster];
+      nco[p] = (int32_t)P.ncols;
+      lv[p] = P.level;
+      io[p] = (int32_t)p;
+      cmo[p] = S.leaf_colmap_off[p];
+      if (P.leaf) {
+        rc[p] = tr.size[P.cluster];
+        kc[p] = (int32_t)std::min<int64_t>(rc[p], P.ncols);
+      } else {
+        for (int j = 0; j < 2; ++j) {
+          son[2 * p + j] = (int32_t)P.son_pair[j];
+          soff[2 * p + j] = (int32_t)P.son_off[j];
+        }
+        rc[p] = std::min(kc[P.son_pair[0]] + kc[P.son_pair[1]], kPmaxF32);
+        kc[p] = (int32_t)std::min<int64_t>(rc[p], P.ncols);
+        xo[p] = X_e;
+        X_e += (int64_t)tr.size[P.cluster] * kc[p];
+      }
+      ro[p] = R_e;
+      R_e += (int64_t)kc[p] * P.ncols;
+      qo[p] = Q_e;
+      Q_e += (int64_t)rc[p] * kc[p];
+      ho[p] = h_e;
+      h_e += kc[p];
+    }
+    D->R_elems[sd] = R_e;
+    D->Q_elems[sd] = Q_e;
+    D->X_elems[sd] = X_e;
+    D->h_elems[sd] = h_e;
+    D->kcap_h[sd] = kc;
+    D->rowcap_h[sd] = rc;
+    D->Qoff_h[sd] = qo;
+    D->nleaf[sd] = (int64_t)S.leaf_pairs.size();
+    std::vector<int32_t> ll(S.leaf_pairs.begin(), S.leaf_pairs.end());
+    // level ranges
+    D->lvl_begin[sd].assign(tr.depth + 1, 0);
+    D->lvl_nl_begin[sd].assign(tr.depth + 1, 0);
+    D->lvl_end[sd].assign(tr.depth + 1, 0);
+    for (int l = 0; l <= tr.depth; ++l) {
+      int64_t b = -1, nb = -1, e = -1;
+      for (int64_t p = 0; p < np; ++p)
+        if (S.pairs[p].level == l) {
+          if (b < 0) b = p;
+          if (!S.pairs[p].leaf && nb < 0) nb = p;
+          e = p + 1;
+        }
+      if (b < 0) b = e = nb = 0;
+      if (nb < 0) nb = e;
+      D->lvl_begin[sd][l] = b;
+      D->lvl_nl_begin[sd][l] = nb;
+      D->lvl_end[sd][l] = e;
+    }
+    add32(std::move(cl), &D->cluster[sd]);
+    add32(std::move(lf), &D->leaf[sd]);
+    add32(std::move(st), &D->start[sd]);
+    add32(std::move(mm), &D->m[sd]);
+    add32(std::move(nco), &D->ncols[sd]);
+    add32(std::move(son), &D->son[sd]);
+    add32(std::move(soff), &D->sonoff[sd]);
+    add32(std::move(lv), &D->level[sd]);
+    add32(std::vector<int32_t>(D->kcap_h[sd]), &D->kcap[sd]);
+    add32(std::vector<int32_t>(D->rowcap_h[sd]), &D->rowcap[sd]);
+    add32(std::move(io), &D->iota[sd]);
+    add32(std::move(ll), &D->leaf_list[sd]);
+    add64(std::move(cmo), &D->cmoff[sd]);
+    add64(std::move(ro), &D->Roff[sd]);
+    add64(std::move(qo), &D->Qoff[sd]);
+    add64(std::move(xo), &D->Xoff[sd]);
+    add64(std::move(ho), &D->hoff[sd]);
+    add32(std::vector<int32_t>(S.gcol), &D->gcol[sd]);
+    add32(std::vector<int32_t>(S.gblk), &D->gblk[sd]);
+  }
+  // blocks
+  const int64_t nb = (int64_t)tr.blocks.size();
+  std::vector<int32_t> bt(nb), bs(nb), ba(nb), bpr(nb), bpc(nb), bo(nb), adm, inadm;
+  std::vector<int64_t> noff(nb, 0), soffs(nb, 0);
+  int64_t S_e = 0, N_e = 0;
+  for (int64_t b = 0; b < nb; ++b) {
+    const Block& B = tr.blocks[b];
+    bt[b] = B.t;
+    bs[b] = B.s;
+    ba[b] = B.adm;
+    bpr[b] = (int32_t)tr.side[0].block_pair[b];
+    bpc[b] = (int32_t)tr.side[1].block_pair[b];
+    bo[b] = (int32_t)tr.side[0].block_off[b];
+    if (B.adm) {
+      adm.push_back((int32_t)b);
+      soffs[b] = S_e;
+      S_e += (int64_t)D->kcap_h[0][bpr[b]] * D->kcap_h[1][bpc[b]];
+    } else {
+      inadm.push_back((int32_t)b);
+      noff[b] = N_e;
+      N_e += (int64_t)tr.size[B.t] * tr.size[B.s];
+    }
+  }
+  D->S_elems = S_e;
+  D->near_elems = N_e;
+  D->nadm = (int64_t)adm.size();
+  D->ninadm = (int64_t)inadm.size();
+  D->Soff_h = soffs;
+  add32(std::move(bt), &D->bt);
+  add32(std::move(bs), &D->bs);
+  add32(std::move(ba), &D->badm);
+  add32(std::move(bpr), &D->bpair[0]);
+  add32(std::move(bpc), &D->bpair[1]);
+  add32(std::move(bo), &D->boff_row);
+  add64(std::move(noff), &D->near_off);
+  add64(std::move(soffs), &D->Soff);
+  add32(std::move(adm), &D->adm_list);
+  add32(std::move(inadm), &D->inadm_list);
+  // row-side matvec lists: own blocks and father pairs per pair
+  {
+    Side& S = tr.side[0];
+    const int64_t np = (int64_t)S.pairs.size();
+    std::vector<int64_t> optr(np + 1, 0), pptr(np + 1, 0);
+    std::vector<int32_t> oblk, ppair, pson;
+    for (int64_t p = 0; p < np; ++p) {
+      for (int32_t b : S.pairs[p].own) oblk.push_back(b);
+      optr[p + 1] = (int64_t)oblk.size();
+      for (auto& seg : S.pairs[p].parents) {
+        const int64_t fp = seg.first;
+        ppair.push_back((int32_t)fp);
+        pson.push_back(S.pairs[fp].son_pair[0] == p ? 0 : 1);
+      }
+      pptr[p + 1] = (int64_t)ppair.size();
+    }
+    add64(std::move(optr), &D->own_ptr);
+    add64(std::move(pptr), &D->par_ptr);
+    add32(std::move(oblk), &D->own_blk);
+    add32(std::move(ppair), &D->par_pair);
+    add32(std::move(pson), &D->par_son);
+  }
+  // launch codes: all leaf pairs of both sides, costliest first; then non-leaf
+  // pairs per level
+  {
+    std::vector<std::pair<double, int32_t>> lc;
+    for (int sd = 0; sd < 2; ++sd)
+      for (int64_t p : tr.side[sd].leaf_pairs) {
+        const double m = tr.size[tr.side[sd].pairs[p].cluster];
+        lc.push_back({-(m * m * (double)tr.side[sd].pairs[p].ncols), (int32_t)((sd << 30) | (int32_t)p)});
+      }
+    std::stable_sort(lc.begin(), lc.end(),
+                     [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+                       return a.first < b.first;
+                     });
+    std::vector<int32_t> codes;
+    for (auto& x : lc) codes.push_back(x.second);
+    D->nleaf_codes = (int64_t)codes.size();
+    D->nl_code_begin.assign(tr.depth + 1, 0);
+    D->nl_code_count.assign(tr.depth + 1, 0);
+    D->nl_rowcap_max.assign(tr.depth + 1, 0);
+    for (int l = tr.depth; l >= 0; --l) {
+      D->nl_code_begin[l] = (int64_t)codes.size();
+      for (int sd = 0; sd < 2; ++sd)
+        for (int64_t p : tr.side[sd].nonleaf_by_level[l]) {
+          codes.push_back((int32_t)((sd << 30) | (int32_t)p));
+          D->nl_rowcap_max[l] = std::max(D->nl_rowcap_max[l], D->rowcap_h[sd][p]);
+        }
+      D->nl_code_count[l] = (int64_t)codes.size() - D->nl_code_begin[l];
+    }
+    add32(std::move(codes), &D->codes);
+  }
+  size_t total = 0;
+  for (auto& b : bufs) total += align256(std::max<size_t>(b.bytes, 4));
+  if (cudaMalloc(&D->arena, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete D;
+    return DH2_ENOMEM;
+  }
+  size_t off = 0;
+  for (auto& b : bufs) {
+    *b.dst = (char*)D->arena + off;
+    if (b.bytes && cudaMemcpy(*b.dst, b.src, b.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(D->arena);
+      delete D;
+      return DH2_ECUDA;
+    }
+    off += align256(std::max<size_t>(b.bytes, 4));
+  }
+  tr.dev = D;
+  return DH2_OK;
+}
+
+dh2_status ensure_device(Tree& tr, int dev) {
+  if (tr.dev) return tr.dev_id == dev ? DH2_OK : DH2_EINVAL;
+  const dh2_status s = upload_tree(tr);
+  if (s == DH2_OK) tr.dev_id = dev;
+  return s;
+}
+
+void set_pool_threshold(int dev) {
+  static int done[64] = {0};
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done[dev] = 1;
+}
+
+template <typename T>
+SideView<T> side_view(const Tree& tr, const dh2_matrix* M, int sd) {
+  const Tree::Dev* D = tr.dev;
+  SideView<T> v;
+  v.cluster = D->cluster[sd];
+  v.leaf = D->leaf[sd];
+  v.son = D->son[sd];
+  v.rowcap = D->rowcap[sd];
+  v.kcap = D->kcap[sd];
+  v.Roff = D->Roff[sd];
+  v.Qoff = D->Qoff[sd];
+  v.Xoff = D->Xoff[sd];
+  v.cstart = D->cstart;
+  v.csize = D->csize;
+  v.rank = M->rank[sd];
+  v.R = (C2<T>*)M->R[sd];
+  v.Q = (C2<T>*)M->Q[sd];
+  v.X = (C2<T>*)M->X[sd];
+  return v;
+}
+
+int even_up(int x) { return x + (x & 1); }
+
+template <typename T>
+dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
+  Tree& tr = M->tree->tr;
+  Tree::Dev* D = tr.dev;
+  cudaStream_t st = M->stream;
+  const int pmax = sizeof(T) == 4 ? kPmaxF32 : kPmaxF64;
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) DH2_CUDA_TRY(cudaEventCreate(&ev[i]));
+  cudaEventRecord(ev[0], st);
+
+  NormsArgs<T> na;
+  na.G = (const C2<T>*)M->G;
+  na.ld = M->ld;
+  na.bt = D->bt;
+  na.bs = D->bs;
+  na.badm = D->badm;
+  na.cstart = D->cstart;
+  na.csize = D->csize;
+  na.clevel = D->clevel;
+  na.zpow = M->zpow;
+  na.invw = M->invw;
+  na.near = (C2<T>*)M->near;
+  na.near_off = D->near_off;
+  na.copy = M->nearfield_copy;
+  launch_norms_near<T>(na, (int)tr.blocks.size(), st);
+  cudaEventRecord(ev[1], st);
+
+  PairArgs<T> pa;
+  pa.order = D->codes;
+  for (int sd = 0; sd < 2; ++sd) {
+    pa.start[sd] = D->start[sd];
+    pa.m[sd] = D->m[sd];
+    pa.ncols[sd] = D->ncols[sd];
+    pa.cmoff[sd] = D->cmoff[sd];
+    pa.gcol[sd] = D->gcol[sd];
+    pa.gblk[sd] = D->gblk[sd];
+    pa.son[sd] = D->son[sd];
+    pa.sonoff[sd] = D->sonoff[sd];
+    pa.level[sd] = D->level[sd];
+    pa.kcap[sd] = D->kcap[sd];
+    pa.rowcap[sd] = D->rowcap[sd];
+    pa.Roff[sd] = D->Roff[sd];
+    pa.Qoff[sd] = D->Qoff[sd];
+    pa.R[sd] = (C2<T>*)M->R[sd];
+    pa.Q[sd] = (C2<T>*)M->Q[sd];
+    pa.sig[sd] = M->sig[sd];
+    pa.rank[sd] = M->rank[sd];
+  }
+  pa.G = (const C2<T>*)M->G;
+  pa.ld = M->ld;
+  pa.invw = M->invw;
+  pa.eps2 = M->eps2;
+  pa.max_sweeps = cp.max_sweeps > 0 ? cp.max_sweeps : 30;
+  pa.status = M->status;
+  // leaf step for every leaf pair of both sides in one launch
+  pa.P = even_up(std::max(2, D->max_leaf));
+  launch_pair_kernel<T>(pa, (int)D->nleaf_codes, false, st);
+  cudaEventRecord(ev[2], st);
+  // non-leaf steps, level by level from the leaves up
+  for (int l = tr.depth; l >= 0; --l) {
+    if (D->nl_code_count[l] == 0) continue;
+    PairArgs<T> pl = pa;
+    pl.order = D->codes + D->nl_code_begin[l];
+    pl.P = even_up(std::max(2, std::min(pmax, D->nl_rowcap_max[l])));
+    launch_pair_kernel<T>(pl, (int)D->nl_code_count[l], true, st);
+  }
+  cudaEventRecord(ev[3], st);
+  // expanded column bases for the projection
+  SideView<T> Vv = side_view<T>(tr, M, 0), Wv = side_view<T>(tr, M, 1);
+  for (int l = tr.depth; l >= 0; --l) {
+    const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
+    if (e > b) launch_expand<T>(Wv, D->iota[1] + b, (int)(e - b), st);
+  }
+  cudaEventRecord(ev[4], st);
+  ProjArgs<T> pj;
+  pj.V = Vv;
+  pj.W = Wv;
+  pj.adm_list = D->adm_list;
+  pj.bpair_row = D->bpair[0];
+  pj.bpair_col = D->bpair[1];
+  pj.boff_row = D->boff_row;
+  pj.bs = D->bs;
+  pj.csize = D->csize;
+  pj.invw = M->invw;
+  pj.S = (C2<T>*)M->S;
+  pj.Soff = D->Soff;
+  launch_project<T>(pj, (int)D->nadm, st);
+  cudaEventRecord(ev[5], st);
+  uint32_t status = 0;
+  cudaError_t e1 = cudaMemcpyAsync(&status, M->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaError_t e3 = cudaGetLastError();
+  for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&M->phase_ms[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return DH2_ECUDA;
+  if (status & kStatusTooLarge) return DH2_EUNSUPPORTED;
+  if (status & kStatusNoConv) return DH2_ENOCONV;
+  if (status & kStatusTimeout) return DH2_ETIMEOUT;
+  return DH2_OK;
+}
+
+void matrix_release(dh2_matrix* M) {
+  if (!M) return;
+  if (M->arena) {
+    cudaFreeAsync(M->arena, M->stream);
+    cudaGetLastError();
+  }
+  delete M;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dh2_status_string(dh2_status s) {
+  switch (s) {
+    case DH2_OK: return "ok";
+    case DH2_EINVAL: return "invalid argument";
+    case DH2_ENOMEM: return "out of memory";
+    case DH2_ECUDA: return "CUDA runtime error";
+    case DH2_ETIMEOUT: return "device wait timed out";
+    case DH2_ENOCONV: return "Jacobi SVD did not converge within the sweep cap";
+    case DH2_EUNSUPPORTED: return "size beyond a compiled limit";
+  }
+  return "unknown status";
+}
+
+const char* dh2_version(void) { return "dh2-gb300 0.1 (sm_103a)"; }
+
+dh2_status dh2_tree_build(const double* pts_xyz, int64_t n, const dh2_tree_params* params, dh2_tree** out) {
+  if (!out) return DH2_EINVAL;
+  *out = nullptr;
+  if (!params || !pts_xyz) return DH2_EINVAL;
+  dh2_tree* T = new (std::nothrow) dh2_tree();
+  if (!T) return DH2_ENOMEM;
+  dh2_status s;
+  try {
+    s = build_tree(pts_xyz, n, *params, T->tr);
+  } catch (const std::bad_alloc&) {
+    s = DH2_ENOMEM;
+  } catch (...) {
+    s = DH2_EINVAL;
+  }
+  if (s != DH2_OK) {
+    delete T;
+    return s;
+  }
+  *out = T;
+  return DH2_OK;
+}
+
+void dh2_tree_free(dh2_tree* T) {
+  if (!T) return;
+  if (T->tr.dev) {
+    cudaFree(T->tr.dev->arena);
+    cudaGetLastError();
+    delete T->tr.dev;
+  }
+  delete T;
+}
+
+dh2_status dh2_tree_stats_get(const dh2_tree* T, dh2_tree_stats* o) {
+  if (!T || !o) return DH2_EINVAL;
+  const Tree& tr = T->tr;
+  std::memset(o, 0, sizeof(*o));
+  o->n = tr.n;
+  o->depth = tr.depth;
+  o->nclusters = tr.nclusters();
+  o->nblocks = (int64_t)tr.blocks.size();
+  o->nadmissible = tr.nadm;
+  o->adm_fraction = tr.adm_fraction;
+  for (int sd = 0; sd < 2; ++sd) {
+    o->npairs[sd] = (int64_t)tr.side[sd].pairs.size();
+    o->nleafpairs[sd] = (int64_t)tr.side[sd].leaf_pairs.size();
+    o->ncolumns[sd] = tr.side[sd].ncols_total;
+    o->nleafcolumns[sd] = tr.side[sd].nleafcols;
+  }
+  o->max_leaf = tr.max_leaf;
+  for (auto& d : tr.dirs) o->ndirs_max = std::max<int32_t>(o->ndirs_max, (int32_t)(d.size() / 3));
+  return DH2_OK;
+}
+
+dh2_status dh2_tree_perm(const dh2_tree* T, int64_t* perm) {
+  if (!T || !perm) return DH2_EINVAL;
+  std::memcpy(perm, T->tr.perm.data(), sizeof(int64_t) * T->tr.perm.size());
+  return DH2_OK;
+}
+
+dh2_status dh2_tree_clusters(const dh2_tree* T, int32_t* start, int32_t* size, int32_t* level, int32_t* parent,
+                             int32_t* son0, int32_t* son1, double* lo, double* hi) {
+  if (!T) return DH2_EINVAL;
+  const Tree& tr = T->tr;
+  const size_t nc = (size_t)tr.nclusters();
+  if (start) std::memcpy(start, tr.start.data(), nc * 4);
+  if (size) std::memcpy(size, tr.size.data(), nc * 4);
+  if (level) std::memcpy(level, tr.level.data(), nc * 4);
+  if (parent) std::memcpy(parent, tr.parent.data(), nc * 4);
+  if (son0) std::memcpy(son0, tr.son0.data(), nc * 4);
+  if (son1) std::memcpy(son1, tr.son1.data(), nc * 4);
+  if (lo) std::memcpy(lo, tr.lo.data(), nc * 24);
+  if (hi) std::memcpy(hi, tr.hi.data(), nc * 24);
+  return DH2_OK;
+}
+
+dh2_status dh2_tree_ndirs(const dh2_tree* T, int32_t level, int32_t* ndirs) {
+  if (!T || !ndirs || level < 0 || level > T->tr.depth) return DH2_EINVAL;
+  *ndirs = (int32_t)(T->tr.dirs[level].size() / 3);
+  return DH2_OK;
+}
+
+dh2_status dh2_tree_directions(const dh2_tree* Tc, int32_t level, double* dirs, int32_t* sd) {
+  if (!Tc || level < 0 || level > Tc->tr.depth) return DH2_EINVAL;
+  Tree& tr = const_cast<dh2_tree*>(Tc)->tr;
+  const size_t nd = tr.dirs[level].size() / 3;
+  if (dirs) std::memcpy(dirs, tr.dirs[level].data(), nd * 24);
+  if (sd)
+    for (size_t c = 0; c < nd; ++c) sd[c] = level < tr.depth ? tr.sd_of(level, (int32_t)c) : -1;
+  return DH2_OK;
+}
+
+dh2_status dh2_tree_blocks(const dh2_tree* T, int32_t* t, int32_t* s, int32_t* adm, int32_t* cb) {
+  if (!T) return DH2_EINVAL;
+  const Tree& tr = T->tr;
+  for (size_t b = 0; b < tr.blocks.size(); ++b) {
+    if (t) t[b] = tr.blocks[b].t;
+    if (s) s[b] = tr.blocks[b].s;
+    if (adm) adm[b] = tr.blocks[b].adm;
+    if (cb) cb[b] = tr.blocks[b].cb;
+  }
+  return DH2_OK;
+}
+
+dh2_status dh2_tree_pairs(const dh2_tree* T, int32_t side, int32_t* cluster, int32_t* dir, int64_t* ncols,
+                          int32_t* is_leaf) {
+  if (!T || (side != 0 && side != 1)) return DH2_EINVAL;
+  const Side& S = T->tr.side[side];
+  for (size_t p = 0; p < S.pairs.size(); ++p) {
+    if (cluster) cluster[p] = S.pairs[p].cluster;
+    if (dir) dir[p] = S.pairs[p].dir;
+    if (ncols) ncols[p] = S.pairs[p].ncols;
+    if (is_leaf) is_leaf[p] = S.pairs[p].leaf;
+  }
+  return DH2_OK;
+}
+
+dh2_status dh2_tree_pair_blocks(const dh2_tree* T, int32_t side, int64_t* offsets, int32_t* block_ids) {
+  if (!T || (side != 0 && side != 1) || !offsets) return DH2_EINVAL;
+  const Side& S = T->tr.side[side];
+  std::vector<int32_t> tmp;
+  std::function<void(int64_t)> emit = [&](int64_t p) {
+    for (int32_t b : S.pairs[p].own) tmp.push_back(b);
+    for (auto& seg : S.pairs[p].parents) emit(seg.first);
+  };
+  int64_t off = 0;
+  for (size_t p = 0; p < S.pairs.size(); ++p) {
+    tmp.clear();
+    emit((int64_t)p);
+    offsets[p] = off;
+    if (block_ids) std::memcpy(block_ids + off, tmp.data(), tmp.size() * 4);
+    off += (int64_t)tmp.size();
+  }
+  offsets[S.pairs.size()] = off;
+  return DH2_OK;
+}
+
+dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld,
+                        const dh2_compress_params* params, void* stream, dh2_matrix** out) {
+  if (!out) return DH2_EINVAL;
+  *out = nullptr;
+  if (!Tc || !G || !params) return DH2_EINVAL;
+  const dh2_compress_params& cp = *params;
+  if (ld < Tc->tr.n || !(cp.eps >= 0.0) || !(cp.zeta > 0.0 && cp.zeta < 1.0) || (cp.err_mode != 0 && cp.err_mode != 1) ||
+      (cp.nearfield != 0 && cp.nearfield != 1))
+    return DH2_EINVAL;
+  if (!((cp.mode == DH2_MODE_FP64 && dtype == DH2_C128) || (cp.mode == DH2_MODE_FP32 && dtype == DH2_C64)))
+    return DH2_EINVAL;
+  if (cp.err_mode == 0 && !(1.0 - 2.0 * cp.zeta * cp.zeta > 0.0)) return DH2_EINVAL;
+  dh2_tree* T = const_cast<dh2_tree*>(Tc);
+  Tree& tr = T->tr;
+  const int pmax = cp.mode == DH2_MODE_FP32 ? kPmaxF32 : kPmaxF64;
+  if (tr.max_leaf > pmax) return DH2_EUNSUPPORTED;
+  int dev = 0;
+  DH2_CUDA_TRY(cudaGetDevice(&dev));
+  set_pool_threshold(dev);
+  {
+    const dh2_status s = ensure_device(tr, dev);
+    if (s != DH2_OK) return s;
+  }
+  Tree::Dev* D = tr.dev;
+  dh2_matrix* M = new (std::nothrow) dh2_matrix();
+  if (!M) return DH2_ENOMEM;
+  M->tree = T;
+  M->device = dev;
+  M->mode = cp.mode;
+  M->dtype = dtype;
+  M->es = dtype == DH2_C128 ? 16 : 8;
+  M->stream = (cudaStream_t)stream;
+  M->G = G;
+  M->ld = ld;
+  M->nearfield_copy = cp.nearfield == 0 ? 1 : 0;
+  const size_t es = M->es;
+  const int nl = tr.depth + 1;
+  size_t sz[20];
+  int ns = 0;
+  sz[ns++] = align256(es * D->R_elems[0]);
+  sz[ns++] = align256(es * D->R_elems[1]);
+  sz[ns++] = align256(es * D->Q_elems[0]);
+  sz[ns++] = align256(es * D->Q_elems[1]);
+  sz[ns++] = align256(es * D->X_elems[0]);
+  sz[ns++] = align256(es * D->X_elems[1]);
+  sz[ns++] = align256(es * D->S_elems);
+  sz[ns++] = align256(M->nearfield_copy ? es * D->near_elems : 0);
+  sz[ns++] = align256(8 * kSigStride * D->npairs[0]);
+  sz[ns++] = align256(8 * kSigStride * D->npairs[1]);
+  sz[ns++] = align256(4 * D->npairs[0]);
+  sz[ns++] = align256(4 * D->npairs[1]);
+  sz[ns++] = align256(8 * tr.blocks.size());
+  sz[ns++] = align256(8 * nl);
+  sz[ns++] = align256(8 * nl);
+  sz[ns++] = align256(16);
+  sz[ns++] = align256(16);
+  size_t total = 0;
+  for (int i = 0; i < ns; ++i) total += sz[i];
+  if (cudaMallocAsync(&M->arena, total, M->stream) != cudaSuccess) {
+    cudaGetLastError();
+    delete M;
+    return DH2_ENOMEM;
+  }
+  M->arena_bytes = total;
+  char* p = (char*)M->arena;
+  void** dst[17] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
+                    (void**)&M->sig[0], (void**)&M->sig[1], (void**)&M->rank[0], (void**)&M->rank[1],
+                    (void**)&M->invw, (void**)&M->eps2, (void**)&M->zpow, (void**)&M->status, (void**)&M->acc};
+  for (int i = 0; i < ns; ++i) {
+    *dst[i] = p;
+    p += sz[i];
+  }
+  if (!M->nearfield_copy) M->near = nullptr;
+  // tolerances eps_l = eps_hat zeta^l (Remark "Error control")
+  const double eh =
+      cp.err_mode == 0 ? cp.eps * std::sqrt(1.0 - 2.0 * cp.zeta * cp.zeta) / std::sqrt(2.0) : cp.eps;
+  M->eps2_h.resize(nl);
+  M->zpow_h.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const double e = eh * std::pow(cp.zeta, (double)l);
+    M->eps2_h[l] = e * e;
+    M->zpow_h[l] = std::pow(cp.zeta, -(double)l);
+  }
+  cudaError_t ce = cudaMemcpyAsync(M->eps2, M->eps2_h.data(), 8 * nl, cudaMemcpyHostToDevice, M->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(M->zpow, M->zpow_h.data(), 8 * nl, cudaMemcpyHostToDevice, M->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(M->status, 0, 16, M->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(M->rank[0], 0, 4 * D->npairs[0], M->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(M->rank[1], 0, 4 * D->npairs[1], M->stream);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    matrix_release(M);
+    return DH2_ECUDA;
+  }
+  const dh2_status s = cp.mode == DH2_MODE_FP32 ? run_compress<float>(M, cp) : run_compress<double>(M, cp);
+  if (s != DH2_OK) {
+    matrix_release(M);
+    return s;
+  }
+  *out = M;
+  return DH2_OK;
+}
+
+void dh2_matrix_free(dh2_matrix* M) { matrix_release(M); }
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+dh2_status run_matvec(const dh2_matrix* M, const void* xv, void* yv, int nrhs, cudaStream_t st) {
+  Tree& tr = M->tree->tr;
+  Tree::Dev* D = tr.dev;
+  const int64_t n = tr.n;
+  void* buf = nullptr;
+  const size_t hx = align256(sizeof(C2<T>) * D->h_elems[1] * nrhs);
+  const size_t hy = align256(sizeof(C2<T>) * D->h_elems[0] * nrhs);
+  DH2_CUDA_TRY(cudaMallocAsync(&buf, hx + hy + 256, st));
+  C2<T>* xh = (C2<T>*)buf;
+  C2<T>* yh = (C2<T>*)((char*)buf + hx);
+  const C2<T>* x = (const C2<T>*)xv;
+  C2<T>* y = (C2<T>*)yv;
+  cudaMemsetAsync(y, 0, sizeof(C2<T>) * n * nrhs, st);
+  SideView<T> Vv = side_view<T>(tr, M, 0), Wv = side_view<T>(tr, M, 1);
+  // forward transformation (column basis), leaves then upwards
+  launch_mv_forward_leaf<T>(Wv, D->leaf_list[1], (int)D->nleaf[1], x, nrhs, n, xh, D->hoff[1], st);
+  for (int l = tr.depth; l >= 0; --l) {
+    const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
+    if (e > b) launch_mv_forward_up<T>(Wv, D->iota[1] + b, (int)(e - b), nrhs, xh, D->hoff[1], st);
+  }
+  MvArgs<T> a;
+  a.V = Vv;
+  a.W = Wv;
+  a.S = (const C2<T>*)M->S;
+  a.Soff = D->Soff;
+  a.own_ptr = D->own_ptr;
+  a.own_blk = D->own_blk;
+  a.bpair_col = D->bpair[1];
+  a.xh = xh;
+  a.xhoff = D->hoff[1];
+  a.yh = yh;
+  a.yhoff = D->hoff[0];
+  a.par_ptr = D->par_ptr;
+  a.par_pair = D->par_pair;
+  a.par_son = D->par_son;
+  a.bt = D->bt;
+  a.bs = D->bs;
+  a.near = (const C2<T>*)M->near;
+  a.near_off = D->near_off;
+  a.G = (const C2<T>*)M->G;
+  a.ld = M->ld;
+  launch_mv_coupling<T>(a, (int)D->npairs[0], nrhs, st);
+  // backward transformation, top-down
+  for (int l = 1; l <= tr.depth; ++l) {
+    const int64_t b = D->lvl_begin[0][l], e = D->lvl_end[0][l];
+    if (e > b) launch_mv_backward_down<T>(a, D->iota[0] + b, (int)(e - b), nrhs, st);
+  }
+  launch_mv_backward_leaf<T>(a, D->leaf_list[0], (int)D->nleaf[0], nrhs, y, n, st);
+  launch_mv_near<T>(a, D->inadm_list, (int)D->ninadm, nrhs, x, y, n, st);
+  cudaFreeAsync(buf, st);
+  DH2_CUDA_TRY(cudaGetLastError());
+  return DH2_OK;
+}
+
+template <typename T>
+dh2_status run_error(dh2_matrix* M, const void* Gref, dh2_dtype rdt, int64_t ldr, cudaStream_t st, double* rel) {
+  Tree& tr = M->tree->tr;
+  Tree::Dev* D = tr.dev;
+  SideView<T> Vv = side_view<T>(tr, M, 0), Wv = side_view<T>(tr, M, 1);
+  if (!M->v_expanded) {
+    for (int l = tr.depth; l >= 0; --l) {
+      const int64_t b = D->lvl_nl_begin[0][l], e = D->lvl_end[0][l];
+      if (e > b) launch_expand<T>(Vv, D->iota[0] + b, (int)(e - b), st);
+    }
+    M->v_expanded = true;
+  }
+  ErrArgs<T> a;
+  a.V = Vv;
+  a.W = Wv;
+  a.S = (const C2<T>*)M->S;
+  a.Soff = D->Soff;
+  a.bt = D->bt;
+  a.bs = D->bs;
+  a.badm = D->badm;
+  a.bpair_row = D->bpair[0];
+  a.bpair_col = D->bpair[1];
+  a.cstart = D->cstart;
+  a.csize = D->csize;
+  a.near = (const C2<T>*)M->near;
+  a.near_off = D->near_off;
+  a.G = (const C2<T>*)M->G;
+  a.ld = M->ld;
+  DH2_CUDA_TRY(cudaMemsetAsync(M->acc, 0, 16, st));
+  if (rdt == DH2_C128)
+    launch_error<T, double>(a, (const C2<double>*)Gref, ldr, (int)tr.blocks.size(), M->acc, st);
+  else
+    launch_error<T, float>(a, (const C2<float>*)Gref, ldr, (int)tr.blocks.size(), M->acc, st);
+  double h[2] = {0, 0};
+  DH2_CUDA_TRY(cudaMemcpyAsync(h, M->acc, 16, cudaMemcpyDeviceToHost, st));
+  DH2_CUDA_TRY(cudaStreamSynchronize(st));
+  *rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  return DH2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream) {
+  if (!M || !x || !y || nrhs < 1) return DH2_EINVAL;
+  return M->mode == DH2_MODE_FP32 ? run_matvec<float>(M, x, y, nrhs, (cudaStream_t)stream)
+                                  : run_matvec<double>(M, x, y, nrhs, (cudaStream_t)stream);
+}
+
+dh2_status dh2_error(const dh2_matrix* Mc, const void* G_ref, dh2_dtype ref_dtype, int64_t ld, void* stream,
+                     double* rel_err) {
+  if (!Mc || !G_ref || !rel_err || ld < Mc->tree->tr.n) return DH2_EINVAL;
+  dh2_matrix* M = const_cast<dh2_matrix*>(Mc);
+  return M->mode == DH2_MODE_FP32 ? run_error<float>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err)
+                                  : run_error<double>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err);
+}
+
+dh2_status dh2_matrix_ranks(const dh2_matrix* M, int32_t side, int32_t* ranks) {
+  if (!M || !ranks || (side != 0 && side != 1)) return DH2_EINVAL;
+  const int64_t np = M->tree->tr.dev->npairs[side];
+  DH2_CUDA_TRY(cudaMemcpyAsync(ranks, M->rank[side], 4 * np, cudaMemcpyDeviceToHost, M->stream));
+  DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_sigma(const dh2_matrix* M, int32_t side, int64_t pair, double* out, int32_t cap,
+                            int32_t* count) {
+  if (!M || !out || (side != 0 && side != 1)) return DH2_EINVAL;
+  const Tree& tr = M->tree->tr;
+  if (pair < 0 || pair >= (int64_t)tr.side[side].pairs.size()) return DH2_EINVAL;
+  const Pair& P = tr.side[side].pairs[pair];
+  int32_t rows = 0;
+  if (P.leaf) {
+    rows = tr.size[P.cluster];
+  } else {
+    int32_t k[2];
+    for (int j = 0; j < 2; ++j)
+      DH2_CUDA_TRY(cudaMemcpy(&k[j], M->rank[side] + P.son_pair[j], 4, cudaMemcpyDeviceToHost));
+    rows = k[0] + k[1];
+  }
+  const int32_t c = std::min(rows, std::min(cap, kSigStride));
+  DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  DH2_CUDA_TRY(cudaMemcpy(out, M->sig[side] + pair * kSigStride, 8 * (size_t)c, cudaMemcpyDeviceToHost));
+  if (count) *count = rows;
+  return DH2_OK;
+}
+
+namespace {
+dh2_status copy_complex_to_host(const void* src, size_t es, int64_t rows, int64_t cols, int64_t ld, double* out) {
+  std::vector<double> tmp((size_t)(2 * std::max<int64_t>(1, ld * cols)));
+  if (rows * cols == 0) return DH2_OK;
+  if (cudaMemcpy(tmp.data(), src, es * (size_t)(ld * (cols - 1) + rows), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    cudaGetLastError();
+    return DH2_ECUDA;
+  }
+  for (int64_t j = 0; j < cols; ++j)
+    for (int64_t i = 0; i < rows; ++i) {
+      const int64_t s = i + j * ld;
+      if (es == 16) {
+        out[2 * (i + j * rows)] = tmp[2 * s];
+        out[2 * (i + j * rows) + 1] = tmp[2 * s + 1];
+      } else {
+        const float* f = (const float*)tmp.data();
+        out[2 * (i + j * rows)] = f[2 * s];
+        out[2 * (i + j * rows) + 1] = f[2 * s + 1];
+      }
+    }
+  return DH2_OK;
+}
+}  // namespace
+
+dh2_status dh2_matrix_pair_basis(const dh2_matrix* M, int32_t side, int64_t pair, double* out, int64_t cap_elems,
+                                 int32_t* rows, int32_t* k) {
+  if (!M || !out || !rows || !k || (side != 0 && side != 1)) return DH2_EINVAL;
+  const Tree& tr = M->tree->tr;
+  if (pair < 0 || pair >= (int64_t)tr.side[side].pairs.size()) return DH2_EINVAL;
+  DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  const Pair& P = tr.side[side].pairs[pair];
+  int32_t kk = 0;
+  DH2_CUDA_TRY(cudaMemcpy(&kk, M->rank[side] + pair, 4, cudaMemcpyDeviceToHost));
+  int32_t r = 0;
+  if (P.leaf) {
+    r = tr.size[P.cluster];
+  } else {
+    int32_t k2[2];
+    for (int j = 0; j < 2; ++j)
+      DH2_CUDA_TRY(cudaMemcpy(&k2[j], M->rank[side] + P.son_pair[j], 4, cudaMemcpyDeviceToHost));
+    r = k2[0] + k2[1];
+  }
+  *rows = r;
+  *k = kk;
+  if ((int64_t)r * kk > cap_elems) return DH2_EINVAL;
+  const Tree::Dev* D = tr.dev;
+  const char* src = (const char*)M->Q[side] + M->es * D->Qoff_h[side][pair];
+  return copy_complex_to_host(src, M->es, r, kk, D->rowcap_h[side][pair], out);
+}
+
+dh2_status dh2_matrix_coupling(const dh2_matrix* M, int64_t block, double* out, int64_t cap_elems, int32_t* kt,
+                               int32_t* ks) {
+  if (!M || !out || !kt || !ks) return DH2_EINVAL;
+  const Tree& tr = M->tree->tr;
+  if (block < 0 || block >= (int64_t)tr.blocks.size() || !tr.blocks[block].adm) return DH2_EINVAL;
+  DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  int32_t a = 0, b = 0;
+  DH2_CUDA_TRY(cudaMemcpy(&a, M->rank[0] + tr.side[0].block_pair[block], 4, cudaMemcpyDeviceToHost));
+  DH2_CUDA_TRY(cudaMemcpy(&b, M->rank[1] + tr.side[1].block_pair[block], 4, cudaMemcpyDeviceToHost));
+  *kt = a;
+  *ks = b;
+  if ((int64_t)a * b > cap_elems) return DH2_EINVAL;
+  const char* src = (const char*)M->S + M->es * tr.dev->Soff_h[block];
+  return copy_complex_to_host(src, M->es, a, b, a, out);
+}
+
+dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts) {
+  if (!M || !total) return DH2_EINVAL;
+  const Tree& tr = M->tree->tr;
+  std::vector<int32_t> rk[2];
+  for (int sd = 0; sd < 2; ++sd) {
+    rk[sd].resize(tr.side[sd].pairs.size());
+    const dh2_status s = dh2_matrix_ranks(M, sd, rk[sd].data());
+    if (s != DH2_OK) return s;
+  }
+  double pr[6] = {0, 0, 0, 0, 0, 0};
+  for (int sd = 0; sd < 2; ++sd)
+    for (size_t p = 0; p < tr.side[sd].pairs.size(); ++p) {
+      const Pair& P = tr.side[sd].pairs[p];
+      if (P.leaf) pr[sd] += (double)tr.size[P.cluster] * rk[sd][p];
+      else pr[2 + sd] += (double)(rk[sd][P.son_pair[0]] + rk[sd][P.son_pair[1]]) * rk[sd][p];
+    }
+  for (size_t b = 0; b < tr.blocks.size(); ++b) {
+    const Block& B = tr.blocks[b];
+    if (B.adm) pr[4] += (double)rk[0][tr.side[0].block_pair[b]] * rk[1][tr.side[1].block_pair[b]];
+    else pr[5] += (double)tr.size[B.t] * tr.size[B.s];
+  }
+  double s = 0;
+  for (int i = 0; i < 6; ++i) {
+    s += pr[i];
+    if (parts) parts[i] = pr[i];
+  }
+  *total = s;
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms5) {
+  if (!M || !ms5) return DH2_EINVAL;
+  for (int i = 0; i < 5; ++i) ms5[i] = M->phase_ms[i];
+  return DH2_OK;
+}
+
+}  // extern "C"

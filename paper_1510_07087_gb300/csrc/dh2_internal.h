@@ -1,0 +1,95 @@
+// Internal structures shared by the host code (tree builder, C ABI) and the
+// CUDA kernels.  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dh2.h"
+
+namespace dh2 {
+
+constexpr int kSideRow = 0;
+constexpr int kSideCol = 1;
+
+// Largest number of rows of a factor (leaf cluster size, or k_t1c' + k_t2c'
+// for a non-leaf pair) the pair kernels accept, per real type.
+constexpr int kPmaxF32 = 128;
+constexpr int kPmaxF64 = 96;
+// Singular values stored per pair (the largest factor size).
+constexpr int kSigStride = 128;
+
+// Device status bits (OR-ed by kernels into one word).
+constexpr uint32_t kStatusNoConv = 1u;
+constexpr uint32_t kStatusTooLarge = 2u;
+constexpr uint32_t kStatusTimeout = 4u;
+
+struct Block {
+  int32_t t, s;
+  int32_t adm;
+  int32_t cb;
+};
+
+// One used (cluster, direction) pair of one side.
+struct Pair {
+  int32_t cluster;
+  int32_t dir;
+  int32_t level;
+  int32_t leaf;
+  int64_t ncols;                    // #F_tc
+  std::vector<int32_t> own;         // own admissible blocks, column order
+  // parent segments: (parent pair id, column offset of that segment in this pair)
+  std::vector<std::pair<int64_t, int64_t>> parents;
+  int64_t son_pair[2] = {-1, -1};   // non-leaf: pairs (t_j, sd(c))
+  int64_t son_off[2] = {0, 0};      // column offset of this pair's columns inside the son pair
+};
+
+struct Side {
+  std::vector<Pair> pairs;                      // ordered by level descending, leaves first per level
+  std::vector<int64_t> level_begin;             // depth+2 entries: pairs of level l in [begin[d-l].. ) (see tree.cpp)
+  std::vector<int64_t> leaf_pairs;              // ids of leaf pairs
+  std::vector<std::vector<int64_t>> nonleaf_by_level;  // per level l: non-leaf pair ids
+  std::vector<int64_t> block_pair;              // per block: pair id of this side (-1 if inadmissible)
+  std::vector<int64_t> block_off;               // per block: column offset of the block in its own pair
+  // leaf column maps (concatenated over leaf pairs): G index of the column and block id
+  std::vector<int64_t> leaf_colmap_off;         // per pair (only leaf pairs meaningful), npairs+1
+  std::vector<int32_t> gcol;
+  std::vector<int32_t> gblk;
+  int64_t ncols_total = 0, nleafcols = 0;
+};
+
+struct Tree {
+  int64_t n = 0;
+  dh2_tree_params params{};
+  std::vector<int64_t> perm;
+  std::vector<int32_t> start, size, level, parent, son0, son1;
+  std::vector<double> lo, hi, center, diam;  // 3 per cluster for lo/hi/center
+  int32_t depth = 0;
+  std::vector<double> delta;
+  std::vector<std::vector<double>> dirs;     // per level, 3 * |D_l|
+  std::vector<std::vector<int32_t>> sd;      // per level, |D_l| (lazy, -2 = not computed)
+  std::vector<Block> blocks;
+  int64_t nadm = 0;
+  double adm_fraction = 0.0;
+  int32_t max_leaf = 0;
+  Side side[2];
+
+  int32_t sd_of(int32_t lvl, int32_t c);     // son map with lazy evaluation
+  int32_t nclusters() const { return (int32_t)start.size(); }
+  bool is_leaf(int32_t t) const { return son0[t] < 0; }
+
+  // device copies (uploaded on first use)
+  struct Dev;
+  Dev* dev = nullptr;
+  int dev_id = -1;
+};
+
+dh2_status build_tree(const double* pts, int64_t n, const dh2_tree_params& p, Tree& tr);
+void free_tree_device(Tree& tr);
+
+}  // namespace dh2
+
+struct dh2_tree {
+  dh2::Tree tr;
+};

@@ -1,0 +1,434 @@
+// Kernels around the per-pair factorisation: block norms and nearfield copy,
+// basis expansion by Eq. (nested), the projection S_b, the matrix-vector
+// product of Section 4 and the blockwise error.
+#include "dh2_internal.h"
+#include "dh2_ops.cuh"
+
+namespace dh2 {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ C2<T> czero() { return C2<T>{T(0), T(0)}; }
+template <typename T>
+__device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return C2<T>{a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return C2<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {  // a * conj(b)
+  return C2<T>{a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cconj(C2<T> a) { return C2<T>{a.re, -a.im}; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of one double (256 threads)
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;  // valid in thread 0
+}
+
+// Expanded basis of a pair: a leaf's stored Q (ld = cluster size) or the
+// expansion buffer of a non-leaf pair (ld = cluster size).
+template <typename T>
+__device__ __forceinline__ const C2<T>* xbasis(const SideView<T>& S, int pid) {
+  return S.leaf[pid] ? S.Q + S.Qoff[pid] : S.X + S.Xoff[pid];
+}
+
+// ---------------------------------------------------------------- norms / nearfield
+// One CTA per block of the block tree: |G_b|_F for an admissible block
+// (weight omega_b = |G_b|_F zeta^-level(t), Remark "Error control"); a copy of
+// G_b into the nearfield buffer for an inadmissible one.
+template <typename T>
+__global__ void __launch_bounds__(256) norms_near_kernel(NormsArgs<T> a) {
+  __shared__ double red[32];
+  const int b = blockIdx.x;
+  const int t = a.bt[b], s = a.bs[b];
+  const int mt = a.csize[t], ms = a.csize[s];
+  const int64_t t0 = a.cstart[t], s0 = a.cstart[s];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (a.badm[b]) {
+    T acc = T(0);
+    for (int j = warp; j < ms; j += nw) {
+      const C2<T>* col = a.G + (s0 + j) * a.ld + t0;
+      for (int r = lane; r < mt; r += 32) {
+        const C2<T> g = col[r];
+        acc += g.re * g.re + g.im * g.im;
+      }
+    }
+    const double tot = block_sum((double)acc, red);
+    if (threadIdx.x == 0) a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+  } else if (a.copy) {
+    C2<T>* out = a.near + a.near_off[b];
+    for (int j = warp; j < ms; j += nw) {
+      const C2<T>* col = a.G + (s0 + j) * a.ld + t0;
+      for (int r = lane; r < mt; r += 32) out[r + (int64_t)j * mt] = col[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- expansion
+// X_tc = [X_t1c' E_t1c ; X_t2c' E_t2c] (Eq. nested), one CTA per non-leaf pair.
+template <typename T>
+__global__ void __launch_bounds__(256) expand_kernel(SideView<T> S, const int32_t* pairs) {
+  const int pid = pairs[blockIdx.x];
+  const int k = S.rank[pid];
+  if (k == 0) return;
+  const int ldq = S.rowcap[pid];
+  const C2<T>* E = S.Q + S.Qoff[pid];
+  C2<T>* out = S.X + S.Xoff[pid];
+  const int ldo = S.csize[S.cluster[pid]];
+  int rowoff = 0, eoff = 0;
+  for (int j = 0; j < 2; ++j) {
+    const int sp = S.son[2 * pid + j];
+    const int kj = S.rank[sp];
+    const int mj = S.csize[S.cluster[sp]];
+    const C2<T>* W = xbasis(S, sp);
+    for (int idx = threadIdx.x; idx < mj * k; idx += blockDim.x) {
+      const int i = idx % mj, qq = idx / mj;
+      C2<T> acc = czero<T>();
+      for (int l = 0; l < kj; ++l) acc = cadd(acc, cmul(W[i + (int64_t)l * mj], E[eoff + l + (int64_t)qq * ldq]));
+      out[rowoff + i + (int64_t)qq * ldo] = acc;
+    }
+    rowoff += mj;
+    eoff += kj;
+  }
+}
+
+// ---------------------------------------------------------------- projection
+// S_b = omega_b R_tc|_b W_sc: R_tc|_b = V_tc^* G_b / omega_b is the block's
+// own column range of R_tc (Section 6), W_sc the expanded column basis.
+template <typename T>
+__global__ void __launch_bounds__(256) project_kernel(ProjArgs<T> a) {
+  __shared__ C2<T> Rs[64][17];
+  __shared__ C2<T> Ws[16][65];
+  const int b = a.adm_list[blockIdx.x];
+  const int Pt = a.bpair_row[b], Ps = a.bpair_col[b];
+  const int off = a.boff_row[b];
+  const int kt = a.V.rank[Pt], ks = a.W.rank[Ps];
+  C2<T>* Sout = a.S + a.Soff[b];
+  if (kt == 0 || ks == 0) return;
+  const int ms = a.csize[a.bs[b]];
+  const int ldr = a.V.kcap[Pt];
+  const C2<T>* R = a.V.R + a.V.Roff[Pt] + (int64_t)off * ldr;
+  const C2<T>* W = xbasis(a.W, Ps);
+  const T w = (T)(1.0 / a.invw[b]);
+  // kt, ks <= 128: tile the output in 64 x 64 pieces
+  for (int q0 = 0; q0 < kt; q0 += 64) {
+    for (int c0 = 0; c0 < ks; c0 += 64) {
+      const int tq = threadIdx.x & 63, tc = threadIdx.x >> 6;  // 64 x 4 threads, 16 outputs each
+      C2<T> acc[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc[u] = czero<T>();
+      for (int j0 = 0; j0 < ms; j0 += 16) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
+          const int qq = idx & 63, jj = idx >> 6;
+          Rs[qq][jj] = (q0 + qq < kt && j0 + jj < ms) ? R[q0 + qq + (int64_t)(j0 + jj) * ldr] : czero<T>();
+        }
+        for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
+          const int jj = idx & 15, cc = idx >> 4;
+          Ws[jj][cc] = (c0 + cc < ks && j0 + jj < ms) ? W[j0 + jj + (int64_t)(c0 + cc) * ms] : czero<T>();
+        }
+        __syncthreads();
+        for (int jj = 0; jj < 16; ++jj) {
+          const C2<T> r = Rs[tq][jj];
+#pragma unroll
+          for (int u = 0; u < 16; ++u) acc[u] = cadd(acc[u], cmul(r, Ws[jj][tc + 4 * u]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int qq = q0 + tq, cc = c0 + tc + 4 * u;
+        if (qq < kt && cc < ks) Sout[qq + (int64_t)cc * kt] = C2<T>{w * acc[u].re, w * acc[u].im};
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- matvec
+// forward transformation, leaves: xh_sc = W_sc^* x|_s (Eq. mvm1)
+template <typename T>
+__global__ void mv_forward_leaf(SideView<T> W, const int32_t* pairs, const C2<T>* x, int nrhs, int64_t n,
+                                C2<T>* xh, const int64_t* hoff) {
+  const int pid = pairs[blockIdx.x];
+  const int k = W.rank[pid];
+  const int m = W.csize[W.cluster[pid]];
+  const int64_t s0 = W.cstart[W.cluster[pid]];
+  const C2<T>* Q = W.Q + W.Qoff[pid];
+  for (int idx = threadIdx.x; idx < k * nrhs; idx += blockDim.x) {
+    const int qq = idx % k, rh = idx / k;
+    C2<T> acc = czero<T>();
+    for (int i = 0; i < m; ++i) acc = cadd(acc, cmulc(x[s0 + i + rh * n], Q[i + (int64_t)qq * m]));
+    xh[hoff[pid] * nrhs + qq + (int64_t)rh * k] = acc;
+  }
+}
+
+// forward transformation, non-leaves: xh_sc = sum_s' E_s'c^* xh_s'c'
+template <typename T>
+__global__ void mv_forward_up(SideView<T> W, const int32_t* pairs, int nrhs, C2<T>* xh, const int64_t* hoff) {
+  const int pid = pairs[blockIdx.x];
+  const int k = W.rank[pid];
+  const int ldq = W.rowcap[pid];
+  const C2<T>* E = W.Q + W.Qoff[pid];
+  for (int idx = threadIdx.x; idx < k * nrhs; idx += blockDim.x) {
+    const int qq = idx % k, rh = idx / k;
+    C2<T> acc = czero<T>();
+    int eoff = 0;
+    for (int j = 0; j < 2; ++j) {
+      const int sp = W.son[2 * pid + j];
+      const int kj = W.rank[sp];
+      const C2<T>* xs = xh + hoff[sp] * nrhs + (int64_t)rh * kj;
+      for (int l = 0; l < kj; ++l) acc = cadd(acc, cmulc(xs[l], E[eoff + l + (int64_t)qq * ldq]));
+      eoff += kj;
+    }
+    xh[hoff[pid] * nrhs + qq + (int64_t)rh * k] = acc;
+  }
+}
+
+// coupling: yh_tc = sum over own blocks b of S_b xh_{s c} (Eq. mvm2)
+template <typename T>
+__global__ void mv_coupling(MvArgs<T> a, int nrhs) {
+  const int pid = blockIdx.x;
+  const int kt = a.V.rank[pid];
+  for (int idx = threadIdx.x; idx < kt * nrhs; idx += blockDim.x) {
+    const int qq = idx % kt, rh = idx / kt;
+    C2<T> acc = czero<T>();
+    for (int64_t e = a.own_ptr[pid]; e < a.own_ptr[pid + 1]; ++e) {
+      const int b = a.own_blk[e];
+      const int Ps = a.bpair_col[b];
+      const int ks = a.W.rank[Ps];
+      const C2<T>* S = a.S + a.Soff[b];
+      const C2<T>* xs = a.xh + a.xhoff[Ps] * nrhs + (int64_t)rh * ks;
+      for (int l = 0; l < ks; ++l) acc = cadd(acc, cmul(S[qq + (int64_t)l * kt], xs[l]));
+    }
+    a.yh[a.yhoff[pid] * nrhs + qq + (int64_t)rh * kt] = acc;
+  }
+}
+
+// backward transformation: yh_t'c' += E_t'c yh_tc over the father pairs (t, c)
+// with sd(c) = c', gathered per son pair (figure "Fast forward and backward
+// transformation", right).
+template <typename T>
+__global__ void mv_backward_down(MvArgs<T> a, const int32_t* pairs, int nrhs) {
+  const int pid = pairs[blockIdx.x];
+  const int k = a.V.rank[pid];
+  for (int idx = threadIdx.x; idx < k * nrhs; idx += blockDim.x) {
+    const int qq = idx % k, rh = idx / k;
+    C2<T> acc = a.yh[a.yhoff[pid] * nrhs + qq + (int64_t)rh * k];
+    for (int64_t e = a.par_ptr[pid]; e < a.par_ptr[pid + 1]; ++e) {
+      const int fp = a.par_pair[e];
+      const int j = a.par_son[e];
+      const int kf = a.V.rank[fp];
+      const int ldq = a.V.rowcap[fp];
+      const int eoff = j == 0 ? 0 : a.V.rank[a.V.son[2 * fp]];
+      const C2<T>* E = a.V.Q + a.V.Qoff[fp];
+      const C2<T>* yf = a.yh + a.yhoff[fp] * nrhs + (int64_t)rh * kf;
+      for (int l = 0; l < kf; ++l) acc = cadd(acc, cmul(E[eoff + qq + (int64_t)l * ldq], yf[l]));
+    }
+    a.yh[a.yhoff[pid] * nrhs + qq + (int64_t)rh * k] = acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void catomic_add(C2<T>* p, C2<T> v) {
+  atomicAdd(&p->re, v.re);
+  atomicAdd(&p->im, v.im);
+}
+
+// leaves: y|_t += V_tc yh_tc (Eq. mvm3)
+template <typename T>
+__global__ void mv_backward_leaf(MvArgs<T> a, const int32_t* pairs, int nrhs, C2<T>* y, int64_t n) {
+  const int pid = pairs[blockIdx.x];
+  const int k = a.V.rank[pid];
+  if (k == 0) return;
+  const int m = a.V.csize[a.V.cluster[pid]];
+  const int64_t t0 = a.V.cstart[a.V.cluster[pid]];
+  const C2<T>* Q = a.V.Q + a.V.Qoff[pid];
+  for (int idx = threadIdx.x; idx < m * nrhs; idx += blockDim.x) {
+    const int i = idx % m, rh = idx / m;
+    const C2<T>* yh = a.yh + a.yhoff[pid] * nrhs + (int64_t)rh * k;
+    C2<T> acc = czero<T>();
+    for (int l = 0; l < k; ++l) acc = cadd(acc, cmul(Q[i + (int64_t)l * m], yh[l]));
+    catomic_add(y + t0 + i + rh * n, acc);
+  }
+}
+
+// nearfield: y|_t += G_b x|_s for inadmissible leaves
+template <typename T>
+__global__ void mv_near(MvArgs<T> a, const int32_t* blocks, int nrhs, const C2<T>* x, C2<T>* y, int64_t n) {
+  const int b = blocks[blockIdx.x];
+  const int t = a.bt[b], s = a.bs[b];
+  const int mt = a.V.csize[t], ms = a.V.csize[s];
+  const int64_t t0 = a.V.cstart[t], s0 = a.V.cstart[s];
+  const C2<T>* Gb;
+  int64_t ldb;
+  if (a.near) {
+    Gb = a.near + a.near_off[b];
+    ldb = mt;
+  } else {
+    Gb = a.G + s0 * a.ld + t0;
+    ldb = a.ld;
+  }
+  for (int idx = threadIdx.x; idx < mt * nrhs; idx += blockDim.x) {
+    const int i = idx % mt, rh = idx / mt;
+    C2<T> acc = czero<T>();
+    for (int j = 0; j < ms; ++j) acc = cadd(acc, cmul(Gb[i + (int64_t)j * ldb], x[s0 + j + rh * n]));
+    catomic_add(y + t0 + i + rh * n, acc);
+  }
+}
+
+// ---------------------------------------------------------------- error
+// sum over blocks of |G_ref - G~|_F^2 and |G_ref|_F^2 in FP64.
+template <typename T, typename RT>
+__global__ void __launch_bounds__(256) error_kernel(ErrArgs<T> a, const C2<RT>* Gref, int64_t ldr,
+                                                    double* acc_out) {
+  __shared__ double red[32];
+  __shared__ C2<double> Ts[128][17];
+  const int b = blockIdx.x;
+  const int t = a.bt[b], s = a.bs[b];
+  const int mt = a.csize[t], ms = a.csize[s];
+  const int64_t t0 = a.cstart[t], s0 = a.cstart[s];
+  double e2 = 0.0, r2 = 0.0;
+  if (!a.badm[b]) {
+    for (int idx = threadIdx.x; idx < mt * ms; idx += blockDim.x) {
+      const int i = idx % mt, j = idx / mt;
+      const C2<RT> g = Gref[(t0 + i) + (s0 + j) * ldr];
+      const C2<T> h = a.near ? a.near[a.near_off[b] + i + (int64_t)j * mt] : a.G[(t0 + i) + (s0 + j) * a.ld];
+      const double dr = (double)g.re - (double)h.re, di = (double)g.im - (double)h.im;
+      e2 += dr * dr + di * di;
+      r2 += (double)g.re * g.re + (double)g.im * g.im;
+    }
+  } else {
+    const int Pt = a.bpair_row[b], Ps = a.bpair_col[b];
+    const int kt = a.V.rank[Pt], ks = a.W.rank[Ps];
+    const C2<T>* Vt = xbasis(a.V, Pt);
+    const C2<T>* Wsb = xbasis(a.W, Ps);
+    const C2<T>* S = a.S + a.Soff[b];
+    for (int j0 = 0; j0 < ms; j0 += 16) {
+      const int cw = min(16, ms - j0);
+      __syncthreads();
+      // T = S W^* for columns j0..j0+cw (kt <= 128)
+      for (int idx = threadIdx.x; idx < kt * cw; idx += blockDim.x) {
+        const int qq = idx % kt, jj = idx / kt;
+        double ar = 0.0, ai = 0.0;
+        for (int l = 0; l < ks; ++l) {
+          const C2<T> sv = S[qq + (int64_t)l * kt];
+          const C2<T> wv = Wsb[j0 + jj + (int64_t)l * ms];
+          // s * conj(w)
+          ar += (double)sv.re * wv.re + (double)sv.im * wv.im;
+          ai += (double)sv.im * wv.re - (double)sv.re * wv.im;
+        }
+        Ts[qq][jj] = C2<double>{ar, ai};
+      }
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < mt * cw; idx += blockDim.x) {
+        const int i = idx % mt, jj = idx / mt;
+        double ar = 0.0, ai = 0.0;
+        for (int qq = 0; qq < kt; ++qq) {
+          const C2<T> v = Vt[i + (int64_t)qq * mt];
+          const C2<double> tv = Ts[qq][jj];
+          ar += (double)v.re * tv.re - (double)v.im * tv.im;
+          ai += (double)v.re * tv.im + (double)v.im * tv.re;
+        }
+        const C2<RT> g = Gref[(t0 + i) + (s0 + j0 + jj) * ldr];
+        const double dr = (double)g.re - ar, di = (double)g.im - ai;
+        e2 += dr * dr + di * di;
+        r2 += (double)g.re * g.re + (double)g.im * g.im;
+      }
+    }
+  }
+  const double se = block_sum(e2, red);
+  const double sr = block_sum(r2, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(acc_out, se);
+    atomicAdd(acc_out + 1, sr);
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_norms_near(const NormsArgs<T>& a, int nblocks, cudaStream_t st) {
+  if (nblocks > 0) norms_near_kernel<T><<<nblocks, 256, 0, st>>>(a);
+}
+template <typename T>
+void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream_t st) {
+  if (n > 0) expand_kernel<T><<<n, 256, 0, st>>>(S, pairs);
+}
+template <typename T>
+void launch_project(const ProjArgs<T>& a, int nadm, cudaStream_t st) {
+  if (nadm > 0) project_kernel<T><<<nadm, 256, 0, st>>>(a);
+}
+template <typename T>
+void launch_mv_forward_leaf(const SideView<T>& W, const int32_t* pairs, int np, const C2<T>* x, int nrhs,
+                            int64_t n, C2<T>* xh, const int64_t* hoff, cudaStream_t st) {
+  if (np > 0) mv_forward_leaf<T><<<np, 128, 0, st>>>(W, pairs, x, nrhs, n, xh, hoff);
+}
+template <typename T>
+void launch_mv_forward_up(const SideView<T>& W, const int32_t* pairs, int np, int nrhs, C2<T>* xh,
+                          const int64_t* hoff, cudaStream_t st) {
+  if (np > 0) mv_forward_up<T><<<np, 128, 0, st>>>(W, pairs, nrhs, xh, hoff);
+}
+template <typename T>
+void launch_mv_coupling(const MvArgs<T>& a, int npairs_row, int nrhs, cudaStream_t st) {
+  if (npairs_row > 0) mv_coupling<T><<<npairs_row, 128, 0, st>>>(a, nrhs);
+}
+template <typename T>
+void launch_mv_backward_down(const MvArgs<T>& a, const int32_t* pairs, int np, int nrhs, cudaStream_t st) {
+  if (np > 0) mv_backward_down<T><<<np, 128, 0, st>>>(a, pairs, nrhs);
+}
+template <typename T>
+void launch_mv_backward_leaf(const MvArgs<T>& a, const int32_t* pairs, int np, int nrhs, C2<T>* y, int64_t n,
+                             cudaStream_t st) {
+  if (np > 0) mv_backward_leaf<T><<<np, 128, 0, st>>>(a, pairs, nrhs, y, n);
+}
+template <typename T>
+void launch_mv_near(const MvArgs<T>& a, const int32_t* blocks, int nb, int nrhs, const C2<T>* x, C2<T>* y,
+                    int64_t n, cudaStream_t st) {
+  if (nb > 0) mv_near<T><<<nb, 128, 0, st>>>(a, blocks, nrhs, x, y, n);
+}
+template <typename T, typename RT>
+void launch_error(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int nblocks, double* acc,
+                  cudaStream_t st) {
+  if (nblocks > 0) error_kernel<T, RT><<<nblocks, 256, 0, st>>>(a, Gref, ldr, acc);
+}
+
+#define DH2_INST(T)                                                                                         \
+  template void launch_norms_near<T>(const NormsArgs<T>&, int, cudaStream_t);                              \
+  template void launch_expand<T>(const SideView<T>&, const int32_t*, int, cudaStream_t);                   \
+  template void launch_project<T>(const ProjArgs<T>&, int, cudaStream_t);                                  \
+  template void launch_mv_forward_leaf<T>(const SideView<T>&, const int32_t*, int, const C2<T>*, int,      \
+                                          int64_t, C2<T>*, const int64_t*, cudaStream_t);                  \
+  template void launch_mv_forward_up<T>(const SideView<T>&, const int32_t*, int, int, C2<T>*,              \
+                                        const int64_t*, cudaStream_t);                                     \
+  template void launch_mv_coupling<T>(const MvArgs<T>&, int, int, cudaStream_t);                           \
+  template void launch_mv_backward_down<T>(const MvArgs<T>&, const int32_t*, int, int, cudaStream_t);      \
+  template void launch_mv_backward_leaf<T>(const MvArgs<T>&, const int32_t*, int, int, C2<T>*, int64_t,    \
+                                           cudaStream_t);                                                  \
+  template void launch_mv_near<T>(const MvArgs<T>&, const int32_t*, int, int, const C2<T>*, C2<T>*,        \
+                                  int64_t, cudaStream_t);                                                  \
+  template void launch_error<T, float>(const ErrArgs<T>&, const C2<float>*, int64_t, int, double*,        \
+                                       cudaStream_t);                                                      \
+  template void launch_error<T, double>(const ErrArgs<T>&, const C2<double>*, int64_t, int, double*,      \
+                                        cudaStream_t);
+
+DH2_INST(float)
+DH2_INST(double)
+
+}  // namespace dh2

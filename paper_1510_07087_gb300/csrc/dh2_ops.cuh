@@ -1,0 +1,121 @@
+// Argument structures of the kernels around the per-pair factorisation.
+#pragma once
+
+#include "dh2_kernels.cuh"
+
+namespace dh2 {
+
+// Device view of one side's pairs and outputs.
+template <typename T>
+struct SideView {
+  const int32_t* cluster;  // per pair
+  const int32_t* leaf;     // per pair
+  const int32_t* son;      // 2 per pair
+  const int32_t* rowcap;   // per pair, ld of stored Q / [E1;E2]
+  const int32_t* kcap;     // per pair, ld of R
+  const int64_t* Roff;
+  const int64_t* Qoff;
+  const int64_t* Xoff;     // expansion buffer offsets (non-leaf pairs)
+  const int32_t* cstart;   // per cluster
+  const int32_t* csize;    // per cluster
+  const int32_t* rank;     // per pair
+  C2<T>* R;
+  C2<T>* Q;
+  C2<T>* X;
+};
+
+template <typename T>
+struct NormsArgs {
+  const C2<T>* G;
+  int64_t ld;
+  const int32_t* bt;
+  const int32_t* bs;
+  const int32_t* badm;
+  const int32_t* cstart;
+  const int32_t* csize;
+  const int32_t* clevel;
+  const double* zpow;      // zeta^-level
+  double* invw;            // per block 1/omega_b
+  C2<T>* near;
+  const int64_t* near_off;
+  int copy;
+};
+
+template <typename T>
+struct ProjArgs {
+  SideView<T> V, W;
+  const int32_t* adm_list;
+  const int32_t* bpair_row;
+  const int32_t* bpair_col;
+  const int32_t* boff_row;
+  const int32_t* bs;
+  const int32_t* csize;
+  const double* invw;
+  C2<T>* S;
+  const int64_t* Soff;
+};
+
+template <typename T>
+struct MvArgs {
+  SideView<T> V, W;
+  const C2<T>* S;
+  const int64_t* Soff;
+  const int64_t* own_ptr;   // row pairs: own blocks (CSR)
+  const int32_t* own_blk;
+  const int32_t* bpair_col;
+  const C2<T>* xh;
+  const int64_t* xhoff;     // column pairs
+  C2<T>* yh;
+  const int64_t* yhoff;     // row pairs
+  const int64_t* par_ptr;   // row pairs: father pairs (CSR)
+  const int32_t* par_pair;
+  const int32_t* par_son;
+  const int32_t* bt;
+  const int32_t* bs;
+  const C2<T>* near;
+  const int64_t* near_off;
+  const C2<T>* G;
+  int64_t ld;
+};
+
+template <typename T>
+struct ErrArgs {
+  SideView<T> V, W;
+  const C2<T>* S;
+  const int64_t* Soff;
+  const int32_t* bt;
+  const int32_t* bs;
+  const int32_t* badm;
+  const int32_t* bpair_row;
+  const int32_t* bpair_col;
+  const int32_t* cstart;
+  const int32_t* csize;
+  const C2<T>* near;
+  const int64_t* near_off;
+  const C2<T>* G;
+  int64_t ld;
+};
+
+template <typename T> void launch_norms_near(const NormsArgs<T>& a, int nblocks, cudaStream_t st);
+template <typename T> void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream_t st);
+template <typename T> void launch_project(const ProjArgs<T>& a, int nadm, cudaStream_t st);
+template <typename T>
+void launch_mv_forward_leaf(const SideView<T>& W, const int32_t* pairs, int np, const C2<T>* x, int nrhs,
+                            int64_t n, C2<T>* xh, const int64_t* hoff, cudaStream_t st);
+template <typename T>
+void launch_mv_forward_up(const SideView<T>& W, const int32_t* pairs, int np, int nrhs, C2<T>* xh,
+                          const int64_t* hoff, cudaStream_t st);
+template <typename T> void launch_mv_coupling(const MvArgs<T>& a, int npairs_row, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_mv_backward_down(const MvArgs<T>& a, const int32_t* pairs, int np, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_mv_backward_leaf(const MvArgs<T>& a, const int32_t* pairs, int np, int nrhs, C2<T>* y, int64_t n,
+                             cudaStream_t st);
+template <typename T>
+void launch_mv_near(const MvArgs<T>& a, const int32_t* blocks, int nb, int nrhs, const C2<T>* x, C2<T>* y,
+                    int64_t n, cudaStream_t st);
+template <typename T, typename RT>
+void launch_error(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int nblocks, double* acc,
+                  cudaStream_t st);
+
+}  // namespace dh2

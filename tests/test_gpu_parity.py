@@ -1,0 +1,261 @@
+"""GPU path against the FP64 oracle, through the C ABI.
+
+Parity rules (ranks, subspaces and products are compared; Q, E and S are
+unique only up to unitary changes and are never compared entrywise):
+  * FP64 mode: ranks equal to the oracle's except at truncation ties
+    (|sum_{i>=k} sigma_i^2 - eps_l^2| <= 1e-8 eps_l^2 for a k between the two);
+    with the oracle re-run at the GPU's ranks, y = G~ x agrees to 1e-11
+    relative for three seeded right-hand sides;
+  * FP32 mode (complex64 input): at most a few percent of the ranks differ by
+    at most 2, the matrix-vector product agrees with the FP64 oracle at the
+    GPU's ranks to 20 eps relative, and |G - G~|_F <= eps |G|_F holds against
+    the complex128 matrix.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dh2_oracle as O
+from synth import fibonacci_sphere, helmholtz_matrix, planted_separable_matrix, random_complex_vectors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1510_07087_gb300 as D
+    return D
+
+
+def _colmajor(G: np.ndarray, dtype):
+    # column-major device copy: memory of G^T row-major == G column-major
+    return torch.from_numpy(np.ascontiguousarray(G.T)).to(device="cuda", dtype=dtype).t()
+
+
+class Case:
+    def __init__(self, n, kappa, leaf, eps, mode, eta1=2 * math.sqrt(2), eta2=1.0, G=None, dir_rule=0,
+                 nearfield=0):
+        D = _dev()
+        self.D = D
+        pts = fibonacci_sphere(n)
+        self.tp = O.TreeParams(leaf_size=leaf, kappa=kappa, eta1=eta1, eta2=eta2, dir_rule=dir_rule)
+        self.cp = O.CompressParams(eps=eps)
+        self.tr = O.build_tree(pts, self.tp)
+        if G is None:
+            G = helmholtz_matrix(pts, kappa)
+        self.G = G[np.ix_(self.tr.perm, self.tr.perm)]
+        self.T = D.dh2_tree_build(pts, leaf, kappa, eta1, eta2, dir_rule)
+        assert np.array_equal(self.T.perm(), self.tr.perm)
+        dt = torch.complex64 if mode == D.MODE_FP32 else torch.complex128
+        self.Gd = _colmajor(self.G, dt)
+        self.mode = mode
+        self.M = D.dh2_compress(self.T, self.Gd, eps=eps, mode=mode, nearfield=nearfield)
+        self.rank = {}
+        for side in (0, 1):
+            pr = self.T.pairs(side)
+            rk = self.M.ranks(side)
+            self.rank[side] = {(int(pr["cluster"][p]), int(pr["dir"][p])): int(rk[p]) for p in range(len(rk))}
+            self.pid = getattr(self, "pid", {})
+            for p in range(len(rk)):
+                self.pid[(side, int(pr["cluster"][p]), int(pr["dir"][p]))] = p
+        w = O.block_weights(self.tr, O.block_norms(self.tr, self.G), self.cp.zeta)
+        self.w = w
+        self.V = O.compress(self.tr, self.G, self.cp, "row", w)
+        self.W = O.compress(self.tr, self.G, self.cp, "col", w)
+        self.Vg = O.compress(self.tr, self.G, self.cp, "row", w, rank_override=self.rank[0])
+        self.Wg = O.compress(self.tr, self.G, self.cp, "col", w, rank_override=self.rank[1])
+        self.Sg = O.project(self.tr, self.G, self.Vg, self.Wg)
+
+    def gpu_matvec(self, x: np.ndarray) -> np.ndarray:
+        dt = self.Gd.dtype
+        xd = torch.from_numpy(np.ascontiguousarray(x.T)).to(device="cuda", dtype=dt).t()
+        yd = torch.empty_like(xd.t().contiguous()).t()
+        self.D.dh2_matvec(self.M, xd, yd)
+        torch.cuda.synchronize()
+        return yd.cpu().numpy().astype(np.complex128)
+
+
+def _tie(sig, k1, k2, eps2, tol):
+    s2 = np.concatenate([np.asarray(sig, dtype=np.float64) ** 2, [0.0]])
+    tails = np.cumsum(s2[::-1])[::-1]
+    lo, hi = min(k1, k2), max(k1, k2)
+    return any(abs(tails[min(k, len(tails) - 1)] - eps2) <= tol * eps2 for k in range(lo, hi + 1))
+
+
+def _rank_report(c: Case, tol):
+    bad, ties, total = 0, 0, 0
+    for side, B in ((0, c.V), (1, c.W)):
+        for key, ko in B.rank.items():
+            kg = c.rank[side][key]
+            total += 1
+            if kg != ko:
+                if _tie(B.sigma[key], kg, ko, B.eps_level[c.tr.level[key[0]]] ** 2, tol):
+                    ties += 1
+                else:
+                    bad += 1
+    return bad, ties, total
+
+
+def _fp64(n, kappa, leaf, eps, **kw):
+    D = _dev()
+    return Case(n, kappa, leaf, eps, D.MODE_FP64, **kw)
+
+
+def _fp32(n, kappa, leaf, eps, **kw):
+    D = _dev()
+    return Case(n, kappa, leaf, eps, D.MODE_FP32, **kw)
+
+
+@pytest.fixture(scope="module")
+def c1_fp64():
+    return _fp64(2048, 4.0, 32, 1e-4)
+
+
+@pytest.fixture(scope="module")
+def c1_fp32():
+    return _fp32(2048, 4.0, 32, 1e-4)
+
+
+def _check_fp64(c: Case, mv_tol=1e-11):
+    bad, ties, total = _rank_report(c, 1e-8)
+    assert bad == 0, f"{bad} rank mismatches outside ties ({ties} ties) of {total}"
+    x = random_complex_vectors(c.tr.n, 3, seed=11)
+    y_ref = O.matvec(c.tr, c.G, c.Vg, c.Wg, c.Sg, x)
+    y = c.gpu_matvec(x)
+    rel = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
+    assert rel <= mv_tol, rel
+    err_gpu = c.D.dh2_error(c.M, c.Gd)
+    err_ora = O.error_fro(c.tr, c.G, c.Vg, c.Wg, c.Sg)
+    assert err_gpu <= c.cp.eps
+    assert abs(err_gpu - err_ora) <= 1e-6 * err_ora + 1e-14
+    st = c.M.storage()
+    so = O.storage(c.tr, c.Vg, c.Wg, c.Sg)
+    for k in ("V", "W", "S", "near"):
+        assert st[k] == so[k], k
+    assert st["E_V"] == so["E_V"] and st["E_W"] == so["E_W"]
+
+
+def test_fp64_config1_parity(c1_fp64):
+    _check_fp64(c1_fp64)
+
+
+def test_fp64_leaf_subspaces(c1_fp64):
+    c = c1_fp64
+    checked = 0
+    for side, B in ((0, c.V), (1, c.W)):
+        for (t, cc), Q in B.Q.items():
+            k = B.rank[(t, cc)]
+            if c.rank[side][(t, cc)] != k or k == 0:
+                continue
+            sig = B.sigma[(t, cc)]
+            if k < len(sig) and sig[k - 1] - sig[k] < 1e-6 * sig[0]:
+                continue
+            Qg = c.M.pair_basis(side, c.pid[(side, t, cc)])
+            assert Qg.shape == Q.shape
+            assert np.linalg.norm(Qg.conj().T @ Qg - np.eye(k)) < 1e-12
+            assert np.linalg.norm(Qg @ Qg.conj().T - Q @ Q.conj().T) < 1e-9
+            sg = c.M.sigma(side, c.pid[(side, t, cc)])
+            np.testing.assert_allclose(sg[:len(sig)], sig, rtol=1e-9, atol=1e-13 * sig[0])
+            checked += 1
+    assert checked > 100
+
+
+def test_fp64_coupling_closed_form(c1_fp64):
+    """|S_b|_F of the GPU equals the oracle's at the same ranks (unitary invariance)."""
+    c = c1_fp64
+    for b, (t, s, adm, cb) in enumerate(c.tr.blocks):
+        if adm and b % 7 == 0:
+            Sg = c.M.coupling(b)
+            So = c.Sg[b]
+            assert Sg.shape == So.shape
+            assert abs(np.linalg.norm(Sg) - np.linalg.norm(So)) <= 1e-10 * max(1e-300, np.linalg.norm(So))
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_fp64_tighter_tolerances(eps):
+    _check_fp64(_fp64(2048, 8.0, 32, eps))
+
+
+def test_fp64_paper_parameters_nonleaf_levels():
+    """eta1 = 20, eta2 = 5 (Section 7) puts admissible blocks on coarse levels:
+    many non-leaf steps, transfer matrices and deep expansions."""
+    c = _fp64(2048, 8.0, 16, 1e-4, eta1=20.0, eta2=5.0)
+    nonleaf = sum(1 for (t, _) in c.V.rank if c.tr.sons[t])
+    assert nonleaf > 50
+    _check_fp64(c)
+
+
+def test_fp64_view_nearfield_and_ragged_leaves():
+    c = _fp64(1500, 6.0, 24, 1e-4, nearfield=1)
+    _check_fp64(c)
+
+
+def test_fp64_no_admissible_blocks():
+    c = _fp64(40, 4.0, 64, 1e-4)
+    assert not any(a for (_, _, a, _) in c.tr.blocks)
+    x = random_complex_vectors(40, 2, seed=5)
+    y = c.gpu_matvec(x)
+    np.testing.assert_allclose(y, c.G @ x, rtol=1e-13, atol=1e-13)
+    assert c.D.dh2_error(c.M, c.Gd) == 0.0
+
+
+def test_fp64_planted_low_rank():
+    pts = fibonacci_sphere(1024)
+    G = planted_separable_matrix(pts, 3)
+    c = _fp64(1024, 6.0, 16, 1e-10, G=G)
+    assert max(max(r.values()) for r in c.rank.values()) <= 3
+    _check_fp64(c)
+
+
+def test_fp64_kappa_zero_single_direction():
+    pts = fibonacci_sphere(1024)
+    c = _fp64(1024, 0.0, 16, 1e-5, G=helmholtz_matrix(pts, 0.0), dir_rule=1)
+    _check_fp64(c)
+
+
+def test_fp64_config2_parity():
+    """n = 8192, kappa = 16, leaf 32 (kappa^2 ~ n scaling)."""
+    _check_fp64(_fp64(8192, 16.0, 32, 1e-4))
+
+
+def test_fp32_config1(c1_fp32):
+    c = c1_fp32
+    bad, ties, total = _rank_report(c, 1e-3)
+    assert bad <= 0.05 * total
+    for side, B in ((0, c.V), (1, c.W)):
+        for key, ko in B.rank.items():
+            assert abs(c.rank[side][key] - ko) <= 2
+    x = random_complex_vectors(c.tr.n, 3, seed=12)
+    y_ref = O.matvec(c.tr, c.G, c.Vg, c.Wg, c.Sg, x)
+    y = c.gpu_matvec(x)
+    rel = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
+    assert rel <= 20 * c.cp.eps, rel
+    G128 = _colmajor(c.G, torch.complex128)
+    err = c.D.dh2_error(c.M, G128)
+    assert err <= c.cp.eps, err
+
+
+def test_fp32_config2_two_tolerances():
+    for eps in (1e-4, 1e-6):
+        c = _fp32(8192, 16.0, 32, eps)
+        bad, ties, total = _rank_report(c, 1e-3)
+        assert bad <= 0.05 * total, (bad, total)
+        G128 = _colmajor(c.G, torch.complex128)
+        assert c.D.dh2_error(c.M, G128) <= eps
+
+
+def test_status_errors_are_reported():
+    D = _dev()
+    pts = fibonacci_sphere(512)
+    T = D.dh2_tree_build(pts, 16, 4.0)
+    G = torch.zeros((512, 512), dtype=torch.complex64, device="cuda").t()
+    with pytest.raises(D.DH2Error):
+        D.dh2_compress(T, G, mode=D.MODE_FP64)  # dtype / mode mismatch
+    with pytest.raises(D.DH2Error):
+        D.dh2_compress(T, G, zeta=0.9)          # err_mode 0 needs zeta < 1/sqrt 2
+    M = D.dh2_compress(T, G)                     # zero matrix: ranks 0, exact
+    assert max(M.ranks(0)) == 0 and max(M.ranks(1)) == 0

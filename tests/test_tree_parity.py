@@ -1,0 +1,108 @@
+"""Host-side parity of the library's tree builder with the oracle (no GPU).
+
+The cluster tree, the direction families, the son maps, the block tree, the
+block directions and the column sets F_tc are integer results decided by
+floating-point comparisons evaluated in the same order on both sides, so they
+must agree exactly.
+"""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import dh2_oracle as O
+from synth import fibonacci_sphere, random_cube_surface, random_ellipsoid, random_sphere
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib_or_skip():
+    from paper_1510_07087_gb300 import _binding
+    if not os.path.exists(_binding.LIB_PATH):
+        pytest.skip("libdh2.so not built")
+    return _binding
+
+
+def test_library_exports_every_declared_symbol():
+    b = _lib_or_skip()
+    header = open(os.path.join(ROOT, "include", "dh2.h")).read()
+    declared = set(re.findall(r"^\s*(?:dh2_status|void|const char\*)\s+(dh2_\w+)\s*\(", header, re.M))
+    assert declared, "no declarations parsed"
+    lib = b._lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(b.exported_symbols())
+    assert b.dh2_version().startswith("dh2")
+
+
+CASES = [
+    ("fib", 2048, 4.0, 32, 2 * math.sqrt(2), 1.0, 0),
+    ("fib", 4096, 12.0, 16, 2 * math.sqrt(2), 1.0, 0),
+    ("fib", 2048, 8.0, 16, 20.0, 5.0, 0),
+    ("sphere", 1500, 6.0, 24, 2 * math.sqrt(2), 1.0, 0),
+    ("ellipsoid", 1200, 10.0, 20, 2 * math.sqrt(2), 2.0, 0),
+    ("cube", 1800, 9.0, 32, 2 * math.sqrt(2), 1.0, 0),
+    ("fib", 1024, 0.0, 16, 2 * math.sqrt(2), 1.0, 1),
+    ("fib", 20, 4.0, 32, 2 * math.sqrt(2), 1.0, 0),
+]
+
+
+def _points(kind, n):
+    return {"fib": fibonacci_sphere, "sphere": random_sphere, "ellipsoid": random_ellipsoid,
+            "cube": random_cube_surface}[kind](n)
+
+
+@pytest.mark.parametrize("kind,n,kappa,leaf,eta1,eta2,rule", CASES)
+def test_tree_matches_oracle(kind, n, kappa, leaf, eta1, eta2, rule):
+    b = _lib_or_skip()
+    pts = _points(kind, n)
+    T = b.dh2_tree_build(pts, leaf, kappa, eta1, eta2, rule)
+    ot = O.build_tree(pts, O.TreeParams(leaf_size=leaf, kappa=kappa, eta1=eta1, eta2=eta2, dir_rule=rule))
+    assert np.array_equal(T.perm(), ot.perm)
+    cl = T.clusters()
+    assert np.array_equal(cl["start"], ot.start)
+    assert np.array_equal(cl["size"], ot.size)
+    assert np.array_equal(cl["level"], ot.level)
+    assert np.array_equal(cl["parent"], ot.parent)
+    assert np.array_equal(cl["lo"], np.array(ot.lo)) and np.array_equal(cl["hi"], np.array(ot.hi))
+    st = T.stats()
+    assert st.depth == ot.depth
+    for l in range(ot.depth + 1):
+        D, sd = T.directions(l)
+        assert np.array_equal(D, ot.dirs[l])
+        if l < ot.depth:
+            assert np.array_equal(sd, ot.sd[l])
+    blk = T.blocks()
+    ob = np.array([(t, s, int(a), c) for (t, s, a, c) in ot.blocks], dtype=np.int64)
+    assert np.array_equal(blk, ob)
+    # used pairs and F_tc (as sets of blocks) on both sides
+    for side, name in ((0, "row"), (1, "col")):
+        F = O.column_sets(ot, name)
+        pr = T.pairs(side)
+        off, ids = T.pair_blocks(side)
+        got = {}
+        for p in range(len(pr["cluster"])):
+            got[(int(pr["cluster"][p]), int(pr["dir"][p]))] = sorted(ids[off[p]:off[p + 1]].tolist())
+            width = 0
+            for bb in ids[off[p]:off[p + 1]]:
+                t, s, _, _ = ot.blocks[bb]
+                width += ot.size[s] if side == 0 else ot.size[t]
+            assert width == pr["ncols"][p]
+            assert bool(pr["leaf"][p]) == ot.is_leaf(int(pr["cluster"][p]))
+        want = {(t, c): sorted(bl) for t in F for c, bl in F[t].items()}
+        assert got == want
+
+
+def test_invalid_arguments_rejected():
+    b = _lib_or_skip()
+    pts = fibonacci_sphere(100)
+    with pytest.raises(b.DH2Error):
+        b.dh2_tree_build(pts, 0, 4.0)
+    with pytest.raises(b.DH2Error):
+        b.dh2_tree_build(pts, 16, -1.0)
+    bad = pts.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(b.DH2Error):
+        b.dh2_tree_build(bad, 16, 4.0)
