@@ -48,7 +48,7 @@ typedef enum {
   DH2_ENOMEM = 2,       /* host or device allocation failed                         */
   DH2_ECUDA = 3,        /* a CUDA runtime call failed                               */
   DH2_ETIMEOUT = 4,     /* a bounded device-side wait ran out                        */
-  DH2_ENOCONV = 5,      /* a Jacobi SVD hit its sweep cap before converging          */
+  DH2_ENOCONV = 5,      /* a Jacobi SVD hit its sweep cap, or met non-finite values  */
   DH2_EUNSUPPORTED = 6  /* size beyond a compiled limit (e.g. rows of a factor)      */
 } dh2_status;
 

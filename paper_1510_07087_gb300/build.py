@@ -38,10 +38,11 @@ def build(verbose: bool = False) -> str:
         objs.append(obj)
         jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wno-unused-function",
                      f"-I{os.path.join(HERE, '..', 'include')}", "-c", os.path.join(CSRC, src), "-o", obj])
+    extra = ["-DDH2_CHECK"] if os.environ.get("DH2_CHECK") == "1" else []
     for src in CUDA_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
-        jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "--extended-lambda",
+        jobs.append([nvcc, "-std=c++17", "-O3", "-lineinfo", *ARCH, "--extended-lambda", *extra,
                      "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
                      "-c", os.path.join(CSRC, src), "-o", obj])
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True) for j in jobs]

@@ -9,6 +9,9 @@
 #include <new>
 #include <vector>
 
+#include <cstdio>
+
+#include "dh2_check.cuh"
 #include "dh2_internal.h"
 #include "dh2_kernels.cuh"
 #include "dh2_ops.cuh"
@@ -362,6 +365,7 @@ SideView<T> side_view(const Tree& tr, const dh2_matrix* M, int sd) {
   v.cstart = D->cstart;
   v.csize = D->csize;
   v.rank = M->rank[sd];
+  v.side = sd;
   v.R = (C2<T>*)M->R[sd];
   v.Q = (C2<T>*)M->Q[sd];
   v.X = (C2<T>*)M->X[sd];
@@ -369,6 +373,21 @@ SideView<T> side_view(const Tree& tr, const dh2_matrix* M, int sd) {
 }
 
 int even_up(int x) { return x + (x & 1); }
+
+#ifdef DH2_CHECK
+#define DH2_PHASE_SYNC(name)                                                                        \
+  do {                                                                                              \
+    const cudaError_t e_ = cudaStreamSynchronize(st);                                               \
+    if (e_ != cudaSuccess) {                                                                        \
+      std::fprintf(stderr, "dh2: launch '%s' failed: %s\n", name, cudaGetErrorString(e_));           \
+      return DH2_ECUDA;                                                                             \
+    }                                                                                               \
+  } while (0)
+#else
+#define DH2_PHASE_SYNC(name) \
+  do {                       \
+  } while (0)
+#endif
 
 template <typename T>
 dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
@@ -378,6 +397,25 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   const int pmax = sizeof(T) == 4 ? kPmaxF32 : kPmaxF64;
   cudaEvent_t ev[6];
   for (int i = 0; i < 6; ++i) DH2_CUDA_TRY(cudaEventCreate(&ev[i]));
+#ifdef DH2_CHECK
+  {
+    CheckLimits lim;
+    lim.G = M->ld * (tr.n - 1) + tr.n;
+    for (int sd = 0; sd < 2; ++sd) {
+      lim.R[sd] = D->R_elems[sd];
+      lim.Q[sd] = D->Q_elems[sd];
+      lim.X[sd] = D->X_elems[sd];
+      lim.npairs[sd] = D->npairs[sd];
+      lim.ncol[sd] = (int64_t)tr.side[sd].gcol.size();
+    }
+    lim.S = D->S_elems;
+    lim.near = M->nearfield_copy ? D->near_elems : 0;
+    lim.nblocks = (int64_t)tr.blocks.size();
+    cudaStreamSynchronize(st);
+    check_set_limits_pair(lim);
+    check_set_limits_ops(lim);
+  }
+#endif
   cudaEventRecord(ev[0], st);
 
   NormsArgs<T> na;
@@ -395,6 +433,7 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   na.near_off = D->near_off;
   na.copy = M->nearfield_copy;
   launch_norms_near<T>(na, (int)tr.blocks.size(), st);
+  DH2_PHASE_SYNC("norms_near");
   cudaEventRecord(ev[1], st);
 
   PairArgs<T> pa;
@@ -427,6 +466,7 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   // leaf step for every leaf pair of both sides in one launch
   pa.P = even_up(std::max(2, D->max_leaf));
   launch_pair_kernel<T>(pa, (int)D->nleaf_codes, false, st);
+  DH2_PHASE_SYNC("leaf pairs");
   cudaEventRecord(ev[2], st);
   // non-leaf steps, level by level from the leaves up
   for (int l = tr.depth; l >= 0; --l) {
@@ -435,6 +475,10 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
     pl.order = D->codes + D->nl_code_begin[l];
     pl.P = even_up(std::max(2, std::min(pmax, D->nl_rowcap_max[l])));
     launch_pair_kernel<T>(pl, (int)D->nl_code_count[l], true, st);
+#ifdef DH2_CHECK
+    std::fprintf(stderr, "dh2: non-leaf level %d: %lld pairs, P=%d\n", l, (long long)D->nl_code_count[l], pl.P);
+#endif
+    DH2_PHASE_SYNC("non-leaf pairs");
   }
   cudaEventRecord(ev[3], st);
   // expanded column bases for the projection
@@ -442,6 +486,7 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   for (int l = tr.depth; l >= 0; --l) {
     const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
     if (e > b) launch_expand<T>(Wv, D->iota[1] + b, (int)(e - b), st);
+    DH2_PHASE_SYNC("expand");
   }
   cudaEventRecord(ev[4], st);
   ProjArgs<T> pj;
@@ -457,6 +502,7 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   pj.S = (C2<T>*)M->S;
   pj.Soff = D->Soff;
   launch_project<T>(pj, (int)D->nadm, st);
+  DH2_PHASE_SYNC("project");
   cudaEventRecord(ev[5], st);
   uint32_t status = 0;
   cudaError_t e1 = cudaMemcpyAsync(&status, M->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
@@ -465,8 +511,20 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&M->phase_ms[i], ev[i], ev[i + 1]);
   for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return DH2_ECUDA;
+#ifdef DH2_CHECK
+  {
+    CheckRecord r1{}, r2{};
+    const bool b1 = check_read_pair(&r1), b2 = check_read_ops(&r2);
+    if (b1 || b2) {
+      const CheckRecord& r = b1 ? r1 : r2;
+      std::fprintf(stderr, "dh2 bounds check: %d violations, first at site %d item %d index %lld limit %lld\n",
+                   r.count, r.where, r.item, (long long)r.index, (long long)r.limit);
+      return DH2_EINVAL;
+    }
+  }
+#endif
   if (status & kStatusTooLarge) return DH2_EUNSUPPORTED;
-  if (status & kStatusNoConv) return DH2_ENOCONV;
+  if (status & (kStatusNoConv | kStatusNaN)) return DH2_ENOCONV;
   if (status & kStatusTimeout) return DH2_ETIMEOUT;
   return DH2_OK;
 }

@@ -24,6 +24,7 @@ constexpr int kSigStride = 128;
 constexpr uint32_t kStatusNoConv = 1u;
 constexpr uint32_t kStatusTooLarge = 2u;
 constexpr uint32_t kStatusTimeout = 4u;
+constexpr uint32_t kStatusNaN = 8u;
 
 struct Block {
   int32_t t, s;

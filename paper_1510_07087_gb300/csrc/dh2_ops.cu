@@ -1,12 +1,15 @@
 // Kernels around the per-pair factorisation: block norms and nearfield copy,
 // basis expansion by Eq. (nested), the projection S_b, the matrix-vector
 // product of Section 4 and the blockwise error.
+#include "dh2_check.cuh"
 #include "dh2_internal.h"
 #include "dh2_ops.cuh"
 
 namespace dh2 {
 
 namespace {
+
+DH2_CHECK_DECLS
 
 template <typename T>
 __device__ __forceinline__ C2<T> czero() { return C2<T>{T(0), T(0)}; }
@@ -67,17 +70,21 @@ __global__ void __launch_bounds__(256) norms_near_kernel(NormsArgs<T> a) {
     for (int j = warp; j < ms; j += nw) {
       const C2<T>* col = a.G + (s0 + j) * a.ld + t0;
       for (int r = lane; r < mt; r += 32) {
+        if (!DH2_IN((s0 + j) * a.ld + t0 + r, c_lim.G, 20, b)) continue;
         const C2<T> g = col[r];
         acc += g.re * g.re + g.im * g.im;
       }
     }
     const double tot = block_sum((double)acc, red);
-    if (threadIdx.x == 0) a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+    if (threadIdx.x == 0 && DH2_IN(b, c_lim.nblocks, 23, b)) a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
   } else if (a.copy) {
     C2<T>* out = a.near + a.near_off[b];
     for (int j = warp; j < ms; j += nw) {
       const C2<T>* col = a.G + (s0 + j) * a.ld + t0;
-      for (int r = lane; r < mt; r += 32) out[r + (int64_t)j * mt] = col[r];
+      for (int r = lane; r < mt; r += 32)
+        if (DH2_IN(a.near_off[b] + r + (int64_t)j * mt, c_lim.near, 21, b) &&
+            DH2_IN((s0 + j) * a.ld + t0 + r, c_lim.G, 22, b))
+          out[r + (int64_t)j * mt] = col[r];
     }
   }
 }
@@ -96,14 +103,21 @@ __global__ void __launch_bounds__(256) expand_kernel(SideView<T> S, const int32_
   int rowoff = 0, eoff = 0;
   for (int j = 0; j < 2; ++j) {
     const int sp = S.son[2 * pid + j];
+    if (!DH2_IN(sp, c_lim.npairs[S.side], 34, pid)) return;
     const int kj = S.rank[sp];
     const int mj = S.csize[S.cluster[sp]];
     const C2<T>* W = xbasis(S, sp);
     for (int idx = threadIdx.x; idx < mj * k; idx += blockDim.x) {
       const int i = idx % mj, qq = idx / mj;
       C2<T> acc = czero<T>();
-      for (int l = 0; l < kj; ++l) acc = cadd(acc, cmul(W[i + (int64_t)l * mj], E[eoff + l + (int64_t)qq * ldq]));
-      out[rowoff + i + (int64_t)qq * ldo] = acc;
+      for (int l = 0; l < kj; ++l) {
+        const bool okw = S.leaf[sp] ? DH2_IN(S.Qoff[sp] + i + (int64_t)l * mj, c_lim.Q[S.side], 30, pid)
+                                    : DH2_IN(S.Xoff[sp] + i + (int64_t)l * mj, c_lim.X[S.side], 31, pid);
+        const bool oke = DH2_IN(S.Qoff[pid] + eoff + l + (int64_t)qq * ldq, c_lim.Q[S.side], 32, pid);
+        if (okw && oke) acc = cadd(acc, cmul(W[i + (int64_t)l * mj], E[eoff + l + (int64_t)qq * ldq]));
+      }
+      if (DH2_IN(S.Xoff[pid] + rowoff + i + (int64_t)qq * ldo, c_lim.X[S.side], 33, pid))
+        out[rowoff + i + (int64_t)qq * ldo] = acc;
     }
     rowoff += mj;
     eoff += kj;
@@ -119,6 +133,7 @@ __global__ void __launch_bounds__(256) project_kernel(ProjArgs<T> a) {
   __shared__ C2<T> Ws[16][65];
   const int b = a.adm_list[blockIdx.x];
   const int Pt = a.bpair_row[b], Ps = a.bpair_col[b];
+  if (!DH2_IN(Pt, c_lim.npairs[0], 44, b) || !DH2_IN(Ps, c_lim.npairs[1], 45, b)) return;
   const int off = a.boff_row[b];
   const int kt = a.V.rank[Pt], ks = a.W.rank[Ps];
   C2<T>* Sout = a.S + a.Soff[b];
@@ -139,11 +154,18 @@ __global__ void __launch_bounds__(256) project_kernel(ProjArgs<T> a) {
         __syncthreads();
         for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
           const int qq = idx & 63, jj = idx >> 6;
-          Rs[qq][jj] = (q0 + qq < kt && j0 + jj < ms) ? R[q0 + qq + (int64_t)(j0 + jj) * ldr] : czero<T>();
+          Rs[qq][jj] = (q0 + qq < kt && j0 + jj < ms &&
+                        DH2_IN(a.V.Roff[Pt] + (int64_t)off * ldr + q0 + qq + (int64_t)(j0 + jj) * ldr, c_lim.R[0], 40, b))
+                           ? R[q0 + qq + (int64_t)(j0 + jj) * ldr]
+                           : czero<T>();
         }
         for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
           const int jj = idx & 15, cc = idx >> 4;
-          Ws[jj][cc] = (c0 + cc < ks && j0 + jj < ms) ? W[j0 + jj + (int64_t)(c0 + cc) * ms] : czero<T>();
+          Ws[jj][cc] = (c0 + cc < ks && j0 + jj < ms &&
+                        (a.W.leaf[Ps] ? DH2_IN(a.W.Qoff[Ps] + j0 + jj + (int64_t)(c0 + cc) * ms, c_lim.Q[1], 41, b)
+                                      : DH2_IN(a.W.Xoff[Ps] + j0 + jj + (int64_t)(c0 + cc) * ms, c_lim.X[1], 42, b)))
+                           ? W[j0 + jj + (int64_t)(c0 + cc) * ms]
+                           : czero<T>();
         }
         __syncthreads();
         for (int jj = 0; jj < 16; ++jj) {
@@ -155,7 +177,8 @@ __global__ void __launch_bounds__(256) project_kernel(ProjArgs<T> a) {
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int qq = q0 + tq, cc = c0 + tc + 4 * u;
-        if (qq < kt && cc < ks) Sout[qq + (int64_t)cc * kt] = C2<T>{w * acc[u].re, w * acc[u].im};
+        if (qq < kt && cc < ks && DH2_IN(a.Soff[b] + qq + (int64_t)cc * kt, c_lim.S, 43, b))
+          Sout[qq + (int64_t)cc * kt] = C2<T>{w * acc[u].re, w * acc[u].im};
       }
     }
   }
@@ -362,6 +385,26 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs<T> a, const C2<RT>* 
 }
 
 }  // namespace
+
+void check_set_limits_ops(const CheckLimits& l) {
+#ifdef DH2_CHECK
+  cudaMemcpyToSymbol(c_lim, &l, sizeof(l));
+  CheckRecord z{};
+  cudaMemcpyToSymbol(g_chk, &z, sizeof(z));
+#else
+  (void)l;
+#endif
+}
+
+bool check_read_ops(CheckRecord* out) {
+#ifdef DH2_CHECK
+  cudaMemcpyFromSymbol(out, g_chk, sizeof(*out));
+  return out->count != 0;
+#else
+  (void)out;
+  return false;
+#endif
+}
 
 template <typename T>
 void launch_norms_near(const NormsArgs<T>& a, int nblocks, cudaStream_t st) {

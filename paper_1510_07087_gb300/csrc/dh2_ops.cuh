@@ -19,6 +19,7 @@ struct SideView {
   const int32_t* cstart;   // per cluster
   const int32_t* csize;    // per cluster
   const int32_t* rank;     // per pair
+  int side;
   C2<T>* R;
   C2<T>* Q;
   C2<T>* X;

@@ -21,12 +21,15 @@
 //   5. streams A once more to form R_tc = Q^* A (Section 6, R recursion).
 #include <cfloat>
 
+#include "dh2_check.cuh"
 #include "dh2_internal.h"
 #include "dh2_kernels.cuh"
 
 namespace dh2 {
 
 namespace {
+
+DH2_CHECK_DECLS
 
 template <typename T>
 __device__ __forceinline__ C2<T> czero() { return C2<T>{T(0), T(0)}; }
@@ -48,10 +51,19 @@ __device__ __forceinline__ T cnorm2(C2<T> a) { return a.re * a.re + a.im * a.im;
 
 template <typename T>
 struct Eps;
+// u: unit roundoff; tiny: squared norms below it are treated as zero (far
+// below any weighted entry, and far enough above the underflow threshold that
+// 1/tiny and the Householder scale factors stay finite).
 template <>
-struct Eps<float> { static constexpr float u = 5.9604645e-08f; };
+struct Eps<float> {
+  static constexpr float u = 5.9604645e-08f;
+  static constexpr float tiny = 1e-30f;
+};
 template <>
-struct Eps<double> { static constexpr double u = 1.1102230246251565e-16; };
+struct Eps<double> {
+  static constexpr double u = 1.1102230246251565e-16;
+  static constexpr double tiny = 1e-280;
+};
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -91,24 +103,31 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
   int p = 0, k1 = 0, off0 = 0, off1 = 0, ld0 = 1, ld1 = 1, r0 = 0;
   const C2<T>* R0 = nullptr;
   const C2<T>* R1 = nullptr;
+  int64_t roff0 = 0, roff1 = 0;
   const int32_t* gcol = nullptr;
   const int32_t* gblk = nullptr;
   if (FROM_R) {
     const int s0 = a.son[side][2 * pid], s1 = a.son[side][2 * pid + 1];
+    if (!DH2_IN(s0, c_lim.npairs[side], 12, pid) || !DH2_IN(s1, c_lim.npairs[side], 13, pid)) return;
     k1 = a.rank[side][s0];
     p = k1 + a.rank[side][s1];
     off0 = a.sonoff[side][2 * pid];
     off1 = a.sonoff[side][2 * pid + 1];
     ld0 = a.kcap[side][s0];
     ld1 = a.kcap[side][s1];
-    R0 = a.R[side] + a.Roff[side][s0];
-    R1 = a.R[side] + a.Roff[side][s1];
+    roff0 = a.Roff[side][s0];
+    roff1 = a.Roff[side][s1];
+    R0 = a.R[side] + roff0;
+    R1 = a.R[side] + roff1;
   } else {
     p = a.m[side][pid];
     r0 = a.start[side][pid];
     gcol = a.gcol[side] + a.cmoff[side][pid];
     gblk = a.gblk[side] + a.cmoff[side][pid];
   }
+  const int64_t cmo = FROM_R ? 0 : a.cmoff[side][pid];
+  (void)cmo;
+  if (!DH2_IN(pid, c_lim.npairs[side], 9, pid)) return;
   int32_t* rank_out = a.rank[side] + pid;
   double* sig_out = a.sig[side] + (int64_t)pid * kSigStride;
   if (p > P || p > NT / LPR) {
@@ -137,19 +156,26 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
         const C2<T>* c1 = R1 + (int64_t)(off1 + j0 + jj) * ld1;
         for (int r = lane; r < p; r += 32) {
           C2<T> v = czero<T>();
-          if (in) v = r < k1 ? c0[r] : c1[r - k1];
+          if (in) {
+            if (r < k1) {
+              if (DH2_IN(roff0 + r + (int64_t)(off0 + j0 + jj) * ld0, c_lim.R[side], 1, pid)) v = c0[r];
+            } else {
+              if (DH2_IN(roff1 + (r - k1) + (int64_t)(off1 + j0 + jj) * ld1, c_lim.R[side], 2, pid)) v = c1[r - k1];
+            }
+          }
           X[r * LDX + P + jj] = v;
         }
       }
     } else if (side == 0) {
       // rows of t, columns from F_tc: contiguous runs down each G column
       for (int jj = warp; jj < C; jj += NW) {
-        if (jj < cw) {
+        if (jj < cw && DH2_IN(cmo + j0 + jj, c_lim.ncol[side], 3, pid)) {
           const int gc = gcol[j0 + jj];
-          const T w = (T)a.invw[gblk[j0 + jj]];
+          const T w = DH2_IN(gblk[j0 + jj], c_lim.nblocks, 4, pid) ? (T)a.invw[gblk[j0 + jj]] : T(0);
           const C2<T>* col = a.G + (int64_t)gc * a.ld + r0;
           for (int r = lane; r < p; r += 32) {
-            const C2<T> g = col[r];
+            C2<T> g = czero<T>();
+            if (DH2_IN((int64_t)gc * a.ld + r0 + r, c_lim.G, 5, pid)) g = col[r];
             X[r * LDX + P + jj] = C2<T>{g.re * w, g.im * w};
           }
         } else {
@@ -162,7 +188,9 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
         const C2<T>* col = a.G + (int64_t)(r0 + r) * a.ld;
         for (int jj = lane; jj < C; jj += 32) {
           C2<T> v = czero<T>();
-          if (jj < cw) {
+          if (jj < cw && DH2_IN(cmo + j0 + jj, c_lim.ncol[side], 6, pid) &&
+              DH2_IN((int64_t)(r0 + r) * a.ld + gcol[j0 + jj], c_lim.G, 7, pid) &&
+              DH2_IN(gblk[j0 + jj], c_lim.nblocks, 8, pid)) {
             const C2<T> g = col[gcol[j0 + jj]];
             const T w = (T)a.invw[gblk[j0 + jj]];
             v = C2<T>{g.re * w, -g.im * w};
@@ -187,7 +215,7 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     if (q == 0) {
-      if (s == T(0)) {
+      if (!(s > Eps<T>::tiny)) {
         sh_skip[slot] = 1;
       } else {
         const C2<T> al = xr[i];
@@ -267,11 +295,11 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
         ga.re = warp_sum(ga.re);
         ga.im = warp_sum(ga.im);
         const T gabs = hypot(ga.re, ga.im);
-        if (gabs > T(0) && gabs > tol * sqrt(al) * sqrt(be)) {
-          const T zt = (be - al) / (T(2) * gabs);
-          const T t = (zt >= T(0) ? T(1) : T(-1)) / (fabs(zt) + hypot(T(1), zt));
-          const T c = T(1) / sqrt(T(1) + t * t);
-          const T s = t * c;
+        const T zt = (be - al) / (T(2) * gabs);
+        const T t = (zt >= T(0) ? T(1) : T(-1)) / (fabs(zt) + hypot(T(1), zt));
+        const T c = T(1) / sqrt(T(1) + t * t);
+        const T s = t * c;
+        if (al > Eps<T>::tiny && be > Eps<T>::tiny && gabs > tol * sqrt(al) * sqrt(be) && s != T(0)) {
           const C2<T> e = C2<T>{ga.re / gabs, -ga.im / gabs};  // e^{-i arg gamma}
           for (int r = lane; r < p; r += 32) {
             const C2<T> xa = X[r * LDX + ia];
@@ -305,15 +333,27 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
     if (lane == 0) sig2[j] = s;
   }
   __syncthreads();
+  // non-finite values (only from non-finite input) are ranked as zero and
+  // reported; ord stays a permutation of 0..p-1 in every case
+  if (tid < p) {
+    ord[tid] = tid;
+    if (!(sig2[tid] >= 0.0 && sig2[tid] <= 1.0e300)) {
+      sig2[tid] = 0.0;
+      atomicOr(a.status, kStatusNaN);
+    }
+  }
+  __syncthreads();
+  int rk = -1;
   if (tid < p) {
     const double v = sig2[tid];
-    int rk = 0;
+    rk = 0;
     for (int i = 0; i < p; ++i) {
       const double u = sig2[i];
       rk += (u > v) || (u == v && i < tid);
     }
-    ord[rk] = tid;
   }
+  __syncthreads();
+  if (rk >= 0 && rk < p) ord[rk] = tid;
   __syncthreads();
   if (tid == 0) {
     const double e2 = a.eps2[lvl];
@@ -346,7 +386,7 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
       C2<T> v = X[r * LDX + j];
       v = C2<T>{v.re * inv, v.im * inv};
       X[r * LDX + j] = v;
-      Qout[r + (int64_t)qq * ldq] = v;
+      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid)) Qout[r + (int64_t)qq * ldq] = v;
     }
   }
   __syncthreads();
@@ -363,7 +403,8 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
       const int j = ord[qq];
       C2<T> acc = czero<T>();
       for (int r = 0; r < p; ++r) acc = cadd(acc, cmulc(X[r * LDX + P + jj], X[r * LDX + j]));
-      Rout[qq + (int64_t)(j0 + jj) * kcap] = acc;
+      if (DH2_IN(a.Roff[side][pid] + qq + (int64_t)(j0 + jj) * kcap, c_lim.R[side], 11, pid))
+        Rout[qq + (int64_t)(j0 + jj) * kcap] = acc;
     }
     __syncthreads();
   }
@@ -381,6 +422,26 @@ void launch_one(const PairArgs<T>& a, int nblocks, cudaStream_t st) {
 }
 
 }  // namespace
+
+void check_set_limits_pair(const CheckLimits& l) {
+#ifdef DH2_CHECK
+  cudaMemcpyToSymbol(c_lim, &l, sizeof(l));
+  CheckRecord z{};
+  cudaMemcpyToSymbol(g_chk, &z, sizeof(z));
+#else
+  (void)l;
+#endif
+}
+
+bool check_read_pair(CheckRecord* out) {
+#ifdef DH2_CHECK
+  cudaMemcpyFromSymbol(out, g_chk, sizeof(*out));
+  return out->count != 0;
+#else
+  (void)out;
+  return false;
+#endif
+}
 
 template <typename T>
 void launch_pair_kernel(const PairArgs<T>& a, int nblocks, bool from_r, cudaStream_t st) {
