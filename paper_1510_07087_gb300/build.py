@@ -39,6 +39,8 @@ def build(verbose: bool = False) -> str:
         jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wno-unused-function",
                      f"-I{os.path.join(HERE, '..', 'include')}", "-c", os.path.join(CSRC, src), "-o", obj])
     extra = ["-DDH2_CHECK"] if os.environ.get("DH2_CHECK") == "1" else []
+    if os.environ.get("DH2_PROFILE") == "1":
+        extra.append("-DDH2_PROFILE")
     for src in CUDA_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)

@@ -465,7 +465,22 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   pa.status = M->status;
   // leaf step for every leaf pair of both sides in one launch
   pa.P = even_up(std::max(2, D->max_leaf));
+#ifdef DH2_PROFILE
+  prof_reset_pair();
+#endif
   launch_pair_kernel<T>(pa, (int)D->nleaf_codes, false, st);
+#ifdef DH2_PROFILE
+  {
+    cudaStreamSynchronize(st);
+    unsigned long long pr[8];
+    prof_read_pair(pr);
+    const double np = pr[5] ? (double)pr[5] : 1.0;
+    std::fprintf(stderr,
+                 "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean N %.1f, mean sweeps %.2f, cycles/pair: "
+                 "LQ %.0f Jacobi %.0f rank+Q %.0f R %.0f\n",
+                 pr[5], pr[6] / np, pr[7] / np, pr[4] / np, pr[0] / np, pr[1] / np, pr[2] / np, pr[3] / np);
+  }
+#endif
   DH2_PHASE_SYNC("leaf pairs");
   cudaEventRecord(ev[2], st);
   // non-leaf steps, level by level from the leaves up

@@ -46,4 +46,8 @@ struct PairArgs {
 template <typename T>
 void launch_pair_kernel(const PairArgs<T>& a, int nblocks, bool from_r, cudaStream_t st);
 
+// Phase cycle counters of the pair kernel (only with -DDH2_PROFILE).
+void prof_reset_pair();
+bool prof_read_pair(unsigned long long* out8);
+
 }  // namespace dh2

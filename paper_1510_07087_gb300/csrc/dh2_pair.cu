@@ -5,20 +5,23 @@
 //   1. streams the columns of its matrix A -- G^omega_tc restricted to the
 //      rows of t for a leaf (Section 6 leaf step, weights of Remark "Error
 //      control"), or Ghat_tc = [R_t1c'|F_tc ; R_t2c'|F_tc] for a non-leaf
-//      (Eq. hatQ_hatG) -- through shared memory in chunks of C columns and
-//      reduces it to a p x p lower-triangular factor L with A = L Omega,
-//      Omega with orthonormal rows (an LQ factorisation by Householder
-//      reflections applied chunk by chunk, so the Gram matrix A A^* is never
-//      formed and singular values are not squared);
-//   2. runs one-sided (Hestenes) Jacobi on the columns of L: L J = U Sigma,
-//      so the normalised columns are the left singular vectors of A and their
-//      norms its singular values;
+//      (Eq. hatQ_hatG) -- in chunks of C columns held in registers (one row
+//      of the chunk per group of LPR threads) and reduces it to a p x p
+//      lower-triangular factor L with A = L Omega, Omega with orthonormal
+//      rows: an LQ factorisation by Householder reflections applied chunk by
+//      chunk, so the Gram matrix A A^* is never formed and singular values
+//      are not squared;
+//   2. runs one-sided (Hestenes) Jacobi on the columns of L held in shared
+//      memory, one column pair per group of 8 threads and all pairs of a
+//      round at once: L J = U Sigma, so the normalised columns are the left
+//      singular vectors of A and their norms its singular values;
 //   3. chooses the rank k = min{k : sum_{i>k} sigma_i^2 <= eps_l^2} with the
 //      tail sums formed in FP64;
 //   4. writes Q = first k left singular vectors (Q_tc for a leaf, the stacked
 //      transfer matrices [E_t1c; E_t2c] for a non-leaf), the singular values
 //      and k, and
-//   5. streams A once more to form R_tc = Q^* A (Section 6, R recursion).
+//   5. streams A once more through shared memory to form R_tc = Q^* A
+//      (Section 6, R recursion).
 #include <cfloat>
 
 #include "dh2_check.cuh"
@@ -30,6 +33,17 @@ namespace dh2 {
 namespace {
 
 DH2_CHECK_DECLS
+
+#ifdef DH2_PROFILE
+// per-phase clock cycles summed over CTAs: LQ, Jacobi, rank+Q, R; sweeps; pairs
+__device__ unsigned long long g_prof[8];
+#define DH2_PROF_T(v) const long long v = clock64()
+#define DH2_PROF_ADD(i, v) \
+  if (threadIdx.x == 0) atomicAdd(&g_prof[i], (unsigned long long)(v))
+#else
+#define DH2_PROF_T(v)
+#define DH2_PROF_ADD(i, v)
+#endif
 
 template <typename T>
 __device__ __forceinline__ C2<T> czero() { return C2<T>{T(0), T(0)}; }
@@ -65,19 +79,64 @@ struct Eps<double> {
   static constexpr double tiny = 1e-280;
 };
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+// Element (r, j) of the pair's matrix A (row r of the factor, column j of F_tc).
+template <typename T, bool FROM_R>
+struct Source {
+  int side, pid;
+  // leaf
+  const C2<T>* G;
+  int64_t ld;
+  int r0;
+  const int32_t* gcol;
+  const int32_t* gblk;
+  const double* invw;
+  int64_t cmo;
+  // non-leaf
+  const C2<T>* R0;
+  const C2<T>* R1;
+  int64_t roff0, roff1;
+  int k1, off0, off1, ld0, ld1;
 
-template <typename T, int C, int LPR, bool FROM_R>
-__global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
+  __device__ __forceinline__ C2<T> get(int r, int j) const {
+    if (FROM_R) {
+      if (r < k1) {
+        const int64_t e = (int64_t)(off0 + j) * ld0 + r;
+        if (!DH2_IN(roff0 + e, c_lim.R[side], 1, pid)) return czero<T>();
+        return R0[e];
+      }
+      const int64_t e = (int64_t)(off1 + j) * ld1 + (r - k1);
+      if (!DH2_IN(roff1 + e, c_lim.R[side], 2, pid)) return czero<T>();
+      return R1[e];
+    } else {
+      if (!DH2_IN(cmo + j, c_lim.ncol[side], 3, pid)) return czero<T>();
+      const int gc = gcol[j];
+      const int b = gblk[j];
+      if (!DH2_IN(b, c_lim.nblocks, 4, pid)) return czero<T>();
+      const T w = (T)invw[b];
+      if (side == 0) {
+        const int64_t e = (int64_t)gc * ld + r0 + r;
+        if (!DH2_IN(e, c_lim.G, 5, pid)) return czero<T>();
+        const C2<T> g = G[e];
+        return C2<T>{g.re * w, g.im * w};
+      }
+      // column basis: the same procedure on G^*; row r of A is column r0+r of G
+      const int64_t e = (int64_t)(r0 + r) * ld + gc;
+      if (!DH2_IN(e, c_lim.G, 7, pid)) return czero<T>();
+      const C2<T> g = G[e];
+      return C2<T>{g.re * w, -g.im * w};
+    }
+  }
+};
+
+// P_T: largest factor size of the instantiation (64 or 128 rows).
+template <typename T, int P_T, bool FROM_R>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const PairArgs<T> a) {
   constexpr int NT = 256;
-  constexpr int NW = NT / 32;
-  constexpr int CPL = C / LPR;  // chunk columns per thread in the LQ updates
-  static_assert(C % LPR == 0, "chunk width must split over the lanes of a row");
+  constexpr int LPR = NT / P_T;      // threads per row in the LQ
+  constexpr int C = P_T == 64 ? 64 : 32;
+  constexpr int CPL = C / LPR;       // chunk entries per thread
+  constexpr int XTRA = 16;           // spare L columns used to stage R chunks
+  static_assert(C % LPR == 0, "chunk width must split over the threads of a row");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ C2<T> sh_v0[2];
   __shared__ T sh_tau[2];
@@ -86,9 +145,11 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
   __shared__ int sh_k;
 
   const int P = a.P;
-  const int LDX = P + C + 1;
-  C2<T>* X = reinterpret_cast<C2<T>*>(smem);
-  size_t soff = ((size_t)P * LDX * sizeof(C2<T>) + 15) & ~(size_t)15;
+  const int LDL = P + 1;              // column-major L: element (r, c) at c * LDL + r
+  C2<T>* Lm = reinterpret_cast<C2<T>*>(smem);
+  size_t soff = ((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15;
+  C2<T>* vbuf = reinterpret_cast<C2<T>*>(smem + soff);  // 2 x C reflector rows
+  soff += 2 * C * sizeof(C2<T>);
   double* sig2 = reinterpret_cast<double*>(smem + soff);
   soff += (size_t)P * sizeof(double);
   int* ord = reinterpret_cast<int*>(smem + soff);
@@ -97,40 +158,41 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
   const int code = a.order[blockIdx.x];
   const int side = code >> 30;
   const int pid = code & 0x3fffffff;
+  if (!DH2_IN(pid, c_lim.npairs[side], 9, pid)) return;
   const int N = a.ncols[side][pid];
   const int kcap = a.kcap[side][pid];
   const int lvl = a.level[side][pid];
-  int p = 0, k1 = 0, off0 = 0, off1 = 0, ld0 = 1, ld1 = 1, r0 = 0;
-  const C2<T>* R0 = nullptr;
-  const C2<T>* R1 = nullptr;
-  int64_t roff0 = 0, roff1 = 0;
-  const int32_t* gcol = nullptr;
-  const int32_t* gblk = nullptr;
+
+  Source<T, FROM_R> src;
+  src.side = side;
+  src.pid = pid;
+  int p = 0;
   if (FROM_R) {
     const int s0 = a.son[side][2 * pid], s1 = a.son[side][2 * pid + 1];
     if (!DH2_IN(s0, c_lim.npairs[side], 12, pid) || !DH2_IN(s1, c_lim.npairs[side], 13, pid)) return;
-    k1 = a.rank[side][s0];
-    p = k1 + a.rank[side][s1];
-    off0 = a.sonoff[side][2 * pid];
-    off1 = a.sonoff[side][2 * pid + 1];
-    ld0 = a.kcap[side][s0];
-    ld1 = a.kcap[side][s1];
-    roff0 = a.Roff[side][s0];
-    roff1 = a.Roff[side][s1];
-    R0 = a.R[side] + roff0;
-    R1 = a.R[side] + roff1;
+    src.k1 = a.rank[side][s0];
+    p = src.k1 + a.rank[side][s1];
+    src.off0 = a.sonoff[side][2 * pid];
+    src.off1 = a.sonoff[side][2 * pid + 1];
+    src.ld0 = a.kcap[side][s0];
+    src.ld1 = a.kcap[side][s1];
+    src.roff0 = a.Roff[side][s0];
+    src.roff1 = a.Roff[side][s1];
+    src.R0 = a.R[side] + src.roff0;
+    src.R1 = a.R[side] + src.roff1;
   } else {
     p = a.m[side][pid];
-    r0 = a.start[side][pid];
-    gcol = a.gcol[side] + a.cmoff[side][pid];
-    gblk = a.gblk[side] + a.cmoff[side][pid];
+    src.r0 = a.start[side][pid];
+    src.cmo = a.cmoff[side][pid];
+    src.gcol = a.gcol[side] + src.cmo;
+    src.gblk = a.gblk[side] + src.cmo;
+    src.G = a.G;
+    src.ld = a.ld;
+    src.invw = a.invw;
   }
-  const int64_t cmo = FROM_R ? 0 : a.cmoff[side][pid];
-  (void)cmo;
-  if (!DH2_IN(pid, c_lim.npairs[side], 9, pid)) return;
   int32_t* rank_out = a.rank[side] + pid;
   double* sig_out = a.sig[side] + (int64_t)pid * kSigStride;
-  if (p > P || p > NT / LPR) {
+  if (p > P || p > P_T) {
     if (tid == 0) {
       atomicOr(a.status, kStatusTooLarge);
       *rank_out = 0;
@@ -143,86 +205,36 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
     return;
   }
 
-  for (int i = tid; i < P * LDX; i += NT) X[i] = czero<T>();
-  __syncthreads();
-
-  // Columns j0 .. j0+C-1 of A into X[:, P .. P+C) (zero beyond N).
-  auto load_chunk = [&](int j0) {
-    const int cw = min(C, N - j0);
-    if (FROM_R) {
-      for (int jj = warp; jj < C; jj += NW) {
-        const bool in = jj < cw;
-        const C2<T>* c0 = R0 + (int64_t)(off0 + j0 + jj) * ld0;
-        const C2<T>* c1 = R1 + (int64_t)(off1 + j0 + jj) * ld1;
-        for (int r = lane; r < p; r += 32) {
-          C2<T> v = czero<T>();
-          if (in) {
-            if (r < k1) {
-              if (DH2_IN(roff0 + r + (int64_t)(off0 + j0 + jj) * ld0, c_lim.R[side], 1, pid)) v = c0[r];
-            } else {
-              if (DH2_IN(roff1 + (r - k1) + (int64_t)(off1 + j0 + jj) * ld1, c_lim.R[side], 2, pid)) v = c1[r - k1];
-            }
-          }
-          X[r * LDX + P + jj] = v;
-        }
-      }
-    } else if (side == 0) {
-      // rows of t, columns from F_tc: contiguous runs down each G column
-      for (int jj = warp; jj < C; jj += NW) {
-        if (jj < cw && DH2_IN(cmo + j0 + jj, c_lim.ncol[side], 3, pid)) {
-          const int gc = gcol[j0 + jj];
-          const T w = DH2_IN(gblk[j0 + jj], c_lim.nblocks, 4, pid) ? (T)a.invw[gblk[j0 + jj]] : T(0);
-          const C2<T>* col = a.G + (int64_t)gc * a.ld + r0;
-          for (int r = lane; r < p; r += 32) {
-            C2<T> g = czero<T>();
-            if (DH2_IN((int64_t)gc * a.ld + r0 + r, c_lim.G, 5, pid)) g = col[r];
-            X[r * LDX + P + jj] = C2<T>{g.re * w, g.im * w};
-          }
-        } else {
-          for (int r = lane; r < p; r += 32) X[r * LDX + P + jj] = czero<T>();
-        }
-      }
-    } else {
-      // column basis: the same procedure on G^*; row r of A is column r0+r of G
-      for (int r = warp; r < p; r += NW) {
-        const C2<T>* col = a.G + (int64_t)(r0 + r) * a.ld;
-        for (int jj = lane; jj < C; jj += 32) {
-          C2<T> v = czero<T>();
-          if (jj < cw && DH2_IN(cmo + j0 + jj, c_lim.ncol[side], 6, pid) &&
-              DH2_IN((int64_t)(r0 + r) * a.ld + gcol[j0 + jj], c_lim.G, 7, pid) &&
-              DH2_IN(gblk[j0 + jj], c_lim.nblocks, 8, pid)) {
-            const C2<T> g = col[gcol[j0 + jj]];
-            const T w = (T)a.invw[gblk[j0 + jj]];
-            v = C2<T>{g.re * w, -g.im * w};
-          }
-          X[r * LDX + P + jj] = v;
-        }
-      }
-    }
-  };
+  for (int i = tid; i < (P + XTRA) * LDL; i += NT) Lm[i] = czero<T>();
+  DH2_PROF_T(t_a);
 
   // ---------------------------------------------------------------- 1. LQ
   const int row = tid / LPR, q = tid % LPR;
   const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << (lane & ~(LPR - 1)));
+  const bool live = row < p;
+  C2<T> ch[CPL];
 
-  // Householder reflection of row i from the right: the row becomes
-  // (beta, 0, ..., 0) on the columns {i} u chunk, beta = -e^{i arg alpha} |x|.
+  // Householder reflection of row i (held by its LPR threads) from the right:
+  // the row becomes (beta, 0, ..., 0) on the columns {i} u chunk,
+  // beta = -e^{i arg alpha} |x|; the chunk part goes to vbuf[slot].
   auto make_reflector = [&](int i, int slot) {
-    C2<T>* xr = X + i * LDX;
     T s = T(0);
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) s += cnorm2(xr[P + q + u * LPR]);
+    for (int u = 0; u < CPL; ++u) {
+      s += cnorm2(ch[u]);
+      vbuf[slot * C + q + u * LPR] = ch[u];
+    }
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     if (q == 0) {
       if (!(s > Eps<T>::tiny)) {
         sh_skip[slot] = 1;
       } else {
-        const C2<T> al = xr[i];
+        const C2<T> al = Lm[i * LDL + i];
         const T an = hypot(al.re, al.im);
         const T xn = sqrt(s + an * an);
         const C2<T> ph = an > T(0) ? C2<T>{al.re / an, al.im / an} : C2<T>{T(1), T(0)};
-        xr[i] = C2<T>{-ph.re * xn, -ph.im * xn};
+        Lm[i * LDL + i] = C2<T>{-ph.re * xn, -ph.im * xn};
         sh_v0[slot] = C2<T>{ph.re * (an + xn), -ph.im * (an + xn)};
         sh_tau[slot] = T(1) / (xn * (xn + an));
         sh_skip[slot] = 0;
@@ -231,24 +243,25 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
   };
 
   for (int j0 = 0; j0 < N; j0 += C) {
-    load_chunk(j0);
-    __syncthreads();
+    const int cw = min(C, N - j0);
+#pragma unroll
+    for (int u = 0; u < CPL; ++u) {
+      const int jj = q + u * LPR;
+      ch[u] = (live && jj < cw) ? src.get(row, j0 + jj) : czero<T>();
+    }
+    __syncthreads();  // L zeroed / previous chunk's last reflector consumed
     if (row == 0) make_reflector(0, 0);
     __syncthreads();
     for (int i = 0; i < p; ++i) {
       const int sl = i & 1;
-      if (!sh_skip[sl] && row > i && row < p) {
+      if (!sh_skip[sl] && row > i && live) {
         const C2<T> v0 = sh_v0[sl];
         const T tau = sh_tau[sl];
-        C2<T>* zr = X + row * LDX;
-        const C2<T>* xi = X + i * LDX + P;
+        const C2<T>* xi = vbuf + sl * C;
         C2<T> w = czero<T>();
-        if (q == 0) w = cmul(zr[i], v0);
+        if (q == 0) w = cmul(Lm[i * LDL + row], v0);
 #pragma unroll
-        for (int u = 0; u < CPL; ++u) {
-          const int jj = q + u * LPR;
-          w = cadd(w, cmulc(zr[P + jj], xi[jj]));
-        }
+        for (int u = 0; u < CPL; ++u) w = cadd(w, cmulc(ch[u], xi[q + u * LPR]));
 #pragma unroll
         for (int o = 1; o < LPR; o <<= 1) {
           w.re += __shfl_xor_sync(gmask, w.re, o);
@@ -256,44 +269,53 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
         }
         const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
 #pragma unroll
-        for (int u = 0; u < CPL; ++u) {
-          const int jj = q + u * LPR;
-          zr[P + jj] = csub(zr[P + jj], cmul(tw, xi[jj]));
-        }
-        if (q == 0) zr[i] = csub(zr[i], cmulc(tw, v0));
+        for (int u = 0; u < CPL; ++u) ch[u] = csub(ch[u], cmul(tw, xi[q + u * LPR]));
+        if (q == 0) Lm[i * LDL + row] = csub(Lm[i * LDL + row], cmulc(tw, v0));
       }
-      if (row == i + 1 && row < p) make_reflector(i + 1, (i + 1) & 1);
+      if (row == i + 1 && live) make_reflector(i + 1, (i + 1) & 1);
       __syncthreads();
     }
   }
 
+  DH2_PROF_T(t_b);
+  DH2_PROF_ADD(0, t_b - t_a);
   // ---------------------------------------------------------------- 2. Jacobi
+  // one column pair per group of 8 threads; round-robin ordering over pe columns
   const int pe = p + (p & 1);
   const T tol = T(p) * Eps<T>::u;
+  const int grp = tid >> 3, gl = tid & 7;
+  const unsigned m8 = 0xffu << (lane & 24);
   if (tid == 0) {
     sh_rot[0] = 0;
     sh_rot[1] = 0;
   }
   __syncthreads();
   bool conv = false;
+  int nsweeps = 0;
   for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+    ++nsweeps;
     const int sp = sweep & 1;
     for (int rd = 0; rd < pe - 1; ++rd) {
-      for (int kk = warp; kk < pe / 2; kk += NW) {
+      for (int kk = grp; kk < pe / 2; kk += NT / 8) {
         const int ia = kk == 0 ? 0 : ((kk - 1 + rd) % (pe - 1)) + 1;
         const int ib = ((pe - 2 - kk + rd) % (pe - 1)) + 1;
+        C2<T>* ca = Lm + ia * LDL;
+        C2<T>* cb = Lm + ib * LDL;
         T al = T(0), be = T(0);
         C2<T> ga = czero<T>();
-        for (int r = lane; r < p; r += 32) {
-          const C2<T> xa = X[r * LDX + ia], xb = X[r * LDX + ib];
+        for (int r = gl; r < p; r += 8) {
+          const C2<T> xa = ca[r], xb = cb[r];
           al += cnorm2(xa);
           be += cnorm2(xb);
           ga = cadd(ga, cmulc(xb, xa));  // conj(xa) * xb
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga.re = warp_sum(ga.re);
-        ga.im = warp_sum(ga.im);
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+          al += __shfl_xor_sync(m8, al, o);
+          be += __shfl_xor_sync(m8, be, o);
+          ga.re += __shfl_xor_sync(m8, ga.re, o);
+          ga.im += __shfl_xor_sync(m8, ga.im, o);
+        }
         const T gabs = hypot(ga.re, ga.im);
         const T zt = (be - al) / (T(2) * gabs);
         const T t = (zt >= T(0) ? T(1) : T(-1)) / (fabs(zt) + hypot(T(1), zt));
@@ -301,13 +323,13 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
         const T s = t * c;
         if (al > Eps<T>::tiny && be > Eps<T>::tiny && gabs > tol * sqrt(al) * sqrt(be) && s != T(0)) {
           const C2<T> e = C2<T>{ga.re / gabs, -ga.im / gabs};  // e^{-i arg gamma}
-          for (int r = lane; r < p; r += 32) {
-            const C2<T> xa = X[r * LDX + ia];
-            const C2<T> eb = cmul(e, X[r * LDX + ib]);
-            X[r * LDX + ia] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
-            X[r * LDX + ib] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
+          for (int r = gl; r < p; r += 8) {
+            const C2<T> xa = ca[r];
+            const C2<T> eb = cmul(e, cb[r]);
+            ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
+            cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
           }
-          if (lane == 0) sh_rot[sp] = 1;
+          if (gl == 0) sh_rot[sp] = 1;
         }
       }
       __syncthreads();
@@ -321,16 +343,24 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
     }
   }
   if (!conv && tid == 0) atomicOr(a.status, kStatusNoConv);
+  DH2_PROF_T(t_c);
+  DH2_PROF_ADD(1, t_c - t_b);
+  DH2_PROF_ADD(4, nsweeps);
+  DH2_PROF_ADD(5, 1);
+  DH2_PROF_ADD(6, p);
+  DH2_PROF_ADD(7, N);
+  (void)nsweeps;
 
   // ---------------------------------------------------------------- 3. rank
-  for (int j = warp; j < p; j += NW) {
+  for (int j = grp; j < p; j += NT / 8) {
     double s = 0.0;
-    for (int r = lane; r < p; r += 32) {
-      const C2<T> x = X[r * LDX + j];
+    for (int r = gl; r < p; r += 8) {
+      const C2<T> x = Lm[j * LDL + r];
       s += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
     }
-    s = warp_sum(s);
-    if (lane == 0) sig2[j] = s;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(m8, s, o);
+    if (gl == 0) sig2[j] = s;
   }
   __syncthreads();
   // non-finite values (only from non-finite input) are ranked as zero and
@@ -379,44 +409,63 @@ __global__ void __launch_bounds__(256) pair_kernel(const PairArgs<T> a) {
   // ---------------------------------------------------------------- 4. Q
   C2<T>* Qout = a.Q[side] + a.Qoff[side][pid];
   const int ldq = a.rowcap[side][pid];
-  for (int qq = warp; qq < k; qq += NW) {
+  for (int qq = grp; qq < k; qq += NT / 8) {
     const int j = ord[qq];
     const T inv = (T)(1.0 / sqrt(sig2[j]));
-    for (int r = lane; r < p; r += 32) {
-      C2<T> v = X[r * LDX + j];
-      v = C2<T>{v.re * inv, v.im * inv};
-      X[r * LDX + j] = v;
-      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid)) Qout[r + (int64_t)qq * ldq] = v;
+    for (int r = gl; r < p; r += 8) {
+      const C2<T> v = Lm[j * LDL + r];
+      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
+        Qout[r + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
     }
+  }
+  if (k == 0) return;
+  __syncthreads();
+  // compact Q into L columns 0..k-1 (re-read from global, visible after the barrier)
+  for (int idx = tid; idx < p * k; idx += NT) {
+    const int r = idx % p, qq = idx / p;
+    Lm[qq * LDL + r] = Qout[r + (int64_t)qq * ldq];
   }
   __syncthreads();
 
+  DH2_PROF_T(t_d);
+  DH2_PROF_ADD(2, t_d - t_c);
   // ---------------------------------------------------------------- 5. R = Q^* A
-  if (k == 0) return;
   C2<T>* Rout = a.R[side] + a.Roff[side][pid];
-  for (int j0 = 0; j0 < N; j0 += C) {
-    load_chunk(j0);
+  const int CR = min(64, (P + XTRA - k)) & ~7;  // staged columns after Q
+  C2<T>* Ast = Lm + (int64_t)k * LDL;
+  for (int j0 = 0; j0 < N; j0 += CR) {
+    const int cw = min(CR, N - j0);
+    if (FROM_R || side == 0) {
+      for (int jj = warp; jj < cw; jj += NT / 32)
+        for (int r = lane; r < p; r += 32) Ast[jj * LDL + r] = src.get(r, j0 + jj);
+    } else {
+      for (int r = warp; r < p; r += NT / 32)
+        for (int jj = lane; jj < cw; jj += 32) Ast[jj * LDL + r] = src.get(r, j0 + jj);
+    }
     __syncthreads();
-    const int cw = min(C, N - j0);
     for (int idx = tid; idx < k * cw; idx += NT) {
       const int qq = idx % k, jj = idx / k;
-      const int j = ord[qq];
+      const C2<T>* qc = Lm + qq * LDL;
+      const C2<T>* ac = Ast + jj * LDL;
       C2<T> acc = czero<T>();
-      for (int r = 0; r < p; ++r) acc = cadd(acc, cmulc(X[r * LDX + P + jj], X[r * LDX + j]));
+      for (int r = 0; r < p; ++r) acc = cadd(acc, cmulc(ac[r], qc[r]));
       if (DH2_IN(a.Roff[side][pid] + qq + (int64_t)(j0 + jj) * kcap, c_lim.R[side], 11, pid))
         Rout[qq + (int64_t)(j0 + jj) * kcap] = acc;
     }
     __syncthreads();
   }
+  DH2_PROF_T(t_e);
+  DH2_PROF_ADD(3, t_e - t_d);
 }
 
-template <typename T, int C, int LPR, bool FROM_R>
+template <typename T, int P_T, bool FROM_R>
 void launch_one(const PairArgs<T>& a, int nblocks, cudaStream_t st) {
+  constexpr int C = P_T == 64 ? 64 : 32;
   const int P = a.P;
-  const int LDX = P + C + 1;
-  size_t smem = (((size_t)P * LDX * sizeof(C2<T>) + 15) & ~(size_t)15) + (size_t)P * sizeof(double) +
-                (size_t)P * sizeof(int);
-  auto kern = pair_kernel<T, C, LPR, FROM_R>;
+  const int LDL = P + 1;
+  size_t smem = (((size_t)(P + 16) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
+                (size_t)P * sizeof(double) + (size_t)P * sizeof(int);
+  auto kern = pair_kernel<T, P_T, FROM_R>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<nblocks, 256, smem, st>>>(a);
 }
@@ -443,16 +492,32 @@ bool check_read_pair(CheckRecord* out) {
 #endif
 }
 
+void prof_reset_pair() {
+#ifdef DH2_PROFILE
+  unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  cudaMemcpyToSymbol(g_prof, z, sizeof(z));
+#endif
+}
+
+bool prof_read_pair(unsigned long long* out8) {
+#ifdef DH2_PROFILE
+  cudaMemcpyFromSymbol(out8, g_prof, 8 * sizeof(unsigned long long));
+  return true;
+#else
+  (void)out8;
+  return false;
+#endif
+}
+
 template <typename T>
 void launch_pair_kernel(const PairArgs<T>& a, int nblocks, bool from_r, cudaStream_t st) {
   if (nblocks <= 0) return;
-  constexpr bool f32 = sizeof(T) == 4;
   if (!from_r) {
-    if (a.P <= 64) launch_one<T, f32 ? 64 : 32, 4, false>(a, nblocks, st);
-    else launch_one<T, f32 ? 32 : 16, 2, false>(a, nblocks, st);
+    if (a.P <= 64) launch_one<T, 64, false>(a, nblocks, st);
+    else launch_one<T, 128, false>(a, nblocks, st);
   } else {
-    if (a.P <= 64) launch_one<T, f32 ? 64 : 32, 4, true>(a, nblocks, st);
-    else launch_one<T, f32 ? 32 : 16, 2, true>(a, nblocks, st);
+    if (a.P <= 64) launch_one<T, 64, true>(a, nblocks, st);
+    else launch_one<T, 128, true>(a, nblocks, st);
   }
 }
 
