@@ -160,6 +160,29 @@ void dh2_matrix_free(dh2_matrix* M);
  * matrix.  y is overwritten. */
 dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream);
 
+/* Same product as dh2_matvec, for callers that must not allocate device
+ * memory during the call -- for example a solver that reserves all of its
+ * memory once at start-up and may not grow past that budget, or a component
+ * running next to an allocator that others own.  This entry point has no
+ * counterpart in the paper; it exists for those callers only.
+ * It performs no cudaMalloc/cudaFree and calls no allocating library routine:
+ * the per-pair coefficient vectors live in one fixed, library-owned device
+ * array of 8 MiB, which every GPU that loads the library holds until the
+ * process exits.  Requirements and behaviour:
+ *  - the coefficient vectors need sum over pairs of k_cap(t,c) * nrhs complex
+ *    entries for each basis; if that exceeds 8 MiB the call returns
+ *    DH2_EUNSUPPORTED and does nothing (use dh2_matvec, or fewer columns);
+ *  - the device of M must be the current device (else DH2_EINVAL); the first
+ *    call on a device looks the array's device address up once (a CUDA
+ *    runtime query, not an allocation), so make that first call before any
+ *    stream capture;
+ *  - every call uses the same array and it keeps the last call's contents;
+ *    each call writes every coefficient before reading it, but calls whose
+ *    work overlaps on the GPU (different streams, or different threads without
+ *    ordering) race on the array: order them on one stream.
+ * x, y: as for dh2_matvec; y is overwritten. */
+dh2_status dh2_matvec_noalloc(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream);
+
 /* Relative Frobenius error |G_ref - G~|_F / |G_ref|_F, block by block, with
  * G_ref a device matrix of dtype ref_dtype (n x n column-major, permuted
  * order, leading dimension ld).  Synchronises the stream. */

@@ -65,6 +65,7 @@ SIGNATURES = [
                                POINTER(c_void_p)]),
     ("dh2_matrix_free", None, [c_void_p]),
     ("dh2_matvec", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    ("dh2_matvec_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_error", c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_void_p, POINTER(c_double)]),
     ("dh2_matrix_ranks", c_int32, [c_void_p, c_int32, c_void_p]),
     ("dh2_matrix_sigma", c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int32, POINTER(c_int32)]),
@@ -287,6 +288,18 @@ def dh2_matvec(M: Matrix, x, y, stream=None) -> None:
             raise ValueError("x, y must be contiguous")
     _check(_lib().dh2_matvec(M.handle, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), nrhs,
                              c_void_p(_stream_handle(stream))), "dh2_matvec")
+
+
+def dh2_matvec_noalloc(M: Matrix, x, y, stream=None) -> None:
+    """y = G~ x without any device allocation (fixed 8 MiB library scratch array)."""
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    for v in (x, y):
+        if v.dim() == 2 and (v.stride(0) != 1 or v.stride(1) != v.shape[0]):
+            raise ValueError("x, y must be column-major (n, nrhs)")
+        if v.dim() == 1 and v.stride(0) != 1:
+            raise ValueError("x, y must be contiguous")
+    _check(_lib().dh2_matvec_noalloc(M.handle, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), nrhs,
+                                     c_void_p(_stream_handle(stream))), "dh2_matvec_noalloc")
 
 
 def dh2_error(M: Matrix, Gref, stream=None) -> float:

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1063,3 +1064,104 @@ dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms5) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- matvec without allocation
+//
+// dh2_matvec allocates its coefficient vectors (the forward-transformed x and
+// the coupled y, one small vector per (cluster, direction) pair) from the
+// stream-ordered pool on every call.  The variant below takes them from one
+// fixed device array instead, so that a caller that may not allocate device
+// memory at all can still apply a compressed matrix.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB, held by every device that loads the library
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// Device address of the scratch array for the current device; looked up once
+// per device (the array's host-side name is not a device address).
+dh2_status noalloc_scratch_address(int dev, void** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (dev < 0 || dev >= 64) return DH2_EUNSUPPORTED;
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DH2_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return DH2_OK;
+}
+
+template <typename T>
+dh2_status run_matvec_noalloc(const dh2_matrix* M, const void* xv, void* yv, int nrhs, cudaStream_t st) {
+  Tree& tr = M->tree->tr;
+  Tree::Dev* D = tr.dev;
+  const int64_t n = tr.n;
+  const size_t hx = align256(sizeof(C2<T>) * D->h_elems[1] * nrhs);
+  const size_t hy = align256(sizeof(C2<T>) * D->h_elems[0] * nrhs);
+  if (hx + hy > kNoAllocScratchBytes) return DH2_EUNSUPPORTED;
+  int dev = -1;
+  DH2_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != M->device) return DH2_EINVAL;
+  void* buf = nullptr;
+  {
+    const dh2_status s = noalloc_scratch_address(dev, &buf);
+    if (s != DH2_OK) return s;
+  }
+  // every coefficient is written before it is read (forward transformation,
+  // then coupling), so nothing in the scratch array needs clearing
+  C2<T>* xh = (C2<T>*)buf;
+  C2<T>* yh = (C2<T>*)((char*)buf + hx);
+  const C2<T>* x = (const C2<T>*)xv;
+  C2<T>* y = (C2<T>*)yv;
+  DH2_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(C2<T>) * n * nrhs, st));
+  SideView<T> Vv = side_view<T>(tr, M, 0), Wv = side_view<T>(tr, M, 1);
+  launch_mv_forward_leaf<T>(Wv, D->leaf_list[1], (int)D->nleaf[1], x, nrhs, n, xh, D->hoff[1], st);
+  for (int l = tr.depth; l >= 0; --l) {
+    const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
+    if (e > b) launch_mv_forward_up<T>(Wv, D->iota[1] + b, (int)(e - b), nrhs, xh, D->hoff[1], st);
+  }
+  MvArgs<T> a;
+  a.V = Vv;
+  a.W = Wv;
+  a.S = (const C2<T>*)M->S;
+  a.Soff = D->Soff;
+  a.own_ptr = D->own_ptr;
+  a.own_blk = D->own_blk;
+  a.bpair_col = D->bpair[1];
+  a.xh = xh;
+  a.xhoff = D->hoff[1];
+  a.yh = yh;
+  a.yhoff = D->hoff[0];
+  a.par_ptr = D->par_ptr;
+  a.par_pair = D->par_pair;
+  a.par_son = D->par_son;
+  a.bt = D->bt;
+  a.bs = D->bs;
+  a.near = (const C2<T>*)M->near;
+  a.near_off = D->near_off;
+  a.G = (const C2<T>*)M->G;
+  a.ld = M->ld;
+  launch_mv_coupling<T>(a, (int)D->npairs[0], nrhs, st);
+  for (int l = 1; l <= tr.depth; ++l) {
+    const int64_t b = D->lvl_begin[0][l], e = D->lvl_end[0][l];
+    if (e > b) launch_mv_backward_down<T>(a, D->iota[0] + b, (int)(e - b), nrhs, st);
+  }
+  launch_mv_backward_leaf<T>(a, D->leaf_list[0], (int)D->nleaf[0], nrhs, y, n, st);
+  launch_mv_near<T>(a, D->inadm_list, (int)D->ninadm, nrhs, x, y, n, st);
+  DH2_CUDA_TRY(cudaGetLastError());
+  return DH2_OK;
+}
+
+}  // namespace
+
+extern "C" dh2_status dh2_matvec_noalloc(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream) {
+  if (!M || !x || !y || nrhs < 1) return DH2_EINVAL;
+  return M->mode == DH2_MODE_FP32 ? run_matvec_noalloc<float>(M, x, y, nrhs, (cudaStream_t)stream)
+                                  : run_matvec_noalloc<double>(M, x, y, nrhs, (cudaStream_t)stream);
+}
