@@ -191,10 +191,14 @@ dh2_status dh2_error(const dh2_matrix* M, const void* G_ref, dh2_dtype ref_dtype
 
 /* Ranks of the used pairs of one side (host, npairs entries). */
 dh2_status dh2_matrix_ranks(const dh2_matrix* M, int32_t side, int32_t* ranks);
-/* Singular values computed for one pair (host, up to `cap` doubles, sorted
- * descending); *count receives the number of values (rows of the factor). */
+/* Singular values resolved individually for one pair (host, up to `cap`
+ * doubles, sorted descending); *count receives how many were resolved.  The
+ * factorisation stops resolving once the remaining energy is below a small
+ * fraction of eps_l^2; dh2_matrix_sigma_rest gives that energy (the sum of
+ * the squares of the unresolved singular values, up to rounding). */
 dh2_status dh2_matrix_sigma(const dh2_matrix* M, int32_t side, int64_t pair, double* out, int32_t cap,
                             int32_t* count);
+dh2_status dh2_matrix_sigma_rest(const dh2_matrix* M, int32_t side, int64_t pair, double* energy);
 /* Stored matrix of one pair, copied to the host as complex128: a leaf pair's
  * basis Q_tc (rows = cluster size) or a non-leaf pair's [E_t1c; E_t2c]
  * (rows = k_t1c' + k_t2c').  out: rows x k column-major, ld = rows. */

@@ -69,6 +69,7 @@ SIGNATURES = [
     ("dh2_error", c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_void_p, POINTER(c_double)]),
     ("dh2_matrix_ranks", c_int32, [c_void_p, c_int32, c_void_p]),
     ("dh2_matrix_sigma", c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int32, POINTER(c_int32)]),
+    ("dh2_matrix_sigma_rest", c_int32, [c_void_p, c_int32, c_int64, POINTER(c_double)]),
     ("dh2_matrix_pair_basis", c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int64, POINTER(c_int32),
                                         POINTER(c_int32)]),
     ("dh2_matrix_coupling", c_int32, [c_void_p, c_int64, c_void_p, c_int64, POINTER(c_int32), POINTER(c_int32)]),
@@ -226,10 +227,17 @@ class Matrix:
         return out
 
     def sigma(self, side: int, pair: int) -> np.ndarray:
+        """Singular values resolved individually (descending)."""
         out = np.empty(128)
         cnt = c_int32()
         _check(_lib().dh2_matrix_sigma(self.handle, side, pair, _ptr(out), 128, byref(cnt)), "dh2_matrix_sigma")
         return out[:min(cnt.value, 128)].copy()
+
+    def sigma_rest(self, side: int, pair: int) -> float:
+        """Sum of squares of the singular values not resolved individually."""
+        e = c_double()
+        _check(_lib().dh2_matrix_sigma_rest(self.handle, side, pair, byref(e)), "dh2_matrix_sigma_rest")
+        return float(e.value)
 
     def pair_basis(self, side: int, pair: int) -> np.ndarray:
         cap = 128 * 128

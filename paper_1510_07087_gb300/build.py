@@ -41,6 +41,10 @@ def build(verbose: bool = False) -> str:
     extra = ["-DDH2_CHECK"] if os.environ.get("DH2_CHECK") == "1" else []
     if os.environ.get("DH2_PROFILE") == "1":
         extra.append("-DDH2_PROFILE")
+    if os.environ.get("DH2_SKIP_NEGLIGIBLE") == "1":
+        extra.append("-DDH2_SKIP_NEGLIGIBLE")
+    if os.environ.get("DH2_PAIR_MINB"):
+        extra.append("-DDH2_PAIR_MINB=" + str(int(os.environ["DH2_PAIR_MINB"])))
     for src in CUDA_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)

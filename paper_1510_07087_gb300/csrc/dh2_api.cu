@@ -477,7 +477,7 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
     prof_read_pair(pr);
     const double np = pr[5] ? (double)pr[5] : 1.0;
     std::fprintf(stderr,
-                 "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean N %.1f, mean sweeps %.2f, cycles/pair: "
+                 "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean K %.1f, mean sweeps %.2f, cycles/pair: "
                  "LQ %.0f Jacobi %.0f rank+Q %.0f R %.0f\n",
                  pr[5], pr[6] / np, pr[7] / np, pr[4] / np, pr[0] / np, pr[1] / np, pr[2] / np, pr[3] / np);
   }
@@ -944,20 +944,22 @@ dh2_status dh2_matrix_sigma(const dh2_matrix* M, int32_t side, int64_t pair, dou
   if (!M || !out || (side != 0 && side != 1)) return DH2_EINVAL;
   const Tree& tr = M->tree->tr;
   if (pair < 0 || pair >= (int64_t)tr.side[side].pairs.size()) return DH2_EINVAL;
-  const Pair& P = tr.side[side].pairs[pair];
-  int32_t rows = 0;
-  if (P.leaf) {
-    rows = tr.size[P.cluster];
-  } else {
-    int32_t k[2];
-    for (int j = 0; j < 2; ++j)
-      DH2_CUDA_TRY(cudaMemcpy(&k[j], M->rank[side] + P.son_pair[j], 4, cudaMemcpyDeviceToHost));
-    rows = k[0] + k[1];
-  }
-  const int32_t c = std::min(rows, std::min(cap, kSigStride));
   DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
-  DH2_CUDA_TRY(cudaMemcpy(out, M->sig[side] + pair * kSigStride, 8 * (size_t)c, cudaMemcpyDeviceToHost));
-  if (count) *count = rows;
+  double buf[kSigStride];
+  DH2_CUDA_TRY(cudaMemcpy(buf, M->sig[side] + pair * kSigStride, sizeof(buf), cudaMemcpyDeviceToHost));
+  const int32_t resolved = (int32_t)buf[kSigValues];
+  const int32_t c = std::max(0, std::min(resolved, std::min(cap, kSigValues)));
+  std::memcpy(out, buf, 8 * (size_t)c);
+  if (count) *count = resolved;
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_sigma_rest(const dh2_matrix* M, int32_t side, int64_t pair, double* energy) {
+  if (!M || !energy || (side != 0 && side != 1)) return DH2_EINVAL;
+  const Tree& tr = M->tree->tr;
+  if (pair < 0 || pair >= (int64_t)tr.side[side].pairs.size()) return DH2_EINVAL;
+  DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  DH2_CUDA_TRY(cudaMemcpy(energy, M->sig[side] + pair * kSigStride + kSigValues + 1, 8, cudaMemcpyDeviceToHost));
   return DH2_OK;
 }
 

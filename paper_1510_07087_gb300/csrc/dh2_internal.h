@@ -17,8 +17,10 @@ constexpr int kSideCol = 1;
 // for a non-leaf pair) the pair kernels accept, per real type.
 constexpr int kPmaxF32 = 128;
 constexpr int kPmaxF64 = 96;
-// Singular values stored per pair (the largest factor size).
-constexpr int kSigStride = 128;
+// Singular values stored per pair: kSigValues values (the largest factor
+// size), then the number resolved individually and the energy of the rest.
+constexpr int kSigValues = 128;
+constexpr int kSigStride = kSigValues + 2;
 
 // Device status bits (OR-ed by kernels into one word).
 constexpr uint32_t kStatusNoConv = 1u;

@@ -79,6 +79,14 @@ struct Eps<double> {
   static constexpr double tiny = 1e-280;
 };
 
+// Reciprocal square root and quotient for the rotation and reflector scalars:
+// hardware approximations in FP32 (a few ulp; the rotations and reflections
+// stay unitary to that level), correctly rounded in FP64.
+__device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
 // Element (r, j) of the pair's matrix A (row r of the factor, column j of F_tc).
 template <typename T, bool FROM_R>
 struct Source {
@@ -130,7 +138,10 @@ struct Source {
 
 // P_T: largest factor size of the instantiation (64 or 128 rows).
 template <typename T, int P_T, bool FROM_R>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const PairArgs<T> a) {
+#ifndef DH2_PAIR_MINB
+#define DH2_PAIR_MINB 3
+#endif
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1) pair_kernel(const PairArgs<T> a) {
   constexpr int NT = 256;
   constexpr int LPR = NT / P_T;      // threads per row in the LQ
   constexpr int C = P_T == 64 ? 64 : 32;
@@ -143,6 +154,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
   __shared__ int sh_skip[2];
   __shared__ int sh_rot[2];
   __shared__ int sh_k;
+  __shared__ int sh_piv;
+  __shared__ double sh_E;
 
   const int P = a.P;
   const int LDL = P + 1;              // column-major L: element (r, c) at c * LDL + r
@@ -153,6 +166,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
   double* sig2 = reinterpret_cast<double*>(smem + soff);
   soff += (size_t)P * sizeof(double);
   int* ord = reinterpret_cast<int*>(smem + soff);
+  soff += (size_t)P * sizeof(int);
+  int* perm = reinterpret_cast<int*>(smem + soff);  // row permutation of the pivoted LQ
+  soff += (size_t)P * sizeof(int);
+  T* nu = reinterpret_cast<T*>(smem + soff);         // residual row norms
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int code = a.order[blockIdx.x];
@@ -218,12 +235,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
   // the row becomes (beta, 0, ..., 0) on the columns {i} u chunk,
   // beta = -e^{i arg alpha} |x|; the chunk part goes to vbuf[slot].
   auto make_reflector = [&](int i, int slot) {
-    T s = T(0);
+    T s0 = T(0), s1 = T(0);
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) {
-      s += cnorm2(ch[u]);
+    for (int u = 0; u < CPL; u += 2) {
+      s0 += cnorm2(ch[u]);
+      s1 += cnorm2(ch[u + 1]);
       vbuf[slot * C + q + u * LPR] = ch[u];
+      vbuf[slot * C + q + (u + 1) * LPR] = ch[u + 1];
     }
+    T s = s0 + s1;
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
     if (q == 0) {
@@ -231,12 +251,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
         sh_skip[slot] = 1;
       } else {
         const C2<T> al = Lm[i * LDL + i];
-        const T an = hypot(al.re, al.im);
-        const T xn = sqrt(s + an * an);
-        const C2<T> ph = an > T(0) ? C2<T>{al.re / an, al.im / an} : C2<T>{T(1), T(0)};
+        const T an2 = cnorm2(al);
+        const T ra = an2 > Eps<T>::tiny ? frsqrt(an2) : T(0);
+        const T an = an2 * ra;
+        const T xn2 = s + an2;
+        const T xn = xn2 * frsqrt(xn2);
+        const C2<T> ph = an2 > Eps<T>::tiny ? C2<T>{al.re * ra, al.im * ra} : C2<T>{T(1), T(0)};
         Lm[i * LDL + i] = C2<T>{-ph.re * xn, -ph.im * xn};
         sh_v0[slot] = C2<T>{ph.re * (an + xn), -ph.im * (an + xn)};
-        sh_tau[slot] = T(1) / (xn * (xn + an));
+        sh_tau[slot] = fdiv(T(1), xn * (xn + an));
         sh_skip[slot] = 0;
       }
     }
@@ -258,10 +281,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
         const C2<T> v0 = sh_v0[sl];
         const T tau = sh_tau[sl];
         const C2<T>* xi = vbuf + sl * C;
-        C2<T> w = czero<T>();
+        C2<T> w = czero<T>(), w1 = czero<T>();
         if (q == 0) w = cmul(Lm[i * LDL + row], v0);
 #pragma unroll
-        for (int u = 0; u < CPL; ++u) w = cadd(w, cmulc(ch[u], xi[q + u * LPR]));
+        for (int u = 0; u < CPL; u += 2) {
+          w = cadd(w, cmulc(ch[u], xi[q + u * LPR]));
+          w1 = cadd(w1, cmulc(ch[u + 1], xi[q + (u + 1) * LPR]));
+        }
+        w = cadd(w, w1);
 #pragma unroll
         for (int o = 1; o < LPR; o <<= 1) {
           w.re += __shfl_xor_sync(gmask, w.re, o);
@@ -279,9 +306,132 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
 
   DH2_PROF_T(t_b);
   DH2_PROF_ADD(0, t_b - t_a);
+
+  // ---------------------------------------------------------------- 1b. pivoted LQ of L
+  // Rank-revealing step: L = Pi^T L' Omega' by Householder reflections from
+  // the right with row pivoting (largest residual row first).  It stops at the
+  // first K whose remaining block L'(K:, K:) has energy E_K <= drop * eps_l^2;
+  // that energy is added to every tail sum below (an upper bound on the
+  // residual of the chosen subspace), and the Jacobi step works on the K
+  // leading columns only.  Pi is kept in perm[].
+  const double drop = sizeof(T) == 4 ? 1e-2 : 1e-10;
+  const double tau_drop = drop * a.eps2[lvl];
+  for (int r = tid; r < P; r += NT) perm[r] = r;
+  int K = p;
+  double E_K = 0.0;
+  for (int i = 0; i < p; ++i) {
+    // residual row norms over columns i..p-1 (row i-1 becomes final: zero its tail)
+    if (i > 0 && row == i - 1)
+      for (int c = i + q; c < p; c += LPR) Lm[c * LDL + row] = czero<T>();
+    if (row >= i && live) {
+      T s = T(0);
+      for (int c = i + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + row]);
+#pragma unroll
+      for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
+      if (q == 0) nu[row] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double e = 0.0;
+      T best = T(-1);
+      int bi = i;
+      for (int r = i + lane; r < p; r += 32) {
+        const T v = nu[r];
+        e += (double)v;
+        if (v > best) {
+          best = v;
+          bi = r;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        sh_E = e;
+        sh_piv = bi;
+      }
+    }
+    __syncthreads();
+    if (sh_E <= tau_drop) {
+      K = i;
+      E_K = sh_E;
+      break;
+    }
+    const int pv = sh_piv;
+    if (pv != i) {
+      for (int c = tid; c < p; c += NT) {
+        const C2<T> t0 = Lm[c * LDL + i];
+        Lm[c * LDL + i] = Lm[c * LDL + pv];
+        Lm[c * LDL + pv] = t0;
+      }
+      if (tid == 0) {
+        const int t1 = perm[i];
+        perm[i] = perm[pv];
+        perm[pv] = t1;
+      }
+    }
+    __syncthreads();
+    if (row == i) {
+      // reflector of row i over columns i..p-1
+      T s = T(0);
+      for (int c = i + 1 + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + i]);
+#pragma unroll
+      for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
+      if (q == 0) {
+        if (!(s > Eps<T>::tiny)) {
+          sh_skip[0] = 1;
+        } else {
+          const C2<T> al = Lm[i * LDL + i];
+          const T an2 = cnorm2(al);
+          const T ra = an2 > Eps<T>::tiny ? frsqrt(an2) : T(0);
+          const T an = an2 * ra;
+          const T xn2 = s + an2;
+          const T xn = xn2 * frsqrt(xn2);
+          const C2<T> ph = an2 > Eps<T>::tiny ? C2<T>{al.re * ra, al.im * ra} : C2<T>{T(1), T(0)};
+          Lm[i * LDL + i] = C2<T>{-ph.re * xn, -ph.im * xn};
+          sh_v0[0] = C2<T>{ph.re * (an + xn), -ph.im * (an + xn)};
+          sh_tau[0] = fdiv(T(1), xn * (xn + an));
+          sh_skip[0] = 0;
+        }
+      }
+    }
+    __syncthreads();
+    if (!sh_skip[0] && row > i && live) {
+      const C2<T> v0 = sh_v0[0];
+      const T tau = sh_tau[0];
+      C2<T> w = czero<T>();
+      if (q == 0) w = cmul(Lm[i * LDL + row], v0);
+      for (int c = i + 1 + q; c < p; c += LPR) w = cadd(w, cmulc(Lm[c * LDL + row], Lm[c * LDL + i]));
+#pragma unroll
+      for (int o = 1; o < LPR; o <<= 1) {
+        w.re += __shfl_xor_sync(gmask, w.re, o);
+        w.im += __shfl_xor_sync(gmask, w.im, o);
+      }
+      const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
+      for (int c = i + 1 + q; c < p; c += LPR)
+        Lm[c * LDL + row] = csub(Lm[c * LDL + row], cmul(tw, Lm[c * LDL + i]));
+      if (q == 0) Lm[i * LDL + row] = csub(Lm[i * LDL + row], cmulc(tw, v0));
+    }
+    __syncthreads();
+  }
+  // the last processed row keeps its (already applied) tail: zero it; with K
+  // odd, column K holds residual entries and is cleared for the pairing
+  if (K > 0 && row == K - 1)
+    for (int c = K + q; c < p; c += LPR) Lm[c * LDL + row] = czero<T>();
+  __syncthreads();
+  if ((K & 1) && K < P)
+    for (int r = tid; r < p; r += NT) Lm[K * LDL + r] = czero<T>();
+  __syncthreads();
   // ---------------------------------------------------------------- 2. Jacobi
   // one column pair per group of 8 threads; round-robin ordering over pe columns
-  const int pe = p + (p & 1);
+  const int pe = K + (K & 1);
   const T tol = T(p) * Eps<T>::u;
   const int grp = tid >> 3, gl = tid & 7;
   const unsigned m8 = 0xffu << (lane & 24);
@@ -290,46 +440,64 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
     sh_rot[1] = 0;
   }
   __syncthreads();
-  bool conv = false;
+  bool conv = pe < 2;
   int nsweeps = 0;
-  for (int sweep = 0; sweep < a.max_sweeps; ++sweep) {
+  for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
     ++nsweeps;
     const int sp = sweep & 1;
-    for (int rd = 0; rd < pe - 1; ++rd) {
-      for (int kk = grp; kk < pe / 2; kk += NT / 8) {
-        const int ia = kk == 0 ? 0 : ((kk - 1 + rd) % (pe - 1)) + 1;
-        const int ib = ((pe - 2 - kk + rd) % (pe - 1)) + 1;
-        C2<T>* ca = Lm + ia * LDL;
-        C2<T>* cb = Lm + ib * LDL;
-        T al = T(0), be = T(0);
-        C2<T> ga = czero<T>();
-        for (int r = gl; r < p; r += 8) {
-          const C2<T> xa = ca[r], xb = cb[r];
-          al += cnorm2(xa);
-          be += cnorm2(xb);
-          ga = cadd(ga, cmulc(xb, xa));  // conj(xa) * xb
-        }
+    // round-robin positions of this group's pairs in round 0; each round
+    // moves every position but the fixed one (index 0) by one place
+    int ia[P_T / 64], ib[P_T / 64];
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-          al += __shfl_xor_sync(m8, al, o);
-          be += __shfl_xor_sync(m8, be, o);
-          ga.re += __shfl_xor_sync(m8, ga.re, o);
-          ga.im += __shfl_xor_sync(m8, ga.im, o);
-        }
-        const T gabs = hypot(ga.re, ga.im);
-        const T zt = (be - al) / (T(2) * gabs);
-        const T t = (zt >= T(0) ? T(1) : T(-1)) / (fabs(zt) + hypot(T(1), zt));
-        const T c = T(1) / sqrt(T(1) + t * t);
-        const T s = t * c;
-        if (al > Eps<T>::tiny && be > Eps<T>::tiny && gabs > tol * sqrt(al) * sqrt(be) && s != T(0)) {
-          const C2<T> e = C2<T>{ga.re / gabs, -ga.im / gabs};  // e^{-i arg gamma}
+    for (int h = 0; h < P_T / 64; ++h) {
+      const int kk = grp + h * (NT / 8);
+      ia[h] = kk;
+      ib[h] = pe - 1 - kk;
+    }
+    for (int rd = 0; rd < pe - 1; ++rd) {
+#pragma unroll
+      for (int h = 0; h < P_T / 64; ++h) {
+        const int kk = grp + h * (NT / 8);
+        if (kk < pe / 2) {
+          C2<T>* ca = Lm + ia[h] * LDL;
+          C2<T>* cb = Lm + ib[h] * LDL;
+          T al = T(0), be = T(0);
+          C2<T> ga = czero<T>();
           for (int r = gl; r < p; r += 8) {
-            const C2<T> xa = ca[r];
-            const C2<T> eb = cmul(e, cb[r]);
-            ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
-            cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
+            const C2<T> xa = ca[r], xb = cb[r];
+            al += cnorm2(xa);
+            be += cnorm2(xb);
+            ga = cadd(ga, cmulc(xb, xa));  // conj(xa) * xb
           }
-          if (gl == 0) sh_rot[sp] = 1;
+#pragma unroll
+          for (int o = 1; o < 8; o <<= 1) {
+            al += __shfl_xor_sync(m8, al, o);
+            be += __shfl_xor_sync(m8, be, o);
+            ga.re += __shfl_xor_sync(m8, ga.re, o);
+            ga.im += __shfl_xor_sync(m8, ga.im, o);
+          }
+          const T g2 = cnorm2(ga);
+          // rotate unless the pair is orthogonal to tol (relative)
+          if (al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
+              sqrt(g2) * frsqrt(al) * frsqrt(be) > tol) {
+            const T rg = frsqrt(g2);
+            const T zt = (be - al) * T(0.5) * rg;
+            const T t = (zt >= T(0) ? T(1) : T(-1)) / (fabs(zt) + sqrt(T(1) + zt * zt));
+            const T c = T(1) / sqrt(T(1) + t * t);
+            const T s = t * c;
+            if (s != T(0)) {
+              const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
+              for (int r = gl; r < p; r += 8) {
+                const C2<T> xa = ca[r];
+                const C2<T> eb = cmul(e, cb[r]);
+                ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
+                cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
+              }
+              if (gl == 0) sh_rot[sp] = 1;
+            }
+          }
+          if (kk > 0) ia[h] = ia[h] == pe - 1 ? 1 : ia[h] + 1;
+          ib[h] = ib[h] == pe - 1 ? 1 : ib[h] + 1;
         }
       }
       __syncthreads();
@@ -348,11 +516,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
   DH2_PROF_ADD(4, nsweeps);
   DH2_PROF_ADD(5, 1);
   DH2_PROF_ADD(6, p);
-  DH2_PROF_ADD(7, N);
+  DH2_PROF_ADD(7, K);
   (void)nsweeps;
 
   // ---------------------------------------------------------------- 3. rank
-  for (int j = grp; j < p; j += NT / 8) {
+  for (int j = grp; j < K; j += NT / 8) {
     double s = 0.0;
     for (int r = gl; r < p; r += 8) {
       const C2<T> x = Lm[j * LDL + r];
@@ -365,7 +533,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
   __syncthreads();
   // non-finite values (only from non-finite input) are ranked as zero and
   // reported; ord stays a permutation of 0..p-1 in every case
-  if (tid < p) {
+  if (tid < K) {
     ord[tid] = tid;
     if (!(sig2[tid] >= 0.0 && sig2[tid] <= 1.0e300)) {
       sig2[tid] = 0.0;
@@ -374,22 +542,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
   }
   __syncthreads();
   int rk = -1;
-  if (tid < p) {
+  if (tid < K) {
     const double v = sig2[tid];
     rk = 0;
-    for (int i = 0; i < p; ++i) {
+    for (int i = 0; i < K; ++i) {
       const double u = sig2[i];
       rk += (u > v) || (u == v && i < tid);
     }
   }
   __syncthreads();
-  if (rk >= 0 && rk < p) ord[rk] = tid;
+  if (rk >= 0 && rk < K) ord[rk] = tid;
   __syncthreads();
   if (tid == 0) {
     const double e2 = a.eps2[lvl];
-    double tail = 0.0;
-    int k = p;
-    for (int r = p - 1; r >= 0; --r) {
+    double tail = E_K;
+    int k = K;
+    for (int r = K - 1; r >= 0; --r) {
       const double v = sig2[ord[r]];
       if (tail + v <= e2) {
         tail += v;
@@ -402,7 +570,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
     sh_k = k;
     *rank_out = k;
   }
-  for (int r = tid; r < kSigStride; r += NT) sig_out[r] = r < p ? sqrt(sig2[ord[r]]) : 0.0;
+  for (int r = tid; r < kSigValues; r += NT) sig_out[r] = r < K ? sqrt(sig2[ord[r]]) : 0.0;
+  if (tid == 0) {
+    sig_out[kSigValues] = (double)K;    // singular values resolved individually
+    sig_out[kSigValues + 1] = E_K;      // energy of the rest (sum of their squares)
+  }
   __syncthreads();
   const int k = sh_k;
 
@@ -414,8 +586,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) pair_kernel(const
     const T inv = (T)(1.0 / sqrt(sig2[j]));
     for (int r = gl; r < p; r += 8) {
       const C2<T> v = Lm[j * LDL + r];
-      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
-        Qout[r + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
+      const int ro = perm[r];
+      if (DH2_IN(a.Qoff[side][pid] + ro + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
+        Qout[ro + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
     }
   }
   if (k == 0) return;
@@ -464,7 +637,7 @@ void launch_one(const PairArgs<T>& a, int nblocks, cudaStream_t st) {
   const int P = a.P;
   const int LDL = P + 1;
   size_t smem = (((size_t)(P + 16) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
-                (size_t)P * sizeof(double) + (size_t)P * sizeof(int);
+                (size_t)P * sizeof(double) + 2 * (size_t)P * sizeof(int) + (size_t)P * sizeof(T);
   auto kern = pair_kernel<T, P_T, FROM_R>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<nblocks, 256, smem, st>>>(a);

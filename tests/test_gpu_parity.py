@@ -162,7 +162,16 @@ def test_fp64_leaf_subspaces(c1_fp64):
             assert np.linalg.norm(Qg.conj().T @ Qg - np.eye(k)) < 1e-12
             assert np.linalg.norm(Qg @ Qg.conj().T - Q @ Q.conj().T) < 1e-9
             sg = c.M.sigma(side, c.pid[(side, t, cc)])
-            np.testing.assert_allclose(sg[:len(sig)], sig, rtol=1e-9, atol=1e-13 * sig[0])
+            rest = c.M.sigma_rest(side, c.pid[(side, t, cc)])
+            K = len(sg)
+            assert K >= k
+            # dropping the residual block moves each singular value by at most
+            # sqrt(rest) (Weyl's inequality)
+            np.testing.assert_allclose(sg, sig[:K], rtol=1e-9, atol=1e-13 * sig[0] + np.sqrt(rest))
+            # the unresolved singular values: their energy, far below eps_l^2
+            eps2 = B.eps_level[c.tr.level[t]] ** 2
+            assert rest <= 1e-9 * eps2
+            assert abs(np.sum(sig[K:] ** 2) - rest) <= 1e-12 * sig[0] ** 2 + 1e-3 * rest
             checked += 1
     assert checked > 100
 
