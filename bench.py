@@ -29,6 +29,15 @@ if ROOT not in sys.path:
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
+# FP32 ALU peak of the GB300 from its unit counts: 152 SMs x 128 FP32 lanes x
+# 2 flops per FMA x 2.07 GHz maximum SM clock.
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes (read + write) of one leaf launch of the pair kernel at n=32768,
+# kappa=32, leaf 64, FP32, from a 1-pass ncu capture (profiles/); valid only
+# for the kernel source it was measured on (sha1 of csrc/dh2_pair.cu).
+PAIR_TRAFFIC = {"sha1": "2514f945ea6cd49f4903b1246033a729ca7ddbd7", "bytes": 10.92e9 + 1.85e9}
+
 
 def _peaks():
     try:
@@ -256,12 +265,32 @@ def run_gpu(args):
     peaks, src = _peaks()
     adm_bytes = elem * st.adm_fraction * args.n * args.n
     leaf_ms = float(phases[1])
-    # dominant kernel: the leaf factorisation launch; algorithmic bytes = one
-    # read of every admissible entry of G (each feeds one row and one column pair)
-    roof = {"bound": "hbm", "kernel": "pair_kernel (leaf launch)", "achieved": adm_bytes / (leaf_ms * 1e-3) / 1e9,
-            "peak": peaks["hbm_gbs"], "peak_source": src, "unit": "GB/s",
-            "frac": adm_bytes / (leaf_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
-            "alg_bytes_per_launch": adm_bytes}
+    # algorithmic flops of the leaf launch (per pair and basis: factor 4 m^2 N,
+    # R = Q^* A 8 k m N; real flops), summed with the computed ranks
+    size = T.clusters()["size"].astype(np.float64)
+    flops = 0.0
+    for sd in (0, 1):
+        pr = T.pairs(sd)
+        lf = pr["leaf"].astype(bool)
+        m = size[pr["cluster"]][lf]
+        N = pr["ncols"][lf].astype(np.float64)
+        k = ranks[sd][lf].astype(np.float64)
+        flops += float(np.sum(4.0 * m * m * N + 8.0 * k * m * N))
+    import hashlib
+    src_sha = hashlib.sha1(open(os.path.join(ROOT, "paper_1510_07087_gb300", "csrc", "dh2_pair.cu"), "rb")
+                           .read()).hexdigest()
+    traffic = (PAIR_TRAFFIC["bytes"] if (src_sha == PAIR_TRAFFIC["sha1"] and args.n == 32768 and args.leaf == 64
+                                         and args.mode == "fp32") else None)
+    achieved = flops / (leaf_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "pair_kernel (leaf launch: LQ, pivoted truncation, Jacobi, R)",
+            "achieved": achieved, "peak": FP32_ALU_TFLOPS, "peak_source": "derived (152 SM x 128 FP32 x 2 x 2.07 GHz)",
+            "unit": "TFLOP/s", "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic,
+            "alg_flops_per_launch": flops, "alg_bytes_per_launch": adm_bytes,
+            "hbm_view": {"achieved_gbs": adm_bytes / (leaf_ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                         "frac": adm_bytes / (leaf_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": src}}
+    t_roof_ms = in_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    step_roof = {"bound": "hbm", "t_roof_ms": t_roof_ms, "frac": t_roof_ms / ms,
+                 "note": "one read of all of G at the measured copy bandwidth, against the whole step"}
     # kernels per compress: norms/nearfield, leaf factors, one non-leaf launch
     # per level with non-leaf pairs, one expansion launch per level with
     # non-leaf column pairs, projection
@@ -286,7 +315,7 @@ def run_gpu(args):
             ["norms_nearfield", "leaf_factors", "level_steps", "expansion", "projection"], phases)},
         "k_max": int(max(ranks[0].max(initial=0), ranks[1].max(initial=0))),
         "mem_per_n_kib_c128": storage["total"] * 16 / 1024 / args.n,
-        "adm_fraction": st.adm_fraction, "roofline": roof, "e2e": e2e,
+        "adm_fraction": st.adm_fraction, "roofline": roof, "step_roofline": step_roof, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": launches * args.steps, "launches_per_step": launches,
     }
     return line

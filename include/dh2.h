@@ -152,6 +152,18 @@ dh2_status dh2_tree_pair_blocks(const dh2_tree* tree, int32_t side, int64_t* off
  * DH2_ENOCONV / DH2_EUNSUPPORTED from the device status word, DH2_ECUDA. */
 dh2_status dh2_compress(const dh2_tree* tree, const void* G, dh2_dtype dtype, int64_t ld,
                         const dh2_compress_params* params, void* stream, dh2_matrix** out);
+/* Matrix-free compression of the Helmholtz collocation matrix
+ * G_ij = exp(i kappa |x_i - x_j|) / (4 pi |x_i - x_j|) (Eq. helmholtz), with
+ * `diag` on the diagonal: every entry the compression reads (block norms,
+ * leaf factors, R, nearfield copy) is generated in the kernels from the
+ * points, so no dense G is needed.  pts_xyz: host, n x 3 row-major doubles in
+ * the caller's order (the array given to dh2_tree_build), copied during the
+ * call.  params->mode selects FP32 (complex64 entries: distances and phase
+ * reduction in FP64, sin/cos of the reduced phase in FP32) or FP64.  The
+ * nearfield is always copied (params->nearfield must be 0).  dh2_error on the
+ * result accepts G_ref = NULL: the reference is then generated in FP64. */
+dh2_status dh2_compress_kernel(const dh2_tree* tree, const double* pts_xyz, double kappa, double diag,
+                               const dh2_compress_params* params, void* stream, dh2_matrix** out);
 void dh2_matrix_free(dh2_matrix* M);
 
 /* y = G~ x for the compressed matrix (Section 4: forward transformation,
@@ -185,7 +197,8 @@ dh2_status dh2_matvec_noalloc(const dh2_matrix* M, const void* x, void* y, int32
 
 /* Relative Frobenius error |G_ref - G~|_F / |G_ref|_F, block by block, with
  * G_ref a device matrix of dtype ref_dtype (n x n column-major, permuted
- * order, leading dimension ld).  Synchronises the stream. */
+ * order, leading dimension ld), or NULL for a matrix from dh2_compress_kernel
+ * (reference entries generated in FP64).  Synchronises the stream. */
 dh2_status dh2_error(const dh2_matrix* M, const void* G_ref, dh2_dtype ref_dtype, int64_t ld,
                      void* stream, double* rel_err);
 

@@ -63,6 +63,8 @@ SIGNATURES = [
     ("dh2_tree_pair_blocks", c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     ("dh2_compress", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p,
                                POINTER(c_void_p)]),
+    ("dh2_compress_kernel", c_int32, [c_void_p, c_void_p, c_double, c_double, POINTER(CompressParams), c_void_p,
+                                      POINTER(c_void_p)]),
     ("dh2_matrix_free", None, [c_void_p]),
     ("dh2_matvec", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_matvec_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
@@ -286,6 +288,18 @@ def dh2_compress(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_
     return Matrix(h.value, tree, mode, G)
 
 
+def dh2_compress_kernel(tree: Tree, points: np.ndarray, kappa: float, diag: float, eps: float = 1e-4,
+                        zeta: float = 2.0 / 3.0, err_mode: int = 0, mode: int = MODE_FP32, max_sweeps: int = 0,
+                        stream=None) -> Matrix:
+    """Matrix-free compression of the Helmholtz collocation matrix of `points` (caller order)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), 0, int(max_sweeps))
+    h = c_void_p()
+    _check(_lib().dh2_compress_kernel(tree.handle, _ptr(pts), float(kappa), float(diag), byref(p),
+                                      c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress_kernel")
+    return Matrix(h.value, tree, mode, None)
+
+
 def dh2_matvec(M: Matrix, x, y, stream=None) -> None:
     """y = G~ x; x, y torch device tensors (n,) or (n, nrhs) column-major, matrix dtype."""
     nrhs = 1 if x.dim() == 1 else x.shape[1]
@@ -310,10 +324,14 @@ def dh2_matvec_noalloc(M: Matrix, x, y, stream=None) -> None:
                                      c_void_p(_stream_handle(stream))), "dh2_matvec_noalloc")
 
 
-def dh2_error(M: Matrix, Gref, stream=None) -> float:
+def dh2_error(M: Matrix, Gref=None, stream=None) -> float:
+    """|G_ref - G~|_F / |G_ref|_F; Gref=None for a matrix-free compression (reference generated in FP64)."""
     out = c_double()
-    _check(_lib().dh2_error(M.handle, c_void_p(Gref.data_ptr()), _dtype_code(Gref), _colmajor_ld(Gref),
-                            c_void_p(_stream_handle(stream)), byref(out)), "dh2_error")
+    if Gref is None:
+        _check(_lib().dh2_error(M.handle, None, 0, 0, c_void_p(_stream_handle(stream)), byref(out)), "dh2_error")
+    else:
+        _check(_lib().dh2_error(M.handle, c_void_p(Gref.data_ptr()), _dtype_code(Gref), _colmajor_ld(Gref),
+                                c_void_p(_stream_handle(stream)), byref(out)), "dh2_error")
     return float(out.value)
 
 

@@ -93,6 +93,11 @@ struct dh2_matrix {
   bool v_expanded = false;
   std::vector<double> eps2_h, zpow_h;
   float phase_ms[5] = {0, 0, 0, 0, 0};
+  // matrix-free mode
+  int gen = 0;
+  double* pts = nullptr;  // device, permuted order
+  double kappa = 0.0, diag = 0.0;
+  std::vector<double> pts_h;
 };
 
 namespace {
@@ -433,6 +438,10 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   na.near = (C2<T>*)M->near;
   na.near_off = D->near_off;
   na.copy = M->nearfield_copy;
+  na.pts = M->pts;
+  na.kappa = M->kappa;
+  na.diag = M->diag;
+  na.gen = M->gen;
   launch_norms_near<T>(na, (int)tr.blocks.size(), st);
   DH2_PHASE_SYNC("norms_near");
   cudaEventRecord(ev[1], st);
@@ -464,6 +473,10 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   pa.eps2 = M->eps2;
   pa.max_sweeps = cp.max_sweeps > 0 ? cp.max_sweeps : 30;
   pa.status = M->status;
+  pa.pts = M->pts;
+  pa.kappa = M->kappa;
+  pa.diag = M->diag;
+  pa.gen = M->gen;
   // leaf step for every leaf pair of both sides in one launch
   pa.P = even_up(std::max(2, D->max_leaf));
 #ifdef DH2_PROFILE
@@ -709,12 +722,22 @@ dh2_status dh2_tree_pair_blocks(const dh2_tree* T, int32_t side, int64_t* offset
   return DH2_OK;
 }
 
-dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld,
-                        const dh2_compress_params* params, void* stream, dh2_matrix** out) {
+}  // extern "C"
+
+namespace {
+
+// Shared body of dh2_compress (G given) and dh2_compress_kernel (pts_host
+// given: entries generated in the kernels).
+dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
+                         double kappa, double diag, const dh2_compress_params* params, void* stream,
+                         dh2_matrix** out) {
   if (!out) return DH2_EINVAL;
   *out = nullptr;
-  if (!Tc || !G || !params) return DH2_EINVAL;
+  if (!Tc || !params || (!G && !pts_host)) return DH2_EINVAL;
   const dh2_compress_params& cp = *params;
+  const bool gen = pts_host != nullptr;
+  if (gen && (cp.nearfield != 0 || !(kappa >= 0.0) || !std::isfinite(diag))) return DH2_EINVAL;
+  if (gen) ld = Tc->tr.n;
   if (ld < Tc->tr.n || !(cp.eps >= 0.0) || !(cp.zeta > 0.0 && cp.zeta < 1.0) || (cp.err_mode != 0 && cp.err_mode != 1) ||
       (cp.nearfield != 0 && cp.nearfield != 1))
     return DH2_EINVAL;
@@ -744,6 +767,9 @@ dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int6
   M->G = G;
   M->ld = ld;
   M->nearfield_copy = cp.nearfield == 0 ? 1 : 0;
+  M->gen = gen ? 1 : 0;
+  M->kappa = kappa;
+  M->diag = diag;
   const size_t es = M->es;
   const int nl = tr.depth + 1;
   size_t sz[20];
@@ -765,6 +791,7 @@ dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int6
   sz[ns++] = align256(8 * nl);
   sz[ns++] = align256(16);
   sz[ns++] = align256(16);
+  sz[ns++] = align256(gen ? 24 * (size_t)tr.n : 0);
   size_t total = 0;
   for (int i = 0; i < ns; ++i) total += sz[i];
   if (cudaMallocAsync(&M->arena, total, M->stream) != cudaSuccess) {
@@ -774,14 +801,16 @@ dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int6
   }
   M->arena_bytes = total;
   char* p = (char*)M->arena;
-  void** dst[17] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
+  void** dst[18] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
                     (void**)&M->sig[0], (void**)&M->sig[1], (void**)&M->rank[0], (void**)&M->rank[1],
-                    (void**)&M->invw, (void**)&M->eps2, (void**)&M->zpow, (void**)&M->status, (void**)&M->acc};
+                    (void**)&M->invw, (void**)&M->eps2, (void**)&M->zpow, (void**)&M->status, (void**)&M->acc,
+                    (void**)&M->pts};
   for (int i = 0; i < ns; ++i) {
     *dst[i] = p;
     p += sz[i];
   }
   if (!M->nearfield_copy) M->near = nullptr;
+  if (!gen) M->pts = nullptr;
   // tolerances eps_l = eps_hat zeta^l (Remark "Error control")
   const double eh =
       cp.err_mode == 0 ? cp.eps * std::sqrt(1.0 - 2.0 * cp.zeta * cp.zeta) / std::sqrt(2.0) : cp.eps;
@@ -798,6 +827,13 @@ dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int6
   if (ce == cudaSuccess) ce = cudaMemsetAsync(M->status, 0, 16, M->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(M->rank[0], 0, 4 * D->npairs[0], M->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(M->rank[1], 0, 4 * D->npairs[1], M->stream);
+  if (ce == cudaSuccess && gen) {
+    // points in the tree's permuted order
+    M->pts_h.resize(3 * (size_t)tr.n);
+    for (int64_t i = 0; i < tr.n; ++i)
+      for (int c = 0; c < 3; ++c) M->pts_h[3 * i + c] = pts_host[3 * tr.perm[i] + c];
+    ce = cudaMemcpyAsync(M->pts, M->pts_h.data(), 24 * (size_t)tr.n, cudaMemcpyHostToDevice, M->stream);
+  }
   if (ce != cudaSuccess) {
     cudaGetLastError();
     matrix_release(M);
@@ -810,6 +846,29 @@ dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int6
   }
   *out = M;
   return DH2_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld,
+                        const dh2_compress_params* params, void* stream, dh2_matrix** out) {
+  if (!G) {
+    if (out) *out = nullptr;
+    return DH2_EINVAL;
+  }
+  return compress_impl(Tc, G, dtype, ld, nullptr, 0.0, 0.0, params, stream, out);
+}
+
+dh2_status dh2_compress_kernel(const dh2_tree* Tc, const double* pts_xyz, double kappa, double diag,
+                               const dh2_compress_params* params, void* stream, dh2_matrix** out) {
+  if (!pts_xyz || !params) {
+    if (out) *out = nullptr;
+    return DH2_EINVAL;
+  }
+  const dh2_dtype dt = params->mode == DH2_MODE_FP32 ? DH2_C64 : DH2_C128;
+  return compress_impl(Tc, nullptr, dt, 0, pts_xyz, kappa, diag, params, stream, out);
 }
 
 void dh2_matrix_free(dh2_matrix* M) { matrix_release(M); }
@@ -901,6 +960,10 @@ dh2_status run_error(dh2_matrix* M, const void* Gref, dh2_dtype rdt, int64_t ldr
   a.near_off = D->near_off;
   a.G = (const C2<T>*)M->G;
   a.ld = M->ld;
+  a.pts = M->pts;
+  a.kappa = M->kappa;
+  a.diag = M->diag;
+  a.ref_gen = Gref == nullptr ? 1 : 0;
   DH2_CUDA_TRY(cudaMemsetAsync(M->acc, 0, 16, st));
   if (rdt == DH2_C128)
     launch_error<T, double>(a, (const C2<double>*)Gref, ldr, (int)tr.blocks.size(), M->acc, st);
@@ -925,7 +988,8 @@ dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs,
 
 dh2_status dh2_error(const dh2_matrix* Mc, const void* G_ref, dh2_dtype ref_dtype, int64_t ld, void* stream,
                      double* rel_err) {
-  if (!Mc || !G_ref || !rel_err || ld < Mc->tree->tr.n) return DH2_EINVAL;
+  if (!Mc || !rel_err) return DH2_EINVAL;
+  if (G_ref ? ld < Mc->tree->tr.n : !Mc->gen) return DH2_EINVAL;
   dh2_matrix* M = const_cast<dh2_matrix*>(Mc);
   return M->mode == DH2_MODE_FP32 ? run_error<float>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err)
                                   : run_error<double>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err);

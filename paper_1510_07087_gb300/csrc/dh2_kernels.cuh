@@ -41,7 +41,39 @@ struct PairArgs {
   int32_t P;                          // rows of the shared-memory factor (even)
   int32_t max_sweeps;
   uint32_t* status;
+  // matrix-free mode: entries generated from points (permuted order, 3 doubles each)
+  const double* pts;
+  double kappa;
+  double diag;
+  int32_t gen;
 };
+
+// Entry G_ij of the Helmholtz collocation matrix, Eq. (helmholtz):
+// exp(i kappa r) / (4 pi r), r = |x_i - x_j|, with `diag` on the diagonal.
+// Distances and the phase reduction are formed in FP64; the FP32 variant
+// evaluates sin/cos of the reduced phase (|phase| <= pi) in FP32.
+template <typename T>
+__device__ __forceinline__ C2<T> helmholtz_entry(const double* pts, int64_t i, int64_t j, double kappa,
+                                                 double diag) {
+  if (i == j) return C2<T>{(T)diag, T(0)};
+  const double dx = pts[3 * i] - pts[3 * j];
+  const double dy = pts[3 * i + 1] - pts[3 * j + 1];
+  const double dz = pts[3 * i + 2] - pts[3 * j + 2];
+  const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  if (sizeof(T) == 8) {
+    double sn, cs;
+    sincos(kappa * r, &sn, &cs);
+    const double inv = 1.0 / (12.566370614359172 * r);
+    return C2<T>{(T)(cs * inv), (T)(sn * inv)};
+  } else {
+    double th = kappa * r * 0.31830988618379067;  // phase / pi
+    th -= 2.0 * rint(0.5 * th);                    // reduced to [-1, 1]
+    float sn, cs;
+    sincospif((float)th, &sn, &cs);
+    const float inv = 1.0f / (12.566370614359172f * (float)r);
+    return C2<T>{(T)(cs * inv), (T)(sn * inv)};
+  }
+}
 
 template <typename T>
 void launch_pair_kernel(const PairArgs<T>& a, int nblocks, bool from_r, cudaStream_t st);

@@ -54,37 +54,86 @@ __device__ __forceinline__ const C2<T>* xbasis(const SideView<T>& S, int pid) {
 }
 
 // ---------------------------------------------------------------- norms / nearfield
-// One CTA per block of the block tree: |G_b|_F for an admissible block
+// One warp per block of the block tree: |G_b|_F for an admissible block
 // (weight omega_b = |G_b|_F zeta^-level(t), Remark "Error control"); a copy of
-// G_b into the nearfield buffer for an inadmissible one.
+// G_b into the nearfield buffer for an inadmissible one.  Each warp walks the
+// block column by column (contiguous runs of the row cluster).
 template <typename T>
-__global__ void __launch_bounds__(256) norms_near_kernel(NormsArgs<T> a) {
-  __shared__ double red[32];
-  const int b = blockIdx.x;
+__global__ void __launch_bounds__(256) norms_near_kernel(NormsArgs<T> a, int nblocks) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= nblocks) return;
   const int t = a.bt[b], s = a.bs[b];
   const int mt = a.csize[t], ms = a.csize[s];
   const int64_t t0 = a.cstart[t], s0 = a.cstart[s];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (a.badm[b]) {
-    T acc = T(0);
-    for (int j = warp; j < ms; j += nw) {
-      const C2<T>* col = a.G + (s0 + j) * a.ld + t0;
-      for (int r = lane; r < mt; r += 32) {
-        if (!DH2_IN((s0 + j) * a.ld + t0 + r, c_lim.G, 20, b)) continue;
-        const C2<T> g = col[r];
-        acc += g.re * g.re + g.im * g.im;
+  if (a.gen) {
+    // matrix-free: generate the block's entries from the points
+    if (a.badm[b]) {
+      double acc = 0.0;
+      for (int64_t e = lane; e < (int64_t)mt * ms; e += 32) {
+        const int r = (int)(e % mt), j = (int)(e / mt);
+        const C2<T> g = helmholtz_entry<T>(a.pts, t0 + r, s0 + j, a.kappa, a.diag);
+        acc += (double)g.re * g.re + (double)g.im * g.im;
+      }
+      const double tot = warp_sum(acc);
+      if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
+        a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+    } else if (a.copy) {
+      C2<T>* out = a.near + a.near_off[b];
+      for (int64_t e = lane; e < (int64_t)mt * ms; e += 32) {
+        const int r = (int)(e % mt), j = (int)(e / mt);
+        if (DH2_IN(a.near_off[b] + e, c_lim.near, 21, b)) out[e] = helmholtz_entry<T>(a.pts, t0 + r, s0 + j, a.kappa, a.diag);
       }
     }
-    const double tot = block_sum((double)acc, red);
-    if (threadIdx.x == 0 && DH2_IN(b, c_lim.nblocks, 23, b)) a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+    return;
+  }
+  // dense input: the block is walked as a flat column-major index space,
+  // 8 independent loads in flight per lane
+  const int total = mt * ms;
+  if (a.badm[b]) {
+    T acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = T(0);
+    for (int e0 = 0; e0 < total; e0 += 256) {
+      C2<T> g[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + lane + 32 * u;
+        g[u] = czero<T>();
+        if (e < total) {
+          const int r = e % mt, j = e / mt;
+          const int64_t gi = (s0 + j) * a.ld + t0 + r;
+          if (DH2_IN(gi, c_lim.G, 20, b)) g[u] = a.G[gi];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += g[u].re * g[u].re + g[u].im * g[u].im;
+    }
+    double tot = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) tot += (double)acc[u];
+    tot = warp_sum(tot);
+    if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
+      a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
   } else if (a.copy) {
     C2<T>* out = a.near + a.near_off[b];
-    for (int j = warp; j < ms; j += nw) {
-      const C2<T>* col = a.G + (s0 + j) * a.ld + t0;
-      for (int r = lane; r < mt; r += 32)
-        if (DH2_IN(a.near_off[b] + r + (int64_t)j * mt, c_lim.near, 21, b) &&
-            DH2_IN((s0 + j) * a.ld + t0 + r, c_lim.G, 22, b))
-          out[r + (int64_t)j * mt] = col[r];
+    for (int e0 = 0; e0 < total; e0 += 256) {
+      C2<T> g[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + lane + 32 * u;
+        g[u] = czero<T>();
+        if (e < total) {
+          const int r = e % mt, j = e / mt;
+          const int64_t gi = (s0 + j) * a.ld + t0 + r;
+          if (DH2_IN(gi, c_lim.G, 22, b)) g[u] = a.G[gi];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + lane + 32 * u;
+        if (e < total && DH2_IN(a.near_off[b] + e, c_lim.near, 21, b)) out[e] = g[u];
+      }
     }
   }
 }
@@ -127,11 +176,14 @@ __global__ void __launch_bounds__(256) expand_kernel(SideView<T> S, const int32_
 // ---------------------------------------------------------------- projection
 // S_b = omega_b R_tc|_b W_sc: R_tc|_b = V_tc^* G_b / omega_b is the block's
 // own column range of R_tc (Section 6), W_sc the expanded column basis.
+// One warp per admissible block; each lane accumulates up to 8 outputs over
+// the block's columns, reading R and W through L1.
 template <typename T>
-__global__ void __launch_bounds__(256) project_kernel(ProjArgs<T> a) {
-  __shared__ C2<T> Rs[64][17];
-  __shared__ C2<T> Ws[16][65];
-  const int b = a.adm_list[blockIdx.x];
+__global__ void __launch_bounds__(128) project_kernel(ProjArgs<T> a, int nadm) {
+  const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (wid >= nadm) return;
+  const int b = a.adm_list[wid];
   const int Pt = a.bpair_row[b], Ps = a.bpair_col[b];
   if (!DH2_IN(Pt, c_lim.npairs[0], 44, b) || !DH2_IN(Ps, c_lim.npairs[1], 45, b)) return;
   const int off = a.boff_row[b];
@@ -140,46 +192,40 @@ __global__ void __launch_bounds__(256) project_kernel(ProjArgs<T> a) {
   if (kt == 0 || ks == 0) return;
   const int ms = a.csize[a.bs[b]];
   const int ldr = a.V.kcap[Pt];
-  const C2<T>* R = a.V.R + a.V.Roff[Pt] + (int64_t)off * ldr;
+  const int64_t rbase = a.V.Roff[Pt] + (int64_t)off * ldr;
+  const C2<T>* R = a.V.R + rbase;
+  const bool wleaf = a.W.leaf[Ps];
+  const int64_t wbase = wleaf ? a.W.Qoff[Ps] : a.W.Xoff[Ps];
   const C2<T>* W = xbasis(a.W, Ps);
   const T w = (T)(1.0 / a.invw[b]);
-  // kt, ks <= 128: tile the output in 64 x 64 pieces
-  for (int q0 = 0; q0 < kt; q0 += 64) {
-    for (int c0 = 0; c0 < ks; c0 += 64) {
-      const int tq = threadIdx.x & 63, tc = threadIdx.x >> 6;  // 64 x 4 threads, 16 outputs each
-      C2<T> acc[16];
+  const int nout = kt * ks;
+  for (int o0 = 0; o0 < nout; o0 += 32 * 8) {
+    C2<T> acc[8];
+    int qq[8], cc[8];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) acc[u] = czero<T>();
-      for (int j0 = 0; j0 < ms; j0 += 16) {
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
-          const int qq = idx & 63, jj = idx >> 6;
-          Rs[qq][jj] = (q0 + qq < kt && j0 + jj < ms &&
-                        DH2_IN(a.V.Roff[Pt] + (int64_t)off * ldr + q0 + qq + (int64_t)(j0 + jj) * ldr, c_lim.R[0], 40, b))
-                           ? R[q0 + qq + (int64_t)(j0 + jj) * ldr]
-                           : czero<T>();
-        }
-        for (int idx = threadIdx.x; idx < 64 * 16; idx += blockDim.x) {
-          const int jj = idx & 15, cc = idx >> 4;
-          Ws[jj][cc] = (c0 + cc < ks && j0 + jj < ms &&
-                        (a.W.leaf[Ps] ? DH2_IN(a.W.Qoff[Ps] + j0 + jj + (int64_t)(c0 + cc) * ms, c_lim.Q[1], 41, b)
-                                      : DH2_IN(a.W.Xoff[Ps] + j0 + jj + (int64_t)(c0 + cc) * ms, c_lim.X[1], 42, b)))
-                           ? W[j0 + jj + (int64_t)(c0 + cc) * ms]
-                           : czero<T>();
-        }
-        __syncthreads();
-        for (int jj = 0; jj < 16; ++jj) {
-          const C2<T> r = Rs[tq][jj];
+    for (int u = 0; u < 8; ++u) {
+      acc[u] = czero<T>();
+      const int o = o0 + lane + 32 * u;
+      qq[u] = o % kt;
+      cc[u] = o / kt;
+    }
+    for (int j = 0; j < ms; ++j) {
 #pragma unroll
-          for (int u = 0; u < 16; ++u) acc[u] = cadd(acc[u], cmul(r, Ws[jj][tc + 4 * u]));
+      for (int u = 0; u < 8; ++u) {
+        if (o0 + lane + 32 * u < nout) {
+          const int64_t ri = qq[u] + (int64_t)j * ldr;
+          const int64_t wi = j + (int64_t)cc[u] * ms;
+          const bool ok = DH2_IN(rbase + ri, c_lim.R[0], 40, b) &&
+                          (wleaf ? DH2_IN(wbase + wi, c_lim.Q[1], 41, b) : DH2_IN(wbase + wi, c_lim.X[1], 42, b));
+          if (ok) acc[u] = cadd(acc[u], cmul(R[ri], W[wi]));
         }
       }
+    }
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int qq = q0 + tq, cc = c0 + tc + 4 * u;
-        if (qq < kt && cc < ks && DH2_IN(a.Soff[b] + qq + (int64_t)cc * kt, c_lim.S, 43, b))
-          Sout[qq + (int64_t)cc * kt] = C2<T>{w * acc[u].re, w * acc[u].im};
-      }
+    for (int u = 0; u < 8; ++u) {
+      const int o = o0 + lane + 32 * u;
+      if (o < nout && DH2_IN(a.Soff[b] + o, c_lim.S, 43, b))
+        Sout[o] = C2<T>{w * acc[u].re, w * acc[u].im};  // column-major, ld = kt
     }
   }
 }
@@ -319,6 +365,14 @@ __global__ void mv_near(MvArgs<T> a, const int32_t* blocks, int nrhs, const C2<T
 // ---------------------------------------------------------------- error
 // sum over blocks of |G_ref - G~|_F^2 and |G_ref|_F^2 in FP64.
 template <typename T, typename RT>
+__device__ __forceinline__ C2<double> ref_entry(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int64_t i,
+                                                int64_t j) {
+  if (a.ref_gen) return helmholtz_entry<double>(a.pts, i, j, a.kappa, a.diag);
+  const C2<RT> g = Gref[i + j * ldr];
+  return C2<double>{(double)g.re, (double)g.im};
+}
+
+template <typename T, typename RT>
 __global__ void __launch_bounds__(256) error_kernel(ErrArgs<T> a, const C2<RT>* Gref, int64_t ldr,
                                                     double* acc_out) {
   __shared__ double red[32];
@@ -331,7 +385,7 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs<T> a, const C2<RT>* 
   if (!a.badm[b]) {
     for (int idx = threadIdx.x; idx < mt * ms; idx += blockDim.x) {
       const int i = idx % mt, j = idx / mt;
-      const C2<RT> g = Gref[(t0 + i) + (s0 + j) * ldr];
+      const C2<double> g = ref_entry<T, RT>(a, Gref, ldr, t0 + i, s0 + j);
       const C2<T> h = a.near ? a.near[a.near_off[b] + i + (int64_t)j * mt] : a.G[(t0 + i) + (s0 + j) * a.ld];
       const double dr = (double)g.re - (double)h.re, di = (double)g.im - (double)h.im;
       e2 += dr * dr + di * di;
@@ -369,7 +423,7 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs<T> a, const C2<RT>* 
           ar += (double)v.re * tv.re - (double)v.im * tv.im;
           ai += (double)v.re * tv.im + (double)v.im * tv.re;
         }
-        const C2<RT> g = Gref[(t0 + i) + (s0 + j0 + jj) * ldr];
+        const C2<double> g = ref_entry<T, RT>(a, Gref, ldr, t0 + i, s0 + j0 + jj);
         const double dr = (double)g.re - ar, di = (double)g.im - ai;
         e2 += dr * dr + di * di;
         r2 += (double)g.re * g.re + (double)g.im * g.im;
@@ -408,7 +462,7 @@ bool check_read_ops(CheckRecord* out) {
 
 template <typename T>
 void launch_norms_near(const NormsArgs<T>& a, int nblocks, cudaStream_t st) {
-  if (nblocks > 0) norms_near_kernel<T><<<nblocks, 256, 0, st>>>(a);
+  if (nblocks > 0) norms_near_kernel<T><<<(nblocks + 7) / 8, 256, 0, st>>>(a, nblocks);
 }
 template <typename T>
 void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream_t st) {
@@ -416,7 +470,7 @@ void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream
 }
 template <typename T>
 void launch_project(const ProjArgs<T>& a, int nadm, cudaStream_t st) {
-  if (nadm > 0) project_kernel<T><<<nadm, 256, 0, st>>>(a);
+  if (nadm > 0) project_kernel<T><<<(nadm + 3) / 4, 128, 0, st>>>(a, nadm);
 }
 template <typename T>
 void launch_mv_forward_leaf(const SideView<T>& W, const int32_t* pairs, int np, const C2<T>* x, int nrhs,

@@ -40,6 +40,10 @@ struct NormsArgs {
   C2<T>* near;
   const int64_t* near_off;
   int copy;
+  const double* pts;  // matrix-free mode
+  double kappa;
+  double diag;
+  int gen;
 };
 
 template <typename T>
@@ -95,6 +99,10 @@ struct ErrArgs {
   const int64_t* near_off;
   const C2<T>* G;
   int64_t ld;
+  const double* pts;  // reference generated from points (FP64) when ref_gen
+  double kappa;
+  double diag;
+  int ref_gen;
 };
 
 template <typename T> void launch_norms_near(const NormsArgs<T>& a, int nblocks, cudaStream_t st);

@@ -99,6 +99,9 @@ struct Source {
   const int32_t* gblk;
   const double* invw;
   int64_t cmo;
+  const double* pts;  // matrix-free mode
+  double kappa, diag;
+  int gen;
   // non-leaf
   const C2<T>* R0;
   const C2<T>* R1;
@@ -121,6 +124,11 @@ struct Source {
       const int b = gblk[j];
       if (!DH2_IN(b, c_lim.nblocks, 4, pid)) return czero<T>();
       const T w = (T)invw[b];
+      if (gen) {
+        C2<T> g = side == 0 ? helmholtz_entry<T>(pts, r0 + r, gc, kappa, diag)
+                            : helmholtz_entry<T>(pts, gc, r0 + r, kappa, diag);
+        return C2<T>{g.re * w, side == 0 ? g.im * w : -g.im * w};
+      }
       if (side == 0) {
         const int64_t e = (int64_t)gc * ld + r0 + r;
         if (!DH2_IN(e, c_lim.G, 5, pid)) return czero<T>();
@@ -206,6 +214,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1) pair_
     src.G = a.G;
     src.ld = a.ld;
     src.invw = a.invw;
+    src.pts = a.pts;
+    src.kappa = a.kappa;
+    src.diag = a.diag;
+    src.gen = a.gen;
   }
   int32_t* rank_out = a.rank[side] + pid;
   double* sig_out = a.sig[side] + (int64_t)pid * kSigStride;
