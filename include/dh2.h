@@ -152,6 +152,15 @@ dh2_status dh2_tree_pair_blocks(const dh2_tree* tree, int32_t side, int64_t* off
  * DH2_ENOCONV / DH2_EUNSUPPORTED from the device status word, DH2_ECUDA. */
 dh2_status dh2_compress(const dh2_tree* tree, const void* G, dh2_dtype dtype, int64_t ld,
                         const dh2_compress_params* params, void* stream, dh2_matrix** out);
+/* Compress nprob independent matrices (each with its own tree, size and
+ * leading dimension; same dtype and parameters) in one schedule: block norms,
+ * leaf factorisations and every level of non-leaf steps are each one launch
+ * over all problems.  out: array of nprob handles (all NULL on failure).
+ * nprob <= 64; each problem as for dh2_compress. */
+dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, const void* const* G,
+                                const int64_t* ld, dh2_dtype dtype, const dh2_compress_params* params,
+                                void* stream, dh2_matrix** out);
+
 /* Matrix-free compression of the Helmholtz collocation matrix
  * G_ij = exp(i kappa |x_i - x_j|) / (4 pi |x_i - x_j|) (Eq. helmholtz), with
  * `diag` on the diagonal: every entry the compression reads (block norms,

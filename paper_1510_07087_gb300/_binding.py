@@ -63,6 +63,8 @@ SIGNATURES = [
     ("dh2_tree_pair_blocks", c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     ("dh2_compress", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p,
                                POINTER(c_void_p)]),
+    ("dh2_compress_batched", c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_int32, POINTER(CompressParams),
+                                       c_void_p, c_void_p]),
     ("dh2_compress_kernel", c_int32, [c_void_p, c_void_p, c_double, c_double, POINTER(CompressParams), c_void_p,
                                       POINTER(c_void_p)]),
     ("dh2_matrix_free", None, [c_void_p]),
@@ -286,6 +288,27 @@ def dh2_compress(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_
     _check(_lib().dh2_compress(tree.handle, c_void_p(G.data_ptr()), dt, ld, byref(p),
                                c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress")
     return Matrix(h.value, tree, mode, G)
+
+
+def dh2_compress_batched(trees, Gs, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,
+                         mode: int | None = None, nearfield: int = 0, max_sweeps: int = 0, stream=None) -> list:
+    """Compress several independent device matrices (column-major views) in one schedule."""
+    n = len(trees)
+    if n != len(Gs) or n == 0:
+        raise ValueError("need one matrix per tree")
+    dt = _dtype_code(Gs[0])
+    if any(_dtype_code(g) != dt for g in Gs):
+        raise TypeError("all matrices must have the same dtype")
+    if mode is None:
+        mode = MODE_FP32 if dt == DH2_C64 else MODE_FP64
+    th = (c_void_p * n)(*[t.handle for t in trees])
+    gp = (c_void_p * n)(*[g.data_ptr() for g in Gs])
+    lds = (c_int64 * n)(*[_colmajor_ld(g) for g in Gs])
+    outs = (c_void_p * n)()
+    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), int(nearfield), int(max_sweeps))
+    _check(_lib().dh2_compress_batched(n, th, gp, lds, dt, byref(p), c_void_p(_stream_handle(stream)), outs),
+           "dh2_compress_batched")
+    return [Matrix(outs[i], trees[i], mode, Gs[i]) for i in range(n)]
 
 
 def dh2_compress_kernel(tree: Tree, points: np.ndarray, kappa: float, diag: float, eps: float = 1e-4,

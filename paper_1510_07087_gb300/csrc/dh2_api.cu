@@ -49,7 +49,7 @@ struct Tree::Dev {
   int64_t *own_ptr, *par_ptr;
   int32_t *own_blk, *par_pair, *par_son;
   // launch orders: leaf launch (both sides) then non-leaf per level
-  int32_t* codes;
+  uint32_t* codes;
   // host-side sizes
   int64_t npairs[2] = {0, 0}, nleaf[2] = {0, 0};
   int64_t R_elems[2] = {0, 0}, Q_elems[2] = {0, 0}, X_elems[2] = {0, 0}, h_elems[2] = {0, 0};
@@ -113,6 +113,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // k_cap(t2c'), #F, 128).  Offsets of R (k_cap x #F), Q ([E1;E2] rowcap x k_cap)
 // and of the expanded non-leaf bases (#t x k_cap) follow.
 dh2_status upload_tree(Tree& tr) {
+  for (int sd = 0; sd < 2; ++sd)
+    if (tr.side[sd].pairs.size() > kCodePairMask) return DH2_EUNSUPPORTED;
+  if (tr.blocks.size() >= (size_t(1) << 26)) return DH2_EUNSUPPORTED;
   Tree::Dev* D = new (std::nothrow) Tree::Dev();
   if (!D) return DH2_ENOMEM;
   const int32_t nc = tr.nclusters();
@@ -292,7 +295,7 @@ dh2_status upload_tree(Tree& tr) {
     for (int sd = 0; sd < 2; ++sd)
       for (int64_t p : tr.side[sd].leaf_pairs) {
         const double m = tr.size[tr.side[sd].pairs[p].cluster];
-        lc.push_back({-(m * m * (double)tr.side[sd].pairs[p].ncols), (int32_t)((sd << 30) | (int32_t)p)});
+        lc.push_back({-(m * m * (double)tr.side[sd].pairs[p].ncols), (int32_t)((sd << kCodeSideShift) | (int32_t)p)});
       }
     std::stable_sort(lc.begin(), lc.end(),
                      [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
@@ -308,12 +311,12 @@ dh2_status upload_tree(Tree& tr) {
       D->nl_code_begin[l] = (int64_t)codes.size();
       for (int sd = 0; sd < 2; ++sd)
         for (int64_t p : tr.side[sd].nonleaf_by_level[l]) {
-          codes.push_back((int32_t)((sd << 30) | (int32_t)p));
+          codes.push_back((int32_t)((sd << kCodeSideShift) | (int32_t)p));
           D->nl_rowcap_max[l] = std::max(D->nl_rowcap_max[l], D->rowcap_h[sd][p]);
         }
       D->nl_code_count[l] = (int64_t)codes.size() - D->nl_code_begin[l];
     }
-    add32(std::move(codes), &D->codes);
+    add32(std::move(codes), (int32_t**)&D->codes);
   }
   size_t total = 0;
   for (auto& b : bufs) total += align256(std::max<size_t>(b.bytes, 4));
@@ -396,35 +399,9 @@ int even_up(int x) { return x + (x & 1); }
 #endif
 
 template <typename T>
-dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
+void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, NormsArgs<T>& na) {
   Tree& tr = M->tree->tr;
   Tree::Dev* D = tr.dev;
-  cudaStream_t st = M->stream;
-  const int pmax = sizeof(T) == 4 ? kPmaxF32 : kPmaxF64;
-  cudaEvent_t ev[6];
-  for (int i = 0; i < 6; ++i) DH2_CUDA_TRY(cudaEventCreate(&ev[i]));
-#ifdef DH2_CHECK
-  {
-    CheckLimits lim;
-    lim.G = M->ld * (tr.n - 1) + tr.n;
-    for (int sd = 0; sd < 2; ++sd) {
-      lim.R[sd] = D->R_elems[sd];
-      lim.Q[sd] = D->Q_elems[sd];
-      lim.X[sd] = D->X_elems[sd];
-      lim.npairs[sd] = D->npairs[sd];
-      lim.ncol[sd] = (int64_t)tr.side[sd].gcol.size();
-    }
-    lim.S = D->S_elems;
-    lim.near = M->nearfield_copy ? D->near_elems : 0;
-    lim.nblocks = (int64_t)tr.blocks.size();
-    cudaStreamSynchronize(st);
-    check_set_limits_pair(lim);
-    check_set_limits_ops(lim);
-  }
-#endif
-  cudaEventRecord(ev[0], st);
-
-  NormsArgs<T> na;
   na.G = (const C2<T>*)M->G;
   na.ld = M->ld;
   na.bt = D->bt;
@@ -442,12 +419,6 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   na.kappa = M->kappa;
   na.diag = M->diag;
   na.gen = M->gen;
-  launch_norms_near<T>(na, (int)tr.blocks.size(), st);
-  DH2_PHASE_SYNC("norms_near");
-  cudaEventRecord(ev[1], st);
-
-  PairArgs<T> pa;
-  pa.order = D->codes;
   for (int sd = 0; sd < 2; ++sd) {
     pa.start[sd] = D->start[sd];
     pa.m[sd] = D->m[sd];
@@ -477,12 +448,137 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
   pa.kappa = M->kappa;
   pa.diag = M->diag;
   pa.gen = M->gen;
-  // leaf step for every leaf pair of both sides in one launch
-  pa.P = even_up(std::max(2, D->max_leaf));
+}
+
+// The compression of one or several independent problems: each phase is one
+// launch over every problem (block norms, leaf factors, one launch per level
+// for the non-leaf steps), then expansion and projection per problem.
+template <typename T>
+dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params& cp, cudaStream_t st) {
+  const int nprob = (int)Ms.size();
+  const int pmax = sizeof(T) == 4 ? kPmaxF32 : kPmaxF64;
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) DH2_CUDA_TRY(cudaEventCreate(&ev[i]));
+  std::vector<PairArgs<T>> pas(nprob);
+  std::vector<NormsArgs<T>> nas(nprob);
+  for (int i = 0; i < nprob; ++i) fill_args<T>(Ms[i], cp, pas[i], nas[i]);
+  // launch codes: cached in the tree for one problem, merged for a batch
+  std::vector<uint32_t> leaf_codes, norm_codes;
+  std::vector<std::vector<uint32_t>> nl_codes;
+  int maxdepth = 0, P_leaf = 2;
+  std::vector<int> P_level;
+  for (dh2_matrix* M : Ms) maxdepth = std::max(maxdepth, M->tree->tr.depth);
+  nl_codes.resize(maxdepth + 1);
+  P_level.assign(maxdepth + 1, 2);
+  for (int i = 0; i < nprob; ++i) {
+    const Tree::Dev* D = Ms[i]->tree->tr.dev;
+    P_leaf = std::max(P_leaf, even_up(std::max(2, D->max_leaf)));
+    for (int l = 0; l <= Ms[i]->tree->tr.depth; ++l)
+      if (D->nl_code_count[l]) P_level[l] = std::max(P_level[l], even_up(std::min(pmax, D->nl_rowcap_max[l])));
+  }
+  const uint32_t* d_leaf = nullptr;
+  const uint32_t* d_norm = nullptr;
+  std::vector<const uint32_t*> d_nl(maxdepth + 1, nullptr);
+  std::vector<int64_t> n_nl(maxdepth + 1, 0);
+  int64_t n_leaf = 0, n_norm = 0;
+  size_t args_bytes = align256(sizeof(PairArgs<T>) * nprob) + align256(sizeof(NormsArgs<T>) * nprob);
+  size_t codes_bytes = 0;
+  if (nprob > 1) {
+    std::vector<std::pair<double, uint32_t>> lc;
+    for (int i = 0; i < nprob; ++i) {
+      const Tree& tr = Ms[i]->tree->tr;
+      for (int sd = 0; sd < 2; ++sd)
+        for (int64_t p : tr.side[sd].leaf_pairs) {
+          const double m = tr.size[tr.side[sd].pairs[p].cluster];
+          lc.push_back({-(m * m * (double)tr.side[sd].pairs[p].ncols),
+                        ((uint32_t)i << kCodeProbShift) | ((uint32_t)sd << kCodeSideShift) | (uint32_t)p});
+        }
+      for (int l = tr.depth; l >= 0; --l)
+        for (int sd = 0; sd < 2; ++sd)
+          for (int64_t p : tr.side[sd].nonleaf_by_level[l])
+            nl_codes[l].push_back(((uint32_t)i << kCodeProbShift) | ((uint32_t)sd << kCodeSideShift) | (uint32_t)p);
+      for (size_t b = 0; b < tr.blocks.size(); ++b) norm_codes.push_back(((uint32_t)i << 26) | (uint32_t)b);
+    }
+    std::stable_sort(lc.begin(), lc.end(), [](const std::pair<double, uint32_t>& a,
+                                              const std::pair<double, uint32_t>& b) { return a.first < b.first; });
+    for (auto& x : lc) leaf_codes.push_back(x.second);
+    codes_bytes = align256(4 * leaf_codes.size()) + align256(4 * norm_codes.size());
+    for (int l = 0; l <= maxdepth; ++l) codes_bytes += align256(4 * nl_codes[l].size());
+  }
+  void* scratch = nullptr;
+  DH2_CUDA_TRY(cudaMallocAsync(&scratch, args_bytes + codes_bytes + 256, st));
+  char* sp = (char*)scratch;
+  PairArgs<T>* d_pa = (PairArgs<T>*)sp;
+  sp += align256(sizeof(PairArgs<T>) * nprob);
+  NormsArgs<T>* d_na = (NormsArgs<T>*)sp;
+  sp += align256(sizeof(NormsArgs<T>) * nprob);
+  cudaError_t ce = cudaMemcpyAsync(d_pa, pas.data(), sizeof(PairArgs<T>) * nprob, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(d_na, nas.data(), sizeof(NormsArgs<T>) * nprob, cudaMemcpyHostToDevice, st);
+  if (nprob > 1) {
+    auto up = [&](const std::vector<uint32_t>& v) -> const uint32_t* {
+      uint32_t* d = (uint32_t*)sp;
+      if (!v.empty() && ce == cudaSuccess) ce = cudaMemcpyAsync(d, v.data(), 4 * v.size(), cudaMemcpyHostToDevice, st);
+      sp += align256(4 * v.size());
+      return d;
+    };
+    d_leaf = up(leaf_codes);
+    n_leaf = (int64_t)leaf_codes.size();
+    d_norm = up(norm_codes);
+    n_norm = (int64_t)norm_codes.size();
+    for (int l = 0; l <= maxdepth; ++l) {
+      d_nl[l] = up(nl_codes[l]);
+      n_nl[l] = (int64_t)nl_codes[l].size();
+    }
+  } else {
+    const Tree& tr = Ms[0]->tree->tr;
+    const Tree::Dev* D = tr.dev;
+    d_leaf = D->codes;
+    n_leaf = D->nleaf_codes;
+    d_norm = nullptr;
+    n_norm = (int64_t)tr.blocks.size();
+    for (int l = 0; l <= tr.depth; ++l) {
+      d_nl[l] = D->codes + D->nl_code_begin[l];
+      n_nl[l] = D->nl_code_count[l];
+    }
+  }
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeAsync(scratch, st);
+    return DH2_ECUDA;
+  }
+#ifdef DH2_CHECK
+  {
+    // one set of limits for the launch: the largest over the problems
+    CheckLimits lim{};
+    for (dh2_matrix* M : Ms) {
+      const Tree& tr = M->tree->tr;
+      const Tree::Dev* D = tr.dev;
+      lim.G = std::max<int64_t>(lim.G, M->ld * (tr.n - 1) + tr.n);
+      for (int sd = 0; sd < 2; ++sd) {
+        lim.R[sd] = std::max(lim.R[sd], D->R_elems[sd]);
+        lim.Q[sd] = std::max(lim.Q[sd], D->Q_elems[sd]);
+        lim.X[sd] = std::max(lim.X[sd], D->X_elems[sd]);
+        lim.npairs[sd] = std::max(lim.npairs[sd], D->npairs[sd]);
+        lim.ncol[sd] = std::max(lim.ncol[sd], (int64_t)tr.side[sd].gcol.size());
+      }
+      lim.S = std::max(lim.S, D->S_elems);
+      lim.near = std::max<int64_t>(lim.near, M->nearfield_copy ? D->near_elems : 0);
+      lim.nblocks = std::max<int64_t>(lim.nblocks, (int64_t)tr.blocks.size());
+    }
+    cudaStreamSynchronize(st);
+    check_set_limits_pair(lim);
+    check_set_limits_ops(lim);
+  }
+#endif
+  cudaEventRecord(ev[0], st);
+  launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
+  DH2_PHASE_SYNC("norms_near");
+  cudaEventRecord(ev[1], st);
 #ifdef DH2_PROFILE
   prof_reset_pair();
 #endif
-  launch_pair_kernel<T>(pa, (int)D->nleaf_codes, false, st);
+  launch_pair_kernel<T>(d_pa, d_leaf, (int)n_leaf, P_leaf, false, st);
 #ifdef DH2_PROFILE
   {
     cudaStreamSynchronize(st);
@@ -497,48 +593,53 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
 #endif
   DH2_PHASE_SYNC("leaf pairs");
   cudaEventRecord(ev[2], st);
-  // non-leaf steps, level by level from the leaves up
-  for (int l = tr.depth; l >= 0; --l) {
-    if (D->nl_code_count[l] == 0) continue;
-    PairArgs<T> pl = pa;
-    pl.order = D->codes + D->nl_code_begin[l];
-    pl.P = even_up(std::max(2, std::min(pmax, D->nl_rowcap_max[l])));
-    launch_pair_kernel<T>(pl, (int)D->nl_code_count[l], true, st);
-#ifdef DH2_CHECK
-    std::fprintf(stderr, "dh2: non-leaf level %d: %lld pairs, P=%d\n", l, (long long)D->nl_code_count[l], pl.P);
-#endif
+  for (int l = maxdepth; l >= 0; --l) {
+    if (n_nl[l] == 0) continue;
+    launch_pair_kernel<T>(d_pa, d_nl[l], (int)n_nl[l], P_level[l], true, st);
     DH2_PHASE_SYNC("non-leaf pairs");
   }
   cudaEventRecord(ev[3], st);
-  // expanded column bases for the projection
-  SideView<T> Vv = side_view<T>(tr, M, 0), Wv = side_view<T>(tr, M, 1);
-  for (int l = tr.depth; l >= 0; --l) {
-    const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
-    if (e > b) launch_expand<T>(Wv, D->iota[1] + b, (int)(e - b), st);
-    DH2_PHASE_SYNC("expand");
+  for (dh2_matrix* M : Ms) {
+    Tree& tr = M->tree->tr;
+    Tree::Dev* D = tr.dev;
+    SideView<T> Wv = side_view<T>(tr, M, 1);
+    for (int l = tr.depth; l >= 0; --l) {
+      const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
+      if (e > b) launch_expand<T>(Wv, D->iota[1] + b, (int)(e - b), st);
+      DH2_PHASE_SYNC("expand");
+    }
   }
   cudaEventRecord(ev[4], st);
-  ProjArgs<T> pj;
-  pj.V = Vv;
-  pj.W = Wv;
-  pj.adm_list = D->adm_list;
-  pj.bpair_row = D->bpair[0];
-  pj.bpair_col = D->bpair[1];
-  pj.boff_row = D->boff_row;
-  pj.bs = D->bs;
-  pj.csize = D->csize;
-  pj.invw = M->invw;
-  pj.S = (C2<T>*)M->S;
-  pj.Soff = D->Soff;
-  launch_project<T>(pj, (int)D->nadm, st);
-  DH2_PHASE_SYNC("project");
+  for (dh2_matrix* M : Ms) {
+    Tree& tr = M->tree->tr;
+    Tree::Dev* D = tr.dev;
+    ProjArgs<T> pj;
+    pj.V = side_view<T>(tr, M, 0);
+    pj.W = side_view<T>(tr, M, 1);
+    pj.adm_list = D->adm_list;
+    pj.bpair_row = D->bpair[0];
+    pj.bpair_col = D->bpair[1];
+    pj.boff_row = D->boff_row;
+    pj.bs = D->bs;
+    pj.csize = D->csize;
+    pj.invw = M->invw;
+    pj.S = (C2<T>*)M->S;
+    pj.Soff = D->Soff;
+    launch_project<T>(pj, (int)D->nadm, st);
+    DH2_PHASE_SYNC("project");
+  }
   cudaEventRecord(ev[5], st);
-  uint32_t status = 0;
-  cudaError_t e1 = cudaMemcpyAsync(&status, M->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(scratch, st);
+  std::vector<uint32_t> status(nprob, 0);
+  cudaError_t e1 = cudaSuccess;
+  for (int i = 0; i < nprob && e1 == cudaSuccess; ++i)
+    e1 = cudaMemcpyAsync(&status[i], Ms[i]->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   cudaError_t e2 = cudaStreamSynchronize(st);
   cudaError_t e3 = cudaGetLastError();
-  for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&M->phase_ms[i], ev[i], ev[i + 1]);
+  float ph[5] = {0, 0, 0, 0, 0};
+  for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ph[i], ev[i], ev[i + 1]);
   for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  for (dh2_matrix* M : Ms) std::memcpy(M->phase_ms, ph, sizeof(ph));
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return DH2_ECUDA;
 #ifdef DH2_CHECK
   {
@@ -552,9 +653,11 @@ dh2_status run_compress(dh2_matrix* M, const dh2_compress_params& cp) {
     }
   }
 #endif
-  if (status & kStatusTooLarge) return DH2_EUNSUPPORTED;
-  if (status & (kStatusNoConv | kStatusNaN)) return DH2_ENOCONV;
-  if (status & kStatusTimeout) return DH2_ETIMEOUT;
+  uint32_t all = 0;
+  for (uint32_t v : status) all |= v;
+  if (all & kStatusTooLarge) return DH2_EUNSUPPORTED;
+  if (all & (kStatusNoConv | kStatusNaN)) return DH2_ENOCONV;
+  if (all & kStatusTimeout) return DH2_ETIMEOUT;
   return DH2_OK;
 }
 
@@ -728,9 +831,9 @@ namespace {
 
 // Shared body of dh2_compress (G given) and dh2_compress_kernel (pts_host
 // given: entries generated in the kernels).
-dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
-                         double kappa, double diag, const dh2_compress_params* params, void* stream,
-                         dh2_matrix** out) {
+dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
+                          double kappa, double diag, const dh2_compress_params* params, void* stream,
+                          dh2_matrix** out) {
   if (!out) return DH2_EINVAL;
   *out = nullptr;
   if (!Tc || !params || (!G && !pts_host)) return DH2_EINVAL;
@@ -839,7 +942,19 @@ dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int
     matrix_release(M);
     return DH2_ECUDA;
   }
-  const dh2_status s = cp.mode == DH2_MODE_FP32 ? run_compress<float>(M, cp) : run_compress<double>(M, cp);
+  *out = M;
+  return DH2_OK;
+}
+
+dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
+                         double kappa, double diag, const dh2_compress_params* params, void* stream,
+                         dh2_matrix** out) {
+  dh2_matrix* M = nullptr;
+  dh2_status s = prepare_matrix(Tc, G, dtype, ld, pts_host, kappa, diag, params, stream, &M);
+  if (s != DH2_OK) return s;
+  std::vector<dh2_matrix*> Ms{M};
+  s = params->mode == DH2_MODE_FP32 ? run_compress<float>(Ms, *params, (cudaStream_t)stream)
+                                    : run_compress<double>(Ms, *params, (cudaStream_t)stream);
   if (s != DH2_OK) {
     matrix_release(M);
     return s;
@@ -869,6 +984,33 @@ dh2_status dh2_compress_kernel(const dh2_tree* Tc, const double* pts_xyz, double
   }
   const dh2_dtype dt = params->mode == DH2_MODE_FP32 ? DH2_C64 : DH2_C128;
   return compress_impl(Tc, nullptr, dt, 0, pts_xyz, kappa, diag, params, stream, out);
+}
+
+dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, const void* const* G,
+                                const int64_t* ld, dh2_dtype dtype, const dh2_compress_params* params, void* stream,
+                                dh2_matrix** out) {
+  if (!out || nprob < 1) return DH2_EINVAL;
+  for (int i = 0; i < nprob; ++i) out[i] = nullptr;
+  if (nprob > kMaxBatch || !trees || !G || !ld || !params) return DH2_EINVAL;
+  std::vector<dh2_matrix*> Ms;
+  for (int i = 0; i < nprob; ++i) {
+    dh2_matrix* M = nullptr;
+    const dh2_status s = G[i] ? prepare_matrix(trees[i], G[i], dtype, ld[i], nullptr, 0.0, 0.0, params, stream, &M)
+                              : DH2_EINVAL;
+    if (s != DH2_OK) {
+      for (dh2_matrix* m : Ms) matrix_release(m);
+      return s;
+    }
+    Ms.push_back(M);
+  }
+  const dh2_status s = params->mode == DH2_MODE_FP32 ? run_compress<float>(Ms, *params, (cudaStream_t)stream)
+                                                     : run_compress<double>(Ms, *params, (cudaStream_t)stream);
+  if (s != DH2_OK) {
+    for (dh2_matrix* m : Ms) matrix_release(m);
+    return s;
+  }
+  for (int i = 0; i < nprob; ++i) out[i] = Ms[i];
+  return DH2_OK;
 }
 
 void dh2_matrix_free(dh2_matrix* M) { matrix_release(M); }

@@ -22,6 +22,12 @@ constexpr int kPmaxF64 = 96;
 constexpr int kSigValues = 128;
 constexpr int kSigStride = kSigValues + 2;
 
+// Launch codes of the pair kernel: problem (6 bits) | side (1 bit) | pair (25 bits).
+constexpr int kCodeSideShift = 25;
+constexpr int kCodeProbShift = 26;
+constexpr uint32_t kCodePairMask = (1u << 25) - 1u;
+constexpr int kMaxBatch = 64;
+
 // Device status bits (OR-ed by kernels into one word).
 constexpr uint32_t kStatusNoConv = 1u;
 constexpr uint32_t kStatusTooLarge = 2u;

@@ -16,7 +16,6 @@ struct __align__(2 * sizeof(T)) C2 {
 // direction) pair).  Index [side] selects the row (0) or column (1) basis.
 template <typename T>
 struct PairArgs {
-  const int32_t* order;               // (side << 30) | pair, launch order
   const int32_t* start[2];            // first row index of the pair's cluster
   const int32_t* m[2];                // leaf rows (cluster size)
   const int32_t* ncols[2];            // #F_tc
@@ -38,7 +37,6 @@ struct PairArgs {
   double* sig[2];                     // per pair P values (descending)
   int32_t* rank[2];
   const double* eps2;                 // per level eps_l^2
-  int32_t P;                          // rows of the shared-memory factor (even)
   int32_t max_sweeps;
   uint32_t* status;
   // matrix-free mode: entries generated from points (permuted order, 3 doubles each)
@@ -75,8 +73,11 @@ __device__ __forceinline__ C2<T> helmholtz_entry(const double* pts, int64_t i, i
   }
 }
 
+// One CTA per launch code: args_dev holds one PairArgs per problem (device
+// memory); P is the row capacity of the shared-memory factor (even).
 template <typename T>
-void launch_pair_kernel(const PairArgs<T>& a, int nblocks, bool from_r, cudaStream_t st);
+void launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
+                        cudaStream_t st);
 
 // Phase cycle counters of the pair kernel (only with -DDH2_PROFILE).
 void prof_reset_pair();

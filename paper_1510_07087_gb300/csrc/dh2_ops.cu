@@ -59,10 +59,14 @@ __device__ __forceinline__ const C2<T>* xbasis(const SideView<T>& S, int pid) {
 // G_b into the nearfield buffer for an inadmissible one.  Each warp walks the
 // block column by column (contiguous runs of the row cluster).
 template <typename T>
-__global__ void __launch_bounds__(256) norms_near_kernel(NormsArgs<T> a, int nblocks) {
-  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+__global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __restrict__ args,
+                                                          const uint32_t* __restrict__ codes, int n) {
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (b >= nblocks) return;
+  if (w >= n) return;
+  const uint32_t code = codes ? codes[w] : (uint32_t)w;
+  const NormsArgs<T>& a = args[code >> 26];
+  const int b = (int)(code & ((1u << 26) - 1u));
   const int t = a.bt[b], s = a.bs[b];
   const int mt = a.csize[t], ms = a.csize[s];
   const int64_t t0 = a.cstart[t], s0 = a.cstart[s];
@@ -461,8 +465,8 @@ bool check_read_ops(CheckRecord* out) {
 }
 
 template <typename T>
-void launch_norms_near(const NormsArgs<T>& a, int nblocks, cudaStream_t st) {
-  if (nblocks > 0) norms_near_kernel<T><<<(nblocks + 7) / 8, 256, 0, st>>>(a, nblocks);
+void launch_norms_near(const NormsArgs<T>* args, const uint32_t* codes, int n, cudaStream_t st) {
+  if (n > 0) norms_near_kernel<T><<<(n + 7) / 8, 256, 0, st>>>(args, codes, n);
 }
 template <typename T>
 void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream_t st) {
@@ -507,7 +511,7 @@ void launch_error(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int nblo
 }
 
 #define DH2_INST(T)                                                                                         \
-  template void launch_norms_near<T>(const NormsArgs<T>&, int, cudaStream_t);                              \
+  template void launch_norms_near<T>(const NormsArgs<T>*, const uint32_t*, int, cudaStream_t);            \
   template void launch_expand<T>(const SideView<T>&, const int32_t*, int, cudaStream_t);                   \
   template void launch_project<T>(const ProjArgs<T>&, int, cudaStream_t);                                  \
   template void launch_mv_forward_leaf<T>(const SideView<T>&, const int32_t*, int, const C2<T>*, int,      \

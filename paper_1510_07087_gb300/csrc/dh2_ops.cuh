@@ -105,7 +105,9 @@ struct ErrArgs {
   int ref_gen;
 };
 
-template <typename T> void launch_norms_near(const NormsArgs<T>& a, int nblocks, cudaStream_t st);
+// codes: (problem << 26) | block for a batch, or NULL for blocks 0..n-1 of args_dev[0]
+template <typename T>
+void launch_norms_near(const NormsArgs<T>* args_dev, const uint32_t* codes, int n, cudaStream_t st);
 template <typename T> void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream_t st);
 template <typename T> void launch_project(const ProjArgs<T>& a, int nadm, cudaStream_t st);
 template <typename T>

@@ -149,7 +149,8 @@ template <typename T, int P_T, bool FROM_R>
 #ifndef DH2_PAIR_MINB
 #define DH2_PAIR_MINB 3
 #endif
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1) pair_kernel(const PairArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
+    pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
   constexpr int NT = 256;
   constexpr int LPR = NT / P_T;      // threads per row in the LQ
   constexpr int C = P_T == 64 ? 64 : 32;
@@ -165,7 +166,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1) pair_
   __shared__ int sh_piv;
   __shared__ double sh_E;
 
-  const int P = a.P;
   const int LDL = P + 1;              // column-major L: element (r, c) at c * LDL + r
   C2<T>* Lm = reinterpret_cast<C2<T>*>(smem);
   size_t soff = ((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15;
@@ -180,9 +180,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1) pair_
   T* nu = reinterpret_cast<T*>(smem + soff);         // residual row norms
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int code = a.order[blockIdx.x];
-  const int side = code >> 30;
-  const int pid = code & 0x3fffffff;
+  const uint32_t code = codes[blockIdx.x];
+  const int prob = (int)(code >> kCodeProbShift);
+  const int side = (int)((code >> kCodeSideShift) & 1u);
+  const int pid = (int)(code & kCodePairMask);
+  const PairArgs<T>& a = args[prob];
   if (!DH2_IN(pid, c_lim.npairs[side], 9, pid)) return;
   const int N = a.ncols[side][pid];
   const int kcap = a.kcap[side][pid];
@@ -644,15 +646,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1) pair_
 }
 
 template <typename T, int P_T, bool FROM_R>
-void launch_one(const PairArgs<T>& a, int nblocks, cudaStream_t st) {
+void launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
   constexpr int C = P_T == 64 ? 64 : 32;
-  const int P = a.P;
   const int LDL = P + 1;
   size_t smem = (((size_t)(P + 16) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
                 (size_t)P * sizeof(double) + 2 * (size_t)P * sizeof(int) + (size_t)P * sizeof(T);
   auto kern = pair_kernel<T, P_T, FROM_R>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<nblocks, 256, smem, st>>>(a);
+  kern<<<nblocks, 256, smem, st>>>(args, codes, P);
 }
 
 }  // namespace
@@ -695,18 +696,19 @@ bool prof_read_pair(unsigned long long* out8) {
 }
 
 template <typename T>
-void launch_pair_kernel(const PairArgs<T>& a, int nblocks, bool from_r, cudaStream_t st) {
+void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
+                        cudaStream_t st) {
   if (nblocks <= 0) return;
   if (!from_r) {
-    if (a.P <= 64) launch_one<T, 64, false>(a, nblocks, st);
-    else launch_one<T, 128, false>(a, nblocks, st);
+    if (P <= 64) launch_one<T, 64, false>(args, codes, nblocks, P, st);
+    else launch_one<T, 128, false>(args, codes, nblocks, P, st);
   } else {
-    if (a.P <= 64) launch_one<T, 64, true>(a, nblocks, st);
-    else launch_one<T, 128, true>(a, nblocks, st);
+    if (P <= 64) launch_one<T, 64, true>(args, codes, nblocks, P, st);
+    else launch_one<T, 128, true>(args, codes, nblocks, P, st);
   }
 }
 
-template void launch_pair_kernel<float>(const PairArgs<float>&, int, bool, cudaStream_t);
-template void launch_pair_kernel<double>(const PairArgs<double>&, int, bool, cudaStream_t);
+template void launch_pair_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t);
+template void launch_pair_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t);
 
 }  // namespace dh2
