@@ -227,6 +227,19 @@ def run_gpu(args):
     M = step()
     ranks = [M.ranks(0), M.ranks(1)]
     storage = M.storage()
+    # matrix-vector product with the compressed matrix (Section 4), one right-hand side
+    xv = torch.randn(args.n, dtype=cdt, device=dev)
+    yv = torch.empty_like(xv)
+    for _ in range(3):
+        D.dh2_matvec(M, xv, yv)
+    torch.cuda.synchronize()
+    m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    m0.record(stream)
+    for _ in range(10):
+        D.dh2_matvec(M, xv, yv)
+    m1.record(stream)
+    torch.cuda.synchronize()
+    matvec_ms = m0.elapsed_time(m1) / 10
     # error against the FP64 matrix (complex128, built the same way)
     del G
     rel_err = None
@@ -314,6 +327,7 @@ def run_gpu(args):
         "rel_err_vs_fp64": rel_err, "phases_ms": {k: float(v) for k, v in zip(
             ["norms_nearfield", "leaf_factors", "level_steps", "expansion", "projection"], phases)},
         "k_max": int(max(ranks[0].max(initial=0), ranks[1].max(initial=0))),
+        "matvec_ms": matvec_ms,
         "mem_per_n_kib_c128": storage["total"] * 16 / 1024 / args.n,
         "adm_fraction": st.adm_fraction, "roofline": roof, "step_roofline": step_roof, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": launches * args.steps, "launches_per_step": launches,

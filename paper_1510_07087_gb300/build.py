@@ -43,6 +43,8 @@ def build(verbose: bool = False) -> str:
         extra.append("-DDH2_PROFILE")
     if os.environ.get("DH2_SKIP_NEGLIGIBLE") == "1":
         extra.append("-DDH2_SKIP_NEGLIGIBLE")
+    if os.environ.get("DH2_LEAF_CHUNK"):
+        extra.append("-DDH2_LEAF_CHUNK=" + str(int(os.environ["DH2_LEAF_CHUNK"])))
     if os.environ.get("DH2_PAIR_MINB"):
         extra.append("-DDH2_PAIR_MINB=" + str(int(os.environ["DH2_PAIR_MINB"])))
     for src in CUDA_SOURCES:

@@ -149,11 +149,14 @@ template <typename T, int P_T, bool FROM_R>
 #ifndef DH2_PAIR_MINB
 #define DH2_PAIR_MINB 3
 #endif
+#ifndef DH2_LEAF_CHUNK
+#define DH2_LEAF_CHUNK 64
+#endif
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
     pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
   constexpr int NT = 256;
   constexpr int LPR = NT / P_T;      // threads per row in the LQ
-  constexpr int C = P_T == 64 ? 64 : 32;
+  constexpr int C = P_T == 64 ? DH2_LEAF_CHUNK : 32;
   constexpr int CPL = C / LPR;       // chunk entries per thread
   constexpr int XTRA = 16;           // spare L columns used to stage R chunks
   static_assert(C % LPR == 0, "chunk width must split over the threads of a row");
@@ -647,7 +650,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
 
 template <typename T, int P_T, bool FROM_R>
 void launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
-  constexpr int C = P_T == 64 ? 64 : 32;
+  constexpr int C = P_T == 64 ? DH2_LEAF_CHUNK : 32;
   const int LDL = P + 1;
   size_t smem = (((size_t)(P + 16) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
                 (size_t)P * sizeof(double) + 2 * (size_t)P * sizeof(int) + (size_t)P * sizeof(T);
