@@ -212,7 +212,7 @@ def run_gpu(args):
         del M
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    phases = np.zeros(5)
+    phases = np.zeros(6)
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -278,35 +278,42 @@ def run_gpu(args):
     peaks, src = _peaks()
     adm_bytes = elem * st.adm_fraction * args.n * args.n
     leaf_ms = float(phases[1])
-    # algorithmic flops of the leaf launch (per pair and basis: factor 4 m^2 N,
-    # R = Q^* A 8 k m N; real flops), summed with the computed ranks
+    rq_ms = float(phases[2])
+    # algorithmic flops of the leaf launches (per pair and basis, real flops):
+    # factor 4 m^2 N (pair_kernel), R = Q^* A 8 k m N (rq_kernel), summed with
+    # the computed ranks; bytes: both bases read every admissible entry once
     size = T.clusters()["size"].astype(np.float64)
     flops = 0.0
+    rq_flops = 0.0
     for sd in (0, 1):
         pr = T.pairs(sd)
         lf = pr["leaf"].astype(bool)
         m = size[pr["cluster"]][lf]
         N = pr["ncols"][lf].astype(np.float64)
         k = ranks[sd][lf].astype(np.float64)
-        flops += float(np.sum(4.0 * m * m * N + 8.0 * k * m * N))
+        flops += float(np.sum(4.0 * m * m * N))
+        rq_flops += float(np.sum(8.0 * k * m * N))
+    leaf_bytes = 2.0 * adm_bytes
     import hashlib
     src_sha = hashlib.sha1(open(os.path.join(ROOT, "paper_1510_07087_gb300", "csrc", "dh2_pair.cu"), "rb")
                            .read()).hexdigest()
     traffic = (PAIR_TRAFFIC["bytes"] if (src_sha == PAIR_TRAFFIC["sha1"] and args.n == 32768 and args.leaf == 64
                                          and args.mode == "fp32") else None)
     achieved = flops / (leaf_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "pair_kernel (leaf launch: LQ, pivoted truncation, Jacobi, R)",
+    roof = {"bound": "alu", "kernel": "pair_kernel (leaf launch: LQ, pivoted truncation, Jacobi, Q)",
             "achieved": achieved, "peak": FP32_ALU_TFLOPS, "peak_source": "derived (152 SM x 128 FP32 x 2 x 2.07 GHz)",
             "unit": "TFLOP/s", "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic,
-            "alg_flops_per_launch": flops, "alg_bytes_per_launch": adm_bytes,
-            "hbm_view": {"achieved_gbs": adm_bytes / (leaf_ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
-                         "frac": adm_bytes / (leaf_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": src}}
+            "alg_flops_per_launch": flops, "alg_bytes_per_launch": leaf_bytes,
+            "hbm_view": {"achieved_gbs": leaf_bytes / (leaf_ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                         "frac": leaf_bytes / (leaf_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": src},
+            "rq_kernel": {"ms": rq_ms, "alg_flops": rq_flops, "alg_bytes": leaf_bytes,
+                          "achieved_gbs": leaf_bytes / (rq_ms * 1e-3) / 1e9,
+                          "hbm_frac": leaf_bytes / (rq_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                          "achieved_tflops": rq_flops / (rq_ms * 1e-3) / 1e12,
+                          "alu_frac": rq_flops / (rq_ms * 1e-3) / 1e12 / FP32_ALU_TFLOPS}}
     t_roof_ms = in_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
     step_roof = {"bound": "hbm", "t_roof_ms": t_roof_ms, "frac": t_roof_ms / ms,
                  "note": "one read of all of G at the measured copy bandwidth, against the whole step"}
-    # kernels per compress: norms/nearfield, leaf factors, one non-leaf launch
-    # per level with non-leaf pairs, one expansion launch per level with
-    # non-leaf column pairs, projection
     lv = T.clusters()["level"]
     nl_levels = set()
     col_nl_levels = set()
@@ -317,7 +324,9 @@ def run_gpu(args):
                 nl_levels.add(int(lv[c]))
                 if sd == 1:
                     col_nl_levels.add(int(lv[c]))
-    launches = 3 + len(nl_levels) + len(col_nl_levels)
+    # norms, leaf factors + R, (factors + R) per non-leaf level, expansion
+    # per level with non-leaf column pairs, projection
+    launches = 4 + 2 * len(nl_levels) + len(col_nl_levels)
     line = {
         "metric": "compression wall time & input GB/s at n=32768, kappa=32, eps=1e-4; rel. error vs FP64",
         "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
@@ -325,7 +334,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "c64/f32 (f64 tail sums)" if args.mode == "fp32" else "c128/f64",
         "data": "synthetic (Fibonacci sphere, Helmholtz collocation)", "config": workload(args),
         "rel_err_vs_fp64": rel_err, "phases_ms": {k: float(v) for k, v in zip(
-            ["norms_nearfield", "leaf_factors", "level_steps", "expansion", "projection"], phases)},
+            ["norms_nearfield", "leaf_factors", "leaf_R", "level_steps", "expansion", "projection"], phases)},
         "k_max": int(max(ranks[0].max(initial=0), ranks[1].max(initial=0))),
         "matvec_ms": matvec_ms,
         "mem_per_n_kib_c128": storage["total"] * 16 / 1024 / args.n,

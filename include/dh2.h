@@ -233,9 +233,11 @@ dh2_status dh2_matrix_coupling(const dh2_matrix* M, int64_t block, double* out, 
 /* Storage in stored entries (Def. "DH^2-matrix representation"):
  * parts[0..5] = V leaves, W leaves, E of V, E of W, S, nearfield; *total = sum. */
 dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts);
-/* Time of the last dh2_compress per phase in ms measured with CUDA events:
- * [0] norms+nearfield, [1] leaf factors, [2] level steps, [3] expansion, [4] projection. */
-dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms5);
+/* Time of the last dh2_compress per phase in ms measured with CUDA events
+ * (ms6: host array of 6 floats): [0] norms+nearfield, [1] leaf factors,
+ * [2] leaf R = Q^* A, [3] level steps (factors and R), [4] expansion,
+ * [5] projection. */
+dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms6);
 
 const char* dh2_status_string(dh2_status s);
 /* Library version string. */

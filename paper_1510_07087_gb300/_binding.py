@@ -271,7 +271,7 @@ class Matrix:
         return d
 
     def phase_ms(self) -> np.ndarray:
-        out = np.zeros(5, dtype=np.float32)
+        out = np.zeros(6, dtype=np.float32)
         _check(_lib().dh2_matrix_phase_ms(self.handle, _ptr(out)), "dh2_matrix_phase_ms")
         return out
 

@@ -41,12 +41,10 @@ def build(verbose: bool = False) -> str:
     extra = ["-DDH2_CHECK"] if os.environ.get("DH2_CHECK") == "1" else []
     if os.environ.get("DH2_PROFILE") == "1":
         extra.append("-DDH2_PROFILE")
-    if os.environ.get("DH2_SKIP_NEGLIGIBLE") == "1":
-        extra.append("-DDH2_SKIP_NEGLIGIBLE")
-    if os.environ.get("DH2_LEAF_CHUNK"):
-        extra.append("-DDH2_LEAF_CHUNK=" + str(int(os.environ["DH2_LEAF_CHUNK"])))
-    if os.environ.get("DH2_PAIR_MINB"):
-        extra.append("-DDH2_PAIR_MINB=" + str(int(os.environ["DH2_PAIR_MINB"])))
+    # tuning macros of the pair kernel (defaults in csrc/dh2_pair.cu)
+    for name in ("DH2_PAIR_MINB", "DH2_PAIR_MINB128", "DH2_LEAF_NT", "DH2_JACOBI_TPP"):
+        if os.environ.get(name):
+            extra.append(f"-D{name}={int(os.environ[name])}")
     for src in CUDA_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)

@@ -78,6 +78,7 @@ struct dh2_matrix {
   void* R[2] = {nullptr, nullptr};
   void* Q[2] = {nullptr, nullptr};
   void* X[2] = {nullptr, nullptr};
+  void* colw[2] = {nullptr, nullptr};  // per column-map entry 1/omega (FP32 or FP64)
   double* sig[2] = {nullptr, nullptr};
   int32_t* rank[2] = {nullptr, nullptr};
   void* S = nullptr;
@@ -92,7 +93,7 @@ struct dh2_matrix {
   int nearfield_copy = 1;
   bool v_expanded = false;
   std::vector<double> eps2_h, zpow_h;
-  float phase_ms[5] = {0, 0, 0, 0, 0};
+  float phase_ms[6] = {0, 0, 0, 0, 0, 0};
   // matrix-free mode
   int gen = 0;
   double* pts = nullptr;  // device, permuted order
@@ -426,6 +427,7 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
     pa.cmoff[sd] = D->cmoff[sd];
     pa.gcol[sd] = D->gcol[sd];
     pa.gblk[sd] = D->gblk[sd];
+    pa.colw[sd] = (const T*)M->colw[sd];
     pa.son[sd] = D->son[sd];
     pa.sonoff[sd] = D->sonoff[sd];
     pa.level[sd] = D->level[sd];
@@ -457,8 +459,8 @@ template <typename T>
 dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params& cp, cudaStream_t st) {
   const int nprob = (int)Ms.size();
   const int pmax = sizeof(T) == 4 ? kPmaxF32 : kPmaxF64;
-  cudaEvent_t ev[6];
-  for (int i = 0; i < 6; ++i) DH2_CUDA_TRY(cudaEventCreate(&ev[i]));
+  cudaEvent_t ev[7];
+  for (int i = 0; i < 7; ++i) DH2_CUDA_TRY(cudaEventCreate(&ev[i]));
   std::vector<PairArgs<T>> pas(nprob);
   std::vector<NormsArgs<T>> nas(nprob);
   for (int i = 0; i < nprob; ++i) fill_args<T>(Ms[i], cp, pas[i], nas[i]);
@@ -573,32 +575,40 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #endif
   cudaEventRecord(ev[0], st);
   launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
+  for (dh2_matrix* M : Ms)
+    for (int sd = 0; sd < 2; ++sd)
+      launch_colw<T>(M->tree->tr.dev->gblk[sd], M->invw, (T*)M->colw[sd],
+                     (int64_t)M->tree->tr.side[sd].gcol.size(), st);
   DH2_PHASE_SYNC("norms_near");
   cudaEventRecord(ev[1], st);
 #ifdef DH2_PROFILE
   prof_reset_pair();
 #endif
   launch_pair_kernel<T>(d_pa, d_leaf, (int)n_leaf, P_leaf, false, st);
+  cudaEventRecord(ev[2], st);
+  launch_rq_kernel<T>(d_pa, d_leaf, (int)n_leaf, P_leaf, false, st);
 #ifdef DH2_PROFILE
   {
     cudaStreamSynchronize(st);
-    unsigned long long pr[8];
+    unsigned long long pr[10];
     prof_read_pair(pr);
     const double np = pr[5] ? (double)pr[5] : 1.0;
     std::fprintf(stderr,
-                 "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean K %.1f, mean sweeps %.2f, cycles/pair: "
-                 "LQ %.0f Jacobi %.0f rank+Q %.0f R %.0f\n",
-                 pr[5], pr[6] / np, pr[7] / np, pr[4] / np, pr[0] / np, pr[1] / np, pr[2] / np, pr[3] / np);
+                 "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean K %.1f, mean sweeps %.2f, mean chunks %.2f, "
+                 "cycles/pair: LQ %.0f (staging %.0f) Jacobi %.0f rank+Q %.0f\n",
+                 pr[5], pr[6] / np, pr[7] / np, pr[4] / np, pr[9] / np, pr[0] / np, pr[8] / np, pr[1] / np,
+                 pr[2] / np);
   }
 #endif
   DH2_PHASE_SYNC("leaf pairs");
-  cudaEventRecord(ev[2], st);
+  cudaEventRecord(ev[3], st);
   for (int l = maxdepth; l >= 0; --l) {
     if (n_nl[l] == 0) continue;
     launch_pair_kernel<T>(d_pa, d_nl[l], (int)n_nl[l], P_level[l], true, st);
+    launch_rq_kernel<T>(d_pa, d_nl[l], (int)n_nl[l], P_level[l], true, st);
     DH2_PHASE_SYNC("non-leaf pairs");
   }
-  cudaEventRecord(ev[3], st);
+  cudaEventRecord(ev[4], st);
   for (dh2_matrix* M : Ms) {
     Tree& tr = M->tree->tr;
     Tree::Dev* D = tr.dev;
@@ -609,7 +619,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       DH2_PHASE_SYNC("expand");
     }
   }
-  cudaEventRecord(ev[4], st);
+  cudaEventRecord(ev[5], st);
   for (dh2_matrix* M : Ms) {
     Tree& tr = M->tree->tr;
     Tree::Dev* D = tr.dev;
@@ -628,7 +638,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     launch_project<T>(pj, (int)D->nadm, st);
     DH2_PHASE_SYNC("project");
   }
-  cudaEventRecord(ev[5], st);
+  cudaEventRecord(ev[6], st);
   cudaFreeAsync(scratch, st);
   std::vector<uint32_t> status(nprob, 0);
   cudaError_t e1 = cudaSuccess;
@@ -636,9 +646,9 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     e1 = cudaMemcpyAsync(&status[i], Ms[i]->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   cudaError_t e2 = cudaStreamSynchronize(st);
   cudaError_t e3 = cudaGetLastError();
-  float ph[5] = {0, 0, 0, 0, 0};
-  for (int i = 0; i < 5; ++i) cudaEventElapsedTime(&ph[i], ev[i], ev[i + 1]);
-  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  float ph[6] = {0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&ph[i], ev[i], ev[i + 1]);
+  for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
   for (dh2_matrix* M : Ms) std::memcpy(M->phase_ms, ph, sizeof(ph));
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return DH2_ECUDA;
 #ifdef DH2_CHECK
@@ -895,6 +905,8 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   sz[ns++] = align256(16);
   sz[ns++] = align256(16);
   sz[ns++] = align256(gen ? 24 * (size_t)tr.n : 0);
+  sz[ns++] = align256(es / 2 * tr.side[0].gcol.size());
+  sz[ns++] = align256(es / 2 * tr.side[1].gcol.size());
   size_t total = 0;
   for (int i = 0; i < ns; ++i) total += sz[i];
   if (cudaMallocAsync(&M->arena, total, M->stream) != cudaSuccess) {
@@ -904,10 +916,10 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   }
   M->arena_bytes = total;
   char* p = (char*)M->arena;
-  void** dst[18] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
+  void** dst[20] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
                     (void**)&M->sig[0], (void**)&M->sig[1], (void**)&M->rank[0], (void**)&M->rank[1],
                     (void**)&M->invw, (void**)&M->eps2, (void**)&M->zpow, (void**)&M->status, (void**)&M->acc,
-                    (void**)&M->pts};
+                    (void**)&M->pts, &M->colw[0], &M->colw[1]};
   for (int i = 0; i < ns; ++i) {
     *dst[i] = p;
     p += sz[i];
@@ -1265,9 +1277,9 @@ dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts) {
   return DH2_OK;
 }
 
-dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms5) {
-  if (!M || !ms5) return DH2_EINVAL;
-  for (int i = 0; i < 5; ++i) ms5[i] = M->phase_ms[i];
+dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms6) {
+  if (!M || !ms6) return DH2_EINVAL;
+  for (int i = 0; i < 6; ++i) ms6[i] = M->phase_ms[i];
   return DH2_OK;
 }
 

@@ -21,7 +21,8 @@ struct PairArgs {
   const int32_t* ncols[2];            // #F_tc
   const int64_t* cmoff[2];            // leaf column-map offsets
   const int32_t* gcol[2];             // leaf column map: index of G's other dimension
-  const int32_t* gblk[2];             // leaf column map: block id (weight)
+  const int32_t* gblk[2];             // leaf column map: block id
+  const T* colw[2];                   // leaf column map: weight 1/omega of the column's block
   const int32_t* son[2];              // non-leaf: 2 son pairs
   const int32_t* sonoff[2];           // non-leaf: column offsets in the son pairs
   const int32_t* level[2];
@@ -79,8 +80,14 @@ template <typename T>
 void launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
                         cudaStream_t st);
 
-// Phase cycle counters of the pair kernel (only with -DDH2_PROFILE).
+// R = Q^* A for the same launch codes, after launch_pair_kernel (one CTA per
+// pair; P as for the pair kernel).
+template <typename T>
+void launch_rq_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
+                      cudaStream_t st);
+
+// Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 10 values.
 void prof_reset_pair();
-bool prof_read_pair(unsigned long long* out8);
+bool prof_read_pair(unsigned long long* out10);
 
 }  // namespace dh2

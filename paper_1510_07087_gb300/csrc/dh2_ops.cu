@@ -510,7 +510,22 @@ void launch_error(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int nblo
   if (nblocks > 0) error_kernel<T, RT><<<nblocks, 256, 0, st>>>(a, Gref, ldr, acc);
 }
 
+// Per-column weights of a column map: colw[j] = 1/omega_b for the block b of
+// column j (Remark "Error control"), so that the pair kernels read the weight
+// of a column without the block-id indirection.
+template <typename T>
+__global__ void colw_kernel(const int32_t* __restrict__ gblk, const double* __restrict__ invw, T* __restrict__ colw,
+                            int64_t n) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    colw[j] = (T)invw[gblk[j]];
+}
+template <typename T>
+void launch_colw(const int32_t* gblk, const double* invw, T* colw, int64_t n, cudaStream_t st) {
+  if (n > 0) colw_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(gblk, invw, colw, n);
+}
+
 #define DH2_INST(T)                                                                                         \
+  template void launch_colw<T>(const int32_t*, const double*, T*, int64_t, cudaStream_t);                  \
   template void launch_norms_near<T>(const NormsArgs<T>*, const uint32_t*, int, cudaStream_t);            \
   template void launch_expand<T>(const SideView<T>&, const int32_t*, int, cudaStream_t);                   \
   template void launch_project<T>(const ProjArgs<T>&, int, cudaStream_t);                                  \

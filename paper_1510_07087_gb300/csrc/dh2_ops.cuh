@@ -105,6 +105,9 @@ struct ErrArgs {
   int ref_gen;
 };
 
+// colw[j] = 1/omega of the block of column j of a column map (n entries)
+template <typename T>
+void launch_colw(const int32_t* gblk, const double* invw, T* colw, int64_t n, cudaStream_t st);
 // codes: (problem << 26) | block for a batch, or NULL for blocks 0..n-1 of args_dev[0]
 template <typename T>
 void launch_norms_near(const NormsArgs<T>* args_dev, const uint32_t* codes, int n, cudaStream_t st);

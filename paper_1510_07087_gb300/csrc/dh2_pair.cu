@@ -19,10 +19,11 @@
 //      tail sums formed in FP64;
 //   4. writes Q = first k left singular vectors (Q_tc for a leaf, the stacked
 //      transfer matrices [E_t1c; E_t2c] for a non-leaf), the singular values
-//      and k, and
-//   5. streams A once more through shared memory to form R_tc = Q^* A
-//      (Section 6, R recursion).
+//      and k.
+// rq_kernel then streams A once more to form R_tc = Q^* A (Section 6, R
+// recursion) for all pairs of the launch at once.
 #include <cfloat>
+#include <cstdlib>
 
 #include "dh2_check.cuh"
 #include "dh2_internal.h"
@@ -35,8 +36,9 @@ namespace {
 DH2_CHECK_DECLS
 
 #ifdef DH2_PROFILE
-// per-phase clock cycles summed over CTAs: LQ, Jacobi, rank+Q, R; sweeps; pairs
-__device__ unsigned long long g_prof[8];
+// summed over CTAs: cycles of LQ, Jacobi, rank+Q, R; sweeps; pairs; p; K;
+// cycles of the LQ staging; chunks
+__device__ unsigned long long g_prof[10];
 #define DH2_PROF_T(v) const long long v = clock64()
 #define DH2_PROF_ADD(i, v) \
   if (threadIdx.x == 0) atomicAdd(&g_prof[i], (unsigned long long)(v))
@@ -87,6 +89,16 @@ __device__ __forceinline__ double frsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
+// Asynchronous global -> shared copies (cp.async): not held up by CTA
+// barriers; completed by cp_async_wait_all in the issuing thread.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Element (r, j) of the pair's matrix A (row r of the factor, column j of F_tc).
 template <typename T, bool FROM_R>
 struct Source {
@@ -96,8 +108,7 @@ struct Source {
   int64_t ld;
   int r0;
   const int32_t* gcol;
-  const int32_t* gblk;
-  const double* invw;
+  const T* colw;
   int64_t cmo;
   const double* pts;  // matrix-free mode
   double kappa, diag;
@@ -107,6 +118,52 @@ struct Source {
   const C2<T>* R1;
   int64_t roff0, roff1;
   int k1, off0, off1, ld0, ld1;
+
+  // leaf: global column index and weight 1/omega_b of column j of F_tc
+  __device__ __forceinline__ void colinfo(int j, int& gc, T& w) const {
+    gc = 0;
+    w = T(0);
+    if (!DH2_IN(cmo + j, c_lim.ncol[side], 3, pid)) return;
+    gc = gcol[j];
+    w = colw[j];
+  }
+  // leaf: address of G's entry behind element (r, j) of A given column j's
+  // global index gc (NULL if out of range: checked builds only)
+  __device__ __forceinline__ const C2<T>* leaf_ptr(int r, int gc) const {
+    const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
+    if (!DH2_IN(e, c_lim.G, side == 0 ? 5 : 7, pid)) return nullptr;
+    return G + e;
+  }
+  // non-leaf: address of element (r, j) of Ghat in the sons' R (NULL as above)
+  __device__ __forceinline__ const C2<T>* sons_ptr(int r, int j) const {
+    if (r < k1) {
+      const int64_t e = (int64_t)(off0 + j) * ld0 + r;
+      if (!DH2_IN(roff0 + e, c_lim.R[side], 1, pid)) return nullptr;
+      return R0 + e;
+    }
+    const int64_t e = (int64_t)(off1 + j) * ld1 + (r - k1);
+    if (!DH2_IN(roff1 + e, c_lim.R[side], 2, pid)) return nullptr;
+    return R1 + e;
+  }
+  // leaf: element (r, j) given column j's global index gc and weight w
+  __device__ __forceinline__ C2<T> leaf_at(int r, int gc, T w) const {
+    if (gen) {
+      C2<T> g = side == 0 ? helmholtz_entry<T>(pts, r0 + r, gc, kappa, diag)
+                          : helmholtz_entry<T>(pts, gc, r0 + r, kappa, diag);
+      return C2<T>{g.re * w, side == 0 ? g.im * w : -g.im * w};
+    }
+    if (side == 0) {
+      const int64_t e = (int64_t)gc * ld + r0 + r;
+      if (!DH2_IN(e, c_lim.G, 5, pid)) return czero<T>();
+      const C2<T> g = G[e];
+      return C2<T>{g.re * w, g.im * w};
+    }
+    // column basis: the same procedure on G^*; row r of A is column r0+r of G
+    const int64_t e = (int64_t)(r0 + r) * ld + gc;
+    if (!DH2_IN(e, c_lim.G, 7, pid)) return czero<T>();
+    const C2<T> g = G[e];
+    return C2<T>{g.re * w, -g.im * w};
+  }
 
   __device__ __forceinline__ C2<T> get(int r, int j) const {
     if (FROM_R) {
@@ -119,66 +176,111 @@ struct Source {
       if (!DH2_IN(roff1 + e, c_lim.R[side], 2, pid)) return czero<T>();
       return R1[e];
     } else {
-      if (!DH2_IN(cmo + j, c_lim.ncol[side], 3, pid)) return czero<T>();
-      const int gc = gcol[j];
-      const int b = gblk[j];
-      if (!DH2_IN(b, c_lim.nblocks, 4, pid)) return czero<T>();
-      const T w = (T)invw[b];
-      if (gen) {
-        C2<T> g = side == 0 ? helmholtz_entry<T>(pts, r0 + r, gc, kappa, diag)
-                            : helmholtz_entry<T>(pts, gc, r0 + r, kappa, diag);
-        return C2<T>{g.re * w, side == 0 ? g.im * w : -g.im * w};
-      }
-      if (side == 0) {
-        const int64_t e = (int64_t)gc * ld + r0 + r;
-        if (!DH2_IN(e, c_lim.G, 5, pid)) return czero<T>();
-        const C2<T> g = G[e];
-        return C2<T>{g.re * w, g.im * w};
-      }
-      // column basis: the same procedure on G^*; row r of A is column r0+r of G
-      const int64_t e = (int64_t)(r0 + r) * ld + gc;
-      if (!DH2_IN(e, c_lim.G, 7, pid)) return czero<T>();
-      const C2<T> g = G[e];
-      return C2<T>{g.re * w, -g.im * w};
+      int gc;
+      T w;
+      colinfo(j, gc, w);
+      return leaf_at(r, gc, w);
     }
   }
 };
 
+// Column table of columns j0 .. j0+cwid-1 of a leaf pair: global index and
+// weight 1/omega_b (read first, so that the element loads do not wait on the
+// column map).
+template <typename T, bool FROM_R, int NT>
+__device__ __forceinline__ void stage_table(const Source<T, FROM_R>& src, int j0, int cwid, int* cgc, T* cwt) {
+  if (FROM_R) return;
+  for (int jj = threadIdx.x; jj < cwid; jj += NT) {
+    int gc;
+    T w;
+    src.colinfo(j0 + jj, gc, w);
+    cgc[jj] = gc;
+    cwt[jj] = w;
+  }
+}
+
+// Columns j0 .. j0+ncols-1 of the pair's matrix A (zero from column cwid on)
+// into dst, column jj at dst[jj * ld]: 8 loads in flight per thread,
+// consecutive threads on the contiguous direction of the source (the rows of
+// A for G and for the sons' R, the columns of A for G^*).  A leaf needs the
+// column table of stage_table, visible to every thread.
+template <typename T, bool FROM_R, int NT>
+__device__ __forceinline__ void stage_cols(const Source<T, FROM_R>& src, int p, int j0, int cwid, int ncols,
+                                           C2<T>* dst, int ld, const int* cgc, const T* cwt) {
+  const int tid = threadIdx.x;
+  const bool down = FROM_R || src.side == 0;
+  const int tot = ncols * p;
+  for (int e0 = 0; e0 < tot; e0 += 8 * NT) {
+    C2<T> v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * NT;
+      const int r = down ? e % p : e / ncols;
+      const int jj = down ? e / p : e % ncols;
+      v[u] = czero<T>();
+      if (e < tot && jj < cwid) v[u] = FROM_R ? src.get(r, j0 + jj) : src.leaf_at(r, cgc[jj], cwt[jj]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + tid + u * NT;
+      const int r = down ? e % p : e / ncols;
+      const int jj = down ? e / p : e % ncols;
+      if (e < tot) dst[jj * ld + r] = v[u];
+    }
+  }
+}
+
 // P_T: largest factor size of the instantiation (64 or 128 rows).
-template <typename T, int P_T, bool FROM_R>
+// NT: threads per CTA (256, or 128 for the leaf launch when DH2_LEAF_NT=128).
 #ifndef DH2_PAIR_MINB
 #define DH2_PAIR_MINB 3
 #endif
-#ifndef DH2_LEAF_CHUNK
-#define DH2_LEAF_CHUNK 64
+#ifndef DH2_PAIR_MINB128
+#define DH2_PAIR_MINB128 5
 #endif
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
+#ifndef DH2_LEAF_NT
+#define DH2_LEAF_NT 256
+#endif
+#ifndef DH2_JACOBI_TPP
+#define DH2_JACOBI_TPP 32  // most threads per column pair in the Jacobi step (4..32)
+#endif
+template <int NT, typename T>
+constexpr int pair_min_blocks() {
+  return sizeof(T) == 4 ? (NT == 256 ? DH2_PAIR_MINB : DH2_PAIR_MINB128) : (NT == 256 ? 1 : 2);
+}
+
+template <typename T, int P_T, bool FROM_R, int NT>
+__global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
-  constexpr int NT = 256;
-  constexpr int LPR = NT / P_T;      // threads per row in the LQ
-  constexpr int C = P_T == 64 ? DH2_LEAF_CHUNK : 32;
-  constexpr int CPL = C / LPR;       // chunk entries per thread
-  constexpr int XTRA = 16;           // spare L columns used to stage R chunks
-  static_assert(C % LPR == 0, "chunk width must split over the threads of a row");
+  constexpr int LPR = NT / P_T;      // threads per row in the pivoted LQ (rows in place)
+  constexpr int LQT = 8;             // threads per row in the streamed LQ (a quarter warp)
+  constexpr int NW = NT / 32;        // warps
+  constexpr int S = P_T / (NT / LQT);  // rows per group of LQT threads
+  constexpr int E = 16 / S;          // chunk entries per thread and row
+  constexpr int C = LQT * E;         // chunk width (16 * NT / P_T)
+  static_assert(LPR >= 1 && LPR <= 32 && S >= 1 && S * E == 16, "16 chunk entries per thread");
+  constexpr int XTRA = C;            // columns after L: the staged chunk of A
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ C2<T> sh_v0[2];
   __shared__ T sh_tau[2];
   __shared__ int sh_skip[2];
+  // leaf column table of the chunk being staged: global index, weight
+  __shared__ int cgc[64];
+  __shared__ T cwt[64];
+  static_assert(C <= 64, "chunk column table");
   __shared__ int sh_rot[2];
   __shared__ int sh_k;
-  __shared__ int sh_piv;
-  __shared__ double sh_E;
 
   const int LDL = P + 1;              // column-major L: element (r, c) at c * LDL + r
   C2<T>* Lm = reinterpret_cast<C2<T>*>(smem);
   size_t soff = ((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15;
-  C2<T>* vbuf = reinterpret_cast<C2<T>*>(smem + soff);  // 2 x C reflector rows
+  C2<T>* vbuf = reinterpret_cast<C2<T>*>(smem + soff);  // 2 x C reflection vectors
   soff += 2 * C * sizeof(C2<T>);
   double* sig2 = reinterpret_cast<double*>(smem + soff);
   soff += (size_t)P * sizeof(double);
   int* ord = reinterpret_cast<int*>(smem + soff);
   soff += (size_t)P * sizeof(int);
-  int* perm = reinterpret_cast<int*>(smem + soff);  // row permutation of the pivoted LQ
+  int* pcol = reinterpret_cast<int*>(smem + soff);  // pivot step of each row in the pivoted LQ
   soff += (size_t)P * sizeof(int);
   T* nu = reinterpret_cast<T*>(smem + soff);         // residual row norms
 
@@ -215,10 +317,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
     src.r0 = a.start[side][pid];
     src.cmo = a.cmoff[side][pid];
     src.gcol = a.gcol[side] + src.cmo;
-    src.gblk = a.gblk[side] + src.cmo;
+    src.colw = a.colw[side] + src.cmo;
     src.G = a.G;
     src.ld = a.ld;
-    src.invw = a.invw;
     src.pts = a.pts;
     src.kappa = a.kappa;
     src.diag = a.diag;
@@ -239,42 +340,61 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
     return;
   }
 
-  for (int i = tid; i < (P + XTRA) * LDL; i += NT) Lm[i] = czero<T>();
+  for (int i = tid; i < P * LDL; i += NT) Lm[i] = czero<T>();  // L; the staging columns need none
   DH2_PROF_T(t_a);
 
   // ---------------------------------------------------------------- 1. LQ
-  const int row = tid / LPR, q = tid % LPR;
-  const unsigned gmask = (LPR == 32) ? 0xffffffffu : (((1u << LPR) - 1u) << (lane & ~(LPR - 1)));
+  // Rows go to groups of LQT threads in blocks of four consecutive rows, the
+  // blocks dealt round-robin over the warps, so that the rows still active at
+  // step i stay spread over all warps and the four rows sharing a warp finish
+  // together.  Each thread keeps E entries of each of its S rows of the
+  // current chunk in registers; the chunk is first staged through shared
+  // memory with coalesced loads.  Step i applies reflection i (row i) to the
+  // rows below it; the warp owning row i+1 updates that row's block first and
+  // forms reflection i+1, then updates its other rows; one barrier per step.
+  // The reductions over a row run on its quarter warp alone (measured faster
+  // than running every quarter converged with the full mask).
+  const int row = tid / LPR, q = tid % LPR;  // row mapping of the pivoted LQ (1b)
   const bool live = row < p;
-  C2<T> ch[CPL];
+  const int lq = lane & (LQT - 1);
+  const int quarter = lane >> 3;
+  // row of slot s of this thread: block warp + NW * s, row `quarter` in it
+  auto lrow = [&](int s) { return 4 * (warp + NW * s) + quarter; };
+  // does slot s of this warp hold a row r > j (r < p)?
+  auto slot_live = [&](int s, int j) { return min(4 * (warp + NW * s) + 3, p - 1) > j; };
+  C2<T>* Xs = Lm + (int64_t)P * LDL;  // staged chunk: column jj at Xs[jj * LDL]
+  C2<T> ch[S][E];
 
-  // Householder reflection of row i (held by its LPR threads) from the right:
-  // the row becomes (beta, 0, ..., 0) on the columns {i} u chunk,
-  // beta = -e^{i arg alpha} |x|; the chunk part goes to vbuf[slot].
-  auto make_reflector = [&](int i, int slot) {
+  // Householder reflection of row r from the right: the row becomes
+  // (beta, 0, ..., 0) on the columns {r} u chunk, beta = -e^{i arg alpha} |x|;
+  // the chunk part x is the reflection's vector (vbuf[slot]).  Called by a
+  // whole warp; only the quarter holding row r (mine) works.
+  auto publish = [&](int r, const C2<T> (&x)[E], bool mine, int slot) {
+    if (!mine) return;
+    const unsigned qmask = 0xffu << (lane & 24);
     T s0 = T(0), s1 = T(0);
 #pragma unroll
-    for (int u = 0; u < CPL; u += 2) {
-      s0 += cnorm2(ch[u]);
-      s1 += cnorm2(ch[u + 1]);
-      vbuf[slot * C + q + u * LPR] = ch[u];
-      vbuf[slot * C + q + (u + 1) * LPR] = ch[u + 1];
+    for (int u = 0; u < E; u += 2) {
+      s0 += cnorm2(x[u]);
+      if (u + 1 < E) s1 += cnorm2(x[u + 1]);
     }
-    T s = s0 + s1;
+    s0 += s1;
 #pragma unroll
-    for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
-    if (q == 0) {
-      if (!(s > Eps<T>::tiny)) {
+    for (int o = 1; o < LQT; o <<= 1) s0 += __shfl_xor_sync(qmask, s0, o);
+#pragma unroll
+    for (int u = 0; u < E; ++u) vbuf[slot * C + lq + u * LQT] = x[u];
+    if (lq == 0) {
+      if (!(s0 > Eps<T>::tiny)) {
         sh_skip[slot] = 1;
       } else {
-        const C2<T> al = Lm[i * LDL + i];
+        const C2<T> al = Lm[r * LDL + r];
         const T an2 = cnorm2(al);
         const T ra = an2 > Eps<T>::tiny ? frsqrt(an2) : T(0);
         const T an = an2 * ra;
-        const T xn2 = s + an2;
+        const T xn2 = s0 + an2;
         const T xn = xn2 * frsqrt(xn2);
         const C2<T> ph = an2 > Eps<T>::tiny ? C2<T>{al.re * ra, al.im * ra} : C2<T>{T(1), T(0)};
-        Lm[i * LDL + i] = C2<T>{-ph.re * xn, -ph.im * xn};
+        Lm[r * LDL + r] = C2<T>{-ph.re * xn, -ph.im * xn};
         sh_v0[slot] = C2<T>{ph.re * (an + xn), -ph.im * (an + xn)};
         sh_tau[slot] = fdiv(T(1), xn * (xn + an));
         sh_skip[slot] = 0;
@@ -282,42 +402,153 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
     }
   };
 
-  for (int j0 = 0; j0 < N; j0 += C) {
-    const int cw = min(C, N - j0);
+  // apply reflection j (vector x, scalars v0, tau) to this thread's row r of a
+  // slot (entries c); called by a whole warp, rows other than j < r < p are
+  // left unchanged (their quarters return at once)
+  auto apply = [&](C2<T> (&c)[E], int r, int j, const C2<T> (&x)[E], C2<T> v0, T tau_j) {
+    const bool act = r > j && r < p;
+    if (!act) return;
+    const unsigned qmask = 0xffu << (lane & 24);
+    const T tau = tau_j;
+    const C2<T> lrj = Lm[j * LDL + r];
+    C2<T> w0 = czero<T>(), w1 = czero<T>();
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) {
-      const int jj = q + u * LPR;
-      ch[u] = (live && jj < cw) ? src.get(row, j0 + jj) : czero<T>();
+    for (int u = 0; u < E; u += 2) {
+      w0 = cadd(w0, cmulc(c[u], x[u]));
+      if (u + 1 < E) w1 = cadd(w1, cmulc(c[u + 1], x[u + 1]));
     }
-    __syncthreads();  // L zeroed / previous chunk's last reflector consumed
-    if (row == 0) make_reflector(0, 0);
+    C2<T> w = cadd(w0, w1);
+#pragma unroll
+    for (int o = 1; o < LQT; o <<= 1) {
+      w.re += __shfl_xor_sync(qmask, w.re, o);
+      w.im += __shfl_xor_sync(qmask, w.im, o);
+    }
+    w = cadd(w, cmul(lrj, v0));
+    const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
+#pragma unroll
+    for (int u = 0; u < E; ++u) c[u] = csub(c[u], cmul(tw, x[u]));
+    if (lq == 0) Lm[j * LDL + r] = csub(lrj, cmulc(tw, v0));
+  };
+
+  auto stage = [&](int j0, int cwid, int ncols, C2<T>* dst) {
+    stage_table<T, FROM_R, NT>(src, j0, cwid, cgc, cwt);
+    if (!FROM_R) __syncthreads();
+    stage_cols<T, FROM_R, NT>(src, p, j0, cwid, ncols, dst, LDL, cgc, cwt);
+  };
+
+  // Asynchronous staging of the next chunk while the steps of the current one
+  // run (all but the matrix-free mode, whose entries are computed): the
+  // column table (leaf) at step 0, the entries at step 2 once the table is
+  // visible, the weights and the conjugation of G^* applied after the last
+  // step.  Xs is free during the steps: the chunk is in registers.
+  const bool async_ok = FROM_R || !src.gen;
+  auto issue_table = [&](int j0n, int cwn) {
+    for (int jj = tid; jj < cwn; jj += NT) {
+      if (DH2_IN(src.cmo + j0n + jj, c_lim.ncol[side], 3, pid)) {
+        cp_async<4>(&cgc[jj], src.gcol + j0n + jj);
+        cp_async<sizeof(T)>(&cwt[jj], src.colw + j0n + jj);
+      } else {
+        cgc[jj] = 0;
+        cwt[jj] = T(0);
+      }
+    }
+    cp_async_commit();
+  };
+  const bool down = FROM_R || side == 0;  // consecutive threads on the contiguous direction
+  auto issue_cols = [&](int j0n, int cwn) {
+    for (int e = tid; e < C * p; e += NT) {
+      const int r = down ? e % p : e / C;
+      const int jj = down ? e / p : e % C;
+      C2<T>* d = Xs + jj * LDL + r;
+      const C2<T>* g = nullptr;
+      if (jj < cwn) g = FROM_R ? src.sons_ptr(r, j0n + jj) : src.leaf_ptr(r, cgc[jj]);
+      if (g) cp_async<sizeof(C2<T>)>(d, g);
+      else *d = czero<T>();
+    }
+    cp_async_commit();
+  };
+  auto finish_cols = [&](int cwn) {
+    if (FROM_R) return;
+    for (int e = tid; e < C * p; e += NT) {
+      const int r = down ? e % p : e / C;
+      const int jj = down ? e / p : e % C;
+      if (jj < cwn) {
+        C2<T>* d = Xs + jj * LDL + r;
+        const C2<T> g = *d;
+        const T w = cwt[jj];
+        *d = C2<T>{g.re * w, side == 0 ? g.im * w : -g.im * w};
+      }
+    }
+  };
+
+  {
+    DH2_PROF_T(t_s0);
+    stage(0, min(C, N), C, Xs);
     __syncthreads();
+    DH2_PROF_T(t_s1);
+    DH2_PROF_ADD(8, t_s1 - t_s0);
+  }
+  for (int j0 = 0; j0 < N; j0 += C) {
+    DH2_PROF_ADD(9, 1);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int r = lrow(s);
+#pragma unroll
+      for (int u = 0; u < E; ++u) ch[s][u] = r < p ? Xs[(lq + u * LQT) * LDL + r] : czero<T>();
+    }
+    if (warp == 0) publish(0, ch[0], lrow(0) == 0, 0);
+    __syncthreads();
+    const int j0n = j0 + C;
+    const int cwn = min(C, N - j0n);
+    const bool pre = async_ok && j0n < N;
+    bool issued = false;
     for (int i = 0; i < p; ++i) {
       const int sl = i & 1;
-      if (!sh_skip[sl] && row > i && live) {
-        const C2<T> v0 = sh_v0[sl];
-        const T tau = sh_tau[sl];
-        const C2<T>* xi = vbuf + sl * C;
-        C2<T> w = czero<T>(), w1 = czero<T>();
-        if (q == 0) w = cmul(Lm[i * LDL + row], v0);
+      // a skipped reflection (zero chunk part) is the identity: tau = 0
+      const bool skip = sh_skip[sl] != 0;
+      C2<T> x[E];
 #pragma unroll
-        for (int u = 0; u < CPL; u += 2) {
-          w = cadd(w, cmulc(ch[u], xi[q + u * LPR]));
-          w1 = cadd(w1, cmulc(ch[u + 1], xi[q + (u + 1) * LPR]));
-        }
-        w = cadd(w, w1);
+      for (int u = 0; u < E; ++u) x[u] = vbuf[sl * C + lq + u * LQT];
+      const C2<T> v0 = skip ? czero<T>() : sh_v0[sl];
+      const T tau = skip ? T(0) : sh_tau[sl];
+      const int b1 = (i + 1) >> 2;  // block of row i+1
+      const int cs = i + 1 < p && (b1 % NW) == warp ? b1 / NW : -1;
+      // slots in increasing order: for the owner of row i+1 that row's slot is
+      // its lowest live one, so the next reflection is formed first
 #pragma unroll
-        for (int o = 1; o < LPR; o <<= 1) {
-          w.re += __shfl_xor_sync(gmask, w.re, o);
-          w.im += __shfl_xor_sync(gmask, w.im, o);
-        }
-        const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
-#pragma unroll
-        for (int u = 0; u < CPL; ++u) ch[u] = csub(ch[u], cmul(tw, xi[q + u * LPR]));
-        if (q == 0) Lm[i * LDL + row] = csub(Lm[i * LDL + row], cmulc(tw, v0));
+      for (int s = 0; s < S; ++s) {
+        if (!slot_live(s, i)) continue;
+        apply(ch[s], lrow(s), i, x, v0, tau);
+        if (s == cs) publish(i + 1, ch[s], lrow(s) == i + 1, sl ^ 1);
       }
-      if (row == i + 1 && live) make_reflector(i + 1, (i + 1) & 1);
+      if (pre) {
+        if (FROM_R) {
+          if (i == 0) {
+            issue_cols(j0n, cwn);
+            issued = true;
+          }
+        } else if (i == 0) {
+          issue_table(j0n, cwn);
+        } else if (i == 1) {
+          cp_async_wait_all();  // the table, visible to all after this step's barrier
+        } else if (i == 2) {
+          issue_cols(j0n, cwn);
+          issued = true;
+        }
+      }
       __syncthreads();
+    }
+    if (j0n < N) {
+      DH2_PROF_T(t_s0);
+      cp_async_wait_all();
+      if (issued) {
+        finish_cols(cwn);
+      } else {
+        stage(j0n, cwn, C, Xs);  // short pair or matrix-free mode
+      }
+      __syncthreads();  // next chunk staged
+      DH2_PROF_T(t_s1);
+      DH2_PROF_ADD(8, t_s1 - t_s0);
     }
   }
 
@@ -325,94 +556,84 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
   DH2_PROF_ADD(0, t_b - t_a);
 
   // ---------------------------------------------------------------- 1b. pivoted LQ of L
-  // Rank-revealing step: L = Pi^T L' Omega' by Householder reflections from
-  // the right with row pivoting (largest residual row first).  It stops at the
-  // first K whose remaining block L'(K:, K:) has energy E_K <= drop * eps_l^2;
-  // that energy is added to every tail sum below (an upper bound on the
-  // residual of the chosen subspace), and the Jacobi step works on the K
-  // leading columns only.  Pi is kept in perm[].
+  // Rank-revealing step: L Omega' = L' by Householder reflections from the
+  // right with row pivoting (the row of largest residual norm first).  Rows
+  // stay in place: pcol[r] records the step at which row r was chosen (-1
+  // while it has not been), so L' is lower triangular up to a row
+  // permutation.  The step stops at the first K whose remaining rows have
+  // residual energy E_K <= drop * eps_l^2 over columns K..p-1; that energy is
+  // added to every tail sum below (an upper bound on the residual of the
+  // chosen subspace), and the Jacobi step works on the K leading columns only.
+  // Two barriers per step: the pivot search is repeated by every warp on the
+  // shared residual norms, so it needs none of its own.
   const double drop = sizeof(T) == 4 ? 1e-2 : 1e-10;
-  const double tau_drop = drop * a.eps2[lvl];
-  for (int r = tid; r < P; r += NT) perm[r] = r;
+  const T tau_drop_t = (T)(drop * a.eps2[lvl]);
+  // (shuffles run converged over whole warps with the full mask; the row
+  // predicates only gate the memory accesses)
+  {
+    T s = T(0);
+    if (live)
+      for (int c = q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + row]);
+#pragma unroll
+    for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (live && q == 0) {
+      nu[row] = s;
+      pcol[row] = -1;
+    }
+  }
+  __syncthreads();
   int K = p;
   double E_K = 0.0;
   for (int i = 0; i < p; ++i) {
-    // residual row norms over columns i..p-1 (row i-1 becomes final: zero its tail)
-    if (i > 0 && row == i - 1)
-      for (int c = i + q; c < p; c += LPR) Lm[c * LDL + row] = czero<T>();
-    if (row >= i && live) {
-      T s = T(0);
-      for (int c = i + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + row]);
-#pragma unroll
-      for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
-      if (q == 0) nu[row] = s;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double e = 0.0;
-      T best = T(-1);
-      int bi = i;
-      for (int r = i + lane; r < p; r += 32) {
+    // residual energy of the unchosen rows and the pivot (lowest row on ties);
+    // the butterfly leaves the same values in every lane of every warp
+    T e = T(0);
+    T best = T(-1);
+    int pv = p;
+    for (int r = lane; r < p; r += 32) {
+      if (pcol[r] < 0) {
         const T v = nu[r];
-        e += (double)v;
+        e += v;
         if (v > best) {
           best = v;
-          bi = r;
+          pv = r;
         }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        e += __shfl_xor_sync(0xffffffffu, e, o);
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (lane == 0) {
-        sh_E = e;
-        sh_piv = bi;
       }
     }
-    __syncthreads();
-    if (sh_E <= tau_drop) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, pv, o);
+      if (ob > best || (ob == best && oi < pv)) {
+        best = ob;
+        pv = oi;
+      }
+    }
+    if (e <= tau_drop_t || pv >= p) {
       K = i;
-      E_K = sh_E;
+      E_K = (double)e;
       break;
     }
-    const int pv = sh_piv;
-    if (pv != i) {
-      for (int c = tid; c < p; c += NT) {
-        const C2<T> t0 = Lm[c * LDL + i];
-        Lm[c * LDL + i] = Lm[c * LDL + pv];
-        Lm[c * LDL + pv] = t0;
-      }
-      if (tid == 0) {
-        const int t1 = perm[i];
-        perm[i] = perm[pv];
-        perm[pv] = t1;
-      }
-    }
-    __syncthreads();
-    if (row == i) {
-      // reflector of row i over columns i..p-1
+    if (warp == pv / (32 / LPR)) {
+      // reflector of row pv over columns i..p-1: the row becomes beta e_i
       T s = T(0);
-      for (int c = i + 1 + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + i]);
+      if (row == pv)
+        for (int c = i + 1 + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + pv]);
 #pragma unroll
-      for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(gmask, s, o);
-      if (q == 0) {
+      for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (row == pv && q == 0) {
         if (!(s > Eps<T>::tiny)) {
           sh_skip[0] = 1;
         } else {
-          const C2<T> al = Lm[i * LDL + i];
+          const C2<T> al = Lm[i * LDL + pv];
           const T an2 = cnorm2(al);
           const T ra = an2 > Eps<T>::tiny ? frsqrt(an2) : T(0);
           const T an = an2 * ra;
           const T xn2 = s + an2;
           const T xn = xn2 * frsqrt(xn2);
           const C2<T> ph = an2 > Eps<T>::tiny ? C2<T>{al.re * ra, al.im * ra} : C2<T>{T(1), T(0)};
-          Lm[i * LDL + i] = C2<T>{-ph.re * xn, -ph.im * xn};
+          Lm[i * LDL + pv] = C2<T>{-ph.re * xn, -ph.im * xn};
           sh_v0[0] = C2<T>{ph.re * (an + xn), -ph.im * (an + xn)};
           sh_tau[0] = fdiv(T(1), xn * (xn + an));
           sh_skip[0] = 0;
@@ -420,38 +641,71 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
       }
     }
     __syncthreads();
-    if (!sh_skip[0] && row > i && live) {
-      const C2<T> v0 = sh_v0[0];
-      const T tau = sh_tau[0];
+    // apply to the unchosen rows and refresh their residual norms (columns > i);
+    // pcol[pv] is set only here, after every warp's pivot search has read it
+    if (row == pv && q == 0) pcol[pv] = i;
+    if (warp * (32 / LPR) < p) {  // warps holding rows
+      const bool act = live && row != pv && pcol[row] < 0;
+      const bool skip = sh_skip[0] != 0;
+      T s = T(0);
       C2<T> w = czero<T>();
-      if (q == 0) w = cmul(Lm[i * LDL + row], v0);
-      for (int c = i + 1 + q; c < p; c += LPR) w = cadd(w, cmulc(Lm[c * LDL + row], Lm[c * LDL + i]));
-#pragma unroll
-      for (int o = 1; o < LPR; o <<= 1) {
-        w.re += __shfl_xor_sync(gmask, w.re, o);
-        w.im += __shfl_xor_sync(gmask, w.im, o);
+      if (act && !skip) {
+        if (q == 0) w = cmul(Lm[i * LDL + row], sh_v0[0]);
+        for (int c = i + 1 + q; c < p; c += LPR) w = cadd(w, cmulc(Lm[c * LDL + row], Lm[c * LDL + pv]));
       }
-      const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
-      for (int c = i + 1 + q; c < p; c += LPR)
-        Lm[c * LDL + row] = csub(Lm[c * LDL + row], cmul(tw, Lm[c * LDL + i]));
-      if (q == 0) Lm[i * LDL + row] = csub(Lm[i * LDL + row], cmulc(tw, v0));
+      if (!skip) {
+#pragma unroll
+        for (int o = 1; o < LPR; o <<= 1) {
+          w.re += __shfl_xor_sync(0xffffffffu, w.re, o);
+          w.im += __shfl_xor_sync(0xffffffffu, w.im, o);
+        }
+      }
+      if (act) {
+        if (!skip) {
+          const C2<T> v0 = sh_v0[0];
+          const T tau = sh_tau[0];
+          const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
+          for (int c = i + 1 + q; c < p; c += LPR) {
+            const C2<T> x = csub(Lm[c * LDL + row], cmul(tw, Lm[c * LDL + pv]));
+            Lm[c * LDL + row] = x;
+            s += cnorm2(x);
+          }
+          if (q == 0) Lm[i * LDL + row] = csub(Lm[i * LDL + row], cmulc(tw, v0));
+        } else {
+          for (int c = i + 1 + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + row]);
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (act && q == 0) nu[row] = s;
     }
     __syncthreads();
   }
-  // the last processed row keeps its (already applied) tail: zero it; with K
-  // odd, column K holds residual entries and is cleared for the pairing
-  if (K > 0 && row == K - 1)
-    for (int c = K + q; c < p; c += LPR) Lm[c * LDL + row] = czero<T>();
-  __syncthreads();
-  if ((K & 1) && K < P)
-    for (int r = tid; r < p; r += NT) Lm[K * LDL + r] = czero<T>();
+  if (!(E_K >= 0.0 && E_K <= 1.0e300)) {  // only from non-finite input
+    if (tid == 0) atomicOr(a.status, kStatusNaN);
+    E_K = 0.0;
+  }
+  // chosen rows keep their reflector vectors right of their pivot column and
+  // unchosen rows their residual right of column K: clear what the Jacobi step
+  // reads (columns < pe, pe = K rounded up to even)
+  {
+    const int pe0 = K + (K & 1);
+    if (live) {
+      const int from = pcol[row] >= 0 ? pcol[row] + 1 : K;
+      for (int c = from + q; c < pe0; c += LPR) Lm[c * LDL + row] = czero<T>();
+    }
+  }
   __syncthreads();
   // ---------------------------------------------------------------- 2. Jacobi
-  // one column pair per group of 8 threads; round-robin ordering over pe columns
+  // one column pair per group of tpp threads (as many as the pe/2 pairs of a
+  // round allow, 4..32); round-robin ordering over pe columns
   const int pe = K + (K & 1);
   const T tol = T(p) * Eps<T>::u;
-  const int grp = tid >> 3, gl = tid & 7;
-  const unsigned m8 = 0xffu << (lane & 24);
+  constexpr int JH = (P_T / 2 + NT / 4 - 1) / (NT / 4);  // pairs per group at most
+  int tpp = DH2_JACOBI_TPP;
+  while (tpp > 4 && tpp * (pe / 2) > NT) tpp >>= 1;
+  const int jng = NT / tpp;
+  const int jg = tid / tpp, jl = tid & (tpp - 1);
   if (tid == 0) {
     sh_rot[0] = 0;
     sh_rot[1] = 0;
@@ -464,38 +718,40 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
     const int sp = sweep & 1;
     // round-robin positions of this group's pairs in round 0; each round
     // moves every position but the fixed one (index 0) by one place
-    int ia[P_T / 64], ib[P_T / 64];
+    int ia[JH], ib[JH];
 #pragma unroll
-    for (int h = 0; h < P_T / 64; ++h) {
-      const int kk = grp + h * (NT / 8);
+    for (int h = 0; h < JH; ++h) {
+      const int kk = jg + h * jng;
       ia[h] = kk;
       ib[h] = pe - 1 - kk;
     }
     for (int rd = 0; rd < pe - 1; ++rd) {
 #pragma unroll
-      for (int h = 0; h < P_T / 64; ++h) {
-        const int kk = grp + h * (NT / 8);
-        if (kk < pe / 2) {
-          C2<T>* ca = Lm + ia[h] * LDL;
-          C2<T>* cb = Lm + ib[h] * LDL;
+      for (int h = 0; h < JH; ++h) {
+        const int kk = jg + h * jng;
+        // warps with an active group run the reductions converged (full mask)
+        if ((warp * 32) / tpp + h * jng < pe / 2) {
+          const bool act = kk < pe / 2;
+          C2<T>* ca = Lm + (act ? ia[h] : 0) * LDL;
+          C2<T>* cb = Lm + (act ? ib[h] : 0) * LDL;
           T al = T(0), be = T(0);
           C2<T> ga = czero<T>();
-          for (int r = gl; r < p; r += 8) {
-            const C2<T> xa = ca[r], xb = cb[r];
-            al += cnorm2(xa);
-            be += cnorm2(xb);
-            ga = cadd(ga, cmulc(xb, xa));  // conj(xa) * xb
-          }
-#pragma unroll
-          for (int o = 1; o < 8; o <<= 1) {
-            al += __shfl_xor_sync(m8, al, o);
-            be += __shfl_xor_sync(m8, be, o);
-            ga.re += __shfl_xor_sync(m8, ga.re, o);
-            ga.im += __shfl_xor_sync(m8, ga.im, o);
+          if (act)
+            for (int r = jl; r < p; r += tpp) {
+              const C2<T> xa = ca[r], xb = cb[r];
+              al += cnorm2(xa);
+              be += cnorm2(xb);
+              ga = cadd(ga, cmulc(xb, xa));  // conj(xa) * xb
+            }
+          for (int o = 1; o < tpp; o <<= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
+            ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
           }
           const T g2 = cnorm2(ga);
           // rotate unless the pair is orthogonal to tol (relative)
-          if (al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
+          if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
               sqrt(g2) * frsqrt(al) * frsqrt(be) > tol) {
             const T rg = frsqrt(g2);
             const T zt = (be - al) * T(0.5) * rg;
@@ -504,17 +760,19 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
             const T s = t * c;
             if (s != T(0)) {
               const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
-              for (int r = gl; r < p; r += 8) {
+              for (int r = jl; r < p; r += tpp) {
                 const C2<T> xa = ca[r];
                 const C2<T> eb = cmul(e, cb[r]);
                 ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
                 cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
               }
-              if (gl == 0) sh_rot[sp] = 1;
+              if (jl == 0) sh_rot[sp] = 1;
             }
           }
-          if (kk > 0) ia[h] = ia[h] == pe - 1 ? 1 : ia[h] + 1;
-          ib[h] = ib[h] == pe - 1 ? 1 : ib[h] + 1;
+          if (act) {
+            if (kk > 0) ia[h] = ia[h] == pe - 1 ? 1 : ia[h] + 1;
+            ib[h] = ib[h] == pe - 1 ? 1 : ib[h] + 1;
+          }
         }
       }
       __syncthreads();
@@ -537,15 +795,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
   (void)nsweeps;
 
   // ---------------------------------------------------------------- 3. rank
-  for (int j = grp; j < K; j += NT / 8) {
-    double s = 0.0;
-    for (int r = gl; r < p; r += 8) {
-      const C2<T> x = Lm[j * LDL + r];
-      s += (double)x.re * (double)x.re + (double)x.im * (double)x.im;
-    }
+  const int grp = tid >> 3, gl = tid & 7;
+  for (int jb = 0; jb < K; jb += NT / 8) {
+    const int j = jb + grp;
+    T s = T(0);
+    if (j < K)
+      for (int r = gl; r < p; r += 8) s += cnorm2(Lm[j * LDL + r]);
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(m8, s, o);
-    if (gl == 0) sig2[j] = s;
+    for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (j < K && gl == 0) sig2[j] = (double)s;
   }
   __syncthreads();
   // non-finite values (only from non-finite input) are ranked as zero and
@@ -600,63 +858,138 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? DH2_PAIR_MINB : 1)
   const int ldq = a.rowcap[side][pid];
   for (int qq = grp; qq < k; qq += NT / 8) {
     const int j = ord[qq];
-    const T inv = (T)(1.0 / sqrt(sig2[j]));
+    const T inv = frsqrt((T)sig2[j]);
     for (int r = gl; r < p; r += 8) {
       const C2<T> v = Lm[j * LDL + r];
-      const int ro = perm[r];
-      if (DH2_IN(a.Qoff[side][pid] + ro + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
-        Qout[ro + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
+      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
+        Qout[r + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
     }
   }
-  if (k == 0) return;
-  __syncthreads();
-  // compact Q into L columns 0..k-1 (re-read from global, visible after the barrier)
-  for (int idx = tid; idx < p * k; idx += NT) {
-    const int r = idx % p, qq = idx / p;
-    Lm[qq * LDL + r] = Qout[r + (int64_t)qq * ldq];
-  }
-  __syncthreads();
-
   DH2_PROF_T(t_d);
   DH2_PROF_ADD(2, t_d - t_c);
-  // ---------------------------------------------------------------- 5. R = Q^* A
-  C2<T>* Rout = a.R[side] + a.Roff[side][pid];
-  const int CR = min(64, (P + XTRA - k)) & ~7;  // staged columns after Q
-  C2<T>* Ast = Lm + (int64_t)k * LDL;
-  for (int j0 = 0; j0 < N; j0 += CR) {
-    const int cw = min(CR, N - j0);
-    if (FROM_R || side == 0) {
-      for (int jj = warp; jj < cw; jj += NT / 32)
-        for (int r = lane; r < p; r += 32) Ast[jj * LDL + r] = src.get(r, j0 + jj);
-    } else {
-      for (int r = warp; r < p; r += NT / 32)
-        for (int jj = lane; jj < cw; jj += 32) Ast[jj * LDL + r] = src.get(r, j0 + jj);
-    }
-    __syncthreads();
-    for (int idx = tid; idx < k * cw; idx += NT) {
-      const int qq = idx % k, jj = idx / k;
-      const C2<T>* qc = Lm + qq * LDL;
-      const C2<T>* ac = Ast + jj * LDL;
-      C2<T> acc = czero<T>();
-      for (int r = 0; r < p; ++r) acc = cadd(acc, cmulc(ac[r], qc[r]));
-      if (DH2_IN(a.Roff[side][pid] + qq + (int64_t)(j0 + jj) * kcap, c_lim.R[side], 11, pid))
-        Rout[qq + (int64_t)(j0 + jj) * kcap] = acc;
-    }
-    __syncthreads();
-  }
-  DH2_PROF_T(t_e);
-  DH2_PROF_ADD(3, t_e - t_d);
 }
 
-template <typename T, int P_T, bool FROM_R>
+// R_tc = Q^* A for the pairs of one launch (Section 6, R recursion: R_tc =
+// V_tc^* G_tc for a leaf, [E_t1c; E_t2c]^* Ghat_tc for a non-leaf), after
+// pair_kernel has written Q and the rank.  One CTA per pair: A is streamed in
+// tiles of TW columns through shared memory and Q is held in blocks of QB
+// columns; each thread forms 2 x 2 output tiles.  A second read of A, but
+// with no serial chain: the loads of many pairs are in flight at once.
+template <typename T, bool FROM_R>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
+    rq_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
+  constexpr int NT = 256;
+  constexpr int QB = 32;
+  constexpr int TW = sizeof(T) == 4 ? 64 : 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int cgc[TW];
+  __shared__ T cwt[TW];
+  const int LD = P + 1;
+  C2<T>* Qs = reinterpret_cast<C2<T>*>(smem);  // QB columns of Q
+  C2<T>* As = Qs + QB * LD;                    // TW columns of A
+  const int tid = threadIdx.x;
+  const uint32_t code = codes[blockIdx.x];
+  const int prob = (int)(code >> kCodeProbShift);
+  const int side = (int)((code >> kCodeSideShift) & 1u);
+  const int pid = (int)(code & kCodePairMask);
+  const PairArgs<T>& a = args[prob];
+  if (!DH2_IN(pid, c_lim.npairs[side], 9, pid)) return;
+  const int N = a.ncols[side][pid];
+  const int k = a.rank[side][pid];
+  if (k <= 0 || N == 0) return;
+  Source<T, FROM_R> src;
+  src.side = side;
+  src.pid = pid;
+  int p = 0;
+  if (FROM_R) {
+    const int s0 = a.son[side][2 * pid], s1 = a.son[side][2 * pid + 1];
+    if (!DH2_IN(s0, c_lim.npairs[side], 12, pid) || !DH2_IN(s1, c_lim.npairs[side], 13, pid)) return;
+    src.k1 = a.rank[side][s0];
+    p = src.k1 + a.rank[side][s1];
+    src.off0 = a.sonoff[side][2 * pid];
+    src.off1 = a.sonoff[side][2 * pid + 1];
+    src.ld0 = a.kcap[side][s0];
+    src.ld1 = a.kcap[side][s1];
+    src.roff0 = a.Roff[side][s0];
+    src.roff1 = a.Roff[side][s1];
+    src.R0 = a.R[side] + src.roff0;
+    src.R1 = a.R[side] + src.roff1;
+  } else {
+    p = a.m[side][pid];
+    src.r0 = a.start[side][pid];
+    src.cmo = a.cmoff[side][pid];
+    src.gcol = a.gcol[side] + src.cmo;
+    src.colw = a.colw[side] + src.cmo;
+    src.G = a.G;
+    src.ld = a.ld;
+    src.pts = a.pts;
+    src.kappa = a.kappa;
+    src.diag = a.diag;
+    src.gen = a.gen;
+  }
+  if (p <= 0 || p > P) return;  // reported by pair_kernel
+  const C2<T>* Qin = a.Q[side] + a.Qoff[side][pid];
+  const int ldq = a.rowcap[side][pid];
+  C2<T>* Rout = a.R[side] + a.Roff[side][pid];
+  const int kcap = a.kcap[side][pid];
+  for (int qb = 0; qb < k; qb += QB) {
+    const int kb = min(QB, k - qb);
+    __syncthreads();  // the previous block's products are done with Qs
+    for (int idx = tid; idx < p * kb; idx += NT) {
+      const int r = idx % p, qq = idx / p;
+      const int64_t e = r + (int64_t)(qb + qq) * ldq;
+      Qs[qq * LD + r] = DH2_IN(a.Qoff[side][pid] + e, c_lim.Q[side], 14, pid) ? Qin[e] : czero<T>();
+    }
+    for (int j0 = 0; j0 < N; j0 += TW) {
+      const int cw = min(TW, N - j0);
+      stage_table<T, FROM_R, NT>(src, j0, cw, cgc, cwt);
+      __syncthreads();  // table and Qs ready; the previous tile's products done with As
+      stage_cols<T, FROM_R, NT>(src, p, j0, cw, cw, As, LD, cgc, cwt);
+      __syncthreads();
+      // 2 x 2 output tiles (columns past kb or cw are read from a clamped
+      // pointer and not stored)
+      const int nqt = (kb + 1) >> 1, njt = (cw + 1) >> 1;
+      for (int t = tid; t < nqt * njt; t += NT) {
+        const int q0 = 2 * (t % nqt), jb = 2 * (t / nqt);
+        const C2<T>* qc0 = Qs + q0 * LD;
+        const C2<T>* qc1 = q0 + 1 < kb ? qc0 + LD : qc0;
+        const C2<T>* ac0 = As + jb * LD;
+        const C2<T>* ac1 = jb + 1 < cw ? ac0 + LD : ac0;
+        C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
+        for (int r = 0; r < p; ++r) {
+          const C2<T> x0 = qc0[r], x1 = qc1[r], y0 = ac0[r], y1 = ac1[r];
+          c00 = cadd(c00, cmulc(y0, x0));
+          c01 = cadd(c01, cmulc(y1, x0));
+          c10 = cadd(c10, cmulc(y0, x1));
+          c11 = cadd(c11, cmulc(y1, x1));
+        }
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+          const int qq = q0 + (d >> 1), jj = jb + (d & 1);
+          const C2<T> v = d == 0 ? c00 : d == 1 ? c01 : d == 2 ? c10 : c11;
+          const int64_t e = (qb + qq) + (int64_t)(j0 + jj) * kcap;
+          if (qq < kb && jj < cw && DH2_IN(a.Roff[side][pid] + e, c_lim.R[side], 11, pid)) Rout[e] = v;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int P_T, bool FROM_R, int NT>
 void launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
-  constexpr int C = P_T == 64 ? DH2_LEAF_CHUNK : 32;
+  constexpr int C = 16 * (NT / P_T);
   const int LDL = P + 1;
-  size_t smem = (((size_t)(P + 16) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
+  size_t smem = (((size_t)(P + C) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
                 (size_t)P * sizeof(double) + 2 * (size_t)P * sizeof(int) + (size_t)P * sizeof(T);
-  auto kern = pair_kernel<T, P_T, FROM_R>;
+  auto kern = pair_kernel<T, P_T, FROM_R, NT>;
+#ifdef DH2_PROFILE
+  // DH2_PROFILE_SOLO=1: one CTA per SM, so the phase counters show latency
+  // without the contention of co-resident pairs
+  if (const char* solo = getenv("DH2_PROFILE_SOLO"))
+    if (solo[0] == '1' && smem < 120 * 1024) smem = 120 * 1024;
+#endif
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<nblocks, 256, smem, st>>>(args, codes, P);
+  kern<<<nblocks, NT, smem, st>>>(args, codes, P);
 }
 
 }  // namespace
@@ -683,31 +1016,50 @@ bool check_read_pair(CheckRecord* out) {
 
 void prof_reset_pair() {
 #ifdef DH2_PROFILE
-  unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long z[10] = {};
   cudaMemcpyToSymbol(g_prof, z, sizeof(z));
 #endif
 }
 
-bool prof_read_pair(unsigned long long* out8) {
+bool prof_read_pair(unsigned long long* out10) {
 #ifdef DH2_PROFILE
-  cudaMemcpyFromSymbol(out8, g_prof, 8 * sizeof(unsigned long long));
+  cudaMemcpyFromSymbol(out10, g_prof, 10 * sizeof(unsigned long long));
   return true;
 #else
-  (void)out8;
+  (void)out10;
   return false;
 #endif
 }
+
+template <typename T, bool FROM_R>
+void launch_rq(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
+  constexpr int TW = sizeof(T) == 4 ? 64 : 32;
+  const size_t smem = (size_t)(32 + TW) * (P + 1) * sizeof(C2<T>);
+  auto kern = rq_kernel<T, FROM_R>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kern<<<nblocks, 256, smem, st>>>(args, codes, P);
+}
+
+template <typename T>
+void launch_rq_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
+                      cudaStream_t st) {
+  if (nblocks <= 0) return;
+  if (from_r) launch_rq<T, true>(args, codes, nblocks, P, st);
+  else launch_rq<T, false>(args, codes, nblocks, P, st);
+}
+template void launch_rq_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t);
+template void launch_rq_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t);
 
 template <typename T>
 void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
                         cudaStream_t st) {
   if (nblocks <= 0) return;
   if (!from_r) {
-    if (P <= 64) launch_one<T, 64, false>(args, codes, nblocks, P, st);
-    else launch_one<T, 128, false>(args, codes, nblocks, P, st);
+    if (P <= 64) launch_one<T, 64, false, DH2_LEAF_NT>(args, codes, nblocks, P, st);
+    else launch_one<T, 128, false, 256>(args, codes, nblocks, P, st);
   } else {
-    if (P <= 64) launch_one<T, 64, true>(args, codes, nblocks, P, st);
-    else launch_one<T, 128, true>(args, codes, nblocks, P, st);
+    if (P <= 64) launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
+    else launch_one<T, 128, true, 256>(args, codes, nblocks, P, st);
   }
 }
 
