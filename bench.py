@@ -256,6 +256,7 @@ def run_gpu(args):
         Gh.copy_(Gd.t(), non_blocking=False)
         Gdev = torch.empty_like(Gh, device=dev)
         rk_h = [torch.empty(len(r), dtype=torch.int32, pin_memory=True) for r in ranks]
+        h2d_ev = []
         Me = None
         for it in range(args.warmup + args.steps):
             if it == args.warmup:
@@ -263,7 +264,13 @@ def run_gpu(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
+            if it >= args.warmup:
+                eh = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                eh[0].record(stream)
             Gdev.copy_(Gh, non_blocking=True)
+            if it >= args.warmup:
+                eh[1].record(stream)
+                h2d_ev.append(eh)
             Me = D.dh2_compress(T, Gdev.t(), eps=args.eps, mode=mode, nearfield=args.nearfield)
             for sd in (0, 1):
                 rk_h[sd].numpy()[:] = Me.ranks(sd)
@@ -271,9 +278,11 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1) / args.steps
+        h2d_ms = sum(a.elapsed_time(b) for a, b in h2d_ev) / len(h2d_ev)
         d2h = sum(4 * len(r) for r in ranks)
         e2e = {"value": in_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
-               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h,
+               "h2d_ms": h2d_ms, "h2d_gbs": in_bytes / (h2d_ms * 1e-3) / 1e9}
         del Gh, Gdev
     peaks, src = _peaks()
     adm_bytes = elem * st.adm_fraction * args.n * args.n

@@ -50,6 +50,8 @@ struct Tree::Dev {
   int32_t *own_blk, *par_pair, *par_son;
   // launch orders: leaf launch (both sides) then non-leaf per level
   uint32_t* codes;
+  // R tiles in the same order: code << 32 | first column, 32 columns each
+  int64_t* tiles;
   // host-side sizes
   int64_t npairs[2] = {0, 0}, nleaf[2] = {0, 0};
   int64_t R_elems[2] = {0, 0}, Q_elems[2] = {0, 0}, X_elems[2] = {0, 0}, h_elems[2] = {0, 0};
@@ -57,6 +59,8 @@ struct Tree::Dev {
   int64_t nadm = 0, ninadm = 0;
   int64_t nleaf_codes = 0;
   std::vector<int64_t> nl_code_begin, nl_code_count;    // per level
+  int64_t nleaf_tiles = 0;
+  std::vector<int64_t> nl_tile_begin, nl_tile_count;    // per level
   std::vector<int32_t> nl_rowcap_max;                   // per level
   std::vector<int64_t> lvl_begin[2], lvl_nl_begin[2], lvl_end[2];
   int32_t max_leaf = 0;
@@ -317,7 +321,25 @@ dh2_status upload_tree(Tree& tr) {
         }
       D->nl_code_count[l] = (int64_t)codes.size() - D->nl_code_begin[l];
     }
+    // R tiles of 32 columns per pair, in the order of the codes
+    std::vector<int64_t> tiles;
+    auto add_tiles = [&](int32_t code) {
+      const int sd = (code >> kCodeSideShift) & 1;
+      const int64_t p = code & (int32_t)kCodePairMask;
+      const int64_t nc = tr.side[sd].pairs[p].ncols;
+      for (int64_t j0 = 0; j0 < nc; j0 += kRTile) tiles.push_back((int64_t)(((uint64_t)(uint32_t)code << 32) | (uint64_t)j0));
+    };
+    for (int64_t i = 0; i < D->nleaf_codes; ++i) add_tiles(codes[i]);
+    D->nleaf_tiles = (int64_t)tiles.size();
+    D->nl_tile_begin.assign(tr.depth + 1, 0);
+    D->nl_tile_count.assign(tr.depth + 1, 0);
+    for (int l = tr.depth; l >= 0; --l) {
+      D->nl_tile_begin[l] = (int64_t)tiles.size();
+      for (int64_t i = 0; i < D->nl_code_count[l]; ++i) add_tiles(codes[D->nl_code_begin[l] + i]);
+      D->nl_tile_count[l] = (int64_t)tiles.size() - D->nl_tile_begin[l];
+    }
     add32(std::move(codes), (int32_t**)&D->codes);
+    add64(std::move(tiles), &D->tiles);
   }
   size_t total = 0;
   for (auto& b : bufs) total += align256(std::max<size_t>(b.bytes, 4));
@@ -483,6 +505,13 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   std::vector<const uint32_t*> d_nl(maxdepth + 1, nullptr);
   std::vector<int64_t> n_nl(maxdepth + 1, 0);
   int64_t n_leaf = 0, n_norm = 0;
+  // R tiles (code << 32 | first column) in the order of the codes
+  const uint64_t* d_ltiles = nullptr;
+  std::vector<const uint64_t*> d_nltiles(maxdepth + 1, nullptr);
+  std::vector<int64_t> n_nltiles(maxdepth + 1, 0);
+  int64_t n_ltiles = 0;
+  std::vector<uint64_t> leaf_tiles;
+  std::vector<std::vector<uint64_t>> nl_tiles(maxdepth + 1);
   size_t args_bytes = align256(sizeof(PairArgs<T>) * nprob) + align256(sizeof(NormsArgs<T>) * nprob);
   size_t codes_bytes = 0;
   if (nprob > 1) {
@@ -504,8 +533,18 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     std::stable_sort(lc.begin(), lc.end(), [](const std::pair<double, uint32_t>& a,
                                               const std::pair<double, uint32_t>& b) { return a.first < b.first; });
     for (auto& x : lc) leaf_codes.push_back(x.second);
-    codes_bytes = align256(4 * leaf_codes.size()) + align256(4 * norm_codes.size());
-    for (int l = 0; l <= maxdepth; ++l) codes_bytes += align256(4 * nl_codes[l].size());
+    auto tiles_of = [&](const std::vector<uint32_t>& codes, std::vector<uint64_t>& out) {
+      for (uint32_t c : codes) {
+        const Tree& tr = Ms[c >> kCodeProbShift]->tree->tr;
+        const int64_t nc = tr.side[(c >> kCodeSideShift) & 1u].pairs[c & kCodePairMask].ncols;
+        for (int64_t j0 = 0; j0 < nc; j0 += kRTile) out.push_back(((uint64_t)c << 32) | (uint64_t)j0);
+      }
+    };
+    tiles_of(leaf_codes, leaf_tiles);
+    for (int l = 0; l <= maxdepth; ++l) tiles_of(nl_codes[l], nl_tiles[l]);
+    codes_bytes = align256(4 * leaf_codes.size()) + align256(4 * norm_codes.size()) + align256(8 * leaf_tiles.size());
+    for (int l = 0; l <= maxdepth; ++l)
+      codes_bytes += align256(4 * nl_codes[l].size()) + align256(8 * nl_tiles[l].size());
   }
   void* scratch = nullptr;
   DH2_CUDA_TRY(cudaMallocAsync(&scratch, args_bytes + codes_bytes + 256, st));
@@ -532,6 +571,18 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       d_nl[l] = up(nl_codes[l]);
       n_nl[l] = (int64_t)nl_codes[l].size();
     }
+    auto up64 = [&](const std::vector<uint64_t>& v) -> const uint64_t* {
+      uint64_t* d = (uint64_t*)sp;
+      if (!v.empty() && ce == cudaSuccess) ce = cudaMemcpyAsync(d, v.data(), 8 * v.size(), cudaMemcpyHostToDevice, st);
+      sp += align256(8 * v.size());
+      return d;
+    };
+    d_ltiles = up64(leaf_tiles);
+    n_ltiles = (int64_t)leaf_tiles.size();
+    for (int l = 0; l <= maxdepth; ++l) {
+      d_nltiles[l] = up64(nl_tiles[l]);
+      n_nltiles[l] = (int64_t)nl_tiles[l].size();
+    }
   } else {
     const Tree& tr = Ms[0]->tree->tr;
     const Tree::Dev* D = tr.dev;
@@ -542,6 +593,12 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int l = 0; l <= tr.depth; ++l) {
       d_nl[l] = D->codes + D->nl_code_begin[l];
       n_nl[l] = D->nl_code_count[l];
+    }
+    d_ltiles = (const uint64_t*)D->tiles;
+    n_ltiles = D->nleaf_tiles;
+    for (int l = 0; l <= tr.depth; ++l) {
+      d_nltiles[l] = (const uint64_t*)D->tiles + D->nl_tile_begin[l];
+      n_nltiles[l] = D->nl_tile_count[l];
     }
   }
   if (ce != cudaSuccess) {
@@ -586,18 +643,20 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #endif
   launch_pair_kernel<T>(d_pa, d_leaf, (int)n_leaf, P_leaf, false, st);
   cudaEventRecord(ev[2], st);
-  launch_rq_kernel<T>(d_pa, d_leaf, (int)n_leaf, P_leaf, false, st);
+  launch_rq_kernel<T>(d_pa, d_ltiles, (int)n_ltiles, P_leaf, false, st);
 #ifdef DH2_PROFILE
   {
     cudaStreamSynchronize(st);
-    unsigned long long pr[10];
+    unsigned long long pr[14];
     prof_read_pair(pr);
     const double np = pr[5] ? (double)pr[5] : 1.0;
+    const double ns = pr[12] ? (double)pr[12] : 1.0;
     std::fprintf(stderr,
                  "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean K %.1f, mean sweeps %.2f, mean chunks %.2f, "
-                 "cycles/pair: LQ %.0f (staging %.0f) Jacobi %.0f rank+Q %.0f\n",
+                 "cycles/pair: LQ %.0f (staging %.0f) Jacobi %.0f rank+Q %.0f; LQ steps %.1f/pair, cycles/step %.0f, "
+                 "per warp-step busy %.0f, critical warp busy %.0f, to reflection %.0f\n",
                  pr[5], pr[6] / np, pr[7] / np, pr[4] / np, pr[9] / np, pr[0] / np, pr[8] / np, pr[1] / np,
-                 pr[2] / np);
+                 pr[2] / np, ns / np, (pr[0] - pr[8]) / ns, pr[11] / (8.0 * ns), pr[10] / ns, pr[13] / ns);
   }
 #endif
   DH2_PHASE_SYNC("leaf pairs");
@@ -605,7 +664,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   for (int l = maxdepth; l >= 0; --l) {
     if (n_nl[l] == 0) continue;
     launch_pair_kernel<T>(d_pa, d_nl[l], (int)n_nl[l], P_level[l], true, st);
-    launch_rq_kernel<T>(d_pa, d_nl[l], (int)n_nl[l], P_level[l], true, st);
+    launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, st);
     DH2_PHASE_SYNC("non-leaf pairs");
   }
   cudaEventRecord(ev[4], st);

@@ -27,6 +27,7 @@ constexpr int kCodeSideShift = 25;
 constexpr int kCodeProbShift = 26;
 constexpr uint32_t kCodePairMask = (1u << 25) - 1u;
 constexpr int kMaxBatch = 64;
+constexpr int kRTile = 32;  // columns per tile of the R = Q^* A kernel
 
 // Device status bits (OR-ed by kernels into one word).
 constexpr uint32_t kStatusNoConv = 1u;

@@ -80,14 +80,15 @@ template <typename T>
 void launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
                         cudaStream_t st);
 
-// R = Q^* A for the same launch codes, after launch_pair_kernel (one CTA per
-// pair; P as for the pair kernel).
+// R = Q^* A for the pairs of a pair-kernel launch, after it: one CTA per tile
+// of 32 columns, tiles[i] = launch code << 32 | first column (P as for the
+// pair kernel).
 template <typename T>
-void launch_rq_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
+void launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int ntiles, int P, bool from_r,
                       cudaStream_t st);
 
-// Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 10 values.
+// Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 14 values.
 void prof_reset_pair();
-bool prof_read_pair(unsigned long long* out10);
+bool prof_read_pair(unsigned long long* out14);
 
 }  // namespace dh2

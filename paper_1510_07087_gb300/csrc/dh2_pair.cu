@@ -37,14 +37,18 @@ DH2_CHECK_DECLS
 
 #ifdef DH2_PROFILE
 // summed over CTAs: cycles of LQ, Jacobi, rank+Q, R; sweeps; pairs; p; K;
-// cycles of the LQ staging; chunks
-__device__ unsigned long long g_prof[10];
+// cycles of the LQ staging; chunks; LQ steps; cycles from a step's start to
+// the end of its own work, summed over the warps (10: the warp forming the
+// next reflection, 11: all warps), and cycles to the formed reflection (13)
+__device__ unsigned long long g_prof[14];
 #define DH2_PROF_T(v) const long long v = clock64()
 #define DH2_PROF_ADD(i, v) \
   if (threadIdx.x == 0) atomicAdd(&g_prof[i], (unsigned long long)(v))
+#define DH2_PROF_ON 1
 #else
 #define DH2_PROF_T(v)
 #define DH2_PROF_ADD(i, v)
+#define DH2_PROF_ON 0
 #endif
 
 template <typename T>
@@ -488,6 +492,9 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     DH2_PROF_T(t_s1);
     DH2_PROF_ADD(8, t_s1 - t_s0);
   }
+#if DH2_PROF_ON
+  long long pw_all = 0, pw_crit = 0, pw_pub = 0, pw_steps = 0;
+#endif
   for (int j0 = 0; j0 < N; j0 += C) {
     DH2_PROF_ADD(9, 1);
 #pragma unroll
@@ -503,6 +510,10 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     const bool pre = async_ok && j0n < N;
     bool issued = false;
     for (int i = 0; i < p; ++i) {
+#if DH2_PROF_ON
+      const long long ts0 = clock64();
+      long long tsp = ts0;
+#endif
       const int sl = i & 1;
       // a skipped reflection (zero chunk part) is the identity: tau = 0
       const bool skip = sh_skip[sl] != 0;
@@ -519,8 +530,26 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
       for (int s = 0; s < S; ++s) {
         if (!slot_live(s, i)) continue;
         apply(ch[s], lrow(s), i, x, v0, tau);
-        if (s == cs) publish(i + 1, ch[s], lrow(s) == i + 1, sl ^ 1);
+        if (s == cs) {
+          publish(i + 1, ch[s], lrow(s) == i + 1, sl ^ 1);
+#if DH2_PROF_ON
+          __syncwarp();
+          tsp = clock64();
+#endif
+        }
       }
+#if DH2_PROF_ON
+      __syncwarp();
+      {
+        const long long ts1 = clock64();
+        pw_all += ts1 - ts0;
+        if (cs >= 0) {
+          pw_crit += ts1 - ts0;
+          pw_pub += tsp - ts0;
+        }
+        ++pw_steps;
+      }
+#endif
       if (pre) {
         if (FROM_R) {
           if (i == 0) {
@@ -554,6 +583,14 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
 
   DH2_PROF_T(t_b);
   DH2_PROF_ADD(0, t_b - t_a);
+#if DH2_PROF_ON
+  if (lane == 0) {
+    atomicAdd(&g_prof[10], (unsigned long long)pw_crit);
+    atomicAdd(&g_prof[11], (unsigned long long)pw_all);
+    atomicAdd(&g_prof[13], (unsigned long long)pw_pub);
+  }
+  if (tid == 0) atomicAdd(&g_prof[12], (unsigned long long)pw_steps);
+#endif
 
   // ---------------------------------------------------------------- 1b. pivoted LQ of L
   // Rank-revealing step: L Omega' = L' by Householder reflections from the
@@ -871,16 +908,18 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
 
 // R_tc = Q^* A for the pairs of one launch (Section 6, R recursion: R_tc =
 // V_tc^* G_tc for a leaf, [E_t1c; E_t2c]^* Ghat_tc for a non-leaf), after
-// pair_kernel has written Q and the rank.  One CTA per pair: A is streamed in
-// tiles of TW columns through shared memory and Q is held in blocks of QB
-// columns; each thread forms 2 x 2 output tiles.  A second read of A, but
-// with no serial chain: the loads of many pairs are in flight at once.
+// pair_kernel has written Q and the rank.  One CTA of 128 threads per tile of
+// TW = 32 columns of one pair (tile = launch code << 32 | first column), so
+// that the loads of many tiles are in flight at once.  The leaf column table
+// is read first; the entries of A and the block of Q then arrive together by
+// cp.async, and the weights and the conjugation of G^* are applied in shared
+// memory.  Each thread forms 2 x 2 outputs of the k x TW tile of R.
 template <typename T, bool FROM_R>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
-    rq_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
-  constexpr int NT = 256;
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
+    rq_kernel(const PairArgs<T>* __restrict__ args, const uint64_t* __restrict__ tiles, const int P) {
+  constexpr int NT = 128;
   constexpr int QB = 32;
-  constexpr int TW = sizeof(T) == 4 ? 64 : 32;
+  constexpr int TW = kRTile;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int cgc[TW];
   __shared__ T cwt[TW];
@@ -888,7 +927,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
   C2<T>* Qs = reinterpret_cast<C2<T>*>(smem);  // QB columns of Q
   C2<T>* As = Qs + QB * LD;                    // TW columns of A
   const int tid = threadIdx.x;
-  const uint32_t code = codes[blockIdx.x];
+  const uint64_t tile = tiles[blockIdx.x];
+  const uint32_t code = (uint32_t)(tile >> 32);
+  const int j0 = (int)(uint32_t)tile;
   const int prob = (int)(code >> kCodeProbShift);
   const int side = (int)((code >> kCodeSideShift) & 1u);
   const int pid = (int)(code & kCodePairMask);
@@ -896,7 +937,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
   if (!DH2_IN(pid, c_lim.npairs[side], 9, pid)) return;
   const int N = a.ncols[side][pid];
   const int k = a.rank[side][pid];
-  if (k <= 0 || N == 0) return;
+  if (k <= 0 || j0 >= N) return;
   Source<T, FROM_R> src;
   src.side = side;
   src.pid = pid;
@@ -928,48 +969,77 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2)
     src.gen = a.gen;
   }
   if (p <= 0 || p > P) return;  // reported by pair_kernel
+  const bool gen = !FROM_R && src.gen;
+  const bool down = FROM_R || side == 0;  // consecutive threads on the contiguous direction
+  const int cw = min(TW, N - j0);
   const C2<T>* Qin = a.Q[side] + a.Qoff[side][pid];
   const int ldq = a.rowcap[side][pid];
   C2<T>* Rout = a.R[side] + a.Roff[side][pid];
   const int kcap = a.kcap[side][pid];
+  if (!FROM_R) {
+    stage_table<T, FROM_R, NT>(src, j0, cw, cgc, cwt);
+    __syncthreads();
+  }
   for (int qb = 0; qb < k; qb += QB) {
     const int kb = min(QB, k - qb);
-    __syncthreads();  // the previous block's products are done with Qs
+    if (qb > 0) __syncthreads();  // the previous block's products are done with Qs
     for (int idx = tid; idx < p * kb; idx += NT) {
       const int r = idx % p, qq = idx / p;
       const int64_t e = r + (int64_t)(qb + qq) * ldq;
-      Qs[qq * LD + r] = DH2_IN(a.Qoff[side][pid] + e, c_lim.Q[side], 14, pid) ? Qin[e] : czero<T>();
+      if (DH2_IN(a.Qoff[side][pid] + e, c_lim.Q[side], 14, pid)) cp_async<sizeof(C2<T>)>(Qs + qq * LD + r, Qin + e);
+      else Qs[qq * LD + r] = czero<T>();
     }
-    for (int j0 = 0; j0 < N; j0 += TW) {
-      const int cw = min(TW, N - j0);
-      stage_table<T, FROM_R, NT>(src, j0, cw, cgc, cwt);
-      __syncthreads();  // table and Qs ready; the previous tile's products done with As
-      stage_cols<T, FROM_R, NT>(src, p, j0, cw, cw, As, LD, cgc, cwt);
-      __syncthreads();
-      // 2 x 2 output tiles (columns past kb or cw are read from a clamped
-      // pointer and not stored)
-      const int nqt = (kb + 1) >> 1, njt = (cw + 1) >> 1;
-      for (int t = tid; t < nqt * njt; t += NT) {
-        const int q0 = 2 * (t % nqt), jb = 2 * (t / nqt);
-        const C2<T>* qc0 = Qs + q0 * LD;
-        const C2<T>* qc1 = q0 + 1 < kb ? qc0 + LD : qc0;
-        const C2<T>* ac0 = As + jb * LD;
-        const C2<T>* ac1 = jb + 1 < cw ? ac0 + LD : ac0;
-        C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
-        for (int r = 0; r < p; ++r) {
-          const C2<T> x0 = qc0[r], x1 = qc1[r], y0 = ac0[r], y1 = ac1[r];
-          c00 = cadd(c00, cmulc(y0, x0));
-          c01 = cadd(c01, cmulc(y1, x0));
-          c10 = cadd(c10, cmulc(y0, x1));
-          c11 = cadd(c11, cmulc(y1, x1));
+    if (qb == 0) {
+      for (int e = tid; e < cw * p; e += NT) {
+        const int r = down ? e % p : e / cw;
+        const int jj = down ? e / p : e % cw;
+        C2<T>* d = As + jj * LD + r;
+        if (gen) {
+          *d = src.leaf_at(r, cgc[jj], cwt[jj]);
+        } else {
+          const C2<T>* g = FROM_R ? src.sons_ptr(r, j0 + jj) : src.leaf_ptr(r, cgc[jj]);
+          if (g) cp_async<sizeof(C2<T>)>(d, g);
+          else *d = czero<T>();
         }
+      }
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    if (qb == 0 && !FROM_R && !gen) {
+      // weights 1/omega_b and, for the column basis, the conjugation of G^*
+      for (int e = tid; e < cw * p; e += NT) {
+        const int r = down ? e % p : e / cw;
+        const int jj = down ? e / p : e % cw;
+        C2<T>* d = As + jj * LD + r;
+        const C2<T> g = *d;
+        const T w = cwt[jj];
+        *d = C2<T>{g.re * w, side == 0 ? g.im * w : -g.im * w};
+      }
+    }
+    __syncthreads();
+    // 2 x 2 output tiles (columns past kb or cw are read from a clamped
+    // pointer and not stored)
+    const int nqt = (kb + 1) >> 1, njt = (cw + 1) >> 1;
+    for (int t = tid; t < nqt * njt; t += NT) {
+      const int q0 = 2 * (t % nqt), jb = 2 * (t / nqt);
+      const C2<T>* qc0 = Qs + q0 * LD;
+      const C2<T>* qc1 = q0 + 1 < kb ? qc0 + LD : qc0;
+      const C2<T>* ac0 = As + jb * LD;
+      const C2<T>* ac1 = jb + 1 < cw ? ac0 + LD : ac0;
+      C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
+      for (int r = 0; r < p; ++r) {
+        const C2<T> x0 = qc0[r], x1 = qc1[r], y0 = ac0[r], y1 = ac1[r];
+        c00 = cadd(c00, cmulc(y0, x0));
+        c01 = cadd(c01, cmulc(y1, x0));
+        c10 = cadd(c10, cmulc(y0, x1));
+        c11 = cadd(c11, cmulc(y1, x1));
+      }
 #pragma unroll
-        for (int d = 0; d < 4; ++d) {
-          const int qq = q0 + (d >> 1), jj = jb + (d & 1);
-          const C2<T> v = d == 0 ? c00 : d == 1 ? c01 : d == 2 ? c10 : c11;
-          const int64_t e = (qb + qq) + (int64_t)(j0 + jj) * kcap;
-          if (qq < kb && jj < cw && DH2_IN(a.Roff[side][pid] + e, c_lim.R[side], 11, pid)) Rout[e] = v;
-        }
+      for (int d = 0; d < 4; ++d) {
+        const int qq = q0 + (d >> 1), jj = jb + (d & 1);
+        const C2<T> v = d == 0 ? c00 : d == 1 ? c01 : d == 2 ? c10 : c11;
+        const int64_t e = (qb + qq) + (int64_t)(j0 + jj) * kcap;
+        if (qq < kb && jj < cw && DH2_IN(a.Roff[side][pid] + e, c_lim.R[side], 11, pid)) Rout[e] = v;
       }
     }
   }
@@ -1016,39 +1086,38 @@ bool check_read_pair(CheckRecord* out) {
 
 void prof_reset_pair() {
 #ifdef DH2_PROFILE
-  unsigned long long z[10] = {};
+  unsigned long long z[14] = {};
   cudaMemcpyToSymbol(g_prof, z, sizeof(z));
 #endif
 }
 
-bool prof_read_pair(unsigned long long* out10) {
+bool prof_read_pair(unsigned long long* out14) {
 #ifdef DH2_PROFILE
-  cudaMemcpyFromSymbol(out10, g_prof, 10 * sizeof(unsigned long long));
+  cudaMemcpyFromSymbol(out14, g_prof, 14 * sizeof(unsigned long long));
   return true;
 #else
-  (void)out10;
+  (void)out14;
   return false;
 #endif
 }
 
 template <typename T, bool FROM_R>
-void launch_rq(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
-  constexpr int TW = sizeof(T) == 4 ? 64 : 32;
-  const size_t smem = (size_t)(32 + TW) * (P + 1) * sizeof(C2<T>);
+void launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
+  const size_t smem = (size_t)(32 + kRTile) * (P + 1) * sizeof(C2<T>);
   auto kern = rq_kernel<T, FROM_R>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<nblocks, 256, smem, st>>>(args, codes, P);
+  kern<<<ntiles, 128, smem, st>>>(args, tiles, P);
 }
 
 template <typename T>
-void launch_rq_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
+void launch_rq_kernel(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, bool from_r,
                       cudaStream_t st) {
-  if (nblocks <= 0) return;
-  if (from_r) launch_rq<T, true>(args, codes, nblocks, P, st);
-  else launch_rq<T, false>(args, codes, nblocks, P, st);
+  if (ntiles <= 0) return;
+  if (from_r) launch_rq<T, true>(args, tiles, ntiles, P, st);
+  else launch_rq<T, false>(args, tiles, ntiles, P, st);
 }
-template void launch_rq_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t);
-template void launch_rq_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t);
+template void launch_rq_kernel<float>(const PairArgs<float>*, const uint64_t*, int, int, bool, cudaStream_t);
+template void launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*, int, int, bool, cudaStream_t);
 
 template <typename T>
 void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
