@@ -647,16 +647,18 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #ifdef DH2_PROFILE
   {
     cudaStreamSynchronize(st);
-    unsigned long long pr[14];
+    unsigned long long pr[17];
     prof_read_pair(pr);
     const double np = pr[5] ? (double)pr[5] : 1.0;
     const double ns = pr[12] ? (double)pr[12] : 1.0;
     std::fprintf(stderr,
                  "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean K %.1f, mean sweeps %.2f, mean chunks %.2f, "
                  "cycles/pair: LQ %.0f (staging %.0f) Jacobi %.0f rank+Q %.0f; LQ steps %.1f/pair, cycles/step %.0f, "
-                 "per warp-step busy %.0f, critical warp busy %.0f, to reflection %.0f\n",
+                 "per warp-step busy %.0f, critical warp busy %.0f, to reflection %.0f (loads %.0f, update %.0f, "
+                 "form %.0f)\n",
                  pr[5], pr[6] / np, pr[7] / np, pr[4] / np, pr[9] / np, pr[0] / np, pr[8] / np, pr[1] / np,
-                 pr[2] / np, ns / np, (pr[0] - pr[8]) / ns, pr[11] / (8.0 * ns), pr[10] / ns, pr[13] / ns);
+                 pr[2] / np, ns / np, (pr[0] - pr[8]) / ns, pr[11] / (8.0 * ns), pr[10] / ns, pr[13] / ns,
+                 pr[14] / ns, pr[15] / ns, pr[16] / ns);
   }
 #endif
   DH2_PHASE_SYNC("leaf pairs");

@@ -87,8 +87,8 @@ template <typename T>
 void launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int ntiles, int P, bool from_r,
                       cudaStream_t st);
 
-// Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 14 values.
+// Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 17 values.
 void prof_reset_pair();
-bool prof_read_pair(unsigned long long* out14);
+bool prof_read_pair(unsigned long long* out17);
 
 }  // namespace dh2

@@ -39,8 +39,10 @@ DH2_CHECK_DECLS
 // summed over CTAs: cycles of LQ, Jacobi, rank+Q, R; sweeps; pairs; p; K;
 // cycles of the LQ staging; chunks; LQ steps; cycles from a step's start to
 // the end of its own work, summed over the warps (10: the warp forming the
-// next reflection, 11: all warps), and cycles to the formed reflection (13)
-__device__ unsigned long long g_prof[14];
+// next reflection, 11: all warps), and cycles to the formed reflection (13),
+// split (14-16) into step start -> update of row i+1 -> its norm reduced ->
+// reflection formed, as seen by the thread that forms it
+__device__ unsigned long long g_prof[17];
 #define DH2_PROF_T(v) const long long v = clock64()
 #define DH2_PROF_ADD(i, v) \
   if (threadIdx.x == 0) atomicAdd(&g_prof[i], (unsigned long long)(v))
@@ -409,12 +411,15 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   // apply reflection j (vector x, scalars v0, tau) to this thread's row r of a
   // slot (entries c); called by a whole warp, rows other than j < r < p are
   // left unchanged (their quarters return at once)
-  auto apply = [&](C2<T> (&c)[E], int r, int j, const C2<T> (&x)[E], C2<T> v0, T tau_j) {
+  auto apply = [&](C2<T> (&c)[E], int r, int j, const C2<T>* xs, C2<T> v0, T tau_j) {
     const bool act = r > j && r < p;
     if (!act) return;
     const unsigned qmask = 0xffu << (lane & 24);
     const T tau = tau_j;
     const C2<T> lrj = Lm[j * LDL + r];
+    C2<T> x[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) x[u] = xs[lq + u * LQT];
     C2<T> w0 = czero<T>(), w1 = czero<T>();
 #pragma unroll
     for (int u = 0; u < E; u += 2) {
@@ -494,6 +499,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   }
 #if DH2_PROF_ON
   long long pw_all = 0, pw_crit = 0, pw_pub = 0, pw_steps = 0;
+  long long pq_a = 0, pq_b = 0, pq_c = 0;
 #endif
   for (int j0 = 0; j0 < N; j0 += C) {
     DH2_PROF_ADD(9, 1);
@@ -517,13 +523,14 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
       const int sl = i & 1;
       // a skipped reflection (zero chunk part) is the identity: tau = 0
       const bool skip = sh_skip[sl] != 0;
-      C2<T> x[E];
-#pragma unroll
-      for (int u = 0; u < E; ++u) x[u] = vbuf[sl * C + lq + u * LQT];
+      const C2<T>* x = vbuf + sl * C;
       const C2<T> v0 = skip ? czero<T>() : sh_v0[sl];
       const T tau = skip ? T(0) : sh_tau[sl];
       const int b1 = (i + 1) >> 2;  // block of row i+1
       const int cs = i + 1 < p && (b1 % NW) == warp ? b1 / NW : -1;
+#if DH2_PROF_ON
+      const long long tsa = clock64();
+#endif
       // slots in increasing order: for the owner of row i+1 that row's slot is
       // its lowest live one, so the next reflection is formed first
 #pragma unroll
@@ -531,8 +538,17 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
         if (!slot_live(s, i)) continue;
         apply(ch[s], lrow(s), i, x, v0, tau);
         if (s == cs) {
+#if DH2_PROF_ON
+          const long long tsb = clock64();
+#endif
           publish(i + 1, ch[s], lrow(s) == i + 1, sl ^ 1);
 #if DH2_PROF_ON
+          if (lrow(s) == i + 1 && lq == 0) {
+            const long long tsc = clock64();
+            pq_a += tsa - ts0;
+            pq_b += tsb - tsa;
+            pq_c += tsc - tsb;
+          }
           __syncwarp();
           tsp = clock64();
 #endif
@@ -590,6 +606,11 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     atomicAdd(&g_prof[13], (unsigned long long)pw_pub);
   }
   if (tid == 0) atomicAdd(&g_prof[12], (unsigned long long)pw_steps);
+  if (pq_a + pq_b + pq_c) {
+    atomicAdd(&g_prof[14], (unsigned long long)pq_a);
+    atomicAdd(&g_prof[15], (unsigned long long)pq_b);
+    atomicAdd(&g_prof[16], (unsigned long long)pq_c);
+  }
 #endif
 
   // ---------------------------------------------------------------- 1b. pivoted LQ of L
@@ -788,12 +809,18 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
           }
           const T g2 = cnorm2(ga);
           // rotate unless the pair is orthogonal to tol (relative)
+          // rotation scalars from reciprocal square roots and one quotient
+          // (hardware approximations in FP32, a few ulp): c^2 + s^2 = 1 to
+          // that level, far inside the convergence test's tol = p u
+          const T rg = frsqrt(g2);
           if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
-              sqrt(g2) * frsqrt(al) * frsqrt(be) > tol) {
-            const T rg = frsqrt(g2);
+              g2 * rg * frsqrt(al) * frsqrt(be) > tol) {
             const T zt = (be - al) * T(0.5) * rg;
-            const T t = (zt >= T(0) ? T(1) : T(-1)) / (fabs(zt) + sqrt(T(1) + zt * zt));
-            const T c = T(1) / sqrt(T(1) + t * t);
+            const T az = fabs(zt);
+            const T q1 = T(1) + zt * zt;
+            const T t = (zt >= T(0) ? T(1) : T(-1)) *
+                        (az > T(1e15) ? fdiv(T(0.5), az) : fdiv(T(1), az + q1 * frsqrt(q1)));
+            const T c = frsqrt(T(1) + t * t);
             const T s = t * c;
             if (s != T(0)) {
               const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
@@ -1086,17 +1113,17 @@ bool check_read_pair(CheckRecord* out) {
 
 void prof_reset_pair() {
 #ifdef DH2_PROFILE
-  unsigned long long z[14] = {};
+  unsigned long long z[17] = {};
   cudaMemcpyToSymbol(g_prof, z, sizeof(z));
 #endif
 }
 
-bool prof_read_pair(unsigned long long* out14) {
+bool prof_read_pair(unsigned long long* out17) {
 #ifdef DH2_PROFILE
-  cudaMemcpyFromSymbol(out14, g_prof, 14 * sizeof(unsigned long long));
+  cudaMemcpyFromSymbol(out17, g_prof, 17 * sizeof(unsigned long long));
   return true;
 #else
-  (void)out14;
+  (void)out17;
   return false;
 #endif
 }
