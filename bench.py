@@ -36,7 +36,7 @@ FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one leaf launch of the pair kernel at n=32768,
 # kappa=32, leaf 64, FP32, from a 1-pass ncu capture (profiles/); valid only
 # for the kernel source it was measured on (sha1 of csrc/dh2_pair.cu).
-PAIR_TRAFFIC = {"sha1": "d77aa0057a53297f72694fe2bbce03d37ab1741b", "bytes": 11.17e9 + 2.14e9}
+PAIR_TRAFFIC = {"sha1": "1494acdb58cae3fe0b9931a34b403a9ebd5c8b2e", "bytes": 5.92e9 + 0.274e9}
 
 
 def _peaks():

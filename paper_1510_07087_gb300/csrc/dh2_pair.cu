@@ -70,6 +70,28 @@ __device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
 }
 template <typename T>
 __device__ __forceinline__ T cnorm2(C2<T> a) { return a.re * a.re + a.im * a.im; }
+// Accumulating forms as fused multiply-adds (the compiler may not reassociate
+// acc + (x*y + z*w) into them itself): acc + a conj(b), c - t x, acc + |a|^2.
+template <typename T>
+__device__ __forceinline__ C2<T> cmacc(C2<T> acc, C2<T> a, C2<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.im, b.re, acc.im);
+  acc.im = fma(-a.re, b.im, acc.im);
+  return acc;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cnmac(C2<T> c, C2<T> t, C2<T> x) {
+  c.re = fma(-t.re, x.re, c.re);
+  c.re = fma(t.im, x.im, c.re);
+  c.im = fma(-t.re, x.im, c.im);
+  c.im = fma(-t.im, x.re, c.im);
+  return c;
+}
+template <typename T>
+__device__ __forceinline__ T nmac(T acc, C2<T> a) {
+  return fma(a.im, a.im, fma(a.re, a.re, acc));
+}
 
 template <typename T>
 struct Eps;
@@ -381,8 +403,8 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     T s0 = T(0), s1 = T(0);
 #pragma unroll
     for (int u = 0; u < E; u += 2) {
-      s0 += cnorm2(x[u]);
-      if (u + 1 < E) s1 += cnorm2(x[u + 1]);
+      s0 = nmac(s0, x[u]);
+      if (u + 1 < E) s1 = nmac(s1, x[u + 1]);
     }
     s0 += s1;
 #pragma unroll
@@ -420,13 +442,10 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     C2<T> x[E];
 #pragma unroll
     for (int u = 0; u < E; ++u) x[u] = xs[lq + u * LQT];
-    C2<T> w0 = czero<T>(), w1 = czero<T>();
+    C2<T> wa[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
 #pragma unroll
-    for (int u = 0; u < E; u += 2) {
-      w0 = cadd(w0, cmulc(c[u], x[u]));
-      if (u + 1 < E) w1 = cadd(w1, cmulc(c[u + 1], x[u + 1]));
-    }
-    C2<T> w = cadd(w0, w1);
+    for (int u = 0; u < E; ++u) wa[u & 3] = cmacc(wa[u & 3], c[u], x[u]);
+    C2<T> w = cadd(cadd(wa[0], wa[1]), cadd(wa[2], wa[3]));
 #pragma unroll
     for (int o = 1; o < LQT; o <<= 1) {
       w.re += __shfl_xor_sync(qmask, w.re, o);
@@ -435,7 +454,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     w = cadd(w, cmul(lrj, v0));
     const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
 #pragma unroll
-    for (int u = 0; u < E; ++u) c[u] = csub(c[u], cmul(tw, x[u]));
+    for (int u = 0; u < E; ++u) c[u] = cnmac(c[u], tw, x[u]);
     if (lq == 0) Lm[j * LDL + r] = csub(lrj, cmulc(tw, v0));
   };
 
@@ -631,7 +650,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   {
     T s = T(0);
     if (live)
-      for (int c = q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + row]);
+      for (int c = q; c < p; c += LPR) s = nmac(s, Lm[c * LDL + row]);
 #pragma unroll
     for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (live && q == 0) {
@@ -677,7 +696,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
       // reflector of row pv over columns i..p-1: the row becomes beta e_i
       T s = T(0);
       if (row == pv)
-        for (int c = i + 1 + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + pv]);
+        for (int c = i + 1 + q; c < p; c += LPR) s = nmac(s, Lm[c * LDL + pv]);
 #pragma unroll
       for (int o = 1; o < LPR; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (row == pv && q == 0) {
@@ -709,7 +728,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
       C2<T> w = czero<T>();
       if (act && !skip) {
         if (q == 0) w = cmul(Lm[i * LDL + row], sh_v0[0]);
-        for (int c = i + 1 + q; c < p; c += LPR) w = cadd(w, cmulc(Lm[c * LDL + row], Lm[c * LDL + pv]));
+        for (int c = i + 1 + q; c < p; c += LPR) w = cmacc(w, Lm[c * LDL + row], Lm[c * LDL + pv]);
       }
       if (!skip) {
 #pragma unroll
@@ -724,13 +743,13 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
           const T tau = sh_tau[0];
           const C2<T> tw = C2<T>{tau * w.re, tau * w.im};
           for (int c = i + 1 + q; c < p; c += LPR) {
-            const C2<T> x = csub(Lm[c * LDL + row], cmul(tw, Lm[c * LDL + pv]));
+            const C2<T> x = cnmac(Lm[c * LDL + row], tw, Lm[c * LDL + pv]);
             Lm[c * LDL + row] = x;
-            s += cnorm2(x);
+            s = nmac(s, x);
           }
           if (q == 0) Lm[i * LDL + row] = csub(Lm[i * LDL + row], cmulc(tw, v0));
         } else {
-          for (int c = i + 1 + q; c < p; c += LPR) s += cnorm2(Lm[c * LDL + row]);
+          for (int c = i + 1 + q; c < p; c += LPR) s = nmac(s, Lm[c * LDL + row]);
         }
       }
 #pragma unroll
@@ -797,9 +816,9 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
           if (act)
             for (int r = jl; r < p; r += tpp) {
               const C2<T> xa = ca[r], xb = cb[r];
-              al += cnorm2(xa);
-              be += cnorm2(xb);
-              ga = cadd(ga, cmulc(xb, xa));  // conj(xa) * xb
+              al = nmac(al, xa);
+              be = nmac(be, xb);
+              ga = cmacc(ga, xb, xa);  // + conj(xa) * xb
             }
           for (int o = 1; o < tpp; o <<= 1) {
             al += __shfl_xor_sync(0xffffffffu, al, o);
@@ -864,7 +883,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     const int j = jb + grp;
     T s = T(0);
     if (j < K)
-      for (int r = gl; r < p; r += 8) s += cnorm2(Lm[j * LDL + r]);
+      for (int r = gl; r < p; r += 8) s = nmac(s, Lm[j * LDL + r]);
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (j < K && gl == 0) sig2[j] = (double)s;
@@ -1056,10 +1075,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
       C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
       for (int r = 0; r < p; ++r) {
         const C2<T> x0 = qc0[r], x1 = qc1[r], y0 = ac0[r], y1 = ac1[r];
-        c00 = cadd(c00, cmulc(y0, x0));
-        c01 = cadd(c01, cmulc(y1, x0));
-        c10 = cadd(c10, cmulc(y0, x1));
-        c11 = cadd(c11, cmulc(y1, x1));
+        c00 = cmacc(c00, y0, x0);
+        c01 = cmacc(c01, y1, x0);
+        c10 = cmacc(c10, y0, x1);
+        c11 = cmacc(c11, y1, x1);
       }
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
