@@ -180,11 +180,27 @@ __global__ void __launch_bounds__(256) expand_kernel(SideView<T> S, const int32_
 // ---------------------------------------------------------------- projection
 // S_b = omega_b R_tc|_b W_sc: R_tc|_b = V_tc^* G_b / omega_b is the block's
 // own column range of R_tc (Section 6), W_sc the expanded column basis.
-// One warp per admissible block; each lane accumulates up to 8 outputs over
-// the block's columns, reading R and W through L1.
+// One warp per admissible block.  For ranks up to KS the warp stages chunks
+// of JC columns of R_tc|_b and rows of W_sc in its own shared memory
+// (coalesced) and each lane forms a 2 x 4 tile of S_b; larger ranks take the
+// generic path, which reads R and W through L1.
+template <typename T>
+__device__ __forceinline__ C2<T> cmac(C2<T> acc, C2<T> x, C2<T> y) {  // acc + x y
+  acc.re = fma(x.re, y.re, acc.re);
+  acc.re = fma(-x.im, y.im, acc.re);
+  acc.im = fma(x.re, y.im, acc.im);
+  acc.im = fma(x.im, y.re, acc.im);
+  return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) project_kernel(ProjArgs<T> a, int nadm) {
-  const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  constexpr int KS = 32;
+  constexpr int JC = sizeof(T) == 4 ? 16 : 8;
+  __shared__ C2<T> sR[4][KS * JC];  // R chunk: kt x jc, column-major, ld KS
+  __shared__ C2<T> sW[4][JC * KS];  // W chunk: jc x ks, column-major, ld JC
+  const int wl = threadIdx.x >> 5;
+  const int wid = blockIdx.x * (blockDim.x >> 5) + wl;
   const int lane = threadIdx.x & 31;
   if (wid >= nadm) return;
   const int b = a.adm_list[wid];
@@ -202,6 +218,60 @@ __global__ void __launch_bounds__(128) project_kernel(ProjArgs<T> a, int nadm) {
   const int64_t wbase = wleaf ? a.W.Qoff[Ps] : a.W.Xoff[Ps];
   const C2<T>* W = xbasis(a.W, Ps);
   const T w = (T)(1.0 / a.invw[b]);
+  if (kt <= KS && ks <= KS) {
+    C2<T>* r_s = sR[wl];
+    C2<T>* w_s = sW[wl];
+    const int nqt = (kt + 1) >> 1, nct = (ks + 3) >> 2, ntile = nqt * nct;
+    for (int t0 = 0; t0 < ntile; t0 += 32) {
+      const int t = t0 + lane;
+      const bool act = t < ntile;
+      const int q0 = act ? 2 * (t % nqt) : 0, c0 = act ? 4 * (t / nqt) : 0;
+      C2<T> acc[2][4];
+#pragma unroll
+      for (int x = 0; x < 2; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = czero<T>();
+      for (int j0 = 0; j0 < ms; j0 += JC) {
+        const int jc = min(JC, ms - j0);
+        __syncwarp();
+        if (lane < kt)
+          for (int jj = 0; jj < jc; ++jj) {
+            const int64_t ri = lane + (int64_t)(j0 + jj) * ldr;
+            r_s[lane + jj * KS] = DH2_IN(rbase + ri, c_lim.R[0], 40, b) ? R[ri] : czero<T>();
+          }
+        for (int idx = lane; idx < jc * ks; idx += 32) {
+          const int jj = idx % jc, c = idx / jc;
+          const int64_t wi = (j0 + jj) + (int64_t)c * ms;
+          const bool ok = wleaf ? DH2_IN(wbase + wi, c_lim.Q[1], 41, b) : DH2_IN(wbase + wi, c_lim.X[1], 42, b);
+          w_s[jj + c * JC] = ok ? W[wi] : czero<T>();
+        }
+        __syncwarp();
+        if (act)
+          for (int jj = 0; jj < jc; ++jj) {
+            // rows past kt and columns past ks read unwritten entries whose
+            // products are never stored
+            const C2<T> x0 = r_s[q0 + jj * KS], x1 = r_s[q0 + 1 + jj * KS];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+              const C2<T> wy = w_s[jj + (c0 + y) * JC];
+              acc[0][y] = cmac(acc[0][y], x0, wy);
+              acc[1][y] = cmac(acc[1][y], x1, wy);
+            }
+          }
+      }
+      if (act)
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) {
+            const int qq = q0 + x, cc = c0 + y;
+            const int o = qq + cc * kt;  // column-major, ld = kt
+            if (qq < kt && cc < ks && DH2_IN(a.Soff[b] + o, c_lim.S, 43, b))
+              Sout[o] = C2<T>{w * acc[x][y].re, w * acc[x][y].im};
+          }
+    }
+    return;
+  }
   const int nout = kt * ks;
   for (int o0 = 0; o0 < nout; o0 += 32 * 8) {
     C2<T> acc[8];
@@ -221,7 +291,7 @@ __global__ void __launch_bounds__(128) project_kernel(ProjArgs<T> a, int nadm) {
           const int64_t wi = j + (int64_t)cc[u] * ms;
           const bool ok = DH2_IN(rbase + ri, c_lim.R[0], 40, b) &&
                           (wleaf ? DH2_IN(wbase + wi, c_lim.Q[1], 41, b) : DH2_IN(wbase + wi, c_lim.X[1], 42, b));
-          if (ok) acc[u] = cadd(acc[u], cmul(R[ri], W[wi]));
+          if (ok) acc[u] = cmac(acc[u], R[ri], W[wi]);
         }
       }
     }
