@@ -127,6 +127,22 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Walk e = start, start + step, ... < slow_n * fast_n over a (slow, fast)
+// index pair, e = slow * fast_n + fast, with one division at set-up.
+struct Walk2 {
+  int f, g, df, dg, fn;
+  __device__ __forceinline__ Walk2(int start, int step, int fast_n)
+      : f(start % fast_n), g(start / fast_n), df(step % fast_n), dg(step / fast_n), fn(fast_n) {}
+  __device__ __forceinline__ void next() {
+    f += df;
+    g += dg;
+    if (f >= fn) {
+      f -= fn;
+      ++g;
+    }
+  }
+};
+
 // Element (r, j) of the pair's matrix A (row r of the factor, column j of F_tc).
 template <typename T, bool FROM_R>
 struct Source {
@@ -400,6 +416,15 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   auto publish = [&](int r, const C2<T> (&x)[E], bool mine, int slot) {
     if (!mine) return;
     const unsigned qmask = 0xffu << (lane & 24);
+    // the diagonal entry and its phase do not depend on the row norm: form
+    // them while the norm is reduced
+    const C2<T> al = Lm[r * LDL + r];
+    const T an2 = cnorm2(al);
+    const T ra = an2 > Eps<T>::tiny ? frsqrt(an2) : T(0);
+    const T an = an2 * ra;
+    const C2<T> ph = an2 > Eps<T>::tiny ? C2<T>{al.re * ra, al.im * ra} : C2<T>{T(1), T(0)};
+#pragma unroll
+    for (int u = 0; u < E; ++u) vbuf[slot * C + lq + u * LQT] = x[u];
     T s0 = T(0), s1 = T(0);
 #pragma unroll
     for (int u = 0; u < E; u += 2) {
@@ -409,19 +434,12 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     s0 += s1;
 #pragma unroll
     for (int o = 1; o < LQT; o <<= 1) s0 += __shfl_xor_sync(qmask, s0, o);
-#pragma unroll
-    for (int u = 0; u < E; ++u) vbuf[slot * C + lq + u * LQT] = x[u];
     if (lq == 0) {
       if (!(s0 > Eps<T>::tiny)) {
         sh_skip[slot] = 1;
       } else {
-        const C2<T> al = Lm[r * LDL + r];
-        const T an2 = cnorm2(al);
-        const T ra = an2 > Eps<T>::tiny ? frsqrt(an2) : T(0);
-        const T an = an2 * ra;
         const T xn2 = s0 + an2;
         const T xn = xn2 * frsqrt(xn2);
-        const C2<T> ph = an2 > Eps<T>::tiny ? C2<T>{al.re * ra, al.im * ra} : C2<T>{T(1), T(0)};
         Lm[r * LDL + r] = C2<T>{-ph.re * xn, -ph.im * xn};
         sh_v0[slot] = C2<T>{ph.re * (an + xn), -ph.im * (an + xn)};
         sh_tau[slot] = fdiv(T(1), xn * (xn + an));
@@ -484,9 +502,9 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   };
   const bool down = FROM_R || side == 0;  // consecutive threads on the contiguous direction
   auto issue_cols = [&](int j0n, int cwn) {
-    for (int e = tid; e < C * p; e += NT) {
-      const int r = down ? e % p : e / C;
-      const int jj = down ? e / p : e % C;
+    for (Walk2 it(tid, NT, down ? p : C); it.g < (down ? C : p); it.next()) {
+      const int r = down ? it.f : it.g;
+      const int jj = down ? it.g : it.f;
       C2<T>* d = Xs + jj * LDL + r;
       const C2<T>* g = nullptr;
       if (jj < cwn) g = FROM_R ? src.sons_ptr(r, j0n + jj) : src.leaf_ptr(r, cgc[jj]);
@@ -497,9 +515,9 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   };
   auto finish_cols = [&](int cwn) {
     if (FROM_R) return;
-    for (int e = tid; e < C * p; e += NT) {
-      const int r = down ? e % p : e / C;
-      const int jj = down ? e / p : e % C;
+    for (Walk2 it(tid, NT, down ? p : C); it.g < (down ? C : p); it.next()) {
+      const int r = down ? it.f : it.g;
+      const int jj = down ? it.g : it.f;
       if (jj < cwn) {
         C2<T>* d = Xs + jj * LDL + r;
         const C2<T> g = *d;
@@ -1029,16 +1047,16 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
   for (int qb = 0; qb < k; qb += QB) {
     const int kb = min(QB, k - qb);
     if (qb > 0) __syncthreads();  // the previous block's products are done with Qs
-    for (int idx = tid; idx < p * kb; idx += NT) {
-      const int r = idx % p, qq = idx / p;
+    for (Walk2 it(tid, NT, p); it.g < kb; it.next()) {
+      const int r = it.f, qq = it.g;
       const int64_t e = r + (int64_t)(qb + qq) * ldq;
       if (DH2_IN(a.Qoff[side][pid] + e, c_lim.Q[side], 14, pid)) cp_async<sizeof(C2<T>)>(Qs + qq * LD + r, Qin + e);
       else Qs[qq * LD + r] = czero<T>();
     }
     if (qb == 0) {
-      for (int e = tid; e < cw * p; e += NT) {
-        const int r = down ? e % p : e / cw;
-        const int jj = down ? e / p : e % cw;
+      for (Walk2 it(tid, NT, down ? p : cw); it.g < (down ? cw : p); it.next()) {
+        const int r = down ? it.f : it.g;
+        const int jj = down ? it.g : it.f;
         C2<T>* d = As + jj * LD + r;
         if (gen) {
           *d = src.leaf_at(r, cgc[jj], cwt[jj]);
@@ -1053,9 +1071,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
     cp_async_wait_all();
     if (qb == 0 && !FROM_R && !gen) {
       // weights 1/omega_b and, for the column basis, the conjugation of G^*
-      for (int e = tid; e < cw * p; e += NT) {
-        const int r = down ? e % p : e / cw;
-        const int jj = down ? e / p : e % cw;
+      for (Walk2 it(tid, NT, down ? p : cw); it.g < (down ? cw : p); it.next()) {
+        const int r = down ? it.f : it.g;
+        const int jj = down ? it.g : it.f;
         C2<T>* d = As + jj * LD + r;
         const C2<T> g = *d;
         const T w = cwt[jj];
