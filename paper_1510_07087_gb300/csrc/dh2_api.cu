@@ -29,6 +29,9 @@ using namespace dh2;
 
 namespace dh2 {
 
+constexpr int kLeafClasses = 4;
+inline int leaf_class(int m) { return m <= 32 ? 0 : m <= 48 ? 1 : m <= 64 ? 2 : 3; }
+
 // Device copy of a tree's work lists (one arena, uploaded on first use).
 struct Tree::Dev {
   void* arena = nullptr;
@@ -58,6 +61,10 @@ struct Tree::Dev {
   int64_t S_elems = 0, near_elems = 0;
   int64_t nadm = 0, ninadm = 0;
   int64_t nleaf_codes = 0;
+  // leaf codes grouped by size class (rows <= 32, <= 48, <= 64, more), each
+  // group costliest first; the pair kernel's CTA is sized to the class
+  int64_t leaf_class_begin[kLeafClasses + 1] = {0, 0, 0, 0, 0};
+  int32_t leaf_class_maxm[kLeafClasses] = {0, 0, 0, 0};
   std::vector<int64_t> nl_code_begin, nl_code_count;    // per level
   int64_t nleaf_tiles = 0;
   std::vector<int64_t> nl_tile_begin, nl_tile_count;    // per level
@@ -293,21 +300,33 @@ dh2_status upload_tree(Tree& tr) {
     add32(std::move(ppair), &D->par_pair);
     add32(std::move(pson), &D->par_son);
   }
-  // launch codes: all leaf pairs of both sides, costliest first; then non-leaf
-  // pairs per level
+  // launch codes: all leaf pairs of both sides by size class, costliest first
+  // within a class; then non-leaf pairs per level
   {
-    std::vector<std::pair<double, int32_t>> lc;
+    struct LC {
+      int cls;
+      double cost;
+      int32_t code;
+      int m;
+    };
+    std::vector<LC> lc;
     for (int sd = 0; sd < 2; ++sd)
       for (int64_t p : tr.side[sd].leaf_pairs) {
-        const double m = tr.size[tr.side[sd].pairs[p].cluster];
-        lc.push_back({-(m * m * (double)tr.side[sd].pairs[p].ncols), (int32_t)((sd << kCodeSideShift) | (int32_t)p)});
+        const int m = tr.size[tr.side[sd].pairs[p].cluster];
+        lc.push_back({leaf_class(m), (double)m * m * (double)tr.side[sd].pairs[p].ncols,
+                      (int32_t)((sd << kCodeSideShift) | (int32_t)p), m});
       }
-    std::stable_sort(lc.begin(), lc.end(),
-                     [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
-                       return a.first < b.first;
-                     });
+    std::stable_sort(lc.begin(), lc.end(), [](const LC& a, const LC& b) {
+      return a.cls != b.cls ? a.cls < b.cls : a.cost > b.cost;
+    });
     std::vector<int32_t> codes;
-    for (auto& x : lc) codes.push_back(x.second);
+    for (size_t i = 0; i < lc.size(); ++i) {
+      codes.push_back(lc[i].code);
+      D->leaf_class_maxm[lc[i].cls] = std::max(D->leaf_class_maxm[lc[i].cls], (int32_t)lc[i].m);
+      D->leaf_class_begin[lc[i].cls + 1] = (int64_t)i + 1;
+    }
+    for (int c = 1; c <= kLeafClasses; ++c)
+      D->leaf_class_begin[c] = std::max(D->leaf_class_begin[c], D->leaf_class_begin[c - 1]);
     D->nleaf_codes = (int64_t)codes.size();
     D->nl_code_begin.assign(tr.depth + 1, 0);
     D->nl_code_count.assign(tr.depth + 1, 0);
@@ -511,18 +530,27 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   std::vector<int64_t> n_nltiles(maxdepth + 1, 0);
   int64_t n_ltiles = 0;
   std::vector<uint64_t> leaf_tiles;
+  // leaf launches per size class: code ranges and largest row count
+  int64_t cls_begin[kLeafClasses + 1] = {0, 0, 0, 0, 0};
+  int cls_maxm[kLeafClasses] = {0, 0, 0, 0};
   std::vector<std::vector<uint64_t>> nl_tiles(maxdepth + 1);
   size_t args_bytes = align256(sizeof(PairArgs<T>) * nprob) + align256(sizeof(NormsArgs<T>) * nprob);
   size_t codes_bytes = 0;
   if (nprob > 1) {
-    std::vector<std::pair<double, uint32_t>> lc;
+    struct LC {
+      int cls;
+      double cost;
+      uint32_t code;
+      int m;
+    };
+    std::vector<LC> lc;
     for (int i = 0; i < nprob; ++i) {
       const Tree& tr = Ms[i]->tree->tr;
       for (int sd = 0; sd < 2; ++sd)
         for (int64_t p : tr.side[sd].leaf_pairs) {
-          const double m = tr.size[tr.side[sd].pairs[p].cluster];
-          lc.push_back({-(m * m * (double)tr.side[sd].pairs[p].ncols),
-                        ((uint32_t)i << kCodeProbShift) | ((uint32_t)sd << kCodeSideShift) | (uint32_t)p});
+          const int m = tr.size[tr.side[sd].pairs[p].cluster];
+          lc.push_back({leaf_class(m), (double)m * m * (double)tr.side[sd].pairs[p].ncols,
+                        ((uint32_t)i << kCodeProbShift) | ((uint32_t)sd << kCodeSideShift) | (uint32_t)p, m});
         }
       for (int l = tr.depth; l >= 0; --l)
         for (int sd = 0; sd < 2; ++sd)
@@ -530,9 +558,15 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
             nl_codes[l].push_back(((uint32_t)i << kCodeProbShift) | ((uint32_t)sd << kCodeSideShift) | (uint32_t)p);
       for (size_t b = 0; b < tr.blocks.size(); ++b) norm_codes.push_back(((uint32_t)i << 26) | (uint32_t)b);
     }
-    std::stable_sort(lc.begin(), lc.end(), [](const std::pair<double, uint32_t>& a,
-                                              const std::pair<double, uint32_t>& b) { return a.first < b.first; });
-    for (auto& x : lc) leaf_codes.push_back(x.second);
+    std::stable_sort(lc.begin(), lc.end(), [](const LC& a, const LC& b) {
+      return a.cls != b.cls ? a.cls < b.cls : a.cost > b.cost;
+    });
+    for (size_t i = 0; i < lc.size(); ++i) {
+      leaf_codes.push_back(lc[i].code);
+      cls_maxm[lc[i].cls] = std::max(cls_maxm[lc[i].cls], lc[i].m);
+      cls_begin[lc[i].cls + 1] = (int64_t)i + 1;
+    }
+    for (int c = 1; c <= kLeafClasses; ++c) cls_begin[c] = std::max(cls_begin[c], cls_begin[c - 1]);
     auto tiles_of = [&](const std::vector<uint32_t>& codes, std::vector<uint64_t>& out) {
       for (uint32_t c : codes) {
         const Tree& tr = Ms[c >> kCodeProbShift]->tree->tr;
@@ -588,6 +622,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     const Tree::Dev* D = tr.dev;
     d_leaf = D->codes;
     n_leaf = D->nleaf_codes;
+    for (int c = 0; c <= kLeafClasses; ++c) cls_begin[c] = D->leaf_class_begin[c];
+    for (int c = 0; c < kLeafClasses; ++c) cls_maxm[c] = D->leaf_class_maxm[c];
     d_norm = nullptr;
     n_norm = (int64_t)tr.blocks.size();
     for (int l = 0; l <= tr.depth; ++l) {
@@ -641,7 +677,11 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #ifdef DH2_PROFILE
   prof_reset_pair();
 #endif
-  launch_pair_kernel<T>(d_pa, d_leaf, (int)n_leaf, P_leaf, false, st);
+  for (int c = 0; c < kLeafClasses; ++c) {
+    const int64_t nc = cls_begin[c + 1] - cls_begin[c];
+    if (nc > 0)
+      launch_pair_kernel<T>(d_pa, d_leaf + cls_begin[c], (int)nc, even_up(std::max(2, cls_maxm[c])), false, st);
+  }
   cudaEventRecord(ev[2], st);
   launch_rq_kernel<T>(d_pa, d_ltiles, (int)n_ltiles, P_leaf, false, st);
 #ifdef DH2_PROFILE

@@ -274,23 +274,19 @@ __device__ __forceinline__ void stage_cols(const Source<T, FROM_R>& src, int p, 
   }
 }
 
-// P_T: largest factor size of the instantiation (64 or 128 rows).
-// NT: threads per CTA (256, or 128 for the leaf launch when DH2_LEAF_NT=128).
+// P_T: largest factor size of the instantiation (32, 48, 64 or 128 rows).
+// NT: threads per CTA: 4 per row of P_T for the leaf sizes (128, 192, 256),
+// 256 for P_T = 128.  Every thread holds 16 chunk entries, so the chunk is
+// 64 columns wide for the three leaf sizes.
 #ifndef DH2_PAIR_MINB
-#define DH2_PAIR_MINB 3
-#endif
-#ifndef DH2_PAIR_MINB128
-#define DH2_PAIR_MINB128 5
-#endif
-#ifndef DH2_LEAF_NT
-#define DH2_LEAF_NT 256
+#define DH2_PAIR_MINB 3  // CTAs per SM at 256 threads (FP32)
 #endif
 #ifndef DH2_JACOBI_TPP
 #define DH2_JACOBI_TPP 32  // most threads per column pair in the Jacobi step (4..32)
 #endif
 template <int NT, typename T>
 constexpr int pair_min_blocks() {
-  return sizeof(T) == 4 ? (NT == 256 ? DH2_PAIR_MINB : DH2_PAIR_MINB128) : (NT == 256 ? 1 : 2);
+  return sizeof(T) == 4 ? (NT >= 256 ? DH2_PAIR_MINB : NT >= 192 ? 4 : 6) : (NT >= 192 ? 1 : 2);
 }
 
 template <typename T, int P_T, bool FROM_R, int NT>
@@ -1188,7 +1184,9 @@ void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
                         cudaStream_t st) {
   if (nblocks <= 0) return;
   if (!from_r) {
-    if (P <= 64) launch_one<T, 64, false, DH2_LEAF_NT>(args, codes, nblocks, P, st);
+    if (P <= 32) launch_one<T, 32, false, 128>(args, codes, nblocks, P, st);
+    else if (P <= 48) launch_one<T, 48, false, 192>(args, codes, nblocks, P, st);
+    else if (P <= 64) launch_one<T, 64, false, 256>(args, codes, nblocks, P, st);
     else launch_one<T, 128, false, 256>(args, codes, nblocks, P, st);
   } else {
     if (P <= 64) launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
