@@ -281,12 +281,19 @@ __device__ __forceinline__ void stage_cols(const Source<T, FROM_R>& src, int p, 
 #ifndef DH2_PAIR_MINB
 #define DH2_PAIR_MINB 3  // CTAs per SM at 256 threads (FP32)
 #endif
+#ifndef DH2_PAIR_MINB192
+#define DH2_PAIR_MINB192 4  // at 192 threads
+#endif
+#ifndef DH2_PAIR_MINB128
+#define DH2_PAIR_MINB128 6  // at 128 threads
+#endif
 #ifndef DH2_JACOBI_TPP
 #define DH2_JACOBI_TPP 32  // most threads per column pair in the Jacobi step (4..32)
 #endif
 template <int NT, typename T>
 constexpr int pair_min_blocks() {
-  return sizeof(T) == 4 ? (NT >= 256 ? DH2_PAIR_MINB : NT >= 192 ? 4 : 6) : (NT >= 192 ? 1 : 2);
+  return sizeof(T) == 4 ? (NT >= 256 ? DH2_PAIR_MINB : NT >= 192 ? DH2_PAIR_MINB192 : DH2_PAIR_MINB128)
+                        : (NT >= 192 ? 1 : 2);
 }
 
 template <typename T, int P_T, bool FROM_R, int NT>
