@@ -103,12 +103,34 @@ class ClockSampler:
 
 
 def workload(args):
-    return {"workload": f"helmholtz-collocation fibonacci-sphere n={args.n} kappa={args.kappa:g} leaf={args.leaf} "
+    kind = ("helmholtz-collocation fibonacci-sphere" if args.kernel == "slp" else
+            "helmholtz-double-layer-collocation ellipsoid-2:1:1")
+    return {"workload": f"{kind} n={args.n} kappa={args.kappa:g} leaf={args.leaf} "
                         f"eps={args.eps:g} {'FP32 complex64' if args.mode == 'fp32' else 'FP64 complex128'}",
+            "kernel": "1/2 I + double layer (Section 7, DLP)" if args.kernel == "dlp" else "single layer",
             "n": args.n, "kappa": args.kappa, "leaf": args.leaf, "eps": args.eps, "eta1": args.eta1,
             "eta2": args.eta2, "zeta": 2.0 / 3.0, "mode": args.mode,
             "nearfield": "copy" if args.nearfield == 0 else "view",
             "l2": "inputs larger than L2 (G is 8 GiB at n=32768)"}
+
+
+def workload_points(args):
+    """Points and (for the double-layer workload) normals of the workload."""
+    from synth import ellipsoid_normals, fibonacci_sphere, random_ellipsoid
+
+    if args.kernel == "dlp":
+        pts = random_ellipsoid(args.n)
+        return pts, ellipsoid_normals(pts)
+    return fibonacci_sphere(args.n), None
+
+
+def workload_matrix(args, P, Nrm, h, dtype, dev):
+    """G in the tree's order as a column-major device view (what dh2_compress takes)."""
+    from synth.inputs import dlp_matrix_torch, helmholtz_matrix_torch
+
+    if args.kernel == "dlp":
+        return dlp_matrix_torch(P, Nrm, args.kappa, dtype, dev)
+    return helmholtz_matrix_torch(P, args.kappa, h, dtype, dev).t()  # symmetric: row-major == column-major
 
 
 # --------------------------------------------------------------------------- oracle baseline
@@ -119,14 +141,15 @@ def oracle_sample(args, budget_s: float, seed: int = 0):
     both bases) to a whole-compression time.  Returns (seconds_total_est,
     sample description, threads)."""
     from oracle import dh2_oracle as O
-    from synth import fibonacci_sphere, mean_nn_distance
+    from synth import mean_nn_distance
 
-    pts = fibonacci_sphere(args.n)
+    pts, nrm = workload_points(args)
     tp = O.TreeParams(leaf_size=args.leaf, kappa=args.kappa, eta1=args.eta1, eta2=args.eta2)
     cp = O.CompressParams(eps=args.eps)
     tr = O.build_tree(pts, tp)
     h = mean_nn_distance(pts)
     P = pts[tr.perm]
+    Nrm = nrm[tr.perm] if nrm is not None else None
     F = O.column_sets(tr, "row")
     eps_l = [O.eps_hat(cp) * cp.zeta ** l for l in range(tr.depth + 1)]
     leaf_pairs = [(t, c) for t in range(tr.nclusters()) if tr.is_leaf(t) for c in F[t]]
@@ -141,10 +164,15 @@ def oracle_sample(args, budget_s: float, seed: int = 0):
     def G_block(r0, r1, c0, c1):
         d = P[r0:r1, None, :] - P[None, c0:c1, :]
         r = np.sqrt((d * d).sum(-1))
+        k = args.kappa
         with np.errstate(divide="ignore", invalid="ignore"):
-            g = np.exp(1j * args.kappa * r) / (4.0 * math.pi * r)
+            if Nrm is None:
+                g = np.exp(1j * k * r) / (4.0 * math.pi * r)
+            else:
+                dn = (d * Nrm[None, c0:c1, :]).sum(-1)
+                g = (1.0 - 1j * k * r) * np.exp(1j * k * r) / (4.0 * math.pi * r ** 3) * dn
         ii, jj = np.nonzero(r == 0.0)
-        g[ii, jj] = 1.0 / (4.0 * math.pi * h)
+        g[ii, jj] = 1.0 / (4.0 * math.pi * h) if Nrm is None else 0.5
         return g
 
     done_work, t_used, npairs = 0.0, 0.0, 0
@@ -184,21 +212,20 @@ def run_gpu(args):
     import torch
 
     import paper_1510_07087_gb300 as D
-    from synth import fibonacci_sphere, mean_nn_distance
-    from synth.inputs import helmholtz_matrix_torch
+    from synth import mean_nn_distance
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    pts = fibonacci_sphere(args.n)
+    pts, nrm = workload_points(args)
     h = mean_nn_distance(pts)
     T = D.dh2_tree_build(pts, args.leaf, args.kappa, args.eta1, args.eta2)
     perm = T.perm()
     st = T.stats()
     P = pts[perm]
+    Nrm = nrm[perm] if nrm is not None else None
     cdt = torch.complex64 if args.mode == "fp32" else torch.complex128
     mode = D.MODE_FP32 if args.mode == "fp32" else D.MODE_FP64
-    G = helmholtz_matrix_torch(P, args.kappa, h, cdt, dev)  # symmetric: row-major == column-major
-    Gd = G.t()
+    Gd = workload_matrix(args, P, Nrm, h, cdt, dev)
     stream = torch.cuda.current_stream()
     elem = 8 if args.mode == "fp32" else 16
     in_bytes = elem * args.n * args.n
@@ -241,11 +268,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     matvec_ms = m0.elapsed_time(m1) / 10
     # error against the FP64 matrix (complex128, built the same way)
-    del G
     rel_err = None
     if args.mode == "fp32" and not args.skip_error:
-        G128 = helmholtz_matrix_torch(P, args.kappa, h, torch.complex128, dev)
-        rel_err = D.dh2_error(M, G128.t())
+        G128 = workload_matrix(args, P, Nrm, h, torch.complex128, dev)
+        rel_err = D.dh2_error(M, G128)
         del G128
     elif not args.skip_error:
         rel_err = D.dh2_error(M, Gd)
@@ -367,6 +393,9 @@ def main():
     ap.add_argument("--eta2", type=float, default=1.0)
     ap.add_argument("--mode", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--nearfield", type=int, default=0)
+    ap.add_argument("--kernel", default="slp", choices=["slp", "dlp"],
+                    help="slp: single-layer collocation on the Fibonacci sphere (the headline); "
+                         "dlp: 1/2 I + double layer on a 2:1:1 ellipsoid")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-error", action="store_true")

@@ -127,6 +127,20 @@ __device__ __forceinline__ void cp_async(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Two consecutive complex entries from a 16-byte aligned shared-memory
+// address (one 16-byte load in FP32).
+template <typename T>
+__device__ __forceinline__ void load_c2x2(const C2<T>* p, C2<T>& a, C2<T>& b) {
+  a = p[0];
+  b = p[1];
+}
+template <>
+__device__ __forceinline__ void load_c2x2<float>(const C2<float>* p, C2<float>& a, C2<float>& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = C2<float>{v.x, v.y};
+  b = C2<float>{v.z, v.w};
+}
+
 // Walk e = start, start + step, ... < slow_n * fast_n over a (slow, fast)
 // index pair, e = slow * fast_n + fast, with one division at set-up.
 struct Walk2 {
@@ -990,9 +1004,11 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int cgc[TW];
   __shared__ T cwt[TW];
-  const int LD = P + 1;
-  C2<T>* Qs = reinterpret_cast<C2<T>*>(smem);  // QB columns of Q
-  C2<T>* As = Qs + QB * LD;                    // TW columns of A
+  // row-major tiles, row r of Q's block at Qs[r * LQ] and of A's tile at
+  // As[r * LA] (padded rows of 16-byte multiples)
+  constexpr int LQ = QB + 2, LA = TW + 2;
+  C2<T>* Qs = reinterpret_cast<C2<T>*>(smem);
+  C2<T>* As = Qs + P * LQ;
   const int tid = threadIdx.x;
   const uint64_t tile = tiles[blockIdx.x];
   const uint32_t code = (uint32_t)(tile >> 32);
@@ -1053,14 +1069,14 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
     for (Walk2 it(tid, NT, p); it.g < kb; it.next()) {
       const int r = it.f, qq = it.g;
       const int64_t e = r + (int64_t)(qb + qq) * ldq;
-      if (DH2_IN(a.Qoff[side][pid] + e, c_lim.Q[side], 14, pid)) cp_async<sizeof(C2<T>)>(Qs + qq * LD + r, Qin + e);
-      else Qs[qq * LD + r] = czero<T>();
+      if (DH2_IN(a.Qoff[side][pid] + e, c_lim.Q[side], 14, pid)) cp_async<sizeof(C2<T>)>(Qs + r * LQ + qq, Qin + e);
+      else Qs[r * LQ + qq] = czero<T>();
     }
     if (qb == 0) {
       for (Walk2 it(tid, NT, down ? p : cw); it.g < (down ? cw : p); it.next()) {
         const int r = down ? it.f : it.g;
         const int jj = down ? it.g : it.f;
-        C2<T>* d = As + jj * LD + r;
+        C2<T>* d = As + r * LA + jj;
         if (gen) {
           *d = src.leaf_at(r, cgc[jj], cwt[jj]);
         } else {
@@ -1077,25 +1093,26 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
       for (Walk2 it(tid, NT, down ? p : cw); it.g < (down ? cw : p); it.next()) {
         const int r = down ? it.f : it.g;
         const int jj = down ? it.g : it.f;
-        C2<T>* d = As + jj * LD + r;
+        C2<T>* d = As + r * LA + jj;
         const C2<T> g = *d;
         const T w = cwt[jj];
         *d = C2<T>{g.re * w, side == 0 ? g.im * w : -g.im * w};
       }
     }
     __syncthreads();
-    // 2 x 2 output tiles (columns past kb or cw are read from a clamped
-    // pointer and not stored)
+    // 2 x 2 output tiles
     const int nqt = (kb + 1) >> 1, njt = (cw + 1) >> 1;
     for (int t = tid; t < nqt * njt; t += NT) {
       const int q0 = 2 * (t % nqt), jb = 2 * (t / nqt);
-      const C2<T>* qc0 = Qs + q0 * LD;
-      const C2<T>* qc1 = q0 + 1 < kb ? qc0 + LD : qc0;
-      const C2<T>* ac0 = As + jb * LD;
-      const C2<T>* ac1 = jb + 1 < cw ? ac0 + LD : ac0;
+      // entries past kb or cw are read (finite or not) but never stored
+      const C2<T>* qp = Qs + q0;
+      const C2<T>* ap = As + jb;
       C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
-      for (int r = 0; r < p; ++r) {
-        const C2<T> x0 = qc0[r], x1 = qc1[r], y0 = ac0[r], y1 = ac1[r];
+#pragma unroll 2
+      for (int r = 0; r < p; ++r, qp += LQ, ap += LA) {
+        C2<T> x0, x1, y0, y1;
+        load_c2x2(qp, x0, x1);
+        load_c2x2(ap, y0, y1);
         c00 = cmacc(c00, y0, x0);
         c01 = cmacc(c01, y1, x0);
         c10 = cmacc(c10, y0, x1);
@@ -1170,7 +1187,7 @@ bool prof_read_pair(unsigned long long* out17) {
 
 template <typename T, bool FROM_R>
 void launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
-  const size_t smem = (size_t)(32 + kRTile) * (P + 1) * sizeof(C2<T>);
+  const size_t smem = (size_t)(32 + 2 + kRTile + 2) * P * sizeof(C2<T>);  // row-major Q block and A tile
   auto kern = rq_kernel<T, FROM_R>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kern<<<ntiles, 128, smem, st>>>(args, tiles, P);

@@ -148,6 +148,73 @@ def helmholtz_matrix_torch(points: np.ndarray, kappa: float, h: float, dtype, de
     return M
 
 
+def sphere_normals(points: np.ndarray) -> np.ndarray:
+    """Outward unit normals of points on a sphere centred at the origin."""
+    pts = np.asarray(points, dtype=np.float64)
+    return pts / np.linalg.norm(pts, axis=1, keepdims=True)
+
+
+def ellipsoid_normals(points: np.ndarray, axes=(1.0, 0.5, 0.5)) -> np.ndarray:
+    """Outward unit normals of points on the ellipsoid sum_d (x_d / a_d)^2 = 1."""
+    pts = np.asarray(points, dtype=np.float64)
+    g = pts / np.asarray(axes, dtype=np.float64) ** 2
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def dlp_matrix(points: np.ndarray, normals: np.ndarray, kappa: float, dtype=np.complex128) -> np.ndarray:
+    """Dense collocation matrix of 1/2 I + the Helmholtz double layer potential.
+
+    G[i, j] = (1 - i kappa r) exp(i kappa r) / (4 pi r^3) <x_i - x_j, n(x_j)>
+    with r = |x_i - x_j| for i != j, and G[i, i] = 1/2: the kernel's normal
+    derivative in the second argument, and the identity standing in for the
+    mass matrix of a Galerkin discretisation in a collocation setting.  On a
+    sphere centred at the origin the matrix is symmetric; in general it is
+    not.  It is returned in C order (G[i, j]).
+    """
+    pts = np.asarray(points, dtype=np.float64)
+    nrm = np.asarray(normals, dtype=np.float64)
+    n = pts.shape[0]
+    G = np.empty((n, n), dtype=dtype)
+    for s in range(0, n, 512):
+        blk = pts[s:s + 512]
+        d = blk[:, None, :] - pts[None, :, :]
+        r = np.sqrt((d * d).sum(-1))
+        dn = (d * nrm[None, :, :]).sum(-1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = (1.0 - 1j * kappa * r) * np.exp(1j * kappa * r) / (4.0 * math.pi * r ** 3) * dn
+        rows = np.arange(blk.shape[0])
+        g[rows, s + rows] = 0.5
+        G[s:s + 512] = g.astype(dtype)
+    return G
+
+
+def dlp_matrix_torch(points: np.ndarray, normals: np.ndarray, kappa: float, dtype, device):
+    """The double-layer matrix of `dlp_matrix`, built with torch on a device.
+
+    Returns a torch tensor whose row-major memory is G in column-major order:
+    a view M with M.t()[i, j] = G[i, j] (shape (n, n)).
+    """
+    import torch
+
+    pts = torch.as_tensor(np.asarray(points, dtype=np.float64), device=device)
+    nrm = torch.as_tensor(np.asarray(normals, dtype=np.float64), device=device)
+    n = pts.shape[0]
+    M = torch.empty((n, n), dtype=dtype, device=device)  # M[j, i] = G[i, j]
+    step = 2048
+    for s in range(0, n, step):
+        src = pts[s:s + step]        # columns j of G
+        d = pts[None, :, :] - src[:, None, :]   # d[jj, i] = x_i - x_j
+        r = torch.sqrt((d * d).sum(-1))
+        dn = (d * nrm[s:s + step][:, None, :]).sum(-1)
+        ph = kappa * r
+        e = torch.complex(torch.cos(ph), torch.sin(ph))
+        g = torch.complex(torch.ones_like(r), -ph) * e * (dn / (4.0 * math.pi * r ** 3))
+        rows = torch.arange(src.shape[0], device=device)
+        g[rows, s + rows] = 0.5
+        M[s:s + step] = g.to(dtype)
+    return M.t()
+
+
 def planted_separable_matrix(points: np.ndarray, rank: int = 3, seed: int = SEED) -> np.ndarray:
     """G_ij = sum_p a_p(x_i) * b_p(x_j) with smooth random a_p, b_p (exact rank <= `rank`)."""
     rng = np.random.default_rng(seed)

@@ -20,7 +20,8 @@ import numpy as np
 import pytest
 
 from oracle import dh2_oracle as O
-from synth import fibonacci_sphere, helmholtz_matrix, planted_separable_matrix, random_complex_vectors
+from synth import (dlp_matrix, ellipsoid_normals, fibonacci_sphere, helmholtz_matrix, planted_separable_matrix,
+                   random_complex_vectors, random_ellipsoid)
 
 pytestmark = pytest.mark.gpu
 
@@ -41,10 +42,10 @@ def _colmajor(G: np.ndarray, dtype):
 
 class Case:
     def __init__(self, n, kappa, leaf, eps, mode, eta1=2 * math.sqrt(2), eta2=1.0, G=None, dir_rule=0,
-                 nearfield=0):
+                 nearfield=0, pts=None):
         D = _dev()
         self.D = D
-        pts = fibonacci_sphere(n)
+        pts = fibonacci_sphere(n) if pts is None else pts
         self.tp = O.TreeParams(leaf_size=leaf, kappa=kappa, eta1=eta1, eta2=eta2, dir_rule=dir_rule)
         self.cp = O.CompressParams(eps=eps)
         self.tr = O.build_tree(pts, self.tp)
@@ -260,6 +261,27 @@ def test_fp32_config2_two_tolerances():
         assert max(abs(c.rank[sd][key] - ko) for sd, B in ((0, c.V), (1, c.W)) for key, ko in B.rank.items()) <= 3
         G128 = _colmajor(c.G, torch.complex128)
         assert c.D.dh2_error(c.M, G128) <= eps
+
+
+def _dlp_case(n, kappa, leaf, eps, mode):
+    """Double-layer matrix 1/2 I + G_dlp on an ellipsoid (not symmetric, so the
+    row and column bases are built from different data)."""
+    pts = random_ellipsoid(n)
+    G = dlp_matrix(pts, ellipsoid_normals(pts), kappa)
+    return Case(n, kappa, leaf, eps, mode, G=G, pts=pts)
+
+
+def test_fp64_double_layer_parity():
+    _check_fp64(_dlp_case(2048, 8.0, 32, 1e-4, _dev().MODE_FP64))
+
+
+def test_fp32_double_layer():
+    c = _dlp_case(2048, 8.0, 32, 1e-4, _dev().MODE_FP32)
+    bad, ties, total = _rank_report(c, 1e-3)
+    assert bad <= 0.20 * total, (bad, total)
+    assert max(abs(c.rank[sd][key] - ko) for sd, B in ((0, c.V), (1, c.W)) for key, ko in B.rank.items()) <= 3
+    G128 = _colmajor(c.G, torch.complex128)
+    assert c.D.dh2_error(c.M, G128) <= c.cp.eps
 
 
 def test_status_errors_are_reported():
