@@ -580,8 +580,14 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int l = 0; l <= maxdepth; ++l)
       codes_bytes += align256(4 * nl_codes[l].size()) + align256(8 * nl_tiles[l].size());
   }
+  // per level: the non-leaf codes sorted into row-count classes
+  int64_t nl_max = 0;
+  for (int l = 0; l <= maxdepth; ++l) nl_max = std::max(nl_max, (int64_t)nl_codes[l].size());
+  for (dh2_matrix* M : Ms)
+    for (int l = 0; l <= M->tree->tr.depth; ++l) nl_max = std::max(nl_max, M->tree->tr.dev->nl_code_count[l]);
+  const size_t cls_bytes = align256(4 * 4 * (size_t)std::max<int64_t>(nl_max, 1)) + 256;
   void* scratch = nullptr;
-  DH2_CUDA_TRY(cudaMallocAsync(&scratch, args_bytes + codes_bytes + 256, st));
+  DH2_CUDA_TRY(cudaMallocAsync(&scratch, args_bytes + codes_bytes + cls_bytes + 256, st));
   char* sp = (char*)scratch;
   PairArgs<T>* d_pa = (PairArgs<T>*)sp;
   sp += align256(sizeof(PairArgs<T>) * nprob);
@@ -703,11 +709,33 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #endif
   DH2_PHASE_SYNC("leaf pairs");
   cudaEventRecord(ev[3], st);
-  for (int l = maxdepth; l >= 0; --l) {
-    if (n_nl[l] == 0) continue;
-    launch_pair_kernel<T>(d_pa, d_nl[l], (int)n_nl[l], P_level[l], true, st);
-    launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, st);
-    DH2_PHASE_SYNC("non-leaf pairs");
+  {
+    // the class split needs the sons' ranks: one 16-byte read-back per level
+    uint32_t* d_cls = (uint32_t*)((char*)scratch + args_bytes + codes_bytes);
+    int* d_cnt = (int*)((char*)d_cls + align256(4 * 4 * (size_t)std::max<int64_t>(nl_max, 1)));
+    for (int l = maxdepth; l >= 0; --l) {
+      if (n_nl[l] == 0) continue;
+      const int n = (int)n_nl[l];
+      int cnt[4] = {0, 0, 0, 0};
+      cudaError_t e = cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), st);
+      launch_classify<T>(d_pa, d_nl[l], n, d_cls, d_cnt, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        cnt[0] = cnt[1] = cnt[2] = 0;
+        cnt[3] = -1;  // fall back to one launch at the level's capacity
+      }
+      if (cnt[3] < 0) {
+        launch_pair_kernel<T>(d_pa, d_nl[l], n, P_level[l], true, st);
+      } else {
+        const int Pc[4] = {32, 48, 64, P_level[l]};
+        for (int c = 0; c < 4; ++c)
+          if (cnt[c] > 0) launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, cnt[c], std::min(Pc[c], std::max(P_level[l], 2)), true, st);
+      }
+      launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, st);
+      DH2_PHASE_SYNC("non-leaf pairs");
+    }
   }
   cudaEventRecord(ev[4], st);
   for (dh2_matrix* M : Ms) {

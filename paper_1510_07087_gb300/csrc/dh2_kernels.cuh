@@ -87,6 +87,12 @@ template <typename T>
 void launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int ntiles, int P, bool from_r,
                       cudaStream_t st);
 
+// Non-leaf codes of one level split by the row count of their Ghat (from the
+// sons' ranks): out = 4 segments of n codes, counts[4] zeroed by the caller.
+template <typename T>
+void launch_classify(const PairArgs<T>* args_dev, const uint32_t* codes, int n, uint32_t* out, int* counts,
+                     cudaStream_t st);
+
 // Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 17 values.
 void prof_reset_pair();
 bool prof_read_pair(unsigned long long* out17);

@@ -1185,6 +1185,23 @@ bool prof_read_pair(unsigned long long* out17) {
 #endif
 }
 
+// Non-leaf pairs of one level by row count p = k_t1c' + k_t2c' (known only
+// once the sons' ranks are): class 0..3 for p <= 32, <= 48, <= 64, more.
+// out holds 4 segments of n codes; counts[c] the class sizes.
+template <typename T>
+__global__ void classify_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, int n,
+                                uint32_t* __restrict__ out, int* __restrict__ counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t code = codes[i];
+  const PairArgs<T>& a = args[code >> kCodeProbShift];
+  const int side = (int)((code >> kCodeSideShift) & 1u);
+  const int pid = (int)(code & kCodePairMask);
+  const int p = a.rank[side][a.son[side][2 * pid]] + a.rank[side][a.son[side][2 * pid + 1]];
+  const int cls = p <= 32 ? 0 : p <= 48 ? 1 : p <= 64 ? 2 : 3;
+  out[(int64_t)cls * n + atomicAdd(&counts[cls], 1)] = code;
+}
+
 template <typename T, bool FROM_R>
 void launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
   const size_t smem = (size_t)(32 + 2 + kRTile + 2) * P * sizeof(C2<T>);  // row-major Q block and A tile
@@ -1200,6 +1217,14 @@ void launch_rq_kernel(const PairArgs<T>* args, const uint64_t* tiles, int ntiles
   if (from_r) launch_rq<T, true>(args, tiles, ntiles, P, st);
   else launch_rq<T, false>(args, tiles, ntiles, P, st);
 }
+template <typename T>
+void launch_classify(const PairArgs<T>* args, const uint32_t* codes, int n, uint32_t* out, int* counts,
+                     cudaStream_t st) {
+  if (n > 0) classify_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(args, codes, n, out, counts);
+}
+template void launch_classify<float>(const PairArgs<float>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
+template void launch_classify<double>(const PairArgs<double>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
+
 template void launch_rq_kernel<float>(const PairArgs<float>*, const uint64_t*, int, int, bool, cudaStream_t);
 template void launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*, int, int, bool, cudaStream_t);
 
@@ -1213,7 +1238,9 @@ void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
     else if (P <= 64) launch_one<T, 64, false, 256>(args, codes, nblocks, P, st);
     else launch_one<T, 128, false, 256>(args, codes, nblocks, P, st);
   } else {
-    if (P <= 64) launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
+    if (P <= 32) launch_one<T, 32, true, 128>(args, codes, nblocks, P, st);
+    else if (P <= 48) launch_one<T, 48, true, 192>(args, codes, nblocks, P, st);
+    else if (P <= 64) launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
     else launch_one<T, 128, true, 256>(args, codes, nblocks, P, st);
   }
 }
