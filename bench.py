@@ -349,19 +349,7 @@ def run_gpu(args):
     t_roof_ms = in_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
     step_roof = {"bound": "hbm", "t_roof_ms": t_roof_ms, "frac": t_roof_ms / ms,
                  "note": "one read of all of G at the measured copy bandwidth, against the whole step"}
-    lv = T.clusters()["level"]
-    nl_levels = set()
-    col_nl_levels = set()
-    for sd in (0, 1):
-        pr = T.pairs(sd)
-        for c, lf in zip(pr["cluster"], pr["leaf"]):
-            if not lf:
-                nl_levels.add(int(lv[c]))
-                if sd == 1:
-                    col_nl_levels.add(int(lv[c]))
-    # norms, leaf factors + R, (factors + R) per non-leaf level, expansion
-    # per level with non-leaf column pairs, projection
-    launches = 4 + 2 * len(nl_levels) + len(col_nl_levels)
+    launches = M.launch_count()  # kernels the library launched for the last compression
     line = {
         "metric": "compression wall time & input GB/s at n=32768, kappa=32, eps=1e-4; rel. error vs FP64",
         "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,

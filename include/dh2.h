@@ -238,6 +238,10 @@ dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts);
  * [2] leaf R = Q^* A, [3] level steps (factors and R), [4] expansion,
  * [5] projection. */
 dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms6);
+/* Number of kernels launched by the last dh2_compress (or batched call) that
+ * produced M (host int32 out). Instrumentation only: the paper has no
+ * counterpart. */
+dh2_status dh2_matrix_launch_count(const dh2_matrix* M, int32_t* launches);
 
 const char* dh2_status_string(dh2_status s);
 /* Library version string. */

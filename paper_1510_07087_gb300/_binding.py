@@ -79,6 +79,7 @@ SIGNATURES = [
     ("dh2_matrix_coupling", c_int32, [c_void_p, c_int64, c_void_p, c_int64, POINTER(c_int32), POINTER(c_int32)]),
     ("dh2_storage", c_int32, [c_void_p, POINTER(c_double), c_void_p]),
     ("dh2_matrix_phase_ms", c_int32, [c_void_p, c_void_p]),
+    ("dh2_matrix_launch_count", c_int32, [c_void_p, c_void_p]),
     ("dh2_status_string", ctypes.c_char_p, [c_int32]),
     ("dh2_version", ctypes.c_char_p, []),
 ]
@@ -269,6 +270,11 @@ class Matrix:
         d = {k: float(v) for k, v in zip(keys, parts)}
         d["total"] = float(tot.value)
         return d
+
+    def launch_count(self) -> int:
+        out = c_int32(0)
+        _check(_lib().dh2_matrix_launch_count(self.handle, byref(out)), "dh2_matrix_launch_count")
+        return int(out.value)
 
     def phase_ms(self) -> np.ndarray:
         out = np.zeros(6, dtype=np.float32)

@@ -105,6 +105,7 @@ struct dh2_matrix {
   bool v_expanded = false;
   std::vector<double> eps2_h, zpow_h;
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  int32_t launches = 0;  // kernels launched by the last compression (shared by a batch)
   // matrix-free mode
   int gen = 0;
   double* pts = nullptr;  // device, permuted order
@@ -673,11 +674,16 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   }
 #endif
   cudaEventRecord(ev[0], st);
+  int nlaunch = 0;  // kernels launched by this compression (counted where they are issued)
   launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
+  nlaunch += n_norm > 0;
   for (dh2_matrix* M : Ms)
     for (int sd = 0; sd < 2; ++sd)
+    {
       launch_colw<T>(M->tree->tr.dev->gblk[sd], M->invw, (T*)M->colw[sd],
                      (int64_t)M->tree->tr.side[sd].gcol.size(), st);
+      nlaunch += !M->tree->tr.side[sd].gcol.empty();
+    }
   DH2_PHASE_SYNC("norms_near");
   cudaEventRecord(ev[1], st);
 #ifdef DH2_PROFILE
@@ -685,11 +691,14 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #endif
   for (int c = 0; c < kLeafClasses; ++c) {
     const int64_t nc = cls_begin[c + 1] - cls_begin[c];
-    if (nc > 0)
+    if (nc > 0) {
       launch_pair_kernel<T>(d_pa, d_leaf + cls_begin[c], (int)nc, even_up(std::max(2, cls_maxm[c])), false, st);
+      ++nlaunch;
+    }
   }
   cudaEventRecord(ev[2], st);
   launch_rq_kernel<T>(d_pa, d_ltiles, (int)n_ltiles, P_leaf, false, st);
+  nlaunch += n_ltiles > 0;
 #ifdef DH2_PROFILE
   {
     cudaStreamSynchronize(st);
@@ -719,6 +728,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       int cnt[4] = {0, 0, 0, 0};
       cudaError_t e = cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), st);
       launch_classify<T>(d_pa, d_nl[l], n, d_cls, d_cnt, st);
+      ++nlaunch;
       if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) {
@@ -728,12 +738,18 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       }
       if (cnt[3] < 0) {
         launch_pair_kernel<T>(d_pa, d_nl[l], n, P_level[l], true, st);
+        ++nlaunch;
       } else {
         const int Pc[4] = {32, 48, 64, P_level[l]};
         for (int c = 0; c < 4; ++c)
-          if (cnt[c] > 0) launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, cnt[c], std::min(Pc[c], std::max(P_level[l], 2)), true, st);
+          if (cnt[c] > 0) {
+            launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, cnt[c], std::min(Pc[c], std::max(P_level[l], 2)),
+                                  true, st);
+            ++nlaunch;
+          }
       }
       launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, st);
+      nlaunch += n_nltiles[l] > 0;
       DH2_PHASE_SYNC("non-leaf pairs");
     }
   }
@@ -744,7 +760,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     SideView<T> Wv = side_view<T>(tr, M, 1);
     for (int l = tr.depth; l >= 0; --l) {
       const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
-      if (e > b) launch_expand<T>(Wv, D->iota[1] + b, (int)(e - b), st);
+      if (e > b) {
+        launch_expand<T>(Wv, D->iota[1] + b, (int)(e - b), st);
+        ++nlaunch;
+      }
       DH2_PHASE_SYNC("expand");
     }
   }
@@ -765,6 +784,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     pj.S = (C2<T>*)M->S;
     pj.Soff = D->Soff;
     launch_project<T>(pj, (int)D->nadm, st);
+    nlaunch += D->nadm > 0;
     DH2_PHASE_SYNC("project");
   }
   cudaEventRecord(ev[6], st);
@@ -778,7 +798,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   float ph[6] = {0, 0, 0, 0, 0, 0};
   for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&ph[i], ev[i], ev[i + 1]);
   for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
-  for (dh2_matrix* M : Ms) std::memcpy(M->phase_ms, ph, sizeof(ph));
+  for (dh2_matrix* M : Ms) {
+    std::memcpy(M->phase_ms, ph, sizeof(ph));
+    M->launches = nlaunch;
+  }
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return DH2_ECUDA;
 #ifdef DH2_CHECK
   {
@@ -1403,6 +1426,12 @@ dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts) {
     if (parts) parts[i] = pr[i];
   }
   *total = s;
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_launch_count(const dh2_matrix* M, int32_t* launches) {
+  if (!M || !launches) return DH2_EINVAL;
+  *launches = M->launches;
   return DH2_OK;
 }
 
