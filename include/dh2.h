@@ -173,6 +173,17 @@ dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, con
  * result accepts G_ref = NULL: the reference is then generated in FP64. */
 dh2_status dh2_compress_kernel(const dh2_tree* tree, const double* pts_xyz, double kappa, double diag,
                                const dh2_compress_params* params, void* stream, dh2_matrix** out);
+
+/* Matrix-free compression of the double-layer collocation matrix of the
+ * paper's second experiment (Section 7, "DLP matrix"):
+ * G_ij = (1 - i kappa r) exp(i kappa r) / (4 pi r^3) <x_i - x_j, n(x_j)>,
+ * r = |x_i - x_j|, and G_ii = 1/2 (the identity standing in for the mass
+ * matrix of 1/2 M + G_dlp).  normals_xyz: host, n x 3 row-major unit normals
+ * in the caller's order, copied during the call.  Otherwise as
+ * dh2_compress_kernel; dh2_error with G_ref = NULL generates this matrix. */
+dh2_status dh2_compress_kernel_dlp(const dh2_tree* tree, const double* pts_xyz, const double* normals_xyz,
+                                   double kappa, const dh2_compress_params* params, void* stream,
+                                   dh2_matrix** out);
 void dh2_matrix_free(dh2_matrix* M);
 
 /* y = G~ x for the compressed matrix (Section 4: forward transformation,

@@ -67,6 +67,8 @@ SIGNATURES = [
                                        c_void_p, c_void_p]),
     ("dh2_compress_kernel", c_int32, [c_void_p, c_void_p, c_double, c_double, POINTER(CompressParams), c_void_p,
                                       POINTER(c_void_p)]),
+    ("dh2_compress_kernel_dlp", c_int32, [c_void_p, c_void_p, c_void_p, c_double, POINTER(CompressParams),
+                                          c_void_p, POINTER(c_void_p)]),
     ("dh2_matrix_free", None, [c_void_p]),
     ("dh2_matvec", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_matvec_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
@@ -326,6 +328,22 @@ def dh2_compress_kernel(tree: Tree, points: np.ndarray, kappa: float, diag: floa
     h = c_void_p()
     _check(_lib().dh2_compress_kernel(tree.handle, _ptr(pts), float(kappa), float(diag), byref(p),
                                       c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress_kernel")
+    return Matrix(h.value, tree, mode, None)
+
+
+def dh2_compress_kernel_dlp(tree: Tree, points: np.ndarray, normals: np.ndarray, kappa: float, eps: float = 1e-4,
+                            zeta: float = 2.0 / 3.0, err_mode: int = 0, mode: int = MODE_FP32, max_sweeps: int = 0,
+                            stream=None) -> Matrix:
+    """Matrix-free compression of 1/2 I + the double-layer collocation matrix of `points` with unit
+    `normals` (both caller order)."""
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    nrm = np.ascontiguousarray(normals, dtype=np.float64)
+    if nrm.shape != pts.shape:
+        raise ValueError("normals must have the shape of points")
+    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), 0, int(max_sweeps))
+    h = c_void_p()
+    _check(_lib().dh2_compress_kernel_dlp(tree.handle, _ptr(pts), _ptr(nrm), float(kappa), byref(p),
+                                          c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress_kernel_dlp")
     return Matrix(h.value, tree, mode, None)
 
 

@@ -42,6 +42,8 @@ struct Tree::Dev {
       *rowcap[2];
   int64_t *cmoff[2], *Roff[2], *Qoff[2], *Xoff[2], *hoff[2];
   int32_t *gcol[2], *gblk[2];
+  int64_t* seg_dst[2];  // column-map segments (expanded into gcol/gblk on upload)
+  int32_t *seg_col0[2], *seg_w[2], *seg_blk[2];
   int32_t* iota[2];        // 0..npairs-1
   int32_t* leaf_list[2];   // leaf pair ids
   // blocks
@@ -111,6 +113,7 @@ struct dh2_matrix {
   double* pts = nullptr;  // device, permuted order
   double kappa = 0.0, diag = 0.0;
   std::vector<double> pts_h;
+  double* nrm = nullptr;  // device normals after the points (double layer), or NULL
 };
 
 namespace {
@@ -238,8 +241,13 @@ dh2_status upload_tree(Tree& tr) {
     add64(std::move(qo), &D->Qoff[sd]);
     add64(std::move(xo), &D->Xoff[sd]);
     add64(std::move(ho), &D->hoff[sd]);
-    add32(std::vector<int32_t>(S.gcol), &D->gcol[sd]);
-    add32(std::vector<int32_t>(S.gblk), &D->gblk[sd]);
+    // column maps: allocated here, expanded from the segments after the upload
+    bufs.push_back({nullptr, 4 * (size_t)S.nleafcols, (void**)&D->gcol[sd]});
+    bufs.push_back({nullptr, 4 * (size_t)S.nleafcols, (void**)&D->gblk[sd]});
+    add64(std::vector<int64_t>(S.seg_dst), &D->seg_dst[sd]);
+    add32(std::vector<int32_t>(S.seg_col0), &D->seg_col0[sd]);
+    add32(std::vector<int32_t>(S.seg_w), &D->seg_w[sd]);
+    add32(std::vector<int32_t>(S.seg_blk), &D->seg_blk[sd]);
   }
   // blocks
   const int64_t nb = (int64_t)tr.blocks.size();
@@ -371,13 +379,22 @@ dh2_status upload_tree(Tree& tr) {
   size_t off = 0;
   for (auto& b : bufs) {
     *b.dst = (char*)D->arena + off;
-    if (b.bytes && cudaMemcpy(*b.dst, b.src, b.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (b.bytes && b.src && cudaMemcpy(*b.dst, b.src, b.bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
       cudaFree(D->arena);
       delete D;
       return DH2_ECUDA;
     }
     off += align256(std::max<size_t>(b.bytes, 4));
+  }
+  for (int sd = 0; sd < 2; ++sd)
+    launch_colmap_expand(D->seg_dst[sd], D->seg_col0[sd], D->seg_w[sd], D->seg_blk[sd],
+                         (int64_t)tr.side[sd].seg_dst.size(), D->gcol[sd], D->gblk[sd], nullptr);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(D->arena);
+    delete D;
+    return DH2_ECUDA;
   }
   tr.dev = D;
   return DH2_OK;
@@ -459,6 +476,7 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   na.near_off = D->near_off;
   na.copy = M->nearfield_copy;
   na.pts = M->pts;
+  na.nrm = M->nrm;
   na.kappa = M->kappa;
   na.diag = M->diag;
   na.gen = M->gen;
@@ -489,6 +507,7 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   pa.max_sweeps = cp.max_sweeps > 0 ? cp.max_sweeps : 30;
   pa.status = M->status;
   pa.pts = M->pts;
+  pa.nrm = M->nrm;
   pa.kappa = M->kappa;
   pa.diag = M->diag;
   pa.gen = M->gen;
@@ -662,7 +681,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         lim.Q[sd] = std::max(lim.Q[sd], D->Q_elems[sd]);
         lim.X[sd] = std::max(lim.X[sd], D->X_elems[sd]);
         lim.npairs[sd] = std::max(lim.npairs[sd], D->npairs[sd]);
-        lim.ncol[sd] = std::max(lim.ncol[sd], (int64_t)tr.side[sd].gcol.size());
+        lim.ncol[sd] = std::max(lim.ncol[sd], tr.side[sd].nleafcols);
       }
       lim.S = std::max(lim.S, D->S_elems);
       lim.near = std::max<int64_t>(lim.near, M->nearfield_copy ? D->near_elems : 0);
@@ -681,8 +700,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int sd = 0; sd < 2; ++sd)
     {
       launch_colw<T>(M->tree->tr.dev->gblk[sd], M->invw, (T*)M->colw[sd],
-                     (int64_t)M->tree->tr.side[sd].gcol.size(), st);
-      nlaunch += !M->tree->tr.side[sd].gcol.empty();
+                     M->tree->tr.side[sd].nleafcols, st);
+      nlaunch += M->tree->tr.side[sd].nleafcols > 0;
     }
   DH2_PHASE_SYNC("norms_near");
   cudaEventRecord(ev[1], st);
@@ -995,7 +1014,7 @@ namespace {
 // given: entries generated in the kernels).
 dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
                           double kappa, double diag, const dh2_compress_params* params, void* stream,
-                          dh2_matrix** out) {
+                          dh2_matrix** out, const double* nrm_host = nullptr) {
   if (!out) return DH2_EINVAL;
   *out = nullptr;
   if (!Tc || !params || (!G && !pts_host)) return DH2_EINVAL;
@@ -1056,9 +1075,9 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   sz[ns++] = align256(8 * nl);
   sz[ns++] = align256(16);
   sz[ns++] = align256(16);
-  sz[ns++] = align256(gen ? 24 * (size_t)tr.n : 0);
-  sz[ns++] = align256(es / 2 * tr.side[0].gcol.size());
-  sz[ns++] = align256(es / 2 * tr.side[1].gcol.size());
+  sz[ns++] = align256(gen ? (nrm_host ? 48 : 24) * (size_t)tr.n : 0);  // points (and normals)
+  sz[ns++] = align256(es / 2 * (size_t)tr.side[0].nleafcols);
+  sz[ns++] = align256(es / 2 * (size_t)tr.side[1].nleafcols);
   size_t total = 0;
   for (int i = 0; i < ns; ++i) total += sz[i];
   if (cudaMallocAsync(&M->arena, total, M->stream) != cudaSuccess) {
@@ -1078,6 +1097,7 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   }
   if (!M->nearfield_copy) M->near = nullptr;
   if (!gen) M->pts = nullptr;
+  M->nrm = gen && nrm_host ? M->pts + 3 * (size_t)tr.n : nullptr;
   // tolerances eps_l = eps_hat zeta^l (Remark "Error control")
   const double eh =
       cp.err_mode == 0 ? cp.eps * std::sqrt(1.0 - 2.0 * cp.zeta * cp.zeta) / std::sqrt(2.0) : cp.eps;
@@ -1095,11 +1115,15 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   if (ce == cudaSuccess) ce = cudaMemsetAsync(M->rank[0], 0, 4 * D->npairs[0], M->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(M->rank[1], 0, 4 * D->npairs[1], M->stream);
   if (ce == cudaSuccess && gen) {
-    // points in the tree's permuted order
-    M->pts_h.resize(3 * (size_t)tr.n);
+    // points (then normals) in the tree's permuted order
+    const size_t n3 = 3 * (size_t)tr.n;
+    M->pts_h.resize(nrm_host ? 2 * n3 : n3);
     for (int64_t i = 0; i < tr.n; ++i)
-      for (int c = 0; c < 3; ++c) M->pts_h[3 * i + c] = pts_host[3 * tr.perm[i] + c];
-    ce = cudaMemcpyAsync(M->pts, M->pts_h.data(), 24 * (size_t)tr.n, cudaMemcpyHostToDevice, M->stream);
+      for (int c = 0; c < 3; ++c) {
+        M->pts_h[3 * i + c] = pts_host[3 * tr.perm[i] + c];
+        if (nrm_host) M->pts_h[n3 + 3 * i + c] = nrm_host[3 * tr.perm[i] + c];
+      }
+    ce = cudaMemcpyAsync(M->pts, M->pts_h.data(), 8 * M->pts_h.size(), cudaMemcpyHostToDevice, M->stream);
   }
   if (ce != cudaSuccess) {
     cudaGetLastError();
@@ -1112,9 +1136,9 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
 
 dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
                          double kappa, double diag, const dh2_compress_params* params, void* stream,
-                         dh2_matrix** out) {
+                         dh2_matrix** out, const double* nrm_host = nullptr) {
   dh2_matrix* M = nullptr;
-  dh2_status s = prepare_matrix(Tc, G, dtype, ld, pts_host, kappa, diag, params, stream, &M);
+  dh2_status s = prepare_matrix(Tc, G, dtype, ld, pts_host, kappa, diag, params, stream, &M, nrm_host);
   if (s != DH2_OK) return s;
   std::vector<dh2_matrix*> Ms{M};
   s = params->mode == DH2_MODE_FP32 ? run_compress<float>(Ms, *params, (cudaStream_t)stream)
@@ -1148,6 +1172,16 @@ dh2_status dh2_compress_kernel(const dh2_tree* Tc, const double* pts_xyz, double
   }
   const dh2_dtype dt = params->mode == DH2_MODE_FP32 ? DH2_C64 : DH2_C128;
   return compress_impl(Tc, nullptr, dt, 0, pts_xyz, kappa, diag, params, stream, out);
+}
+
+dh2_status dh2_compress_kernel_dlp(const dh2_tree* Tc, const double* pts_xyz, const double* normals_xyz, double kappa,
+                                   const dh2_compress_params* params, void* stream, dh2_matrix** out) {
+  if (!pts_xyz || !normals_xyz || !params) {
+    if (out) *out = nullptr;
+    return DH2_EINVAL;
+  }
+  const dh2_dtype dt = params->mode == DH2_MODE_FP32 ? DH2_C64 : DH2_C128;
+  return compress_impl(Tc, nullptr, dt, 0, pts_xyz, kappa, 0.5, params, stream, out, normals_xyz);
 }
 
 dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, const void* const* G,
@@ -1267,6 +1301,7 @@ dh2_status run_error(dh2_matrix* M, const void* Gref, dh2_dtype rdt, int64_t ldr
   a.G = (const C2<T>*)M->G;
   a.ld = M->ld;
   a.pts = M->pts;
+  a.nrm = M->nrm;
   a.kappa = M->kappa;
   a.diag = M->diag;
   a.ref_gen = Gref == nullptr ? 1 : 0;

@@ -62,10 +62,14 @@ struct Side {
   std::vector<std::vector<int64_t>> nonleaf_by_level;  // per level l: non-leaf pair ids
   std::vector<int64_t> block_pair;              // per block: pair id of this side (-1 if inadmissible)
   std::vector<int64_t> block_off;               // per block: column offset of the block in its own pair
-  // leaf column maps (concatenated over leaf pairs): G index of the column and block id
+  // leaf column maps (concatenated over leaf pairs): G index of the column and
+  // block id, kept as segments (one per block of a leaf pair's F_tc, in column
+  // order) and expanded on the device when the tree is uploaded
   std::vector<int64_t> leaf_colmap_off;         // per pair (only leaf pairs meaningful), npairs+1
-  std::vector<int32_t> gcol;
-  std::vector<int32_t> gblk;
+  std::vector<int64_t> seg_dst;                 // per segment: first entry in the column map
+  std::vector<int32_t> seg_col0;                // first column of G (the other cluster's start)
+  std::vector<int32_t> seg_w;                   // number of columns
+  std::vector<int32_t> seg_blk;                 // block id
   int64_t ncols_total = 0, nleafcols = 0;
 };
 

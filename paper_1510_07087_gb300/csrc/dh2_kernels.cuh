@@ -40,37 +40,54 @@ struct PairArgs {
   const double* eps2;                 // per level eps_l^2
   int32_t max_sweeps;
   uint32_t* status;
-  // matrix-free mode: entries generated from points (permuted order, 3 doubles each)
+  // matrix-free mode: entries generated from points (permuted order, 3 doubles
+  // each) and, for the double layer, their normals (NULL for the single layer)
   const double* pts;
+  const double* nrm;
   double kappa;
   double diag;
   int32_t gen;
 };
 
-// Entry G_ij of the Helmholtz collocation matrix, Eq. (helmholtz):
-// exp(i kappa r) / (4 pi r), r = |x_i - x_j|, with `diag` on the diagonal.
-// Distances and the phase reduction are formed in FP64; the FP32 variant
-// evaluates sin/cos of the reduced phase (|phase| <= pi) in FP32.
+// Entry G_ij generated from the points, with `diag` on the diagonal:
+//  - nrm == NULL: the Helmholtz single layer of Eq. (helmholtz),
+//    exp(i kappa r) / (4 pi r), r = |x_i - x_j|;
+//  - otherwise the double layer of Section 7 ("DLP matrix"),
+//    (1 - i kappa r) exp(i kappa r) / (4 pi r^3) <x_i - x_j, n(x_j)>, with
+//    nrm the unit normals (3 doubles per point, same order as pts).
+// Distances, <x_i - x_j, n_j> and the phase reduction are formed in FP64; the
+// FP32 variant evaluates sin/cos of the reduced phase (|phase| <= pi) in FP32.
 template <typename T>
-__device__ __forceinline__ C2<T> helmholtz_entry(const double* pts, int64_t i, int64_t j, double kappa,
-                                                 double diag) {
+__device__ __forceinline__ C2<T> kernel_entry(const double* pts, const double* nrm, int64_t i, int64_t j,
+                                              double kappa, double diag) {
   if (i == j) return C2<T>{(T)diag, T(0)};
   const double dx = pts[3 * i] - pts[3 * j];
   const double dy = pts[3 * i + 1] - pts[3 * j + 1];
   const double dz = pts[3 * i + 2] - pts[3 * j + 2];
   const double r = sqrt(dx * dx + dy * dy + dz * dz);
+  // single layer: scale 1/(4 pi r); double layer: <x_i - x_j, n_j>/(4 pi r^3)
+  // times (1 - i kappa r)
+  double scale;
+  double kr = 0.0;
+  if (nrm) {
+    const double dn = dx * nrm[3 * j] + dy * nrm[3 * j + 1] + dz * nrm[3 * j + 2];
+    scale = dn / (12.566370614359172 * r * r * r);
+    kr = kappa * r;
+  } else {
+    scale = 1.0 / (12.566370614359172 * r);
+  }
   if (sizeof(T) == 8) {
     double sn, cs;
     sincos(kappa * r, &sn, &cs);
-    const double inv = 1.0 / (12.566370614359172 * r);
-    return C2<T>{(T)(cs * inv), (T)(sn * inv)};
+    // (cs + i sn)(1 - i kr) = cs + kr sn + i (sn - kr cs)
+    return C2<T>{(T)((cs + kr * sn) * scale), (T)((sn - kr * cs) * scale)};
   } else {
     double th = kappa * r * 0.31830988618379067;  // phase / pi
     th -= 2.0 * rint(0.5 * th);                    // reduced to [-1, 1]
     float sn, cs;
     sincospif((float)th, &sn, &cs);
-    const float inv = 1.0f / (12.566370614359172f * (float)r);
-    return C2<T>{(T)(cs * inv), (T)(sn * inv)};
+    const float krf = (float)kr, sc = (float)scale;
+    return C2<T>{(T)((cs + krf * sn) * sc), (T)((sn - krf * cs) * sc)};
   }
 }
 

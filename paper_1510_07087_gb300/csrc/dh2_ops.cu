@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
       double acc = 0.0;
       for (int64_t e = lane; e < (int64_t)mt * ms; e += 32) {
         const int r = (int)(e % mt), j = (int)(e / mt);
-        const C2<T> g = helmholtz_entry<T>(a.pts, t0 + r, s0 + j, a.kappa, a.diag);
+        const C2<T> g = kernel_entry<T>(a.pts, a.nrm, t0 + r, s0 + j, a.kappa, a.diag);
         acc += (double)g.re * g.re + (double)g.im * g.im;
       }
       const double tot = warp_sum(acc);
@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
       C2<T>* out = a.near + a.near_off[b];
       for (int64_t e = lane; e < (int64_t)mt * ms; e += 32) {
         const int r = (int)(e % mt), j = (int)(e / mt);
-        if (DH2_IN(a.near_off[b] + e, c_lim.near, 21, b)) out[e] = helmholtz_entry<T>(a.pts, t0 + r, s0 + j, a.kappa, a.diag);
+        if (DH2_IN(a.near_off[b] + e, c_lim.near, 21, b))
+          out[e] = kernel_entry<T>(a.pts, a.nrm, t0 + r, s0 + j, a.kappa, a.diag);
       }
     }
     return;
@@ -441,7 +442,7 @@ __global__ void mv_near(MvArgs<T> a, const int32_t* blocks, int nrhs, const C2<T
 template <typename T, typename RT>
 __device__ __forceinline__ C2<double> ref_entry(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int64_t i,
                                                 int64_t j) {
-  if (a.ref_gen) return helmholtz_entry<double>(a.pts, i, j, a.kappa, a.diag);
+  if (a.ref_gen) return kernel_entry<double>(a.pts, a.nrm, i, j, a.kappa, a.diag);
   const C2<RT> g = Gref[i + j * ldr];
   return C2<double>{(double)g.re, (double)g.im};
 }
@@ -578,6 +579,26 @@ template <typename T, typename RT>
 void launch_error(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int nblocks, double* acc,
                   cudaStream_t st) {
   if (nblocks > 0) error_kernel<T, RT><<<nblocks, 256, 0, st>>>(a, Gref, ldr, acc);
+}
+
+// Column maps from their segments: one warp per segment writes the global
+// column index and the block id of each of the segment's w columns.
+__global__ void colmap_expand_kernel(const int64_t* __restrict__ dst, const int32_t* __restrict__ col0,
+                                     const int32_t* __restrict__ w, const int32_t* __restrict__ blk, int64_t nseg,
+                                     int32_t* __restrict__ gcol, int32_t* __restrict__ gblk) {
+  const int64_t sg = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (sg >= nseg) return;
+  const int64_t d = dst[sg];
+  const int32_t c0 = col0[sg], b = blk[sg];
+  for (int j = lane; j < w[sg]; j += 32) {
+    gcol[d + j] = c0 + j;
+    gblk[d + j] = b;
+  }
+}
+void launch_colmap_expand(const int64_t* dst, const int32_t* col0, const int32_t* w, const int32_t* blk, int64_t nseg,
+                          int32_t* gcol, int32_t* gblk, cudaStream_t st) {
+  if (nseg > 0) colmap_expand_kernel<<<(unsigned)((nseg + 7) / 8), 256, 0, st>>>(dst, col0, w, blk, nseg, gcol, gblk);
 }
 
 // Per-column weights of a column map: colw[j] = 1/omega_b for the block b of

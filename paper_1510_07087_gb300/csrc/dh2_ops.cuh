@@ -41,6 +41,7 @@ struct NormsArgs {
   const int64_t* near_off;
   int copy;
   const double* pts;  // matrix-free mode
+  const double* nrm;  // matrix-free double layer: normals (NULL: single layer)
   double kappa;
   double diag;
   int gen;
@@ -100,11 +101,16 @@ struct ErrArgs {
   const C2<T>* G;
   int64_t ld;
   const double* pts;  // reference generated from points (FP64) when ref_gen
+  const double* nrm;  // and normals for the double layer (NULL: single layer)
   double kappa;
   double diag;
   int ref_gen;
 };
 
+// Leaf column maps (global column, block id) from their segments (dst, first
+// column, width, block)
+void launch_colmap_expand(const int64_t* dst, const int32_t* col0, const int32_t* w, const int32_t* blk, int64_t nseg,
+                          int32_t* gcol, int32_t* gblk, cudaStream_t st);
 // colw[j] = 1/omega of the block of column j of a column map (n entries)
 template <typename T>
 void launch_colw(const int32_t* gblk, const double* invw, T* colw, int64_t n, cudaStream_t st);

@@ -169,6 +169,7 @@ struct Source {
   const T* colw;
   int64_t cmo;
   const double* pts;  // matrix-free mode
+  const double* nrm;  // double layer: normals (NULL: single layer)
   double kappa, diag;
   int gen;
   // non-leaf
@@ -206,8 +207,8 @@ struct Source {
   // leaf: element (r, j) given column j's global index gc and weight w
   __device__ __forceinline__ C2<T> leaf_at(int r, int gc, T w) const {
     if (gen) {
-      C2<T> g = side == 0 ? helmholtz_entry<T>(pts, r0 + r, gc, kappa, diag)
-                          : helmholtz_entry<T>(pts, gc, r0 + r, kappa, diag);
+      C2<T> g = side == 0 ? kernel_entry<T>(pts, nrm, r0 + r, gc, kappa, diag)
+                          : kernel_entry<T>(pts, nrm, gc, r0 + r, kappa, diag);
       return C2<T>{g.re * w, side == 0 ? g.im * w : -g.im * w};
     }
     if (side == 0) {
@@ -382,6 +383,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     src.G = a.G;
     src.ld = a.ld;
     src.pts = a.pts;
+    src.nrm = a.nrm;
     src.kappa = a.kappa;
     src.diag = a.diag;
     src.gen = a.gen;
@@ -1047,6 +1049,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
     src.G = a.G;
     src.ld = a.ld;
     src.pts = a.pts;
+    src.nrm = a.nrm;
     src.kappa = a.kappa;
     src.diag = a.diag;
     src.gen = a.gen;

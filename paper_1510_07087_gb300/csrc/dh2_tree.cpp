@@ -258,28 +258,32 @@ void build_side(Tree& tr, int side) {
       off += width(b);
     }
   }
-  // leaf column maps: expand the father segments recursively
+  // leaf column maps: one segment per block, the father segments expanded
+  // recursively (the per-column entries are written on the device)
   S.leaf_colmap_off.assign(S.pairs.size() + 1, 0);
-  S.gcol.clear();
-  S.gblk.clear();
+  S.seg_dst.clear();
+  S.seg_col0.clear();
+  S.seg_w.clear();
+  S.seg_blk.clear();
+  int64_t pos = 0;
   std::function<void(int64_t)> emit = [&](int64_t p) {
     const Pair& P = S.pairs[p];
     for (int32_t b : P.own) {
-      const int32_t o = other_start(b);
       const int64_t w = width(b);
-      for (int64_t j = 0; j < w; ++j) {
-        S.gcol.push_back((int32_t)(o + j));
-        S.gblk.push_back(b);
-      }
+      S.seg_dst.push_back(pos);
+      S.seg_col0.push_back(other_start(b));
+      S.seg_w.push_back((int32_t)w);
+      S.seg_blk.push_back(b);
+      pos += w;
     }
     for (auto& seg : P.parents) emit(seg.first);
   };
   for (int64_t p = 0; p < (int64_t)S.pairs.size(); ++p) {
-    S.leaf_colmap_off[p] = (int64_t)S.gcol.size();
+    S.leaf_colmap_off[p] = pos;
     if (S.pairs[p].leaf) emit(p);
   }
-  S.leaf_colmap_off[S.pairs.size()] = (int64_t)S.gcol.size();
-  S.nleafcols = (int64_t)S.gcol.size();
+  S.leaf_colmap_off[S.pairs.size()] = pos;
+  S.nleafcols = pos;
 }
 
 }  // namespace

@@ -6,7 +6,8 @@ import numpy as np
 import pytest
 
 from oracle import dh2_oracle as O
-from synth import fibonacci_sphere, helmholtz_matrix, mean_nn_distance, random_complex_vectors
+from synth import (dlp_matrix, ellipsoid_normals, fibonacci_sphere, helmholtz_matrix, mean_nn_distance,
+                   random_complex_vectors, random_ellipsoid)
 
 pytestmark = pytest.mark.gpu
 
@@ -86,6 +87,44 @@ def test_matrix_free_fp32():
     total = sum(len(rd[s]) for s in (0, 1))
     diff = sum(rd[s][k] != rf[s][k] for s in (0, 1) for k in rd[s])
     assert diff <= 0.02 * total, (diff, total)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_matrix_free_double_layer_matches_dense(fp64):
+    """1/2 I + double layer on an ellipsoid, generated in the kernels from points and normals,
+    against the compression of the materialised (non-symmetric) matrix and the oracle."""
+    D = _dev()
+    n, kappa, leaf, eps = 2048, 8.0, 32, 1e-4
+    pts = random_ellipsoid(n)
+    nrm = ellipsoid_normals(pts)
+    T = D.dh2_tree_build(pts, leaf, kappa)
+    perm = T.perm()
+    G = dlp_matrix(pts, nrm, kappa)[np.ix_(perm, perm)]
+    mode = D.MODE_FP64 if fp64 else D.MODE_FP32
+    dt = torch.complex128 if fp64 else torch.complex64
+    Gd = torch.from_numpy(np.ascontiguousarray(G.T)).to("cuda", dt).t()
+    G128 = torch.from_numpy(np.ascontiguousarray(G.T)).to("cuda", torch.complex128).t()
+    Md = D.dh2_compress(T, Gd, eps=eps, mode=mode)
+    Mf = D.dh2_compress_kernel_dlp(T, pts, nrm, kappa, eps=eps, mode=mode)
+    rd, rf = _ranks(D, T, Md), _ranks(D, T, Mf)
+    total = sum(len(rd[s]) for s in (0, 1))
+    diff = sum(rd[s][k] != rf[s][k] for s in (0, 1) for k in rd[s])
+    assert diff <= (2 if fp64 else 0.02 * total), (diff, total)
+    e_gen = D.dh2_error(Mf)            # reference generated in FP64 from points and normals
+    e_dense = D.dh2_error(Mf, G128)    # reference = the numpy matrix
+    assert e_gen <= eps and e_dense <= eps
+    assert abs(e_gen - e_dense) <= 1e-6 * e_dense
+    if fp64:
+        tr = O.build_tree(pts, O.TreeParams(leaf_size=leaf, kappa=kappa))
+        cp = O.CompressParams(eps=eps)
+        w = O.block_weights(tr, O.block_norms(tr, G), cp.zeta)
+        V = O.compress(tr, G, cp, "row", w, rank_override=rf[0])
+        W = O.compress(tr, G, cp, "col", w, rank_override=rf[1])
+        S = O.project(tr, G, V, W)
+        x = random_complex_vectors(n, 2, seed=23)
+        y_ref = O.matvec(tr, G, V, W, S, x)
+        y = _matvec(D, Mf, x, torch.complex128)
+        assert np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref) <= 1e-11
 
 
 def test_matrix_free_rejects_view_nearfield():
