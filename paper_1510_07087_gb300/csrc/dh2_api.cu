@@ -29,8 +29,8 @@ using namespace dh2;
 
 namespace dh2 {
 
-constexpr int kLeafClasses = 4;
-inline int leaf_class(int m) { return m <= 32 ? 0 : m <= 48 ? 1 : m <= 64 ? 2 : 3; }
+constexpr int kLeafClasses = 5;
+inline int leaf_class(int m) { return m <= 32 ? 0 : m <= 40 ? 1 : m <= 48 ? 2 : m <= 64 ? 3 : 4; }
 
 // Device copy of a tree's work lists (one arena, uploaded on first use).
 struct Tree::Dev {
@@ -65,8 +65,8 @@ struct Tree::Dev {
   int64_t nleaf_codes = 0;
   // leaf codes grouped by size class (rows <= 32, <= 48, <= 64, more), each
   // group costliest first; the pair kernel's CTA is sized to the class
-  int64_t leaf_class_begin[kLeafClasses + 1] = {0, 0, 0, 0, 0};
-  int32_t leaf_class_maxm[kLeafClasses] = {0, 0, 0, 0};
+  int64_t leaf_class_begin[kLeafClasses + 1] = {};
+  int32_t leaf_class_maxm[kLeafClasses] = {};
   std::vector<int64_t> nl_code_begin, nl_code_count;    // per level
   int64_t nleaf_tiles = 0;
   std::vector<int64_t> nl_tile_begin, nl_tile_count;    // per level
@@ -518,6 +518,8 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
 // for the non-leaf steps), then expansion and projection per problem.
 template <typename T>
 dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params& cp, cudaStream_t st) {
+  bool any_gen = false;  // entries generated in the kernels (matrix-free mode)
+  for (const dh2_matrix* M : Ms) any_gen = any_gen || M->gen != 0;
   const int nprob = (int)Ms.size();
   const int pmax = sizeof(T) == 4 ? kPmaxF32 : kPmaxF64;
   cudaEvent_t ev[7];
@@ -551,8 +553,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   int64_t n_ltiles = 0;
   std::vector<uint64_t> leaf_tiles;
   // leaf launches per size class: code ranges and largest row count
-  int64_t cls_begin[kLeafClasses + 1] = {0, 0, 0, 0, 0};
-  int cls_maxm[kLeafClasses] = {0, 0, 0, 0};
+  int64_t cls_begin[kLeafClasses + 1] = {};
+  int cls_maxm[kLeafClasses] = {};
   std::vector<std::vector<uint64_t>> nl_tiles(maxdepth + 1);
   size_t args_bytes = align256(sizeof(PairArgs<T>) * nprob) + align256(sizeof(NormsArgs<T>) * nprob);
   size_t codes_bytes = 0;
@@ -716,7 +718,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
   }
   cudaEventRecord(ev[2], st);
-  launch_rq_kernel<T>(d_pa, d_ltiles, (int)n_ltiles, P_leaf, false, st);
+  launch_rq_kernel<T>(d_pa, d_ltiles, (int)n_ltiles, P_leaf, false, any_gen, st);
   nlaunch += n_ltiles > 0;
 #ifdef DH2_PROFILE
   {
@@ -767,7 +769,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
             ++nlaunch;
           }
       }
-      launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, st);
+      launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, any_gen, st);
       nlaunch += n_nltiles[l] > 0;
       DH2_PHASE_SYNC("non-leaf pairs");
     }

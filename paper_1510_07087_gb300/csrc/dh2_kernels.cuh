@@ -97,11 +97,12 @@ template <typename T>
 void launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
                         cudaStream_t st);
 
-// R = Q^* A for the pairs of a pair-kernel launch, after it: one CTA per tile
-// of 32 columns, tiles[i] = launch code << 32 | first column (P as for the
-// pair kernel).
+// R = Q^* A for the pairs of a pair-kernel launch, after it, by tiles of 32
+// columns, tiles[i] = launch code << 32 | first column (P as for the pair
+// kernel).  Leaf tiles of a stored G (gen false) go to a persistent kernel
+// that keeps the next tile's loads in flight; the others get one CTA per tile.
 template <typename T>
-void launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int ntiles, int P, bool from_r,
+void launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int ntiles, int P, bool from_r, bool gen,
                       cudaStream_t st);
 
 // Non-leaf codes of one level split by the row count of their Ghat (from the

@@ -141,6 +141,16 @@ __device__ __forceinline__ void load_c2x2<float>(const C2<float>* p, C2<float>& 
   b = C2<float>{v.z, v.w};
 }
 
+template <typename T>
+__device__ __forceinline__ void store_c2x2(C2<T>* p, C2<T> a, C2<T> b) {
+  p[0] = a;
+  p[1] = b;
+}
+template <>
+__device__ __forceinline__ void store_c2x2<float>(C2<float>* p, C2<float> a, C2<float> b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.re, a.im, b.re, b.im);
+}
+
 // Walk e = start, start + step, ... < slow_n * fast_n over a (slow, fast)
 // index pair, e = slow * fast_n + fast, with one division at set-up.
 struct Walk2 {
@@ -299,23 +309,33 @@ __device__ __forceinline__ void stage_cols(const Source<T, FROM_R>& src, int p, 
 #ifndef DH2_PAIR_MINB192
 #define DH2_PAIR_MINB192 4  // at 192 threads
 #endif
+#ifndef DH2_PAIR_MINB160
+#define DH2_PAIR_MINB160 5  // at 160 threads
+#endif
 #ifndef DH2_PAIR_MINB128
 #define DH2_PAIR_MINB128 6  // at 128 threads
+#endif
+#ifndef DH2_LQT
+#define DH2_LQT 8  // threads per row in the streamed LQ (4 or 8)
 #endif
 #ifndef DH2_JACOBI_TPP
 #define DH2_JACOBI_TPP 32  // most threads per column pair in the Jacobi step (4..32)
 #endif
 template <int NT, typename T>
 constexpr int pair_min_blocks() {
-  return sizeof(T) == 4 ? (NT >= 256 ? DH2_PAIR_MINB : NT >= 192 ? DH2_PAIR_MINB192 : DH2_PAIR_MINB128)
-                        : (NT >= 192 ? 1 : 2);
+  return sizeof(T) == 4 ? (NT >= 256   ? DH2_PAIR_MINB
+                           : NT >= 192 ? DH2_PAIR_MINB192
+                           : NT >= 160 ? DH2_PAIR_MINB160
+                                       : DH2_PAIR_MINB128)
+                        : (NT >= 160 ? 1 : 2);
 }
 
 template <typename T, int P_T, bool FROM_R, int NT>
 __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
   constexpr int LPR = NT / P_T;      // threads per row in the pivoted LQ (rows in place)
-  constexpr int LQT = 8;             // threads per row in the streamed LQ (a quarter warp)
+  constexpr int LQT = DH2_LQT;       // threads per row in the streamed LQ
+  constexpr int GPW = 32 / LQT;      // rows per warp and per block of rows
   constexpr int NW = NT / 32;        // warps
   constexpr int S = P_T / (NT / LQT);  // rows per group of LQT threads
   constexpr int E = 16 / S;          // chunk entries per thread and row
@@ -407,24 +427,27 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   DH2_PROF_T(t_a);
 
   // ---------------------------------------------------------------- 1. LQ
-  // Rows go to groups of LQT threads in blocks of four consecutive rows, the
-  // blocks dealt round-robin over the warps, so that the rows still active at
-  // step i stay spread over all warps and the four rows sharing a warp finish
-  // together.  Each thread keeps E entries of each of its S rows of the
-  // current chunk in registers; the chunk is first staged through shared
-  // memory with coalesced loads.  Step i applies reflection i (row i) to the
-  // rows below it; the warp owning row i+1 updates that row's block first and
-  // forms reflection i+1, then updates its other rows; one barrier per step.
-  // The reductions over a row run on its quarter warp alone (measured faster
-  // than running every quarter converged with the full mask).
+  // Rows go to groups of LQT threads in blocks of GPW = 32/LQT consecutive
+  // rows (one row per group of a warp), the blocks dealt round-robin over the
+  // warps.  Each thread keeps E entries of each of its S rows of the current
+  // chunk in registers (S = 1 for LQT = 4 in the classes up to 64 rows); the
+  // chunk is first staged through shared memory with coalesced loads.  Step i
+  // applies reflection i (row i) to the rows below it; the warp owning row
+  // i+1 updates that row's block first and forms reflection i+1, then updates
+  // its other blocks; one barrier per step.  The reductions over a row run on
+  // its group alone (measured faster than running every group converged with
+  // the full mask).
   const int row = tid / LPR, q = tid % LPR;  // row mapping of the pivoted LQ (1b)
   const bool live = row < p;
   const int lq = lane & (LQT - 1);
-  const int quarter = lane >> 3;
-  // row of slot s of this thread: block warp + NW * s, row `quarter` in it
-  auto lrow = [&](int s) { return 4 * (warp + NW * s) + quarter; };
+  const int lgrp = lane / LQT;
+  // row of slot s of this thread: block warp + NW * s, row `lgrp` in it
+  auto lrow = [&](int s) { return GPW * (warp + NW * s) + lgrp; };
   // does slot s of this warp hold a row r > j (r < p)?
-  auto slot_live = [&](int s, int j) { return min(4 * (warp + NW * s) + 3, p - 1) > j; };
+  auto slot_live = [&](int s, int j) { return min(GPW * (warp + NW * s) + GPW - 1, p - 1) > j; };
+  // chunk column of entry u of a thread: pairs of adjacent columns, so that
+  // the reflection vector moves in 16-byte words
+  auto ccol = [&](int u) { return 2 * lq + (u & 1) + (u >> 1) * 2 * LQT; };
   C2<T>* Xs = Lm + (int64_t)P * LDL;  // staged chunk: column jj at Xs[jj * LDL]
   C2<T> ch[S][E];
 
@@ -434,7 +457,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   // whole warp; only the quarter holding row r (mine) works.
   auto publish = [&](int r, const C2<T> (&x)[E], bool mine, int slot) {
     if (!mine) return;
-    const unsigned qmask = 0xffu << (lane & 24);
+    const unsigned qmask = ((1u << LQT) - 1u) << (lane & (32 - LQT));
     // the diagonal entry and its phase do not depend on the row norm: form
     // them while the norm is reduced
     const C2<T> al = Lm[r * LDL + r];
@@ -443,7 +466,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     const T an = an2 * ra;
     const C2<T> ph = an2 > Eps<T>::tiny ? C2<T>{al.re * ra, al.im * ra} : C2<T>{T(1), T(0)};
 #pragma unroll
-    for (int u = 0; u < E; ++u) vbuf[slot * C + lq + u * LQT] = x[u];
+    for (int u = 0; u < E; u += 2) store_c2x2(vbuf + slot * C + ccol(u), x[u], x[u + 1]);
     T s0 = T(0), s1 = T(0);
 #pragma unroll
     for (int u = 0; u < E; u += 2) {
@@ -473,12 +496,12 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   auto apply = [&](C2<T> (&c)[E], int r, int j, const C2<T>* xs, C2<T> v0, T tau_j) {
     const bool act = r > j && r < p;
     if (!act) return;
-    const unsigned qmask = 0xffu << (lane & 24);
+    const unsigned qmask = ((1u << LQT) - 1u) << (lane & (32 - LQT));
     const T tau = tau_j;
     const C2<T> lrj = Lm[j * LDL + r];
     C2<T> x[E];
 #pragma unroll
-    for (int u = 0; u < E; ++u) x[u] = xs[lq + u * LQT];
+    for (int u = 0; u < E; u += 2) load_c2x2(xs + ccol(u), x[u], x[u + 1]);
     C2<T> wa[4] = {czero<T>(), czero<T>(), czero<T>(), czero<T>()};
 #pragma unroll
     for (int u = 0; u < E; ++u) wa[u & 3] = cmacc(wa[u & 3], c[u], x[u]);
@@ -563,7 +586,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     for (int s = 0; s < S; ++s) {
       const int r = lrow(s);
 #pragma unroll
-      for (int u = 0; u < E; ++u) ch[s][u] = r < p ? Xs[(lq + u * LQT) * LDL + r] : czero<T>();
+      for (int u = 0; u < E; ++u) ch[s][u] = r < p ? Xs[ccol(u) * LDL + r] : czero<T>();
     }
     if (warp == 0) publish(0, ch[0], lrow(0) == 0, 0);
     __syncthreads();
@@ -582,7 +605,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
       const C2<T>* x = vbuf + sl * C;
       const C2<T> v0 = skip ? czero<T>() : sh_v0[sl];
       const T tau = skip ? T(0) : sh_tau[sl];
-      const int b1 = (i + 1) >> 2;  // block of row i+1
+      const int b1 = (i + 1) / GPW;  // block of row i+1
       const int cs = i + 1 < p && (b1 % NW) == warp ? b1 / NW : -1;
 #if DH2_PROF_ON
       const long long tsa = clock64();
@@ -1132,6 +1155,199 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 6 : 2)
   }
 }
 
+// One tile of the leaf R = Q^* A: pair, columns and the addresses its loads
+// and stores need (live = false for a tile past the list or with rank 0).
+template <typename T>
+struct RqLeafTile {
+  const C2<T>* G;
+  const int32_t* gcol;  // column map of the pair, from its first column
+  const T* colw;
+  const C2<T>* Q;
+  C2<T>* R;
+  int64_t ld, cmo, qoff, roff;
+  int side, pid, r0, p, k, cw, j0, ldq, kcap;
+  bool live;
+};
+
+template <typename T>
+__device__ __forceinline__ RqLeafTile<T> rq_leaf_tile(const PairArgs<T>* __restrict__ args,
+                                                      const uint64_t* __restrict__ tiles, int64_t t,
+                                                      int64_t ntiles, int P) {
+  RqLeafTile<T> x;
+  x.live = false;
+  x.side = x.pid = x.r0 = x.p = x.k = x.cw = x.j0 = x.ldq = x.kcap = 0;
+  x.ld = x.cmo = x.qoff = x.roff = 0;
+  x.G = x.Q = nullptr;
+  x.R = nullptr;
+  x.gcol = nullptr;
+  x.colw = nullptr;
+  if (t >= ntiles) return x;
+  const uint64_t tile = tiles[t];
+  const uint32_t code = (uint32_t)(tile >> 32);
+  x.j0 = (int)(uint32_t)tile;
+  const int prob = (int)(code >> kCodeProbShift);
+  x.side = (int)((code >> kCodeSideShift) & 1u);
+  x.pid = (int)(code & kCodePairMask);
+  const PairArgs<T>& a = args[prob];
+  if (!DH2_IN(x.pid, c_lim.npairs[x.side], 9, x.pid)) return x;
+  const int sd = x.side, pid = x.pid;
+  const int N = a.ncols[sd][pid];
+  x.k = a.rank[sd][pid];
+  x.p = a.m[sd][pid];
+  if (x.k <= 0 || x.j0 >= N || x.p <= 0 || x.p > P) return x;  // p > P: reported by pair_kernel
+  x.cw = min(kRTile, N - x.j0);
+  x.r0 = a.start[sd][pid];
+  x.cmo = a.cmoff[sd][pid];
+  x.gcol = a.gcol[sd] + x.cmo;
+  x.colw = a.colw[sd] + x.cmo;
+  x.G = a.G;
+  x.ld = a.ld;
+  x.qoff = a.Qoff[sd][pid];
+  x.Q = a.Q[sd] + x.qoff;
+  x.ldq = a.rowcap[sd][pid];
+  x.roff = a.Roff[sd][pid];
+  x.R = a.R[sd] + x.roff;
+  x.kcap = a.kcap[sd][pid];
+  x.live = true;
+  return x;
+}
+
+// R_tc = Q^* A for the leaf pairs (Section 6, R_tc = V_tc^* G_tc), the
+// dense-matrix modes.  A persistent kernel: CTA b takes tiles b, b + grid,
+// ... of the tile list.  While it forms the products of one tile, the next
+// tile's entries and Q block and the column table of the tile after that are
+// in flight (cp.async), in a second shared-memory stage and a third table
+// slot, so that the load latency of a tile hides behind the arithmetic of the
+// one before.  The weight 1/omega_b and the conjugation of G^* are applied to
+// the outputs: for the row basis R = w sum_r conj(Q) G, for the column basis
+// R = w conj(sum_r Q G') with G' the stored entries of G.
+template <typename T>
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
+    rq_leaf_kernel(const PairArgs<T>* __restrict__ args, const uint64_t* __restrict__ tiles, const int64_t ntiles,
+                   const int P) {
+  constexpr int NT = 128;
+  constexpr int QB = 32;
+  constexpr int TW = kRTile;
+  constexpr int LQ = QB + 2, LA = TW + 2;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int cgc[3][TW];
+  __shared__ T cwt[3][TW];
+  C2<T>* const base = reinterpret_cast<C2<T>*>(smem);
+  auto stQ = [&](int s) { return base + (size_t)s * P * (LQ + LA); };
+  auto stA = [&](int s) { return base + (size_t)s * P * (LQ + LA) + (size_t)P * LQ; };
+  const int tid = threadIdx.x;
+  const int64_t stride = gridDim.x;
+
+  auto issue_table = [&](const RqLeafTile<T>& x, int slot) {
+    if (!x.live) return;
+    for (int jj = tid; jj < x.cw; jj += NT) {
+      if (DH2_IN(x.cmo + x.j0 + jj, c_lim.ncol[x.side], 3, x.pid)) {
+        cp_async<4>(&cgc[slot][jj], x.gcol + x.j0 + jj);
+        cp_async<sizeof(T)>(&cwt[slot][jj], x.colw + x.j0 + jj);
+      } else {
+        cgc[slot][jj] = 0;
+        cwt[slot][jj] = T(0);
+      }
+    }
+  };
+  // entries of the tile (needs its table) and block qb of Q
+  auto issue_q = [&](const RqLeafTile<T>& x, int s, int qb) {
+    C2<T>* Qs = stQ(s);
+    const int kb = min(QB, x.k - qb);
+    for (Walk2 it(tid, NT, x.p); it.g < kb; it.next()) {
+      const int r = it.f, qq = it.g;
+      const int64_t e = r + (int64_t)(qb + qq) * x.ldq;
+      if (DH2_IN(x.qoff + e, c_lim.Q[x.side], 14, x.pid)) cp_async<sizeof(C2<T>)>(Qs + r * LQ + qq, x.Q + e);
+      else Qs[r * LQ + qq] = czero<T>();
+    }
+  };
+  auto issue_a = [&](const RqLeafTile<T>& x, int s, int slot) {
+    if (!x.live) return;
+    C2<T>* As = stA(s);
+    const bool down = x.side == 0;  // consecutive threads on the contiguous direction
+    for (Walk2 it(tid, NT, down ? x.p : x.cw); it.g < (down ? x.cw : x.p); it.next()) {
+      const int r = down ? it.f : it.g;
+      const int jj = down ? it.g : it.f;
+      const int gc = cgc[slot][jj];
+      const int64_t e = x.side == 0 ? (int64_t)gc * x.ld + x.r0 + r : (int64_t)(x.r0 + r) * x.ld + gc;
+      if (DH2_IN(e, c_lim.G, x.side == 0 ? 5 : 7, x.pid)) cp_async<sizeof(C2<T>)>(As + r * LA + jj, x.G + e);
+      else As[r * LA + jj] = czero<T>();
+    }
+    issue_q(x, s, 0);
+  };
+  // 2 x 2 output tiles of block qb; entries past kb or cw are read (finite or
+  // not) but never stored
+  auto products = [&](const RqLeafTile<T>& x, int s, int slot, int qb) {
+    const C2<T>* Qs = stQ(s);
+    const C2<T>* As = stA(s);
+    const int kb = min(QB, x.k - qb);
+    const int nqt = (kb + 1) >> 1, njt = (x.cw + 1) >> 1;
+    const T sg = x.side == 0 ? T(1) : T(-1);  // conj(Q) for the row basis, Q for the column basis
+    for (int u = tid; u < nqt * njt; u += NT) {
+      const int q0 = 2 * (u % nqt), jb = 2 * (u / nqt);
+      const C2<T>* qp = Qs + q0;
+      const C2<T>* ap = As + jb;
+      C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
+#pragma unroll 2
+      for (int r = 0; r < x.p; ++r, qp += LQ, ap += LA) {
+        C2<T> x0, x1, y0, y1;
+        load_c2x2(qp, x0, x1);
+        load_c2x2(ap, y0, y1);
+        x0.im *= sg;
+        x1.im *= sg;
+        c00 = cmacc(c00, y0, x0);
+        c01 = cmacc(c01, y1, x0);
+        c10 = cmacc(c10, y0, x1);
+        c11 = cmacc(c11, y1, x1);
+      }
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const int qq = q0 + (d >> 1), jj = jb + (d & 1);
+        if (qq < kb && jj < x.cw) {
+          const C2<T> v = d == 0 ? c00 : d == 1 ? c01 : d == 2 ? c10 : c11;
+          const T w = cwt[slot][jj];
+          const int64_t e = (qb + qq) + (int64_t)(x.j0 + jj) * x.kcap;
+          if (DH2_IN(x.roff + e, c_lim.R[x.side], 11, x.pid)) x.R[e] = C2<T>{v.re * w, sg * v.im * w};
+        }
+      }
+    }
+  };
+
+  int64_t t = blockIdx.x;
+  RqLeafTile<T> cur = rq_leaf_tile(args, tiles, t, ntiles, P);
+  RqLeafTile<T> nxt = rq_leaf_tile(args, tiles, t + stride, ntiles, P);
+  issue_table(cur, 0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  issue_a(cur, 0, 0);
+  issue_table(nxt, 1);
+  cp_async_commit();
+  for (int i = 0; t < ntiles; ++i, t += stride) {
+    const int s = i & 1, slot = i % 3;
+    const RqLeafTile<T> nn = rq_leaf_tile(args, tiles, t + 2 * stride, ntiles, P);
+    cp_async_wait_all();
+    __syncthreads();  // this tile's stage and the next tile's table have landed; stage s^1 is free
+    issue_a(nxt, s ^ 1, (i + 1) % 3);
+    issue_table(nn, (i + 2) % 3);
+    cp_async_commit();
+    if (cur.live) {
+      products(cur, s, slot, 0);
+      for (int qb = QB; qb < cur.k; qb += QB) {  // ranks above 32: further Q blocks, loaded in place
+        __syncthreads();
+        issue_q(cur, s, qb);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        products(cur, s, slot, qb);
+      }
+    }
+    cur = nxt;
+    nxt = nn;
+  }
+  cp_async_wait_all();
+}
+
 template <typename T, int P_T, bool FROM_R, int NT>
 void launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
   constexpr int C = 16 * (NT / P_T);
@@ -1214,11 +1430,26 @@ void launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P
 }
 
 template <typename T>
-void launch_rq_kernel(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, bool from_r,
+void launch_rq_leaf(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
+  constexpr int QB = 32, LQ = QB + 2, LA = kRTile + 2;
+  const size_t smem = 2 * (size_t)(LQ + LA) * P * sizeof(C2<T>);  // two stages of Q block and A tile
+  auto kern = rq_leaf_kernel<T>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)std::max(1, nsm) * std::max(1, per_sm));
+  kern<<<grid, 128, smem, st>>>(args, tiles, (int64_t)ntiles, P);
+}
+
+template <typename T>
+void launch_rq_kernel(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, bool from_r, bool gen,
                       cudaStream_t st) {
   if (ntiles <= 0) return;
   if (from_r) launch_rq<T, true>(args, tiles, ntiles, P, st);
-  else launch_rq<T, false>(args, tiles, ntiles, P, st);
+  else if (gen) launch_rq<T, false>(args, tiles, ntiles, P, st);
+  else launch_rq_leaf<T>(args, tiles, ntiles, P, st);
 }
 template <typename T>
 void launch_classify(const PairArgs<T>* args, const uint32_t* codes, int n, uint32_t* out, int* counts,
@@ -1228,8 +1459,8 @@ void launch_classify(const PairArgs<T>* args, const uint32_t* codes, int n, uint
 template void launch_classify<float>(const PairArgs<float>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
 template void launch_classify<double>(const PairArgs<double>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
 
-template void launch_rq_kernel<float>(const PairArgs<float>*, const uint64_t*, int, int, bool, cudaStream_t);
-template void launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*, int, int, bool, cudaStream_t);
+template void launch_rq_kernel<float>(const PairArgs<float>*, const uint64_t*, int, int, bool, bool, cudaStream_t);
+template void launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*, int, int, bool, bool, cudaStream_t);
 
 template <typename T>
 void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
@@ -1237,6 +1468,7 @@ void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
   if (nblocks <= 0) return;
   if (!from_r) {
     if (P <= 32) launch_one<T, 32, false, 128>(args, codes, nblocks, P, st);
+    else if (P <= 40) launch_one<T, 40, false, 160>(args, codes, nblocks, P, st);
     else if (P <= 48) launch_one<T, 48, false, 192>(args, codes, nblocks, P, st);
     else if (P <= 64) launch_one<T, 64, false, 256>(args, codes, nblocks, P, st);
     else launch_one<T, 128, false, 256>(args, codes, nblocks, P, st);
