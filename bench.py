@@ -33,10 +33,11 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # 2 flops per FMA x 2.07 GHz maximum SM clock.
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes (read + write) of one leaf launch of the pair kernel at n=32768,
-# kappa=32, leaf 64, FP32, from a 1-pass ncu capture (profiles/); valid only
-# for the kernel source it was measured on (sha1 of csrc/dh2_pair.cu).
-PAIR_TRAFFIC = {"sha1": "1494acdb58cae3fe0b9931a34b403a9ebd5c8b2e", "bytes": 5.92e9 + 0.274e9}
+# DRAM bytes (read + write) of the leaf launches of the pair kernel (one per
+# leaf-size class, together) at n=32768, kappa=32, leaf 64, FP32, from a
+# 1-pass ncu capture (profiles/); valid only for the kernel source it was
+# measured on (sha1 of csrc/dh2_pair.cu).
+PAIR_TRAFFIC = {"sha1": "244416117d122cbc1a919c4c36efb296508a3320", "bytes": 5.839e9 + 0.308e9}
 
 
 def _peaks():
@@ -370,7 +371,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n", type=int, default=32768)
