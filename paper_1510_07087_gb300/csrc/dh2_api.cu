@@ -69,6 +69,7 @@ struct Tree::Dev {
   int32_t leaf_class_maxm[kLeafClasses] = {};
   std::vector<int64_t> nl_code_begin, nl_code_count;    // per level
   int64_t nleaf_tiles = 0;
+  int64_t leaf_tile_class_begin[kLeafClasses + 1] = {};  // leaf tiles of each size class
   std::vector<int64_t> nl_tile_begin, nl_tile_count;    // per level
   std::vector<int32_t> nl_rowcap_max;                   // per level
   std::vector<int64_t> lvl_begin[2], lvl_nl_begin[2], lvl_end[2];
@@ -357,8 +358,12 @@ dh2_status upload_tree(Tree& tr) {
       const int64_t nc = tr.side[sd].pairs[p].ncols;
       for (int64_t j0 = 0; j0 < nc; j0 += kRTile) tiles.push_back((int64_t)(((uint64_t)(uint32_t)code << 32) | (uint64_t)j0));
     };
-    for (int64_t i = 0; i < D->nleaf_codes; ++i) add_tiles(codes[i]);
+    for (int c = 0; c < kLeafClasses; ++c) {
+      D->leaf_tile_class_begin[c] = (int64_t)tiles.size();
+      for (int64_t i = D->leaf_class_begin[c]; i < D->leaf_class_begin[c + 1]; ++i) add_tiles(codes[i]);
+    }
     D->nleaf_tiles = (int64_t)tiles.size();
+    D->leaf_tile_class_begin[kLeafClasses] = D->nleaf_tiles;
     D->nl_tile_begin.assign(tr.depth + 1, 0);
     D->nl_tile_count.assign(tr.depth + 1, 0);
     for (int l = tr.depth; l >= 0; --l) {
@@ -555,6 +560,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // leaf launches per size class: code ranges and largest row count
   int64_t cls_begin[kLeafClasses + 1] = {};
   int cls_maxm[kLeafClasses] = {};
+  int64_t tile_cls_begin[kLeafClasses + 1] = {};
   std::vector<std::vector<uint64_t>> nl_tiles(maxdepth + 1);
   size_t args_bytes = align256(sizeof(PairArgs<T>) * nprob) + align256(sizeof(NormsArgs<T>) * nprob);
   size_t codes_bytes = 0;
@@ -596,7 +602,12 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         for (int64_t j0 = 0; j0 < nc; j0 += kRTile) out.push_back(((uint64_t)c << 32) | (uint64_t)j0);
       }
     };
-    tiles_of(leaf_codes, leaf_tiles);
+    for (int c = 0; c < kLeafClasses; ++c) {
+      tile_cls_begin[c] = (int64_t)leaf_tiles.size();
+      const std::vector<uint32_t> seg(leaf_codes.begin() + cls_begin[c], leaf_codes.begin() + cls_begin[c + 1]);
+      tiles_of(seg, leaf_tiles);
+    }
+    tile_cls_begin[kLeafClasses] = (int64_t)leaf_tiles.size();
     for (int l = 0; l <= maxdepth; ++l) tiles_of(nl_codes[l], nl_tiles[l]);
     codes_bytes = align256(4 * leaf_codes.size()) + align256(4 * norm_codes.size()) + align256(8 * leaf_tiles.size());
     for (int l = 0; l <= maxdepth; ++l)
@@ -652,6 +663,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     n_leaf = D->nleaf_codes;
     for (int c = 0; c <= kLeafClasses; ++c) cls_begin[c] = D->leaf_class_begin[c];
     for (int c = 0; c < kLeafClasses; ++c) cls_maxm[c] = D->leaf_class_maxm[c];
+    for (int c = 0; c <= kLeafClasses; ++c) tile_cls_begin[c] = D->leaf_tile_class_begin[c];
     d_norm = nullptr;
     n_norm = (int64_t)tr.blocks.size();
     for (int l = 0; l <= tr.depth; ++l) {
@@ -718,8 +730,15 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
   }
   cudaEventRecord(ev[2], st);
-  launch_rq_kernel<T>(d_pa, d_ltiles, (int)n_ltiles, P_leaf, false, any_gen, st);
-  nlaunch += n_ltiles > 0;
+  // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
+  for (int c = 0; c < kLeafClasses; ++c) {
+    const int64_t nt = tile_cls_begin[c + 1] - tile_cls_begin[c];
+    if (nt > 0) {
+      launch_rq_kernel<T>(d_pa, d_ltiles + tile_cls_begin[c], (int)nt, even_up(std::max(2, cls_maxm[c])), false,
+                          any_gen, st);
+      ++nlaunch;
+    }
+  }
 #ifdef DH2_PROFILE
   {
     cudaStreamSynchronize(st);
