@@ -36,7 +36,7 @@ def build(verbose: bool = False) -> str:
     for src in HOST_SOURCES:
         obj = os.path.join(BUILD, src + ".o")
         objs.append(obj)
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-Wall", "-Wno-unused-function",
+        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-pthread", "-ffp-contract=off", "-Wall", "-Wno-unused-function",
                      f"-I{os.path.join(HERE, '..', 'include')}", "-c", os.path.join(CSRC, src), "-o", obj])
     extra = ["-DDH2_CHECK"] if os.environ.get("DH2_CHECK") == "1" else []
     if os.environ.get("DH2_PROFILE") == "1":
@@ -62,7 +62,7 @@ def build(verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(" ".join(j) + "\n" + out for j, out in failed)
         raise RuntimeError("libdh2 build failed:\n" + msg)
-    link = [nvcc, "-shared", *ARCH, "-o", LIB + ".tmp", *objs]
+    link = [nvcc, "-shared", *ARCH, "-o", LIB + ".tmp", *objs, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
     if r.returncode != 0:
         raise RuntimeError("libdh2 link failed:\n" + r.stdout)

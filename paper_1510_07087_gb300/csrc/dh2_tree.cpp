@@ -5,7 +5,9 @@
 // direction) are computed in IEEE double with the operation order written
 // here and no contraction (built with -ffp-contract=off), so that another
 // implementation evaluating the same formulas in the same order reaches the
-// same integer decisions.
+// same integer decisions.  The nearest-direction searches and the two sides'
+// work lists run on several host threads; each result is written by one
+// thread only, so the output does not depend on the thread count.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -13,12 +15,33 @@
 #include <map>
 #include <new>
 #include <stdexcept>
+#include <thread>
 
 #include "dh2_internal.h"
 
 namespace dh2 {
 
 namespace {
+
+// f(i) for i in [0, n) on up to 16 host threads, contiguous ranges (each f(i)
+// writes only its own outputs, so the result does not depend on the split).
+template <typename F>
+void parallel_for(int64_t n, F f) {
+  const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+  const int64_t nt = std::min<int64_t>({hw, (int64_t)16, std::max<int64_t>(1, n / 256)});
+  if (nt <= 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve((size_t)nt);
+  for (int64_t k = 0; k < nt; ++k)
+    th.emplace_back([&, k] {
+      const int64_t lo = n * k / nt, hi = n * (k + 1) / nt;
+      for (int64_t i = lo; i < hi; ++i) f(i);
+    });
+  for (auto& t : th) t.join();
+}
 
 // Section 3: midpoints of an m x m subdivision of each face of [-1,1]^3
 // (face order +x,-x,+y,-y,+z,-z, squares row-major), projected to the sphere.
@@ -336,15 +359,38 @@ dh2_status build_tree(const double* pts, int64_t n, const dh2_tree_params& p, Tr
     if (!b.adm) continue;
     ++tr.nadm;
     adm_entries += (double)tr.size[b.t] * (double)tr.size[b.s];
+  }
+  parallel_for((int64_t)tr.blocks.size(), [&](int64_t i) {
+    Block& b = tr.blocks[i];
+    if (!b.adm) return;
     double dv[3];
     for (int a = 0; a < 3; ++a) dv[a] = tr.center[3 * b.t + a] - tr.center[3 * b.s + a];
     const double nd = std::sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
     const double u[3] = {dv[0] / nd, dv[1] / nd, dv[2] / nd};
     b.cb = nearest(u, tr.dirs[tr.level[b.t]]);
-  }
+  });
   tr.adm_fraction = adm_entries / ((double)n * (double)n);
+  // son maps of every direction a pair can take, level by level from the
+  // root (a level's directions: its blocks' c_b and the son directions of the
+  // level above), so that the two sides below read them concurrently
+  {
+    std::vector<std::vector<char>> used(tr.depth + 1);
+    for (int32_t l = 0; l <= tr.depth; ++l) used[l].assign(tr.dirs[l].size() / 3, 0);
+    for (const Block& b : tr.blocks)
+      if (b.adm) used[tr.level[b.t]][b.cb] = 1;
+    for (int32_t l = 0; l < tr.depth; ++l) {
+      std::vector<int32_t> cs;
+      for (int32_t c = 0; c < (int32_t)used[l].size(); ++c)
+        if (used[l][c]) cs.push_back(c);
+      parallel_for((int64_t)cs.size(), [&](int64_t i) {
+        tr.sd[l][cs[i]] = nearest(&tr.dirs[l][3 * (size_t)cs[i]], tr.dirs[l + 1]);
+      });
+      for (int32_t c : cs) used[l + 1][tr.sd[l][c]] = 1;
+    }
+  }
+  std::thread col([&] { build_side(tr, kSideCol); });
   build_side(tr, kSideRow);
-  build_side(tr, kSideCol);
+  col.join();
   return DH2_OK;
 }
 
