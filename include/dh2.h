@@ -152,6 +152,25 @@ dh2_status dh2_tree_pair_blocks(const dh2_tree* tree, int32_t side, int64_t* off
  * DH2_ENOCONV / DH2_EUNSUPPORTED from the device status word, DH2_ECUDA. */
 dh2_status dh2_compress(const dh2_tree* tree, const void* G, dh2_dtype dtype, int64_t ld,
                         const dh2_compress_params* params, void* stream, dh2_matrix** out);
+
+/* The same compression of a G held in HOST memory (n x n column-major,
+ * permuted order, leading dimension ld >= n; page-locked memory gives the
+ * full copy rate, pageable memory is accepted).  The library copies G into a
+ * device buffer owned by the tree (n*n elements of the dtype, allocated on
+ * the first call and kept until dh2_tree_free; a larger dtype reallocates it
+ * and synchronises the device).  The copy runs in column panels made of whole
+ * clusters of the shallowest level that holds an admissible block, on a
+ * second stream: each panel's block norms, nearfield copies and column-basis
+ * leaf factors (which read only that panel's columns of G, Section 6 applied
+ * to G^*) run while the next panel is copied.  Copy mode only
+ * (params->nearfield == 0): the buffer is reused by the next call on the same
+ * tree, so calls on one tree must be ordered (same stream, or synchronised).
+ * The call returns when the compression is complete, so G_host may be freed
+ * after it; the matrix keeps no reference to G (dh2_error needs the
+ * reference passed explicitly).  Errors as dh2_compress;
+ * DH2_EINVAL also for view mode, DH2_ENOMEM if the buffer cannot be allocated. */
+dh2_status dh2_compress_host(const dh2_tree* tree, const void* G_host, dh2_dtype dtype, int64_t ld,
+                             const dh2_compress_params* params, void* stream, dh2_matrix** out);
 /* Compress nprob independent matrices (each with its own tree, size and
  * leading dimension; same dtype and parameters) in one schedule: block norms,
  * leaf factorisations and every level of non-leaf steps are each one launch

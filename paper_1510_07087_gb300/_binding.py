@@ -63,6 +63,8 @@ SIGNATURES = [
     ("dh2_tree_pair_blocks", c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
     ("dh2_compress", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p,
                                POINTER(c_void_p)]),
+    ("dh2_compress_host", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p,
+                                    POINTER(c_void_p)]),
     ("dh2_compress_batched", c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_int32, POINTER(CompressParams),
                                        c_void_p, c_void_p]),
     ("dh2_compress_kernel", c_int32, [c_void_p, c_void_p, c_double, c_double, POINTER(CompressParams), c_void_p,
@@ -296,6 +298,23 @@ def dh2_compress(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_
     _check(_lib().dh2_compress(tree.handle, c_void_p(G.data_ptr()), dt, ld, byref(p),
                                c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress")
     return Matrix(h.value, tree, mode, G)
+
+
+def dh2_compress_host(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,
+                      mode: int | None = None, max_sweeps: int = 0, stream=None) -> Matrix:
+    """Compress a host matrix G (torch CPU tensor, column-major view, tree's permuted order;
+    pinned memory for the full copy rate).  The library copies it to the device itself."""
+    if G.device.type != "cpu":
+        raise ValueError("G must be in host memory")
+    dt = _dtype_code(G)
+    if mode is None:
+        mode = MODE_FP32 if dt == DH2_C64 else MODE_FP64
+    ld = _colmajor_ld(G)
+    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), 0, int(max_sweeps))
+    h = c_void_p()
+    _check(_lib().dh2_compress_host(tree.handle, c_void_p(G.data_ptr()), dt, ld, byref(p),
+                                    c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress_host")
+    return Matrix(h.value, tree, mode, None)
 
 
 def dh2_compress_batched(trees, Gs, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,

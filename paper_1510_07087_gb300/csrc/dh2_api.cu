@@ -518,11 +518,106 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   pa.gen = M->gen;
 }
 
+// Panel plan of a tree for a host-resident G (see PanelPlan).
+void make_panel_plan(const Tree& tr, PanelPlan& pp) {
+  constexpr int kPanels = 8;
+  const int64_t n = tr.n;
+  int32_t lmin = INT32_MAX;
+  for (const Block& B : tr.blocks)
+    if (B.adm) lmin = std::min(lmin, tr.level[B.t]);
+  // atoms: clusters of level lmin and leaves above it, in increasing start
+  // order (pre-order with the first son first)
+  std::vector<int32_t> atoms;
+  if (lmin == INT32_MAX) {
+    atoms.push_back(0);
+  } else {
+    std::vector<int32_t> stack{0};
+    while (!stack.empty()) {
+      const int32_t c = stack.back();
+      stack.pop_back();
+      if (tr.level[c] >= lmin || tr.is_leaf(c)) {
+        atoms.push_back(c);
+      } else {
+        stack.push_back(tr.son1[c]);
+        stack.push_back(tr.son0[c]);
+      }
+    }
+  }
+  const int64_t target = (n + kPanels - 1) / kPanels;
+  auto assign = [&](bool one_panel) -> bool {
+    pp.col.assign(1, 0);
+    if (!one_panel) {
+      int64_t acc = 0;
+      for (int32_t a : atoms) {
+        acc += tr.size[a];
+        const int64_t end = (int64_t)tr.start[a] + tr.size[a];
+        if (acc >= target && end < n) {
+          pp.col.push_back(end);
+          acc = 0;
+        }
+      }
+    }
+    pp.col.push_back(n);
+    const int K = (int)pp.col.size() - 1;
+    auto panel_of = [&](int64_t j) {
+      return (int)(std::upper_bound(pp.col.begin(), pp.col.end(), j) - pp.col.begin()) - 1;
+    };
+    pp.blk.assign(K, {});
+    pp.blk_rest.clear();
+    for (size_t b = 0; b < tr.blocks.size(); ++b) {
+      const Block& B = tr.blocks[b];
+      const int k0 = panel_of(tr.start[B.s]), k1 = panel_of((int64_t)tr.start[B.s] + tr.size[B.s] - 1);
+      if (k0 == k1) pp.blk[k0].push_back((uint32_t)b);
+      else if (B.adm) return false;  // not expected by construction
+      else pp.blk_rest.push_back((uint32_t)b);
+    }
+    struct E {
+      double cost;
+      uint32_t code;
+    };
+    std::vector<std::vector<std::vector<E>>> cl(K, std::vector<std::vector<E>>(kLeafClasses));
+    std::vector<std::vector<E>> rl(kLeafClasses);
+    for (int sd = 0; sd < 2; ++sd)
+      for (int64_t p : tr.side[sd].leaf_pairs) {
+        const int32_t c = tr.side[sd].pairs[p].cluster;
+        const int m = tr.size[c];
+        const E e{(double)m * m * (double)tr.side[sd].pairs[p].ncols,
+                  (uint32_t)((sd << kCodeSideShift) | (int32_t)p)};
+        if (sd == kSideCol) cl[panel_of(tr.start[c])][leaf_class(m)].push_back(e);
+        else rl[leaf_class(m)].push_back(e);
+      }
+    auto codes = [](std::vector<E>& v) {
+      std::stable_sort(v.begin(), v.end(), [](const E& a, const E& b) { return a.cost > b.cost; });
+      std::vector<uint32_t> out;
+      out.reserve(v.size());
+      for (const E& e : v) out.push_back(e.code);
+      return out;
+    };
+    pp.col_leaf.assign(K, std::vector<std::vector<uint32_t>>(kLeafClasses));
+    pp.row_leaf.assign(kLeafClasses, {});
+    for (int k = 0; k < K; ++k)
+      for (int c = 0; c < kLeafClasses; ++c) pp.col_leaf[k][c] = codes(cl[k][c]);
+    for (int c = 0; c < kLeafClasses; ++c) pp.row_leaf[c] = codes(rl[c]);
+    return true;
+  };
+  if (!assign(false)) assign(true);
+}
+
+// G in host memory (dh2_compress_host): copied panel by panel into the
+// staging buffer (the matrix's G, ld = n).
+struct HostStage {
+  const void* G_host;
+  int64_t ld;   // leading dimension of G_host, elements
+  size_t elem;  // bytes per element
+  const PanelPlan* plan;
+};
+
 // The compression of one or several independent problems: each phase is one
 // launch over every problem (block norms, leaf factors, one launch per level
 // for the non-leaf steps), then expansion and projection per problem.
 template <typename T>
-dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params& cp, cudaStream_t st) {
+dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params& cp, cudaStream_t st,
+                        const HostStage* hs = nullptr) {
   bool any_gen = false;  // entries generated in the kernels (matrix-free mode)
   for (const dh2_matrix* M : Ms) any_gen = any_gen || M->gen != 0;
   const int nprob = (int)Ms.size();
@@ -619,8 +714,38 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   for (dh2_matrix* M : Ms)
     for (int l = 0; l <= M->tree->tr.depth; ++l) nl_max = std::max(nl_max, M->tree->tr.dev->nl_code_count[l]);
   const size_t cls_bytes = align256(4 * 4 * (size_t)std::max<int64_t>(nl_max, 1)) + 256;
+  // host-input schedule: the plan's launch lists (blocks per panel, the blocks
+  // across panels, column-basis leaves per panel and class, row-basis leaves
+  // per class) with their R tiles, uploaded behind the other lists
+  struct HList {
+    const std::vector<uint32_t>* codes = nullptr;
+    std::vector<uint64_t> tiles;
+    const uint32_t* d_codes = nullptr;
+    const uint64_t* d_tiles = nullptr;
+  };
+  std::vector<HList> hl;
+  size_t host_bytes = 0;
+  int hK = 0;
+  if (hs) {
+    const PanelPlan& pl = *hs->plan;
+    const Tree& tr = Ms[0]->tree->tr;
+    hK = (int)pl.col.size() - 1;
+    hl.resize((size_t)hK + 1 + (size_t)(hK + 1) * kLeafClasses);
+    for (int k = 0; k < hK; ++k) hl[k].codes = &pl.blk[k];
+    hl[hK].codes = &pl.blk_rest;
+    for (int k = 0; k <= hK; ++k)
+      for (int c = 0; c < kLeafClasses; ++c) {
+        HList& L = hl[(size_t)hK + 1 + (size_t)k * kLeafClasses + c];
+        L.codes = k < hK ? &pl.col_leaf[k][c] : &pl.row_leaf[c];
+        for (uint32_t code : *L.codes) {
+          const int64_t nc = tr.side[(code >> kCodeSideShift) & 1u].pairs[code & kCodePairMask].ncols;
+          for (int64_t j0 = 0; j0 < nc; j0 += kRTile) L.tiles.push_back(((uint64_t)code << 32) | (uint64_t)j0);
+        }
+      }
+    for (const HList& L : hl) host_bytes += align256(4 * L.codes->size()) + align256(8 * L.tiles.size());
+  }
   void* scratch = nullptr;
-  DH2_CUDA_TRY(cudaMallocAsync(&scratch, args_bytes + codes_bytes + cls_bytes + 256, st));
+  DH2_CUDA_TRY(cudaMallocAsync(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + 256, st));
   char* sp = (char*)scratch;
   PairArgs<T>* d_pa = (PairArgs<T>*)sp;
   sp += align256(sizeof(PairArgs<T>) * nprob);
@@ -677,6 +802,19 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       n_nltiles[l] = D->nl_tile_count[l];
     }
   }
+  if (hs) {
+    char* hp = (char*)scratch + args_bytes + codes_bytes + cls_bytes;
+    for (HList& L : hl) {
+      L.d_codes = (const uint32_t*)hp;
+      if (!L.codes->empty() && ce == cudaSuccess)
+        ce = cudaMemcpyAsync(hp, L.codes->data(), 4 * L.codes->size(), cudaMemcpyHostToDevice, st);
+      hp += align256(4 * L.codes->size());
+      L.d_tiles = (const uint64_t*)hp;
+      if (!L.tiles.empty() && ce == cudaSuccess)
+        ce = cudaMemcpyAsync(hp, L.tiles.data(), 8 * L.tiles.size(), cudaMemcpyHostToDevice, st);
+      hp += align256(8 * L.tiles.size());
+    }
+  }
   if (ce != cudaSuccess) {
     cudaGetLastError();
     cudaFreeAsync(scratch, st);
@@ -708,35 +846,107 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #endif
   cudaEventRecord(ev[0], st);
   int nlaunch = 0;  // kernels launched by this compression (counted where they are issued)
-  launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
-  nlaunch += n_norm > 0;
-  for (dh2_matrix* M : Ms)
-    for (int sd = 0; sd < 2; ++sd)
-    {
-      launch_colw<T>(M->tree->tr.dev->gblk[sd], M->invw, (T*)M->colw[sd],
-                     M->tree->tr.side[sd].nleafcols, st);
+  auto colw_side = [&](int sd) {
+    for (dh2_matrix* M : Ms) {
+      launch_colw<T>(M->tree->tr.dev->gblk[sd], M->invw, (T*)M->colw[sd], M->tree->tr.side[sd].nleafcols, st);
       nlaunch += M->tree->tr.side[sd].nleafcols > 0;
     }
-  DH2_PHASE_SYNC("norms_near");
-  cudaEventRecord(ev[1], st);
+  };
+  // leaf factors and R of one launch list per size class
+  auto leaf_lists = [&](const HList* L) {
+    for (int c = 0; c < kLeafClasses; ++c)
+      if (!L[c].codes->empty()) {
+        launch_pair_kernel<T>(d_pa, L[c].d_codes, (int)L[c].codes->size(), even_up(std::max(2, cls_maxm[c])), false,
+                              st);
+        ++nlaunch;
+      }
+  };
+  auto leaf_rq = [&](const HList* L) {
+    for (int c = 0; c < kLeafClasses; ++c)
+      if (!L[c].tiles.empty()) {
+        launch_rq_kernel<T>(d_pa, L[c].d_tiles, (int)L[c].tiles.size(), even_up(std::max(2, cls_maxm[c])), false,
+                            any_gen, st);
+        ++nlaunch;
+      }
+  };
+  if (hs) {
+    // Host-resident G: copied panel by panel on a second stream.  A panel's
+    // block norms (and nearfield copies) and its column-basis leaf factors
+    // and R run as soon as it has arrived, under the copy of the next; the
+    // row-basis leaves read every panel and follow the last one.
+    const PanelPlan& pl = *hs->plan;
+    dh2_matrix* M = Ms[0];
+    const int64_t n = M->tree->tr.n;
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> pev(hK + 1, nullptr);
+    bool own = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k <= hK && own; ++k) own = cudaEventCreateWithFlags(&pev[k], cudaEventDisableTiming) == cudaSuccess;
+    cudaStream_t copy_st = own ? cs : st;  // without a second stream: copies in order on st
+    if (own) {
+      cudaEventRecord(pev[hK], st);
+      cudaStreamWaitEvent(cs, pev[hK], 0);
+    }
+    for (int k = 0; k < hK; ++k) {
+      const int64_t c0 = pl.col[k], nc = pl.col[k + 1] - c0;
+      cudaMemcpy2DAsync((char*)M->G + (size_t)c0 * n * hs->elem, (size_t)n * hs->elem,
+                        (const char*)hs->G_host + (size_t)c0 * hs->ld * hs->elem, (size_t)hs->ld * hs->elem,
+                        (size_t)n * hs->elem, (size_t)nc, cudaMemcpyHostToDevice, copy_st);
+      if (own) cudaEventRecord(pev[k], cs);
+    }
 #ifdef DH2_PROFILE
-  prof_reset_pair();
+    prof_reset_pair();
 #endif
-  for (int c = 0; c < kLeafClasses; ++c) {
-    const int64_t nc = cls_begin[c + 1] - cls_begin[c];
-    if (nc > 0) {
-      launch_pair_kernel<T>(d_pa, d_leaf + cls_begin[c], (int)nc, even_up(std::max(2, cls_maxm[c])), false, st);
+    for (int k = 0; k < hK; ++k) {
+      if (own) cudaStreamWaitEvent(st, pev[k], 0);
+      if (!pl.blk[k].empty()) {
+        launch_norms_near<T>(d_na, hl[k].d_codes, (int)pl.blk[k].size(), st);
+        ++nlaunch;
+      }
+      colw_side(kSideCol);
+      const HList* L = &hl[(size_t)hK + 1 + (size_t)k * kLeafClasses];
+      leaf_lists(L);
+      leaf_rq(L);
+    }
+    if (!pl.blk_rest.empty()) {
+      launch_norms_near<T>(d_na, hl[hK].d_codes, (int)pl.blk_rest.size(), st);
       ++nlaunch;
     }
-  }
-  cudaEventRecord(ev[2], st);
-  // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
-  for (int c = 0; c < kLeafClasses; ++c) {
-    const int64_t nt = tile_cls_begin[c + 1] - tile_cls_begin[c];
-    if (nt > 0) {
-      launch_rq_kernel<T>(d_pa, d_ltiles + tile_cls_begin[c], (int)nt, even_up(std::max(2, cls_maxm[c])), false,
-                          any_gen, st);
-      ++nlaunch;
+    colw_side(kSideRow);
+    DH2_PHASE_SYNC("panels");
+    cudaEventRecord(ev[1], st);
+    const HList* Lr = &hl[(size_t)hK + 1 + (size_t)hK * kLeafClasses];
+    leaf_lists(Lr);
+    cudaEventRecord(ev[2], st);
+    leaf_rq(Lr);
+    for (cudaEvent_t e : pev)
+      if (e) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+  } else {
+    launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
+    nlaunch += n_norm > 0;
+    colw_side(kSideRow);
+    colw_side(kSideCol);
+    DH2_PHASE_SYNC("norms_near");
+    cudaEventRecord(ev[1], st);
+#ifdef DH2_PROFILE
+    prof_reset_pair();
+#endif
+    for (int c = 0; c < kLeafClasses; ++c) {
+      const int64_t nc = cls_begin[c + 1] - cls_begin[c];
+      if (nc > 0) {
+        launch_pair_kernel<T>(d_pa, d_leaf + cls_begin[c], (int)nc, even_up(std::max(2, cls_maxm[c])), false, st);
+        ++nlaunch;
+      }
+    }
+    cudaEventRecord(ev[2], st);
+    // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
+    for (int c = 0; c < kLeafClasses; ++c) {
+      const int64_t nt = tile_cls_begin[c + 1] - tile_cls_begin[c];
+      if (nt > 0) {
+        launch_rq_kernel<T>(d_pa, d_ltiles + tile_cls_begin[c], (int)nt, even_up(std::max(2, cls_maxm[c])), false,
+                            any_gen, st);
+        ++nlaunch;
+      }
     }
   }
 #ifdef DH2_PROFILE
@@ -915,6 +1125,10 @@ dh2_status dh2_tree_build(const double* pts_xyz, int64_t n, const dh2_tree_param
 
 void dh2_tree_free(dh2_tree* T) {
   if (!T) return;
+  if (T->g_stage) {
+    cudaFree(T->g_stage);
+    cudaGetLastError();
+  }
   if (T->tr.dev) {
     cudaFree(T->tr.dev->arena);
     cudaGetLastError();
@@ -1183,6 +1397,48 @@ dh2_status dh2_compress(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int6
     return DH2_EINVAL;
   }
   return compress_impl(Tc, G, dtype, ld, nullptr, 0.0, 0.0, params, stream, out);
+}
+
+dh2_status dh2_compress_host(const dh2_tree* Tc, const void* G_host, dh2_dtype dtype, int64_t ld,
+                             const dh2_compress_params* params, void* stream, dh2_matrix** out) {
+  if (out) *out = nullptr;
+  if (!Tc || !G_host || !params || !out || params->nearfield != 0) return DH2_EINVAL;
+  if (dtype != DH2_C64 && dtype != DH2_C128) return DH2_EINVAL;
+  const int64_t n = Tc->tr.n;
+  if (ld < n) return DH2_EINVAL;
+  const size_t elem = dtype == DH2_C64 ? 8 : 16;
+  // the staging buffer and the panel plan are caches of the tree handle
+  dh2_tree* T = const_cast<dh2_tree*>(Tc);
+  const size_t bytes = (size_t)n * (size_t)n * elem;
+  if (T->g_stage_bytes < bytes) {
+    if (T->g_stage) cudaFree(T->g_stage);  // synchronises: no earlier call still reads it
+    T->g_stage = nullptr;
+    T->g_stage_bytes = 0;
+    if (cudaMalloc(&T->g_stage, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      T->g_stage = nullptr;
+      return DH2_ENOMEM;
+    }
+    T->g_stage_bytes = bytes;
+  }
+  if (!T->plan_built) {
+    make_panel_plan(T->tr, T->plan);
+    T->plan_built = true;
+  }
+  dh2_matrix* M = nullptr;
+  dh2_status s = prepare_matrix(Tc, T->g_stage, dtype, n, nullptr, 0.0, 0.0, params, stream, &M);
+  if (s != DH2_OK) return s;
+  const HostStage hs{G_host, ld, elem, &T->plan};
+  std::vector<dh2_matrix*> Ms{M};
+  s = params->mode == DH2_MODE_FP32 ? run_compress<float>(Ms, *params, (cudaStream_t)stream, &hs)
+                                    : run_compress<double>(Ms, *params, (cudaStream_t)stream, &hs);
+  if (s != DH2_OK) {
+    matrix_release(M);
+    return s;
+  }
+  M->G = nullptr;  // the staging buffer stays the tree's, for the next call
+  *out = M;
+  return DH2_OK;
 }
 
 dh2_status dh2_compress_kernel(const dh2_tree* Tc, const double* pts_xyz, double kappa, double diag,

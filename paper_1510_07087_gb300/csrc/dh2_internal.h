@@ -102,8 +102,28 @@ struct Tree {
 dh2_status build_tree(const double* pts, int64_t n, const dh2_tree_params& p, Tree& tr);
 void free_tree_device(Tree& tr);
 
+// Column panels of a host-resident G (dh2_compress_host): whole clusters of
+// the shallowest level that holds an admissible block (or leaves above it),
+// grouped into ranges of similar width.  Every admissible block's column
+// cluster lies in one panel, and so does every column-basis leaf pair
+// together with the blocks it inherits from its ancestors.  Launch codes as
+// in the compression schedule (side << 25 | pair, or block).
+struct PanelPlan {
+  std::vector<int64_t> col;                                  // panel k: columns [col[k], col[k+1])
+  std::vector<std::vector<uint32_t>> blk;                    // per panel: blocks whose columns lie in it
+  std::vector<uint32_t> blk_rest;                            // blocks across panels (inadmissible only)
+  std::vector<std::vector<std::vector<uint32_t>>> col_leaf;  // per panel, per size class: column-basis leaves
+  std::vector<std::vector<uint32_t>> row_leaf;               // per size class: row-basis leaves
+};
+
 }  // namespace dh2
 
 struct dh2_tree {
   dh2::Tree tr;
+  // host-input compression: the panel plan and the device buffer G is copied
+  // into (built and allocated on first use, reused by later calls)
+  dh2::PanelPlan plan;
+  bool plan_built = false;
+  void* g_stage = nullptr;
+  size_t g_stage_bytes = 0;
 };
