@@ -286,7 +286,9 @@ def run_gpu(args):
         rk_h = [torch.empty(len(r), dtype=torch.int32, pin_memory=True) for r in ranks]
         d2h = sum(4 * len(r) for r in ranks)
 
-        def timed(step):
+        last_phases = {}
+
+        def timed(step, tag):
             for it in range(args.warmup + args.steps):
                 if it == args.warmup:
                     torch.cuda.synchronize()
@@ -296,6 +298,7 @@ def run_gpu(args):
                 Me = step(it)
                 for sd in (0, 1):
                     rk_h[sd].numpy()[:] = Me.ranks(sd)
+                last_phases[tag] = [float(v) for v in Me.phase_ms()]
                 del Me
             e1.record(stream)
             torch.cuda.synchronize()
@@ -303,7 +306,7 @@ def run_gpu(args):
 
         seq = None
         if args.nearfield == 0:
-            e2e_ms = timed(lambda it: D.dh2_compress_host(T, Gh.t(), eps=args.eps, mode=mode))
+            e2e_ms = timed(lambda it: D.dh2_compress_host(T, Gh.t(), eps=args.eps, mode=mode), "host")
         Gdev = torch.empty_like(Gh, device=dev)
         h2d_ev = []
 
@@ -317,7 +320,7 @@ def run_gpu(args):
                 h2d_ev.append(eh)
             return D.dh2_compress(T, Gdev.t(), eps=args.eps, mode=mode, nearfield=args.nearfield)
 
-        seq_ms = timed(copy_then_compress)
+        seq_ms = timed(copy_then_compress, "seq")
         h2d_ms = sum(a.elapsed_time(b) for a, b in h2d_ev) / len(h2d_ev)
         seq = {"ms_per_step": seq_ms, "value": in_bytes / (seq_ms * 1e-3) / 1e9, "h2d_ms": h2d_ms,
                "h2d_gbs": in_bytes / (h2d_ms * 1e-3) / 1e9}
@@ -326,7 +329,9 @@ def run_gpu(args):
         e2e = {"value": in_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h,
                "api": "dh2_compress_host" if args.nearfield == 0 else "H2D copy + dh2_compress",
-               "copy_then_compress": seq}
+               # host path phases: [panel copies with the leaf work overlapped, 0, 0, level steps,
+               # expansion, projection]
+               "phases_ms": last_phases.get("host"), "copy_then_compress": seq}
         del Gh, Gdev
     peaks, src = _peaks()
     adm_bytes = elem * st.adm_fraction * args.n * args.n

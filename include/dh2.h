@@ -162,7 +162,8 @@ dh2_status dh2_compress(const dh2_tree* tree, const void* G, dh2_dtype dtype, in
  * clusters of the shallowest level that holds an admissible block, on a
  * second stream: each panel's block norms, nearfield copies and column-basis
  * leaf factors (which read only that panel's columns of G, Section 6 applied
- * to G^*) run while the next panel is copied.  Copy mode only
+ * to G^*), and the row-basis leaf factors whose columns lie in the panels
+ * copied so far, run while the next panel is copied.  Copy mode only
  * (params->nearfield == 0): the buffer is reused by the next call on the same
  * tree, so calls on one tree must be ordered (same stream, or synchronised).
  * The call returns when the compression is complete, so G_host may be freed

@@ -576,7 +576,21 @@ void make_panel_plan(const Tree& tr, PanelPlan& pp) {
       uint32_t code;
     };
     std::vector<std::vector<std::vector<E>>> cl(K, std::vector<std::vector<E>>(kLeafClasses));
-    std::vector<std::vector<E>> rl(kLeafClasses);
+    std::vector<std::vector<std::vector<E>>> rl(K, std::vector<std::vector<E>>(kLeafClasses));
+    // row basis: the last panel a pair reads (its own blocks' column clusters
+    // and, recursively, its father pairs')
+    const Side& S0 = tr.side[kSideRow];
+    std::vector<int> lastp(S0.pairs.size(), -1);
+    std::function<int(int64_t)> last = [&](int64_t p) -> int {
+      if (lastp[p] >= 0) return lastp[p];
+      int m = 0;
+      for (int32_t b : S0.pairs[p].own) {
+        const Block& B = tr.blocks[b];
+        m = std::max(m, panel_of((int64_t)tr.start[B.s] + tr.size[B.s] - 1));
+      }
+      for (const auto& seg : S0.pairs[p].parents) m = std::max(m, last(seg.first));
+      return lastp[p] = m;
+    };
     for (int sd = 0; sd < 2; ++sd)
       for (int64_t p : tr.side[sd].leaf_pairs) {
         const int32_t c = tr.side[sd].pairs[p].cluster;
@@ -584,7 +598,7 @@ void make_panel_plan(const Tree& tr, PanelPlan& pp) {
         const E e{(double)m * m * (double)tr.side[sd].pairs[p].ncols,
                   (uint32_t)((sd << kCodeSideShift) | (int32_t)p)};
         if (sd == kSideCol) cl[panel_of(tr.start[c])][leaf_class(m)].push_back(e);
-        else rl[leaf_class(m)].push_back(e);
+        else rl[last(p)][leaf_class(m)].push_back(e);
       }
     auto codes = [](std::vector<E>& v) {
       std::stable_sort(v.begin(), v.end(), [](const E& a, const E& b) { return a.cost > b.cost; });
@@ -594,10 +608,12 @@ void make_panel_plan(const Tree& tr, PanelPlan& pp) {
       return out;
     };
     pp.col_leaf.assign(K, std::vector<std::vector<uint32_t>>(kLeafClasses));
-    pp.row_leaf.assign(kLeafClasses, {});
+    pp.row_leaf.assign(K, std::vector<std::vector<uint32_t>>(kLeafClasses));
     for (int k = 0; k < K; ++k)
-      for (int c = 0; c < kLeafClasses; ++c) pp.col_leaf[k][c] = codes(cl[k][c]);
-    for (int c = 0; c < kLeafClasses; ++c) pp.row_leaf[c] = codes(rl[c]);
+      for (int c = 0; c < kLeafClasses; ++c) {
+        pp.col_leaf[k][c] = codes(cl[k][c]);
+        pp.row_leaf[k][c] = codes(rl[k][c]);
+      }
     return true;
   };
   if (!assign(false)) assign(true);
@@ -730,13 +746,15 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     const PanelPlan& pl = *hs->plan;
     const Tree& tr = Ms[0]->tree->tr;
     hK = (int)pl.col.size() - 1;
-    hl.resize((size_t)hK + 1 + (size_t)(hK + 1) * kLeafClasses);
+    // lists: blocks per panel, blocks across panels, then per panel the
+    // column-basis and the row-basis leaves per class
+    hl.resize((size_t)hK + 1 + (size_t)2 * hK * kLeafClasses);
     for (int k = 0; k < hK; ++k) hl[k].codes = &pl.blk[k];
     hl[hK].codes = &pl.blk_rest;
-    for (int k = 0; k <= hK; ++k)
+    for (int k = 0; k < 2 * hK; ++k)
       for (int c = 0; c < kLeafClasses; ++c) {
         HList& L = hl[(size_t)hK + 1 + (size_t)k * kLeafClasses + c];
-        L.codes = k < hK ? &pl.col_leaf[k][c] : &pl.row_leaf[c];
+        L.codes = k < hK ? &pl.col_leaf[k][c] : &pl.row_leaf[k - hK][c];
         for (uint32_t code : *L.codes) {
           const int64_t nc = tr.side[(code >> kCodeSideShift) & 1u].pairs[code & kCodePairMask].ncols;
           for (int64_t j0 = 0; j0 < nc; j0 += kRTile) L.tiles.push_back(((uint64_t)code << 32) | (uint64_t)j0);
@@ -870,10 +888,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       }
   };
   if (hs) {
-    // Host-resident G: copied panel by panel on a second stream.  A panel's
-    // block norms (and nearfield copies) and its column-basis leaf factors
-    // and R run as soon as it has arrived, under the copy of the next; the
-    // row-basis leaves read every panel and follow the last one.
+    // Host-resident G: copied panel by panel on a second stream.  As soon as
+    // a panel has arrived, its block norms (and nearfield copies), its
+    // column-basis leaf factors and R, and the row-basis leaves whose columns
+    // lie in the panels so far run, under the copy of the next panel.
     const PanelPlan& pl = *hs->plan;
     dh2_matrix* M = Ms[0];
     const int64_t n = M->tree->tr.n;
@@ -903,21 +921,21 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         ++nlaunch;
       }
       colw_side(kSideCol);
-      const HList* L = &hl[(size_t)hK + 1 + (size_t)k * kLeafClasses];
-      leaf_lists(L);
-      leaf_rq(L);
+      const HList* Lc = &hl[(size_t)hK + 1 + (size_t)k * kLeafClasses];
+      leaf_lists(Lc);
+      leaf_rq(Lc);
+      colw_side(kSideRow);
+      const HList* Lr = &hl[(size_t)hK + 1 + (size_t)(hK + k) * kLeafClasses];
+      leaf_lists(Lr);
+      leaf_rq(Lr);
     }
     if (!pl.blk_rest.empty()) {
       launch_norms_near<T>(d_na, hl[hK].d_codes, (int)pl.blk_rest.size(), st);
       ++nlaunch;
     }
-    colw_side(kSideRow);
     DH2_PHASE_SYNC("panels");
     cudaEventRecord(ev[1], st);
-    const HList* Lr = &hl[(size_t)hK + 1 + (size_t)hK * kLeafClasses];
-    leaf_lists(Lr);
     cudaEventRecord(ev[2], st);
-    leaf_rq(Lr);
     for (cudaEvent_t e : pev)
       if (e) cudaEventDestroy(e);
     if (cs) cudaStreamDestroy(cs);

@@ -106,14 +106,17 @@ void free_tree_device(Tree& tr);
 // the shallowest level that holds an admissible block (or leaves above it),
 // grouped into ranges of similar width.  Every admissible block's column
 // cluster lies in one panel, and so does every column-basis leaf pair
-// together with the blocks it inherits from its ancestors.  Launch codes as
-// in the compression schedule (side << 25 | pair, or block).
+// together with the blocks it inherits from its ancestors; a row-basis leaf
+// pair can start once the last panel its columns touch has arrived.  Launch
+// codes as in the compression schedule (side << 25 | pair, or block).
 struct PanelPlan {
   std::vector<int64_t> col;                                  // panel k: columns [col[k], col[k+1])
   std::vector<std::vector<uint32_t>> blk;                    // per panel: blocks whose columns lie in it
   std::vector<uint32_t> blk_rest;                            // blocks across panels (inadmissible only)
   std::vector<std::vector<std::vector<uint32_t>>> col_leaf;  // per panel, per size class: column-basis leaves
-  std::vector<std::vector<uint32_t>> row_leaf;               // per size class: row-basis leaves
+  // per panel k, per size class: row-basis leaves whose columns (own and
+  // inherited blocks) all lie in panels 0..k
+  std::vector<std::vector<std::vector<uint32_t>>> row_leaf;
 };
 
 }  // namespace dh2
