@@ -519,8 +519,14 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
 }
 
 // Panel plan of a tree for a host-resident G (see PanelPlan).
+#ifndef DH2_HOST_PANELS
+#define DH2_HOST_PANELS 4  // column panels of a host-resident G
+#endif
+
 void make_panel_plan(const Tree& tr, PanelPlan& pp) {
-  constexpr int kPanels = 8;
+  // few panels: each panel's leaf lists must still fill the GPU (a launch of
+  // a few hundred pairs leaves most SMs idle in its last wave)
+  constexpr int kPanels = DH2_HOST_PANELS;
   const int64_t n = tr.n;
   int32_t lmin = INT32_MAX;
   for (const Block& B : tr.blocks)
