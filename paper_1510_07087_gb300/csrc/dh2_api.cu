@@ -63,7 +63,7 @@ struct Tree::Dev {
   int64_t S_elems = 0, near_elems = 0;
   int64_t nadm = 0, ninadm = 0;
   int64_t nleaf_codes = 0;
-  // leaf codes grouped by size class (rows <= 32, <= 48, <= 64, more), each
+  // leaf codes grouped by size class (rows <= 32, <= 40, <= 48, <= 64, more), each
   // group costliest first; the pair kernel's CTA is sized to the class
   int64_t leaf_class_begin[kLeafClasses + 1] = {};
   int32_t leaf_class_maxm[kLeafClasses] = {};
