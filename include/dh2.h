@@ -140,6 +140,11 @@ dh2_status dh2_tree_blocks(const dh2_tree* tree, int32_t* t, int32_t* s, int32_t
 dh2_status dh2_tree_pairs(const dh2_tree* tree, int32_t side, int32_t* cluster, int32_t* dir,
                           int64_t* ncols, int32_t* is_leaf);
 dh2_status dh2_tree_pair_blocks(const dh2_tree* tree, int32_t side, int64_t* offsets, int32_t* block_ids);
+/* Column panels of dh2_compress_host (built on first use and kept in the tree):
+ * *npanels; col[0..npanels] the panel boundaries in the permuted order (may be
+ * NULL); row_panel[p] for each row-basis pair p the panel after whose arrival
+ * its leaf factor runs, -1 for a non-leaf pair (may be NULL). */
+dh2_status dh2_tree_panels(const dh2_tree* tree, int32_t* npanels, int64_t* col, int32_t* row_panel);
 
 /* ---------------------------------------------------------------- compression (GPU) */
 

@@ -61,6 +61,7 @@ SIGNATURES = [
     ("dh2_tree_blocks", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("dh2_tree_pairs", c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
     ("dh2_tree_pair_blocks", c_int32, [c_void_p, c_int32, c_void_p, c_void_p]),
+    ("dh2_tree_panels", c_int32, [c_void_p, POINTER(c_int32), c_void_p, c_void_p]),
     ("dh2_compress", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p,
                                POINTER(c_void_p)]),
     ("dh2_compress_host", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p,
@@ -178,6 +179,16 @@ class Tree:
         ids = np.empty(max(1, int(off[-1])), dtype=np.int32)
         _check(_lib().dh2_tree_pair_blocks(self.handle, side, _ptr(off), _ptr(ids)), "dh2_tree_pair_blocks")
         return off, ids[:int(off[-1])]
+
+    def panels(self):
+        """Column panels of the host-input compression: boundaries and, per row-basis pair, the
+        panel after which its leaf factor runs (-1 for non-leaf pairs)."""
+        k = c_int32()
+        _check(_lib().dh2_tree_panels(self.handle, byref(k), None, None), "dh2_tree_panels")
+        col = np.empty(k.value + 1, dtype=np.int64)
+        rp = np.empty(self.stats().npairs[0], dtype=np.int32)
+        _check(_lib().dh2_tree_panels(self.handle, byref(k), _ptr(col), _ptr(rp)), "dh2_tree_panels")
+        return col, rp
 
 
 def dh2_tree_build(points: np.ndarray, leaf_size: int = 32, kappa: float = 4.0,

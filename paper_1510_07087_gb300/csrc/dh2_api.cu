@@ -1265,6 +1265,27 @@ dh2_status dh2_tree_pair_blocks(const dh2_tree* T, int32_t side, int64_t* offset
   return DH2_OK;
 }
 
+dh2_status dh2_tree_panels(const dh2_tree* Tc, int32_t* npanels, int64_t* col, int32_t* row_panel) {
+  if (!Tc || !npanels) return DH2_EINVAL;
+  dh2_tree* T = const_cast<dh2_tree*>(Tc);  // the plan is a cache of the handle
+  if (!T->plan_built) {
+    make_panel_plan(T->tr, T->plan);
+    T->plan_built = true;
+  }
+  const PanelPlan& pl = T->plan;
+  const int K = (int)pl.col.size() - 1;
+  *npanels = K;
+  if (col) std::memcpy(col, pl.col.data(), sizeof(int64_t) * pl.col.size());
+  if (row_panel) {
+    const Side& S = T->tr.side[kSideRow];
+    for (size_t p = 0; p < S.pairs.size(); ++p) row_panel[p] = -1;
+    for (int k = 0; k < K; ++k)
+      for (const auto& list : pl.row_leaf[k])
+        for (uint32_t code : list) row_panel[code & kCodePairMask] = k;
+  }
+  return DH2_OK;
+}
+
 }  // extern "C"
 
 namespace {

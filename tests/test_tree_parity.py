@@ -106,3 +106,36 @@ def test_invalid_arguments_rejected():
     bad[3, 1] = np.nan
     with pytest.raises(b.DH2Error):
         b.dh2_tree_build(bad, 16, 4.0)
+
+
+@pytest.mark.parametrize("kind,n,kappa,leaf,eta1,eta2,rule", CASES)
+def test_host_input_panels(kind, n, kappa, leaf, eta1, eta2, rule):
+    """Schedule of dh2_compress_host: panels are unions of whole clusters; every admissible
+    block's column cluster lies in one panel; a column-basis leaf pair's blocks (own and
+    inherited) lie in the panel of its cluster; a row-basis leaf pair runs after the last panel
+    its blocks' columns touch."""
+    b = _lib_or_skip()
+    T = b.dh2_tree_build(_points(kind, n), leaf, kappa, eta1, eta2, rule)
+    col, row_panel = T.panels()
+    cl = T.clusters()
+    start, size = cl["start"].astype(np.int64), cl["size"].astype(np.int64)
+    assert col[0] == 0 and col[-1] == n and np.all(np.diff(col) > 0)
+    assert set(col[1:-1].tolist()) <= set(start.tolist())
+    panel = lambda j: int(np.searchsorted(col, j, side="right") - 1)  # noqa: E731
+    blk = T.blocks()
+    s_first = np.array([panel(j) for j in start[blk[:, 1]]])
+    s_last = np.array([panel(j) for j in start[blk[:, 1]] + size[blk[:, 1]] - 1])
+    adm = blk[:, 2] == 1
+    assert np.array_equal(s_first[adm], s_last[adm])
+    for side in (0, 1):
+        pr = T.pairs(side)
+        off, ids = T.pair_blocks(side)
+        for p in range(len(pr["cluster"])):
+            bl = ids[off[p]:off[p + 1]]
+            if side == 1:
+                if pr["leaf"][p] and len(bl):
+                    assert set(s_first[bl].tolist()) == {panel(start[pr["cluster"][p]])}
+            elif pr["leaf"][p]:
+                assert row_panel[p] == (int(s_last[bl].max()) if len(bl) else 0)
+            else:
+                assert row_panel[p] == -1
