@@ -23,12 +23,13 @@ namespace dh2 {
 
 namespace {
 
-// f(i) for i in [0, n) on up to 16 host threads, contiguous ranges (each f(i)
-// writes only its own outputs, so the result does not depend on the split).
+// f(i) for i in [0, n) on up to 16 host threads, contiguous ranges of at
+// least `grain` indices (each f(i) writes only its own outputs, so the result
+// does not depend on the split).
 template <typename F>
-void parallel_for(int64_t n, F f) {
+void parallel_for(int64_t n, F f, int64_t grain = 256) {
   const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
-  const int64_t nt = std::min<int64_t>({hw, (int64_t)16, std::max<int64_t>(1, n / 256)});
+  const int64_t nt = std::min<int64_t>({hw, (int64_t)16, std::max<int64_t>(1, n / grain)});
   if (nt <= 1) {
     for (int64_t i = 0; i < n; ++i) f(i);
     return;
@@ -153,21 +154,28 @@ struct Builder {
     return cid;
   }
 
-  // Def. 2 by the standard recursion with Eqs. (adm_standard), (adm_parabolic).
-  void blocks(int32_t t, int32_t s) {
+  // Def. 2 by the standard recursion with Eqs. (adm_standard), (adm_parabolic),
+  // appending the leaves to `out` in depth-first order.  Below depth `cut`
+  // the subtrees are not entered: their (t, s) pairs are appended to `defer`
+  // and a placeholder (adm = -1, cb = index in defer) marks their place.
+  void blocks(int32_t t, int32_t s, std::vector<Block>& out, int depth, int cut,
+              std::vector<std::pair<int32_t, int32_t>>* defer) const {
     const double md = std::max(tr.diam[t], tr.diam[s]);
     const double d = box_dist(&tr.lo[3 * t], &tr.hi[3 * t], &tr.lo[3 * s], &tr.hi[3 * s]);
     const double eta2 = tr.params.eta2, kappa = tr.params.kappa;
     const bool adm = d > 0.0 && md <= eta2 * d && kappa * (md * md) <= eta2 * d;
     if (adm) {
-      tr.blocks.push_back({t, s, 1, -1});
+      out.push_back({t, s, 1, -1});
     } else if (tr.is_leaf(t) || tr.is_leaf(s)) {
-      tr.blocks.push_back({t, s, 0, -1});
+      out.push_back({t, s, 0, -1});
+    } else if (defer && depth >= cut) {
+      out.push_back({t, s, -1, (int32_t)defer->size()});
+      defer->push_back({t, s});
     } else {
       const int32_t ts[2] = {tr.son0[t], tr.son1[t]};
       const int32_t ss[2] = {tr.son0[s], tr.son1[s]};
       for (int i = 0; i < 2; ++i)
-        for (int j = 0; j < 2; ++j) blocks(ts[i], ss[j]);
+        for (int j = 0; j < 2; ++j) blocks(ts[i], ss[j], out, depth + 1, cut, defer);
     }
   }
 };
@@ -183,52 +191,78 @@ void build_side(Tree& tr, int side) {
     const Block& B = tr.blocks[b];
     return side == kSideRow ? tr.start[B.s] : tr.start[B.t];
   };
-  // own admissible blocks per cluster and direction, ordered by the other cluster's start
-  std::vector<std::map<int32_t, std::vector<int32_t>>> own(nc);
+  // own admissible blocks per cluster and direction, ordered by the other
+  // cluster's start: one sorted array with a range per cluster (clusters at
+  // one level have distinct starts, so the order has no ties)
+  struct OwnE {
+    int32_t r, c, os, b;
+  };
+  std::vector<OwnE> ownv;
   for (int32_t b = 0; b < (int32_t)tr.blocks.size(); ++b) {
     const Block& B = tr.blocks[b];
     if (!B.adm) continue;
-    const int32_t r = side == kSideRow ? B.t : B.s;
-    own[r][B.cb].push_back(b);
+    ownv.push_back({side == kSideRow ? B.t : B.s, B.cb, other_start(b), b});
   }
-  for (auto& m : own)
-    for (auto& kv : m)
-      std::sort(kv.second.begin(), kv.second.end(),
-                [&](int32_t a, int32_t b) { return other_start(a) < other_start(b); });
+  std::sort(ownv.begin(), ownv.end(), [](const OwnE& x, const OwnE& y) {
+    if (x.r != y.r) return x.r < y.r;
+    if (x.c != y.c) return x.c < y.c;
+    return x.os < y.os;
+  });
+  std::vector<int64_t> own_ptr(nc + 1, 0);
+  for (const OwnE& e : ownv) ++own_ptr[e.r + 1];
+  for (int32_t r = 0; r < nc; ++r) own_ptr[r + 1] += own_ptr[r];
 
   // used pairs, top-down (pre-order numbering puts fathers first).  Column
   // order of (t, c): own blocks, then for each father pair (father, c_p) with
   // sd(c_p) = c in ascending c_p the father's columns -- so every father pair
   // is one contiguous column range of each of its son pairs.
   std::vector<Pair> tmp;
-  std::vector<std::map<int32_t, int64_t>> pair_of(nc);
+  std::vector<std::vector<std::pair<int32_t, int64_t>>> pair_of(nc);  // per cluster: (direction, pair), ascending
+  std::vector<std::pair<int32_t, int64_t>> segs;                      // (son direction, father pair)
+  std::vector<int32_t> used;
   for (int32_t r = 0; r < nc; ++r) {
-    std::map<int32_t, std::vector<int64_t>> segs;
+    segs.clear();
     const int32_t par = tr.parent[r];
     if (par >= 0)
-      for (auto& kv : pair_of[par]) segs[tr.sd_of(tr.level[par], kv.first)].push_back(kv.second);
-    std::map<int32_t, int> used;
-    for (auto& kv : own[r]) used[kv.first] = 1;
-    for (auto& kv : segs) used[kv.first] = 1;
-    for (auto& kv : used) {
-      const int32_t c = kv.first;
+      for (const auto& kv : pair_of[par]) segs.push_back({tr.sd_of(tr.level[par], kv.first), kv.second});
+    // by son direction; the father pairs of one direction stay in ascending c_p
+    std::stable_sort(segs.begin(), segs.end(),
+                     [](const std::pair<int32_t, int64_t>& x, const std::pair<int32_t, int64_t>& y) {
+                       return x.first < y.first;
+                     });
+    used.clear();
+    for (int64_t i = own_ptr[r]; i < own_ptr[r + 1]; ++i) used.push_back(ownv[i].c);
+    for (const auto& sg : segs) used.push_back(sg.first);
+    std::sort(used.begin(), used.end());
+    used.erase(std::unique(used.begin(), used.end()), used.end());
+    int64_t oi = own_ptr[r];
+    size_t si = 0;
+    for (const int32_t c : used) {
       Pair P;
       P.cluster = r;
       P.dir = c;
       P.level = tr.level[r];
       P.leaf = tr.is_leaf(r) ? 1 : 0;
       int64_t off = 0;
-      auto it = own[r].find(c);
-      if (it != own[r].end())
-        for (int32_t b : it->second) { P.own.push_back(b); off += width(b); }
-      auto is = segs.find(c);
-      if (is != segs.end())
-        for (int64_t pp : is->second) { P.parents.push_back({pp, off}); off += tmp[pp].ncols; }
+      for (; oi < own_ptr[r + 1] && ownv[oi].c == c; ++oi) {
+        P.own.push_back(ownv[oi].b);
+        off += width(ownv[oi].b);
+      }
+      for (; si < segs.size() && segs[si].first == c; ++si) {
+        P.parents.push_back({segs[si].second, off});
+        off += tmp[segs[si].second].ncols;
+      }
       P.ncols = off;
-      pair_of[r][c] = (int64_t)tmp.size();
+      pair_of[r].push_back({c, (int64_t)tmp.size()});
       tmp.push_back(std::move(P));
     }
   }
+  auto pair_at = [&](int32_t r, int32_t c) -> int64_t {
+    const auto& v = pair_of[r];
+    const auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(c, (int64_t)INT64_MIN));
+    if (it == v.end() || it->first != c) throw std::logic_error("son pair not used");
+    return it->second;
+  };
   // son links
   for (int64_t p = 0; p < (int64_t)tmp.size(); ++p) {
     Pair& P = tmp[p];
@@ -236,7 +270,7 @@ void build_side(Tree& tr, int side) {
     const int32_t cs = tr.sd_of(P.level, P.dir);
     const int32_t sons[2] = {tr.son0[P.cluster], tr.son1[P.cluster]};
     for (int j = 0; j < 2; ++j) {
-      const int64_t q = pair_of[sons[j]].at(cs);
+      const int64_t q = pair_at(sons[j], cs);
       P.son_pair[j] = q;
       bool found = false;
       for (auto& seg : tmp[q].parents)
@@ -352,7 +386,22 @@ dh2_status build_tree(const double* pts, int64_t n, const dh2_tree_params& p, Tr
     }
     tr.sd[l].assign(tr.dirs[l].size() / 3, l < tr.depth ? -2 : -1);
   }
-  B.blocks(0, 0);
+  {
+    // the block tree to depth 3, then its subtrees on several threads, spliced
+    // back in depth-first order
+    std::vector<Block> top;
+    std::vector<std::pair<int32_t, int32_t>> defer;
+    B.blocks(0, 0, top, 0, 3, &defer);
+    std::vector<std::vector<Block>> sub(defer.size());
+    parallel_for(
+        (int64_t)defer.size(),
+        [&](int64_t k) { B.blocks(defer[k].first, defer[k].second, sub[k], 0, 0, nullptr); }, 1);
+    tr.blocks.clear();
+    for (const Block& b : top) {
+      if (b.adm >= 0) tr.blocks.push_back(b);
+      else tr.blocks.insert(tr.blocks.end(), sub[b.cb].begin(), sub[b.cb].end());
+    }
+  }
   // block directions c_b: nearest direction to (m_t - m_s)/|m_t - m_s|
   double adm_entries = 0.0;
   for (Block& b : tr.blocks) {
