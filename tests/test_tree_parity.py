@@ -108,6 +108,29 @@ def test_invalid_arguments_rejected():
         b.dh2_tree_build(bad, 16, 4.0)
 
 
+def test_host_input_arguments_rejected_before_any_device_work():
+    """dh2_compress_host checks its arguments on the host first: view mode (the staging buffer
+    is reused), ld < n, an unknown dtype and null pointers return DH2_EINVAL with no handle."""
+    b = _lib_or_skip()
+    n = 64
+    T = b.dh2_tree_build(fibonacci_sphere(n), 16, 4.0)
+    host = np.zeros(2 * n * n, dtype=np.float32)
+    lib = b._lib()
+
+    def call(G, dtype, ld, nearfield, params=True):
+        p = b.CompressParams(1e-4, 2.0 / 3.0, 0, b.MODE_FP32, nearfield, 0)
+        h = b.c_void_p(12345)
+        st = lib.dh2_compress_host(T.handle, G, dtype, ld, b.byref(p) if params else None, None, b.byref(h))
+        return st, h.value
+
+    ptr = b._ptr(host)
+    assert call(ptr, b.DH2_C64, n, 1) == (1, None)          # view mode
+    assert call(ptr, b.DH2_C64, n - 1, 0) == (1, None)      # ld < n
+    assert call(ptr, 7, n, 0) == (1, None)                  # unknown dtype
+    assert call(None, b.DH2_C64, n, 0) == (1, None)         # no matrix
+    assert call(ptr, b.DH2_C64, n, 0, params=False) == (1, None)
+
+
 @pytest.mark.parametrize("kind,n,kappa,leaf,eta1,eta2,rule", CASES)
 def test_host_input_panels(kind, n, kappa, leaf, eta1, eta2, rule):
     """Schedule of dh2_compress_host: panels are unions of whole clusters; every admissible
