@@ -136,28 +136,38 @@ def workload_matrix(args, P, Nrm, h, dtype, dev):
 
 # --------------------------------------------------------------------------- oracle baseline
 
+_ORACLE_SETUP = {}
+
+
+def _oracle_setup(args):
+    """The oracle's tree, column sets and per-pair work for the workload (built once per process)."""
+    key = (args.n, args.kappa, args.leaf, args.eta1, args.eta2, args.eps, args.kernel)
+    if key not in _ORACLE_SETUP:
+        from oracle import dh2_oracle as O
+        from synth import mean_nn_distance
+
+        pts, nrm = workload_points(args)
+        tp = O.TreeParams(leaf_size=args.leaf, kappa=args.kappa, eta1=args.eta1, eta2=args.eta2)
+        cp = O.CompressParams(eps=args.eps)
+        tr = O.build_tree(pts, tp)
+        F = O.column_sets(tr, "row")
+        leaf_pairs = [(t, c) for t in range(tr.nclusters()) if tr.is_leaf(t) for c in F[t]]
+        work = {}
+        for (t, c) in leaf_pairs:
+            N = sum(tr.size[tr.blocks[b][1]] for b in F[t][c])
+            work[(t, c)] = tr.size[t] ** 2 * N
+        _ORACLE_SETUP[key] = (O, cp, tr, F, leaf_pairs, work, mean_nn_distance(pts), pts[tr.perm],
+                              nrm[tr.perm] if nrm is not None else None)
+    return _ORACLE_SETUP[key]
+
+
 def oracle_sample(args, budget_s: float, seed: int = 0):
     """Time the FP64 oracle's leaf step on a seeded sample of leaf pairs of the
     workload and scale by work (m_t^2 * #F_tc summed over all leaf pairs of
     both bases) to a whole-compression time.  Returns (seconds_total_est,
     sample description, threads)."""
-    from oracle import dh2_oracle as O
-    from synth import mean_nn_distance
-
-    pts, nrm = workload_points(args)
-    tp = O.TreeParams(leaf_size=args.leaf, kappa=args.kappa, eta1=args.eta1, eta2=args.eta2)
-    cp = O.CompressParams(eps=args.eps)
-    tr = O.build_tree(pts, tp)
-    h = mean_nn_distance(pts)
-    P = pts[tr.perm]
-    Nrm = nrm[tr.perm] if nrm is not None else None
-    F = O.column_sets(tr, "row")
+    O, cp, tr, F, leaf_pairs, work, h, P, Nrm = _oracle_setup(args)
     eps_l = [O.eps_hat(cp) * cp.zeta ** l for l in range(tr.depth + 1)]
-    leaf_pairs = [(t, c) for t in range(tr.nclusters()) if tr.is_leaf(t) for c in F[t]]
-    work = {}
-    for (t, c) in leaf_pairs:
-        N = sum(tr.size[tr.blocks[b][1]] for b in F[t][c])
-        work[(t, c)] = tr.size[t] ** 2 * N
     total_work = 2.0 * sum(work.values())  # both bases
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(leaf_pairs))
@@ -421,10 +431,12 @@ def main():
             return
         vals = []
         desc, thr = "", 1
+        # each step a bounded sample: the whole run stays within a few minutes for any K
+        step_budget = max(1.0, min(args.cpu_budget, 120.0 / max(1, args.steps)))
         for _ in range(args.warmup):
-            oracle_sample(args, budget_s=max(1.0, args.cpu_budget / 5))
+            oracle_sample(args, budget_s=max(0.5, step_budget / 5))
         for s in range(args.steps):
-            est, desc, thr = oracle_sample(args, budget_s=args.cpu_budget, seed=s)
+            est, desc, thr = oracle_sample(args, budget_s=step_budget, seed=s)
             vals.append(in_bytes / est / 1e9)
         v = statistics.median(vals)
         line = {"impl": "reference", "metric": "compression wall time & input GB/s at n=32768, kappa=32, "
