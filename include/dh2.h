@@ -214,7 +214,12 @@ void dh2_matrix_free(dh2_matrix* M);
 /* y = G~ x for the compressed matrix (Section 4: forward transformation,
  * coupling, backward transformation, plus the nearfield).  x, y: device,
  * n x nrhs column-major (leading dimension n), permuted order, dtype of the
- * matrix.  y is overwritten. */
+ * matrix.  y is overwritten.  Preconditions the library cannot check (it
+ * receives plain pointers): x and y are allocations on the matrix's device
+ * holding at least n * nrhs elements of the matrix's complex type (complex64
+ * for DH2_MODE_FP32, complex128 for DH2_MODE_FP64); a shorter or wrongly typed
+ * buffer is read or written out of bounds.  The Python binding checks dtype,
+ * device, row count and shape before the call. */
 dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream);
 
 /* Same product as dh2_matvec, for callers that must not allocate device
@@ -236,7 +241,11 @@ dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs,
  *  - every call uses the same array and it keeps the last call's contents;
  *    each call writes every coefficient before reading it, but calls whose
  *    work overlaps on the GPU (different streams, or different threads without
- *    ordering) race on the array: order them on one stream.
+ *    ordering) race on the array: order them on one stream;
+ *  - the array's device address is looked up once per device and cached for
+ *    the life of the process: after cudaDeviceReset (or any other teardown of
+ *    the device's primary context) the cached address is stale, so do not
+ *    call this entry point again in such a process.
  * x, y: as for dh2_matvec; y is overwritten. */
 dh2_status dh2_matvec_noalloc(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream);
 
@@ -278,6 +287,36 @@ dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms6);
  * produced M (host int32 out). Instrumentation only: the paper has no
  * counterpart. */
 dh2_status dh2_matrix_launch_count(const dh2_matrix* M, int32_t* launches);
+
+/* Kernel classes of dh2_matrix_class_launches (instrumentation only; the paper
+ * has no counterpart).  A factor kernel's class is its row class: leaf pairs by
+ * cluster size (0: <= 32, 1: <= 40, 2: <= 48, 3: <= 64, 4: more rows),
+ * non-leaf pairs by k_t1c' + k_t2c' (0: <= 32, 1: <= 48, 2: <= 64, 3: more). */
+enum {
+  DH2_KC_LEAF_FACTOR = 0,   /* + leaf row class 0..4: leaf factorisation (Section 6, leaf step)  */
+  DH2_KC_LEAF_R = 5,        /* + leaf row class 0..4: R_tc = Q_tc^* G^omega_tc                   */
+  DH2_KC_LEVEL_FACTOR = 10, /* + non-leaf row class 0..3: factorisation of Ghat_tc               */
+  DH2_KC_LEVEL_R = 14,      /* R_tc = Qhat^* Ghat_tc of a level                                  */
+  DH2_KC_NORMS = 15,        /* block norms and nearfield copy                                    */
+  DH2_KC_COLW = 16,         /* per-column weights of the leaf column maps                        */
+  DH2_KC_CLASSIFY = 17,     /* row classes of a level's non-leaf pairs                           */
+  DH2_KC_EXPAND = 18,       /* expansion of non-leaf column bases (Eq. nested)                   */
+  DH2_KC_PROJECT = 19,      /* coupling matrices S_b                                             */
+  DH2_KC_COUNT = 32
+};
+/* Launches of the last compression that produced M, by kernel class
+ * (counts: host, DH2_KC_COUNT int32 entries; unused classes are 0). */
+dh2_status dh2_matrix_class_launches(const dh2_matrix* M, int32_t* counts);
+
+/* Test instrumentation (the paper has no counterpart): the nth device
+ * allocation the library makes from now on (every cudaMalloc and
+ * cudaMallocAsync it issues: tree upload, matrix arena, schedule lists,
+ * host-input staging buffer, matrix-vector scratch) is refused as if the
+ * device were out of memory, so that the failure path of each entry point can
+ * be checked without exhausting a GPU; the call that meets it returns
+ * DH2_ENOMEM with its output handle NULL.  nth = 0 disarms; DH2_EINVAL for
+ * nth < 0.  Process-wide, not thread-specific. */
+dh2_status dh2_debug_fail_alloc(int32_t nth);
 
 const char* dh2_status_string(dh2_status s);
 /* Library version string. */

@@ -22,6 +22,17 @@ MODE_FP64 = 0
 MODE_FP32 = 1
 SIDE_ROW = 0
 SIDE_COL = 1
+# kernel classes of Matrix.class_launches (DH2_KC_* in include/dh2.h)
+KC_LEAF_FACTOR = 0
+KC_LEAF_R = 5
+KC_LEVEL_FACTOR = 10
+KC_LEVEL_R = 14
+KC_NORMS = 15
+KC_COLW = 16
+KC_CLASSIFY = 17
+KC_EXPAND = 18
+KC_PROJECT = 19
+KC_COUNT = 32
 
 
 class TreeParams(ctypes.Structure):
@@ -85,6 +96,8 @@ SIGNATURES = [
     ("dh2_storage", c_int32, [c_void_p, POINTER(c_double), c_void_p]),
     ("dh2_matrix_phase_ms", c_int32, [c_void_p, c_void_p]),
     ("dh2_matrix_launch_count", c_int32, [c_void_p, c_void_p]),
+    ("dh2_matrix_class_launches", c_int32, [c_void_p, c_void_p]),
+    ("dh2_debug_fail_alloc", c_int32, [c_int32]),
     ("dh2_status_string", ctypes.c_char_p, [c_int32]),
     ("dh2_version", ctypes.c_char_p, []),
 ]
@@ -291,6 +304,12 @@ class Matrix:
         _check(_lib().dh2_matrix_launch_count(self.handle, byref(out)), "dh2_matrix_launch_count")
         return int(out.value)
 
+    def class_launches(self) -> np.ndarray:
+        """Launches of the last compression by kernel class (KC_* indices)."""
+        out = np.zeros(KC_COUNT, dtype=np.int32)
+        _check(_lib().dh2_matrix_class_launches(self.handle, _ptr(out)), "dh2_matrix_class_launches")
+        return out
+
     def phase_ms(self) -> np.ndarray:
         out = np.zeros(6, dtype=np.float32)
         _check(_lib().dh2_matrix_phase_ms(self.handle, _ptr(out)), "dh2_matrix_phase_ms")
@@ -377,28 +396,50 @@ def dh2_compress_kernel_dlp(tree: Tree, points: np.ndarray, normals: np.ndarray,
     return Matrix(h.value, tree, mode, None)
 
 
+def _matvec_operands(M: Matrix, x, y) -> int:
+    """Check x and y against M before any C call (the kernels trust their sizes): CUDA tensors on the
+    current device, the matrix's complex dtype, n rows, column-major (n,) or (n, nrhs) with the same
+    shape.  Returns nrhs."""
+    import torch
+
+    want = torch.complex64 if M.mode == MODE_FP32 else torch.complex128
+    dev = torch.cuda.current_device()
+    for name, v in (("x", x), ("y", y)):
+        if not isinstance(v, torch.Tensor) or v.device.type != "cuda" or v.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if v.dtype != want:
+            raise TypeError(f"{name} must be {want} for this matrix, got {v.dtype}")
+        if v.dim() not in (1, 2) or v.shape[0] != M.tree.n:
+            raise ValueError(f"{name} must have {M.tree.n} rows")
+        if v.dim() == 2 and (v.stride(0) != 1 or v.stride(1) != v.shape[0]):
+            raise ValueError(f"{name} must be column-major (n, nrhs)")
+        if v.dim() == 1 and v.stride(0) != 1:
+            raise ValueError(f"{name} must be contiguous")
+    if tuple(x.shape) != tuple(y.shape):
+        raise ValueError("x and y must have the same shape")
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    if nrhs < 1:
+        raise ValueError("nrhs must be at least 1")
+    return nrhs
+
+
 def dh2_matvec(M: Matrix, x, y, stream=None) -> None:
     """y = G~ x; x, y torch device tensors (n,) or (n, nrhs) column-major, matrix dtype."""
-    nrhs = 1 if x.dim() == 1 else x.shape[1]
-    for v in (x, y):
-        if v.dim() == 2 and (v.stride(0) != 1 or v.stride(1) != v.shape[0]):
-            raise ValueError("x, y must be column-major (n, nrhs)")
-        if v.dim() == 1 and v.stride(0) != 1:
-            raise ValueError("x, y must be contiguous")
+    nrhs = _matvec_operands(M, x, y)
     _check(_lib().dh2_matvec(M.handle, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), nrhs,
                              c_void_p(_stream_handle(stream))), "dh2_matvec")
 
 
 def dh2_matvec_noalloc(M: Matrix, x, y, stream=None) -> None:
     """y = G~ x without any device allocation (fixed 8 MiB library scratch array)."""
-    nrhs = 1 if x.dim() == 1 else x.shape[1]
-    for v in (x, y):
-        if v.dim() == 2 and (v.stride(0) != 1 or v.stride(1) != v.shape[0]):
-            raise ValueError("x, y must be column-major (n, nrhs)")
-        if v.dim() == 1 and v.stride(0) != 1:
-            raise ValueError("x, y must be contiguous")
+    nrhs = _matvec_operands(M, x, y)
     _check(_lib().dh2_matvec_noalloc(M.handle, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), nrhs,
                                      c_void_p(_stream_handle(stream))), "dh2_matvec_noalloc")
+
+
+def dh2_debug_fail_alloc(nth: int) -> None:
+    """Refuse the nth device allocation the library makes from now on (0 disarms); test instrumentation."""
+    _check(_lib().dh2_debug_fail_alloc(int(nth)), "dh2_debug_fail_alloc")
 
 
 def dh2_error(M: Matrix, Gref=None, stream=None) -> float:

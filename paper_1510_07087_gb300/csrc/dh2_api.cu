@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -109,6 +110,7 @@ struct dh2_matrix {
   std::vector<double> eps2_h, zpow_h;
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
   int32_t launches = 0;  // kernels launched by the last compression (shared by a batch)
+  int32_t class_launches[DH2_KC_COUNT] = {};  // the same launches by kernel class
   // matrix-free mode
   int gen = 0;
   double* pts = nullptr;  // device, permuted order
@@ -125,6 +127,35 @@ size_t bytes_of(const std::vector<V>& v) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Every device allocation of the library goes through dev_malloc /
+// dev_malloc_async, so that a test can make the n-th one fail as if the device
+// were out of memory (dh2_debug_fail_alloc): 0 = off, k > 0 = the k-th
+// allocation from now is refused.
+std::atomic<int> g_fail_alloc{0};
+
+bool alloc_refused() {
+  int k = g_fail_alloc.load();
+  while (k > 0)
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1)) return k == 1;
+  return false;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (alloc_refused()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+  if (alloc_refused()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, st);
+}
 
 // Capacities: leaf rank <= min(rows, #F); non-leaf rank <= min(k_cap(t1c') +
 // k_cap(t2c'), #F, 128).  Offsets of R (k_cap x #F), Q ([E1;E2] rowcap x k_cap)
@@ -376,7 +407,7 @@ dh2_status upload_tree(Tree& tr) {
   }
   size_t total = 0;
   for (auto& b : bufs) total += align256(std::max<size_t>(b.bytes, 4));
-  if (cudaMalloc(&D->arena, total) != cudaSuccess) {
+  if (dev_malloc(&D->arena, total) != cudaSuccess) {
     cudaGetLastError();
     delete D;
     return DH2_ENOMEM;
@@ -644,8 +675,6 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   for (const dh2_matrix* M : Ms) any_gen = any_gen || M->gen != 0;
   const int nprob = (int)Ms.size();
   const int pmax = sizeof(T) == 4 ? kPmaxF32 : kPmaxF64;
-  cudaEvent_t ev[7];
-  for (int i = 0; i < 7; ++i) DH2_CUDA_TRY(cudaEventCreate(&ev[i]));
   std::vector<PairArgs<T>> pas(nprob);
   std::vector<NormsArgs<T>> nas(nprob);
   for (int i = 0; i < nprob; ++i) fill_args<T>(Ms[i], cp, pas[i], nas[i]);
@@ -769,7 +798,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (const HList& L : hl) host_bytes += align256(4 * L.codes->size()) + align256(8 * L.tiles.size());
   }
   void* scratch = nullptr;
-  DH2_CUDA_TRY(cudaMallocAsync(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + 256, st));
+  if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return DH2_ENOMEM;
+  }
   char* sp = (char*)scratch;
   PairArgs<T>* d_pa = (PairArgs<T>*)sp;
   sp += align256(sizeof(PairArgs<T>) * nprob);
@@ -839,8 +871,12 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       hp += align256(8 * L.tiles.size());
     }
   }
+  cudaEvent_t ev[7] = {};
+  for (int i = 0; i < 7 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&ev[i]);
   if (ce != cudaSuccess) {
     cudaGetLastError();
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
     cudaFreeAsync(scratch, st);
     return DH2_ECUDA;
   }
@@ -869,28 +905,35 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   }
 #endif
   cudaEventRecord(ev[0], st);
+  bool ok_launch = true;  // false once a launch needed more shared memory than the device has
   int nlaunch = 0;  // kernels launched by this compression (counted where they are issued)
+  int32_t kcl[DH2_KC_COUNT] = {};  // the same, by kernel class
+  auto counted = [&](int kc, bool launched) {
+    if (!launched) return;
+    ++nlaunch;
+    ++kcl[kc];
+  };
   auto colw_side = [&](int sd) {
     for (dh2_matrix* M : Ms) {
       launch_colw<T>(M->tree->tr.dev->gblk[sd], M->invw, (T*)M->colw[sd], M->tree->tr.side[sd].nleafcols, st);
-      nlaunch += M->tree->tr.side[sd].nleafcols > 0;
+      counted(DH2_KC_COLW, M->tree->tr.side[sd].nleafcols > 0);
     }
   };
   // leaf factors and R of one launch list per size class
   auto leaf_lists = [&](const HList* L) {
     for (int c = 0; c < kLeafClasses; ++c)
       if (!L[c].codes->empty()) {
-        launch_pair_kernel<T>(d_pa, L[c].d_codes, (int)L[c].codes->size(), even_up(std::max(2, cls_maxm[c])), false,
+        ok_launch &= launch_pair_kernel<T>(d_pa, L[c].d_codes, (int)L[c].codes->size(), even_up(std::max(2, cls_maxm[c])), false,
                               st);
-        ++nlaunch;
+        counted(DH2_KC_LEAF_FACTOR + c, true);
       }
   };
   auto leaf_rq = [&](const HList* L) {
     for (int c = 0; c < kLeafClasses; ++c)
       if (!L[c].tiles.empty()) {
-        launch_rq_kernel<T>(d_pa, L[c].d_tiles, (int)L[c].tiles.size(), even_up(std::max(2, cls_maxm[c])), false,
+        ok_launch &= launch_rq_kernel<T>(d_pa, L[c].d_tiles, (int)L[c].tiles.size(), even_up(std::max(2, cls_maxm[c])), false,
                             any_gen, st);
-        ++nlaunch;
+        counted(DH2_KC_LEAF_R + c, true);
       }
   };
   if (hs) {
@@ -924,7 +967,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       if (own) cudaStreamWaitEvent(st, pev[k], 0);
       if (!pl.blk[k].empty()) {
         launch_norms_near<T>(d_na, hl[k].d_codes, (int)pl.blk[k].size(), st);
-        ++nlaunch;
+        counted(DH2_KC_NORMS, true);
       }
       colw_side(kSideCol);
       const HList* Lc = &hl[(size_t)hK + 1 + (size_t)k * kLeafClasses];
@@ -937,7 +980,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
     if (!pl.blk_rest.empty()) {
       launch_norms_near<T>(d_na, hl[hK].d_codes, (int)pl.blk_rest.size(), st);
-      ++nlaunch;
+      counted(DH2_KC_NORMS, true);
     }
     DH2_PHASE_SYNC("panels");
     cudaEventRecord(ev[1], st);
@@ -947,7 +990,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     if (cs) cudaStreamDestroy(cs);
   } else {
     launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
-    nlaunch += n_norm > 0;
+    counted(DH2_KC_NORMS, n_norm > 0);
     colw_side(kSideRow);
     colw_side(kSideCol);
     DH2_PHASE_SYNC("norms_near");
@@ -958,8 +1001,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int c = 0; c < kLeafClasses; ++c) {
       const int64_t nc = cls_begin[c + 1] - cls_begin[c];
       if (nc > 0) {
-        launch_pair_kernel<T>(d_pa, d_leaf + cls_begin[c], (int)nc, even_up(std::max(2, cls_maxm[c])), false, st);
-        ++nlaunch;
+        ok_launch &= launch_pair_kernel<T>(d_pa, d_leaf + cls_begin[c], (int)nc, even_up(std::max(2, cls_maxm[c])), false, st);
+        counted(DH2_KC_LEAF_FACTOR + c, true);
       }
     }
     cudaEventRecord(ev[2], st);
@@ -967,9 +1010,9 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int c = 0; c < kLeafClasses; ++c) {
       const int64_t nt = tile_cls_begin[c + 1] - tile_cls_begin[c];
       if (nt > 0) {
-        launch_rq_kernel<T>(d_pa, d_ltiles + tile_cls_begin[c], (int)nt, even_up(std::max(2, cls_maxm[c])), false,
+        ok_launch &= launch_rq_kernel<T>(d_pa, d_ltiles + tile_cls_begin[c], (int)nt, even_up(std::max(2, cls_maxm[c])), false,
                             any_gen, st);
-        ++nlaunch;
+        counted(DH2_KC_LEAF_R + c, true);
       }
     }
   }
@@ -1002,7 +1045,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       int cnt[4] = {0, 0, 0, 0};
       cudaError_t e = cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), st);
       launch_classify<T>(d_pa, d_nl[l], n, d_cls, d_cnt, st);
-      ++nlaunch;
+      counted(DH2_KC_CLASSIFY, true);
       if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) {
@@ -1011,19 +1054,19 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         cnt[3] = -1;  // fall back to one launch at the level's capacity
       }
       if (cnt[3] < 0) {
-        launch_pair_kernel<T>(d_pa, d_nl[l], n, P_level[l], true, st);
-        ++nlaunch;
+        ok_launch &= launch_pair_kernel<T>(d_pa, d_nl[l], n, P_level[l], true, st);
+        counted(DH2_KC_LEVEL_FACTOR + 3, true);
       } else {
         const int Pc[4] = {32, 48, 64, P_level[l]};
         for (int c = 0; c < 4; ++c)
           if (cnt[c] > 0) {
-            launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, cnt[c], std::min(Pc[c], std::max(P_level[l], 2)),
+            ok_launch &= launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, cnt[c], std::min(Pc[c], std::max(P_level[l], 2)),
                                   true, st);
-            ++nlaunch;
+            counted(DH2_KC_LEVEL_FACTOR + c, true);
           }
       }
-      launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, any_gen, st);
-      nlaunch += n_nltiles[l] > 0;
+      ok_launch &= launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, any_gen, st);
+      counted(DH2_KC_LEVEL_R, n_nltiles[l] > 0);
       DH2_PHASE_SYNC("non-leaf pairs");
     }
   }
@@ -1036,7 +1079,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       const int64_t b = D->lvl_nl_begin[1][l], e = D->lvl_end[1][l];
       if (e > b) {
         launch_expand<T>(Wv, D->iota[1] + b, (int)(e - b), st);
-        ++nlaunch;
+        counted(DH2_KC_EXPAND, true);
       }
       DH2_PHASE_SYNC("expand");
     }
@@ -1058,7 +1101,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     pj.S = (C2<T>*)M->S;
     pj.Soff = D->Soff;
     launch_project<T>(pj, (int)D->nadm, st);
-    nlaunch += D->nadm > 0;
+    counted(DH2_KC_PROJECT, D->nadm > 0);
     DH2_PHASE_SYNC("project");
   }
   cudaEventRecord(ev[6], st);
@@ -1075,6 +1118,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   for (dh2_matrix* M : Ms) {
     std::memcpy(M->phase_ms, ph, sizeof(ph));
     M->launches = nlaunch;
+    std::memcpy(M->class_launches, kcl, sizeof(kcl));
   }
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return DH2_ECUDA;
 #ifdef DH2_CHECK
@@ -1089,7 +1133,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
   }
 #endif
-  uint32_t all = 0;
+  uint32_t all = ok_launch ? 0u : kStatusTooLarge;
   for (uint32_t v : status) all |= v;
   if (all & kStatusTooLarge) return DH2_EUNSUPPORTED;
   if (all & (kStatusNoConv | kStatusNaN)) return DH2_ENOCONV;
@@ -1360,7 +1404,7 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   sz[ns++] = align256(es / 2 * (size_t)tr.side[1].nleafcols);
   size_t total = 0;
   for (int i = 0; i < ns; ++i) total += sz[i];
-  if (cudaMallocAsync(&M->arena, total, M->stream) != cudaSuccess) {
+  if (dev_malloc_async(&M->arena, total, M->stream) != cudaSuccess) {
     cudaGetLastError();
     delete M;
     return DH2_ENOMEM;
@@ -1459,7 +1503,7 @@ dh2_status dh2_compress_host(const dh2_tree* Tc, const void* G_host, dh2_dtype d
     if (T->g_stage) cudaFree(T->g_stage);  // synchronises: no earlier call still reads it
     T->g_stage = nullptr;
     T->g_stage_bytes = 0;
-    if (cudaMalloc(&T->g_stage, bytes) != cudaSuccess) {
+    if (dev_malloc(&T->g_stage, bytes) != cudaSuccess) {
       cudaGetLastError();
       T->g_stage = nullptr;
       return DH2_ENOMEM;
@@ -1547,7 +1591,10 @@ dh2_status run_matvec(const dh2_matrix* M, const void* xv, void* yv, int nrhs, c
   void* buf = nullptr;
   const size_t hx = align256(sizeof(C2<T>) * D->h_elems[1] * nrhs);
   const size_t hy = align256(sizeof(C2<T>) * D->h_elems[0] * nrhs);
-  DH2_CUDA_TRY(cudaMallocAsync(&buf, hx + hy + 256, st));
+  if (dev_malloc_async(&buf, hx + hy + 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return DH2_ENOMEM;
+  }
   C2<T>* xh = (C2<T>*)buf;
   C2<T>* yh = (C2<T>*)((char*)buf + hx);
   const C2<T>* x = (const C2<T>*)xv;
@@ -1789,6 +1836,18 @@ dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts) {
 dh2_status dh2_matrix_launch_count(const dh2_matrix* M, int32_t* launches) {
   if (!M || !launches) return DH2_EINVAL;
   *launches = M->launches;
+  return DH2_OK;
+}
+
+dh2_status dh2_debug_fail_alloc(int32_t nth) {
+  if (nth < 0) return DH2_EINVAL;
+  g_fail_alloc.store(nth);
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_class_launches(const dh2_matrix* M, int32_t* counts) {
+  if (!M || !counts) return DH2_EINVAL;
+  std::memcpy(counts, M->class_launches, sizeof(M->class_launches));
   return DH2_OK;
 }
 

@@ -92,9 +92,11 @@ __device__ __forceinline__ C2<T> kernel_entry(const double* pts, const double* n
 }
 
 // One CTA per launch code: args_dev holds one PairArgs per problem (device
-// memory); P is the row capacity of the shared-memory factor (even).
+// memory); P is the row capacity of the shared-memory factor (even).  Returns
+// false, launching nothing, if the shared memory the launch needs exceeds the
+// device's per-block limit.
 template <typename T>
-void launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
+bool launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
                         cudaStream_t st);
 
 // R = Q^* A for the pairs of a pair-kernel launch, after it, by tiles of 32
@@ -102,7 +104,7 @@ void launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int 
 // kernel).  Leaf tiles of a stored G (gen false) go to a persistent kernel
 // that keeps the next tile's loads in flight; the others get one CTA per tile.
 template <typename T>
-void launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int ntiles, int P, bool from_r, bool gen,
+bool launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int ntiles, int P, bool from_r, bool gen,
                       cudaStream_t st);
 
 // Non-leaf codes of one level split by the row count of their Ghat (from the

@@ -1348,8 +1348,22 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
   cp_async_wait_all();
 }
 
+// Dynamic shared memory of `smem` bytes for kern, checked against the
+// device's opt-in limit (false: the launch cannot run, nothing was launched).
+template <typename K>
+bool set_smem(K kern, size_t smem) {
+  int dev = 0, maxopt = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      smem > (size_t)maxopt || cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
 template <typename T, int P_T, bool FROM_R, int NT>
-void launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
+bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
   constexpr int C = 16 * (NT / P_T);
   const int LDL = P + 1;
   size_t smem = (((size_t)(P + C) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
@@ -1361,8 +1375,9 @@ void launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int
   if (const char* solo = getenv("DH2_PROFILE_SOLO"))
     if (solo[0] == '1' && smem < 120 * 1024) smem = 120 * 1024;
 #endif
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!set_smem(kern, smem)) return false;
   kern<<<nblocks, NT, smem, st>>>(args, codes, P);
+  return true;
 }
 
 }  // namespace
@@ -1422,34 +1437,36 @@ __global__ void classify_kernel(const PairArgs<T>* __restrict__ args, const uint
 }
 
 template <typename T, bool FROM_R>
-void launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
+bool launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
   const size_t smem = (size_t)(32 + 2 + kRTile + 2) * P * sizeof(C2<T>);  // row-major Q block and A tile
   auto kern = rq_kernel<T, FROM_R>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!set_smem(kern, smem)) return false;
   kern<<<ntiles, 128, smem, st>>>(args, tiles, P);
+  return true;
 }
 
 template <typename T>
-void launch_rq_leaf(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
+bool launch_rq_leaf(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
   constexpr int QB = 32, LQ = QB + 2, LA = kRTile + 2;
   const size_t smem = 2 * (size_t)(LQ + LA) * P * sizeof(C2<T>);  // two stages of Q block and A tile
   auto kern = rq_leaf_kernel<T>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (!set_smem(kern, smem)) return false;
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)std::max(1, nsm) * std::max(1, per_sm));
   kern<<<grid, 128, smem, st>>>(args, tiles, (int64_t)ntiles, P);
+  return true;
 }
 
 template <typename T>
-void launch_rq_kernel(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, bool from_r, bool gen,
+bool launch_rq_kernel(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, bool from_r, bool gen,
                       cudaStream_t st) {
-  if (ntiles <= 0) return;
-  if (from_r) launch_rq<T, true>(args, tiles, ntiles, P, st);
-  else if (gen) launch_rq<T, false>(args, tiles, ntiles, P, st);
-  else launch_rq_leaf<T>(args, tiles, ntiles, P, st);
+  if (ntiles <= 0) return true;
+  if (from_r) return launch_rq<T, true>(args, tiles, ntiles, P, st);
+  if (gen) return launch_rq<T, false>(args, tiles, ntiles, P, st);
+  return launch_rq_leaf<T>(args, tiles, ntiles, P, st);
 }
 template <typename T>
 void launch_classify(const PairArgs<T>* args, const uint32_t* codes, int n, uint32_t* out, int* counts,
@@ -1459,28 +1476,27 @@ void launch_classify(const PairArgs<T>* args, const uint32_t* codes, int n, uint
 template void launch_classify<float>(const PairArgs<float>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
 template void launch_classify<double>(const PairArgs<double>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
 
-template void launch_rq_kernel<float>(const PairArgs<float>*, const uint64_t*, int, int, bool, bool, cudaStream_t);
-template void launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*, int, int, bool, bool, cudaStream_t);
+template bool launch_rq_kernel<float>(const PairArgs<float>*, const uint64_t*, int, int, bool, bool, cudaStream_t);
+template bool launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*, int, int, bool, bool, cudaStream_t);
 
 template <typename T>
-void launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
+bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
                         cudaStream_t st) {
-  if (nblocks <= 0) return;
+  if (nblocks <= 0) return true;
   if (!from_r) {
-    if (P <= 32) launch_one<T, 32, false, 128>(args, codes, nblocks, P, st);
-    else if (P <= 40) launch_one<T, 40, false, 160>(args, codes, nblocks, P, st);
-    else if (P <= 48) launch_one<T, 48, false, 192>(args, codes, nblocks, P, st);
-    else if (P <= 64) launch_one<T, 64, false, 256>(args, codes, nblocks, P, st);
-    else launch_one<T, 128, false, 256>(args, codes, nblocks, P, st);
-  } else {
-    if (P <= 32) launch_one<T, 32, true, 128>(args, codes, nblocks, P, st);
-    else if (P <= 48) launch_one<T, 48, true, 192>(args, codes, nblocks, P, st);
-    else if (P <= 64) launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
-    else launch_one<T, 128, true, 256>(args, codes, nblocks, P, st);
+    if (P <= 32) return launch_one<T, 32, false, 128>(args, codes, nblocks, P, st);
+    if (P <= 40) return launch_one<T, 40, false, 160>(args, codes, nblocks, P, st);
+    if (P <= 48) return launch_one<T, 48, false, 192>(args, codes, nblocks, P, st);
+    if (P <= 64) return launch_one<T, 64, false, 256>(args, codes, nblocks, P, st);
+    return launch_one<T, 128, false, 256>(args, codes, nblocks, P, st);
   }
+  if (P <= 32) return launch_one<T, 32, true, 128>(args, codes, nblocks, P, st);
+  if (P <= 48) return launch_one<T, 48, true, 192>(args, codes, nblocks, P, st);
+  if (P <= 64) return launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
+  return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st);
 }
 
-template void launch_pair_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t);
-template void launch_pair_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t);
+template bool launch_pair_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t);
+template bool launch_pair_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t);
 
 }  // namespace dh2

@@ -1,24 +1,19 @@
-"""GPU path against the FP64 oracle, through the C ABI.
+"""GPU path against the FP64 oracle, through the C ABI (parity rules in gpu_cases.py).
 
-Parity rules (ranks, subspaces and products are compared; Q, E and S are
-unique only up to unitary changes and are never compared entrywise):
-  * FP64 mode: ranks equal to the oracle's except at truncation ties
-    (|sum_{i>=k} sigma_i^2 - eps_l^2| <= 1e-8 eps_l^2 for a k between the two);
-    with the oracle re-run at the GPU's ranks, y = G~ x agrees to 1e-11
-    relative for three seeded right-hand sides;
-  * FP32 mode (complex64 input, FP32 factorisations): singular values carry
-    absolute errors of a few u_32 * sigma_1, comparable to the truncation
-    threshold sigma ~ eps_l, so ranks may differ from the FP64 oracle's near
-    the threshold; the tests bound the fraction of differing ranks (20%) and
-    the size of a difference (3), require |G - G~|_F <= eps |G|_F against the
-    complex128 matrix, and the matrix-vector product to agree with the FP64
-    oracle at the GPU's ranks to 20 eps relative.
+The reduced-precision (FP32) bounds: at eps = 1e-4 the FP32 ranks matched the
+FP64 oracle on 10222 of 10232 pairs at n = 8192 (0.1 % differ, by one), so
+the tests allow 1 % of the ranks to differ outside ties, by at most 1.  At
+eps = 1e-6 the truncation threshold sits near the FP32 rounding level of the
+singular values (absolute errors of a few u_32 sigma_1 against eps_l of about
+5e-6 sigma_1 relative): there about 10 % of the ranks were measured to
+differ, by at most 3, and the bound is 15 %, 3.
 """
 import math
 
 import numpy as np
 import pytest
 
+from gpu_cases import (Case, check_fp64, check_reduced, colmajor, dev, fp32_case, fp64_case, rank_report)
 from oracle import dh2_oracle as O
 from synth import (dlp_matrix, ellipsoid_normals, fibonacci_sphere, helmholtz_matrix, planted_separable_matrix,
                    random_complex_vectors, random_ellipsoid)
@@ -27,91 +22,11 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-
-def _dev():
-    if not torch.cuda.is_available():
-        pytest.skip("no CUDA device")
-    import paper_1510_07087_gb300 as D
-    return D
-
-
-def _colmajor(G: np.ndarray, dtype):
-    # column-major device copy: memory of G^T row-major == G column-major
-    return torch.from_numpy(np.ascontiguousarray(G.T)).to(device="cuda", dtype=dtype).t()
-
-
-class Case:
-    def __init__(self, n, kappa, leaf, eps, mode, eta1=2 * math.sqrt(2), eta2=1.0, G=None, dir_rule=0,
-                 nearfield=0, pts=None):
-        D = _dev()
-        self.D = D
-        pts = fibonacci_sphere(n) if pts is None else pts
-        self.tp = O.TreeParams(leaf_size=leaf, kappa=kappa, eta1=eta1, eta2=eta2, dir_rule=dir_rule)
-        self.cp = O.CompressParams(eps=eps)
-        self.tr = O.build_tree(pts, self.tp)
-        if G is None:
-            G = helmholtz_matrix(pts, kappa)
-        self.G = G[np.ix_(self.tr.perm, self.tr.perm)]
-        self.T = D.dh2_tree_build(pts, leaf, kappa, eta1, eta2, dir_rule)
-        assert np.array_equal(self.T.perm(), self.tr.perm)
-        dt = torch.complex64 if mode == D.MODE_FP32 else torch.complex128
-        self.Gd = _colmajor(self.G, dt)
-        self.mode = mode
-        self.M = D.dh2_compress(self.T, self.Gd, eps=eps, mode=mode, nearfield=nearfield)
-        self.rank = {}
-        for side in (0, 1):
-            pr = self.T.pairs(side)
-            rk = self.M.ranks(side)
-            self.rank[side] = {(int(pr["cluster"][p]), int(pr["dir"][p])): int(rk[p]) for p in range(len(rk))}
-            self.pid = getattr(self, "pid", {})
-            for p in range(len(rk)):
-                self.pid[(side, int(pr["cluster"][p]), int(pr["dir"][p]))] = p
-        w = O.block_weights(self.tr, O.block_norms(self.tr, self.G), self.cp.zeta)
-        self.w = w
-        self.V = O.compress(self.tr, self.G, self.cp, "row", w)
-        self.W = O.compress(self.tr, self.G, self.cp, "col", w)
-        self.Vg = O.compress(self.tr, self.G, self.cp, "row", w, rank_override=self.rank[0])
-        self.Wg = O.compress(self.tr, self.G, self.cp, "col", w, rank_override=self.rank[1])
-        self.Sg = O.project(self.tr, self.G, self.Vg, self.Wg)
-
-    def gpu_matvec(self, x: np.ndarray) -> np.ndarray:
-        dt = self.Gd.dtype
-        xd = torch.from_numpy(np.ascontiguousarray(x.T)).to(device="cuda", dtype=dt).t()
-        yd = torch.empty_like(xd.t().contiguous()).t()
-        self.D.dh2_matvec(self.M, xd, yd)
-        torch.cuda.synchronize()
-        return yd.cpu().numpy().astype(np.complex128)
-
-
-def _tie(sig, k1, k2, eps2, tol):
-    s2 = np.concatenate([np.asarray(sig, dtype=np.float64) ** 2, [0.0]])
-    tails = np.cumsum(s2[::-1])[::-1]
-    lo, hi = min(k1, k2), max(k1, k2)
-    return any(abs(tails[min(k, len(tails) - 1)] - eps2) <= tol * eps2 for k in range(lo, hi + 1))
-
-
-def _rank_report(c: Case, tol):
-    bad, ties, total = 0, 0, 0
-    for side, B in ((0, c.V), (1, c.W)):
-        for key, ko in B.rank.items():
-            kg = c.rank[side][key]
-            total += 1
-            if kg != ko:
-                if _tie(B.sigma[key], kg, ko, B.eps_level[c.tr.level[key[0]]] ** 2, tol):
-                    ties += 1
-                else:
-                    bad += 1
-    return bad, ties, total
-
-
-def _fp64(n, kappa, leaf, eps, **kw):
-    D = _dev()
-    return Case(n, kappa, leaf, eps, D.MODE_FP64, **kw)
-
-
-def _fp32(n, kappa, leaf, eps, **kw):
-    D = _dev()
-    return Case(n, kappa, leaf, eps, D.MODE_FP32, **kw)
+_dev = dev
+_colmajor = colmajor
+_check_fp64 = check_fp64
+_fp64 = fp64_case
+_fp32 = fp32_case
 
 
 @pytest.fixture(scope="module")
@@ -122,25 +37,6 @@ def c1_fp64():
 @pytest.fixture(scope="module")
 def c1_fp32():
     return _fp32(2048, 4.0, 32, 1e-4)
-
-
-def _check_fp64(c: Case, mv_tol=1e-11):
-    bad, ties, total = _rank_report(c, 1e-8)
-    assert bad == 0, f"{bad} rank mismatches outside ties ({ties} ties) of {total}"
-    x = random_complex_vectors(c.tr.n, 3, seed=11)
-    y_ref = O.matvec(c.tr, c.G, c.Vg, c.Wg, c.Sg, x)
-    y = c.gpu_matvec(x)
-    rel = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
-    assert rel <= mv_tol, rel
-    err_gpu = c.D.dh2_error(c.M, c.Gd)
-    err_ora = O.error_fro(c.tr, c.G, c.Vg, c.Wg, c.Sg)
-    assert err_gpu <= c.cp.eps
-    assert abs(err_gpu - err_ora) <= 1e-6 * err_ora + 1e-14
-    st = c.M.storage()
-    so = O.storage(c.tr, c.Vg, c.Wg, c.Sg)
-    for k in ("V", "W", "S", "near"):
-        assert st[k] == so[k], k
-    assert st["E_V"] == so["E_V"] and st["E_W"] == so["E_W"]
 
 
 def test_fp64_config1_parity(c1_fp64):
@@ -236,31 +132,12 @@ def test_fp64_config2_parity():
 
 
 def test_fp32_config1(c1_fp32):
-    c = c1_fp32
-    bad, ties, total = _rank_report(c, 1e-3)
-    assert bad <= 0.20 * total
-    for side, B in ((0, c.V), (1, c.W)):
-        for key, ko in B.rank.items():
-            assert abs(c.rank[side][key] - ko) <= 3
-    x = random_complex_vectors(c.tr.n, 3, seed=12)
-    y_ref = O.matvec(c.tr, c.G, c.Vg, c.Wg, c.Sg, x)
-    y = c.gpu_matvec(x)
-    rel = np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref)
-    assert rel <= 20 * c.cp.eps, rel
-    G128 = _colmajor(c.G, torch.complex128)
-    err = c.D.dh2_error(c.M, G128)
-    assert err <= c.cp.eps, err
+    check_reduced(c1_fp32, max_bad_frac=0.01, max_diff=1)
 
 
-def test_fp32_config2_two_tolerances():
-    for eps in (1e-4, 1e-6):
-        c = _fp32(8192, 16.0, 32, eps)
-        bad, ties, total = _rank_report(c, 1e-3)
-        print(f"eps={eps:g}: {bad} of {total} ranks differ from the FP64 oracle outside ties")
-        assert bad <= 0.20 * total, (bad, total)
-        assert max(abs(c.rank[sd][key] - ko) for sd, B in ((0, c.V), (1, c.W)) for key, ko in B.rank.items()) <= 3
-        G128 = _colmajor(c.G, torch.complex128)
-        assert c.D.dh2_error(c.M, G128) <= eps
+@pytest.mark.parametrize("eps,frac,diff", [(1e-4, 0.01, 1), (1e-6, 0.15, 3)])
+def test_fp32_config2_two_tolerances(eps, frac, diff):
+    check_reduced(_fp32(8192, 16.0, 32, eps), max_bad_frac=frac, max_diff=diff)
 
 
 def _dlp_case(n, kappa, leaf, eps, mode):
@@ -276,12 +153,7 @@ def test_fp64_double_layer_parity():
 
 
 def test_fp32_double_layer():
-    c = _dlp_case(2048, 8.0, 32, 1e-4, _dev().MODE_FP32)
-    bad, ties, total = _rank_report(c, 1e-3)
-    assert bad <= 0.20 * total, (bad, total)
-    assert max(abs(c.rank[sd][key] - ko) for sd, B in ((0, c.V), (1, c.W)) for key, ko in B.rank.items()) <= 3
-    G128 = _colmajor(c.G, torch.complex128)
-    assert c.D.dh2_error(c.M, G128) <= c.cp.eps
+    check_reduced(_dlp_case(2048, 8.0, 32, 1e-4, _dev().MODE_FP32), max_bad_frac=0.01, max_diff=1)
 
 
 def test_status_errors_are_reported():

@@ -49,3 +49,5 @@ def test_noalloc_matvec_matches_matvec(mode_name):
     yb = torch.zeros_like(xb.t().contiguous()).t()
     with pytest.raises(D.DH2Error):
         D.dh2_matvec_noalloc(M, xb, yb)
+    torch.cuda.synchronize()
+    assert not torch.any(torch.view_as_real(yb) != 0)
