@@ -1461,6 +1461,8 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
 dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
                          double kappa, double diag, const dh2_compress_params* params, void* stream,
                          dh2_matrix** out, const double* nrm_host = nullptr) {
+  if (!out) return DH2_EINVAL;
+  *out = nullptr;  // stays NULL on every failure below
   dh2_matrix* M = nullptr;
   dh2_status s = prepare_matrix(Tc, G, dtype, ld, pts_host, kappa, diag, params, stream, &M, nrm_host);
   if (s != DH2_OK) return s;
