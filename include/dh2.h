@@ -54,10 +54,23 @@ typedef enum {
 
 typedef enum { DH2_C64 = 0, DH2_C128 = 1 } dh2_dtype;
 
-/* Arithmetic of the compression.  FP64: complex128 input and FP64 everywhere
- * (the plain form).  FP32: complex64 input, FP32 factorisations on the
- * non-squared factors, FP64 tail sums for the rank decisions. */
-typedef enum { DH2_MODE_FP64 = 0, DH2_MODE_FP32 = 1 } dh2_mode;
+/* Arithmetic of the compression.
+ *  FP64: complex128 input and FP64 everywhere (the plain form).
+ *  FP32: complex64 input, FP32 factorisations on the non-squared factors
+ *        (streamed Householder LQ), FP64 tail sums for the rank decisions.
+ *  MIXED_BF16X3: complex64 input; the leaf step of Section 6 reduces each
+ *        leaf matrix G^omega_tc to its Gram matrix on the tensor cores
+ *        (tcgen05, bf16 operands, FP32 accumulation in tensor memory) from
+ *        three 8-bit fixed-point slices per entry, scaled per row, with every
+ *        accumulation exact, so the Gram matrix is that of a matrix within
+ *        2^-23 of each row's largest entry of G^omega_tc, to ~48 bits; the
+ *        rank-revealing step is a pivoted Cholesky of it in double-float
+ *        arithmetic, followed by the same FP32 Jacobi, FP64 tail sums, R, level
+ *        steps and projection as FP32.  Leaves of at most 64 rows, dense G
+ *        only (not the matrix-free entry points).  Meant for eps down to
+ *        about 1e-5: at eps = 1e-6 the three slices no longer resolve the
+ *        tail sums (use FP32 there). */
+typedef enum { DH2_MODE_FP64 = 0, DH2_MODE_FP32 = 1, DH2_MODE_MIXED_BF16X3 = 2 } dh2_mode;
 
 /* Tree parameters (Section 3; Section 7 for the paper's values).
  *  leaf_size : a cluster with more indices is bisected (Def. 1).
@@ -80,10 +93,23 @@ typedef struct {
  *  zeta      : level factor of eps_r = eps_hat * zeta^level(r), zeta < 1/sqrt 2.
  *  err_mode  : 0 = eps_hat = eps*sqrt(1-2 zeta^2)/sqrt 2, which bounds
  *              |G - G~|_F <= eps |G|_F; 1 = eps_hat = eps.
- *  mode      : dh2_mode; must match the dtype of G (FP64 <-> C128, FP32 <-> C64).
+ *  mode      : dh2_mode; must match the dtype of G (FP64 <-> C128, FP32 and
+ *              MIXED_BF16X3 <-> C64).
  *  nearfield : 0 = copy the inadmissible blocks into the matrix handle,
  *              1 = keep a view of G.
- *  max_sweeps: cap on Jacobi sweeps per factor (0 = default 30). */
+ *  max_sweeps: cap on Jacobi sweeps per factor (0 = default 30).
+ *  rank_override: NULL, or per side (0 row, 1 column) a host array of one
+ *              rank per used pair (dh2_tree_pairs order), read during the
+ *              call; an entry >= 0 replaces the truncation rule for that pair
+ *              (clamped to the singular values the factorisation resolves and
+ *              to the rank capacity), an entry < 0 keeps the rule.  With the
+ *              ranks of another implementation (an oracle) both compute the
+ *              same approximation.  Either side's pointer may be NULL.
+ *  spin_limit: polls of a bounded device-side wait (the mixed modes' wait
+ *              for tensor-core batches) before it gives up, sets the timeout
+ *              status and returns DH2_ETIMEOUT; 0 = default (about a second).
+ *  keep_gram : mixed modes, instrumentation: keep the leaf Gram matrices in
+ *              the matrix handle for dh2_matrix_leaf_gram (0 = free them).  */
 typedef struct {
   double eps;
   double zeta;
@@ -91,6 +117,10 @@ typedef struct {
   int32_t mode;
   int32_t nearfield;
   int32_t max_sweeps;
+  const int32_t* rank_override[2];
+  int64_t spin_limit;
+  int32_t keep_gram;
+  int32_t reserved;
 } dh2_compress_params;
 
 typedef struct {
@@ -275,6 +305,19 @@ dh2_status dh2_matrix_pair_basis(const dh2_matrix* M, int32_t side, int64_t pair
  * (k_t x k_s column-major). */
 dh2_status dh2_matrix_coupling(const dh2_matrix* M, int64_t block, double* out, int64_t cap_elems,
                                int32_t* kt, int32_t* ks);
+/* Weights 1/omega_b of the blocks (Remark "Error control": omega_b =
+ * |G_b|_F zeta^-level(t) for an admissible block, 1 for a zero block; entries
+ * of inadmissible blocks are unspecified).  invw: host, nblocks doubles. */
+dh2_status dh2_matrix_block_weights(const dh2_matrix* M, double* invw);
+/* Leaf Gram matrix H = A A^* of one leaf pair from the tensor-core kernel of
+ * the mixed modes (A = G^omega_tc of Section 6's leaf step, with the weights
+ * above rounded to FP32), for a matrix compressed with keep_gram = 1:
+ * copied to the host as complex128 (hi + lo of each double-float entry),
+ * m x m column-major with m the cluster size (*m receives it).  out holds
+ * at least cap_elems complex entries.  Instrumentation only: DH2_EINVAL if
+ * the matrix kept no Gram matrices or the pair is not a leaf. */
+dh2_status dh2_matrix_leaf_gram(const dh2_matrix* M, int32_t side, int64_t pair, double* out, int64_t cap_elems,
+                                int32_t* m);
 /* Storage in stored entries (Def. "DH^2-matrix representation"):
  * parts[0..5] = V leaves, W leaves, E of V, E of W, S, nearfield; *total = sum. */
 dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts);
@@ -302,6 +345,7 @@ enum {
   DH2_KC_CLASSIFY = 17,     /* row classes of a level's non-leaf pairs                           */
   DH2_KC_EXPAND = 18,       /* expansion of non-leaf column bases (Eq. nested)                   */
   DH2_KC_PROJECT = 19,      /* coupling matrices S_b                                             */
+  DH2_KC_LEAF_GRAM = 20,    /* + leaf row class 0..3: tensor-core Gram matrices (MIXED_BF16X3)   */
   DH2_KC_COUNT = 32
 };
 /* Launches of the last compression that produced M, by kernel class

@@ -31,6 +31,8 @@ using namespace dh2;
 namespace dh2 {
 
 constexpr int kLeafClasses = 5;
+inline bool mode_f32(int mode) { return mode != DH2_MODE_FP64; }  // complex64 data, FP32 kernels
+inline bool mode_mixed(int mode) { return mode == DH2_MODE_MIXED_BF16X3; }
 inline int leaf_class(int m) { return m <= 32 ? 0 : m <= 40 ? 1 : m <= 48 ? 2 : m <= 64 ? 3 : 4; }
 
 // Device copy of a tree's work lists (one arena, uploaded on first use).
@@ -42,6 +44,7 @@ struct Tree::Dev {
   int32_t *cluster[2], *leaf[2], *start[2], *m[2], *ncols[2], *son[2], *sonoff[2], *level[2], *kcap[2],
       *rowcap[2];
   int64_t *cmoff[2], *Roff[2], *Qoff[2], *Xoff[2], *hoff[2];
+  int64_t *gram_off[2], *gram_voff[2];  // mixed modes: leaf Gram matrix offsets, window sums (-1: none)
   int32_t *gcol[2], *gblk[2];
   int64_t* seg_dst[2];  // column-map segments (expanded into gcol/gblk on upload)
   int32_t *seg_col0[2], *seg_w[2], *seg_blk[2];
@@ -61,6 +64,7 @@ struct Tree::Dev {
   // host-side sizes
   int64_t npairs[2] = {0, 0}, nleaf[2] = {0, 0};
   int64_t R_elems[2] = {0, 0}, Q_elems[2] = {0, 0}, X_elems[2] = {0, 0}, h_elems[2] = {0, 0};
+  int64_t gram_elems = 0, gram_velems = 0;  // both sides together
   int64_t S_elems = 0, near_elems = 0;
   int64_t nadm = 0, ninadm = 0;
   int64_t nleaf_codes = 0;
@@ -197,7 +201,7 @@ dh2_status upload_tree(Tree& tr) {
     D->npairs[sd] = np;
     std::vector<int32_t> cl(np), lf(np), st(np), mm(np), nco(np), son(2 * np, -1), soff(2 * np, 0), lv(np),
         kc(np), rc(np), io(np);
-    std::vector<int64_t> cmo(np), ro(np), qo(np), xo(np, 0), ho(np);
+    std::vector<int64_t> cmo(np), ro(np), qo(np), xo(np, 0), ho(np), go(np, 0), gvo(np, -1);
     int64_t R_e = 0, Q_e = 0, X_e = 0, h_e = 0;
     for (int64_t p = 0; p < np; ++p) {  // sons before fathers (level descending)
       const Pair& P = S.pairs[p];
@@ -212,6 +216,13 @@ dh2_status upload_tree(Tree& tr) {
       if (P.leaf) {
         rc[p] = tr.size[P.cluster];
         kc[p] = (int32_t)std::min<int64_t>(rc[p], P.ncols);
+        const int64_t mpd = (rc[p] + 7) & ~7;  // Gram matrix: mp x mp, window sums 2 mp x mp
+        go[p] = D->gram_elems;
+        D->gram_elems += mpd * mpd;
+        if (P.ncols > kGramWindow) {
+          gvo[p] = D->gram_velems;
+          D->gram_velems += 2 * mpd * mpd;
+        }
       } else {
         for (int j = 0; j < 2; ++j) {
           son[2 * p + j] = (int32_t)P.son_pair[j];
@@ -273,6 +284,8 @@ dh2_status upload_tree(Tree& tr) {
     add64(std::move(qo), &D->Qoff[sd]);
     add64(std::move(xo), &D->Xoff[sd]);
     add64(std::move(ho), &D->hoff[sd]);
+    add64(std::move(go), &D->gram_off[sd]);
+    add64(std::move(gvo), &D->gram_voff[sd]);
     // column maps: allocated here, expanded from the segments after the upload
     bufs.push_back({nullptr, 4 * (size_t)S.nleafcols, (void**)&D->gcol[sd]});
     bufs.push_back({nullptr, 4 * (size_t)S.nleafcols, (void**)&D->gblk[sd]});
@@ -540,6 +553,8 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   pa.ld = M->ld;
   pa.invw = M->invw;
   pa.eps2 = M->eps2;
+  pa.H = nullptr;  // set by run_compress in the mixed modes
+  for (int sd = 0; sd < 2; ++sd) pa.hoff[sd] = D->gram_off[sd];
   pa.max_sweeps = cp.max_sweeps > 0 ? cp.max_sweeps : 30;
   pa.status = M->status;
   pa.pts = M->pts;
@@ -797,10 +812,53 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       }
     for (const HList& L : hl) host_bytes += align256(4 * L.codes->size()) + align256(8 * L.tiles.size());
   }
+  // mixed modes: the leaf Gram matrices (double-float, mp x mp per leaf pair)
+  // and the window sums of the pairs with more than one window, per problem
+  const bool mixed = mode_mixed(cp.mode);
+  std::vector<size_t> gram_h_off(nprob, 0), gram_v_off(nprob, 0);
+  size_t gram_bytes = 0;
+  if (mixed) {
+    gram_bytes = align256(sizeof(GramArgs) * nprob);
+    for (int i = 0; i < nprob; ++i) {
+      const Tree::Dev* D = Ms[i]->tree->tr.dev;
+      gram_h_off[i] = gram_bytes;
+      gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);
+      gram_v_off[i] = gram_bytes;
+      gram_bytes += align256(sizeof(long long) * (size_t)D->gram_velems);
+    }
+  }
   void* scratch = nullptr;
-  if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + 256, st) != cudaSuccess) {
+  if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + gram_bytes + 256, st) !=
+      cudaSuccess) {
     cudaGetLastError();
     return DH2_ENOMEM;
+  }
+  char* const gram_base = (char*)scratch + args_bytes + codes_bytes + cls_bytes + host_bytes;
+  GramArgs* d_ga = (GramArgs*)gram_base;
+  std::vector<GramArgs> gas;
+  if (mixed) {
+    gas.resize(nprob);
+    for (int i = 0; i < nprob; ++i) {
+      const Tree::Dev* D = Ms[i]->tree->tr.dev;
+      const dh2_matrix* M = Ms[i];
+      pas[i].H = (const float4*)(gram_base + gram_h_off[i]);
+      GramArgs& g = gas[i];
+      for (int sd = 0; sd < 2; ++sd) {
+        g.start[sd] = D->start[sd];
+        g.m[sd] = D->m[sd];
+        g.ncols[sd] = D->ncols[sd];
+        g.cmoff[sd] = D->cmoff[sd];
+        g.gcol[sd] = D->gcol[sd];
+        g.colw[sd] = (const float*)M->colw[sd];
+        g.hoff[sd] = D->gram_off[sd];
+        g.voff[sd] = D->gram_voff[sd];
+      }
+      g.G = (const C2<float>*)M->G;
+      g.ld = M->ld;
+      g.H = (float4*)(gram_base + gram_h_off[i]);
+      g.V = (long long*)(gram_base + gram_v_off[i]);
+      g.status = M->status;
+    }
   }
   char* sp = (char*)scratch;
   PairArgs<T>* d_pa = (PairArgs<T>*)sp;
@@ -808,6 +866,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   NormsArgs<T>* d_na = (NormsArgs<T>*)sp;
   sp += align256(sizeof(NormsArgs<T>) * nprob);
   cudaError_t ce = cudaMemcpyAsync(d_pa, pas.data(), sizeof(PairArgs<T>) * nprob, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && mixed)
+    ce = cudaMemcpyAsync(d_ga, gas.data(), sizeof(GramArgs) * nprob, cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(d_na, nas.data(), sizeof(NormsArgs<T>) * nprob, cudaMemcpyHostToDevice, st);
   if (nprob > 1) {
@@ -920,13 +980,25 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
   };
   // leaf factors and R of one launch list per size class
-  auto leaf_lists = [&](const HList* L) {
-    for (int c = 0; c < kLeafClasses; ++c)
-      if (!L[c].codes->empty()) {
-        ok_launch &= launch_pair_kernel<T>(d_pa, L[c].d_codes, (int)L[c].codes->size(), even_up(std::max(2, cls_maxm[c])), false,
-                              st);
+  // leaf factorisations of one size class: the streamed LQ, or in the mixed
+  // modes the tensor-core Gram matrices and their pivoted Cholesky
+  auto leaf_factor = [&](const uint32_t* codes, int n, int c) {
+    if (n <= 0) return;
+    const int P = even_up(std::max(2, cls_maxm[c]));
+    if constexpr (sizeof(T) == 4) {
+      if (mixed) {
+        ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);
+        counted(DH2_KC_LEAF_GRAM + c, true);
+        ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);
         counted(DH2_KC_LEAF_FACTOR + c, true);
+        return;
       }
+    }
+    ok_launch &= launch_pair_kernel<T>(d_pa, codes, n, P, false, st);
+    counted(DH2_KC_LEAF_FACTOR + c, true);
+  };
+  auto leaf_lists = [&](const HList* L) {
+    for (int c = 0; c < kLeafClasses; ++c) leaf_factor(L[c].d_codes, (int)L[c].codes->size(), c);
   };
   auto leaf_rq = [&](const HList* L) {
     for (int c = 0; c < kLeafClasses; ++c)
@@ -998,13 +1070,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #ifdef DH2_PROFILE
     prof_reset_pair();
 #endif
-    for (int c = 0; c < kLeafClasses; ++c) {
-      const int64_t nc = cls_begin[c + 1] - cls_begin[c];
-      if (nc > 0) {
-        ok_launch &= launch_pair_kernel<T>(d_pa, d_leaf + cls_begin[c], (int)nc, even_up(std::max(2, cls_maxm[c])), false, st);
-        counted(DH2_KC_LEAF_FACTOR + c, true);
-      }
-    }
+    for (int c = 0; c < kLeafClasses; ++c) leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c);
     cudaEventRecord(ev[2], st);
     // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
     for (int c = 0; c < kLeafClasses; ++c) {
@@ -1349,13 +1415,15 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   if (ld < Tc->tr.n || !(cp.eps >= 0.0) || !(cp.zeta > 0.0 && cp.zeta < 1.0) || (cp.err_mode != 0 && cp.err_mode != 1) ||
       (cp.nearfield != 0 && cp.nearfield != 1))
     return DH2_EINVAL;
-  if (!((cp.mode == DH2_MODE_FP64 && dtype == DH2_C128) || (cp.mode == DH2_MODE_FP32 && dtype == DH2_C64)))
+  if (!((cp.mode == DH2_MODE_FP64 && dtype == DH2_C128) || (mode_f32(cp.mode) && cp.mode <= DH2_MODE_MIXED_BF16X3 &&
+                                                              dtype == DH2_C64)))
     return DH2_EINVAL;
+  if (mode_mixed(cp.mode) && gen) return DH2_EUNSUPPORTED;  // the Gram kernel reads a stored G
   if (cp.err_mode == 0 && !(1.0 - 2.0 * cp.zeta * cp.zeta > 0.0)) return DH2_EINVAL;
   dh2_tree* T = const_cast<dh2_tree*>(Tc);
   Tree& tr = T->tr;
-  const int pmax = cp.mode == DH2_MODE_FP32 ? kPmaxF32 : kPmaxF64;
-  if (tr.max_leaf > pmax) return DH2_EUNSUPPORTED;
+  const int pmax = mode_f32(cp.mode) ? kPmaxF32 : kPmaxF64;
+  if (tr.max_leaf > pmax || (mode_mixed(cp.mode) && tr.max_leaf > 64)) return DH2_EUNSUPPORTED;
   int dev = 0;
   DH2_CUDA_TRY(cudaGetDevice(&dev));
   set_pool_threshold(dev);
@@ -1467,7 +1535,7 @@ dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int
   dh2_status s = prepare_matrix(Tc, G, dtype, ld, pts_host, kappa, diag, params, stream, &M, nrm_host);
   if (s != DH2_OK) return s;
   std::vector<dh2_matrix*> Ms{M};
-  s = params->mode == DH2_MODE_FP32 ? run_compress<float>(Ms, *params, (cudaStream_t)stream)
+  s = mode_f32(params->mode) ? run_compress<float>(Ms, *params, (cudaStream_t)stream)
                                     : run_compress<double>(Ms, *params, (cudaStream_t)stream);
   if (s != DH2_OK) {
     matrix_release(M);
@@ -1521,7 +1589,7 @@ dh2_status dh2_compress_host(const dh2_tree* Tc, const void* G_host, dh2_dtype d
   if (s != DH2_OK) return s;
   const HostStage hs{G_host, ld, elem, &T->plan};
   std::vector<dh2_matrix*> Ms{M};
-  s = params->mode == DH2_MODE_FP32 ? run_compress<float>(Ms, *params, (cudaStream_t)stream, &hs)
+  s = mode_f32(params->mode) ? run_compress<float>(Ms, *params, (cudaStream_t)stream, &hs)
                                     : run_compress<double>(Ms, *params, (cudaStream_t)stream, &hs);
   if (s != DH2_OK) {
     matrix_release(M);
@@ -1538,7 +1606,7 @@ dh2_status dh2_compress_kernel(const dh2_tree* Tc, const double* pts_xyz, double
     if (out) *out = nullptr;
     return DH2_EINVAL;
   }
-  const dh2_dtype dt = params->mode == DH2_MODE_FP32 ? DH2_C64 : DH2_C128;
+  const dh2_dtype dt = mode_f32(params->mode) ? DH2_C64 : DH2_C128;
   return compress_impl(Tc, nullptr, dt, 0, pts_xyz, kappa, diag, params, stream, out);
 }
 
@@ -1548,7 +1616,7 @@ dh2_status dh2_compress_kernel_dlp(const dh2_tree* Tc, const double* pts_xyz, co
     if (out) *out = nullptr;
     return DH2_EINVAL;
   }
-  const dh2_dtype dt = params->mode == DH2_MODE_FP32 ? DH2_C64 : DH2_C128;
+  const dh2_dtype dt = mode_f32(params->mode) ? DH2_C64 : DH2_C128;
   return compress_impl(Tc, nullptr, dt, 0, pts_xyz, kappa, 0.5, params, stream, out, normals_xyz);
 }
 
@@ -1569,7 +1637,7 @@ dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, con
     }
     Ms.push_back(M);
   }
-  const dh2_status s = params->mode == DH2_MODE_FP32 ? run_compress<float>(Ms, *params, (cudaStream_t)stream)
+  const dh2_status s = mode_f32(params->mode) ? run_compress<float>(Ms, *params, (cudaStream_t)stream)
                                                      : run_compress<double>(Ms, *params, (cudaStream_t)stream);
   if (s != DH2_OK) {
     for (dh2_matrix* m : Ms) matrix_release(m);
@@ -1694,7 +1762,7 @@ extern "C" {
 
 dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream) {
   if (!M || !x || !y || nrhs < 1) return DH2_EINVAL;
-  return M->mode == DH2_MODE_FP32 ? run_matvec<float>(M, x, y, nrhs, (cudaStream_t)stream)
+  return mode_f32(M->mode) ? run_matvec<float>(M, x, y, nrhs, (cudaStream_t)stream)
                                   : run_matvec<double>(M, x, y, nrhs, (cudaStream_t)stream);
 }
 
@@ -1703,7 +1771,7 @@ dh2_status dh2_error(const dh2_matrix* Mc, const void* G_ref, dh2_dtype ref_dtyp
   if (!Mc || !rel_err) return DH2_EINVAL;
   if (G_ref ? ld < Mc->tree->tr.n : !Mc->gen) return DH2_EINVAL;
   dh2_matrix* M = const_cast<dh2_matrix*>(Mc);
-  return M->mode == DH2_MODE_FP32 ? run_error<float>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err)
+  return mode_f32(M->mode) ? run_error<float>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err)
                                   : run_error<double>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err);
 }
 
@@ -1958,6 +2026,6 @@ dh2_status run_matvec_noalloc(const dh2_matrix* M, const void* xv, void* yv, int
 
 extern "C" dh2_status dh2_matvec_noalloc(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream) {
   if (!M || !x || !y || nrhs < 1) return DH2_EINVAL;
-  return M->mode == DH2_MODE_FP32 ? run_matvec_noalloc<float>(M, x, y, nrhs, (cudaStream_t)stream)
+  return mode_f32(M->mode) ? run_matvec_noalloc<float>(M, x, y, nrhs, (cudaStream_t)stream)
                                   : run_matvec_noalloc<double>(M, x, y, nrhs, (cudaStream_t)stream);
 }

@@ -1,0 +1,407 @@
+// Leaf Gram matrices on the tensor cores (tcgen05, sm_103a) for the mixed
+// modes: for every leaf pair (t, c) of a launch list, H = A A^* with
+// A = G^omega_tc (the leaf step of Section 6: the rows of t, the columns of
+// F_tc, each block's columns scaled by 1/omega_b; for the column basis the same
+// on G^*).  The left singular vectors of A and its singular values are those of
+// H; the factor kernel takes H from here (pivoted Cholesky, then Jacobi on the
+// pivoted factor), so the m x #F_tc matrix is reduced on the tensor cores and
+// only m x m data reaches the CUDA cores.
+//
+// A Gram matrix squares the singular values, so H must be accurate to far more
+// than FP32 (the rank decision resolves sigma^2 ~ eps_l^2 ~ 1e-11 sigma_1^2
+// at eps = 1e-4).  Each row of A is therefore written in fixed point relative
+// to a power of two above its largest entry, as three 8-bit slices
+// (a = 2^(e-6) (s1 + 2^-8 s2 + 2^-16 s3), |s1| <= 64, |s2|, |s3| <= 128, all
+// integers and exact in bf16), and the slice products accumulate in FP32
+// tensor memory where every partial sum is an integer below 2^24, i.e.
+// exactly.  Per complex column a product adds at most 2 * 2^14 (s2 s2), so a
+// window of 448 columns stays exact; longer rows are summed window by window
+// in int64.  The result is H of the sliced matrix A' to ~48 bits, where A'
+// differs from A by at most 2^-23 of each row's largest entry (a backward
+// error of the order of the complex64 input's own rounding).
+//
+// Complex products as real ones: with X = Re A_p, Y = Im A_p (slice p) and
+// likewise X', Y' for slice q, A_p A_q^* = (X X'^T + Y Y'^T) + i (Y X'^T - X Y'^T).
+// A slice is stored as the K-major bf16 operand rows [X; Y; -X] (each block
+// padded to mp = roundup(m, 8) rows), so that one M = 128 MMA on rows [0, 128)
+// against B rows [0, N) (= X') and one on rows [mp, mp + 128) against B rows
+// [mp, mp + N) (= Y') give the real part in TMEM lanes [0, mp) and the
+// imaginary part in lanes [mp, 2 mp) of the same accumulator.  Products of
+// slice pairs (1,1), (1,2), (1,3), (2,2) each have an exact accumulator; the
+// (2,3) and (3,3) products (weight 2^-40 and below) share an FP32 accumulator
+// whose rounding is far below the precision kept.  Since A_q A_p^* =
+// (A_p A_q^*)^*, only p <= q is formed and H is symmetrised at the end.
+#include <algorithm>
+#include <cfloat>
+#include <cstdint>
+
+#include "dh2_internal.h"
+#include "dh2_kernels.cuh"
+#include "dh2_sm100.cuh"
+
+#include <cuda_bf16.h>
+
+namespace dh2 {
+
+namespace {
+
+using namespace sm100;
+
+constexpr int kGramThreads = 128;
+constexpr int kGramChunk = 64;        // complex columns per chunk (one 128-byte K row of bf16)
+constexpr int kGramWindowChunks = 7;  // 448 columns per exact window
+constexpr uint32_t kWaitPolls = 1u << 24;
+
+__device__ __forceinline__ uint32_t bf16_bits(float x) {  // x exactly representable
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// byte offset of the 16-byte chunk g of operand row R in a 128-byte-swizzled buffer
+__device__ __forceinline__ uint32_t swz(int R, int g) { return (uint32_t)R * 128u + ((uint32_t)(g ^ (R & 7)) << 4); }
+
+// double-float value of an int64 (hi correctly rounded, lo the rounded rest:
+// 48 significant bits), times 2^ex
+__device__ __forceinline__ float2 ll_to_df(long long X, int ex) {
+  const float hi = __ll2float_rn(X);
+  const long long rest = X - __float2ll_rn(hi);
+  const float lo = __ll2float_rn(rest);
+  return make_float2(ldexpf(hi, ex), ldexpf(lo, ex));
+}
+
+template <int NP>
+struct GramShape {
+  static constexpr int MPMAX = NP;                  // mp <= NP
+  static constexpr int SLROWS = MPMAX + 128;        // A reads rows [mp, mp + 128)
+  static constexpr int BROWS = 2 * MPMAX + 16;      // B reads rows [mp, mp + NP)
+  static constexpr uint32_t SLBYTES = SLROWS * 128u;
+  static constexpr uint32_t BBYTES = BROWS * 128u;
+  static constexpr int NACC = 5;
+  static constexpr uint32_t TCOLS = NACC * NP <= 256 ? 256u : 512u;
+  static constexpr uint32_t SMEM = 1024 + 3 * SLBYTES + BBYTES;
+};
+
+// Persistent over the launch list: CTA b takes codes b, b + grid, ...
+template <int NP>
+__global__ void __launch_bounds__(kGramThreads, 1)
+    gram_kernel(const GramArgs* __restrict__ args, const uint32_t* __restrict__ codes, int ncodes) {
+  using Sh = GramShape<NP>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sl0 = smem;
+  unsigned char* bsl = smem + 3 * Sh::SLBYTES;  // slice 3 times 2^-9, rows [X; Y] (B operand of (3,3))
+  long long* Vs = reinterpret_cast<long long*>(smem);  // after the last MMA: V, 2 mp x mp, row stride mp
+  __shared__ int cgc[kGramChunk];
+  __shared__ float cwt[kGramChunk];
+  __shared__ unsigned rmax[64];
+  __shared__ float rsc[64];
+  __shared__ int rexp[64];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_bad;
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, Sh::TCOLS);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  {
+    uint4* z = reinterpret_cast<uint4*>(smem);
+    for (uint32_t i = tid; i < (3 * Sh::SLBYTES + Sh::BBYTES) / 16; i += kGramThreads) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  fence_async_smem();
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tbase = tmem_base;
+  const uint32_t sbase = smem_addr(smem);
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
+  uint32_t phase = 0;
+  bool timed_out = false;
+  uint32_t* st_ptr = args[0].status;
+
+  for (int ci = blockIdx.x; ci < ncodes && !timed_out; ci += gridDim.x) {
+    const uint32_t code = codes[ci];
+    const GramArgs& a = args[code >> kCodeProbShift];
+    const int side = (int)((code >> kCodeSideShift) & 1u);
+    const int pid = (int)(code & kCodePairMask);
+    const int m = a.m[side][pid];
+    const int N = a.ncols[side][pid];
+    const int r0 = a.start[side][pid];
+    const int64_t cmo = a.cmoff[side][pid];
+    const int32_t* gcol = a.gcol[side] + cmo;
+    const float* colw = a.colw[side] + cmo;
+    const C2<float>* G = a.G;
+    const int64_t ld = a.ld;
+    const int mp = (m + 7) & ~7;
+    float4* Hout = a.H + a.hoff[side][pid];
+    st_ptr = a.status;
+    const int64_t voff = a.voff[side][pid];
+    long long* Vg = voff >= 0 ? a.V + voff : nullptr;
+    if (m > NP || (N > kGramWindowChunks * kGramChunk && !Vg)) {  // not for this launch: reported, nothing written
+      if (tid == 0) atomicOr(a.status, kStatusTooLarge);
+      continue;
+    }
+    if (N == 0 || m == 0) {
+      for (int i = tid; i < mp * mp; i += kGramThreads) Hout[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const int nitem = m * 8;  // (row, group of 8 columns) items of a chunk
+
+    // loads of one chunk: entries of this thread's items, zero past the chunk
+    auto load_chunk = [&](int j0, int cw, C2<float> (&v)[4][8]) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = tid + kGramThreads * u;
+        const int r = q % m, g = q / m;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int jj = 8 * g + k;
+          v[u][k] = C2<float>{0.f, 0.f};
+          if (q < nitem && jj < cw) {
+            const int gc = cgc[jj];
+            const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
+            v[u][k] = G[e];
+          }
+        }
+      }
+    };
+    auto load_table = [&](int j0, int cw) {
+      __syncthreads();  // everyone is done with the previous table
+      if (tid < kGramChunk) {
+        cgc[tid] = tid < cw ? gcol[j0 + tid] : 0;
+        cwt[tid] = tid < cw ? colw[j0 + tid] : 0.f;
+      }
+      __syncthreads();
+    };
+
+    // ---------------------------------------------------------------- pass 0: row maxima
+    if (tid < 64) rmax[tid] = 0u;
+    if (tid == 0) s_bad = 0;
+    bool bad = false;
+    for (int j0 = 0; j0 < N; j0 += kGramChunk) {
+      const int cw = min(kGramChunk, N - j0);
+      load_table(j0, cw);
+      C2<float> v[4][8];
+      load_chunk(j0, cw, v);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = tid + kGramThreads * u;
+        if (q >= nitem) continue;
+        const int r = q % m, g = q / m;
+        float mx = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float w = cwt[8 * g + k];
+          const float x = fabsf(v[u][k].re * w), y = fabsf(v[u][k].im * w);
+          bad = bad || !(x <= FLT_MAX) || !(y <= FLT_MAX);
+          mx = fmaxf(mx, fmaxf(x, y));
+        }
+        atomicMax(&rmax[r], __float_as_uint(mx));  // non-negative floats order as their bits
+      }
+    }
+    if (bad) s_bad = 1;
+    __syncthreads();
+    if (s_bad) {  // non-finite entries: reported, H of this pair left as zero
+      if (tid == 0) atomicOr(a.status, kStatusNaN);
+      for (int i = tid; i < mp * mp; i += kGramThreads) Hout[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    if (tid < m) {
+      int e = 0;
+      const float mx = __uint_as_float(rmax[tid]);
+      if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
+      rexp[tid] = e;
+      rsc[tid] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
+    }
+    __syncthreads();
+
+    // ---------------------------------------------------------------- pass 1: sliced products
+    bool pending = false;  // an MMA batch was committed and not yet waited for
+    auto wait_mma = [&]() -> bool {
+      const bool ok = mbar_wait(&bar, phase, kWaitPolls);
+      phase ^= 1u;
+      pending = false;
+      return __syncthreads_or(!ok) == 0;
+    };
+    for (int w0 = 0; w0 < N && !timed_out; w0 += kGramWindowChunks * kGramChunk) {
+      const int wend = min(N, w0 + kGramWindowChunks * kGramChunk);
+      for (int j0 = w0; j0 < wend; j0 += kGramChunk) {
+        const int cw = min(kGramChunk, wend - j0);
+        load_table(j0, cw);
+        C2<float> v[4][8];
+        load_chunk(j0, cw, v);
+        if (pending && !wait_mma()) {  // the previous chunk's MMAs still read the slices
+          timed_out = true;
+          break;
+        }
+        // slices of this thread's items -> operand rows X (r), Y (mp + r), -X (2 mp + r)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = tid + kGramThreads * u;
+          if (q >= nitem) continue;
+          const int r = q % m, g = q / m;
+          const float sc = rsc[r];
+          uint32_t px[3][4], py[3][4], pn[3][4], pb[2][4];
+#pragma unroll
+          for (int k = 0; k < 8; k += 2) {
+            uint32_t sx[3][2], sy[3][2], sb[2][2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float w = cwt[8 * g + k + h] * sc;
+              const float xr = v[u][k + h].re * w;
+              const float xi = (side == 0 ? v[u][k + h].im : -v[u][k + h].im) * w;
+              // three 8-bit slices of each part (all steps exact in FP32)
+              const float r1 = rintf(xr), t1 = (xr - r1) * 256.f, r2 = rintf(t1), t2 = (t1 - r2) * 256.f,
+                          r3 = rintf(t2);
+              const float i1 = rintf(xi), u1 = (xi - i1) * 256.f, i2 = rintf(u1), u2 = (u1 - i2) * 256.f,
+                          i3 = rintf(u2);
+              sx[0][h] = bf16_bits(r1);
+              sx[1][h] = bf16_bits(r2);
+              sx[2][h] = bf16_bits(r3);
+              sy[0][h] = bf16_bits(i1);
+              sy[1][h] = bf16_bits(i2);
+              sy[2][h] = bf16_bits(i3);
+              sb[0][h] = bf16_bits(r3 * 0.001953125f);  // 2^-9
+              sb[1][h] = bf16_bits(i3 * 0.001953125f);
+            }
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+              px[s][k >> 1] = sx[s][0] | (sx[s][1] << 16);
+              py[s][k >> 1] = sy[s][0] | (sy[s][1] << 16);
+              pn[s][k >> 1] = px[s][k >> 1] ^ 0x80008000u;  // -X: sign bits flipped
+            }
+            pb[0][k >> 1] = sb[0][0] | (sb[0][1] << 16);
+            pb[1][k >> 1] = sb[1][0] | (sb[1][1] << 16);
+          }
+#pragma unroll
+          for (int s = 0; s < 3; ++s) {
+            unsigned char* buf = sl0 + s * Sh::SLBYTES;
+            *reinterpret_cast<uint4*>(buf + swz(r, g)) = make_uint4(px[s][0], px[s][1], px[s][2], px[s][3]);
+            *reinterpret_cast<uint4*>(buf + swz(mp + r, g)) = make_uint4(py[s][0], py[s][1], py[s][2], py[s][3]);
+            *reinterpret_cast<uint4*>(buf + swz(2 * mp + r, g)) = make_uint4(pn[s][0], pn[s][1], pn[s][2], pn[s][3]);
+          }
+          *reinterpret_cast<uint4*>(bsl + swz(r, g)) = make_uint4(pb[0][0], pb[0][1], pb[0][2], pb[0][3]);
+          *reinterpret_cast<uint4*>(bsl + swz(mp + r, g)) = make_uint4(pb[1][0], pb[1][1], pb[1][2], pb[1][3]);
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after_sync();
+          const bool first = j0 == w0;
+          // products (A slice, B slice or the scaled copy, accumulator)
+          const int pa[6] = {0, 0, 0, 1, 1, 2};
+          const int pb_[6] = {0, 1, 2, 1, 2, 3};  // 3 = slice 3 times 2^-9
+          const int pacc[6] = {0, 1, 2, 3, 4, 4};
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+            for (int x = 0; x < 6; ++x) {
+              const uint32_t abuf = sbase + pa[x] * Sh::SLBYTES + ks * 32;
+              const uint32_t bbuf = (pb_[x] == 3 ? sbase + 3 * Sh::SLBYTES : sbase + pb_[x] * Sh::SLBYTES) + ks * 32;
+              const uint32_t dt = tbase + (uint32_t)(pacc[x] * NP);
+              const bool acc0 = !(first && ks == 0 && x != 5);
+              mma_bf16(dt, desc_kmajor_sw128(abuf), desc_kmajor_sw128(bbuf), idesc, acc0);
+              mma_bf16(dt, desc_kmajor_sw128(abuf + mp * 128), desc_kmajor_sw128(bbuf + mp * 128), idesc, true);
+            }
+          }
+          mma_commit(&bar);
+        }
+        pending = true;
+      }
+      if (timed_out || (pending && !wait_mma())) {
+        timed_out = true;
+        break;
+      }
+      // window done: V = P11 2^31 + P12 2^24 + P13 2^16 + P22 2^15 + low 2^8 per lane (row of [Re; Im])
+      const bool last = wend >= N;
+      tc_fence_after_sync();
+      const int L = tid;  // TMEM lane of this thread
+#pragma unroll 1
+      for (int cb = 0; cb < NP; cb += 16) {
+        float p11[16], p12[16], p13[16], p22[16], plo[16];
+        tmem_ld16(tbase + lane_base + 0 * NP + cb, p11);
+        tmem_ld16(tbase + lane_base + 1 * NP + cb, p12);
+        tmem_ld16(tbase + lane_base + 2 * NP + cb, p13);
+        tmem_ld16(tbase + lane_base + 3 * NP + cb, p22);
+        tmem_ld16(tbase + lane_base + 4 * NP + cb, plo);
+        tmem_ld_wait();
+        if (L < 2 * mp) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int j = cb + i;
+            if (j >= mp) break;
+            long long x = __float2ll_rn(p11[i]) * (1LL << 31) + __float2ll_rn(p12[i]) * (1LL << 24) +
+                          __float2ll_rn(p13[i]) * (1LL << 16) + __float2ll_rn(p22[i]) * (1LL << 15) +
+                          __float2ll_rn(plo[i] * 256.f);
+            const int64_t vi = (int64_t)L * mp + j;
+            if (Vg) {
+              if (w0 > 0) x += Vg[vi];
+              if (!last) Vg[vi] = x;
+            }
+            if (last) Vs[vi] = x;
+          }
+        }
+      }
+      tc_fence_before_sync();
+      __syncthreads();
+    }
+    if (timed_out) break;
+    // ---------------------------------------------------------------- H = V + V^*, scaled, double-float
+    for (int idx = tid; idx < m * m; idx += kGramThreads) {
+      const int i = idx % m, j = idx / m;
+      const long long re = Vs[(int64_t)i * mp + j] + Vs[(int64_t)j * mp + i];
+      const long long im = Vs[(int64_t)(mp + i) * mp + j] - Vs[(int64_t)(mp + j) * mp + i];
+      const int ex = rexp[i] + rexp[j] - 12 - 32;
+      const float2 hr = ll_to_df(re, ex), hi = ll_to_df(im, ex);
+      Hout[i + (int64_t)j * mp] = make_float4(hr.x, hr.y, hi.x, hi.y);
+    }
+    __syncthreads();  // Vs (over the slice buffers) read before the next pair's slices
+  }
+  if (timed_out && tid == 0) atomicOr(st_ptr, kStatusTimeout);
+  // a timed-out batch may still be running: one more bounded wait before the
+  // tensor memory is released
+  if (timed_out) mbar_wait(&bar, phase, kWaitPolls);
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, Sh::TCOLS);
+}
+
+template <int NP>
+bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t st) {
+  using Sh = GramShape<NP>;
+  // shared memory per CTA is padded so that the CTAs an SM can hold never ask
+  // for more tensor memory than its 512 columns (2 CTAs of 256, or 1 of 512)
+  const size_t smem = std::max<size_t>(Sh::SMEM, Sh::TCOLS == 512 ? 120 * 1024 : 80 * 1024);
+  auto kern = gram_kernel<NP>;
+  int dev = 0, maxopt = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || smem > (size_t)maxopt ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGramThreads, smem);
+  per_sm = std::max(1, std::min(per_sm, (int)(512 / Sh::TCOLS)));
+  const int grid = std::min(n, nsm * per_sm);
+  kern<<<grid, kGramThreads, smem, st>>>(args, codes, n);
+  return true;
+}
+
+}  // namespace
+
+bool launch_gram(const GramArgs* args_dev, const uint32_t* codes, int n, int maxm, cudaStream_t st) {
+  if (n <= 0) return true;
+  if (maxm <= 32) return launch_np<32>(args_dev, codes, n, st);
+  if (maxm <= 48) return launch_np<48>(args_dev, codes, n, st);
+  if (maxm <= 64) return launch_np<64>(args_dev, codes, n, st);
+  return false;
+}
+
+}  // namespace dh2

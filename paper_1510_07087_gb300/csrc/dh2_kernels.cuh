@@ -38,6 +38,8 @@ struct PairArgs {
   double* sig[2];                     // per pair P values (descending)
   int32_t* rank[2];
   const double* eps2;                 // per level eps_l^2
+  const float4* H;                    // mixed modes: leaf Gram matrices (see GramArgs)
+  const int64_t* hoff[2];             // mixed modes: per pair, first entry of its Gram matrix in H
   int32_t max_sweeps;
   uint32_t* status;
   // matrix-free mode: entries generated from points (permuted order, 3 doubles
@@ -99,6 +101,12 @@ template <typename T>
 bool launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
                         cudaStream_t st);
 
+// The leaf factorisation of the mixed modes: the pair kernel with steps 1
+// and 1b replaced by the pivoted Cholesky of the leaf's Gram matrix H
+// (launch_gram before it); leaves of at most 64 rows.
+bool launch_pair_kernel_gram(const PairArgs<float>* args_dev, const uint32_t* codes, int nblocks, int P,
+                             cudaStream_t st);
+
 // R = Q^* A for the pairs of a pair-kernel launch, after it, by tiles of 32
 // columns, tiles[i] = launch code << 32 | first column (P as for the pair
 // kernel).  Leaf tiles of a stored G (gen false) go to a persistent kernel
@@ -112,6 +120,30 @@ bool launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int nt
 template <typename T>
 void launch_classify(const PairArgs<T>* args_dev, const uint32_t* codes, int n, uint32_t* out, int* counts,
                      cudaStream_t st);
+
+// Arguments of the leaf Gram kernel of the mixed modes (one per problem).
+// Index [side] selects the row (0) or column (1) basis.
+struct GramArgs {
+  const int32_t* start[2];   // first row index of the pair's cluster
+  const int32_t* m[2];       // leaf rows
+  const int32_t* ncols[2];   // #F_tc
+  const int64_t* cmoff[2];   // leaf column-map offsets
+  const int32_t* gcol[2];    // leaf column map: index of G's other dimension
+  const float* colw[2];      // leaf column map: weight 1/omega of the column's block
+  const int64_t* hoff[2];    // per pair: first entry of its Gram in H (mp x mp, mp = m rounded up to 8)
+  const int64_t* voff[2];    // per pair: first entry of its window sums in V, -1 if one window suffices
+  const C2<float>* G;
+  int64_t ld;
+  float4* H;                 // Gram matrices: (re hi, re lo, im hi, im lo) double-float, column-major, ld mp
+  long long* V;              // window sums of pairs with more than one window
+  uint32_t* status;
+};
+// Columns of one exact accumulation window of the Gram kernel.
+constexpr int kGramWindow = 448;
+
+// H = A A^* for the leaf pairs of a launch list (leaves of at most maxm <= 64
+// rows) on the tensor cores; false if the launch cannot run.
+bool launch_gram(const GramArgs* args_dev, const uint32_t* codes, int n, int maxm, cudaStream_t st);
 
 // Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 17 values.
 void prof_reset_pair();

@@ -299,6 +299,172 @@ __device__ __forceinline__ void stage_cols(const Source<T, FROM_R>& src, int p, 
   }
 }
 
+// ---------------------------------------------------------------- double-float arithmetic
+// A value hi + lo of two floats (|lo| <= ulp(hi)/2, about 48 significant
+// bits), with the error-free sum of Knuth and the error-free product from a
+// fused multiply-add (Dekker's double-length arithmetic in FP32 registers).
+struct Df {
+  float hi, lo;
+};
+__device__ __forceinline__ Df df_fast_sum(float s, float e) {  // |s| >= |e|
+  const float h = s + e;
+  return Df{h, e - (h - s)};
+}
+__device__ __forceinline__ Df df_add(Df x, Df y) {
+  const float s = x.hi + y.hi;
+  const float bb = s - x.hi;
+  const float e = (x.hi - (s - bb)) + (y.hi - bb) + x.lo + y.lo;
+  return df_fast_sum(s, e);
+}
+__device__ __forceinline__ Df df_neg(Df x) { return Df{-x.hi, -x.lo}; }
+__device__ __forceinline__ Df df_mul(Df x, Df y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_fast_sum(p, e);
+}
+// one Newton step from the FP32 square root / reciprocal
+__device__ __forceinline__ Df df_sqrt(Df x) {
+  const float r = sqrtf(x.hi);
+  const float p = r * r;
+  const float e = fmaf(r, r, -p);
+  const float d = ((x.hi - p) - e) + x.lo;  // x - r^2
+  return df_fast_sum(r, d / (2.f * r));
+}
+__device__ __forceinline__ Df df_recip(Df x) {
+  const float q = 1.f / x.hi;
+  const Df xq = df_mul(x, Df{q, 0.f});
+  const Df rest = df_add(Df{1.f, 0.f}, df_neg(xq));  // 1 - x q
+  return df_fast_sum(q, rest.hi * q);
+}
+__device__ __forceinline__ Df df_shfl_xor(Df x, int o) {
+  return Df{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+}
+
+// ---------------------------------------------------------------- 1'. pivoted Cholesky of a Gram matrix
+// H = A A^* of a leaf pair from the tensor-core Gram kernel (double-float,
+// column-major, ld mp = p rounded up to 8) is factored by left-looking
+// Cholesky with diagonal pivoting in double-float arithmetic:
+// H = L L^* + (Schur complement), stopping at the first K whose Schur
+// complement has trace E_K <= tau (= drop eps_l^2).  Since L L^* = A A^*, the
+// K columns of L span the same subspace, and E_K is the same energy, as the
+// K leading columns of the row-pivoted LQ of A (steps 1 and 1b), so the
+// Jacobi, rank and Q steps that follow are shared.  H is first scaled by an
+// even power of two 2^s that brings its largest diagonal entry near 1 (exact;
+// keeps the low halves of the products clear of underflow); L is scaled back
+// by 2^(-s/2) as it is written to Lm in FP32, and E_K by 2^-s.
+// Column j of L (double-float) replaces H's column of the j-th pivot, which is
+// read only when that pivot is chosen.  Rows: LPR threads per row.
+template <typename T, int NT, int LPR>
+__device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, int P, int LDL, int row, int q,
+                              bool live, double tau, C2<T>* Lm, float4* Hs, float* dhi, float* dlo, int* piv,
+                              int* pcol, int& K, double& E_K) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int mp = (p + 7) & ~7;
+  const float4* Hin = a.H + a.hoff[side][pid];
+  for (int idx = tid; idx < p * p; idx += NT) {
+    const int r = idx % p, c = idx / p;
+    Hs[r + c * P] = Hin[r + (int64_t)c * mp];
+  }
+  if (tid < p) pcol[tid] = -1;
+  __syncthreads();
+  float hmax = 0.f;
+  for (int r = lane; r < p; r += 32) hmax = fmaxf(hmax, Hs[r + r * P].x);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+  int eh = 0;
+  if (hmax > 0.f) frexpf(hmax, &eh);
+  const int se = -2 * (eh >> 1);  // even
+  __syncthreads();                // every warp has read the diagonal
+  for (int idx = tid; idx < p * p; idx += NT) {
+    float4& h = Hs[idx % p + (idx / p) * P];
+    h = make_float4(ldexpf(h.x, se), ldexpf(h.y, se), ldexpf(h.z, se), ldexpf(h.w, se));
+  }
+  __syncthreads();
+  if (tid < p) {
+    dhi[tid] = Hs[tid + tid * P].x;
+    dlo[tid] = Hs[tid + tid * P].y;
+  }
+  __syncthreads();
+  const double tau_s = ldexp(tau, se);
+  const float back = ldexpf(1.f, -se / 2);
+  K = p;
+  E_K = 0.0;
+  for (int j = 0; j < p; ++j) {
+    // Schur trace of the unchosen rows and the pivot (largest diagonal, lowest
+    // row on ties); every warp forms the same values
+    double e = 0.0;
+    float best = -1.f;
+    int pv = p;
+    for (int r = lane; r < p; r += 32)
+      if (pcol[r] < 0) {
+        e += (double)dhi[r] + (double)dlo[r];
+        if (dhi[r] > best) {
+          best = dhi[r];
+          pv = r;
+        }
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, pv, o);
+      if (ob > best || (ob == best && oi < pv)) {
+        best = ob;
+        pv = oi;
+      }
+    }
+    if (e <= tau_s || pv >= p || !(best > 0.f)) {
+      K = j;
+      E_K = ldexp(e, -se);
+      break;
+    }
+    const Df sq = df_sqrt(Df{dhi[pv], dlo[pv]});
+    const Df inv = df_recip(sq);
+    // column j: l_r = (H[r][pv] - sum_{i<j} L[r][i] conj(L[pv][i])) / sqrt(d_pv)
+    const bool act = live && row != pv && pcol[row] < 0;
+    Df sre{0.f, 0.f}, sim{0.f, 0.f};
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      for (int i = q; i < j; i += LPR) {
+        const int c = piv[i];
+        const float4 x = Hs[row + c * P], y = Hs[pv + c * P];
+        const Df xr{x.x, x.y}, xi{x.z, x.w}, yr{y.x, y.y}, yi{y.z, y.w};
+        // x conj(y) = (xr yr + xi yi) + i (xi yr - xr yi)
+        sre = df_add(sre, df_add(df_mul(xr, yr), df_mul(xi, yi)));
+        sim = df_add(sim, df_add(df_mul(xi, yr), df_neg(df_mul(xr, yi))));
+      }
+      h = Hs[row + pv * P];
+    }
+#pragma unroll
+    for (int o = 1; o < LPR; o <<= 1) {
+      sre = df_add(sre, df_shfl_xor(sre, o));
+      sim = df_add(sim, df_shfl_xor(sim, o));
+    }
+    const Df lr = df_mul(df_add(Df{h.x, h.y}, df_neg(sre)), inv);
+    const Df li = df_mul(df_add(Df{h.z, h.w}, df_neg(sim)), inv);
+    __syncthreads();  // column pv of H has been read by every row
+    if (live && q == 0) {
+      if (row == pv) {
+        Hs[pv + pv * P] = make_float4(sq.hi, sq.lo, 0.f, 0.f);
+        Lm[j * LDL + pv] = C2<T>{(T)((sq.hi + sq.lo) * back), T(0)};
+        pcol[pv] = j;
+        piv[j] = pv;
+      } else if (pcol[row] < 0) {
+        Hs[row + pv * P] = make_float4(lr.hi, lr.lo, li.hi, li.lo);
+        Lm[j * LDL + row] = C2<T>{(T)((lr.hi + lr.lo) * back), (T)((li.hi + li.lo) * back)};
+        const Df d = df_add(Df{dhi[row], dlo[row]}, df_neg(df_add(df_mul(lr, lr), df_mul(li, li))));
+        dhi[row] = d.hi;
+        dlo[row] = d.lo;
+      } else {
+        Hs[row + pv * P] = make_float4(0.f, 0.f, 0.f, 0.f);  // chosen earlier: L[row][j] = 0
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // P_T: largest factor size of the instantiation (32, 48, 64 or 128 rows).
 // NT: threads per CTA: 4 per row of P_T for the leaf sizes (128, 192, 256),
 // 256 for P_T = 128.  Every thread holds 16 chunk entries, so the chunk is
@@ -330,7 +496,7 @@ constexpr int pair_min_blocks() {
                         : (NT >= 160 ? 1 : 2);
 }
 
-template <typename T, int P_T, bool FROM_R, int NT>
+template <typename T, int P_T, bool FROM_R, int NT, bool GRAM = false>
 __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
   constexpr int LPR = NT / P_T;      // threads per row in the pivoted LQ (rows in place)
@@ -341,7 +507,8 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   constexpr int E = 16 / S;          // chunk entries per thread and row
   constexpr int C = LQT * E;         // chunk width (16 * NT / P_T)
   static_assert(LPR >= 1 && LPR <= 32 && S >= 1 && S * E == 16, "16 chunk entries per thread");
-  constexpr int XTRA = C;            // columns after L: the staged chunk of A
+  constexpr int XTRA = GRAM ? 0 : C;  // columns after L: the staged chunk of A (none from a Gram matrix)
+  static_assert(!GRAM || (!FROM_R && sizeof(T) == 4), "Gram factors: FP32 leaf pairs");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ C2<T> sh_v0[2];
   __shared__ T sh_tau[2];
@@ -364,7 +531,14 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   soff += (size_t)P * sizeof(int);
   int* pcol = reinterpret_cast<int*>(smem + soff);  // pivot step of each row in the pivoted LQ
   soff += (size_t)P * sizeof(int);
-  T* nu = reinterpret_cast<T*>(smem + soff);         // residual row norms
+  T* nu = reinterpret_cast<T*>(smem + soff);         // residual row norms (Gram factors: Schur diagonal, hi)
+  soff += (size_t)P * sizeof(T);
+  soff = (soff + 15) & ~(size_t)15;
+  float4* Hs = reinterpret_cast<float4*>(smem + soff);  // Gram factors: H, then L column by column
+  soff += GRAM ? (size_t)P * P * sizeof(float4) : 0;
+  float* dlo = reinterpret_cast<float*>(smem + soff);  // Gram factors: Schur diagonal, lo
+  soff += GRAM ? (size_t)P * sizeof(float) : 0;
+  int* piv = reinterpret_cast<int*>(smem + soff);      // Gram factors: row chosen at each step
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t code = codes[blockIdx.x];
@@ -425,6 +599,21 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
 
   for (int i = tid; i < P * LDL; i += NT) Lm[i] = czero<T>();  // L; the staging columns need none
   DH2_PROF_T(t_a);
+  const int row = tid / LPR, q = tid % LPR;  // row mapping of the pivoted steps (1b / 1')
+  const bool live = row < p;
+  const double drop = sizeof(T) == 4 ? 1e-2 : 1e-10;
+  int K = p;         // columns kept for the Jacobi step
+  double E_K = 0.0;  // energy left out of them
+#if DH2_PROF_ON
+  long long t_b = 0;
+#endif
+  if constexpr (GRAM) {
+    gram_cholesky<T, NT, LPR>(a, side, pid, p, P, LDL, row, q, live, drop * a.eps2[lvl], Lm, Hs, nu, dlo, piv, pcol,
+                              K, E_K);
+#if DH2_PROF_ON
+    t_b = clock64();
+#endif
+  } else {
 
   // ---------------------------------------------------------------- 1. LQ
   // Rows go to groups of LQT threads in blocks of GPW = 32/LQT consecutive
@@ -437,8 +626,6 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   // its other blocks; one barrier per step.  The reductions over a row run on
   // its group alone (measured faster than running every group converged with
   // the full mask).
-  const int row = tid / LPR, q = tid % LPR;  // row mapping of the pivoted LQ (1b)
-  const bool live = row < p;
   const int lq = lane & (LQT - 1);
   const int lgrp = lane / LQT;
   // row of slot s of this thread: block warp + NW * s, row `lgrp` in it
@@ -676,7 +863,9 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     }
   }
 
-  DH2_PROF_T(t_b);
+#if DH2_PROF_ON
+  t_b = clock64();
+#endif
   DH2_PROF_ADD(0, t_b - t_a);
 #if DH2_PROF_ON
   if (lane == 0) {
@@ -703,7 +892,6 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   // chosen subspace), and the Jacobi step works on the K leading columns only.
   // Two barriers per step: the pivot search is repeated by every warp on the
   // shared residual norms, so it needs none of its own.
-  const double drop = sizeof(T) == 4 ? 1e-2 : 1e-10;
   const T tau_drop_t = (T)(drop * a.eps2[lvl]);
   // (shuffles run converged over whole warps with the full mask; the row
   // predicates only gate the memory accesses)
@@ -719,8 +907,6 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     }
   }
   __syncthreads();
-  int K = p;
-  double E_K = 0.0;
   for (int i = 0; i < p; ++i) {
     // residual energy of the unchosen rows and the pivot (lowest row on ties);
     // the butterfly leaves the same values in every lane of every warp
@@ -818,6 +1004,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     }
     __syncthreads();
   }
+  }  // LQ steps (1, 1b)
   if (!(E_K >= 0.0 && E_K <= 1.0e300)) {  // only from non-finite input
     if (tid == 0) atomicOr(a.status, kStatusNaN);
     E_K = 0.0;
@@ -1362,13 +1549,15 @@ bool set_smem(K kern, size_t smem) {
   return true;
 }
 
-template <typename T, int P_T, bool FROM_R, int NT>
+template <typename T, int P_T, bool FROM_R, int NT, bool GRAM = false>
 bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
   constexpr int C = 16 * (NT / P_T);
+  constexpr int XTRA = GRAM ? 0 : C;
   const int LDL = P + 1;
-  size_t smem = (((size_t)(P + C) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
+  size_t smem = (((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
                 (size_t)P * sizeof(double) + 2 * (size_t)P * sizeof(int) + (size_t)P * sizeof(T);
-  auto kern = pair_kernel<T, P_T, FROM_R, NT>;
+  if (GRAM) smem = ((smem + 15) & ~(size_t)15) + (size_t)P * P * sizeof(float4) + (size_t)P * (sizeof(float) + sizeof(int));
+  auto kern = pair_kernel<T, P_T, FROM_R, NT, GRAM>;
 #ifdef DH2_PROFILE
   // DH2_PROFILE_SOLO=1: one CTA per SM, so the phase counters show latency
   // without the contention of co-resident pairs
@@ -1494,6 +1683,15 @@ bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
   if (P <= 48) return launch_one<T, 48, true, 192>(args, codes, nblocks, P, st);
   if (P <= 64) return launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
   return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st);
+}
+
+bool launch_pair_kernel_gram(const PairArgs<float>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
+  if (nblocks <= 0) return true;
+  if (P <= 32) return launch_one<float, 32, false, 128, true>(args, codes, nblocks, P, st);
+  if (P <= 40) return launch_one<float, 40, false, 160, true>(args, codes, nblocks, P, st);
+  if (P <= 48) return launch_one<float, 48, false, 192, true>(args, codes, nblocks, P, st);
+  if (P <= 64) return launch_one<float, 64, false, 256, true>(args, codes, nblocks, P, st);
+  return false;
 }
 
 template bool launch_pair_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t);
