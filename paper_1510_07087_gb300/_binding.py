@@ -20,6 +20,7 @@ DH2_C64 = 0
 DH2_C128 = 1
 MODE_FP64 = 0
 MODE_FP32 = 1
+MODE_MIXED_BF16X3 = 2
 SIDE_ROW = 0
 SIDE_COL = 1
 # kernel classes of Matrix.class_launches (DH2_KC_* in include/dh2.h)
@@ -32,6 +33,7 @@ KC_COLW = 16
 KC_CLASSIFY = 17
 KC_EXPAND = 18
 KC_PROJECT = 19
+KC_LEAF_GRAM = 20
 KC_COUNT = 32
 
 
@@ -42,7 +44,26 @@ class TreeParams(ctypes.Structure):
 
 class CompressParams(ctypes.Structure):
     _fields_ = [("eps", c_double), ("zeta", c_double), ("err_mode", c_int32), ("mode", c_int32),
-                ("nearfield", c_int32), ("max_sweeps", c_int32)]
+                ("nearfield", c_int32), ("max_sweeps", c_int32), ("rank_override", c_void_p * 2),
+                ("spin_limit", c_int64), ("keep_gram", c_int32), ("reserved", c_int32)]
+
+
+def _params(eps, zeta, err_mode, mode, nearfield, max_sweeps, rank_override=None, spin_limit=0, keep_gram=0):
+    """dh2_compress_params; rank_override: None or (row ranks, column ranks), each None or int32 per pair
+    (kept alive on the returned structure until the call returns)."""
+    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), int(nearfield), int(max_sweeps))
+    p.spin_limit = int(spin_limit)
+    p.keep_gram = int(keep_gram)
+    keep = []
+    if rank_override is not None:
+        for sd in (0, 1):
+            r = rank_override[sd]
+            if r is not None:
+                a = np.ascontiguousarray(r, dtype=np.int32)
+                keep.append(a)
+                p.rank_override[sd] = a.ctypes.data
+    p._keep = keep
+    return p
 
 
 class TreeStats(ctypes.Structure):
@@ -97,6 +118,8 @@ SIGNATURES = [
     ("dh2_matrix_phase_ms", c_int32, [c_void_p, c_void_p]),
     ("dh2_matrix_launch_count", c_int32, [c_void_p, c_void_p]),
     ("dh2_matrix_class_launches", c_int32, [c_void_p, c_void_p]),
+    ("dh2_matrix_block_weights", c_int32, [c_void_p, c_void_p]),
+    ("dh2_matrix_leaf_gram", c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int64, POINTER(c_int32)]),
     ("dh2_debug_fail_alloc", c_int32, [c_int32]),
     ("dh2_status_string", ctypes.c_char_p, [c_int32]),
     ("dh2_version", ctypes.c_char_p, []),
@@ -304,6 +327,21 @@ class Matrix:
         _check(_lib().dh2_matrix_launch_count(self.handle, byref(out)), "dh2_matrix_launch_count")
         return int(out.value)
 
+    def block_weights(self) -> np.ndarray:
+        """1/omega_b per block (Remark "Error control")."""
+        out = np.empty(max(1, int(self.tree.stats().nblocks)))
+        _check(_lib().dh2_matrix_block_weights(self.handle, _ptr(out)), "dh2_matrix_block_weights")
+        return out[:int(self.tree.stats().nblocks)]
+
+    def leaf_gram(self, side: int, pair: int) -> np.ndarray:
+        """The tensor-core Gram matrix of a leaf pair (compressed with keep_gram=1), complex128."""
+        cap = 64 * 64
+        out = np.empty(2 * cap)
+        m = c_int32()
+        _check(_lib().dh2_matrix_leaf_gram(self.handle, side, pair, _ptr(out), cap, byref(m)), "dh2_matrix_leaf_gram")
+        k = m.value
+        return out[:2 * k * k].view(np.complex128).reshape(k, k).T.copy()
+
     def class_launches(self) -> np.ndarray:
         """Launches of the last compression by kernel class (KC_* indices)."""
         out = np.zeros(KC_COUNT, dtype=np.int32)
@@ -317,13 +355,17 @@ class Matrix:
 
 
 def dh2_compress(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,
-                 mode: int | None = None, nearfield: int = 0, max_sweeps: int = 0, stream=None) -> Matrix:
-    """Compress a device matrix G (torch, column-major view, tree's permuted order)."""
+                 mode: int | None = None, nearfield: int = 0, max_sweeps: int = 0, stream=None,
+                 rank_override=None, spin_limit: int = 0, keep_gram: int = 0) -> Matrix:
+    """Compress a device matrix G (torch, column-major view, tree's permuted order).
+
+    rank_override: None or (row ranks, column ranks) per used pair (dh2_tree_pairs order), entries < 0
+    keep the truncation rule; spin_limit, keep_gram: see dh2_compress_params in include/dh2.h."""
     dt = _dtype_code(G)
     if mode is None:
         mode = MODE_FP32 if dt == DH2_C64 else MODE_FP64
     ld = _colmajor_ld(G)
-    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), int(nearfield), int(max_sweeps))
+    p = _params(eps, zeta, err_mode, mode, nearfield, max_sweeps, rank_override, spin_limit, keep_gram)
     h = c_void_p()
     _check(_lib().dh2_compress(tree.handle, c_void_p(G.data_ptr()), dt, ld, byref(p),
                                c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress")
@@ -340,7 +382,7 @@ def dh2_compress_host(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0,
     if mode is None:
         mode = MODE_FP32 if dt == DH2_C64 else MODE_FP64
     ld = _colmajor_ld(G)
-    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), 0, int(max_sweeps))
+    p = _params(eps, zeta, err_mode, mode, 0, max_sweeps)
     h = c_void_p()
     _check(_lib().dh2_compress_host(tree.handle, c_void_p(G.data_ptr()), dt, ld, byref(p),
                                     c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress_host")
@@ -362,7 +404,7 @@ def dh2_compress_batched(trees, Gs, eps: float = 1e-4, zeta: float = 2.0 / 3.0, 
     gp = (c_void_p * n)(*[g.data_ptr() for g in Gs])
     lds = (c_int64 * n)(*[_colmajor_ld(g) for g in Gs])
     outs = (c_void_p * n)()
-    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), int(nearfield), int(max_sweeps))
+    p = _params(eps, zeta, err_mode, mode, nearfield, max_sweeps)
     _check(_lib().dh2_compress_batched(n, th, gp, lds, dt, byref(p), c_void_p(_stream_handle(stream)), outs),
            "dh2_compress_batched")
     return [Matrix(outs[i], trees[i], mode, Gs[i]) for i in range(n)]
@@ -373,7 +415,7 @@ def dh2_compress_kernel(tree: Tree, points: np.ndarray, kappa: float, diag: floa
                         stream=None) -> Matrix:
     """Matrix-free compression of the Helmholtz collocation matrix of `points` (caller order)."""
     pts = np.ascontiguousarray(points, dtype=np.float64)
-    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), 0, int(max_sweeps))
+    p = _params(eps, zeta, err_mode, mode, 0, max_sweeps)
     h = c_void_p()
     _check(_lib().dh2_compress_kernel(tree.handle, _ptr(pts), float(kappa), float(diag), byref(p),
                                       c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress_kernel")
@@ -389,7 +431,7 @@ def dh2_compress_kernel_dlp(tree: Tree, points: np.ndarray, normals: np.ndarray,
     nrm = np.ascontiguousarray(normals, dtype=np.float64)
     if nrm.shape != pts.shape:
         raise ValueError("normals must have the shape of points")
-    p = CompressParams(float(eps), float(zeta), int(err_mode), int(mode), 0, int(max_sweeps))
+    p = _params(eps, zeta, err_mode, mode, 0, max_sweeps)
     h = c_void_p()
     _check(_lib().dh2_compress_kernel_dlp(tree.handle, _ptr(pts), _ptr(nrm), float(kappa), byref(p),
                                           c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress_kernel_dlp")
@@ -402,7 +444,7 @@ def _matvec_operands(M: Matrix, x, y) -> int:
     shape.  Returns nrhs."""
     import torch
 
-    want = torch.complex64 if M.mode == MODE_FP32 else torch.complex128
+    want = torch.complex128 if M.mode == MODE_FP64 else torch.complex64
     dev = torch.cuda.current_device()
     for name, v in (("x", x), ("y", y)):
         if not isinstance(v, torch.Tensor) or v.device.type != "cuda" or v.device.index != dev:

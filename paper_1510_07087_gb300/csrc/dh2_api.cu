@@ -115,6 +115,7 @@ struct dh2_matrix {
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
   int32_t launches = 0;  // kernels launched by the last compression (shared by a batch)
   int32_t class_launches[DH2_KC_COUNT] = {};  // the same launches by kernel class
+  void* gram = nullptr;  // mixed modes with keep_gram: the leaf Gram matrices (double-float complex)
   // matrix-free mode
   int gen = 0;
   double* pts = nullptr;  // device, permuted order
@@ -554,7 +555,10 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   pa.invw = M->invw;
   pa.eps2 = M->eps2;
   pa.H = nullptr;  // set by run_compress in the mixed modes
-  for (int sd = 0; sd < 2; ++sd) pa.hoff[sd] = D->gram_off[sd];
+  for (int sd = 0; sd < 2; ++sd) {
+    pa.hoff[sd] = D->gram_off[sd];
+    pa.rank_ovr[sd] = nullptr;  // set by run_compress when ranks are given
+  }
   pa.max_sweeps = cp.max_sweeps > 0 ? cp.max_sweeps : 30;
   pa.status = M->status;
   pa.pts = M->pts;
@@ -822,18 +826,36 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int i = 0; i < nprob; ++i) {
       const Tree::Dev* D = Ms[i]->tree->tr.dev;
       gram_h_off[i] = gram_bytes;
-      gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);
+      if (!Ms[i]->gram) gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);  // else kept by the matrix
       gram_v_off[i] = gram_bytes;
       gram_bytes += align256(sizeof(long long) * (size_t)D->gram_velems);
     }
   }
+  // ranks given instead of the truncation rule (one problem only)
+  size_t ovr_bytes = 0;
+  if (nprob == 1)
+    for (int sd = 0; sd < 2; ++sd)
+      if (cp.rank_override[sd]) ovr_bytes += align256(4 * (size_t)Ms[0]->tree->tr.dev->npairs[sd]);
   void* scratch = nullptr;
-  if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + gram_bytes + 256, st) !=
-      cudaSuccess) {
+  if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + gram_bytes + ovr_bytes + 256,
+                       st) != cudaSuccess) {
     cudaGetLastError();
     return DH2_ENOMEM;
   }
   char* const gram_base = (char*)scratch + args_bytes + codes_bytes + cls_bytes + host_bytes;
+  char* const ovr_base = gram_base + gram_bytes;
+  cudaError_t ce_ovr = cudaSuccess;
+  if (ovr_bytes) {
+    char* op = ovr_base;
+    for (int sd = 0; sd < 2; ++sd)
+      if (cp.rank_override[sd]) {
+        const int64_t np = Ms[0]->tree->tr.dev->npairs[sd];
+        if (ce_ovr == cudaSuccess)
+          ce_ovr = cudaMemcpyAsync(op, cp.rank_override[sd], 4 * (size_t)np, cudaMemcpyHostToDevice, st);
+        pas[0].rank_ovr[sd] = (const int32_t*)op;
+        op += align256(4 * (size_t)np);
+      }
+  }
   GramArgs* d_ga = (GramArgs*)gram_base;
   std::vector<GramArgs> gas;
   if (mixed) {
@@ -841,7 +863,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int i = 0; i < nprob; ++i) {
       const Tree::Dev* D = Ms[i]->tree->tr.dev;
       const dh2_matrix* M = Ms[i];
-      pas[i].H = (const float4*)(gram_base + gram_h_off[i]);
+      float4* Hbuf = Ms[i]->gram ? (float4*)Ms[i]->gram : (float4*)(gram_base + gram_h_off[i]);
+      pas[i].H = Hbuf;
       GramArgs& g = gas[i];
       for (int sd = 0; sd < 2; ++sd) {
         g.start[sd] = D->start[sd];
@@ -855,9 +878,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       }
       g.G = (const C2<float>*)M->G;
       g.ld = M->ld;
-      g.H = (float4*)(gram_base + gram_h_off[i]);
+      g.H = Hbuf;
       g.V = (long long*)(gram_base + gram_v_off[i]);
       g.status = M->status;
+      g.spin_limit = (uint32_t)std::min<int64_t>(std::max<int64_t>(cp.spin_limit, 0), (int64_t)UINT32_MAX);
     }
   }
   char* sp = (char*)scratch;
@@ -868,6 +892,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   cudaError_t ce = cudaMemcpyAsync(d_pa, pas.data(), sizeof(PairArgs<T>) * nprob, cudaMemcpyHostToDevice, st);
   if (ce == cudaSuccess && mixed)
     ce = cudaMemcpyAsync(d_ga, gas.data(), sizeof(GramArgs) * nprob, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = ce_ovr;
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync(d_na, nas.data(), sizeof(NormsArgs<T>) * nprob, cudaMemcpyHostToDevice, st);
   if (nprob > 1) {
@@ -1201,14 +1226,19 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #endif
   uint32_t all = ok_launch ? 0u : kStatusTooLarge;
   for (uint32_t v : status) all |= v;
+  // a timed-out wait leaves later results undefined: it is reported first
+  if (all & kStatusTimeout) return DH2_ETIMEOUT;
   if (all & kStatusTooLarge) return DH2_EUNSUPPORTED;
   if (all & (kStatusNoConv | kStatusNaN)) return DH2_ENOCONV;
-  if (all & kStatusTimeout) return DH2_ETIMEOUT;
   return DH2_OK;
 }
 
 void matrix_release(dh2_matrix* M) {
   if (!M) return;
+  if (M->gram) {
+    cudaFreeAsync(M->gram, M->stream);
+    cudaGetLastError();
+  }
   if (M->arena) {
     cudaFreeAsync(M->arena, M->stream);
     cudaGetLastError();
@@ -1478,6 +1508,14 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
     return DH2_ENOMEM;
   }
   M->arena_bytes = total;
+  if (mode_mixed(cp.mode) && cp.keep_gram &&
+      dev_malloc_async(&M->gram, std::max<size_t>(256, sizeof(float4) * (size_t)D->gram_elems), M->stream) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    M->gram = nullptr;
+    matrix_release(M);
+    return DH2_ENOMEM;
+  }
   char* p = (char*)M->arena;
   void** dst[20] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
                     (void**)&M->sig[0], (void**)&M->sig[1], (void**)&M->rank[0], (void**)&M->rank[1],
@@ -1626,6 +1664,7 @@ dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, con
   if (!out || nprob < 1) return DH2_EINVAL;
   for (int i = 0; i < nprob; ++i) out[i] = nullptr;
   if (nprob > kMaxBatch || !trees || !G || !ld || !params) return DH2_EINVAL;
+  if (nprob > 1 && (params->rank_override[0] || params->rank_override[1])) return DH2_EINVAL;  // one problem's ranks
   std::vector<dh2_matrix*> Ms;
   for (int i = 0; i < nprob; ++i) {
     dh2_matrix* M = nullptr;
@@ -1912,6 +1951,46 @@ dh2_status dh2_matrix_launch_count(const dh2_matrix* M, int32_t* launches) {
 dh2_status dh2_debug_fail_alloc(int32_t nth) {
   if (nth < 0) return DH2_EINVAL;
   g_fail_alloc.store(nth);
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_block_weights(const dh2_matrix* M, double* invw) {
+  if (!M || !invw) return DH2_EINVAL;
+  const size_t nb = M->tree->tr.blocks.size();
+  DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  if (nb) DH2_CUDA_TRY(cudaMemcpy(invw, M->invw, 8 * nb, cudaMemcpyDeviceToHost));
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_leaf_gram(const dh2_matrix* M, int32_t side, int64_t pair, double* out, int64_t cap_elems,
+                                int32_t* m) {
+  if (!M || !out || !m || (side != 0 && side != 1) || !M->gram) return DH2_EINVAL;
+  const Tree& tr = M->tree->tr;
+  if (pair < 0 || pair >= (int64_t)tr.side[side].pairs.size() || !tr.side[side].pairs[pair].leaf) return DH2_EINVAL;
+  const int mm = tr.size[tr.side[side].pairs[pair].cluster];
+  const int mp = (mm + 7) & ~7;
+  *m = mm;
+  if ((int64_t)mm * mm > cap_elems) return DH2_EINVAL;
+  // the pair's offset: recomputed as at upload (leaf pairs in order, mp^2 each, row side first)
+  int64_t off = 0;
+  for (int sd = 0; sd <= side; ++sd)
+    for (int64_t p = 0; p < (int64_t)tr.side[sd].pairs.size(); ++p) {
+      if (sd == side && p == pair) break;
+      const Pair& P = tr.side[sd].pairs[p];
+      if (P.leaf) {
+        const int64_t q = (tr.size[P.cluster] + 7) & ~7;
+        off += q * q;
+      }
+    }
+  std::vector<float4> h((size_t)mp * mp);
+  DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
+  DH2_CUDA_TRY(cudaMemcpy(h.data(), (const float4*)M->gram + off, sizeof(float4) * h.size(), cudaMemcpyDeviceToHost));
+  for (int j = 0; j < mm; ++j)
+    for (int i = 0; i < mm; ++i) {
+      const float4 v = h[i + (size_t)j * mp];
+      out[2 * (i + (int64_t)j * mm)] = (double)v.x + (double)v.y;
+      out[2 * (i + (int64_t)j * mm) + 1] = (double)v.z + (double)v.w;
+    }
   return DH2_OK;
 }
 

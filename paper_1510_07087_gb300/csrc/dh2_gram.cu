@@ -50,7 +50,7 @@ using namespace sm100;
 constexpr int kGramThreads = 128;
 constexpr int kGramChunk = 64;        // complex columns per chunk (one 128-byte K row of bf16)
 constexpr int kGramWindowChunks = 7;  // 448 columns per exact window
-constexpr uint32_t kWaitPolls = 1u << 24;
+constexpr uint32_t kWaitPolls = 1u << 23;  // default bound of a wait: about a second of polls
 
 __device__ __forceinline__ uint32_t bf16_bits(float x) {  // x exactly representable
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   uint32_t phase = 0;
   bool timed_out = false;
   uint32_t* st_ptr = args[0].status;
+  const uint32_t polls = args[0].spin_limit > 0 ? args[0].spin_limit : kWaitPolls;
 
   for (int ci = blockIdx.x; ci < ncodes && !timed_out; ci += gridDim.x) {
     const uint32_t code = codes[ci];
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     // ---------------------------------------------------------------- pass 1: sliced products
     bool pending = false;  // an MMA batch was committed and not yet waited for
     auto wait_mma = [&]() -> bool {
-      const bool ok = mbar_wait(&bar, phase, kWaitPolls);
+      const bool ok = mbar_wait(&bar, phase, polls);
       phase ^= 1u;
       pending = false;
       return __syncthreads_or(!ok) == 0;

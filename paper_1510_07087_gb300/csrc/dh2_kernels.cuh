@@ -40,6 +40,7 @@ struct PairArgs {
   const double* eps2;                 // per level eps_l^2
   const float4* H;                    // mixed modes: leaf Gram matrices (see GramArgs)
   const int64_t* hoff[2];             // mixed modes: per pair, first entry of its Gram matrix in H
+  const int32_t* rank_ovr[2];         // per pair a rank replacing the truncation rule (< 0: the rule), or NULL
   int32_t max_sweeps;
   uint32_t* status;
   // matrix-free mode: entries generated from points (permuted order, 3 doubles
@@ -137,6 +138,7 @@ struct GramArgs {
   float4* H;                 // Gram matrices: (re hi, re lo, im hi, im lo) double-float, column-major, ld mp
   long long* V;              // window sums of pairs with more than one window
   uint32_t* status;
+  uint32_t spin_limit;       // polls of a wait for a tensor-core batch (0: default)
 };
 // Columns of one exact accumulation window of the Gram kernel.
 constexpr int kGramWindow = 448;

@@ -1171,6 +1171,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
         break;
       }
     }
+    if (a.rank_ovr[side] && a.rank_ovr[side][pid] >= 0) k = min(a.rank_ovr[side][pid], K);
     if (k > kcap) k = kcap;
     sh_k = k;
     *rank_out = k;

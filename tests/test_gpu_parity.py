@@ -167,3 +167,36 @@ def test_status_errors_are_reported():
         D.dh2_compress(T, G, zeta=0.9)          # err_mode 0 needs zeta < 1/sqrt 2
     M = D.dh2_compress(T, G)                     # zero matrix: ranks 0, exact
     assert max(M.ranks(0)) == 0 and max(M.ranks(1)) == 0
+
+
+def test_fp64_rank_override_gives_the_oracles_approximation():
+    """rank_override set to the oracle's own ranks: the GPU keeps exactly those ranks, and its
+    product agrees with the oracle's (no re-run of the oracle) to 1e-11."""
+    D = _dev()
+    n, kappa, leaf, eps = 2048, 8.0, 32, 1e-4
+    pts = fibonacci_sphere(n)
+    tp = O.TreeParams(leaf_size=leaf, kappa=kappa)
+    cp = O.CompressParams(eps=eps)
+    tr = O.build_tree(pts, tp)
+    G = helmholtz_matrix(pts, kappa)[np.ix_(tr.perm, tr.perm)]
+    w = O.block_weights(tr, O.block_norms(tr, G), cp.zeta)
+    V = O.compress(tr, G, cp, "row", w)
+    W = O.compress(tr, G, cp, "col", w)
+    S = O.project(tr, G, V, W)
+    T = D.dh2_tree_build(pts, leaf, kappa)
+    ovr = []
+    for side, B in ((0, V), (1, W)):
+        pr = T.pairs(side)
+        ovr.append(np.array([B.rank[(int(pr["cluster"][p]), int(pr["dir"][p]))] for p in range(len(pr["cluster"]))],
+                            dtype=np.int32))
+    M = D.dh2_compress(T, _colmajor(G, torch.complex128), eps=eps, mode=D.MODE_FP64, rank_override=ovr)
+    for side in (0, 1):
+        assert np.array_equal(M.ranks(side), ovr[side])
+    x = random_complex_vectors(n, 2, seed=21)
+    y_ref = O.matvec(tr, G, V, W, S, x)
+    xd = torch.from_numpy(np.ascontiguousarray(x.T)).to("cuda").t()
+    yd = torch.empty_like(xd.t().contiguous()).t()
+    D.dh2_matvec(M, xd, yd)
+    torch.cuda.synchronize()
+    rel = np.linalg.norm(yd.cpu().numpy() - y_ref) / np.linalg.norm(y_ref)
+    assert rel <= 1e-11, rel
