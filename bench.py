@@ -28,6 +28,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+MODE_LABEL = {"fp32": "FP32 complex64", "fp64": "FP64 complex128",
+              "mixed": "mixed complex64 (tensor-core bf16x3 Gram, double-float pivoted Cholesky)"}
 
 # FP32 ALU peak of the GB300 from its unit counts: 152 SMs x 128 FP32 lanes x
 # 2 flops per FMA x 2.07 GHz maximum SM clock.
@@ -107,7 +109,7 @@ def workload(args):
     kind = ("helmholtz-collocation fibonacci-sphere" if args.kernel == "slp" else
             "helmholtz-double-layer-collocation ellipsoid-2:1:1")
     return {"workload": f"{kind} n={args.n} kappa={args.kappa:g} leaf={args.leaf} "
-                        f"eps={args.eps:g} {'FP32 complex64' if args.mode == 'fp32' else 'FP64 complex128'}",
+                        f"eps={args.eps:g} {MODE_LABEL[args.mode]}",
             "kernel": "1/2 I + double layer (Section 7, DLP)" if args.kernel == "dlp" else "single layer",
             "n": args.n, "kappa": args.kappa, "leaf": args.leaf, "eps": args.eps, "eta1": args.eta1,
             "eta2": args.eta2, "zeta": 2.0 / 3.0, "mode": args.mode,
@@ -234,11 +236,11 @@ def run_gpu(args):
     st = T.stats()
     P = pts[perm]
     Nrm = nrm[perm] if nrm is not None else None
-    cdt = torch.complex64 if args.mode == "fp32" else torch.complex128
-    mode = D.MODE_FP32 if args.mode == "fp32" else D.MODE_FP64
+    cdt = torch.complex128 if args.mode == "fp64" else torch.complex64
+    mode = {"fp32": D.MODE_FP32, "fp64": D.MODE_FP64, "mixed": D.MODE_MIXED_BF16X3}[args.mode]
     Gd = workload_matrix(args, P, Nrm, h, cdt, dev)
     stream = torch.cuda.current_stream()
-    elem = 8 if args.mode == "fp32" else 16
+    elem = 16 if args.mode == "fp64" else 8
     in_bytes = elem * args.n * args.n
 
     def step():
@@ -280,7 +282,7 @@ def run_gpu(args):
     matvec_ms = m0.elapsed_time(m1) / 10
     # error against the FP64 matrix (complex128, built the same way)
     rel_err = None
-    if args.mode == "fp32" and not args.skip_error:
+    if args.mode != "fp64" and not args.skip_error:
         G128 = workload_matrix(args, P, Nrm, h, torch.complex128, dev)
         rel_err = D.dh2_error(M, G128)
         del G128
@@ -387,7 +389,8 @@ def run_gpu(args):
         "metric": "compression wall time & input GB/s at n=32768, kappa=32, eps=1e-4; rel. error vs FP64",
         "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "replicas only",
-        "vs_baseline": None, "dtype": "c64/f32 (f64 tail sums)" if args.mode == "fp32" else "c128/f64",
+        "vs_baseline": None, "dtype": {"fp32": "c64/f32 (f64 tail sums)", "fp64": "c128/f64",
+                                       "mixed": "c64/bf16x3-tc/f32 (f64 tail sums)"}[args.mode],
         "data": "synthetic (Fibonacci sphere, Helmholtz collocation)", "config": workload(args),
         "rel_err_vs_fp64": rel_err, "phases_ms": {k: float(v) for k, v in zip(
             ["norms_nearfield", "leaf_factors", "leaf_R", "level_steps", "expansion", "projection"], phases)},
@@ -412,7 +415,7 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--eta1", type=float, default=2.0 * math.sqrt(2.0))
     ap.add_argument("--eta2", type=float, default=1.0)
-    ap.add_argument("--mode", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--mode", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--nearfield", type=int, default=0)
     ap.add_argument("--kernel", default="slp", choices=["slp", "dlp"],
                     help="slp: single-layer collocation on the Fibonacci sphere (the headline); "
@@ -424,7 +427,7 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    elem = 8 if args.mode == "fp32" else 16
+    elem = 16 if args.mode == "fp64" else 8
     in_bytes = elem * args.n * args.n
     if args.impl == "reference":
         if rank != 0:
