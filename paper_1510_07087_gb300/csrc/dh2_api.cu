@@ -783,7 +783,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   for (int l = 0; l <= maxdepth; ++l) nl_max = std::max(nl_max, (int64_t)nl_codes[l].size());
   for (dh2_matrix* M : Ms)
     for (int l = 0; l <= M->tree->tr.depth; ++l) nl_max = std::max(nl_max, M->tree->tr.dev->nl_code_count[l]);
-  const size_t cls_bytes = align256(4 * 4 * (size_t)std::max<int64_t>(nl_max, 1)) + 256;
+  const size_t cls_bytes = align256(4 * 4 * (size_t)std::max<int64_t>(nl_max, 1)) + align256(16 * (maxdepth + 1));
   // host-input schedule: the plan's launch lists (blocks per panel, the blocks
   // across panels, column-basis leaves per panel and class, row-basis leaves
   // per class) with their R tiles, uploaded behind the other lists
@@ -1127,34 +1127,28 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   DH2_PHASE_SYNC("leaf pairs");
   cudaEventRecord(ev[3], st);
   {
-    // the class split needs the sons' ranks: one 16-byte read-back per level
+    // the class split needs the sons' ranks, known only on the device: each
+    // class is launched at the level's capacity and its CTAs past the class's
+    // count (written by the classify kernel) return at once -- no read-back,
+    // no host synchronisation inside the schedule
     uint32_t* d_cls = (uint32_t*)((char*)scratch + args_bytes + codes_bytes);
-    int* d_cnt = (int*)((char*)d_cls + align256(4 * 4 * (size_t)std::max<int64_t>(nl_max, 1)));
+    int* d_cnt0 = (int*)((char*)d_cls + align256(4 * 4 * (size_t)std::max<int64_t>(nl_max, 1)));
     for (int l = maxdepth; l >= 0; --l) {
       if (n_nl[l] == 0) continue;
       const int n = (int)n_nl[l];
-      int cnt[4] = {0, 0, 0, 0};
-      cudaError_t e = cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), st);
+      int* d_cnt = d_cnt0 + 4 * l;  // per level, so that no launch waits on the host
+      if (cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), st) != cudaSuccess) {
+        cudaGetLastError();
+        ok_launch = false;
+      }
       launch_classify<T>(d_pa, d_nl[l], n, d_cls, d_cnt, st);
       counted(DH2_KC_CLASSIFY, true);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, d_cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        cnt[0] = cnt[1] = cnt[2] = 0;
-        cnt[3] = -1;  // fall back to one launch at the level's capacity
-      }
-      if (cnt[3] < 0) {
-        ok_launch &= launch_pair_kernel<T>(d_pa, d_nl[l], n, P_level[l], true, st);
-        counted(DH2_KC_LEVEL_FACTOR + 3, true);
-      } else {
-        const int Pc[4] = {32, 48, 64, P_level[l]};
-        for (int c = 0; c < 4; ++c)
-          if (cnt[c] > 0) {
-            ok_launch &= launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, cnt[c], std::min(Pc[c], std::max(P_level[l], 2)),
-                                  true, st);
-            counted(DH2_KC_LEVEL_FACTOR + c, true);
-          }
+      const int Pc[4] = {32, 48, 64, P_level[l]};
+      for (int c = 0; c < 4; ++c) {
+        if (c > 0 && Pc[c - 1] >= P_level[l]) break;  // no pair of this level has more rows
+        ok_launch &= launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, n, std::min(Pc[c], std::max(P_level[l], 2)),
+                                           true, st, d_cnt + c);
+        counted(DH2_KC_LEVEL_FACTOR + c, true);
       }
       ok_launch &= launch_rq_kernel<T>(d_pa, d_nltiles[l], (int)n_nltiles[l], P_level[l], true, any_gen, st);
       counted(DH2_KC_LEVEL_R, n_nltiles[l] > 0);

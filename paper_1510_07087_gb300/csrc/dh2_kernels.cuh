@@ -95,12 +95,14 @@ __device__ __forceinline__ C2<T> kernel_entry(const double* pts, const double* n
 }
 
 // One CTA per launch code: args_dev holds one PairArgs per problem (device
-// memory); P is the row capacity of the shared-memory factor (even).  Returns
-// false, launching nothing, if the shared memory the launch needs exceeds the
-// device's per-block limit.
+// memory); P is the row capacity of the shared-memory factor (even).  With
+// `count` (device int) the launch is sized at capacity nblocks and CTAs at or
+// past *count return at once, so a list whose length is known only on the
+// device needs no read-back.  Returns false, launching nothing, if the shared
+// memory the launch needs exceeds the device's per-block limit.
 template <typename T>
 bool launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
-                        cudaStream_t st);
+                        cudaStream_t st, const int* count = nullptr);
 
 // The leaf factorisation of the mixed modes: the pair kernel with steps 1
 // and 1b replaced by the pivoted Cholesky of the leaf's Gram matrix H

@@ -417,7 +417,9 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
     }
     if (e <= tau_s || pv >= p || !(best > 0.f)) {
       K = j;
-      E_K = ldexp(e, -se);
+      // the Schur diagonal is formed by subtraction: a trace below zero is
+      // rounding (|e| at most a few units of 2^-48 of the largest diagonal)
+      E_K = e != e ? e : ldexp(fmax(e, 0.0), -se);
       break;
     }
     const Df sq = df_sqrt(Df{dhi[pv], dlo[pv]});
@@ -498,7 +500,8 @@ constexpr int pair_min_blocks() {
 
 template <typename T, int P_T, bool FROM_R, int NT, bool GRAM = false>
 __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
-    pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
+    pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P,
+                const int* __restrict__ count) {
   constexpr int LPR = NT / P_T;      // threads per row in the pivoted LQ (rows in place)
   constexpr int LQT = DH2_LQT;       // threads per row in the streamed LQ
   constexpr int GPW = 32 / LQT;      // rows per warp and per block of rows
@@ -541,6 +544,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   int* piv = reinterpret_cast<int*>(smem + soff);      // Gram factors: row chosen at each step
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (count && (int)blockIdx.x >= *count) return;  // launched at capacity: slots past the list's length
   const uint32_t code = codes[blockIdx.x];
   const int prob = (int)(code >> kCodeProbShift);
   const int side = (int)((code >> kCodeSideShift) & 1u);
@@ -1551,7 +1555,8 @@ bool set_smem(K kern, size_t smem) {
 }
 
 template <typename T, int P_T, bool FROM_R, int NT, bool GRAM = false>
-bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
+bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st,
+                const int* count = nullptr) {
   constexpr int C = 16 * (NT / P_T);
   constexpr int XTRA = GRAM ? 0 : C;
   const int LDL = P + 1;
@@ -1566,7 +1571,7 @@ bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int
     if (solo[0] == '1' && smem < 120 * 1024) smem = 120 * 1024;
 #endif
   if (!set_smem(kern, smem)) return false;
-  kern<<<nblocks, NT, smem, st>>>(args, codes, P);
+  kern<<<nblocks, NT, smem, st>>>(args, codes, P, count);
   return true;
 }
 
@@ -1671,19 +1676,19 @@ template bool launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*,
 
 template <typename T>
 bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* count) {
   if (nblocks <= 0) return true;
   if (!from_r) {
-    if (P <= 32) return launch_one<T, 32, false, 128>(args, codes, nblocks, P, st);
-    if (P <= 40) return launch_one<T, 40, false, 160>(args, codes, nblocks, P, st);
-    if (P <= 48) return launch_one<T, 48, false, 192>(args, codes, nblocks, P, st);
-    if (P <= 64) return launch_one<T, 64, false, 256>(args, codes, nblocks, P, st);
-    return launch_one<T, 128, false, 256>(args, codes, nblocks, P, st);
+    if (P <= 32) return launch_one<T, 32, false, 128>(args, codes, nblocks, P, st, count);
+    if (P <= 40) return launch_one<T, 40, false, 160>(args, codes, nblocks, P, st, count);
+    if (P <= 48) return launch_one<T, 48, false, 192>(args, codes, nblocks, P, st, count);
+    if (P <= 64) return launch_one<T, 64, false, 256>(args, codes, nblocks, P, st, count);
+    return launch_one<T, 128, false, 256>(args, codes, nblocks, P, st, count);
   }
-  if (P <= 32) return launch_one<T, 32, true, 128>(args, codes, nblocks, P, st);
-  if (P <= 48) return launch_one<T, 48, true, 192>(args, codes, nblocks, P, st);
-  if (P <= 64) return launch_one<T, 64, true, 256>(args, codes, nblocks, P, st);
-  return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st);
+  if (P <= 32) return launch_one<T, 32, true, 128>(args, codes, nblocks, P, st, count);
+  if (P <= 48) return launch_one<T, 48, true, 192>(args, codes, nblocks, P, st, count);
+  if (P <= 64) return launch_one<T, 64, true, 256>(args, codes, nblocks, P, st, count);
+  return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st, count);
 }
 
 bool launch_pair_kernel_gram(const PairArgs<float>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
@@ -1695,7 +1700,9 @@ bool launch_pair_kernel_gram(const PairArgs<float>* args, const uint32_t* codes,
   return false;
 }
 
-template bool launch_pair_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t);
-template bool launch_pair_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t);
+template bool launch_pair_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t,
+                                        const int*);
+template bool launch_pair_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t,
+                                         const int*);
 
 }  // namespace dh2
