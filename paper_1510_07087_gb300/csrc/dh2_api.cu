@@ -47,12 +47,13 @@ struct Tree::Dev {
   int64_t *gram_off[2], *gram_voff[2];  // mixed modes: leaf Gram matrix offsets, window sums (-1: none)
   int32_t *gcol[2], *gblk[2];
   int64_t* seg_dst[2];  // column-map segments (expanded into gcol/gblk on upload)
+  int64_t* seg_begin[2];  // per pair: first segment
   int32_t *seg_col0[2], *seg_w[2], *seg_blk[2];
   int32_t* iota[2];        // 0..npairs-1
   int32_t* leaf_list[2];   // leaf pair ids
   // blocks
   int32_t *bt, *bs, *badm, *bpair[2], *boff_row;
-  int64_t *near_off, *Soff;
+  int64_t *near_off, *Soff, *bmax_off;
   int32_t *adm_list, *inadm_list;
   // matvec lists (row side)
   int64_t *own_ptr, *par_ptr;
@@ -65,7 +66,7 @@ struct Tree::Dev {
   int64_t npairs[2] = {0, 0}, nleaf[2] = {0, 0};
   int64_t R_elems[2] = {0, 0}, Q_elems[2] = {0, 0}, X_elems[2] = {0, 0}, h_elems[2] = {0, 0};
   int64_t gram_elems = 0, gram_velems = 0;  // both sides together
-  int64_t S_elems = 0, near_elems = 0;
+  int64_t S_elems = 0, near_elems = 0, bmax_elems = 0;
   int64_t nadm = 0, ninadm = 0;
   int64_t nleaf_codes = 0;
   // leaf codes grouped by size class (rows <= 32, <= 40, <= 48, <= 64, more), each
@@ -294,12 +295,13 @@ dh2_status upload_tree(Tree& tr) {
     add32(std::vector<int32_t>(S.seg_col0), &D->seg_col0[sd]);
     add32(std::vector<int32_t>(S.seg_w), &D->seg_w[sd]);
     add32(std::vector<int32_t>(S.seg_blk), &D->seg_blk[sd]);
+    add64(std::vector<int64_t>(S.seg_begin), &D->seg_begin[sd]);
   }
   // blocks
   const int64_t nb = (int64_t)tr.blocks.size();
   std::vector<int32_t> bt(nb), bs(nb), ba(nb), bpr(nb), bpc(nb), bo(nb), adm, inadm;
-  std::vector<int64_t> noff(nb, 0), soffs(nb, 0);
-  int64_t S_e = 0, N_e = 0;
+  std::vector<int64_t> noff(nb, 0), soffs(nb, 0), mxoff(nb, -1);
+  int64_t S_e = 0, N_e = 0, MX_e = 0;
   for (int64_t b = 0; b < nb; ++b) {
     const Block& B = tr.blocks[b];
     bt[b] = B.t;
@@ -312,6 +314,8 @@ dh2_status upload_tree(Tree& tr) {
       adm.push_back((int32_t)b);
       soffs[b] = S_e;
       S_e += (int64_t)D->kcap_h[0][bpr[b]] * D->kcap_h[1][bpc[b]];
+      mxoff[b] = MX_e;  // mixed modes: largest |re|, |im| of each row, then of each column
+      MX_e += (int64_t)tr.size[B.t] + tr.size[B.s];
     } else {
       inadm.push_back((int32_t)b);
       noff[b] = N_e;
@@ -320,6 +324,7 @@ dh2_status upload_tree(Tree& tr) {
   }
   D->S_elems = S_e;
   D->near_elems = N_e;
+  D->bmax_elems = MX_e;
   D->nadm = (int64_t)adm.size();
   D->ninadm = (int64_t)inadm.size();
   D->Soff_h = soffs;
@@ -331,6 +336,7 @@ dh2_status upload_tree(Tree& tr) {
   add32(std::move(bo), &D->boff_row);
   add64(std::move(noff), &D->near_off);
   add64(std::move(soffs), &D->Soff);
+  add64(std::move(mxoff), &D->bmax_off);
   add32(std::move(adm), &D->adm_list);
   add32(std::move(inadm), &D->inadm_list);
   // row-side matvec lists: own blocks and father pairs per pair
@@ -530,6 +536,8 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   na.kappa = M->kappa;
   na.diag = M->diag;
   na.gen = M->gen;
+  na.bmax = nullptr;  // set by run_compress in the mixed modes
+  na.bmax_off = D->bmax_off;
   for (int sd = 0; sd < 2; ++sd) {
     pa.start[sd] = D->start[sd];
     pa.m[sd] = D->m[sd];
@@ -819,7 +827,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // mixed modes: the leaf Gram matrices (double-float, mp x mp per leaf pair)
   // and the window sums of the pairs with more than one window, per problem
   const bool mixed = mode_mixed(cp.mode);
-  std::vector<size_t> gram_h_off(nprob, 0), gram_v_off(nprob, 0);
+  std::vector<size_t> gram_h_off(nprob, 0), gram_v_off(nprob, 0), gram_m_off(nprob, 0);
   size_t gram_bytes = 0;
   if (mixed) {
     gram_bytes = align256(sizeof(GramArgs) * nprob);
@@ -829,6 +837,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       if (!Ms[i]->gram) gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);  // else kept by the matrix
       gram_v_off[i] = gram_bytes;
       gram_bytes += align256(sizeof(long long) * (size_t)D->gram_velems);
+      gram_m_off[i] = gram_bytes;
+      gram_bytes += align256(sizeof(float) * (size_t)D->bmax_elems);
     }
   }
   // ranks given instead of the truncation rule (one problem only)
@@ -875,7 +885,17 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         g.colw[sd] = (const float*)M->colw[sd];
         g.hoff[sd] = D->gram_off[sd];
         g.voff[sd] = D->gram_voff[sd];
+        g.seg_begin[sd] = D->seg_begin[sd];
+        g.seg_blk[sd] = D->seg_blk[sd];
       }
+      g.bt = D->bt;
+      g.bs = D->bs;
+      g.cstart = D->cstart;
+      g.csize = D->csize;
+      g.invw = M->invw;
+      g.bmax = (const float*)(gram_base + gram_m_off[i]);
+      g.bmax_off = D->bmax_off;
+      nas[i].bmax = (float*)(gram_base + gram_m_off[i]);
       g.G = (const C2<float>*)M->G;
       g.ld = M->ld;
       g.H = Hbuf;

@@ -49,7 +49,8 @@ using namespace sm100;
 
 constexpr int kGramThreads = 128;
 constexpr int kGramChunk = 64;        // complex columns per chunk (one 128-byte K row of bf16)
-constexpr int kGramWindowChunks = 7;  // 448 columns per exact window
+constexpr int kTableCols = 1024;      // columns of the pair's column table held in shared memory at once
+static_assert(kGramWindow % kGramChunk == 0 && kTableCols % kGramChunk == 0, "chunk-aligned windows and tables");
 constexpr uint32_t kWaitPolls = 1u << 23;  // default bound of a wait: about a second of polls
 
 __device__ __forceinline__ uint32_t bf16_bits(float x) {  // x exactly representable
@@ -59,13 +60,24 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {  // x exactly represent
 // byte offset of the 16-byte chunk g of operand row R in a 128-byte-swizzled buffer
 __device__ __forceinline__ uint32_t swz(int R, int g) { return (uint32_t)R * 128u + ((uint32_t)(g ^ (R & 7)) << 4); }
 
-// double-float value of an int64 (hi correctly rounded, lo the rounded rest:
-// 48 significant bits), times 2^ex
+// 2^ex as a float (exponent field for the normal range)
+__device__ __forceinline__ float pow2f(int ex) {
+  return (ex >= -126 && ex <= 127) ? __int_as_float((ex + 127) << 23) : ldexpf(1.f, ex);
+}
+
+// double-float value hi + lo of an integer |X| < 2^59, times 2^ex, from
+// 32-bit conversions only: hi holds the top 24 bits of X >> 31, lo the rest
+// (to within 2^11, far below 2^-40 of the largest entries of a Gram matrix)
 __device__ __forceinline__ float2 ll_to_df(long long X, int ex) {
-  const float hi = __ll2float_rn(X);
-  const long long rest = X - __float2ll_rn(hi);
-  const float lo = __ll2float_rn(rest);
-  return make_float2(ldexpf(hi, ex), ldexpf(lo, ex));
+  const int xh = (int)(X >> 31);                               // |xh| < 2^28
+  const float fh = __int2float_rn(xh);
+  const long long rest = X - (long long)__float2int_rn(fh) * (1LL << 31);  // |rest| < 2^35
+  const float fl = __int2float_rn((int)(rest >> 4)) * 16.f;
+  const float h0 = fh * 2147483648.f;
+  const float hs = h0 + fl;                                     // |h0| >= |fl| unless h0 == 0
+  const float ls = fl - (hs - h0);
+  const float sc = pow2f(ex);
+  return make_float2(hs * sc, ls * sc);
 }
 
 template <int NP>
@@ -90,14 +102,12 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   unsigned char* sl0 = smem;
   unsigned char* bsl = smem + 3 * Sh::SLBYTES;  // slice 3 times 2^-9, rows [X; Y] (B operand of (3,3))
   long long* Vs = reinterpret_cast<long long*>(smem);  // after the last MMA: V, 2 mp x mp, row stride mp
-  __shared__ int cgc[kGramChunk];
-  __shared__ float cwt[kGramChunk];
-  __shared__ unsigned rmax[64];
+  __shared__ int cgcT[kTableCols];  // column table of the pair: G index of each column
+  __shared__ float cwtT[kTableCols]; // and its weight 1/omega_b
   __shared__ float rsc[64];
   __shared__ int rexp[64];
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_bad;
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     st_ptr = a.status;
     const int64_t voff = a.voff[side][pid];
     long long* Vg = voff >= 0 ? a.V + voff : nullptr;
-    if (m > NP || (N > kGramWindowChunks * kGramChunk && !Vg)) {  // not for this launch: reported, nothing written
+    if (m > NP || (N > kGramWindow && !Vg)) {  // not for this launch: reported, nothing written
       if (tid == 0) atomicOr(a.status, kStatusTooLarge);
       continue;
     }
@@ -153,8 +163,53 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     }
     const int nitem = m * 8;  // (row, group of 8 columns) items of a chunk
 
-    // loads of one chunk: entries of this thread's items, zero past the chunk
-    auto load_chunk = [&](int j0, int cw, C2<float> (&v)[4][8]) {
+    // ---------------------------------------------------------------- row scales
+    // the largest |re|, |im| of each row of A = G^omega_tc from the block
+    // norms pass: per block of F_tc its row (column basis: column) maxima
+    // times the block's FP32 weight -- the same value as the maximum over the
+    // weighted entries, since rounding a product with a positive factor is
+    // monotonic.  Two threads per row, each over half of the blocks.
+    {
+      const int64_t sg0 = a.seg_begin[side][pid], sg1 = a.seg_begin[side][pid + 1];
+      const int i = tid >> 1;
+      float mx = 0.f;
+      bool bad = false;
+      if (i < m)
+        for (int64_t sg = sg0 + (tid & 1); sg < sg1; sg += 2) {
+          const int b = a.seg_blk[side][sg];
+          const float w = (float)a.invw[b];
+          // the block's maxima: rows of t+ first (row basis), then columns of s+ (column basis)
+          const int cl = side == 0 ? a.bt[b] : a.bs[b];  // the block's cluster on this side
+          const int64_t off = a.bmax_off[b] + (side == 0 ? 0 : a.csize[a.bt[b]]) + (r0 - a.cstart[cl]) + i;
+          const float v = a.bmax[off] * w;
+          bad = bad || !(v <= FLT_MAX);
+          mx = fmaxf(mx, v);
+        }
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      bad = __syncthreads_or(bad);
+      if (bad) {  // non-finite entries: reported, H of this pair left as zero
+        if (tid == 0) atomicOr(a.status, kStatusNaN);
+        for (int k = tid; k < mp * mp; k += kGramThreads) Hout[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      if (i < m && (tid & 1) == 0) {
+        int e = 0;
+        if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
+        rexp[i] = e;
+        rsc[i] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
+      }
+    }
+    // column table of the pair (segments of kTableCols columns)
+    auto load_table = [&](int tb) {
+      __syncthreads();  // no thread still reads the previous segment
+      for (int jj = tid; jj < kTableCols && tb + jj < N; jj += kGramThreads) {
+        cgcT[jj] = gcol[tb + jj];
+        cwtT[jj] = colw[tb + jj];
+      }
+      __syncthreads();
+    };
+    // entries of this thread's items of the chunk at j0 (zero past the chunk)
+    auto load_chunk = [&](int j0, int cw, int tb, C2<float> (&v)[4][8]) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = tid + kGramThreads * u;
@@ -164,64 +219,15 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           const int jj = 8 * g + k;
           v[u][k] = C2<float>{0.f, 0.f};
           if (q < nitem && jj < cw) {
-            const int gc = cgc[jj];
+            const int gc = cgcT[j0 - tb + jj];
             const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
             v[u][k] = G[e];
           }
         }
       }
     };
-    auto load_table = [&](int j0, int cw) {
-      __syncthreads();  // everyone is done with the previous table
-      if (tid < kGramChunk) {
-        cgc[tid] = tid < cw ? gcol[j0 + tid] : 0;
-        cwt[tid] = tid < cw ? colw[j0 + tid] : 0.f;
-      }
-      __syncthreads();
-    };
 
-    // ---------------------------------------------------------------- pass 0: row maxima
-    if (tid < 64) rmax[tid] = 0u;
-    if (tid == 0) s_bad = 0;
-    bool bad = false;
-    for (int j0 = 0; j0 < N; j0 += kGramChunk) {
-      const int cw = min(kGramChunk, N - j0);
-      load_table(j0, cw);
-      C2<float> v[4][8];
-      load_chunk(j0, cw, v);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q = tid + kGramThreads * u;
-        if (q >= nitem) continue;
-        const int r = q % m, g = q / m;
-        float mx = 0.f;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float w = cwt[8 * g + k];
-          const float x = fabsf(v[u][k].re * w), y = fabsf(v[u][k].im * w);
-          bad = bad || !(x <= FLT_MAX) || !(y <= FLT_MAX);
-          mx = fmaxf(mx, fmaxf(x, y));
-        }
-        atomicMax(&rmax[r], __float_as_uint(mx));  // non-negative floats order as their bits
-      }
-    }
-    if (bad) s_bad = 1;
-    __syncthreads();
-    if (s_bad) {  // non-finite entries: reported, H of this pair left as zero
-      if (tid == 0) atomicOr(a.status, kStatusNaN);
-      for (int i = tid; i < mp * mp; i += kGramThreads) Hout[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    if (tid < m) {
-      int e = 0;
-      const float mx = __uint_as_float(rmax[tid]);
-      if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
-      rexp[tid] = e;
-      rsc[tid] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
-    }
-    __syncthreads();
-
-    // ---------------------------------------------------------------- pass 1: sliced products
+    // ---------------------------------------------------------------- sliced products
     bool pending = false;  // an MMA batch was committed and not yet waited for
     auto wait_mma = [&]() -> bool {
       const bool ok = mbar_wait(&bar, phase, polls);
@@ -229,13 +235,14 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       pending = false;
       return __syncthreads_or(!ok) == 0;
     };
-    for (int w0 = 0; w0 < N && !timed_out; w0 += kGramWindowChunks * kGramChunk) {
-      const int wend = min(N, w0 + kGramWindowChunks * kGramChunk);
+    int tb = 0;
+    load_table(0);
+    C2<float> v[4][8];
+    load_chunk(0, min(kGramChunk, N), 0, v);
+    for (int w0 = 0; w0 < N && !timed_out; w0 += kGramWindow) {
+      const int wend = min(N, w0 + kGramWindow);
       for (int j0 = w0; j0 < wend; j0 += kGramChunk) {
         const int cw = min(kGramChunk, wend - j0);
-        load_table(j0, cw);
-        C2<float> v[4][8];
-        load_chunk(j0, cw, v);
         if (pending && !wait_mma()) {  // the previous chunk's MMAs still read the slices
           timed_out = true;
           break;
@@ -253,7 +260,8 @@ __global__ void __launch_bounds__(kGramThreads, 1)
             uint32_t sx[3][2], sy[3][2], sb[2][2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              const float w = cwt[8 * g + k + h] * sc;
+              const int jj = 8 * g + k + h;
+              const float w = (jj < cw ? cwtT[j0 - tb + jj] : 0.f) * sc;
               const float xr = v[u][k + h].re * w;
               const float xi = (side == 0 ? v[u][k + h].im : -v[u][k + h].im) * w;
               // three 8-bit slices of each part (all steps exact in FP32)
@@ -313,12 +321,22 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           mma_commit(&bar);
         }
         pending = true;
+        // the next chunk's loads go out while the tensor cores work on this one
+        const int jn = j0 + kGramChunk;
+        if (jn < N) {
+          if (jn >= tb + kTableCols) {
+            tb = jn;
+            load_table(tb);
+          }
+          load_chunk(jn, min(kGramChunk, min(N, jn < wend ? wend : jn + kGramWindow) - jn), tb, v);
+        }
       }
       if (timed_out || (pending && !wait_mma())) {
         timed_out = true;
         break;
       }
-      // window done: V = P11 2^31 + P12 2^24 + P13 2^16 + P22 2^15 + low 2^8 per lane (row of [Re; Im])
+      // window done: V = P11 2^31 + P12 2^24 + P13 2^16 + P22 2^15 + low 2^8 per lane (row of [Re; Im]);
+      // every P is an integer below 2^24 held exactly in FP32
       const bool last = wend >= N;
       tc_fence_after_sync();
       const int L = tid;  // TMEM lane of this thread
@@ -336,9 +354,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           for (int i = 0; i < 16; ++i) {
             const int j = cb + i;
             if (j >= mp) break;
-            long long x = __float2ll_rn(p11[i]) * (1LL << 31) + __float2ll_rn(p12[i]) * (1LL << 24) +
-                          __float2ll_rn(p13[i]) * (1LL << 16) + __float2ll_rn(p22[i]) * (1LL << 15) +
-                          __float2ll_rn(plo[i] * 256.f);
+            long long x = (long long)__float2int_rn(p11[i]) * (1LL << 31) +
+                          (long long)__float2int_rn(p12[i]) * (1LL << 24) +
+                          (long long)__float2int_rn(p13[i]) * (1LL << 16) +
+                          (long long)__float2int_rn(p22[i]) * (1LL << 15) + (long long)__float2int_rn(plo[i] * 256.f);
             const int64_t vi = (int64_t)L * mp + j;
             if (Vg) {
               if (w0 > 0) x += Vg[vi];

@@ -70,6 +70,7 @@ struct Side {
   std::vector<int32_t> seg_col0;                // first column of G (the other cluster's start)
   std::vector<int32_t> seg_w;                   // number of columns
   std::vector<int32_t> seg_blk;                 // block id
+  std::vector<int64_t> seg_begin;               // per pair: its first segment (npairs+1; leaf pairs only non-empty)
   int64_t ncols_total = 0, nleafcols = 0;
 };
 

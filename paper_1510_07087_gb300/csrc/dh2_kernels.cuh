@@ -135,6 +135,15 @@ struct GramArgs {
   const float* colw[2];      // leaf column map: weight 1/omega of the column's block
   const int64_t* hoff[2];    // per pair: first entry of its Gram in H (mp x mp, mp = m rounded up to 8)
   const int64_t* voff[2];    // per pair: first entry of its window sums in V, -1 if one window suffices
+  const int64_t* seg_begin[2];  // per pair: its blocks of F_tc as a range of column-map segments
+  const int32_t* seg_blk[2];    // per segment: block id
+  const int32_t* bt;         // per block: row cluster
+  const int32_t* bs;         // per block: column cluster
+  const int32_t* cstart;     // per cluster: first index
+  const int32_t* csize;      // per cluster: size
+  const double* invw;        // per block: 1/omega_b
+  const float* bmax;         // per admissible block: largest |re|, |im| per row, then per column
+  const int64_t* bmax_off;
   const C2<float>* G;
   int64_t ld;
   float4* H;                 // Gram matrices: (re hi, re lo, im hi, im lo) double-float, column-major, ld mp

@@ -95,7 +95,43 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
   // dense input: the block is walked as a flat column-major index space,
   // 8 independent loads in flight per lane
   const int total = mt * ms;
-  if (a.badm[b]) {
+  if (a.badm[b] && a.bmax) {
+    // mixed modes: besides the norm, the largest |re|, |im| of every row and
+    // every column of the block (the row scales of the leaf Gram slices).
+    // Lanes take 32 consecutive rows, 8 columns in flight; a column's maximum
+    // is a warp reduction, merged over the row slabs by lane 0.
+    float* rmx = a.bmax + a.bmax_off[b];
+    float* cmx = rmx + mt;
+    T acc = T(0);
+    for (int rs = 0; rs < mt; rs += 32) {
+      const int r = rs + lane;
+      float rm = 0.f;
+      for (int j0 = 0; j0 < ms; j0 += 8) {
+        C2<T> g[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          g[u] = czero<T>();
+          if (r < mt && j0 + u < ms) {
+            const int64_t gi = (s0 + j0 + u) * a.ld + t0 + r;
+            if (DH2_IN(gi, c_lim.G, 20, b)) g[u] = a.G[gi];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          acc += g[u].re * g[u].re + g[u].im * g[u].im;
+          float v = fmaxf(fabsf((float)g[u].re), fabsf((float)g[u].im));
+          rm = fmaxf(rm, v);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+          if (lane == 0 && j0 + u < ms) cmx[j0 + u] = rs == 0 ? v : fmaxf(cmx[j0 + u], v);
+        }
+      }
+      if (r < mt) rmx[r] = rm;
+    }
+    const double tot = warp_sum((double)acc);
+    if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
+      a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+  } else if (a.badm[b]) {
     T acc[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] = T(0);

@@ -45,6 +45,10 @@ struct NormsArgs {
   double kappa;
   double diag;
   int gen;
+  // mixed modes: per admissible block the largest |re|, |im| of each of its
+  // rows, then of each of its columns (bmax + bmax_off[b]); NULL otherwise
+  float* bmax;
+  const int64_t* bmax_off;
 };
 
 template <typename T>

@@ -335,11 +335,14 @@ void build_side(Tree& tr, int side) {
     }
     for (auto& seg : P.parents) emit(seg.first);
   };
+  S.seg_begin.assign(S.pairs.size() + 1, 0);
   for (int64_t p = 0; p < (int64_t)S.pairs.size(); ++p) {
     S.leaf_colmap_off[p] = pos;
+    S.seg_begin[p] = (int64_t)S.seg_dst.size();
     if (S.pairs[p].leaf) emit(p);
   }
   S.leaf_colmap_off[S.pairs.size()] = pos;
+  S.seg_begin[S.pairs.size()] = (int64_t)S.seg_dst.size();
   S.nleafcols = pos;
 }
 
