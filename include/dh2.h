@@ -279,11 +279,32 @@ dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs,
  * x, y: as for dh2_matvec; y is overwritten. */
 dh2_status dh2_matvec_noalloc(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream);
 
-/* Relative Frobenius error |G_ref - G~|_F / |G_ref|_F, block by block, with
- * G_ref a device matrix of dtype ref_dtype (n x n column-major, permuted
- * order, leading dimension ld), or NULL for a matrix from dh2_compress_kernel
- * (reference entries generated in FP64).  Synchronises the stream. */
-dh2_status dh2_error(const dh2_matrix* M, const void* G_ref, dh2_dtype ref_dtype, int64_t ld,
+/* y = G~^* x, the adjoint of dh2_matvec's product: the transformations of
+ * Section 4 with the roles of the row and column bases exchanged (forward on
+ * V, coupling with S_b^*, backward on W) plus G_b^* on the nearfield.
+ * Arguments and preconditions as dh2_matvec. */
+dh2_status dh2_matvec_adjoint(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream);
+
+/* Error measures of dh2_error. */
+enum {
+  DH2_ERR_FRO_BLOCKWISE = 0, /* |G_ref - G~|_F / |G_ref|_F, block by block (FP64 sums)          */
+  DH2_ERR_FRO_CLOSED = 1,    /* the same from sum_b |G_b|_F^2 - |S_b|_F^2 over admissible blocks,
+                                the squared error of the orthogonal projection (Section 6,
+                                Def. "Orthogonality"; exact for orthonormal bases); G_ref is not
+                                read (the block norms of the compressed G are used), so the value
+                                only means something in FP64 mode: in the complex64 modes the
+                                difference is below the rounding of the two norms             */
+  DH2_ERR_SPECTRAL = 2       /* |G_ref - G~|_2 / |G_ref|_2 by power iteration (the measure of
+                                the paper's experiments, Section 7): products with G_ref, G_ref^*
+                                in FP64 and with G~, G~^* (dh2_matvec, dh2_matvec_adjoint), from a
+                                fixed seeded start vector, until the estimate changes by less than
+                                1e-6 relative or after 60 products                             */
+};
+/* Relative error of the compressed matrix against G_ref, a device matrix of
+ * dtype ref_dtype (n x n column-major, permuted order, leading dimension ld),
+ * or NULL for a matrix from dh2_compress_kernel[_dlp] (reference entries
+ * generated in FP64), by the measure `which`.  Synchronises the stream. */
+dh2_status dh2_error(const dh2_matrix* M, const void* G_ref, dh2_dtype ref_dtype, int64_t ld, int32_t which,
                      void* stream, double* rel_err);
 
 /* Ranks of the used pairs of one side (host, npairs entries). */

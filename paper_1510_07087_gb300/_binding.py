@@ -107,7 +107,8 @@ SIGNATURES = [
     ("dh2_matrix_free", None, [c_void_p]),
     ("dh2_matvec", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_matvec_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
-    ("dh2_error", c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_void_p, POINTER(c_double)]),
+    ("dh2_matvec_adjoint", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
+    ("dh2_error", c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_int32, c_void_p, POINTER(c_double)]),
     ("dh2_matrix_ranks", c_int32, [c_void_p, c_int32, c_void_p]),
     ("dh2_matrix_sigma", c_int32, [c_void_p, c_int32, c_int64, c_void_p, c_int32, POINTER(c_int32)]),
     ("dh2_matrix_sigma_rest", c_int32, [c_void_p, c_int32, c_int64, POINTER(c_double)]),
@@ -484,15 +485,30 @@ def dh2_debug_fail_alloc(nth: int) -> None:
     _check(_lib().dh2_debug_fail_alloc(int(nth)), "dh2_debug_fail_alloc")
 
 
-def dh2_error(M: Matrix, Gref=None, stream=None) -> float:
-    """|G_ref - G~|_F / |G_ref|_F; Gref=None for a matrix-free compression (reference generated in FP64)."""
+ERR_FRO_BLOCKWISE = 0
+ERR_FRO_CLOSED = 1
+ERR_SPECTRAL = 2
+
+
+def dh2_error(M: Matrix, Gref=None, stream=None, which: int = ERR_FRO_BLOCKWISE) -> float:
+    """Relative error against Gref by `which` (ERR_FRO_BLOCKWISE |G - G~|_F/|G|_F, ERR_FRO_CLOSED its
+    closed form from the block norms, ERR_SPECTRAL |G - G~|_2/|G|_2 by power iteration); Gref=None for a
+    matrix-free compression (reference generated in FP64)."""
     out = c_double()
     if Gref is None:
-        _check(_lib().dh2_error(M.handle, None, 0, 0, c_void_p(_stream_handle(stream)), byref(out)), "dh2_error")
+        _check(_lib().dh2_error(M.handle, None, 0, 0, int(which), c_void_p(_stream_handle(stream)), byref(out)),
+               "dh2_error")
     else:
         _check(_lib().dh2_error(M.handle, c_void_p(Gref.data_ptr()), _dtype_code(Gref), _colmajor_ld(Gref),
-                                c_void_p(_stream_handle(stream)), byref(out)), "dh2_error")
+                                int(which), c_void_p(_stream_handle(stream)), byref(out)), "dh2_error")
     return float(out.value)
+
+
+def dh2_matvec_adjoint(M: Matrix, x, y, stream=None) -> None:
+    """y = G~^* x (adjoint product); operands as dh2_matvec."""
+    nrhs = _matvec_operands(M, x, y)
+    _check(_lib().dh2_matvec_adjoint(M.handle, c_void_p(x.data_ptr()), c_void_p(y.data_ptr()), nrhs,
+                                     c_void_p(_stream_handle(stream))), "dh2_matvec_adjoint")
 
 
 def dh2_version() -> str:

@@ -55,9 +55,11 @@ struct Tree::Dev {
   int32_t *bt, *bs, *badm, *bpair[2], *boff_row;
   int64_t *near_off, *Soff, *bmax_off;
   int32_t *adm_list, *inadm_list;
-  // matvec lists (row side)
+  // matvec lists (row side; the column side's serve the adjoint product)
   int64_t *own_ptr, *par_ptr;
   int32_t *own_blk, *par_pair, *par_son;
+  int64_t *own_ptr_c, *par_ptr_c;
+  int32_t *own_blk_c, *par_pair_c, *par_son_c;
   // launch orders: leaf launch (both sides) then non-leaf per level
   uint32_t* codes;
   // R tiles in the same order: code << 32 | first column, 32 columns each
@@ -104,6 +106,7 @@ struct dh2_matrix {
   void* S = nullptr;
   void* near = nullptr;
   double* invw = nullptr;
+  double* bnorm2 = nullptr;  // per block |G_b|_F^2 (admissible blocks)
   double* eps2 = nullptr;
   double* zpow = nullptr;
   uint32_t* status = nullptr;
@@ -339,9 +342,10 @@ dh2_status upload_tree(Tree& tr) {
   add64(std::move(mxoff), &D->bmax_off);
   add32(std::move(adm), &D->adm_list);
   add32(std::move(inadm), &D->inadm_list);
-  // row-side matvec lists: own blocks and father pairs per pair
-  {
-    Side& S = tr.side[0];
+  // matvec lists: own blocks and father pairs per pair, row side (the
+  // product) and column side (the adjoint product)
+  for (int sd = 0; sd < 2; ++sd) {
+    Side& S = tr.side[sd];
     const int64_t np = (int64_t)S.pairs.size();
     std::vector<int64_t> optr(np + 1, 0), pptr(np + 1, 0);
     std::vector<int32_t> oblk, ppair, pson;
@@ -355,11 +359,11 @@ dh2_status upload_tree(Tree& tr) {
       }
       pptr[p + 1] = (int64_t)ppair.size();
     }
-    add64(std::move(optr), &D->own_ptr);
-    add64(std::move(pptr), &D->par_ptr);
-    add32(std::move(oblk), &D->own_blk);
-    add32(std::move(ppair), &D->par_pair);
-    add32(std::move(pson), &D->par_son);
+    add64(std::move(optr), sd == 0 ? &D->own_ptr : &D->own_ptr_c);
+    add64(std::move(pptr), sd == 0 ? &D->par_ptr : &D->par_ptr_c);
+    add32(std::move(oblk), sd == 0 ? &D->own_blk : &D->own_blk_c);
+    add32(std::move(ppair), sd == 0 ? &D->par_pair : &D->par_pair_c);
+    add32(std::move(pson), sd == 0 ? &D->par_son : &D->par_son_c);
   }
   // launch codes: all leaf pairs of both sides by size class, costliest first
   // within a class; then non-leaf pairs per level
@@ -538,6 +542,7 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   na.gen = M->gen;
   na.bmax = nullptr;  // set by run_compress in the mixed modes
   na.bmax_off = D->bmax_off;
+  na.bnorm2 = M->bnorm2;
   for (int sd = 0; sd < 2; ++sd) {
     pa.start[sd] = D->start[sd];
     pa.m[sd] = D->m[sd];
@@ -1492,7 +1497,7 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   M->diag = diag;
   const size_t es = M->es;
   const int nl = tr.depth + 1;
-  size_t sz[20];
+  size_t sz[21];
   int ns = 0;
   sz[ns++] = align256(es * D->R_elems[0]);
   sz[ns++] = align256(es * D->R_elems[1]);
@@ -1514,6 +1519,7 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   sz[ns++] = align256(gen ? (nrm_host ? 48 : 24) * (size_t)tr.n : 0);  // points (and normals)
   sz[ns++] = align256(es / 2 * (size_t)tr.side[0].nleafcols);
   sz[ns++] = align256(es / 2 * (size_t)tr.side[1].nleafcols);
+  sz[ns++] = align256(8 * tr.blocks.size());
   size_t total = 0;
   for (int i = 0; i < ns; ++i) total += sz[i];
   if (dev_malloc_async(&M->arena, total, M->stream) != cudaSuccess) {
@@ -1531,10 +1537,10 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
     return DH2_ENOMEM;
   }
   char* p = (char*)M->arena;
-  void** dst[20] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
+  void** dst[21] = {&M->R[0], &M->R[1], &M->Q[0], &M->Q[1], &M->X[0], &M->X[1], &M->S, &M->near,
                     (void**)&M->sig[0], (void**)&M->sig[1], (void**)&M->rank[0], (void**)&M->rank[1],
                     (void**)&M->invw, (void**)&M->eps2, (void**)&M->zpow, (void**)&M->status, (void**)&M->acc,
-                    (void**)&M->pts, &M->colw[0], &M->colw[1]};
+                    (void**)&M->pts, &M->colw[0], &M->colw[1], (void**)&M->bnorm2};
   for (int i = 0; i < ns; ++i) {
     *dst[i] = p;
     p += sz[i];
@@ -1764,8 +1770,168 @@ dh2_status run_matvec(const dh2_matrix* M, const void* xv, void* yv, int nrhs, c
   return DH2_OK;
 }
 
+// y = G~^* x: the product of Section 4 with the roles of the row and column
+// bases exchanged (forward on V, coupling with S_b^*, backward on W) plus
+// G_b^* on the nearfield.
 template <typename T>
-dh2_status run_error(dh2_matrix* M, const void* Gref, dh2_dtype rdt, int64_t ldr, cudaStream_t st, double* rel) {
+dh2_status run_matvec_adj(const dh2_matrix* M, const void* xv, void* yv, int nrhs, cudaStream_t st) {
+  Tree& tr = M->tree->tr;
+  Tree::Dev* D = tr.dev;
+  const int64_t n = tr.n;
+  void* buf = nullptr;
+  const size_t hx = align256(sizeof(C2<T>) * D->h_elems[0] * nrhs);
+  const size_t hy = align256(sizeof(C2<T>) * D->h_elems[1] * nrhs);
+  if (dev_malloc_async(&buf, hx + hy + 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return DH2_ENOMEM;
+  }
+  C2<T>* xh = (C2<T>*)buf;
+  C2<T>* yh = (C2<T>*)((char*)buf + hx);
+  const C2<T>* x = (const C2<T>*)xv;
+  C2<T>* y = (C2<T>*)yv;
+  cudaMemsetAsync(y, 0, sizeof(C2<T>) * n * nrhs, st);
+  SideView<T> Vv = side_view<T>(tr, M, 0), Wv = side_view<T>(tr, M, 1);
+  launch_mv_forward_leaf<T>(Vv, D->leaf_list[0], (int)D->nleaf[0], x, nrhs, n, xh, D->hoff[0], st);
+  for (int l = tr.depth; l >= 0; --l) {
+    const int64_t b = D->lvl_nl_begin[0][l], e = D->lvl_end[0][l];
+    if (e > b) launch_mv_forward_up<T>(Vv, D->iota[0] + b, (int)(e - b), nrhs, xh, D->hoff[0], st);
+  }
+  MvArgs<T> a;
+  a.V = Wv;  // exchanged sides
+  a.W = Vv;
+  a.S = (const C2<T>*)M->S;
+  a.Soff = D->Soff;
+  a.own_ptr = D->own_ptr_c;
+  a.own_blk = D->own_blk_c;
+  a.bpair_col = D->bpair[0];
+  a.xh = xh;
+  a.xhoff = D->hoff[0];
+  a.yh = yh;
+  a.yhoff = D->hoff[1];
+  a.par_ptr = D->par_ptr_c;
+  a.par_pair = D->par_pair_c;
+  a.par_son = D->par_son_c;
+  a.bt = D->bt;
+  a.bs = D->bs;
+  a.near = (const C2<T>*)M->near;
+  a.near_off = D->near_off;
+  a.G = (const C2<T>*)M->G;
+  a.ld = M->ld;
+  launch_mv_coupling_adj<T>(a, (int)D->npairs[1], nrhs, st);
+  for (int l = 1; l <= tr.depth; ++l) {
+    const int64_t b = D->lvl_begin[1][l], e = D->lvl_end[1][l];
+    if (e > b) launch_mv_backward_down<T>(a, D->iota[1] + b, (int)(e - b), nrhs, st);
+  }
+  launch_mv_backward_leaf<T>(a, D->leaf_list[1], (int)D->nleaf[1], nrhs, y, n, st);
+  launch_mv_near_adj<T>(a, D->inadm_list, (int)D->ninadm, nrhs, x, y, n, st);
+  cudaFreeAsync(buf, st);
+  DH2_CUDA_TRY(cudaGetLastError());
+  return DH2_OK;
+}
+
+// Relative spectral error |G_ref - G~|_2 / |G_ref|_2 by power iteration (the
+// error measure of the paper's experiments, Section 7): the largest
+// eigenvalue of E^* E with E = G_ref - G~ (products with G_ref and G_ref^* in
+// FP64, with G~ and G~^* by the library's product and adjoint product in the
+// matrix's arithmetic), and likewise of G_ref^* G_ref, each from a fixed
+// seeded start vector until the estimate changes by less than 1e-6 relative
+// (at most kSpectralIters products).
+constexpr int kSpectralIters = 60;
+
+template <typename T>
+dh2_status run_error_spectral(dh2_matrix* M, const void* Gref, dh2_dtype rdt, int64_t ldr, cudaStream_t st,
+                              double* rel) {
+  Tree& tr = M->tree->tr;
+  const int64_t n = tr.n;
+  ErrArgs<float> gen{};
+  gen.pts = M->pts;
+  gen.nrm = M->nrm;
+  gen.kappa = M->kappa;
+  gen.diag = M->diag;
+  void* buf = nullptr;
+  const size_t vb = align256(sizeof(C2<double>) * n), tb = align256(sizeof(C2<T>) * n);
+  if (dev_malloc_async(&buf, 3 * vb + 2 * tb + 256, st) != cudaSuccess) {
+    cudaGetLastError();
+    return DH2_ENOMEM;
+  }
+  C2<double>* v = (C2<double>*)buf;
+  C2<double>* u = (C2<double>*)((char*)buf + vb);
+  C2<double>* w = (C2<double>*)((char*)buf + 2 * vb);
+  C2<T>* xt = (C2<T>*)((char*)buf + 3 * vb);
+  C2<T>* yt = (C2<T>*)((char*)buf + 3 * vb + tb);
+  auto gemv = [&](bool trans, const C2<double>* x, C2<double>* y) {
+    if (rdt == DH2_C128 && Gref) launch_gemv<double>((const C2<double>*)Gref, ldr, gen, n, trans, x, y, st);
+    else launch_gemv<float>((const C2<float>*)Gref, ldr, gen, n, trans, x, y, st);
+  };
+  std::vector<C2<double>> h(n);
+  auto start = [&]() -> dh2_status {  // seeded start vector, unit norm
+    uint64_t z = 0x9E3779B97F4A7C15ull;
+    double s2 = 0;
+    for (int64_t i = 0; i < n; ++i) {
+      z ^= z << 13;
+      z ^= z >> 7;
+      z ^= z << 17;
+      const double re = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+      z ^= z << 13;
+      z ^= z >> 7;
+      z ^= z << 17;
+      const double im = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+      h[i] = C2<double>{re, im};
+      s2 += re * re + im * im;
+    }
+    const double sc = 1.0 / std::sqrt(s2);
+    for (auto& e : h) e = C2<double>{e.re * sc, e.im * sc};
+    DH2_CUDA_TRY(cudaMemcpyAsync(v, h.data(), sizeof(C2<double>) * n, cudaMemcpyHostToDevice, st));
+    return DH2_OK;
+  };
+  // lambda_max(A^* A) for A = G_ref - G~ (err) or A = G_ref; w = A^* A v, v <- w / |w|
+  auto power = [&](bool err, double* lam) -> dh2_status {
+    dh2_status s = start();
+    if (s != DH2_OK) return s;
+    double prev = 0.0;
+    for (int it = 0; it < kSpectralIters; ++it) {
+      gemv(false, v, u);
+      if (err) {
+        launch_to_type<T>(v, xt, n, st);
+        s = run_matvec<T>(M, xt, yt, 1, st);
+        if (s != DH2_OK) return s;
+        launch_sub<T>(u, yt, n, st);
+      }
+      gemv(true, u, w);
+      if (err) {
+        launch_to_type<T>(u, xt, n, st);
+        s = run_matvec_adj<T>(M, xt, yt, 1, st);
+        if (s != DH2_OK) return s;
+        launch_sub<T>(w, yt, n, st);
+      }
+      DH2_CUDA_TRY(cudaMemcpyAsync(h.data(), w, sizeof(C2<double>) * n, cudaMemcpyDeviceToHost, st));
+      DH2_CUDA_TRY(cudaStreamSynchronize(st));
+      double s2 = 0;
+      for (const auto& e : h) s2 += e.re * e.re + e.im * e.im;
+      const double nw = std::sqrt(s2);  // |A^* A v| with |v| = 1
+      *lam = nw;
+      if (!(nw > 0.0)) return DH2_OK;
+      const double sc = 1.0 / nw;
+      for (auto& e : h) e = C2<double>{e.re * sc, e.im * sc};
+      DH2_CUDA_TRY(cudaMemcpyAsync(v, h.data(), sizeof(C2<double>) * n, cudaMemcpyHostToDevice, st));
+      if (it > 2 && std::fabs(nw - prev) <= 1e-6 * nw) break;
+      prev = nw;
+    }
+    return DH2_OK;
+  };
+  double le = 0.0, lg = 0.0;
+  dh2_status s = power(true, &le);
+  if (s == DH2_OK) s = power(false, &lg);
+  cudaFreeAsync(buf, st);
+  if (s != DH2_OK) return s;
+  DH2_CUDA_TRY(cudaStreamSynchronize(st));
+  *rel = lg > 0.0 ? std::sqrt(le / lg) : 0.0;
+  return DH2_OK;
+}
+
+template <typename T>
+dh2_status run_error(dh2_matrix* M, const void* Gref, dh2_dtype rdt, int64_t ldr, int which, cudaStream_t st,
+                     double* rel) {
   Tree& tr = M->tree->tr;
   Tree::Dev* D = tr.dev;
   SideView<T> Vv = side_view<T>(tr, M, 0), Wv = side_view<T>(tr, M, 1);
@@ -1797,15 +1963,17 @@ dh2_status run_error(dh2_matrix* M, const void* Gref, dh2_dtype rdt, int64_t ldr
   a.kappa = M->kappa;
   a.diag = M->diag;
   a.ref_gen = Gref == nullptr ? 1 : 0;
+  if (which == DH2_ERR_SPECTRAL) return run_error_spectral<T>(M, Gref, rdt, ldr, st, rel);
   DH2_CUDA_TRY(cudaMemsetAsync(M->acc, 0, 16, st));
-  if (rdt == DH2_C128)
+  if (which == DH2_ERR_FRO_CLOSED) launch_closed_form<T>(a, M->bnorm2, (int)tr.blocks.size(), M->acc, st);
+  else if (rdt == DH2_C128)
     launch_error<T, double>(a, (const C2<double>*)Gref, ldr, (int)tr.blocks.size(), M->acc, st);
   else
     launch_error<T, float>(a, (const C2<float>*)Gref, ldr, (int)tr.blocks.size(), M->acc, st);
   double h[2] = {0, 0};
   DH2_CUDA_TRY(cudaMemcpyAsync(h, M->acc, 16, cudaMemcpyDeviceToHost, st));
   DH2_CUDA_TRY(cudaStreamSynchronize(st));
-  *rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : 0.0;
+  *rel = h[1] > 0 ? std::sqrt(std::max(0.0, h[0]) / h[1]) : 0.0;
   return DH2_OK;
 }
 
@@ -1819,13 +1987,20 @@ dh2_status dh2_matvec(const dh2_matrix* M, const void* x, void* y, int32_t nrhs,
                                   : run_matvec<double>(M, x, y, nrhs, (cudaStream_t)stream);
 }
 
-dh2_status dh2_error(const dh2_matrix* Mc, const void* G_ref, dh2_dtype ref_dtype, int64_t ld, void* stream,
-                     double* rel_err) {
-  if (!Mc || !rel_err) return DH2_EINVAL;
-  if (G_ref ? ld < Mc->tree->tr.n : !Mc->gen) return DH2_EINVAL;
+dh2_status dh2_matvec_adjoint(const dh2_matrix* M, const void* x, void* y, int32_t nrhs, void* stream) {
+  if (!M || !x || !y || nrhs < 1) return DH2_EINVAL;
+  return mode_f32(M->mode) ? run_matvec_adj<float>(M, x, y, nrhs, (cudaStream_t)stream)
+                           : run_matvec_adj<double>(M, x, y, nrhs, (cudaStream_t)stream);
+}
+
+dh2_status dh2_error(const dh2_matrix* Mc, const void* G_ref, dh2_dtype ref_dtype, int64_t ld, int32_t which,
+                     void* stream, double* rel_err) {
+  if (!Mc || !rel_err || which < DH2_ERR_FRO_BLOCKWISE || which > DH2_ERR_SPECTRAL) return DH2_EINVAL;
+  if (which != DH2_ERR_FRO_CLOSED && (G_ref ? ld < Mc->tree->tr.n : !Mc->gen)) return DH2_EINVAL;
+  if (G_ref && ref_dtype != DH2_C64 && ref_dtype != DH2_C128) return DH2_EINVAL;
   dh2_matrix* M = const_cast<dh2_matrix*>(Mc);
-  return mode_f32(M->mode) ? run_error<float>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err)
-                                  : run_error<double>(M, G_ref, ref_dtype, ld, (cudaStream_t)stream, rel_err);
+  return mode_f32(M->mode) ? run_error<float>(M, G_ref, ref_dtype, ld, which, (cudaStream_t)stream, rel_err)
+                           : run_error<double>(M, G_ref, ref_dtype, ld, which, (cudaStream_t)stream, rel_err);
 }
 
 dh2_status dh2_matrix_ranks(const dh2_matrix* M, int32_t side, int32_t* ranks) {

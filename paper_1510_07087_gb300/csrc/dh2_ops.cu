@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
       const double tot = warp_sum(acc);
       if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
         a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+    if (lane == 0 && a.bnorm2) a.bnorm2[b] = tot;
     } else if (a.copy) {
       C2<T>* out = a.near + a.near_off[b];
       for (int64_t e = lane; e < (int64_t)mt * ms; e += 32) {
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
     const double tot = warp_sum((double)acc);
     if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
       a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+    if (lane == 0 && a.bnorm2) a.bnorm2[b] = tot;
   } else if (a.badm[b]) {
     T acc[8];
 #pragma unroll
@@ -156,6 +158,7 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
     tot = warp_sum(tot);
     if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
       a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
+    if (lane == 0 && a.bnorm2) a.bnorm2[b] = tot;
   } else if (a.copy) {
     C2<T>* out = a.near + a.near_off[b];
     for (int e0 = 0; e0 < total; e0 += 256) {
@@ -549,6 +552,157 @@ __global__ void __launch_bounds__(256) error_kernel(ErrArgs<T> a, const C2<RT>* 
   }
 }
 
+// ---------------------------------------------------------------- adjoint product
+// y = G~^* x: the forward transformation runs on the row basis V, the
+// coupling applies S_b^* from row pairs to column pairs, the backward
+// transformation runs on the column basis W (the roles of V and W in
+// Section 4 exchanged), plus G_b^* on the nearfield.  The kernels of the
+// product are reused with an MvArgs whose V and W, coefficient vectors and
+// pair lists are those of the exchanged sides; coupling and nearfield need
+// their own (conjugate-transposed) loops.
+//
+// coupling: yh_sc = sum over the column pair's blocks b of S_b^* xh_tc
+template <typename T>
+__global__ void mv_coupling_adj(MvArgs<T> a, int nrhs) {
+  const int pid = blockIdx.x;
+  const int kout = a.V.rank[pid];  // rank of this column pair
+  for (int idx = threadIdx.x; idx < kout * nrhs; idx += blockDim.x) {
+    const int qq = idx % kout, rh = idx / kout;
+    C2<T> acc = czero<T>();
+    for (int64_t e = a.own_ptr[pid]; e < a.own_ptr[pid + 1]; ++e) {
+      const int b = a.own_blk[e];
+      const int Pt = a.bpair_col[b];   // the block's row pair
+      const int kin = a.W.rank[Pt];
+      const C2<T>* S = a.S + a.Soff[b];  // kin x kout, column-major
+      const C2<T>* xs = a.xh + a.xhoff[Pt] * nrhs + (int64_t)rh * kin;
+      for (int l = 0; l < kin; ++l) acc = cadd(acc, cmul(cconj(S[l + (int64_t)qq * kin]), xs[l]));
+    }
+    a.yh[a.yhoff[pid] * nrhs + qq + (int64_t)rh * kout] = acc;
+  }
+}
+
+// nearfield: y|_s += G_b^* x|_t for inadmissible leaves
+template <typename T>
+__global__ void mv_near_adj(MvArgs<T> a, const int32_t* blocks, int nrhs, const C2<T>* x, C2<T>* y, int64_t n) {
+  const int b = blocks[blockIdx.x];
+  const int t = a.bt[b], s = a.bs[b];
+  const int mt = a.V.csize[t], ms = a.V.csize[s];
+  const int64_t t0 = a.V.cstart[t], s0 = a.V.cstart[s];
+  const C2<T>* Gb;
+  int64_t ldb;
+  if (a.near) {
+    Gb = a.near + a.near_off[b];
+    ldb = mt;
+  } else {
+    Gb = a.G + s0 * a.ld + t0;
+    ldb = a.ld;
+  }
+  // one warp per column of the block: lanes over its rows
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int cj = wp; cj < ms * nrhs; cj += nw) {
+    const int j = cj % ms, rh = cj / ms;
+    C2<T> acc = czero<T>();
+    for (int i = lane; i < mt; i += 32) acc = cadd(acc, cmul(cconj(Gb[i + (int64_t)j * ldb]), x[t0 + i + rh * n]));
+    acc.re = warp_sum(acc.re);
+    acc.im = warp_sum(acc.im);
+    if (lane == 0) catomic_add(y + s0 + j + rh * n, acc);
+  }
+}
+
+// ---------------------------------------------------------------- dense products with the reference
+// y = G_ref x (trans = false) or y = G_ref^* x (trans = true), complex128
+// vectors, FP64 accumulation; G_ref stored (column-major, ld) or generated
+// from the points (matrix-free compression: gen != 0).
+template <typename RT>
+__device__ __forceinline__ C2<double> gref(const C2<RT>* G, int64_t ld, const ErrArgs<float>& g, int64_t i,
+                                           int64_t j) {
+  if (!G) return kernel_entry<double>(g.pts, g.nrm, i, j, g.kappa, g.diag);
+  const C2<RT> v = G[i + j * ld];
+  return C2<double>{(double)v.re, (double)v.im};
+}
+
+template <typename RT>
+__global__ void __launch_bounds__(256) gemv_n_kernel(const C2<RT>* G, int64_t ld, ErrArgs<float> g, int64_t n,
+                                                     const C2<double>* x, C2<double>* y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double ar = 0.0, ai = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    const C2<double> v = gref<RT>(G, ld, g, i, j);
+    const C2<double> u = x[j];
+    ar = fma(v.re, u.re, fma(-v.im, u.im, ar));
+    ai = fma(v.re, u.im, fma(v.im, u.re, ai));
+  }
+  y[i] = C2<double>{ar, ai};
+}
+
+template <typename RT>
+__global__ void __launch_bounds__(256) gemv_c_kernel(const C2<RT>* G, int64_t ld, ErrArgs<float> g, int64_t n,
+                                                     const C2<double>* x, C2<double>* y) {
+  const int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (j >= n) return;
+  double ar = 0.0, ai = 0.0;
+  for (int64_t i = lane; i < n; i += 32) {
+    const C2<double> v = gref<RT>(G, ld, g, i, j);
+    const C2<double> u = x[i];
+    // conj(v) u
+    ar = fma(v.re, u.re, fma(v.im, u.im, ar));
+    ai = fma(v.re, u.im, fma(-v.im, u.re, ai));
+  }
+  ar = warp_sum(ar);
+  ai = warp_sum(ai);
+  if (lane == 0) y[j] = C2<double>{ar, ai};
+}
+
+// ---------------------------------------------------------------- closed-form error
+// sum over admissible blocks of |G_b|_F^2 - |S_b|_F^2 (the squared error of
+// the orthogonal projection, Section 6) and over all blocks of |G_b|_F^2
+// (inadmissible blocks from the nearfield copy or the viewed G).
+template <typename T>
+__global__ void __launch_bounds__(256) closed_form_kernel(ErrArgs<T> a, const double* bnorm2, int nblocks,
+                                                           double* acc_out) {
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= nblocks) return;
+  double e = 0.0, r = 0.0;
+  if (a.badm[b]) {
+    const int kt = a.V.rank[a.bpair_row[b]], ks = a.W.rank[a.bpair_col[b]];
+    const C2<T>* S = a.S + a.Soff[b];
+    double s2 = 0.0;
+    for (int i = lane; i < kt * ks; i += 32) s2 += (double)S[i].re * S[i].re + (double)S[i].im * S[i].im;
+    s2 = warp_sum(s2);
+    e = bnorm2[b] - s2;
+    r = bnorm2[b];
+  } else {
+    const int t = a.bt[b], s = a.bs[b];
+    const int mt = a.csize[t], ms = a.csize[s];
+    double g2 = 0.0;
+    for (int idx = lane; idx < mt * ms; idx += 32) {
+      const int i = idx % mt, j = idx / mt;
+      const C2<T> v = a.near ? a.near[a.near_off[b] + idx] : a.G[(a.cstart[t] + i) + (a.cstart[s] + j) * a.ld];
+      g2 += (double)v.re * v.re + (double)v.im * v.im;
+    }
+    r = warp_sum(g2);
+  }
+  if (lane == 0) {
+    atomicAdd(acc_out, e);
+    atomicAdd(acc_out + 1, r);
+  }
+}
+
+// ---------------------------------------------------------------- vector helpers of the power iteration
+template <typename T>
+__global__ void to_type_kernel(const C2<double>* __restrict__ v, C2<T>* __restrict__ o, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    o[i] = C2<T>{(T)v[i].re, (T)v[i].im};
+}
+template <typename T>
+__global__ void sub_kernel(C2<double>* __restrict__ u, const C2<T>* __restrict__ t, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    u[i] = C2<double>{u[i].re - (double)t[i].re, u[i].im - (double)t[i].im};
+}
+
 }  // namespace
 
 void check_set_limits_ops(const CheckLimits& l) {
@@ -617,6 +771,39 @@ void launch_error(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int nblo
   if (nblocks > 0) error_kernel<T, RT><<<nblocks, 256, 0, st>>>(a, Gref, ldr, acc);
 }
 
+template <typename T>
+void launch_mv_coupling_adj(const MvArgs<T>& a, int npairs_col, int nrhs, cudaStream_t st) {
+  if (npairs_col > 0) mv_coupling_adj<T><<<npairs_col, 128, 0, st>>>(a, nrhs);
+}
+template <typename T>
+void launch_mv_near_adj(const MvArgs<T>& a, const int32_t* blocks, int nb, int nrhs, const C2<T>* x, C2<T>* y,
+                        int64_t n, cudaStream_t st) {
+  if (nb > 0) mv_near_adj<T><<<nb, 128, 0, st>>>(a, blocks, nrhs, x, y, n);
+}
+template <typename RT>
+void launch_gemv(const C2<RT>* G, int64_t ld, const ErrArgs<float>& gen, int64_t n, bool trans, const C2<double>* x,
+                 C2<double>* y, cudaStream_t st) {
+  if (n <= 0) return;
+  if (!trans) gemv_n_kernel<RT><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, ld, gen, n, x, y);
+  else gemv_c_kernel<RT><<<(unsigned)((n + 7) / 8), 256, 0, st>>>(G, ld, gen, n, x, y);
+}
+template <typename T>
+void launch_closed_form(const ErrArgs<T>& a, const double* bnorm2, int nblocks, double* acc, cudaStream_t st) {
+  if (nblocks > 0) closed_form_kernel<T><<<(nblocks + 7) / 8, 256, 0, st>>>(a, bnorm2, nblocks, acc);
+}
+template <typename T>
+void launch_to_type(const C2<double>* v, C2<T>* o, int64_t n, cudaStream_t st) {
+  if (n > 0) to_type_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, o, n);
+}
+template <typename T>
+void launch_sub(C2<double>* u, const C2<T>* t, int64_t n, cudaStream_t st) {
+  if (n > 0) sub_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(u, t, n);
+}
+template void launch_gemv<float>(const C2<float>*, int64_t, const ErrArgs<float>&, int64_t, bool, const C2<double>*,
+                                 C2<double>*, cudaStream_t);
+template void launch_gemv<double>(const C2<double>*, int64_t, const ErrArgs<float>&, int64_t, bool,
+                                  const C2<double>*, C2<double>*, cudaStream_t);
+
 // Column maps from their segments: one warp per segment writes the global
 // column index and the block id of each of the segment's w columns.
 __global__ void colmap_expand_kernel(const int64_t* __restrict__ dst, const int32_t* __restrict__ col0,
@@ -669,7 +856,13 @@ void launch_colw(const int32_t* gblk, const double* invw, T* colw, int64_t n, cu
   template void launch_error<T, float>(const ErrArgs<T>&, const C2<float>*, int64_t, int, double*,        \
                                        cudaStream_t);                                                      \
   template void launch_error<T, double>(const ErrArgs<T>&, const C2<double>*, int64_t, int, double*,      \
-                                        cudaStream_t);
+                                        cudaStream_t);                                                      \
+  template void launch_mv_coupling_adj<T>(const MvArgs<T>&, int, int, cudaStream_t);                       \
+  template void launch_mv_near_adj<T>(const MvArgs<T>&, const int32_t*, int, int, const C2<T>*, C2<T>*,    \
+                                      int64_t, cudaStream_t);                                              \
+  template void launch_closed_form<T>(const ErrArgs<T>&, const double*, int, double*, cudaStream_t);            \
+  template void launch_to_type<T>(const C2<double>*, C2<T>*, int64_t, cudaStream_t);                       \
+  template void launch_sub<T>(C2<double>*, const C2<T>*, int64_t, cudaStream_t);
 
 DH2_INST(float)
 DH2_INST(double)

@@ -49,6 +49,7 @@ struct NormsArgs {
   // rows, then of each of its columns (bmax + bmax_off[b]); NULL otherwise
   float* bmax;
   const int64_t* bmax_off;
+  double* bnorm2;  // per block |G_b|_F^2 of the admissible blocks (closed-form error)
 };
 
 template <typename T>
@@ -141,5 +142,22 @@ void launch_mv_near(const MvArgs<T>& a, const int32_t* blocks, int nb, int nrhs,
 template <typename T, typename RT>
 void launch_error(const ErrArgs<T>& a, const C2<RT>* Gref, int64_t ldr, int nblocks, double* acc,
                   cudaStream_t st);
+// adjoint product: coupling with S_b^* into column pairs, nearfield with G_b^*
+// (MvArgs with the sides exchanged: V = column basis, W = row basis, own and
+// father lists of the column side, bpair_col = the blocks' row pairs)
+template <typename T> void launch_mv_coupling_adj(const MvArgs<T>& a, int npairs_col, int nrhs, cudaStream_t st);
+template <typename T>
+void launch_mv_near_adj(const MvArgs<T>& a, const int32_t* blocks, int nb, int nrhs, const C2<T>* x, C2<T>* y,
+                        int64_t n, cudaStream_t st);
+// y = G_ref x or G_ref^* x in FP64 (G NULL: entries generated from gen's points)
+template <typename RT>
+void launch_gemv(const C2<RT>* G, int64_t ld, const ErrArgs<float>& gen, int64_t n, bool trans, const C2<double>* x,
+                 C2<double>* y, cudaStream_t st);
+// acc[0] += sum_adm |G_b|^2 - |S_b|^2, acc[1] += sum_all |G_b|^2
+template <typename T>
+void launch_closed_form(const ErrArgs<T>& a, const double* bnorm2, int nblocks, double* acc, cudaStream_t st);
+// o = (T) v; u -= t  (vectors of n complex entries)
+template <typename T> void launch_to_type(const C2<double>* v, C2<T>* o, int64_t n, cudaStream_t st);
+template <typename T> void launch_sub(C2<double>* u, const C2<T>* t, int64_t n, cudaStream_t st);
 
 }  // namespace dh2

@@ -200,3 +200,31 @@ def test_fp64_rank_override_gives_the_oracles_approximation():
     torch.cuda.synchronize()
     rel = np.linalg.norm(yd.cpu().numpy() - y_ref) / np.linalg.norm(y_ref)
     assert rel <= 1e-11, rel
+
+
+def test_fp64_error_measures_and_adjoint(c1_fp64):
+    """dh2_error's three measures and dh2_matvec_adjoint against the oracle's dense approximation
+    (at the GPU's ranks): the closed form sum |G_b|^2 - |S_b|^2 equals the blockwise Frobenius error
+    (orthogonal projection, Section 6); the power-iteration spectral error matches the dense spectral
+    norm; the adjoint product equals G~^* y and satisfies <G~ x, y> = <x, G~^* y>."""
+    c = c1_fp64
+    D = c.D
+    Gt = O.dense_approximation(c.tr, c.G, c.Vg, c.Wg, c.Sg)
+    fro = D.dh2_error(c.M, c.Gd, which=D.ERR_FRO_BLOCKWISE)
+    closed = D.dh2_error(c.M, c.Gd, which=D.ERR_FRO_CLOSED)
+    assert abs(closed - fro) <= 1e-5 * fro, (closed, fro)
+    spec = D.dh2_error(c.M, c.Gd, which=D.ERR_SPECTRAL)
+    ref = np.linalg.norm(c.G - Gt, 2) / np.linalg.norm(c.G, 2)
+    print(f"spectral error: power iteration {spec:.6e}, dense {ref:.6e}; Frobenius {fro:.6e}")
+    assert abs(spec - ref) <= 0.05 * ref, (spec, ref)
+    x = random_complex_vectors(c.tr.n, 2, seed=31)
+    y = random_complex_vectors(c.tr.n, 2, seed=32)
+    yd = torch.from_numpy(np.ascontiguousarray(y.T)).to("cuda").t()
+    zd = torch.empty_like(yd.t().contiguous()).t()
+    D.dh2_matvec_adjoint(c.M, yd, zd)
+    torch.cuda.synchronize()
+    z = zd.cpu().numpy()
+    zr = Gt.conj().T @ y
+    assert np.linalg.norm(z - zr) <= 1e-11 * np.linalg.norm(zr)
+    gx = c.gpu_matvec(x)
+    assert abs(np.vdot(y, gx) - np.vdot(z, x)) <= 1e-11 * np.linalg.norm(y) * np.linalg.norm(gx)
