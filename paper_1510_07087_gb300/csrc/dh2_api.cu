@@ -1119,6 +1119,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     cudaEventRecord(ev[1], st);
 #ifdef DH2_PROFILE
     prof_reset_pair();
+    prof_reset_gram();
 #endif
     for (int c = 0; c < kLeafClasses; ++c) leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c);
     cudaEventRecord(ev[2], st);
@@ -1139,6 +1140,15 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     prof_read_pair(pr);
     const double np = pr[5] ? (double)pr[5] : 1.0;
     const double ns = pr[12] ? (double)pr[12] : 1.0;
+    unsigned long long gq[10];
+    if (prof_read_gram(gq) && gq[0]) {
+      const double gp = (double)gq[0];
+      std::fprintf(stderr,
+                   "dh2 gram profile: %llu pairs, %.2f chunks/pair; cycles/pair (CTA thread 0): scales %.0f, table %.0f, "
+                   "chunk loads %.0f, MMA waits %.0f, slicing %.0f, MMA issue %.0f, flush %.0f, H out %.0f\n",
+                   gq[0], gq[1] / gp, gq[2] / gp, gq[3] / gp, gq[4] / gp, gq[5] / gp, gq[6] / gp, gq[7] / gp,
+                   gq[8] / gp, gq[9] / gp);
+    }
     std::fprintf(stderr,
                  "dh2 leaf-launch profile: %llu pairs, mean p %.1f, mean K %.1f, mean sweeps %.2f, mean chunks %.2f, "
                  "cycles/pair: LQ %.0f (staging %.0f) Jacobi %.0f rank+Q %.0f; LQ steps %.1f/pair, cycles/step %.0f, "

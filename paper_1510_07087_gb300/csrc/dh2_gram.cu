@@ -47,6 +47,18 @@ namespace {
 
 using namespace sm100;
 
+#ifdef DH2_PROFILE
+// summed over CTAs, seen by thread 0: pairs, chunks, then cycles in row
+// scales, table loads, issuing chunk loads, waits for MMA batches, slicing,
+// issuing MMAs, window flushes, H output
+__device__ unsigned long long g_gprof[10];
+#define GP_T(v) v = clock64()
+#define GP_ON 1
+#else
+#define GP_T(v)
+#define GP_ON 0
+#endif
+
 constexpr int kGramThreads = 128;
 constexpr int kGramChunk = 64;        // complex columns per chunk (one 128-byte K row of bf16)
 constexpr int kTableCols = 1024;      // columns of the pair's column table held in shared memory at once
@@ -134,6 +146,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   bool timed_out = false;
   uint32_t* st_ptr = args[0].status;
   const uint32_t polls = args[0].spin_limit > 0 ? args[0].spin_limit : kWaitPolls;
+#if GP_ON
+  long long gp[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  long long ga = 0, gb = 0;
+#endif
 
   for (int ci = blockIdx.x; ci < ncodes && !timed_out; ci += gridDim.x) {
     const uint32_t code = codes[ci];
@@ -162,6 +178,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       continue;
     }
     const int nitem = m * 8;  // (row, group of 8 columns) items of a chunk
+#if GP_ON
+    gp[0] += 1;
+    GP_T(ga);
+#endif
 
     // ---------------------------------------------------------------- row scales
     // the largest |re|, |im| of each row of A = G^omega_tc from the block
@@ -199,17 +219,30 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         rsc[i] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
       }
     }
+#if GP_ON
+    GP_T(gb);
+    gp[2] += gb - ga;
+#endif
     // column table of the pair (segments of kTableCols columns)
     auto load_table = [&](int tb) {
+#if GP_ON
+      long long t0 = clock64();
+#endif
       __syncthreads();  // no thread still reads the previous segment
       for (int jj = tid; jj < kTableCols && tb + jj < N; jj += kGramThreads) {
         cgcT[jj] = gcol[tb + jj];
         cwtT[jj] = colw[tb + jj];
       }
       __syncthreads();
+#if GP_ON
+      gp[3] += clock64() - t0;
+#endif
     };
     // entries of this thread's items of the chunk at j0 (zero past the chunk)
     auto load_chunk = [&](int j0, int cw, int tb, C2<float> (&v)[4][8]) {
+#if GP_ON
+      long long t0 = clock64();
+#endif
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int q = tid + kGramThreads * u;
@@ -225,15 +258,25 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           }
         }
       }
+#if GP_ON
+      gp[4] += clock64() - t0;
+#endif
     };
 
     // ---------------------------------------------------------------- sliced products
     bool pending = false;  // an MMA batch was committed and not yet waited for
     auto wait_mma = [&]() -> bool {
+#if GP_ON
+      long long t0 = clock64();
+#endif
       const bool ok = mbar_wait(&bar, phase, polls);
       phase ^= 1u;
       pending = false;
-      return __syncthreads_or(!ok) == 0;
+      const bool r = __syncthreads_or(!ok) == 0;
+#if GP_ON
+      gp[5] += clock64() - t0;
+#endif
+      return r;
     };
     int tb = 0;
     load_table(0);
@@ -248,6 +291,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           break;
         }
         // slices of this thread's items -> operand rows X (r), Y (mp + r), -X (2 mp + r)
+#if GP_ON
+        gp[1] += 1;
+        GP_T(ga);
+#endif
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int q = tid + kGramThreads * u;
@@ -299,6 +346,10 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         }
         fence_async_smem();
         __syncthreads();
+#if GP_ON
+        GP_T(gb);
+        gp[6] += gb - ga;
+#endif
         if (tid == 0) {
           tc_fence_after_sync();
           const bool first = j0 == w0;
@@ -319,6 +370,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
             }
           }
           mma_commit(&bar);
+#if GP_ON
+          gp[7] += clock64() - gb;
+#endif
         }
         pending = true;
         // the next chunk's loads go out while the tensor cores work on this one
@@ -338,6 +392,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       // window done: V = P11 2^31 + P12 2^24 + P13 2^16 + P22 2^15 + low 2^8 per lane (row of [Re; Im]);
       // every P is an integer below 2^24 held exactly in FP32
       const bool last = wend >= N;
+#if GP_ON
+      GP_T(ga);
+#endif
       tc_fence_after_sync();
       const int L = tid;  // TMEM lane of this thread
 #pragma unroll 1
@@ -369,8 +426,14 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       }
       tc_fence_before_sync();
       __syncthreads();
+#if GP_ON
+      gp[8] += clock64() - ga;
+#endif
     }
     if (timed_out) break;
+#if GP_ON
+    GP_T(ga);
+#endif
     // ---------------------------------------------------------------- H = V + V^*, scaled, double-float
     for (int idx = tid; idx < m * m; idx += kGramThreads) {
       const int i = idx % m, j = idx / m;
@@ -381,7 +444,14 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       Hout[i + (int64_t)j * mp] = make_float4(hr.x, hr.y, hi.x, hi.y);
     }
     __syncthreads();  // Vs (over the slice buffers) read before the next pair's slices
+#if GP_ON
+    gp[9] += clock64() - ga;
+#endif
   }
+#if GP_ON
+  if (tid == 0)
+    for (int i = 0; i < 10; ++i) atomicAdd(&g_gprof[i], (unsigned long long)gp[i]);
+#endif
   if (timed_out && tid == 0) atomicOr(st_ptr, kStatusTimeout);
   // a timed-out batch may still be running: one more bounded wait before the
   // tensor memory is released
@@ -415,6 +485,23 @@ bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t 
 }
 
 }  // namespace
+
+void prof_reset_gram() {
+#ifdef DH2_PROFILE
+  unsigned long long z[10] = {};
+  cudaMemcpyToSymbol(g_gprof, z, sizeof(z));
+#endif
+}
+
+bool prof_read_gram(unsigned long long* out10) {
+#ifdef DH2_PROFILE
+  cudaMemcpyFromSymbol(out10, g_gprof, 10 * sizeof(unsigned long long));
+  return true;
+#else
+  (void)out10;
+  return false;
+#endif
+}
 
 bool launch_gram(const GramArgs* args_dev, const uint32_t* codes, int n, int maxm, cudaStream_t st) {
   if (n <= 0) return true;

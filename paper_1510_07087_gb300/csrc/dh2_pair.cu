@@ -617,6 +617,7 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
 #if DH2_PROF_ON
     t_b = clock64();
 #endif
+    DH2_PROF_ADD(0, t_b - t_a);
   } else {
 
   // ---------------------------------------------------------------- 1. LQ
