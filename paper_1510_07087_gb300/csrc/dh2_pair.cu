@@ -387,19 +387,22 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
     dlo[tid] = Hs[tid + tid * P].y;
   }
   __syncthreads();
-  const double tau_s = ldexp(tau, se);
+  // the stopping threshold in the scaled units, as a double-float (the loop
+  // runs on the FP32 pipes only: GB300's FP64 pipe is narrow)
+  const double tau_d = ldexp(tau, se);
+  const Df tau_s{(float)tau_d, (float)(tau_d - (double)(float)tau_d)};
   const float back = ldexpf(1.f, -se / 2);
   K = p;
   E_K = 0.0;
   for (int j = 0; j < p; ++j) {
-    // Schur trace of the unchosen rows and the pivot (largest diagonal, lowest
-    // row on ties); every warp forms the same values
-    double e = 0.0;
+    // Schur trace of the unchosen rows (double-float) and the pivot (largest
+    // diagonal, lowest row on ties); every warp forms the same values
+    Df e{0.f, 0.f};
     float best = -1.f;
     int pv = p;
     for (int r = lane; r < p; r += 32)
       if (pcol[r] < 0) {
-        e += (double)dhi[r] + (double)dlo[r];
+        e = df_add(e, Df{dhi[r], dlo[r]});
         if (dhi[r] > best) {
           best = dhi[r];
           pv = r;
@@ -407,7 +410,7 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
       }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      e += __shfl_xor_sync(0xffffffffu, e, o);
+      e = df_add(e, df_shfl_xor(e, o));
       const float ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, pv, o);
       if (ob > best || (ob == best && oi < pv)) {
@@ -415,11 +418,13 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
         pv = oi;
       }
     }
-    if (e <= tau_s || pv >= p || !(best > 0.f)) {
+    const Df gap = df_add(e, df_neg(tau_s));  // e - tau
+    if (!(gap.hi > 0.f) || pv >= p || !(best > 0.f)) {
       K = j;
       // the Schur diagonal is formed by subtraction: a trace below zero is
       // rounding (|e| at most a few units of 2^-48 of the largest diagonal)
-      E_K = e != e ? e : ldexp(fmax(e, 0.0), -se);
+      const double ed = (double)e.hi + (double)e.lo;
+      E_K = ed != ed ? ed : ldexp(fmax(ed, 0.0), -se);
       break;
     }
     const Df sq = df_sqrt(Df{dhi[pv], dlo[pv]});
