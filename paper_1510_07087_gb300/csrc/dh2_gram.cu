@@ -113,11 +113,13 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sl0 = smem;
   unsigned char* bsl = smem + 3 * Sh::SLBYTES;  // slice 3 times 2^-9, rows [X; Y] (B operand of (3,3))
-  long long* Vs = reinterpret_cast<long long*>(smem);  // after the last MMA: V, 2 mp x mp, row stride mp
+  long long* Vs = reinterpret_cast<long long*>(smem);  // after the last MMA: V, 2 mp x mp, row stride mp + 1
   __shared__ int cgcT[kTableCols];  // column table of the pair: G index of each column
   __shared__ float cwtT[kTableCols]; // and its weight 1/omega_b
   __shared__ float rsc[64];
   __shared__ int rexp[64];
+  __shared__ int64_t sgoff[kGramThreads];  // row scales: per block of F_tc its maxima's offset
+  __shared__ float sgw[kGramThreads];      // and its FP32 weight
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
 
@@ -188,23 +190,32 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     // norms pass: per block of F_tc its row (column basis: column) maxima
     // times the block's FP32 weight -- the same value as the maximum over the
     // weighted entries, since rounding a product with a positive factor is
-    // monotonic.  Two threads per row, each over half of the blocks.
+    // monotonic.  The blocks' offsets and weights are gathered first (one
+    // thread per block), then two threads per row take half of the blocks each.
     {
       const int64_t sg0 = a.seg_begin[side][pid], sg1 = a.seg_begin[side][pid + 1];
       const int i = tid >> 1;
       float mx = 0.f;
       bool bad = false;
-      if (i < m)
-        for (int64_t sg = sg0 + (tid & 1); sg < sg1; sg += 2) {
-          const int b = a.seg_blk[side][sg];
-          const float w = (float)a.invw[b];
+      for (int64_t sb = sg0; sb < sg1; sb += kGramThreads) {
+        const int nb = (int)(sg1 - sb < kGramThreads ? sg1 - sb : kGramThreads);
+        __syncthreads();  // the previous batch of block data has been used
+        if (tid < nb) {
+          const int b = a.seg_blk[side][sb + tid];
           // the block's maxima: rows of t+ first (row basis), then columns of s+ (column basis)
           const int cl = side == 0 ? a.bt[b] : a.bs[b];  // the block's cluster on this side
-          const int64_t off = a.bmax_off[b] + (side == 0 ? 0 : a.csize[a.bt[b]]) + (r0 - a.cstart[cl]) + i;
-          const float v = a.bmax[off] * w;
-          bad = bad || !(v <= FLT_MAX);
-          mx = fmaxf(mx, v);
+          sgoff[tid] = a.bmax_off[b] + (side == 0 ? 0 : a.csize[a.bt[b]]) + (r0 - a.cstart[cl]);
+          sgw[tid] = (float)a.invw[b];
         }
+        __syncthreads();
+        if (i < m)
+#pragma unroll 4
+          for (int k = tid & 1; k < nb; k += 2) {
+            const float v = a.bmax[sgoff[k] + i] * sgw[k];
+            bad = bad || !(v <= FLT_MAX);
+            mx = fmaxf(mx, v);
+          }
+      }
       mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
       bad = __syncthreads_or(bad);
       if (bad) {  // non-finite entries: reported, H of this pair left as zero
@@ -278,6 +289,19 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 #endif
       return r;
     };
+    // operand descriptors of this pair: slices 1-3 (rows 0 and mp) and the
+    // scaled copy of slice 3
+    uint64_t dA0[3], dA1[3], dB0[4], dB1[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const uint32_t base = sbase + (uint32_t)x * Sh::SLBYTES;  // x = 3: the scaled copy follows slice 3
+      dB0[x] = desc_kmajor_sw128(base);
+      dB1[x] = desc_kmajor_sw128(base + (uint32_t)mp * 128u);
+      if (x < 3) {
+        dA0[x] = dB0[x];
+        dA1[x] = dB1[x];
+      }
+    }
     int tb = 0;
     load_table(0);
     C2<float> v[4][8];
@@ -353,7 +377,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         if (tid == 0) {
           tc_fence_after_sync();
           const bool first = j0 == w0;
-          // products (A slice, B slice or the scaled copy, accumulator)
+          // products (A slice, B slice or the scaled copy, accumulator); the
+          // descriptors of the pair's operand tiles are formed once, a K step
+          // adds 32 bytes (2 units of 16) to their start address
           const int pa[6] = {0, 0, 0, 1, 1, 2};
           const int pb_[6] = {0, 1, 2, 1, 2, 3};  // 3 = slice 3 times 2^-9
           const int pacc[6] = {0, 1, 2, 3, 4, 4};
@@ -361,12 +387,11 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           for (int ks = 0; ks < 4; ++ks) {
 #pragma unroll
             for (int x = 0; x < 6; ++x) {
-              const uint32_t abuf = sbase + pa[x] * Sh::SLBYTES + ks * 32;
-              const uint32_t bbuf = (pb_[x] == 3 ? sbase + 3 * Sh::SLBYTES : sbase + pb_[x] * Sh::SLBYTES) + ks * 32;
+              const uint64_t ko = (uint64_t)(2 * ks);
               const uint32_t dt = tbase + (uint32_t)(pacc[x] * NP);
               const bool acc0 = !(first && ks == 0 && x != 5);
-              mma_bf16(dt, desc_kmajor_sw128(abuf), desc_kmajor_sw128(bbuf), idesc, acc0);
-              mma_bf16(dt, desc_kmajor_sw128(abuf + mp * 128), desc_kmajor_sw128(bbuf + mp * 128), idesc, true);
+              mma_bf16(dt, dA0[pa[x]] + ko, dB0[pb_[x]] + ko, idesc, acc0);
+              mma_bf16(dt, dA1[pa[x]] + ko, dB1[pb_[x]] + ko, idesc, true);
             }
           }
           mma_commit(&bar);
@@ -415,7 +440,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
                           (long long)__float2int_rn(p12[i]) * (1LL << 24) +
                           (long long)__float2int_rn(p13[i]) * (1LL << 16) +
                           (long long)__float2int_rn(p22[i]) * (1LL << 15) + (long long)__float2int_rn(plo[i] * 256.f);
-            const int64_t vi = (int64_t)L * mp + j;
+            const int64_t vi = (int64_t)L * (mp + 1) + j;  // padded rows: no shared-memory bank conflicts
             if (Vg) {
               if (w0 > 0) x += Vg[vi];
               if (!last) Vg[vi] = x;
@@ -437,8 +462,9 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     // ---------------------------------------------------------------- H = V + V^*, scaled, double-float
     for (int idx = tid; idx < m * m; idx += kGramThreads) {
       const int i = idx % m, j = idx / m;
-      const long long re = Vs[(int64_t)i * mp + j] + Vs[(int64_t)j * mp + i];
-      const long long im = Vs[(int64_t)(mp + i) * mp + j] - Vs[(int64_t)(mp + j) * mp + i];
+      const int64_t ls = mp + 1;
+      const long long re = Vs[(int64_t)i * ls + j] + Vs[(int64_t)j * ls + i];
+      const long long im = Vs[(int64_t)(mp + i) * ls + j] - Vs[(int64_t)(mp + j) * ls + i];
       const int ex = rexp[i] + rexp[j] - 12 - 32;
       const float2 hr = ll_to_df(re, ex), hi = ll_to_df(im, ex);
       Hout[i + (int64_t)j * mp] = make_float4(hr.x, hr.y, hi.x, hi.y);
@@ -476,6 +502,9 @@ bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t 
     cudaGetLastError();
     return false;
   }
+  // the whole shared-memory carveout: two CTAs of the 256-column classes per SM
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaGetLastError();
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGramThreads, smem);
   per_sm = std::max(1, std::min(per_sm, (int)(512 / Sh::TCOLS)));
