@@ -65,8 +65,25 @@ constexpr int kTableCols = 1024;      // columns of the pair's column table held
 static_assert(kGramWindow % kGramChunk == 0 && kTableCols % kGramChunk == 0, "chunk-aligned windows and tables");
 constexpr uint32_t kWaitPolls = 1u << 23;  // default bound of a wait: about a second of polls
 
-__device__ __forceinline__ uint32_t bf16_bits(float x) {  // x exactly representable
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+// Two floats that bf16 represents exactly (integers of at most 8 significant
+// bits, times powers of two) as two bf16 in one word, the first in the low
+// half: their upper 16 bits, since the lower 16 are zero.
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// x (|x| < 64, an FP32 value) = s1 + 2^-8 s2 + 2^-16 s3 + rest with s1, s2, s3
+// the nearest integers in turn (|s1| <= 64, |s2|, |s3| <= 128): adding and
+// subtracting 1.5 * 2^23 rounds to the nearest integer (ties to even) for
+// |x| < 2^22, and x - s, (x - s) * 256 are exact.  Written with _rn
+// intrinsics so that no step is contracted into a fused multiply-add.
+__device__ __forceinline__ void slice3(float x, float& s1, float& s2, float& s3) {
+  constexpr float M = 12582912.f;  // 1.5 * 2^23
+  s1 = __fsub_rn(__fadd_rn(x, M), M);
+  const float t1 = __fmul_rn(__fsub_rn(x, s1), 256.f);
+  s2 = __fsub_rn(__fadd_rn(t1, M), M);
+  const float t2 = __fmul_rn(__fsub_rn(t1, s2), 256.f);
+  s3 = __fsub_rn(__fadd_rn(t2, M), M);
 }
 
 // byte offset of the 16-byte chunk g of operand row R in a 128-byte-swizzled buffer
@@ -328,35 +345,28 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           uint32_t px[3][4], py[3][4], pn[3][4], pb[2][4];
 #pragma unroll
           for (int k = 0; k < 8; k += 2) {
-            uint32_t sx[3][2], sy[3][2], sb[2][2];
+            float sx[3][2], sy[3][2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int jj = 8 * g + k + h;
-              const float w = (jj < cw ? cwtT[j0 - tb + jj] : 0.f) * sc;
-              const float xr = v[u][k + h].re * w;
-              const float xi = (side == 0 ? v[u][k + h].im : -v[u][k + h].im) * w;
-              // three 8-bit slices of each part (all steps exact in FP32)
-              const float r1 = rintf(xr), t1 = (xr - r1) * 256.f, r2 = rintf(t1), t2 = (t1 - r2) * 256.f,
-                          r3 = rintf(t2);
-              const float i1 = rintf(xi), u1 = (xi - i1) * 256.f, i2 = rintf(u1), u2 = (u1 - i2) * 256.f,
-                          i3 = rintf(u2);
-              sx[0][h] = bf16_bits(r1);
-              sx[1][h] = bf16_bits(r2);
-              sx[2][h] = bf16_bits(r3);
-              sy[0][h] = bf16_bits(i1);
-              sy[1][h] = bf16_bits(i2);
-              sy[2][h] = bf16_bits(i3);
-              sb[0][h] = bf16_bits(r3 * 0.001953125f);  // 2^-9
-              sb[1][h] = bf16_bits(i3 * 0.001953125f);
+              const float w = __fmul_rn(jj < cw ? cwtT[j0 - tb + jj] : 0.f, sc);  // exact: sc is a power of two
+              const float xr = __fmul_rn(v[u][k + h].re, w);
+              const float xi = __fmul_rn(side == 0 ? v[u][k + h].im : -v[u][k + h].im, w);
+              // three 8-bit slices of each part, every step exact in FP32
+              // (|x| < 64: adding and subtracting 1.5 * 2^23 rounds to the
+              // nearest integer, ties to even)
+              slice3(xr, sx[0][h], sx[1][h], sx[2][h]);
+              slice3(xi, sy[0][h], sy[1][h], sy[2][h]);
             }
 #pragma unroll
             for (int s = 0; s < 3; ++s) {
-              px[s][k >> 1] = sx[s][0] | (sx[s][1] << 16);
-              py[s][k >> 1] = sy[s][0] | (sy[s][1] << 16);
+              px[s][k >> 1] = pack_bf16(sx[s][0], sx[s][1]);
+              py[s][k >> 1] = pack_bf16(sy[s][0], sy[s][1]);
               pn[s][k >> 1] = px[s][k >> 1] ^ 0x80008000u;  // -X: sign bits flipped
             }
-            pb[0][k >> 1] = sb[0][0] | (sb[0][1] << 16);
-            pb[1][k >> 1] = sb[1][0] | (sb[1][1] << 16);
+            // slice 3 times 2^-9 (a power of two: still exact in bf16)
+            pb[0][k >> 1] = pack_bf16(__fmul_rn(sx[2][0], 0.001953125f), __fmul_rn(sx[2][1], 0.001953125f));
+            pb[1][k >> 1] = pack_bf16(__fmul_rn(sy[2][0], 0.001953125f), __fmul_rn(sy[2][1], 0.001953125f));
           }
 #pragma unroll
           for (int s = 0; s < 3; ++s) {

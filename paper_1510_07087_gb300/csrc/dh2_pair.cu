@@ -394,41 +394,61 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
   const float back = ldexpf(1.f, -se / 2);
   K = p;
   E_K = 0.0;
+  __shared__ int sh_pv;
+  __shared__ float sh_piv[4];  // sqrt(d_pv) and 1/sqrt(d_pv), double-float
+  __shared__ double sh_e;
   for (int j = 0; j < p; ++j) {
-    // Schur trace of the unchosen rows (double-float) and the pivot (largest
-    // diagonal, lowest row on ties); every warp forms the same values
-    Df e{0.f, 0.f};
-    float best = -1.f;
-    int pv = p;
-    for (int r = lane; r < p; r += 32)
-      if (pcol[r] < 0) {
-        e = df_add(e, Df{dhi[r], dlo[r]});
-        if (dhi[r] > best) {
-          best = dhi[r];
-          pv = r;
+    // warp 0: Schur trace of the unchosen rows (double-float), the pivot
+    // (largest diagonal, lowest row on ties) and its scalars; -1 = stop
+    if ((tid >> 5) == 0) {
+      Df e{0.f, 0.f};
+      float best = -1.f;
+      int pv = p;
+      for (int r = lane; r < p; r += 32)
+        if (pcol[r] < 0) {
+          e = df_add(e, Df{dhi[r], dlo[r]});
+          if (dhi[r] > best) {
+            best = dhi[r];
+            pv = r;
+          }
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        e = df_add(e, df_shfl_xor(e, o));
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, pv, o);
+        if (ob > best || (ob == best && oi < pv)) {
+          best = ob;
+          pv = oi;
         }
       }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      e = df_add(e, df_shfl_xor(e, o));
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, pv, o);
-      if (ob > best || (ob == best && oi < pv)) {
-        best = ob;
-        pv = oi;
+      const Df gap = df_add(e, df_neg(tau_s));  // e - tau
+      const bool stop = !(gap.hi > 0.f) || pv >= p || !(best > 0.f);
+      if (lane == 0) {
+        sh_pv = stop ? -1 : pv;
+        sh_e = (double)e.hi + (double)e.lo;
+        if (!stop) {
+          const Df sq = df_sqrt(Df{dhi[pv], dlo[pv]});
+          const Df inv = df_recip(sq);
+          sh_piv[0] = sq.hi;
+          sh_piv[1] = sq.lo;
+          sh_piv[2] = inv.hi;
+          sh_piv[3] = inv.lo;
+        }
       }
     }
-    const Df gap = df_add(e, df_neg(tau_s));  // e - tau
-    if (!(gap.hi > 0.f) || pv >= p || !(best > 0.f)) {
+    __syncthreads();
+    const int pv = sh_pv;
+    if (pv < 0) {
       K = j;
       // the Schur diagonal is formed by subtraction: a trace below zero is
       // rounding (|e| at most a few units of 2^-48 of the largest diagonal)
-      const double ed = (double)e.hi + (double)e.lo;
+      const double ed = sh_e;
       E_K = ed != ed ? ed : ldexp(fmax(ed, 0.0), -se);
       break;
     }
-    const Df sq = df_sqrt(Df{dhi[pv], dlo[pv]});
-    const Df inv = df_recip(sq);
+    const Df sq{sh_piv[0], sh_piv[1]};
+    const Df inv{sh_piv[2], sh_piv[3]};
     // column j: l_r = (H[r][pv] - sum_{i<j} L[r][i] conj(L[pv][i])) / sqrt(d_pv)
     const bool act = live && row != pv && pcol[row] < 0;
     Df sre{0.f, 0.f}, sim{0.f, 0.f};
