@@ -401,3 +401,130 @@ def test_planted_mistake_breaks_pythagoras(medium, monkeypatch):
     S = O.project(tr, G, V, B)
     # the column basis now approximates the wrong matrix: the global bound fails
     assert O.error_fro(tr, G, V, B, S) > cp.eps
+
+
+# ---------------------------------------------------------------- split rule (Def. 1), by hand
+
+def _son_sets(tr, t):
+    return [sorted(tr.perm[tr.start[s]:tr.start[s] + tr.size[s]].tolist()) for s in tr.sons[t]]
+
+
+def test_split_rule_midpoint_of_longest_side_by_hand():
+    """Geometrically regular subdivision: halve the bounding box across its longest
+    side; a point on the cutting plane goes to the first son.  The point set is
+    chosen so that a median split, another axis or a strict '<' all differ."""
+    P = np.array([
+        [3.0, 0.0, 0.0],   # 0
+        [0.0, 1.0, 0.0],   # 1
+        [2.0, 0.0, 1.0],   # 2: on the plane x = 2 of the root's box [0,4]x[0,1]x[0,1]
+        [4.0, 1.0, 1.0],   # 3
+        [0.5, 0.0, 0.0],   # 4
+        [1.5, 1.0, 0.0],   # 5
+        [3.5, 0.0, 1.0],   # 6
+        [1.0, 0.2, 0.7],   # 7: on the plane x = 1 of the first son's box [0,2]x[0,1]x[0,1]
+    ])
+    tr = O.build_tree(P, O.TreeParams(leaf_size=4, kappa=0.0))
+    assert _son_sets(tr, 0) == [[1, 2, 4, 5, 7], [0, 3, 6]]
+    s1, s2 = tr.sons[0]
+    assert tr.sons[s2] == []                      # 3 points: a leaf
+    assert _son_sets(tr, s1) == [[1, 4, 7], [2, 5]]
+    assert tr.level[tr.sons[s1][0]] == 2 and tr.depth == 2
+    # boxes are the points' bounding boxes, diameters their diagonals
+    assert tr.lo[s1] == [0.0, 0.0, 0.0] and tr.hi[s1] == [2.0, 1.0, 1.0]
+    assert tr.diam[s2] == pytest.approx(math.sqrt(1.0 + 1.0 + 1.0))
+
+
+def test_split_rule_lowest_axis_on_ties_by_hand():
+    """Equal extents along x and y: the cut is across x (the first axis)."""
+    P = np.array([[0.0, 0.0, 0.0], [2.0, 2.0, 1.0], [0.5, 1.9, 0.0], [1.5, 0.1, 0.0]])
+    tr = O.build_tree(P, O.TreeParams(leaf_size=2, kappa=0.0))
+    assert _son_sets(tr, 0) == [[0, 2], [1, 3]]   # across y it would be [[0, 3], [1, 2]]
+
+
+def test_single_point_clusters_and_duplicates_stop():
+    """Coincident points cannot be separated by a cut: the cluster stays a leaf."""
+    P = np.zeros((5, 3))
+    tr = O.build_tree(P, O.TreeParams(leaf_size=2, kappa=0.0))
+    assert tr.nclusters() == 1 and tr.size[0] == 5
+
+
+# ---------------------------------------------------------------- weights (Remark "Error control")
+
+def _single_block_leaf_pairs(tr, B):
+    """Leaf pairs (t, c) whose F_tc holds exactly one block, that block's row cluster being t."""
+    out = []
+    for t, cmap in B.F.items():
+        if not tr.is_leaf(t):
+            continue
+        for c, blocks in cmap.items():
+            if len(blocks) == 1:
+                bt, bs, _, _ = tr.blocks[blocks[0]]
+                if (bt if B.side == "row" else bs) == t:
+                    out.append((t, c, blocks[0]))
+    return out
+
+
+@pytest.mark.parametrize("side", ["row", "col"])
+def test_weights_make_leaf_truncation_block_relative(medium, side):
+    """With omega_b = |G_b| zeta^-level(t) and eps_r ~ zeta^level(r), a leaf pair whose
+    only block is b = (t, s) is truncated block-relatively and level-free: its rank is
+    the least k with sum_{i>k} sigma_i(G_b)^2 <= eps_hat^2 |G_b|^2, sigma_i taken here
+    from G_b itself.  A wrong norm power or exponent sign changes these ranks."""
+    tr, G, cp = medium["tr"], medium["G"], medium["cp"]
+    B = medium["V"] if side == "row" else medium["W"]
+    eh = O.eps_hat(cp)
+    pairs = _single_block_leaf_pairs(tr, B)
+    checked = 0
+    for t, c, b in pairs:
+        bt, bs, _, _ = tr.blocks[b]
+        Gb = G[tr.start[bt]:tr.start[bt] + tr.size[bt], tr.start[bs]:tr.start[bs] + tr.size[bs]]
+        if side == "col":
+            Gb = Gb.conj().T
+        sig = scipy.linalg.svdvals(Gb)
+        thr = (eh * np.linalg.norm(Gb)) ** 2
+        tails = np.array([np.sum(sig[k:] ** 2) for k in range(len(sig) + 1)])
+        k = int(np.argmax(tails <= thr))
+        if abs(tails[k] - thr) < 1e-6 * thr or (k > 0 and abs(tails[k - 1] - thr) < 1e-6 * thr):
+            continue  # a tie at the threshold: either rank is right
+        assert B.rank[(t, c)] == k, (t, c, B.rank[(t, c)], k)
+        checked += 1
+    assert checked >= 10, (len(pairs), checked)
+
+
+def test_block_scaling_by_powers_of_two_leaves_bases_unchanged(medium):
+    """omega_b proportional to |G_b|: scaling one admissible block by 2^j leaves every
+    G^omega_tc, hence every rank and basis, bit-identical."""
+    tr, G, cp = medium["tr"], medium["G"], medium["cp"]
+    rng = np.random.default_rng(11)
+    adm = [b for b, (t, s, a, c) in enumerate(tr.blocks) if a]
+    G2 = G.copy()
+    for b, j in zip(rng.choice(adm, 6, replace=False), (3, -5, 7, 1, -2, 9)):
+        t, s, _, _ = tr.blocks[b]
+        G2[tr.start[t]:tr.start[t] + tr.size[t], tr.start[s]:tr.start[s] + tr.size[s]] *= 2.0 ** j
+    for side, ref in (("row", medium["V"]), ("col", medium["W"])):
+        B = O.compress(tr, G2, cp, side)
+        assert B.rank == ref.rank
+        for key, Q in ref.Q.items():
+            assert np.array_equal(B.Q[key], Q)
+        for key, E in ref.E.items():
+            assert np.array_equal(B.E[key], E)
+
+
+# ---------------------------------------------------------------- storage of the transfer matrices
+
+def test_transfer_matrix_shapes_and_storage(medium):
+    """Def. of the directional cluster basis: E_{t'c} maps the rank k_tc of the father
+    to the rank k_{t'c'} of the son t' at c' = sd(c); storage counts those entries."""
+    tr, V, W, S = medium["tr"], medium["V"], medium["W"], medium["S"]
+    for B, key in ((V, "E_V"), (W, "E_W")):
+        total = 0
+        for t in range(tr.nclusters()):
+            if not tr.sons[t]:
+                continue
+            for c in B.F[t]:
+                cs = int(tr.sd[tr.level[t]][c])
+                for son in tr.sons[t]:
+                    assert B.E[(son, c)].shape == (B.rank[(son, cs)], B.rank[(t, c)])
+                    total += B.rank[(son, cs)] * B.rank[(t, c)]
+        assert O.storage(tr, V, W, S)[key] == total
+        assert total > 0
