@@ -1,10 +1,15 @@
 """Benchmark: directional H^2 compression of a dense Helmholtz collocation matrix.
 
 Workload (default): n = 32768 Fibonacci-sphere points, kappa = 32, leaf 64,
-eps = 1e-4, dense complex64 G (8 GiB) resident in HBM, FP32 mode; the reported
+eps = 1e-4, dense complex64 G (8 GiB) resident in HBM, mixed mode (leaf Gram
+matrices from exact bf16 slice products on the tensor cores); the reported
 relative error is measured against the complex128 matrix.  One step = one call
 of dh2_compress: block norms + nearfield copy, the leaf factorisations of both
 bases, the non-leaf level steps, the basis expansion and the projection.
+
+Beside the headline the line carries (unless --skip-secondary) the plain FP64
+GPU form and the FP32 form on the same problem with the rank deviations from
+them, and the paper's parameter set (eta1 = 20, eta2 = 5) on the same points.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead on
 a bounded sample of the same workload (rank 0 only).
@@ -41,11 +46,11 @@ MODE_LABEL = {"fp32": "FP32 complex64", "fp64": "FP64 complex128",
 # 2 flops per FMA x 2.07 GHz maximum SM clock.
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes (read + write) of the leaf launches of the pair kernel (one per
-# leaf-size class, together) at n=32768, kappa=32, leaf 64, FP32, from a
-# 1-pass ncu capture (profiles/); valid only for the kernel source it was
-# measured on (sha1 of csrc/dh2_pair.cu).
-PAIR_TRAFFIC = {"sha1": "244416117d122cbc1a919c4c36efb296508a3320", "bytes": 5.839e9 + 0.308e9}
+# DRAM bytes (read + write) of the leaf launches of a kernel (all size classes
+# together) at n=32768, kappa=32, leaf 64, from an ncu capture summarised under
+# profiles/; valid only for the kernel sources it was measured on (sha1 of
+# csrc/dh2_gram.cu + csrc/dh2_pair.cu).
+KERNEL_TRAFFIC = {}
 
 
 def _peaks():
@@ -314,6 +319,60 @@ def oracle_baseline(args, budget_s: float, seed: int = 0):
 
 # --------------------------------------------------------------------------- GPU arm
 
+def _alg_flops(T, ranks):
+    """Algorithmic flops of the leaf launches per basis pair (real flops, 8 per complex MAC):
+    factor 4 m^2 N, R = Q^* A 8 k m N, summed with the computed ranks over both bases."""
+    size = T.clusters()["size"].astype(np.float64)
+    fac = rq = 0.0
+    for sd in (0, 1):
+        pr = T.pairs(sd)
+        lf = pr["leaf"].astype(bool)
+        m = size[pr["cluster"]][lf]
+        N = pr["ncols"][lf].astype(np.float64)
+        k = ranks[sd][lf].astype(np.float64)
+        fac += float(np.sum(4.0 * m * m * N))
+        rq += float(np.sum(8.0 * k * m * N))
+    return fac, rq
+
+
+def _timed_compress(D, T, G, mode, args, steps, warmup, clk=None):
+    """Mean ms per dh2_compress over `steps` calls (CUDA events on the launching stream) and the
+    per-phase and leaf-split means from the library's own events; returns the last matrix too."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        M = D.dh2_compress(T, G, eps=args.eps, mode=mode, nearfield=args.nearfield)
+        del M
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phases = np.zeros(6)
+    split = np.zeros(2)
+    if clk is not None:
+        clk.__enter__()
+    try:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            M = D.dh2_compress(T, G, eps=args.eps, mode=mode, nearfield=args.nearfield)
+            phases += M.phase_ms()
+            split += M.leaf_split_ms()
+            del M
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    finally:
+        if clk is not None:
+            clk.__exit__(None, None, None)
+    M = D.dh2_compress(T, G, eps=args.eps, mode=mode, nearfield=args.nearfield)
+    return ev0.elapsed_time(ev1) / steps, phases / steps, split / steps, M
+
+
+def _rank_hist(a, b):
+    d = np.asarray(a, dtype=np.int64) - np.asarray(b, dtype=np.int64)
+    vals, cnt = np.unique(d, return_counts=True)
+    return {str(int(v)): int(c) for v, c in zip(vals, cnt)}
+
+
 def run_gpu(args):
     import torch
 
@@ -330,34 +389,14 @@ def run_gpu(args):
     P = pts[perm]
     Nrm = nrm[perm] if nrm is not None else None
     cdt = torch.complex128 if args.mode == "fp64" else torch.complex64
-    mode = {"fp32": D.MODE_FP32, "fp64": D.MODE_FP64, "mixed": D.MODE_MIXED_BF16X3}[args.mode]
+    mode = MODE_CODE(D)[args.mode]
     Gd = workload_matrix(args, P, Nrm, h, cdt, dev)
     stream = torch.cuda.current_stream()
     elem = 16 if args.mode == "fp64" else 8
     in_bytes = elem * args.n * args.n
 
-    def step():
-        M = D.dh2_compress(T, Gd, eps=args.eps, mode=mode, nearfield=args.nearfield)
-        return M
-
-    for _ in range(args.warmup):
-        M = step()
-        del M
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    phases = np.zeros(6)
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            M = step()
-            phases += M.phase_ms()
-            del M
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    phases /= args.steps
-    M = step()
+    clk = ClockSampler(torch.cuda.current_device())
+    ms, phases, split, M = _timed_compress(D, T, Gd, mode, args, args.steps, args.warmup, clk)
     ranks = [M.ranks(0), M.ranks(1)]
     storage = M.storage()
     # matrix-vector product with the compressed matrix (Section 4), one right-hand side
@@ -375,9 +414,29 @@ def run_gpu(args):
     matvec_ms = m0.elapsed_time(m1) / 10
     # error against the FP64 matrix (complex128, built the same way)
     rel_err = None
+    secondary = {}
     if args.mode != "fp64" and not args.skip_error:
         G128 = workload_matrix(args, P, Nrm, h, torch.complex128, dev)
         rel_err = D.dh2_error(M, G128)
+        if not args.skip_secondary:
+            # the plain FP64 GPU form on the same problem (complex128 G), and the rank deviations of
+            # this run's ranks from it (the FP64 form's ranks are the oracle's outside ties)
+            ms64, ph64, _, M64 = _timed_compress(D, T, G128, D.MODE_FP64, args, 2, 1)
+            r64 = [M64.ranks(0), M64.ranks(1)]
+            secondary["fp64_form"] = {
+                "ms_per_step": ms64, "value": 16 * args.n * args.n / (ms64 * 1e-3) / 1e9, "unit": "GB/s",
+                "input": "complex128 G (16 B per entry)", "rel_err_vs_fp64": D.dh2_error(M64, G128),
+                "phases_ms": [float(v) for v in ph64], "steps": 2, "warmup": 1,
+                "speedup_of_headline": ms64 / ms}
+            secondary["rank_deviation_vs_fp64_form"] = {
+                "row": _rank_hist(ranks[0], r64[0]), "col": _rank_hist(ranks[1], r64[1])}
+            del M64
+            if args.mode == "mixed":
+                ms32, _, _, M32 = _timed_compress(D, T, Gd, D.MODE_FP32, args, 2, 1)
+                secondary["fp32_form"] = {"ms_per_step": ms32, "rel_err_vs_fp64": D.dh2_error(M32, G128)}
+                secondary["rank_deviation_vs_fp32_form"] = {
+                    "row": _rank_hist(ranks[0], M32.ranks(0)), "col": _rank_hist(ranks[1], M32.ranks(1))}
+                del M32
         del G128
     elif not args.skip_error:
         rel_err = D.dh2_error(M, Gd)
@@ -438,45 +497,77 @@ def run_gpu(args):
                # expansion, projection]
                "phases_ms": last_phases.get("host"), "copy_then_compress": seq}
         del Gh, Gdev
+    if not args.skip_secondary and args.kernel == "slp" and args.eta1 != 20.0:
+        # the paper's parameter set (Section 7: eta1 = 20, eta2 = 5) on the same points: many coarse
+        # admissible blocks, long column lists per pair
+        del Gd
+        Tp = D.dh2_tree_build(pts, args.leaf, args.kappa, 20.0, 5.0)
+        Pp = pts[Tp.perm()]
+        Gp = workload_matrix(args, Pp, None, h, cdt, dev)
+        msp, php, spp, Mp = _timed_compress(D, Tp, Gp, mode, args, 3, 2)
+        rp = [Mp.ranks(0), Mp.ranks(1)]
+        errp = None
+        if not args.skip_error:
+            del Gp
+            Gp128 = workload_matrix(args, Pp, None, h, torch.complex128, dev)
+            errp = D.dh2_error(Mp, Gp128)
+            del Gp128
+        secondary["p_paper"] = {
+            "eta1": 20.0, "eta2": 5.0, "ms_per_step": msp, "value": in_bytes / (msp * 1e-3) / 1e9, "unit": "GB/s",
+            "adm_fraction": Tp.stats().adm_fraction, "rel_err_vs_fp64": errp,
+            "k_max": int(max(rp[0].max(initial=0), rp[1].max(initial=0))),
+            "phases_ms": [float(v) for v in php], "leaf_split_ms": [float(v) for v in spp], "steps": 3, "warmup": 2,
+            "step_roofline_frac": in_bytes / (_peaks()[0]["hbm_gbs"] * 1e9) * 1e3 / msp}
+        del Mp
     peaks, src = _peaks()
     adm_bytes = elem * st.adm_fraction * args.n * args.n
     leaf_ms = float(phases[1])
     rq_ms = float(phases[2])
-    # algorithmic flops of the leaf launches (per pair and basis, real flops):
-    # factor 4 m^2 N (pair_kernel), R = Q^* A 8 k m N (rq_kernel), summed with
-    # the computed ranks; bytes: both bases read every admissible entry once
-    size = T.clusters()["size"].astype(np.float64)
-    flops = 0.0
-    rq_flops = 0.0
-    for sd in (0, 1):
-        pr = T.pairs(sd)
-        lf = pr["leaf"].astype(bool)
-        m = size[pr["cluster"]][lf]
-        N = pr["ncols"][lf].astype(np.float64)
-        k = ranks[sd][lf].astype(np.float64)
-        flops += float(np.sum(4.0 * m * m * N))
-        rq_flops += float(np.sum(8.0 * k * m * N))
-    leaf_bytes = 2.0 * adm_bytes
-    import hashlib
-    src_sha = hashlib.sha1(open(os.path.join(ROOT, "paper_1510_07087_gb300", "csrc", "dh2_pair.cu"), "rb")
-                           .read()).hexdigest()
-    traffic = (PAIR_TRAFFIC["bytes"] if (src_sha == PAIR_TRAFFIC["sha1"] and args.n == 32768 and args.leaf == 64
-                                         and args.mode == "fp32") else None)
-    achieved = flops / (leaf_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "pair_kernel (leaf launch: LQ, pivoted truncation, Jacobi, Q)",
-            "achieved": achieved, "peak": FP32_ALU_TFLOPS, "peak_source": "derived (152 SM x 128 FP32 x 2 x 2.07 GHz)",
-            "unit": "TFLOP/s", "frac": achieved / FP32_ALU_TFLOPS, "traffic": traffic,
-            "alg_flops_per_launch": flops, "alg_bytes_per_launch": leaf_bytes,
-            "hbm_view": {"achieved_gbs": leaf_bytes / (leaf_ms * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
-                         "frac": leaf_bytes / (leaf_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": src},
-            "rq_kernel": {"ms": rq_ms, "alg_flops": rq_flops, "alg_bytes": leaf_bytes,
-                          "achieved_gbs": leaf_bytes / (rq_ms * 1e-3) / 1e9,
-                          "hbm_frac": leaf_bytes / (rq_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                          "achieved_tflops": rq_flops / (rq_ms * 1e-3) / 1e12,
-                          "alu_frac": rq_flops / (rq_ms * 1e-3) / 1e12 / FP32_ALU_TFLOPS}}
-    t_roof_ms = in_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
-    step_roof = {"bound": "hbm", "t_roof_ms": t_roof_ms, "frac": t_roof_ms / ms,
-                 "note": "one read of all of G at the measured copy bandwidth, against the whole step"}
+    fac_flops, rq_flops = _alg_flops(T, ranks)
+    leaf_bytes = 2.0 * adm_bytes  # each basis reads every admissible entry once
+    out_bytes = elem * (storage["V"] + storage["W"] + storage["E_V"] + storage["E_W"] + storage["S"])
+    # the step roofline of the method: every entry of G read once, the representation written once;
+    # the contractions at the measured dense bf16 tensor rate
+    t_bytes = (in_bytes + out_bytes) / (peaks["hbm_gbs"] * 1e9) * 1e3
+    t_flops = (fac_flops + rq_flops) / (peaks["bf16_tflops"] * 1e12) * 1e3
+    t_roof_ms = max(t_bytes, t_flops)
+    step_roof = {"bound": "hbm" if t_bytes >= t_flops else "tensor", "t_roof_ms": t_roof_ms, "frac": t_roof_ms / ms,
+                 "achieved": (in_bytes + out_bytes) / (ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "peak_source": src, "alg_bytes": in_bytes + out_bytes, "t_hbm_ms": t_bytes,
+                 "alg_flops": fac_flops + rq_flops, "t_tensor_ms": t_flops,
+                 "note": "whole compression step: G read once plus V, W, E, S written once, at the measured copy "
+                         "bandwidth; against max(that, leaf flops at the measured bf16 rate)"}
+    mixed = args.mode == "mixed"
+    gram_ms, fac_ms = float(split[0]), float(split[1])
+    src_sha = _kernel_sha()
+    if mixed:
+        kern_ms = gram_ms
+        roof = {"bound": "hbm", "kernel": "gram_kernel (leaf launches: tcgen05 bf16x3 sliced Gram of G^omega_tc, "
+                                          "both bases)",
+                "achieved": leaf_bytes / (kern_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": leaf_bytes / (kern_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": src,
+                "traffic": _traffic("gram", src_sha, args), "alg_bytes_per_launch": leaf_bytes,
+                "launch_ms": kern_ms,
+                "tensor_view": {"alg_flops": fac_flops, "achieved_tflops": fac_flops / (kern_ms * 1e-3) / 1e12,
+                                "peak_tflops": peaks["bf16_tflops"],
+                                "frac": fac_flops / (kern_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                                "note": "4 m^2 N per pair; the bf16 slice products are not counted"},
+                "factor_kernel": {"kernel": "pair_kernel<...,GRAM> (pivoted Cholesky, Jacobi, truncation, Q)",
+                                  "ms": fac_ms}}
+    else:
+        kern_ms = leaf_ms
+        roof = {"bound": "hbm", "kernel": "pair_kernel (leaf launches: LQ, pivoted truncation, Jacobi, Q)",
+                "achieved": leaf_bytes / (kern_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": leaf_bytes / (kern_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": src,
+                "traffic": _traffic("pair", src_sha, args), "alg_bytes_per_launch": leaf_bytes,
+                "launch_ms": kern_ms}
+    roof["alu_view"] = {"alg_flops": fac_flops, "achieved_tflops": fac_flops / (leaf_ms * 1e-3) / 1e12,
+                        "peak_tflops": FP32_ALU_TFLOPS, "frac": fac_flops / (leaf_ms * 1e-3) / 1e12 / FP32_ALU_TFLOPS,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz", "scope": "leaf phase"}
+    roof["rq_kernel"] = {"ms": rq_ms, "alg_flops": rq_flops, "alg_bytes": leaf_bytes,
+                         "achieved_gbs": leaf_bytes / (rq_ms * 1e-3) / 1e9,
+                         "hbm_frac": leaf_bytes / (rq_ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "achieved_tflops": rq_flops / (rq_ms * 1e-3) / 1e12}
     launches = M.launch_count()  # kernels the library launched for the last compression
     line = {
         "metric": "compression wall time & input GB/s at n=32768, kappa=32, eps=1e-4; rel. error vs FP64",
@@ -485,15 +576,197 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": {"fp32": "c64/f32 (f64 tail sums)", "fp64": "c128/f64",
                                        "mixed": "c64/bf16x3-tc/f32 (f64 tail sums)"}[args.mode],
         "data": "synthetic (Fibonacci sphere, Helmholtz collocation)", "config": workload(args),
-        "rel_err_vs_fp64": rel_err, "phases_ms": {k: float(v) for k, v in zip(
+        "rel_err_vs_fp64": rel_err, "step_roofline": step_roof, "roofline": roof,
+        "phases_ms": {k: float(v) for k, v in zip(
             ["norms_nearfield", "leaf_factors", "leaf_R", "level_steps", "expansion", "projection"], phases)},
+        "leaf_split_ms": {"gram": gram_ms, "factor": fac_ms} if mixed else None,
         "k_max": int(max(ranks[0].max(initial=0), ranks[1].max(initial=0))),
         "matvec_ms": matvec_ms,
         "mem_per_n_kib_c128": storage["total"] * 16 / 1024 / args.n,
-        "adm_fraction": st.adm_fraction, "roofline": roof, "step_roofline": step_roof, "e2e": e2e,
+        "adm_fraction": st.adm_fraction, "e2e": e2e, "secondary": secondary or None,
         "clocks": clk.summary(), "gpu_launches": launches * args.steps, "launches_per_step": launches,
     }
     return line
+
+
+def _storage_ratios(M, n, kappa, depth):
+    """Stored entries against n k_max and n k_max + kappa^2 k_max^2 p (theorem on the complexity of
+    DH^2 storage, Section 5: O(nk + kappa^2 k^2 log n)), with and without the nearfield."""
+    st = M.storage()
+    k_max = int(max(M.ranks(0).max(initial=0), M.ranks(1).max(initial=0)))
+    far = st["total"] - st["near"]
+    nk = max(1.0, float(n) * k_max)
+    bound = nk + kappa * kappa * k_max * k_max * max(1, depth)
+    return {"entries_total": st["total"], "entries_far": far, "entries_near": st["near"], "k_max": k_max,
+            "total_over_nk": st["total"] / nk, "far_over_nk": far / nk, "total_over_bound": st["total"] / bound,
+            "far_over_bound": far / bound, "mem_per_n_kib_c128": st["total"] * 16 / 1024 / n}
+
+
+def sweep_cube(args):
+    """The high-frequency sweep: unit-cube surface, uniform random points, n in {4096, 16384, 65536},
+    kappa = 0.2 sqrt(n), eps in {1e-3, 1e-5}, leaf 64, both parameter sets.  n <= 16384: dense G in the
+    mixed mode (complex64) and the FP64 mode (complex128); every n: matrix-free in FP32.  One JSON
+    line per case."""
+    import torch
+
+    import paper_1510_07087_gb300 as D
+    from synth import mean_nn_distance, random_cube_surface
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks, src = _peaks()
+    for n in (4096, 16384, 65536):
+        pts = random_cube_surface(n)
+        h = mean_nn_distance(pts)
+        kappa = 0.2 * math.sqrt(n)
+        diag = 1.0 / (4.0 * math.pi * h)
+        for eta1, eta2, pname in ((2.0 * math.sqrt(2.0), 1.0, "P-lit"), (20.0, 5.0, "P-paper")):
+            T = D.dh2_tree_build(pts, 64, kappa, eta1, eta2)
+            st = T.stats()
+            P = pts[T.perm()]
+            forms = []
+            if n <= 16384:
+                forms += [("mixed", D.MODE_MIXED_BF16X3, torch.complex64), ("fp64", D.MODE_FP64, torch.complex128)]
+            forms.append(("fp32-matrix-free", D.MODE_FP32, None))
+            G128 = None
+            if n <= 16384:
+                from synth.inputs import helmholtz_matrix_torch
+                G128 = helmholtz_matrix_torch(P, kappa, h, torch.complex128, dev).t()
+            for eps in (1e-3, 1e-5):
+                for name, mode, cdt in forms:
+                    sub = argparse.Namespace(**vars(args))
+                    sub.eps, sub.n = eps, n
+                    if cdt is not None:
+                        G = G128 if cdt == torch.complex128 else G128.to(torch.complex64)
+                        ms, ph, _, M = _timed_compress(D, T, G, mode, sub, 3, 2)
+                        err = D.dh2_error(M, G128)
+                        elem = 16 if cdt == torch.complex128 else 8
+                    else:
+                        def one():
+                            return D.dh2_compress_kernel(T, pts, kappa, diag, eps=eps, mode=mode)
+                        for _ in range(2):
+                            del_ = one()
+                            del del_
+                        torch.cuda.synchronize()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(torch.cuda.current_stream())
+                        for _ in range(3):
+                            M = one()
+                            ph = M.phase_ms()
+                            del M
+                        e1.record(torch.cuda.current_stream())
+                        torch.cuda.synchronize()
+                        ms = e0.elapsed_time(e1) / 3
+                        M = one()
+                        err = D.dh2_error(M, None, which=D.ERR_FRO_CLOSED if n > 16384 else D.ERR_FRO_BLOCKWISE)
+                        elem = 8
+                    line = {"sweep": "unit-cube high-frequency", "n": n, "kappa": kappa, "eps": eps, "params": pname,
+                            "eta1": eta1, "eta2": eta2, "form": name, "ms_per_step": ms,
+                            "input_gbs": elem * n * n / (ms * 1e-3) / 1e9 if cdt is not None else None,
+                            "entries_per_s": n * n / (ms * 1e-3), "rel_err_vs_fp64": err,
+                            "error_measure": "closed form" if (cdt is None and n > 16384) else "blockwise",
+                            "adm_fraction": st.adm_fraction, "depth": st.depth,
+                            "phases_ms": [float(v) for v in ph],
+                            "storage": _storage_ratios(M, n, kappa, st.depth),
+                            "step_roofline_frac": (elem * n * n / (peaks["hbm_gbs"] * 1e9) * 1e3 / ms
+                                                   if cdt is not None else None)}
+                    del M
+                    print(json.dumps(line), flush=True)
+            del G128
+
+
+def _surface_problem(i):
+    """Problem i of the 48-surface batch: 16 each of sphere, 2:1:1 ellipsoid and unit-cube surface,
+    uniform random points with seed 151007087 + i, n ~ U{1024..12288}, kappa = U[8, 40] / diam."""
+    from synth import random_cube_surface, random_ellipsoid, random_sphere
+
+    seed = 151007087 + i
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1024, 12289))
+    kind = ("sphere", "ellipsoid", "cube")[i // 16]
+    diam = {"sphere": 2.0, "ellipsoid": 2.0, "cube": math.sqrt(3.0)}[kind]
+    kappa = float(rng.uniform(8.0, 40.0)) / diam
+    pts = {"sphere": random_sphere, "ellipsoid": random_ellipsoid, "cube": random_cube_surface}[kind](n, seed=seed)
+    return kind, n, kappa, pts
+
+
+def sweep_surfaces(args):
+    """48 independent surfaces compressed by one dh2_compress_batched call (one launch per phase over
+    all problems) against the same problems compressed one after the other; mixed mode, complex64."""
+    import torch
+
+    import paper_1510_07087_gb300 as D
+    from synth import mean_nn_distance
+    from synth.inputs import helmholtz_matrix_torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    trees, Gs, meta = [], [], []
+    for i in range(48):
+        kind, n, kappa, pts = _surface_problem(i)
+        T = D.dh2_tree_build(pts, 64, kappa)
+        h = mean_nn_distance(pts)
+        G = helmholtz_matrix_torch(pts[T.perm()], kappa, h, torch.complex64, dev).t()
+        trees.append(T)
+        Gs.append(G)
+        meta.append((kind, n, kappa, T.stats().adm_fraction))
+    total_bytes = sum(8 * n * n for _, n, _, _ in meta)
+    mode = D.MODE_MIXED_BF16X3
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            r = fn()
+            del r
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            r = fn()
+            del r
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    batched_ms = timed(lambda: D.dh2_compress_batched(trees, Gs, eps=args.eps, mode=mode), args.steps, args.warmup)
+    seq_ms = timed(lambda: [D.dh2_compress(T, G, eps=args.eps, mode=mode) for T, G in zip(trees, Gs)],
+                   max(1, args.steps // 2), 1)
+    Ms = D.dh2_compress_batched(trees, Gs, eps=args.eps, mode=mode)
+    errs = [D.dh2_error(M, G, which=D.ERR_FRO_CLOSED) for M, G in zip(Ms, Gs)]
+    launches = Ms[0].launch_count()
+    line = {"sweep": "48 surfaces, one batched call", "problems": 48, "mode": "mixed", "eps": args.eps,
+            "bytes": total_bytes, "batched_ms": batched_ms, "batched_gbs": total_bytes / (batched_ms * 1e-3) / 1e9,
+            "sequential_ms": seq_ms, "sequential_gbs": total_bytes / (seq_ms * 1e-3) / 1e9,
+            "launches_batched": launches, "max_rel_err_closed_form_vs_c64": max(errs),
+            "n_range": [min(m[1] for m in meta), max(m[1] for m in meta)],
+            "adm_fraction_range": [min(m[3] for m in meta), max(m[3] for m in meta)],
+            "steps": args.steps, "warmup": args.warmup}
+    print(json.dumps(line), flush=True)
+
+
+def MODE_CODE(D):
+    return {"fp32": D.MODE_FP32, "fp64": D.MODE_FP64, "mixed": D.MODE_MIXED_BF16X3}
+
+
+def _kernel_sha():
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in ("dh2_gram.cu", "dh2_pair.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1510_07087_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def _traffic(kernel, sha, args):
+    """DRAM bytes (read + write) of the kernel's leaf launches from an ncu capture of this exact kernel
+    source (KERNEL_TRAFFIC), scaled to the workload's admissible entries; None when the source has
+    changed since the capture or the workload is another one."""
+    rec = KERNEL_TRAFFIC.get((kernel, args.mode))
+    if not rec or rec["sha1"] != sha or args.kernel != "slp" or args.leaf != 64 or args.kappa != 32.0:
+        return None
+    if args.eta1 != 2.0 * math.sqrt(2.0) or args.eta2 != 1.0 or args.n != 32768:
+        return None
+    return rec["bytes"]
 
 
 def main():
@@ -508,7 +781,7 @@ def main():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--eta1", type=float, default=2.0 * math.sqrt(2.0))
     ap.add_argument("--eta2", type=float, default=1.0)
-    ap.add_argument("--mode", default="fp32", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--mode", default="mixed", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--nearfield", type=int, default=0)
     ap.add_argument("--kernel", default="slp", choices=["slp", "dlp"],
                     help="slp: single-layer collocation on the Fibonacci sphere (the headline); "
@@ -517,6 +790,11 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-error", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--sweep", default=None, choices=["cube", "surfaces"],
+                    help="instead of the headline: the unit-cube high-frequency sweep or the 48-surface batch "
+                         "(one JSON line per case)")
+    ap.add_argument("--skip-secondary", action="store_true",
+                    help="skip the FP64 / FP32 forms, the rank report and the eta1=20, eta2=5 run")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -548,6 +826,10 @@ def main():
                                  "sample": desc, "threads": "BLAS/OpenMP fixed to 1"},
                 "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+    if args.sweep is not None:
+        if rank == 0:
+            (sweep_cube if args.sweep == "cube" else sweep_surfaces)(args)
         return
     line = run_gpu(args)
     line["n_gpus"] = world

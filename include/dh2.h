@@ -347,6 +347,12 @@ dh2_status dh2_storage(const dh2_matrix* M, double* total, double* parts);
  * [2] leaf R = Q^* A, [3] level steps (factors and R), [4] expansion,
  * [5] projection. */
 dh2_status dh2_matrix_phase_ms(const dh2_matrix* M, float* ms6);
+/* The leaf-factor phase of the last dh2_compress in the mixed modes with G on
+ * the device, split by kernel (ms2: host array of 2 floats, CUDA events around
+ * each launch): [0] the tensor-core Gram launches, [1] the pivoted Cholesky,
+ * Jacobi and truncation launches.  Both 0 in the other modes and for host
+ * input.  Instrumentation only. */
+dh2_status dh2_matrix_leaf_split_ms(const dh2_matrix* M, float* ms2);
 /* Number of kernels launched by the last dh2_compress (or batched call) that
  * produced M (host int32 out). Instrumentation only: the paper has no
  * counterpart. */

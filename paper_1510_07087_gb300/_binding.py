@@ -117,6 +117,7 @@ SIGNATURES = [
     ("dh2_matrix_coupling", c_int32, [c_void_p, c_int64, c_void_p, c_int64, POINTER(c_int32), POINTER(c_int32)]),
     ("dh2_storage", c_int32, [c_void_p, POINTER(c_double), c_void_p]),
     ("dh2_matrix_phase_ms", c_int32, [c_void_p, c_void_p]),
+    ("dh2_matrix_leaf_split_ms", c_int32, [c_void_p, c_void_p]),
     ("dh2_matrix_launch_count", c_int32, [c_void_p, c_void_p]),
     ("dh2_matrix_class_launches", c_int32, [c_void_p, c_void_p]),
     ("dh2_matrix_block_weights", c_int32, [c_void_p, c_void_p]),
@@ -352,6 +353,12 @@ class Matrix:
     def phase_ms(self) -> np.ndarray:
         out = np.zeros(6, dtype=np.float32)
         _check(_lib().dh2_matrix_phase_ms(self.handle, _ptr(out)), "dh2_matrix_phase_ms")
+        return out
+
+    def leaf_split_ms(self) -> np.ndarray:
+        """Mixed modes, device input: the leaf phase as [Gram launches, factor launches] in ms."""
+        out = np.zeros(2, dtype=np.float32)
+        _check(_lib().dh2_matrix_leaf_split_ms(self.handle, _ptr(out)), "dh2_matrix_leaf_split_ms")
         return out
 
 

@@ -117,6 +117,7 @@ struct dh2_matrix {
   bool v_expanded = false;
   std::vector<double> eps2_h, zpow_h;
   float phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  float leaf_split_ms[2] = {0, 0};  // mixed modes, device input: leaf Gram launches, leaf factor launches
   int32_t launches = 0;  // kernels launched by the last compression (shared by a batch)
   int32_t class_launches[DH2_KC_COUNT] = {};  // the same launches by kernel class
   void* gram = nullptr;  // mixed modes with keep_gram: the leaf Gram matrices (double-float complex)
@@ -1032,15 +1033,22 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // leaf factors and R of one launch list per size class
   // leaf factorisations of one size class: the streamed LQ, or in the mixed
   // modes the tensor-core Gram matrices and their pivoted Cholesky
-  auto leaf_factor = [&](const uint32_t* codes, int n, int c) {
+  // events around the Gram and factor launches of each class (mixed modes,
+  // device input): the leaf phase split into its two kernels
+  cudaEvent_t kev[3 * kLeafClasses] = {};
+  bool kev_ok = false;
+  auto leaf_factor = [&](const uint32_t* codes, int n, int c, bool timed) {
     if (n <= 0) return;
     const int P = even_up(std::max(2, cls_maxm[c]));
     if constexpr (sizeof(T) == 4) {
       if (mixed) {
+        if (timed) cudaEventRecord(kev[3 * c], st);
         ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);
         counted(DH2_KC_LEAF_GRAM + c, true);
+        if (timed) cudaEventRecord(kev[3 * c + 1], st);
         ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);
         counted(DH2_KC_LEAF_FACTOR + c, true);
+        if (timed) cudaEventRecord(kev[3 * c + 2], st);
         return;
       }
     }
@@ -1048,7 +1056,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     counted(DH2_KC_LEAF_FACTOR + c, true);
   };
   auto leaf_lists = [&](const HList* L) {
-    for (int c = 0; c < kLeafClasses; ++c) leaf_factor(L[c].d_codes, (int)L[c].codes->size(), c);
+    for (int c = 0; c < kLeafClasses; ++c) leaf_factor(L[c].d_codes, (int)L[c].codes->size(), c, false);
   };
   auto leaf_rq = [&](const HList* L) {
     for (int c = 0; c < kLeafClasses; ++c)
@@ -1121,7 +1129,15 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     prof_reset_pair();
     prof_reset_gram();
 #endif
-    for (int c = 0; c < kLeafClasses; ++c) leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c);
+    if (mixed) {
+      kev_ok = true;
+      for (int i = 0; i < 3 * kLeafClasses && kev_ok; ++i)
+        kev_ok = cudaEventCreate(&kev[i]) == cudaSuccess;
+      if (!kev_ok) cudaGetLastError();  // no split timing; the compression itself goes on
+    }
+    for (int c = 0; c < kLeafClasses; ++c)
+      leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c,
+                  kev_ok && cls_begin[c + 1] > cls_begin[c]);
     cudaEventRecord(ev[2], st);
     // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
     for (int c = 0; c < kLeafClasses; ++c) {
@@ -1235,8 +1251,20 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   float ph[6] = {0, 0, 0, 0, 0, 0};
   for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&ph[i], ev[i], ev[i + 1]);
   for (int i = 0; i < 7; ++i) cudaEventDestroy(ev[i]);
+  float split[2] = {0, 0};
+  for (int c = 0; c < kLeafClasses; ++c) {
+    float a = 0, b = 0;
+    if (kev_ok && cls_begin[c + 1] > cls_begin[c] && cudaEventElapsedTime(&a, kev[3 * c], kev[3 * c + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, kev[3 * c + 1], kev[3 * c + 2]) == cudaSuccess) {
+      split[0] += a;
+      split[1] += b;
+    }
+  }
+  for (cudaEvent_t e : kev)
+    if (e) cudaEventDestroy(e);
   for (dh2_matrix* M : Ms) {
     std::memcpy(M->phase_ms, ph, sizeof(ph));
+    std::memcpy(M->leaf_split_ms, split, sizeof(split));
     M->launches = nlaunch;
     std::memcpy(M->class_launches, kcl, sizeof(kcl));
   }
@@ -2196,6 +2224,13 @@ dh2_status dh2_matrix_leaf_gram(const dh2_matrix* M, int32_t side, int64_t pair,
 dh2_status dh2_matrix_class_launches(const dh2_matrix* M, int32_t* counts) {
   if (!M || !counts) return DH2_EINVAL;
   std::memcpy(counts, M->class_launches, sizeof(M->class_launches));
+  return DH2_OK;
+}
+
+dh2_status dh2_matrix_leaf_split_ms(const dh2_matrix* M, float* ms2) {
+  if (!M || !ms2) return DH2_EINVAL;
+  ms2[0] = M->leaf_split_ms[0];
+  ms2[1] = M->leaf_split_ms[1];
   return DH2_OK;
 }
 
