@@ -658,13 +658,13 @@ def sweep_cube(args):
                         torch.cuda.synchronize()
                         ms = e0.elapsed_time(e1) / 3
                         M = one()
-                        err = D.dh2_error(M, None, which=D.ERR_FRO_CLOSED if n > 16384 else D.ERR_FRO_BLOCKWISE)
+                        err = D.dh2_error(M, None)
                         elem = 8
                     line = {"sweep": "unit-cube high-frequency", "n": n, "kappa": kappa, "eps": eps, "params": pname,
                             "eta1": eta1, "eta2": eta2, "form": name, "ms_per_step": ms,
                             "input_gbs": elem * n * n / (ms * 1e-3) / 1e9 if cdt is not None else None,
                             "entries_per_s": n * n / (ms * 1e-3), "rel_err_vs_fp64": err,
-                            "error_measure": "closed form" if (cdt is None and n > 16384) else "blockwise",
+                            "error_measure": "blockwise",
                             "adm_fraction": st.adm_fraction, "depth": st.depth,
                             "phases_ms": [float(v) for v in ph],
                             "storage": _storage_ratios(M, n, kappa, st.depth),

@@ -227,7 +227,7 @@ dh2_status upload_tree(Tree& tr) {
         D->gram_elems += mpd * mpd;
         if (P.ncols > kGramWindow) {
           gvo[p] = D->gram_velems;
-          D->gram_velems += 2 * mpd * (mpd + 1);  // rows of mp + 1 (padded, as in shared memory)
+          D->gram_velems += 2 * mpd * mpd;  // 2 mp lanes x mp columns, column-major
         }
       } else {
         for (int j = 0; j < 2; ++j) {

@@ -59,7 +59,7 @@ __device__ unsigned long long g_gprof[10];
 #define GP_ON 0
 #endif
 
-constexpr int kGramThreads = 128;
+constexpr int kGramThreads = 256;
 constexpr int kGramChunk = 64;        // complex columns per chunk (one 128-byte K row of bf16)
 constexpr int kTableCols = 1024;      // columns of the pair's column table held in shared memory at once
 static_assert(kGramWindow % kGramChunk == 0 && kTableCols % kGramChunk == 0, "chunk-aligned windows and tables");
@@ -122,10 +122,16 @@ struct GramShape {
 };
 
 // Persistent over the launch list: CTA b takes codes b, b + grid, ...
+// Eight warps: all of them load and slice (two (row, 8-column) items per
+// thread and chunk); thread 0 issues the MMAs; the window sums are read from
+// tensor memory by all eight (warp w: lanes 32 (w % 4) .., every other group
+// of 8 columns).  The loads of chunk c + 1 are issued as soon as chunk c is
+// sliced, so that they are in flight while the tensor cores work on chunk c.
 template <int NP>
-__global__ void __launch_bounds__(kGramThreads, 1)
+__global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 : 2)
     gram_kernel(const GramArgs* __restrict__ args, const uint32_t* __restrict__ codes, int ncodes) {
   using Sh = GramShape<NP>;
+  constexpr int U = (64 * 8 + kGramThreads - 1) / kGramThreads;  // items per thread and chunk (m <= 64)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sl0 = smem;
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     tmem_alloc(&tmem_base, Sh::TCOLS);
     tmem_relinquish();
@@ -159,7 +165,6 @@ __global__ void __launch_bounds__(kGramThreads, 1)
   tc_fence_after_sync();
   const uint32_t tbase = tmem_base;
   const uint32_t sbase = smem_addr(smem);
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
   constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
   uint32_t phase = 0;
   bool timed_out = false;
@@ -201,56 +206,6 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     gp[0] += 1;
     GP_T(ga);
 #endif
-
-    // ---------------------------------------------------------------- row scales
-    // the largest |re|, |im| of each row of A = G^omega_tc from the block
-    // norms pass: per block of F_tc its row (column basis: column) maxima
-    // times the block's FP32 weight -- the same value as the maximum over the
-    // weighted entries, since rounding a product with a positive factor is
-    // monotonic.  The blocks' offsets and weights are gathered first (one
-    // thread per block), then two threads per row take half of the blocks each.
-    {
-      const int64_t sg0 = a.seg_begin[side][pid], sg1 = a.seg_begin[side][pid + 1];
-      const int i = tid >> 1;
-      float mx = 0.f;
-      bool bad = false;
-      for (int64_t sb = sg0; sb < sg1; sb += kGramThreads) {
-        const int nb = (int)(sg1 - sb < kGramThreads ? sg1 - sb : kGramThreads);
-        __syncthreads();  // the previous batch of block data has been used
-        if (tid < nb) {
-          const int b = a.seg_blk[side][sb + tid];
-          // the block's maxima: rows of t+ first (row basis), then columns of s+ (column basis)
-          const int cl = side == 0 ? a.bt[b] : a.bs[b];  // the block's cluster on this side
-          sgoff[tid] = a.bmax_off[b] + (side == 0 ? 0 : a.csize[a.bt[b]]) + (r0 - a.cstart[cl]);
-          sgw[tid] = (float)a.invw[b];
-        }
-        __syncthreads();
-        if (i < m)
-#pragma unroll 4
-          for (int k = tid & 1; k < nb; k += 2) {
-            const float v = a.bmax[sgoff[k] + i] * sgw[k];
-            bad = bad || !(v <= FLT_MAX);
-            mx = fmaxf(mx, v);
-          }
-      }
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      bad = __syncthreads_or(bad);
-      if (bad) {  // non-finite entries: reported, H of this pair left as zero
-        if (tid == 0) atomicOr(a.status, kStatusNaN);
-        for (int k = tid; k < mp * mp; k += kGramThreads) Hout[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        continue;
-      }
-      if (i < m && (tid & 1) == 0) {
-        int e = 0;
-        if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
-        rexp[i] = e;
-        rsc[i] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
-      }
-    }
-#if GP_ON
-    GP_T(gb);
-    gp[2] += gb - ga;
-#endif
     // column table of the pair (segments of kTableCols columns)
     auto load_table = [&](int tb) {
 #if GP_ON
@@ -267,12 +222,12 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 #endif
     };
     // entries of this thread's items of the chunk at j0 (zero past the chunk)
-    auto load_chunk = [&](int j0, int cw, int tb, C2<float> (&v)[4][8]) {
+    auto load_chunk = [&](int j0, int cw, int tb, C2<float> (&v)[U][8]) {
 #if GP_ON
       long long t0 = clock64();
 #endif
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         const int q = tid + kGramThreads * u;
         const int r = q % m, g = q / m;
 #pragma unroll
@@ -290,6 +245,64 @@ __global__ void __launch_bounds__(kGramThreads, 1)
       gp[4] += clock64() - t0;
 #endif
     };
+    // the table and the first chunk's loads go out before the row scales, so
+    // that their latencies overlap
+    int tb = 0;
+    load_table(0);
+    C2<float> v[U][8];
+    load_chunk(0, min(kGramChunk, N), 0, v);
+
+    // ---------------------------------------------------------------- row scales
+    // the largest |re|, |im| of each row of A = G^omega_tc from the block
+    // norms pass: per block of F_tc its row (column basis: column) maxima
+    // times the block's FP32 weight -- the same value as the maximum over the
+    // weighted entries, since rounding a product with a positive factor is
+    // monotonic.  The blocks' offsets and weights are gathered first (one
+    // thread per block), then four threads per row take a quarter of the blocks each.
+    {
+      const int64_t sg0 = a.seg_begin[side][pid], sg1 = a.seg_begin[side][pid + 1];
+      const int i = tid >> 2;
+      float mx = 0.f;
+      bool bad = false;
+      for (int64_t sb = sg0; sb < sg1; sb += kGramThreads) {
+        const int nb = (int)(sg1 - sb < kGramThreads ? sg1 - sb : kGramThreads);
+        __syncthreads();  // the previous batch of block data has been used
+        if (tid < nb) {
+          const int b = a.seg_blk[side][sb + tid];
+          // the block's maxima: rows of t+ first (row basis), then columns of s+ (column basis)
+          const int cl = side == 0 ? a.bt[b] : a.bs[b];  // the block's cluster on this side
+          sgoff[tid] = a.bmax_off[b] + (side == 0 ? 0 : a.csize[a.bt[b]]) + (r0 - a.cstart[cl]);
+          sgw[tid] = (float)a.invw[b];
+        }
+        __syncthreads();
+        if (i < m)
+#pragma unroll 4
+          for (int k = tid & 3; k < nb; k += 4) {
+            const float x = a.bmax[sgoff[k] + i] * sgw[k];
+            bad = bad || !(x <= FLT_MAX);
+            mx = fmaxf(mx, x);
+          }
+      }
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      bad = __syncthreads_or(bad);
+      if (bad) {  // non-finite entries: reported, H of this pair left as zero
+        if (tid == 0) atomicOr(a.status, kStatusNaN);
+        for (int k = tid; k < mp * mp; k += kGramThreads) Hout[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      if (i < m && (tid & 3) == 0) {
+        int e = 0;
+        if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
+        rexp[i] = e;
+        rsc[i] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
+      }
+      __syncthreads();
+    }
+#if GP_ON
+    GP_T(gb);
+    gp[2] += gb - ga;
+#endif
 
     // ---------------------------------------------------------------- sliced products
     bool pending = false;  // an MMA batch was committed and not yet waited for
@@ -319,10 +332,6 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         dA1[x] = dB1[x];
       }
     }
-    int tb = 0;
-    load_table(0);
-    C2<float> v[4][8];
-    load_chunk(0, min(kGramChunk, N), 0, v);
     for (int w0 = 0; w0 < N && !timed_out; w0 += kGramWindow) {
       const int wend = min(N, w0 + kGramWindow);
       for (int j0 = w0; j0 < wend; j0 += kGramChunk) {
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
         GP_T(ga);
 #endif
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
           const int q = tid + kGramThreads * u;
           if (q >= nitem) continue;
           const int r = q % m, g = q / m;
@@ -353,8 +362,6 @@ __global__ void __launch_bounds__(kGramThreads, 1)
               const float xr = __fmul_rn(v[u][k + h].re, w);
               const float xi = __fmul_rn(side == 0 ? v[u][k + h].im : -v[u][k + h].im, w);
               // three 8-bit slices of each part, every step exact in FP32
-              // (|x| < 64: adding and subtracting 1.5 * 2^23 rounds to the
-              // nearest integer, ties to even)
               slice3(xr, sx[0][h], sx[1][h], sx[2][h]);
               slice3(xi, sy[0][h], sy[1][h], sy[2][h]);
             }
@@ -378,13 +385,27 @@ __global__ void __launch_bounds__(kGramThreads, 1)
           *reinterpret_cast<uint4*>(bsl + swz(r, g)) = make_uint4(pb[0][0], pb[0][1], pb[0][2], pb[0][3]);
           *reinterpret_cast<uint4*>(bsl + swz(mp + r, g)) = make_uint4(pb[1][0], pb[1][1], pb[1][2], pb[1][3]);
         }
-        fence_async_smem();
-        __syncthreads();
 #if GP_ON
         GP_T(gb);
         gp[6] += gb - ga;
 #endif
+        // the next chunk's loads go out now: in flight while the tensor cores
+        // work on this chunk (a new table segment waits until every thread has
+        // sliced, inside load_table)
+        const int jn = j0 + kGramChunk;
+        if (jn < N) {
+          if (jn >= tb + kTableCols) {
+            tb = jn;
+            load_table(tb);
+          }
+          load_chunk(jn, min(kGramChunk, min(N, jn < wend ? wend : jn + kGramWindow) - jn), tb, v);
+        }
+        fence_async_smem();
+        __syncthreads();
         if (tid == 0) {
+#if GP_ON
+          GP_T(gb);
+#endif
           tc_fence_after_sync();
           const bool first = j0 == w0;
           // products (A slice, B slice or the scaled copy, accumulator); the
@@ -410,52 +431,45 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 #endif
         }
         pending = true;
-        // the next chunk's loads go out while the tensor cores work on this one
-        const int jn = j0 + kGramChunk;
-        if (jn < N) {
-          if (jn >= tb + kTableCols) {
-            tb = jn;
-            load_table(tb);
-          }
-          load_chunk(jn, min(kGramChunk, min(N, jn < wend ? wend : jn + kGramWindow) - jn), tb, v);
-        }
       }
       if (timed_out || (pending && !wait_mma())) {
         timed_out = true;
         break;
       }
       // window done: V = P11 2^31 + P12 2^24 + P13 2^16 + P22 2^15 + low 2^8 per lane (row of [Re; Im]);
-      // every P is an integer below 2^24 held exactly in FP32
+      // every P is an integer below 2^24 held exactly in FP32.  Partial sums of
+      // long rows go to global memory column by column (lanes contiguous).
       const bool last = wend >= N;
 #if GP_ON
       GP_T(ga);
 #endif
       tc_fence_after_sync();
-      const int L = tid;  // TMEM lane of this thread
+      const int L = (warp & 3) * 32 + lane;  // TMEM lane of this thread
+      const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 #pragma unroll 1
-      for (int cb = 0; cb < NP; cb += 16) {
-        float p11[16], p12[16], p13[16], p22[16], plo[16];
-        tmem_ld16(tbase + lane_base + 0 * NP + cb, p11);
-        tmem_ld16(tbase + lane_base + 1 * NP + cb, p12);
-        tmem_ld16(tbase + lane_base + 2 * NP + cb, p13);
-        tmem_ld16(tbase + lane_base + 3 * NP + cb, p22);
-        tmem_ld16(tbase + lane_base + 4 * NP + cb, plo);
+      for (int cb = (warp >> 2) * 8; cb < NP; cb += 16) {
+        float p11[8], p12[8], p13[8], p22[8], plo[8];
+        tmem_ld8(tbase + lane_base + 0 * NP + cb, p11);
+        tmem_ld8(tbase + lane_base + 1 * NP + cb, p12);
+        tmem_ld8(tbase + lane_base + 2 * NP + cb, p13);
+        tmem_ld8(tbase + lane_base + 3 * NP + cb, p22);
+        tmem_ld8(tbase + lane_base + 4 * NP + cb, plo);
         tmem_ld_wait();
         if (L < 2 * mp) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
+          for (int i = 0; i < 8; ++i) {
             const int j = cb + i;
             if (j >= mp) break;
             long long x = (long long)__float2int_rn(p11[i]) * (1LL << 31) +
                           (long long)__float2int_rn(p12[i]) * (1LL << 24) +
                           (long long)__float2int_rn(p13[i]) * (1LL << 16) +
                           (long long)__float2int_rn(p22[i]) * (1LL << 15) + (long long)__float2int_rn(plo[i] * 256.f);
-            const int64_t vi = (int64_t)L * (mp + 1) + j;  // padded rows: no shared-memory bank conflicts
             if (Vg) {
-              if (w0 > 0) x += Vg[vi];
-              if (!last) Vg[vi] = x;
+              const int64_t gi = (int64_t)j * (2 * mp) + L;
+              if (w0 > 0) x += Vg[gi];
+              if (!last) Vg[gi] = x;
             }
-            if (last) Vs[vi] = x;
+            if (last) Vs[(int64_t)L * (mp + 1) + j] = x;  // padded rows: no shared-memory bank conflicts
           }
         }
       }
