@@ -675,6 +675,67 @@ def sweep_cube(args):
             del G128
 
 
+def sweep_small(args):
+    """The two small configurations, median of 10 timed calls each after 3 warm-up calls:
+    Fibonacci sphere n = 2048, kappa = 4, leaf 32, eps = 1e-4 in FP64 (complex128 G), and n = 8192,
+    kappa = 16, leaf 32 at eps in {1e-4, 1e-6} in FP64, mixed and FP32, with the rank deviations of the
+    reduced forms from the FP64 form.  One JSON line per case."""
+    import torch
+
+    import paper_1510_07087_gb300 as D
+    from synth import fibonacci_sphere, mean_nn_distance
+    from synth.inputs import helmholtz_matrix_torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    for n, kappa, eps_list, forms in ((2048, 4.0, (1e-4,), ("fp64",)),
+                                      (8192, 16.0, (1e-4, 1e-6), ("fp64", "mixed", "fp32"))):
+        pts = fibonacci_sphere(n)
+        h = mean_nn_distance(pts)
+        T = D.dh2_tree_build(pts, 32, kappa)
+        st = T.stats()
+        P = pts[T.perm()]
+        G128 = helmholtz_matrix_torch(P, kappa, h, torch.complex128, dev).t()
+        G64 = G128.to(torch.complex64)
+        for eps in eps_list:
+            r64 = None
+            for form in forms:
+                mode = MODE_CODE(D)[form]
+                G = G128 if form == "fp64" else G64
+                for _ in range(3):
+                    M = D.dh2_compress(T, G, eps=eps, mode=mode)
+                    del M
+                times = []
+                for _ in range(10):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    M = D.dh2_compress(T, G, eps=eps, mode=mode)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                    del M
+                ms = statistics.median(times)
+                M = D.dh2_compress(T, G, eps=eps, mode=mode)
+                rk = [M.ranks(0), M.ranks(1)]
+                if form == "fp64":
+                    r64 = rk
+                stg = M.storage()
+                elem = 16 if form == "fp64" else 8
+                line = {"sweep": "small configurations", "n": n, "kappa": kappa, "leaf": 32, "eps": eps,
+                        "form": form, "ms_median_of_10": ms, "input_gbs": elem * n * n / (ms * 1e-3) / 1e9,
+                        "rel_err_vs_fp64": D.dh2_error(M, G128), "adm_fraction": st.adm_fraction,
+                        "k_max": int(max(rk[0].max(initial=0), rk[1].max(initial=0))),
+                        "mem_per_n_kib_c128": stg["total"] * 16 / 1024 / n,
+                        "rank_deviation_vs_fp64_form": (None if form == "fp64" or r64 is None else
+                                                        {"row": _rank_hist(rk[0], r64[0]),
+                                                         "col": _rank_hist(rk[1], r64[1])})}
+                del M
+                print(json.dumps(line), flush=True)
+        del G128, G64
+
+
 def _surface_problem(i):
     """Problem i of the 48-surface batch: 16 each of sphere, 2:1:1 ellipsoid and unit-cube surface,
     uniform random points with seed 151007087 + i, n ~ U{1024..12288}, kappa = U[8, 40] / diam."""
@@ -790,8 +851,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-error", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--sweep", default=None, choices=["cube", "surfaces"],
-                    help="instead of the headline: the unit-cube high-frequency sweep or the 48-surface batch "
+    ap.add_argument("--sweep", default=None, choices=["small", "cube", "surfaces"],
+                    help="instead of the headline: the small configurations, the unit-cube high-frequency sweep "
+                         "or the 48-surface batch "
                          "(one JSON line per case)")
     ap.add_argument("--skip-secondary", action="store_true",
                     help="skip the FP64 / FP32 forms, the rank report and the eta1=20, eta2=5 run")
@@ -829,7 +891,7 @@ def main():
         return
     if args.sweep is not None:
         if rank == 0:
-            (sweep_cube if args.sweep == "cube" else sweep_surfaces)(args)
+            {"small": sweep_small, "cube": sweep_cube, "surfaces": sweep_surfaces}[args.sweep](args)
         return
     line = run_gpu(args)
     line["n_gpus"] = world

@@ -34,6 +34,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstdint>
+#include <cstdio>
 
 #include "dh2_internal.h"
 #include "dh2_kernels.cuh"
@@ -533,6 +534,14 @@ bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t 
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGramThreads, smem);
   per_sm = std::max(1, std::min(per_sm, (int)(512 / Sh::TCOLS)));
   const int grid = std::min(n, nsm * per_sm);
+#ifdef DH2_PROFILE
+  {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kern);
+    std::fprintf(stderr, "dh2 gram<%d>: %d pairs, %d CTAs per SM, grid %d, %zu + %zu bytes shared memory, %d registers\n",
+                 NP, n, per_sm, grid, smem, fa.sharedSizeBytes, fa.numRegs);
+  }
+#endif
   kern<<<grid, kGramThreads, smem, st>>>(args, codes, n);
   return true;
 }

@@ -1051,45 +1051,63 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   }
   __syncthreads();
   // ---------------------------------------------------------------- 2. Jacobi
-  // round-robin ordering over pe columns (pe = K rounded up to even).  Up to
-  // 16 columns all pairs of a round fit in warp 0 (a power-of-two group of
-  // lanes per pair), so a round ends with a warp barrier only; wider factors
-  // use one column pair per group of tpp threads over the CTA (4..32 threads,
-  // as many as the pe/2 pairs of a round allow) and a CTA barrier per round.
+  // one column pair per group of tpp threads (as many as the pe/2 pairs of a
+  // round allow, 4..32); round-robin ordering over pe columns
   const int pe = K + (K & 1);
   const T tol = T(p) * Eps<T>::u;
+  constexpr int JH = (P_T / 2 + NT / 4 - 1) / (NT / 4);  // pairs per group at most
+  int tpp = DH2_JACOBI_TPP;
+  while (tpp > 4 && tpp * (pe / 2) > NT) tpp >>= 1;
+  const int jng = NT / tpp;
+  const int jg = tid / tpp, jl = tid & (tpp - 1);
+  if (tid == 0) {
+    sh_rot[0] = 0;
+    sh_rot[1] = 0;
+  }
+  __syncthreads();
   bool conv = pe < 2;
   int nsweeps = 0;
-  if (pe <= 16) {
-    __shared__ int sh_conv;
-    if (warp == 0) {
-      int tw = 32;
-      while (tw * (pe / 2) > 32) tw >>= 1;
-      const int g = lane / tw, l = lane & (tw - 1);
-      const bool act = g < pe / 2;
-      for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
-        ++nsweeps;
-        int ia = g, ib = pe - 1 - g;  // this group's pair in round 0
-        bool rot = false;
-        for (int rd = 0; rd < pe - 1; ++rd) {
-          C2<T>* ca = Lm + (act ? ia : 0) * LDL;
-          C2<T>* cb = Lm + (act ? ib : 0) * LDL;
+  for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
+    ++nsweeps;
+    const int sp = sweep & 1;
+    // round-robin positions of this group's pairs in round 0; each round
+    // moves every position but the fixed one (index 0) by one place
+    int ia[JH], ib[JH];
+#pragma unroll
+    for (int h = 0; h < JH; ++h) {
+      const int kk = jg + h * jng;
+      ia[h] = kk;
+      ib[h] = pe - 1 - kk;
+    }
+    for (int rd = 0; rd < pe - 1; ++rd) {
+#pragma unroll
+      for (int h = 0; h < JH; ++h) {
+        const int kk = jg + h * jng;
+        // warps with an active group run the reductions converged (full mask)
+        if ((warp * 32) / tpp + h * jng < pe / 2) {
+          const bool act = kk < pe / 2;
+          C2<T>* ca = Lm + (act ? ia[h] : 0) * LDL;
+          C2<T>* cb = Lm + (act ? ib[h] : 0) * LDL;
           T al = T(0), be = T(0);
           C2<T> ga = czero<T>();
           if (act)
-            for (int r = l; r < p; r += tw) {
+            for (int r = jl; r < p; r += tpp) {
               const C2<T> xa = ca[r], xb = cb[r];
               al = nmac(al, xa);
               be = nmac(be, xb);
               ga = cmacc(ga, xb, xa);  // + conj(xa) * xb
             }
-          for (int o = 1; o < tw; o <<= 1) {
+          for (int o = 1; o < tpp; o <<= 1) {
             al += __shfl_xor_sync(0xffffffffu, al, o);
             be += __shfl_xor_sync(0xffffffffu, be, o);
             ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
             ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
           }
           const T g2 = cnorm2(ga);
+          // rotate unless the pair is orthogonal to tol (relative)
+          // rotation scalars from reciprocal square roots and one quotient
+          // (hardware approximations in FP32, a few ulp): c^2 + s^2 = 1 to
+          // that level, far inside the convergence test's tol = p u
           const T rg = frsqrt(g2);
           if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
               g2 * rg * frsqrt(al) * frsqrt(be) > tol) {
@@ -1099,121 +1117,32 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
             const T t = (zt >= T(0) ? T(1) : T(-1)) *
                         (az > T(1e15) ? fdiv(T(0.5), az) : fdiv(T(1), az + q1 * frsqrt(q1)));
             const T c = frsqrt(T(1) + t * t);
-            const T sn = t * c;
-            if (sn != T(0)) {
+            const T s = t * c;
+            if (s != T(0)) {
               const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
-              for (int r = l; r < p; r += tw) {
+              for (int r = jl; r < p; r += tpp) {
                 const C2<T> xa = ca[r];
                 const C2<T> eb = cmul(e, cb[r]);
-                ca[r] = C2<T>{c * xa.re - sn * eb.re, c * xa.im - sn * eb.im};
-                cb[r] = C2<T>{sn * xa.re + c * eb.re, sn * xa.im + c * eb.im};
+                ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
+                cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
               }
-              rot = true;
+              if (jl == 0) sh_rot[sp] = 1;
             }
           }
           if (act) {
-            if (g > 0) ia = ia == pe - 1 ? 1 : ia + 1;
-            ib = ib == pe - 1 ? 1 : ib + 1;
-          }
-          __syncwarp();
-        }
-        if (!__any_sync(0xffffffffu, rot)) {
-          conv = true;
-          break;
-        }
-      }
-      if (lane == 0) sh_conv = conv ? 1 : 0;
-    }
-    __syncthreads();
-    conv = sh_conv != 0;
-  } else {
-    constexpr int JH = (P_T / 2 + NT / 4 - 1) / (NT / 4);  // pairs per group at most
-    int tpp = DH2_JACOBI_TPP;
-    while (tpp > 4 && tpp * (pe / 2) > NT) tpp >>= 1;
-    const int jng = NT / tpp;
-    const int jg = tid / tpp, jl = tid & (tpp - 1);
-    if (tid == 0) {
-      sh_rot[0] = 0;
-      sh_rot[1] = 0;
-    }
-    __syncthreads();
-    for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
-      ++nsweeps;
-      const int sp = sweep & 1;
-      // round-robin positions of this group's pairs in round 0; each round
-      // moves every position but the fixed one (index 0) by one place
-      int ia[JH], ib[JH];
-#pragma unroll
-      for (int h = 0; h < JH; ++h) {
-        const int kk = jg + h * jng;
-        ia[h] = kk;
-        ib[h] = pe - 1 - kk;
-      }
-      for (int rd = 0; rd < pe - 1; ++rd) {
-#pragma unroll
-        for (int h = 0; h < JH; ++h) {
-          const int kk = jg + h * jng;
-          // warps with an active group run the reductions converged (full mask)
-          if ((warp * 32) / tpp + h * jng < pe / 2) {
-            const bool act = kk < pe / 2;
-            C2<T>* ca = Lm + (act ? ia[h] : 0) * LDL;
-            C2<T>* cb = Lm + (act ? ib[h] : 0) * LDL;
-            T al = T(0), be = T(0);
-            C2<T> ga = czero<T>();
-            if (act)
-              for (int r = jl; r < p; r += tpp) {
-                const C2<T> xa = ca[r], xb = cb[r];
-                al = nmac(al, xa);
-                be = nmac(be, xb);
-                ga = cmacc(ga, xb, xa);  // + conj(xa) * xb
-              }
-            for (int o = 1; o < tpp; o <<= 1) {
-              al += __shfl_xor_sync(0xffffffffu, al, o);
-              be += __shfl_xor_sync(0xffffffffu, be, o);
-              ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
-              ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
-            }
-            const T g2 = cnorm2(ga);
-            // rotate unless the pair is orthogonal to tol (relative)
-            // rotation scalars from reciprocal square roots and one quotient
-            // (hardware approximations in FP32, a few ulp): c^2 + s^2 = 1 to
-            // that level, far inside the convergence test's tol = p u
-            const T rg = frsqrt(g2);
-            if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
-                g2 * rg * frsqrt(al) * frsqrt(be) > tol) {
-              const T zt = (be - al) * T(0.5) * rg;
-              const T az = fabs(zt);
-              const T q1 = T(1) + zt * zt;
-              const T t = (zt >= T(0) ? T(1) : T(-1)) *
-                          (az > T(1e15) ? fdiv(T(0.5), az) : fdiv(T(1), az + q1 * frsqrt(q1)));
-              const T c = frsqrt(T(1) + t * t);
-              const T s = t * c;
-              if (s != T(0)) {
-                const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
-                for (int r = jl; r < p; r += tpp) {
-                  const C2<T> xa = ca[r];
-                  const C2<T> eb = cmul(e, cb[r]);
-                  ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
-                  cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
-                }
-                if (jl == 0) sh_rot[sp] = 1;
-              }
-            }
-            if (act) {
-              if (kk > 0) ia[h] = ia[h] == pe - 1 ? 1 : ia[h] + 1;
-              ib[h] = ib[h] == pe - 1 ? 1 : ib[h] + 1;
-            }
+            if (kk > 0) ia[h] = ia[h] == pe - 1 ? 1 : ia[h] + 1;
+            ib[h] = ib[h] == pe - 1 ? 1 : ib[h] + 1;
           }
         }
-        __syncthreads();
-        if (rd == 0 && tid == 0) sh_rot[sp ^ 1] = 0;
       }
-      const int rot = sh_rot[sp];
       __syncthreads();
-      if (rot == 0) {
-        conv = true;
-        break;
-      }
+      if (rd == 0 && tid == 0) sh_rot[sp ^ 1] = 0;
+    }
+    const int rot = sh_rot[sp];
+    __syncthreads();
+    if (rot == 0) {
+      conv = true;
+      break;
     }
   }
   if (!conv && tid == 0) atomicOr(a.status, kStatusNoConv);
