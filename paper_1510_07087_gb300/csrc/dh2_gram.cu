@@ -35,6 +35,7 @@
 #include <cfloat>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 
 #include "dh2_internal.h"
 #include "dh2_kernels.cuh"
@@ -533,6 +534,18 @@ bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t 
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGramThreads, smem);
   per_sm = std::max(1, std::min(per_sm, (int)(512 / Sh::TCOLS)));
+#ifdef DH2_PROFILE
+  {
+    int smem_sm = 0, regs_sm = 0, occ0 = 0, occ64 = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, kern, kGramThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, kern, kGramThreads, 64 * 1024);
+    std::fprintf(stderr, "dh2 gram<%d> occupancy: %d at %zu B, %d at 0 B, %d at 64 KiB; SM: %d B shared, %d registers\n",
+                 NP, per_sm, smem, occ0, occ64, smem_sm, regs_sm);
+    if (const char* e = std::getenv("DH2_GRAM_PER_SM")) per_sm = std::max(1, std::min(atoi(e), (int)(512 / Sh::TCOLS)));
+  }
+#endif
   const int grid = std::min(n, nsm * per_sm);
 #ifdef DH2_PROFILE
   {
