@@ -373,6 +373,7 @@ enum {
   DH2_KC_EXPAND = 18,       /* expansion of non-leaf column bases (Eq. nested)                   */
   DH2_KC_PROJECT = 19,      /* coupling matrices S_b                                             */
   DH2_KC_LEAF_GRAM = 20,    /* + leaf row class 0..3: tensor-core Gram matrices (MIXED_BF16X3)   */
+  DH2_KC_GRAM_SCALES = 24,  /* row scales of the leaf Gram matrices (MIXED_BF16X3)               */
   DH2_KC_COUNT = 32
 };
 /* Launches of the last compression that produced M, by kernel class

@@ -1043,7 +1043,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     if constexpr (sizeof(T) == 4) {
       if (mixed) {
         if (timed) cudaEventRecord(kev[3 * c], st);
-        ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);
+        ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);  // row scales, then the Gram matrices
+        counted(DH2_KC_GRAM_SCALES, true);
         counted(DH2_KC_LEAF_GRAM + c, true);
         if (timed) cudaEventRecord(kev[3 * c + 1], st);
         ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);

@@ -35,7 +35,6 @@
 #include <cfloat>
 #include <cstdint>
 #include <cstdio>
-#include <cstdlib>
 
 #include "dh2_internal.h"
 #include "dh2_kernels.cuh"
@@ -123,6 +122,65 @@ struct GramShape {
   static constexpr uint32_t SMEM = 1024 + 3 * SLBYTES + BBYTES;
 };
 
+constexpr int kBadRow = 0x7fffffff;  // row-scale marker of a non-finite entry
+
+// Row scales of the leaf pairs of a launch list, one warp per pair: for row i
+// of A = G^omega_tc the exponent e_i >= -120 with every |re|, |im| of the row
+// below 2^e_i, from the block norms pass's per-block row (column basis:
+// column) maxima times the block's FP32 weight -- the same value as the
+// maximum over the weighted entries, since rounding a product with a positive
+// factor is monotonic.  Written as int bits over the first m entries of the
+// pair's Gram slot, where the Gram kernel reads them before it writes H.
+__global__ void __launch_bounds__(256) gram_scales_kernel(const GramArgs* __restrict__ args,
+                                                          const uint32_t* __restrict__ codes, int ncodes) {
+  const int w = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= ncodes) return;
+  const uint32_t code = codes[w];
+  const GramArgs& a = args[code >> kCodeProbShift];
+  const int side = (int)((code >> kCodeSideShift) & 1u);
+  const int pid = (int)(code & kCodePairMask);
+  const int m = a.m[side][pid];
+  if (m > 64 || m <= 0) return;  // the Gram kernel reports rows beyond its class
+  const int r0 = a.start[side][pid];
+  float4* Hout = a.H + a.hoff[side][pid];
+  const int64_t sg0 = a.seg_begin[side][pid], sg1 = a.seg_begin[side][pid + 1];
+  float mx0 = 0.f, mx1 = 0.f;  // rows lane and lane + 32
+  bool bad = false;
+  for (int64_t sb = sg0; sb < sg1; sb += 32) {
+    const int nb = (int)(sg1 - sb < 32 ? sg1 - sb : 32);
+    long long off = 0;
+    float wt = 0.f;
+    if (lane < nb) {
+      const int b = a.seg_blk[side][sb + lane];
+      const int cl = side == 0 ? a.bt[b] : a.bs[b];  // the block's cluster on this side
+      // the block's maxima: rows of t+ first (row basis), then columns of s+ (column basis)
+      off = a.bmax_off[b] + (side == 0 ? 0 : a.csize[a.bt[b]]) + (r0 - a.cstart[cl]);
+      wt = (float)a.invw[b];
+    }
+    for (int k = 0; k < nb; ++k) {
+      const long long o = __shfl_sync(0xffffffffu, off, k);
+      const float ww = __shfl_sync(0xffffffffu, wt, k);
+      if (lane < m) {
+        const float x = a.bmax[o + lane] * ww;
+        bad = bad || !(x <= FLT_MAX);
+        mx0 = fmaxf(mx0, x);
+      }
+      if (lane + 32 < m) {
+        const float x = a.bmax[o + lane + 32] * ww;
+        bad = bad || !(x <= FLT_MAX);
+        mx1 = fmaxf(mx1, x);
+      }
+    }
+  }
+  auto expo = [](float mx) {
+    int e = 0;
+    if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
+    return e < -120 ? -120 : e;    // keeps 2^(6 - e) finite; smaller entries slice to zero
+  };
+  if (lane < m) Hout[lane].x = __int_as_float(bad ? kBadRow : expo(mx0));
+  if (lane + 32 < m) Hout[lane + 32].x = __int_as_float(bad ? kBadRow : expo(mx1));
+}
+
 // Persistent over the launch list: CTA b takes codes b, b + grid, ...
 // Eight warps: all of them load and slice (two (row, 8-column) items per
 // thread and chunk); thread 0 issues the MMAs; the window sums are read from
@@ -143,8 +201,6 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
   __shared__ float cwtT[kTableCols]; // and its weight 1/omega_b
   __shared__ float rsc[64];
   __shared__ int rexp[64];
-  __shared__ int64_t sgoff[kGramThreads];  // row scales: per block of F_tc its maxima's offset
-  __shared__ float sgw[kGramThreads];      // and its FP32 weight
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t tmem_base;
 
@@ -232,14 +288,37 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
       for (int u = 0; u < U; ++u) {
         const int q = tid + kGramThreads * u;
         const int r = q % m, g = q / m;
+        // column basis: the item's 8 entries lie in one row of G; where their
+        // columns are consecutive and the first is 16-byte aligned they arrive
+        // as four 16-byte loads
+        bool vec = false;
+        int64_t e0 = 0;
+        if (side == 1 && q < nitem && 8 * g + 7 < cw) {
+          const int* cg = cgcT + (j0 - tb + 8 * g);
+          const int gc0 = cg[0];
+          e0 = (int64_t)(r0 + r) * ld + gc0;
+          vec = (e0 & 1) == 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int jj = 8 * g + k;
-          v[u][k] = C2<float>{0.f, 0.f};
-          if (q < nitem && jj < cw) {
-            const int gc = cgcT[j0 - tb + jj];
-            const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
-            v[u][k] = G[e];
+          for (int k = 1; k < 8; ++k) vec = vec && cg[k] == gc0 + k;
+        }
+        if (vec) {
+          const float4* src = reinterpret_cast<const float4*>(G + e0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 x = src[k];
+            v[u][2 * k] = C2<float>{x.x, x.y};
+            v[u][2 * k + 1] = C2<float>{x.z, x.w};
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int jj = 8 * g + k;
+            v[u][k] = C2<float>{0.f, 0.f};
+            if (q < nitem && jj < cw) {
+              const int gc = cgcT[j0 - tb + jj];
+              const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
+              v[u][k] = G[e];
+            }
           }
         }
       }
@@ -255,51 +334,22 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
     load_chunk(0, min(kGramChunk, N), 0, v);
 
     // ---------------------------------------------------------------- row scales
-    // the largest |re|, |im| of each row of A = G^omega_tc from the block
-    // norms pass: per block of F_tc its row (column basis: column) maxima
-    // times the block's FP32 weight -- the same value as the maximum over the
-    // weighted entries, since rounding a product with a positive factor is
-    // monotonic.  The blocks' offsets and weights are gathered first (one
-    // thread per block), then four threads per row take a quarter of the blocks each.
+    // e_i with every |re|, |im| of row i of A below 2^e_i, from
+    // gram_scales_kernel (over the first m entries of this pair's H slot;
+    // kBadRow marks non-finite entries)
     {
-      const int64_t sg0 = a.seg_begin[side][pid], sg1 = a.seg_begin[side][pid + 1];
-      const int i = tid >> 2;
-      float mx = 0.f;
-      bool bad = false;
-      for (int64_t sb = sg0; sb < sg1; sb += kGramThreads) {
-        const int nb = (int)(sg1 - sb < kGramThreads ? sg1 - sb : kGramThreads);
-        __syncthreads();  // the previous batch of block data has been used
-        if (tid < nb) {
-          const int b = a.seg_blk[side][sb + tid];
-          // the block's maxima: rows of t+ first (row basis), then columns of s+ (column basis)
-          const int cl = side == 0 ? a.bt[b] : a.bs[b];  // the block's cluster on this side
-          sgoff[tid] = a.bmax_off[b] + (side == 0 ? 0 : a.csize[a.bt[b]]) + (r0 - a.cstart[cl]);
-          sgw[tid] = (float)a.invw[b];
-        }
-        __syncthreads();
-        if (i < m)
-#pragma unroll 4
-          for (int k = tid & 3; k < nb; k += 4) {
-            const float x = a.bmax[sgoff[k] + i] * sgw[k];
-            bad = bad || !(x <= FLT_MAX);
-            mx = fmaxf(mx, x);
-          }
+      int bad = 0;
+      if (tid < m) {
+        const int e = __float_as_int(Hout[tid].x);
+        bad = e == kBadRow;
+        rexp[tid] = e;
+        rsc[tid] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
       }
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-      bad = __syncthreads_or(bad);
-      if (bad) {  // non-finite entries: reported, H of this pair left as zero
+      if (__syncthreads_or(bad)) {  // non-finite entries: reported, H of this pair left as zero
         if (tid == 0) atomicOr(a.status, kStatusNaN);
         for (int k = tid; k < mp * mp; k += kGramThreads) Hout[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         continue;
       }
-      if (i < m && (tid & 3) == 0) {
-        int e = 0;
-        if (mx > 0.f) frexpf(mx, &e);  // mx < 2^e
-        rexp[i] = e;
-        rsc[i] = ldexpf(1.f, 6 - e);  // |a| * rsc < 64
-      }
-      __syncthreads();
     }
 #if GP_ON
     GP_T(gb);
@@ -531,30 +581,31 @@ bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t 
   // the whole shared-memory carveout: two CTAs of the 256-column classes per SM
   cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   cudaGetLastError();
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGramThreads, smem);
-  per_sm = std::max(1, std::min(per_sm, (int)(512 / Sh::TCOLS)));
+  // CTAs per SM from the SM's registers and shared memory (the occupancy
+  // query reports one CTA for these kernels where two run side by side),
+  // capped by tensor memory: 512 columns per SM
+  cudaFuncAttributes fa{};
+  int smem_sm = 0, regs_sm = 0;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int regs_cta = ((fa.numRegs * 32 + 255) / 256 * 256) * (kGramThreads / 32);  // per-warp granules of 256
+  const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 1;
+  const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);  // 1 KiB reserved per CTA
+  const int per_sm = std::max(1, std::min(std::min(by_regs, by_smem), (int)(512 / Sh::TCOLS)));
 #ifdef DH2_PROFILE
   {
-    int smem_sm = 0, regs_sm = 0, occ0 = 0, occ64 = 0;
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, kern, kGramThreads, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, kern, kGramThreads, 64 * 1024);
-    std::fprintf(stderr, "dh2 gram<%d> occupancy: %d at %zu B, %d at 0 B, %d at 64 KiB; SM: %d B shared, %d registers\n",
-                 NP, per_sm, smem, occ0, occ64, smem_sm, regs_sm);
-    if (const char* e = std::getenv("DH2_GRAM_PER_SM")) per_sm = std::max(1, std::min(atoi(e), (int)(512 / Sh::TCOLS)));
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kGramThreads, smem);
+    std::fprintf(stderr, "dh2 gram<%d>: %d pairs, %d CTAs per SM (occupancy query: %d), %zu + %zu B shared, %d registers\n",
+                 NP, n, per_sm, occ, smem, fa.sharedSizeBytes, fa.numRegs);
   }
 #endif
   const int grid = std::min(n, nsm * per_sm);
-#ifdef DH2_PROFILE
-  {
-    cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, kern);
-    std::fprintf(stderr, "dh2 gram<%d>: %d pairs, %d CTAs per SM, grid %d, %zu + %zu bytes shared memory, %d registers\n",
-                 NP, n, per_sm, grid, smem, fa.sharedSizeBytes, fa.numRegs);
-  }
-#endif
+  gram_scales_kernel<<<(n + 7) / 8, 256, 0, st>>>(args, codes, n);
   kern<<<grid, kGramThreads, smem, st>>>(args, codes, n);
   return true;
 }
