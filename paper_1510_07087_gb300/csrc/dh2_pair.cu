@@ -362,6 +362,7 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
                               int* pcol, int& K, double& E_K) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int mp = (p + 7) & ~7;
+  DH2_PROF_T(t_h0);
   const float4* Hin = a.H + a.hoff[side][pid];
   for (int idx = tid; idx < p * p; idx += NT) {
     const int r = idx % p, c = idx / p;
@@ -392,12 +393,21 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
   const double tau_d = ldexp(tau, se);
   const Df tau_s{(float)tau_d, (float)(tau_d - (double)(float)tau_d)};
   const float back = ldexpf(1.f, -se / 2);
+  DH2_PROF_T(t_h1);
+  DH2_PROF_ADD(8, t_h1 - t_h0);  // H staged and scaled
+#if DH2_PROF_ON
+  long long pc_n = 0, pc_piv = 0, pc_col = 0;  // columns, cycles of the pivot searches and of the columns
+#endif
   K = p;
   E_K = 0.0;
   __shared__ int sh_pv;
   __shared__ float sh_piv[4];  // sqrt(d_pv) and 1/sqrt(d_pv), double-float
   __shared__ double sh_e;
   for (int j = 0; j < p; ++j) {
+#if DH2_PROF_ON
+    ++pc_n;
+#endif
+    DH2_PROF_T(t_c0);
     // warp 0: Schur trace of the unchosen rows (double-float), the pivot
     // (largest diagonal, lowest row on ties) and its scalars; -1 = stop
     if ((tid >> 5) == 0) {
@@ -438,6 +448,10 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
       }
     }
     __syncthreads();
+    DH2_PROF_T(t_c1);
+#if DH2_PROF_ON
+    pc_piv += t_c1 - t_c0;  // pivot search and its broadcast
+#endif
     const int pv = sh_pv;
     if (pv < 0) {
       K = j;
@@ -472,6 +486,10 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
     const Df lr = df_mul(df_add(Df{h.x, h.y}, df_neg(sre)), inv);
     const Df li = df_mul(df_add(Df{h.z, h.w}, df_neg(sim)), inv);
     __syncthreads();  // column pv of H has been read by every row
+    DH2_PROF_T(t_c2);
+#if DH2_PROF_ON
+    pc_col += t_c2 - t_c1;  // the column's entries
+#endif
     if (live && q == 0) {
       if (row == pv) {
         Hs[pv + pv * P] = make_float4(sq.hi, sq.lo, 0.f, 0.f);
@@ -490,6 +508,11 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
     }
     __syncthreads();
   }
+#if DH2_PROF_ON
+  DH2_PROF_ADD(12, pc_n);
+  DH2_PROF_ADD(13, pc_piv);
+  DH2_PROF_ADD(14, pc_col);
+#endif
 }
 
 // P_T: largest factor size of the instantiation (32, 48, 64 or 128 rows).
