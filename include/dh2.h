@@ -374,6 +374,7 @@ enum {
   DH2_KC_PROJECT = 19,      /* coupling matrices S_b                                             */
   DH2_KC_LEAF_GRAM = 20,    /* + leaf row class 0..3: tensor-core Gram matrices (MIXED_BF16X3)   */
   DH2_KC_GRAM_SCALES = 24,  /* row scales of the leaf Gram matrices (MIXED_BF16X3)               */
+  DH2_KC_LEAF_JACOBI = 25,  /* + leaf row class 0..3: Jacobi, rank and Q after the Cholesky (MIXED) */
   DH2_KC_COUNT = 32
 };
 /* Launches of the last compression that produced M, by kernel class

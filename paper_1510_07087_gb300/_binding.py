@@ -35,6 +35,7 @@ KC_EXPAND = 18
 KC_PROJECT = 19
 KC_LEAF_GRAM = 20
 KC_GRAM_SCALES = 24
+KC_LEAF_JACOBI = 25
 KC_GRAM_SCALES = 24
 KC_COUNT = 32
 

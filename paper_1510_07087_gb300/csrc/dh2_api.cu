@@ -569,6 +569,7 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   pa.invw = M->invw;
   pa.eps2 = M->eps2;
   pa.H = nullptr;  // set by run_compress in the mixed modes
+  pa.L4 = nullptr;
   for (int sd = 0; sd < 2; ++sd) {
     pa.hoff[sd] = D->gram_off[sd];
     pa.rank_ovr[sd] = nullptr;  // set by run_compress when ranks are given
@@ -833,7 +834,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // mixed modes: the leaf Gram matrices (double-float, mp x mp per leaf pair)
   // and the window sums of the pairs with more than one window, per problem
   const bool mixed = mode_mixed(cp.mode);
-  std::vector<size_t> gram_h_off(nprob, 0), gram_v_off(nprob, 0), gram_m_off(nprob, 0);
+  std::vector<size_t> gram_h_off(nprob, 0), gram_l_off(nprob, 0), gram_v_off(nprob, 0), gram_m_off(nprob, 0);
   size_t gram_bytes = 0;
   if (mixed) {
     gram_bytes = align256(sizeof(GramArgs) * nprob);
@@ -841,6 +842,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       const Tree::Dev* D = Ms[i]->tree->tr.dev;
       gram_h_off[i] = gram_bytes;
       if (!Ms[i]->gram) gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);  // else kept by the matrix
+      gram_l_off[i] = gram_bytes;  // Cholesky factors: over H, or beside the kept Gram matrices
+      if (Ms[i]->gram) gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);
       gram_v_off[i] = gram_bytes;
       gram_bytes += align256(sizeof(long long) * (size_t)D->gram_velems);
       gram_m_off[i] = gram_bytes;
@@ -881,6 +884,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       const dh2_matrix* M = Ms[i];
       float4* Hbuf = Ms[i]->gram ? (float4*)Ms[i]->gram : (float4*)(gram_base + gram_h_off[i]);
       pas[i].H = Hbuf;
+      pas[i].L4 = Ms[i]->gram ? (float4*)(gram_base + gram_l_off[i]) : Hbuf;
       GramArgs& g = gas[i];
       for (int sd = 0; sd < 2; ++sd) {
         g.start[sd] = D->start[sd];
@@ -1047,8 +1051,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         counted(DH2_KC_GRAM_SCALES, true);
         counted(DH2_KC_LEAF_GRAM + c, true);
         if (timed) cudaEventRecord(kev[3 * c + 1], st);
+        // pivoted Cholesky, then Jacobi, rank and Q
         ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);
         counted(DH2_KC_LEAF_FACTOR + c, true);
+        counted(DH2_KC_LEAF_JACOBI + c, true);
         if (timed) cudaEventRecord(kev[3 * c + 2], st);
         return;
       }

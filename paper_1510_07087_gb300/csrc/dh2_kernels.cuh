@@ -39,6 +39,7 @@ struct PairArgs {
   int32_t* rank[2];
   const double* eps2;                 // per level eps_l^2
   const float4* H;                    // mixed modes: leaf Gram matrices (see GramArgs)
+  float4* L4;                         // mixed modes: leaf Cholesky factors, pair at L4 + its Gram offset (FP32 complex, ld p)
   const int64_t* hoff[2];             // mixed modes: per pair, first entry of its Gram matrix in H
   const int32_t* rank_ovr[2];         // per pair a rank replacing the truncation rule (< 0: the rule), or NULL
   int32_t max_sweeps;

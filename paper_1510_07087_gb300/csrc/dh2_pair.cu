@@ -355,37 +355,44 @@ __device__ __forceinline__ Df df_shfl_xor(Df x, int o) {
 // keeps the low halves of the products clear of underflow); L is scaled back
 // by 2^(-s/2) as it is written to Lm in FP32, and E_K by 2^-s.
 // Column j of L (double-float) replaces H's column of the j-th pivot, which is
-// read only when that pivot is chosen.  Rows: LPR threads per row.
+// read only when that pivot is chosen; in FP32 it goes to Lg (global, ld p;
+// the pair's Gram slot itself unless the Gram matrices are kept: H has been
+// read into shared memory first).
+// Rows: LPR threads per row.
 template <typename T, int NT, int LPR>
-__device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, int P, int LDL, int row, int q,
-                              bool live, double tau, C2<T>* Lm, float4* Hs, float* dhi, float* dlo, int* piv,
+__device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, int P, int row, int q,
+                              bool live, double tau, C2<T>* Lg, float4* Hs, float* dhi, float* dlo, int* piv,
                               int* pcol, int& K, double& E_K) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int mp = (p + 7) & ~7;
   DH2_PROF_T(t_h0);
   const float4* Hin = a.H + a.hoff[side][pid];
-  for (int idx = tid; idx < p * p; idx += NT) {
-    const int r = idx % p, c = idx / p;
-    Hs[r + c * P] = Hin[r + (int64_t)c * mp];
+  // the scale from the largest diagonal entry (warp 0), then H is read,
+  // scaled (a power of two: exact) and stored in one pass that also fills the
+  // Schur diagonal
+  __shared__ int sh_se;
+  if ((tid >> 5) == 0) {
+    float hmax = 0.f;
+    for (int r = lane; r < p; r += 32) hmax = fmaxf(hmax, Hin[r + (int64_t)r * mp].x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    int eh = 0;
+    if (hmax > 0.f) frexpf(hmax, &eh);
+    if (lane == 0) sh_se = -2 * (eh >> 1);  // even
   }
   if (tid < p) pcol[tid] = -1;
   __syncthreads();
-  float hmax = 0.f;
-  for (int r = lane; r < p; r += 32) hmax = fmaxf(hmax, Hs[r + r * P].x);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
-  int eh = 0;
-  if (hmax > 0.f) frexpf(hmax, &eh);
-  const int se = -2 * (eh >> 1);  // even
-  __syncthreads();                // every warp has read the diagonal
+  const int se = sh_se;
+  const float sc = ldexpf(1.f, se);  // 2^se, se in [-128, 126]: exact (subnormal at the low end)
   for (int idx = tid; idx < p * p; idx += NT) {
-    float4& h = Hs[idx % p + (idx / p) * P];
-    h = make_float4(ldexpf(h.x, se), ldexpf(h.y, se), ldexpf(h.z, se), ldexpf(h.w, se));
-  }
-  __syncthreads();
-  if (tid < p) {
-    dhi[tid] = Hs[tid + tid * P].x;
-    dlo[tid] = Hs[tid + tid * P].y;
+    const int r = idx % p, c = idx / p;
+    const float4 h = Hin[r + (int64_t)c * mp];
+    const float4 hs = make_float4(h.x * sc, h.y * sc, h.z * sc, h.w * sc);
+    Hs[r + c * P] = hs;
+    if (r == c) {
+      dhi[r] = hs.x;
+      dlo[r] = hs.y;
+    }
   }
   __syncthreads();
   // the stopping threshold in the scaled units, as a double-float (the loop
@@ -493,17 +500,18 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
     if (live && q == 0) {
       if (row == pv) {
         Hs[pv + pv * P] = make_float4(sq.hi, sq.lo, 0.f, 0.f);
-        Lm[j * LDL + pv] = C2<T>{(T)((sq.hi + sq.lo) * back), T(0)};
+        Lg[(int64_t)j * p + pv] = C2<T>{(T)((sq.hi + sq.lo) * back), T(0)};
         pcol[pv] = j;
         piv[j] = pv;
       } else if (pcol[row] < 0) {
         Hs[row + pv * P] = make_float4(lr.hi, lr.lo, li.hi, li.lo);
-        Lm[j * LDL + row] = C2<T>{(T)((lr.hi + lr.lo) * back), (T)((li.hi + li.lo) * back)};
+        Lg[(int64_t)j * p + row] = C2<T>{(T)((lr.hi + lr.lo) * back), (T)((li.hi + li.lo) * back)};
         const Df d = df_add(Df{dhi[row], dlo[row]}, df_neg(df_add(df_mul(lr, lr), df_mul(li, li))));
         dhi[row] = d.hi;
         dlo[row] = d.lo;
       } else {
         Hs[row + pv * P] = make_float4(0.f, 0.f, 0.f, 0.f);  // chosen earlier: L[row][j] = 0
+        Lg[(int64_t)j * p + row] = C2<T>{T(0), T(0)};
       }
     }
     __syncthreads();
@@ -537,6 +545,197 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
 #ifndef DH2_JACOBI_TPP
 #define DH2_JACOBI_TPP 32  // most threads per column pair in the Jacobi step (4..32)
 #endif
+// Steps 2-4 of a pair (Jacobi on the K leading columns of L in shared memory,
+// the rank from the tail sums, Q), shared by pair_kernel and
+// gram_jacobi_kernel.
+template <typename T, int P_T, int NT>
+__device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, int pid, int p, int LDL, int K,
+                                              double E_K, int kcap, int lvl, C2<T>* Lm, double* sig2, int* ord,
+                                              int32_t* rank_out, double* sig_out, long long t_b) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  __shared__ int sh_rot[2];
+  __shared__ int sh_k;
+  (void)t_b;
+  // ---------------------------------------------------------------- 2. Jacobi
+  // one column pair per group of tpp threads (as many as the pe/2 pairs of a
+  // round allow, 4..32); round-robin ordering over pe columns
+  const int pe = K + (K & 1);
+  const T tol = T(p) * Eps<T>::u;
+  constexpr int JH = (P_T / 2 + NT / 4 - 1) / (NT / 4);  // pairs per group at most
+  int tpp = DH2_JACOBI_TPP;
+  while (tpp > 4 && tpp * (pe / 2) > NT) tpp >>= 1;
+  const int jng = NT / tpp;
+  const int jg = tid / tpp, jl = tid & (tpp - 1);
+  if (tid == 0) {
+    sh_rot[0] = 0;
+    sh_rot[1] = 0;
+  }
+  __syncthreads();
+  bool conv = pe < 2;
+  int nsweeps = 0;
+  for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
+    ++nsweeps;
+    const int sp = sweep & 1;
+    // round-robin positions of this group's pairs in round 0; each round
+    // moves every position but the fixed one (index 0) by one place
+    int ia[JH], ib[JH];
+#pragma unroll
+    for (int h = 0; h < JH; ++h) {
+      const int kk = jg + h * jng;
+      ia[h] = kk;
+      ib[h] = pe - 1 - kk;
+    }
+    for (int rd = 0; rd < pe - 1; ++rd) {
+#pragma unroll
+      for (int h = 0; h < JH; ++h) {
+        const int kk = jg + h * jng;
+        // warps with an active group run the reductions converged (full mask)
+        if ((warp * 32) / tpp + h * jng < pe / 2) {
+          const bool act = kk < pe / 2;
+          C2<T>* ca = Lm + (act ? ia[h] : 0) * LDL;
+          C2<T>* cb = Lm + (act ? ib[h] : 0) * LDL;
+          T al = T(0), be = T(0);
+          C2<T> ga = czero<T>();
+          if (act)
+            for (int r = jl; r < p; r += tpp) {
+              const C2<T> xa = ca[r], xb = cb[r];
+              al = nmac(al, xa);
+              be = nmac(be, xb);
+              ga = cmacc(ga, xb, xa);  // + conj(xa) * xb
+            }
+          for (int o = 1; o < tpp; o <<= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, o);
+            be += __shfl_xor_sync(0xffffffffu, be, o);
+            ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
+            ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
+          }
+          const T g2 = cnorm2(ga);
+          // rotate unless the pair is orthogonal to tol (relative)
+          // rotation scalars from reciprocal square roots and one quotient
+          // (hardware approximations in FP32, a few ulp): c^2 + s^2 = 1 to
+          // that level, far inside the convergence test's tol = p u
+          const T rg = frsqrt(g2);
+          if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
+              g2 * rg * frsqrt(al) * frsqrt(be) > tol) {
+            const T zt = (be - al) * T(0.5) * rg;
+            const T az = fabs(zt);
+            const T q1 = T(1) + zt * zt;
+            const T t = (zt >= T(0) ? T(1) : T(-1)) *
+                        (az > T(1e15) ? fdiv(T(0.5), az) : fdiv(T(1), az + q1 * frsqrt(q1)));
+            const T c = frsqrt(T(1) + t * t);
+            const T s = t * c;
+            if (s != T(0)) {
+              const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
+              for (int r = jl; r < p; r += tpp) {
+                const C2<T> xa = ca[r];
+                const C2<T> eb = cmul(e, cb[r]);
+                ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
+                cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
+              }
+              if (jl == 0) sh_rot[sp] = 1;
+            }
+          }
+          if (act) {
+            if (kk > 0) ia[h] = ia[h] == pe - 1 ? 1 : ia[h] + 1;
+            ib[h] = ib[h] == pe - 1 ? 1 : ib[h] + 1;
+          }
+        }
+      }
+      __syncthreads();
+      if (rd == 0 && tid == 0) sh_rot[sp ^ 1] = 0;
+    }
+    const int rot = sh_rot[sp];
+    __syncthreads();
+    if (rot == 0) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv && tid == 0) atomicOr(a.status, kStatusNoConv);
+  DH2_PROF_T(t_c);
+  DH2_PROF_ADD(1, t_c - t_b);
+  DH2_PROF_ADD(4, nsweeps);
+  DH2_PROF_ADD(5, 1);
+  DH2_PROF_ADD(6, p);
+  DH2_PROF_ADD(7, K);
+  (void)nsweeps;
+
+  // ---------------------------------------------------------------- 3. rank
+  const int grp = tid >> 3, gl = tid & 7;
+  for (int jb = 0; jb < K; jb += NT / 8) {
+    const int j = jb + grp;
+    T s = T(0);
+    if (j < K)
+      for (int r = gl; r < p; r += 8) s = nmac(s, Lm[j * LDL + r]);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (j < K && gl == 0) sig2[j] = (double)s;
+  }
+  __syncthreads();
+  // non-finite values (only from non-finite input) are ranked as zero and
+  // reported; ord stays a permutation of 0..p-1 in every case
+  if (tid < K) {
+    ord[tid] = tid;
+    if (!(sig2[tid] >= 0.0 && sig2[tid] <= 1.0e300)) {
+      sig2[tid] = 0.0;
+      atomicOr(a.status, kStatusNaN);
+    }
+  }
+  __syncthreads();
+  int rk = -1;
+  if (tid < K) {
+    const double v = sig2[tid];
+    rk = 0;
+    for (int i = 0; i < K; ++i) {
+      const double u = sig2[i];
+      rk += (u > v) || (u == v && i < tid);
+    }
+  }
+  __syncthreads();
+  if (rk >= 0 && rk < K) ord[rk] = tid;
+  __syncthreads();
+  if (tid == 0) {
+    const double e2 = a.eps2[lvl];
+    double tail = E_K;
+    int k = K;
+    for (int r = K - 1; r >= 0; --r) {
+      const double v = sig2[ord[r]];
+      if (tail + v <= e2) {
+        tail += v;
+        k = r;
+      } else {
+        break;
+      }
+    }
+    if (a.rank_ovr[side] && a.rank_ovr[side][pid] >= 0) k = min(a.rank_ovr[side][pid], K);
+    if (k > kcap) k = kcap;
+    sh_k = k;
+    *rank_out = k;
+  }
+  for (int r = tid; r < kSigValues; r += NT) sig_out[r] = r < K ? sqrt(sig2[ord[r]]) : 0.0;
+  if (tid == 0) {
+    sig_out[kSigValues] = (double)K;    // singular values resolved individually
+    sig_out[kSigValues + 1] = E_K;      // energy of the rest (sum of their squares)
+  }
+  __syncthreads();
+  const int k = sh_k;
+
+  // ---------------------------------------------------------------- 4. Q
+  C2<T>* Qout = a.Q[side] + a.Qoff[side][pid];
+  const int ldq = a.rowcap[side][pid];
+  for (int qq = grp; qq < k; qq += NT / 8) {
+    const int j = ord[qq];
+    const T inv = frsqrt((T)sig2[j]);
+    for (int r = gl; r < p; r += 8) {
+      const C2<T> v = Lm[j * LDL + r];
+      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
+        Qout[r + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
+    }
+  }
+  DH2_PROF_T(t_d);
+  DH2_PROF_ADD(2, t_d - t_c);
+}
+
 template <int NT, typename T>
 constexpr int pair_min_blocks() {
   return sizeof(T) == 4 ? (NT >= 256   ? DH2_PAIR_MINB
@@ -568,14 +767,12 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
   __shared__ int cgc[64];
   __shared__ T cwt[64];
   static_assert(C <= 64, "chunk column table");
-  __shared__ int sh_rot[2];
-  __shared__ int sh_k;
 
   const int LDL = P + 1;              // column-major L: element (r, c) at c * LDL + r
-  C2<T>* Lm = reinterpret_cast<C2<T>*>(smem);
-  size_t soff = ((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15;
+  C2<T>* Lm = reinterpret_cast<C2<T>*>(smem);  // (Gram factors: L goes to global memory)
+  size_t soff = GRAM ? 0 : ((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15;
   C2<T>* vbuf = reinterpret_cast<C2<T>*>(smem + soff);  // 2 x C reflection vectors
-  soff += 2 * C * sizeof(C2<T>);
+  soff += GRAM ? 0 : 2 * C * sizeof(C2<T>);
   double* sig2 = reinterpret_cast<double*>(smem + soff);
   soff += (size_t)P * sizeof(double);
   int* ord = reinterpret_cast<int*>(smem + soff);
@@ -649,19 +846,18 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     return;
   }
 
-  for (int i = tid; i < P * LDL; i += NT) Lm[i] = czero<T>();  // L; the staging columns need none
+  if constexpr (!GRAM)
+    for (int i = tid; i < P * LDL; i += NT) Lm[i] = czero<T>();  // L; the staging columns need none
   DH2_PROF_T(t_a);
   const int row = tid / LPR, q = tid % LPR;  // row mapping of the pivoted steps (1b / 1')
   const bool live = row < p;
   const double drop = sizeof(T) == 4 ? 1e-2 : 1e-10;
   int K = p;         // columns kept for the Jacobi step
   double E_K = 0.0;  // energy left out of them
-#if DH2_PROF_ON
-  long long t_b = 0;
-#endif
+  long long t_b = 0;  // start of the Jacobi step (profile build)
   if constexpr (GRAM) {
-    gram_cholesky<T, NT, LPR>(a, side, pid, p, P, LDL, row, q, live, drop * a.eps2[lvl], Lm, Hs, nu, dlo, piv, pcol,
-                              K, E_K);
+    gram_cholesky<T, NT, LPR>(a, side, pid, p, P, row, q, live, drop * a.eps2[lvl],
+                              reinterpret_cast<C2<T>*>(a.L4 + a.hoff[side][pid]), Hs, nu, dlo, piv, pcol, K, E_K);
 #if DH2_PROF_ON
     t_b = clock64();
 #endif
@@ -1062,6 +1258,19 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     if (tid == 0) atomicOr(a.status, kStatusNaN);
     E_K = 0.0;
   }
+  if constexpr (GRAM) {
+    // L (columns < K) is in the factor buffer; a zero column pads it to
+    // even width; K and E_K go to the singular-value record, and
+    // gram_jacobi_kernel takes it from there
+    C2<T>* Lg = reinterpret_cast<C2<T>*>(a.L4 + a.hoff[side][pid]);
+    if (K & 1)
+      for (int i = tid; i < p; i += NT) Lg[(int64_t)K * p + i] = czero<T>();
+    if (tid == 0) {
+      sig_out[kSigValues] = (double)K;
+      sig_out[kSigValues + 1] = E_K;
+    }
+    return;
+  }
   // chosen rows keep their reflector vectors right of their pivot column and
   // unchosen rows their residual right of column K: clear what the Jacobi step
   // reads (columns < pe, pe = K rounded up to even)
@@ -1073,184 +1282,48 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     }
   }
   __syncthreads();
-  // ---------------------------------------------------------------- 2. Jacobi
-  // one column pair per group of tpp threads (as many as the pe/2 pairs of a
-  // round allow, 4..32); round-robin ordering over pe columns
+  jacobi_rank_q<T, P_T, NT>(a, side, pid, p, LDL, K, E_K, kcap, lvl, Lm, sig2, ord, rank_out, sig_out, t_b);
+}
+
+// Steps 2-4 of the leaf pairs of a mixed-mode launch list, after the
+// pivoted Cholesky of their Gram matrices (pair_kernel<..., GRAM>): L (p x K,
+// ld p, columns < K rounded up to even) from the factor buffer L4, K and E_K
+// from its singular-value record.  Only L is held in shared memory, so that
+// more pairs run side by side than in the Cholesky, whose shared memory holds
+// all of H.
+template <int P_T, int NT>
+__global__ void __launch_bounds__(NT, 2048 / NT - 4)
+    gram_jacobi_kernel(const PairArgs<float>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int LDL = P + 1;
+  C2<float>* Lm = reinterpret_cast<C2<float>*>(smem);
+  size_t soff = ((size_t)P * LDL * sizeof(C2<float>) + 15) & ~(size_t)15;
+  double* sig2 = reinterpret_cast<double*>(smem + soff);
+  soff += (size_t)P * sizeof(double);
+  int* ord = reinterpret_cast<int*>(smem + soff);
+  const int tid = threadIdx.x;
+  const uint32_t code = codes[blockIdx.x];
+  const PairArgs<float>& a = args[code >> kCodeProbShift];
+  const int side = (int)((code >> kCodeSideShift) & 1u);
+  const int pid = (int)(code & kCodePairMask);
+  if (!DH2_IN(pid, c_lim.npairs[side], 14, pid)) return;
+  const int p = a.m[side][pid];
+  const int N = a.ncols[side][pid];
+  if (p > P || p > P_T || p == 0 || N == 0) return;  // rank and record already written by the Cholesky launch
+  int32_t* rank_out = a.rank[side] + pid;
+  double* sig_out = a.sig[side] + (int64_t)pid * kSigStride;
+  const int K = (int)sig_out[kSigValues];
+  const double E_K = sig_out[kSigValues + 1];
   const int pe = K + (K & 1);
-  const T tol = T(p) * Eps<T>::u;
-  constexpr int JH = (P_T / 2 + NT / 4 - 1) / (NT / 4);  // pairs per group at most
-  int tpp = DH2_JACOBI_TPP;
-  while (tpp > 4 && tpp * (pe / 2) > NT) tpp >>= 1;
-  const int jng = NT / tpp;
-  const int jg = tid / tpp, jl = tid & (tpp - 1);
-  if (tid == 0) {
-    sh_rot[0] = 0;
-    sh_rot[1] = 0;
-  }
+  const C2<float>* Lg = reinterpret_cast<const C2<float>*>(a.L4 + a.hoff[side][pid]);
+  for (int i = tid; i < pe * p; i += NT) Lm[(i / p) * LDL + i % p] = Lg[i];
   __syncthreads();
-  bool conv = pe < 2;
-  int nsweeps = 0;
-  for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
-    ++nsweeps;
-    const int sp = sweep & 1;
-    // round-robin positions of this group's pairs in round 0; each round
-    // moves every position but the fixed one (index 0) by one place
-    int ia[JH], ib[JH];
-#pragma unroll
-    for (int h = 0; h < JH; ++h) {
-      const int kk = jg + h * jng;
-      ia[h] = kk;
-      ib[h] = pe - 1 - kk;
-    }
-    for (int rd = 0; rd < pe - 1; ++rd) {
-#pragma unroll
-      for (int h = 0; h < JH; ++h) {
-        const int kk = jg + h * jng;
-        // warps with an active group run the reductions converged (full mask)
-        if ((warp * 32) / tpp + h * jng < pe / 2) {
-          const bool act = kk < pe / 2;
-          C2<T>* ca = Lm + (act ? ia[h] : 0) * LDL;
-          C2<T>* cb = Lm + (act ? ib[h] : 0) * LDL;
-          T al = T(0), be = T(0);
-          C2<T> ga = czero<T>();
-          if (act)
-            for (int r = jl; r < p; r += tpp) {
-              const C2<T> xa = ca[r], xb = cb[r];
-              al = nmac(al, xa);
-              be = nmac(be, xb);
-              ga = cmacc(ga, xb, xa);  // + conj(xa) * xb
-            }
-          for (int o = 1; o < tpp; o <<= 1) {
-            al += __shfl_xor_sync(0xffffffffu, al, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
-            ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
-          }
-          const T g2 = cnorm2(ga);
-          // rotate unless the pair is orthogonal to tol (relative)
-          // rotation scalars from reciprocal square roots and one quotient
-          // (hardware approximations in FP32, a few ulp): c^2 + s^2 = 1 to
-          // that level, far inside the convergence test's tol = p u
-          const T rg = frsqrt(g2);
-          if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
-              g2 * rg * frsqrt(al) * frsqrt(be) > tol) {
-            const T zt = (be - al) * T(0.5) * rg;
-            const T az = fabs(zt);
-            const T q1 = T(1) + zt * zt;
-            const T t = (zt >= T(0) ? T(1) : T(-1)) *
-                        (az > T(1e15) ? fdiv(T(0.5), az) : fdiv(T(1), az + q1 * frsqrt(q1)));
-            const T c = frsqrt(T(1) + t * t);
-            const T s = t * c;
-            if (s != T(0)) {
-              const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
-              for (int r = jl; r < p; r += tpp) {
-                const C2<T> xa = ca[r];
-                const C2<T> eb = cmul(e, cb[r]);
-                ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
-                cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
-              }
-              if (jl == 0) sh_rot[sp] = 1;
-            }
-          }
-          if (act) {
-            if (kk > 0) ia[h] = ia[h] == pe - 1 ? 1 : ia[h] + 1;
-            ib[h] = ib[h] == pe - 1 ? 1 : ib[h] + 1;
-          }
-        }
-      }
-      __syncthreads();
-      if (rd == 0 && tid == 0) sh_rot[sp ^ 1] = 0;
-    }
-    const int rot = sh_rot[sp];
-    __syncthreads();
-    if (rot == 0) {
-      conv = true;
-      break;
-    }
-  }
-  if (!conv && tid == 0) atomicOr(a.status, kStatusNoConv);
-  DH2_PROF_T(t_c);
-  DH2_PROF_ADD(1, t_c - t_b);
-  DH2_PROF_ADD(4, nsweeps);
-  DH2_PROF_ADD(5, 1);
-  DH2_PROF_ADD(6, p);
-  DH2_PROF_ADD(7, K);
-  (void)nsweeps;
-
-  // ---------------------------------------------------------------- 3. rank
-  const int grp = tid >> 3, gl = tid & 7;
-  for (int jb = 0; jb < K; jb += NT / 8) {
-    const int j = jb + grp;
-    T s = T(0);
-    if (j < K)
-      for (int r = gl; r < p; r += 8) s = nmac(s, Lm[j * LDL + r]);
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (j < K && gl == 0) sig2[j] = (double)s;
-  }
-  __syncthreads();
-  // non-finite values (only from non-finite input) are ranked as zero and
-  // reported; ord stays a permutation of 0..p-1 in every case
-  if (tid < K) {
-    ord[tid] = tid;
-    if (!(sig2[tid] >= 0.0 && sig2[tid] <= 1.0e300)) {
-      sig2[tid] = 0.0;
-      atomicOr(a.status, kStatusNaN);
-    }
-  }
-  __syncthreads();
-  int rk = -1;
-  if (tid < K) {
-    const double v = sig2[tid];
-    rk = 0;
-    for (int i = 0; i < K; ++i) {
-      const double u = sig2[i];
-      rk += (u > v) || (u == v && i < tid);
-    }
-  }
-  __syncthreads();
-  if (rk >= 0 && rk < K) ord[rk] = tid;
-  __syncthreads();
-  if (tid == 0) {
-    const double e2 = a.eps2[lvl];
-    double tail = E_K;
-    int k = K;
-    for (int r = K - 1; r >= 0; --r) {
-      const double v = sig2[ord[r]];
-      if (tail + v <= e2) {
-        tail += v;
-        k = r;
-      } else {
-        break;
-      }
-    }
-    if (a.rank_ovr[side] && a.rank_ovr[side][pid] >= 0) k = min(a.rank_ovr[side][pid], K);
-    if (k > kcap) k = kcap;
-    sh_k = k;
-    *rank_out = k;
-  }
-  for (int r = tid; r < kSigValues; r += NT) sig_out[r] = r < K ? sqrt(sig2[ord[r]]) : 0.0;
-  if (tid == 0) {
-    sig_out[kSigValues] = (double)K;    // singular values resolved individually
-    sig_out[kSigValues + 1] = E_K;      // energy of the rest (sum of their squares)
-  }
-  __syncthreads();
-  const int k = sh_k;
-
-  // ---------------------------------------------------------------- 4. Q
-  C2<T>* Qout = a.Q[side] + a.Qoff[side][pid];
-  const int ldq = a.rowcap[side][pid];
-  for (int qq = grp; qq < k; qq += NT / 8) {
-    const int j = ord[qq];
-    const T inv = frsqrt((T)sig2[j]);
-    for (int r = gl; r < p; r += 8) {
-      const C2<T> v = Lm[j * LDL + r];
-      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
-        Qout[r + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
-    }
-  }
-  DH2_PROF_T(t_d);
-  DH2_PROF_ADD(2, t_d - t_c);
+  long long t_b = 0;
+#if DH2_PROF_ON
+  t_b = clock64();
+#endif
+  jacobi_rank_q<float, P_T, NT>(a, side, pid, p, LDL, K, E_K, a.kcap[side][pid], a.level[side][pid], Lm, sig2, ord,
+                                rank_out, sig_out, t_b);
 }
 
 // R_tc = Q^* A for the pairs of one launch (Section 6, R recursion: R_tc =
@@ -1609,7 +1682,7 @@ bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int
   constexpr int C = 16 * (NT / P_T);
   constexpr int XTRA = GRAM ? 0 : C;
   const int LDL = P + 1;
-  size_t smem = (((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>) +
+  size_t smem = (GRAM ? 0 : (((size_t)(P + XTRA) * LDL * sizeof(C2<T>) + 15) & ~(size_t)15) + 2 * C * sizeof(C2<T>)) +
                 (size_t)P * sizeof(double) + 2 * (size_t)P * sizeof(int) + (size_t)P * sizeof(T);
   if (GRAM) smem = ((smem + 15) & ~(size_t)15) + (size_t)P * P * sizeof(float4) + (size_t)P * (sizeof(float) + sizeof(int));
   auto kern = pair_kernel<T, P_T, FROM_R, NT, GRAM>;
@@ -1740,12 +1813,23 @@ bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
   return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st, count);
 }
 
+template <int P_T, int NT>
+bool launch_gram_factor(const PairArgs<float>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
+  if (!launch_one<float, P_T, false, NT, true>(args, codes, nblocks, P, st)) return false;
+  const size_t smem = (((size_t)P * (P + 1) * sizeof(C2<float>) + 15) & ~(size_t)15) + (size_t)P * sizeof(double) +
+                      (size_t)P * sizeof(int);
+  auto kern = gram_jacobi_kernel<P_T, NT>;
+  if (!set_smem(kern, smem)) return false;
+  kern<<<nblocks, NT, smem, st>>>(args, codes, P);
+  return true;
+}
+
 bool launch_pair_kernel_gram(const PairArgs<float>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
   if (nblocks <= 0) return true;
-  if (P <= 32) return launch_one<float, 32, false, 128, true>(args, codes, nblocks, P, st);
-  if (P <= 40) return launch_one<float, 40, false, 160, true>(args, codes, nblocks, P, st);
-  if (P <= 48) return launch_one<float, 48, false, 192, true>(args, codes, nblocks, P, st);
-  if (P <= 64) return launch_one<float, 64, false, 256, true>(args, codes, nblocks, P, st);
+  if (P <= 32) return launch_gram_factor<32, 128>(args, codes, nblocks, P, st);
+  if (P <= 40) return launch_gram_factor<40, 160>(args, codes, nblocks, P, st);
+  if (P <= 48) return launch_gram_factor<48, 192>(args, codes, nblocks, P, st);
+  if (P <= 64) return launch_gram_factor<64, 256>(args, codes, nblocks, P, st);
   return false;
 }
 
