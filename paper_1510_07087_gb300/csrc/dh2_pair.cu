@@ -384,9 +384,10 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
   __syncthreads();
   const int se = sh_se;
   const float sc = ldexpf(1.f, se);  // 2^se, se in [-128, 126]: exact (subnormal at the low end)
+#pragma unroll 4
   for (int idx = tid; idx < p * p; idx += NT) {
     const int r = idx % p, c = idx / p;
-    const float4 h = Hin[r + (int64_t)c * mp];
+    const float4 h = __ldg(Hin + r + (int64_t)c * mp);
     const float4 hs = make_float4(h.x * sc, h.y * sc, h.z * sc, h.w * sc);
     Hs[r + c * P] = hs;
     if (r == c) {
@@ -1589,41 +1590,45 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
     }
     issue_q(x, s, 0);
   };
-  // 2 x 2 output tiles of block qb; entries past kb or cw are read (finite or
-  // not) but never stored
+  // outputs of block qb: lane = column of the tile, warp w = a quarter of the
+  // block's rows of R (QB / 4 at most); per row r of A one entry of A per
+  // lane and the warp's Q entries, read by all lanes at one address
+  // (broadcast).  Entries past kb or cw are formed (finite or not) but never
+  // stored.
+  static_assert(TW == 32 && NT == 128 && QB % 8 == 0, "one column per lane, four warps over the rows of R");
+  constexpr int QW = QB / 4;  // rows of R per warp
   auto products = [&](const RqLeafTile<T>& x, int s, int slot, int qb) {
     const C2<T>* Qs = stQ(s);
     const C2<T>* As = stA(s);
     const int kb = min(QB, x.k - qb);
-    const int nqt = (kb + 1) >> 1, njt = (x.cw + 1) >> 1;
+    const int jj = tid & 31, q0 = (tid >> 5) * QW;
+    if (q0 >= kb) return;
     const T sg = x.side == 0 ? T(1) : T(-1);  // conj(Q) for the row basis, Q for the column basis
-    for (int u = tid; u < nqt * njt; u += NT) {
-      const int q0 = 2 * (u % nqt), jb = 2 * (u / nqt);
-      const C2<T>* qp = Qs + q0;
-      const C2<T>* ap = As + jb;
-      C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
+    C2<T> acc[QW];
+#pragma unroll
+    for (int i = 0; i < QW; ++i) acc[i] = czero<T>();
+    const C2<T>* qp = Qs + q0;
+    const C2<T>* ap = As + jj;
 #pragma unroll 2
-      for (int r = 0; r < x.p; ++r, qp += LQ, ap += LA) {
-        C2<T> x0, x1, y0, y1;
-        load_c2x2(qp, x0, x1);
-        load_c2x2(ap, y0, y1);
+    for (int r = 0; r < x.p; ++r, qp += LQ, ap += LA) {
+      const C2<T> y = *ap;
+#pragma unroll
+      for (int i = 0; i < QW; i += 2) {
+        C2<T> x0, x1;
+        load_c2x2(qp + i, x0, x1);
         x0.im *= sg;
         x1.im *= sg;
-        c00 = cmacc(c00, y0, x0);
-        c01 = cmacc(c01, y1, x0);
-        c10 = cmacc(c10, y0, x1);
-        c11 = cmacc(c11, y1, x1);
+        acc[i] = cmacc(acc[i], y, x0);
+        acc[i + 1] = cmacc(acc[i + 1], y, x1);
       }
+    }
+    if (jj < x.cw) {
+      const T w = cwt[slot][jj];
+      const int64_t e0 = qb + q0 + (int64_t)(x.j0 + jj) * x.kcap;
 #pragma unroll
-      for (int d = 0; d < 4; ++d) {
-        const int qq = q0 + (d >> 1), jj = jb + (d & 1);
-        if (qq < kb && jj < x.cw) {
-          const C2<T> v = d == 0 ? c00 : d == 1 ? c01 : d == 2 ? c10 : c11;
-          const T w = cwt[slot][jj];
-          const int64_t e = (qb + qq) + (int64_t)(x.j0 + jj) * x.kcap;
-          if (DH2_IN(x.roff + e, c_lim.R[x.side], 11, x.pid)) x.R[e] = C2<T>{v.re * w, sg * v.im * w};
-        }
-      }
+      for (int i = 0; i < QW; ++i)
+        if (q0 + i < kb && DH2_IN(x.roff + e0 + i, c_lim.R[x.side], 11, x.pid))
+          x.R[e0 + i] = C2<T>{acc[i].re * w, sg * acc[i].im * w};
     }
   };
 
