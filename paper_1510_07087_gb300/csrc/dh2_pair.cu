@@ -549,109 +549,31 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
 // Steps 2-4 of a pair (Jacobi on the K leading columns of L in shared memory,
 // the rank from the tail sums, Q), shared by pair_kernel and
 // gram_jacobi_kernel.
-//
-// QR = true (gram_jacobi_kernel): Lm holds R (K x K upper triangular, the
-// rows below K zero) of the Householder QR L = H_0 ... H_{K-1} [R; 0] and p is
-// K; the reflectors H_j = I - tauH[j] v_j v_j^* (v_j in column j of Vm, rows
-// >= j) turn the kept normalised columns of R J into the columns of Q (prow
-// rows).  Since R^* R = L^* L, the rotations, singular values and rank are
-// those of L itself.  Up to 16 columns of at most 16 rows, all pairs of a
-// round fit in warp 0 (a power-of-two group of lanes per pair) and a round
-// ends with a warp barrier only.
-template <typename T, int P_T, int NT, bool QR = false>
+template <typename T, int P_T, int NT>
 __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, int pid, int p, int LDL, int K,
                                               double E_K, int kcap, int lvl, C2<T>* Lm, double* sig2, int* ord,
-                                              int32_t* rank_out, double* sig_out, long long t_b,
-                                              const C2<T>* Vm = nullptr, const T* tauH = nullptr, int prow = 0) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+                                              int32_t* rank_out, double* sig_out, long long t_b) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   __shared__ int sh_rot[2];
   __shared__ int sh_k;
   (void)t_b;
-  (void)lane;
   // ---------------------------------------------------------------- 2. Jacobi
   // one column pair per group of tpp threads (as many as the pe/2 pairs of a
   // round allow, 4..32); round-robin ordering over pe columns
   const int pe = K + (K & 1);
-  const T tol = T(QR ? prow : p) * Eps<T>::u;
+  const T tol = T(p) * Eps<T>::u;
   constexpr int JH = (P_T / 2 + NT / 4 - 1) / (NT / 4);  // pairs per group at most
   int tpp = DH2_JACOBI_TPP;
   while (tpp > 4 && tpp * (pe / 2) > NT) tpp >>= 1;
   const int jng = NT / tpp;
   const int jg = tid / tpp, jl = tid & (tpp - 1);
-  bool conv = pe < 2;
-  int nsweeps = 0;
-  if (QR && pe <= 16 && p <= 16) {
-    __shared__ int sh_conv;
-    if (warp == 0) {
-      int tw = 32;
-      while (tw * (pe / 2) > 32) tw >>= 1;
-      const int g = lane / tw, l = lane & (tw - 1);
-      const bool act = g < pe / 2;
-      for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
-        ++nsweeps;
-        int ia = g, ib = pe - 1 - g;  // this group's pair in round 0
-        bool rot = false;
-        for (int rd = 0; rd < pe - 1; ++rd) {
-          C2<T>* ca = Lm + (act ? ia : 0) * LDL;
-          C2<T>* cb = Lm + (act ? ib : 0) * LDL;
-          T al = T(0), be = T(0);
-          C2<T> ga = czero<T>();
-          if (act)
-            for (int r = l; r < p; r += tw) {
-              const C2<T> xa = ca[r], xb = cb[r];
-              al = nmac(al, xa);
-              be = nmac(be, xb);
-              ga = cmacc(ga, xb, xa);  // + conj(xa) * xb
-            }
-          for (int o = 1; o < tw; o <<= 1) {
-            al += __shfl_xor_sync(0xffffffffu, al, o);
-            be += __shfl_xor_sync(0xffffffffu, be, o);
-            ga.re += __shfl_xor_sync(0xffffffffu, ga.re, o);
-            ga.im += __shfl_xor_sync(0xffffffffu, ga.im, o);
-          }
-          const T g2 = cnorm2(ga);
-          const T rg = frsqrt(g2);
-          if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
-              g2 * rg * frsqrt(al) * frsqrt(be) > tol) {
-            const T zt = (be - al) * T(0.5) * rg;
-            const T az = fabs(zt);
-            const T q1 = T(1) + zt * zt;
-            const T t = (zt >= T(0) ? T(1) : T(-1)) *
-                        (az > T(1e15) ? fdiv(T(0.5), az) : fdiv(T(1), az + q1 * frsqrt(q1)));
-            const T c = frsqrt(T(1) + t * t);
-            const T sn = t * c;
-            if (sn != T(0)) {
-              const C2<T> e = C2<T>{ga.re * rg, -ga.im * rg};  // e^{-i arg gamma}
-              for (int r = l; r < p; r += tw) {
-                const C2<T> xa = ca[r];
-                const C2<T> eb = cmul(e, cb[r]);
-                ca[r] = C2<T>{c * xa.re - sn * eb.re, c * xa.im - sn * eb.im};
-                cb[r] = C2<T>{sn * xa.re + c * eb.re, sn * xa.im + c * eb.im};
-              }
-              rot = true;
-            }
-          }
-          if (act) {
-            if (g > 0) ia = ia == pe - 1 ? 1 : ia + 1;
-            ib = ib == pe - 1 ? 1 : ib + 1;
-          }
-          __syncwarp();
-        }
-        if (!__any_sync(0xffffffffu, rot)) {
-          conv = true;
-          break;
-        }
-      }
-      if (lane == 0) sh_conv = conv ? 1 : 0;
-    }
-    __syncthreads();
-    conv = sh_conv != 0;
-  } else {
   if (tid == 0) {
     sh_rot[0] = 0;
     sh_rot[1] = 0;
   }
   __syncthreads();
+  bool conv = pe < 2;
+  int nsweeps = 0;
   for (int sweep = 0; sweep < a.max_sweeps && pe >= 2; ++sweep) {
     ++nsweeps;
     const int sp = sweep & 1;
@@ -730,7 +652,6 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
       break;
     }
   }
-  }  // CTA-wide rounds
   if (!conv && tid == 0) atomicOr(a.status, kStatusNoConv);
   DH2_PROF_T(t_c);
   DH2_PROF_ADD(1, t_c - t_b);
@@ -803,38 +724,13 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
   // ---------------------------------------------------------------- 4. Q
   C2<T>* Qout = a.Q[side] + a.Qoff[side][pid];
   const int ldq = a.rowcap[side][pid];
-  if constexpr (QR) {
-    // one warp per kept column x (rows < K of R J, zero below): x <- H_0 (...
-    // (H_{K-1} x)), each reflector a reduction over the lanes; no CTA barrier
-    for (int qq = warp; qq < k; qq += NT / 32) {
-      C2<T>* x = Lm + ord[qq] * LDL;
-      for (int j = K - 1; j >= 0; --j) {
-        const C2<T>* v = Vm + j * LDL;
-        C2<T> d = czero<T>();
-        for (int r = j + lane; r < prow; r += 32) d = cmacc(d, x[r], v[r]);  // + conj(v) x
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          d.re += __shfl_xor_sync(0xffffffffu, d.re, o);
-          d.im += __shfl_xor_sync(0xffffffffu, d.im, o);
-        }
-        const C2<T> td = C2<T>{tauH[j] * d.re, tauH[j] * d.im};
-        for (int r = j + lane; r < prow; r += 32) x[r] = csub(x[r], cmul(td, v[r]));
-        __syncwarp();
-      }
-      const T inv = frsqrt((T)sig2[ord[qq]]);
-      for (int r = lane; r < prow; r += 32)
-        if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
-          Qout[r + (int64_t)qq * ldq] = C2<T>{x[r].re * inv, x[r].im * inv};
-    }
-  } else {
-    for (int qq = grp; qq < k; qq += NT / 8) {
-      const int j = ord[qq];
-      const T inv = frsqrt((T)sig2[j]);
-      for (int r = gl; r < p; r += 8) {
-        const C2<T> v = Lm[j * LDL + r];
-        if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
-          Qout[r + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
-      }
+  for (int qq = grp; qq < k; qq += NT / 8) {
+    const int j = ord[qq];
+    const T inv = frsqrt((T)sig2[j]);
+    for (int r = gl; r < p; r += 8) {
+      const C2<T> v = Lm[j * LDL + r];
+      if (DH2_IN(a.Qoff[side][pid] + r + (int64_t)qq * ldq, c_lim.Q[side], 10, pid))
+        Qout[r + (int64_t)qq * ldq] = C2<T>{v.re * inv, v.im * inv};
     }
   }
   DH2_PROF_T(t_d);
@@ -1392,32 +1288,23 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
 
 // Steps 2-4 of the leaf pairs of a mixed-mode launch list, after the
 // pivoted Cholesky of their Gram matrices (pair_kernel<..., GRAM>): L (p x K,
-// ld p) from the factor buffer L4, K and E_K from its singular-value record.
-// L is reduced to the K x K triangle R by Householder reflections first, so
-// that the Jacobi rounds run on columns of K rather than p entries (in one
-// warp up to K = 16); Q is formed from the kept columns of R J by the same
-// reflections.  Only L and R are held in shared memory, so that more pairs
-// run side by side than in the Cholesky, whose shared memory holds all of H.
+// ld p, columns < K rounded up to even) from the factor buffer L4, K and E_K
+// from its singular-value record.  Only L is held in shared memory, so that
+// more pairs run side by side than in the Cholesky, whose shared memory holds
+// all of H.
 template <int P_T, int NT>
 __global__ void __launch_bounds__(NT, 2048 / NT - 4)
     gram_jacobi_kernel(const PairArgs<float>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
-  using T = float;
-  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   const int LDL = P + 1;
-  C2<T>* Vm = reinterpret_cast<C2<T>*>(smem);  // L, then the reflector vectors below the diagonal
-  C2<T>* Rm = Vm + (size_t)P * LDL;             // R, then R J
-  size_t soff = (2 * (size_t)P * LDL * sizeof(C2<T>) + 15) & ~(size_t)15;
+  C2<float>* Lm = reinterpret_cast<C2<float>*>(smem);
+  size_t soff = ((size_t)P * LDL * sizeof(C2<float>) + 15) & ~(size_t)15;
   double* sig2 = reinterpret_cast<double*>(smem + soff);
   soff += (size_t)P * sizeof(double);
   int* ord = reinterpret_cast<int*>(smem + soff);
-  soff += (size_t)P * sizeof(int);
-  T* tauH = reinterpret_cast<T*>(smem + soff);
-  soff += (size_t)P * sizeof(T);
-  C2<T>* betaH = reinterpret_cast<C2<T>*>(smem + ((soff + 7) & ~(size_t)7));
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   const uint32_t code = codes[blockIdx.x];
-  const PairArgs<T>& a = args[code >> kCodeProbShift];
+  const PairArgs<float>& a = args[code >> kCodeProbShift];
   const int side = (int)((code >> kCodeSideShift) & 1u);
   const int pid = (int)(code & kCodePairMask);
   if (!DH2_IN(pid, c_lim.npairs[side], 14, pid)) return;
@@ -1429,64 +1316,15 @@ __global__ void __launch_bounds__(NT, 2048 / NT - 4)
   const int K = (int)sig_out[kSigValues];
   const double E_K = sig_out[kSigValues + 1];
   const int pe = K + (K & 1);
-  const C2<T>* Lg = reinterpret_cast<const C2<T>*>(a.L4 + a.hoff[side][pid]);
-  for (int i = tid; i < K * p; i += NT) Vm[(i / p) * LDL + i % p] = Lg[i];
-  for (int i = tid; i < pe * LDL; i += NT) Rm[i] = czero<T>();
+  const C2<float>* Lg = reinterpret_cast<const C2<float>*>(a.L4 + a.hoff[side][pid]);
+  for (int i = tid; i < pe * p; i += NT) Lm[(i / p) * LDL + i % p] = Lg[i];
   __syncthreads();
   long long t_b = 0;
 #if DH2_PROF_ON
   t_b = clock64();
 #endif
-  // Householder QR of L (p x K): for column j, x = L[j:p, j], beta = -s ||x||
-  // with s = x_0 / |x_0|, v = x - beta e_0 (v_0 = s (|x_0| + ||x||)) and
-  // tau = 2 / (v^* v) = 1 / (||x|| (||x|| + |x_0|)); H_j = I - tau v v^* maps
-  // x to beta e_0 and is applied to the columns right of j
-  for (int j = 0; j < K; ++j) {
-    if (warp == 0) {
-      T nx2 = T(0);
-      for (int r = j + lane; r < p; r += 32) nx2 = nmac(nx2, Vm[j * LDL + r]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) nx2 += __shfl_xor_sync(0xffffffffu, nx2, o);
-      if (lane == 0) {
-        const C2<T> x0 = Vm[j * LDL + j];
-        const T a0 = sqrtf(cnorm2(x0)), nx = sqrtf(nx2);
-        T tau = T(0);
-        C2<T> beta = czero<T>();
-        if (nx > T(0)) {
-          const C2<T> sg = a0 > T(0) ? C2<T>{x0.re / a0, x0.im / a0} : C2<T>{T(1), T(0)};
-          beta = C2<T>{-sg.re * nx, -sg.im * nx};
-          Vm[j * LDL + j] = C2<T>{sg.re * (a0 + nx), sg.im * (a0 + nx)};
-          tau = T(1) / (nx * (nx + a0));
-        }
-        tauH[j] = tau;
-        betaH[j] = beta;
-      }
-    }
-    __syncthreads();
-    const T tau = tauH[j];
-    const C2<T>* v = Vm + j * LDL;
-    for (int c = j + 1 + warp; c < K; c += NW) {
-      C2<T>* y = Vm + c * LDL;
-      C2<T> d = czero<T>();
-      for (int r = j + lane; r < p; r += 32) d = cmacc(d, y[r], v[r]);  // + conj(v) y
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        d.re += __shfl_xor_sync(0xffffffffu, d.re, o);
-        d.im += __shfl_xor_sync(0xffffffffu, d.im, o);
-      }
-      const C2<T> td = C2<T>{tau * d.re, tau * d.im};
-      for (int r = j + lane; r < p; r += 32) y[r] = csub(y[r], cmul(td, v[r]));
-    }
-    __syncthreads();
-  }
-  // R: diagonal beta, strictly upper part from the reduced columns
-  for (int i = tid; i < K * K; i += NT) {
-    const int r = i % K, c = i / K;
-    Rm[c * LDL + r] = r < c ? Vm[c * LDL + r] : r == c ? betaH[c] : czero<T>();
-  }
-  __syncthreads();
-  jacobi_rank_q<T, P_T, NT, true>(a, side, pid, K, LDL, K, E_K, a.kcap[side][pid], a.level[side][pid], Rm, sig2, ord,
-                                  rank_out, sig_out, t_b, Vm, tauH, p);
+  jacobi_rank_q<float, P_T, NT>(a, side, pid, p, LDL, K, E_K, a.kcap[side][pid], a.level[side][pid], Lm, sig2, ord,
+                                rank_out, sig_out, t_b);
 }
 
 // R_tc = Q^* A for the pairs of one launch (Section 6, R recursion: R_tc =
@@ -1752,47 +1590,41 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
     }
     issue_q(x, s, 0);
   };
-  // outputs of block qb: lane = column of the tile, warp w = a quarter of the
-  // block's rows of R (QB / 4 at most, an even count); per row r of A one entry of A per
-  // lane and the warp's Q entries, read by all lanes at one address
-  // (broadcast).  Entries past kb or cw are formed (finite or not) but never
-  // stored.
-  static_assert(TW == 32 && NT == 128 && QB % 8 == 0, "one column per lane, four warps over the rows of R");
-  constexpr int QW = QB / 4;  // rows of R per warp
+  // 2 x 2 output tiles of block qb; entries past kb or cw are read (finite or
+  // not) but never stored
   auto products = [&](const RqLeafTile<T>& x, int s, int slot, int qb) {
     const C2<T>* Qs = stQ(s);
     const C2<T>* As = stA(s);
     const int kb = min(QB, x.k - qb);
-    const int nq = (((kb + 3) >> 2) + 1) & ~1;  // rows of R per warp: a quarter of kb, even
-    const int jj = tid & 31, q0 = (tid >> 5) * nq;
-    if (q0 >= kb) return;
+    const int nqt = (kb + 1) >> 1, njt = (x.cw + 1) >> 1;
     const T sg = x.side == 0 ? T(1) : T(-1);  // conj(Q) for the row basis, Q for the column basis
-    C2<T> acc[QW];
-#pragma unroll
-    for (int i = 0; i < QW; ++i) acc[i] = czero<T>();
-    const C2<T>* qp = Qs + q0;
-    const C2<T>* ap = As + jj;
+    for (int u = tid; u < nqt * njt; u += NT) {
+      const int q0 = 2 * (u % nqt), jb = 2 * (u / nqt);
+      const C2<T>* qp = Qs + q0;
+      const C2<T>* ap = As + jb;
+      C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
 #pragma unroll 2
-    for (int r = 0; r < x.p; ++r, qp += LQ, ap += LA) {
-      const C2<T> y = *ap;
-#pragma unroll
-      for (int i = 0; i < QW; i += 2) {
-        if (i >= nq) break;
-        C2<T> x0, x1;
-        load_c2x2(qp + i, x0, x1);
+      for (int r = 0; r < x.p; ++r, qp += LQ, ap += LA) {
+        C2<T> x0, x1, y0, y1;
+        load_c2x2(qp, x0, x1);
+        load_c2x2(ap, y0, y1);
         x0.im *= sg;
         x1.im *= sg;
-        acc[i] = cmacc(acc[i], y, x0);
-        acc[i + 1] = cmacc(acc[i + 1], y, x1);
+        c00 = cmacc(c00, y0, x0);
+        c01 = cmacc(c01, y1, x0);
+        c10 = cmacc(c10, y0, x1);
+        c11 = cmacc(c11, y1, x1);
       }
-    }
-    if (jj < x.cw) {
-      const T w = cwt[slot][jj];
-      const int64_t e0 = qb + q0 + (int64_t)(x.j0 + jj) * x.kcap;
 #pragma unroll
-      for (int i = 0; i < QW; ++i)
-        if (i < nq && q0 + i < kb && DH2_IN(x.roff + e0 + i, c_lim.R[x.side], 11, x.pid))
-          x.R[e0 + i] = C2<T>{acc[i].re * w, sg * acc[i].im * w};
+      for (int d = 0; d < 4; ++d) {
+        const int qq = q0 + (d >> 1), jj = jb + (d & 1);
+        if (qq < kb && jj < x.cw) {
+          const C2<T> v = d == 0 ? c00 : d == 1 ? c01 : d == 2 ? c10 : c11;
+          const T w = cwt[slot][jj];
+          const int64_t e = (qb + qq) + (int64_t)(x.j0 + jj) * x.kcap;
+          if (DH2_IN(x.roff + e, c_lim.R[x.side], 11, x.pid)) x.R[e] = C2<T>{v.re * w, sg * v.im * w};
+        }
+      }
     }
   };
 
@@ -1985,8 +1817,8 @@ bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
 template <int P_T, int NT>
 bool launch_gram_factor(const PairArgs<float>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
   if (!launch_one<float, P_T, false, NT, true>(args, codes, nblocks, P, st)) return false;
-  const size_t smem = ((2 * (size_t)P * (P + 1) * sizeof(C2<float>) + 15) & ~(size_t)15) +
-                      (size_t)P * (sizeof(double) + sizeof(int) + sizeof(float)) + 8 + (size_t)P * sizeof(C2<float>);
+  const size_t smem = (((size_t)P * (P + 1) * sizeof(C2<float>) + 15) & ~(size_t)15) + (size_t)P * sizeof(double) +
+                      (size_t)P * sizeof(int);
   auto kern = gram_jacobi_kernel<P_T, NT>;
   if (!set_smem(kern, smem)) return false;
   kern<<<nblocks, NT, smem, st>>>(args, codes, P);
