@@ -555,6 +555,7 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
                                               int32_t* rank_out, double* sig_out, long long t_b) {
   const int tid = threadIdx.x, warp = tid >> 5;
   __shared__ int sh_rot[2];
+  __shared__ unsigned sh_off[2];  // per sweep parity: largest |gamma| / sqrt(alpha beta) rotated (float bits)
   __shared__ int sh_k;
   (void)t_b;
   // ---------------------------------------------------------------- 2. Jacobi
@@ -570,6 +571,8 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
   if (tid == 0) {
     sh_rot[0] = 0;
     sh_rot[1] = 0;
+    sh_off[0] = 0u;
+    sh_off[1] = 0u;
   }
   __syncthreads();
   bool conv = pe < 2;
@@ -616,8 +619,8 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
           // (hardware approximations in FP32, a few ulp): c^2 + s^2 = 1 to
           // that level, far inside the convergence test's tol = p u
           const T rg = frsqrt(g2);
-          if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) &&
-              g2 * rg * frsqrt(al) * frsqrt(be) > tol) {
+          const T off = g2 * rg * frsqrt(al) * frsqrt(be);  // |gamma| / sqrt(alpha beta)
+          if (act && al > Eps<T>::tiny && be > Eps<T>::tiny && g2 > T(0) && off > tol) {
             const T zt = (be - al) * T(0.5) * rg;
             const T az = fabs(zt);
             const T q1 = T(1) + zt * zt;
@@ -633,7 +636,10 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
                 ca[r] = C2<T>{c * xa.re - s * eb.re, c * xa.im - s * eb.im};
                 cb[r] = C2<T>{s * xa.re + c * eb.re, s * xa.im + c * eb.im};
               }
-              if (jl == 0) sh_rot[sp] = 1;
+              if (jl == 0) {
+                sh_rot[sp] = 1;
+                atomicMax(&sh_off[sp], __float_as_uint((float)off));
+              }
             }
           }
           if (act) {
@@ -643,11 +649,18 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
         }
       }
       __syncthreads();
-      if (rd == 0 && tid == 0) sh_rot[sp ^ 1] = 0;
+      if (rd == 0 && tid == 0) {
+        sh_rot[sp ^ 1] = 0;
+        sh_off[sp ^ 1] = 0u;
+      }
     }
     const int rot = sh_rot[sp];
+    // quadratic convergence: once the largest rotated off-diagonal ratio of a
+    // sweep is below sqrt(tol) / 4, the next sweep's ratios stay below tol,
+    // so that confirming sweep is not run
+    const T offmax = (T)__uint_as_float(sh_off[sp]);
     __syncthreads();
-    if (rot == 0) {
+    if (rot == 0 || offmax * offmax * T(16) <= tol) {
       conv = true;
       break;
     }
