@@ -563,6 +563,381 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
   if (warp == 0) tmem_dealloc(tbase, Sh::TCOLS);
 }
 
+// ---------------------------------------------------------------- pipelined form (leaves of <= 48 rows)
+// One CTA per SM, 13 warps in three roles that walk the same schedule (the
+// launch list's pairs, their windows of kGramWindow columns, their chunks of
+// kGramChunk columns), so that no work description passes between them:
+//   warps 0-7   producers: load a chunk of A, slice it into one of two
+//               shared-memory stages, arrive on full[s];
+//   warp 8      one thread issues the chunk's 48 MMAs into one of two
+//               accumulator sets of tensor memory (one set per window,
+//               alternating), then commits to empty[s] (the stage may be
+//               refilled) and, after a window's last chunk, to accfull[a];
+//   warps 9-12  epilogue: reads a finished window's accumulators (warp w the
+//               TMEM lanes 32 (w % 4) ..), adds it to the pair's window sums,
+//               arrives on accempty[a], and after a pair's last window forms
+//               H = V + V^* in double-float.
+// Loading and slicing of chunk c + 1 run while the tensor cores work on chunk
+// c, and a pair's window sums and H while the next pair's chunks are sliced
+// and multiplied.  Every wait is bounded: a wait that runs out sets the CTA's
+// abort flag and every role leaves its schedule at its next wait.
+constexpr int kPipeProd = 256;                // producer threads (warps 0-7)
+constexpr int kPipeMmaWarp = 8;
+constexpr int kPipeEpi0 = 9;                  // first epilogue warp
+constexpr int kPipeThreads = 13 * 32;
+constexpr uint32_t kBarProd = 1, kBarEpi = 2;  // named barriers of the producers, of the epilogue
+
+template <int NP>
+struct PipeShape {
+  static constexpr uint32_t SLBYTES = (NP + 128) * 128u;  // one slice: rows [X; Y; -X], MMA reads [0,128), [mp, mp+128)
+  static constexpr uint32_t BBYTES = (2 * NP + 16) * 128u;  // slice 3 times 2^-9, rows [X; Y]
+  static constexpr uint32_t STAGE = 3 * SLBYTES + BBYTES;
+  static constexpr uint32_t VSBYTES = 2 * NP * (NP + 1) * 8;  // last window's sums, 2 mp rows of mp + 1
+  static constexpr uint32_t SMEM = 1024 + 2 * STAGE + VSBYTES;
+  static constexpr uint32_t SETCOLS = 5 * NP;  // accumulators of one set
+  static_assert(STAGE % 1024 == 0 && 2 * SETCOLS <= 512, "stages on 1 KiB, two sets in 512 columns");
+};
+
+// the schedule's per-pair facts, the same in every role
+struct PipePair {
+  int side, pid, m, N, r0, mp;
+  bool run;  // false: nothing to multiply (empty, or beyond the launch's size)
+};
+__device__ __forceinline__ PipePair pipe_pair(const GramArgs& a, uint32_t code, int np) {
+  PipePair q;
+  q.side = (int)((code >> kCodeSideShift) & 1u);
+  q.pid = (int)(code & kCodePairMask);
+  q.m = a.m[q.side][q.pid];
+  q.N = a.ncols[q.side][q.pid];
+  q.r0 = a.start[q.side][q.pid];
+  q.mp = (q.m + 7) & ~7;
+  const bool fits = q.m <= np && (q.N <= kGramWindow || a.voff[q.side][q.pid] >= 0);
+  q.run = fits && q.m > 0 && q.N > 0;
+  return q;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+    gram_pipe_kernel(const GramArgs* __restrict__ args, const uint32_t* __restrict__ codes, int ncodes) {
+  using Sh = PipeShape<NP>;
+  constexpr int U = (64 * 8 + kPipeProd - 1) / kPipeProd;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  long long* Vs = reinterpret_cast<long long*>(smem + 2 * Sh::STAGE);
+  __shared__ int cgcT[kTableCols];
+  __shared__ float cwtT[kTableCols];
+  __shared__ float rsc[64];
+  __shared__ int erexp[64];
+  __shared__ __align__(8) uint64_t full[2], empty[2], accfull[2], accempty[2], drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], kPipeProd);
+      mbar_init(&empty[i], 1);
+      mbar_init(&accfull[i], 1);
+      mbar_init(&accempty[i], 128);
+    }
+    mbar_init(&drain, 1);
+    mbar_init_fence();
+    abort_flag = 0;
+  }
+  {
+    uint4* z = reinterpret_cast<uint4*>(smem);
+    for (uint32_t i = tid; i < 2 * Sh::STAGE / 16; i += kPipeThreads) z[i] = make_uint4(0, 0, 0, 0);
+  }
+  fence_async_smem();
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tbase = tmem_base;
+  const uint32_t sbase = smem_addr(smem);
+  const uint32_t polls = args[0].spin_limit > 0 ? args[0].spin_limit : kWaitPolls;
+  // a bounded wait; false (and the abort flag set) when it runs out
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (*(volatile int*)&abort_flag) return false;
+    if (mbar_wait(bar, parity, polls)) return true;
+    atomicExch(&abort_flag, 1);
+    return false;
+  };
+
+  if (warp < kPipeProd / 32) {
+    // ================================================================ producers
+    uint32_t cc = 0;  // chunks produced
+    bool ok = true;   // the same in every producer thread (decided by thread 0, spread by a barrier)
+    for (int ci = blockIdx.x; ci < ncodes && ok; ci += gridDim.x) {
+      const uint32_t code = codes[ci];
+      const GramArgs& a = args[code >> kCodeProbShift];
+      const PipePair q = pipe_pair(a, code, NP);
+      if (!q.run) continue;
+      const int m = q.m, N = q.N, mp = q.mp, side = q.side, r0 = q.r0;
+      const int64_t cmo = a.cmoff[side][q.pid];
+      const int32_t* gcol = a.gcol[side] + cmo;
+      const float* colw = a.colw[side] + cmo;
+      const C2<float>* G = a.G;
+      const int64_t ld = a.ld;
+      const float4* Hin = a.H + a.hoff[side][q.pid];
+      const int nitem = m * 8;
+      auto load_table = [&](int tb) {
+        named_bar_sync(kBarProd, kPipeProd);  // no producer still reads the previous segment
+        for (int jj = tid; jj < kTableCols && tb + jj < N; jj += kPipeProd) {
+          cgcT[jj] = gcol[tb + jj];
+          cwtT[jj] = colw[tb + jj];
+        }
+        named_bar_sync(kBarProd, kPipeProd);
+      };
+      auto load_chunk = [&](int j0, int cw, int tb, C2<float> (&v)[U][8]) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int qi = tid + kPipeProd * u;
+          const int r = qi % m, g = qi / m;
+          bool vec = false;
+          int64_t e0 = 0;
+          if (side == 1 && qi < nitem && 8 * g + 7 < cw) {
+            const int* cg = cgcT + (j0 - tb + 8 * g);
+            const int gc0 = cg[0];
+            e0 = (int64_t)(r0 + r) * ld + gc0;
+            vec = (e0 & 1) == 0;
+#pragma unroll
+            for (int k = 1; k < 8; ++k) vec = vec && cg[k] == gc0 + k;
+          }
+          if (vec) {
+            const float4* src = reinterpret_cast<const float4*>(G + e0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float4 x = src[k];
+              v[u][2 * k] = C2<float>{x.x, x.y};
+              v[u][2 * k + 1] = C2<float>{x.z, x.w};
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int jj = 8 * g + k;
+              v[u][k] = C2<float>{0.f, 0.f};
+              if (qi < nitem && jj < cw) {
+                const int gc = cgcT[j0 - tb + jj];
+                const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
+                v[u][k] = G[e];
+              }
+            }
+          }
+        }
+      };
+      int tb = 0;
+      load_table(0);
+      C2<float> v[U][8];
+      load_chunk(0, min(kGramChunk, N), 0, v);
+      if (tid < m) {
+        const int e = __float_as_int(Hin[tid].x);  // row scale from gram_scales_kernel (kBadRow: see the epilogue)
+        rsc[tid] = ldexpf(1.f, 6 - (e == kBadRow ? 0 : e));
+      }
+      named_bar_sync(kBarProd, kPipeProd);
+      for (int w0 = 0; w0 < N && ok; w0 += kGramWindow) {
+        const int wend = min(N, w0 + kGramWindow);
+        for (int j0 = w0; j0 < wend; j0 += kGramChunk, ++cc) {
+          const int cw = min(kGramChunk, wend - j0);
+          const int s = (int)(cc & 1u);
+          // stage s is free once the MMAs of the chunk it held have completed
+          ok = named_bar_and(kBarProd, kPipeProd, tid == 0 ? wait(&empty[s], ((cc >> 1) & 1u) ^ 1u) : true);
+          if (!ok) break;
+          unsigned char* sl0 = smem + s * Sh::STAGE;
+          unsigned char* bsl = sl0 + 3 * Sh::SLBYTES;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int qi = tid + kPipeProd * u;
+            if (qi >= nitem) continue;
+            const int r = qi % m, g = qi / m;
+            const float sc = rsc[r];
+            uint32_t px[3][4], py[3][4], pn[3][4], pb[2][4];
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+              float sx[3][2], sy[3][2];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int jj = 8 * g + k + h;
+                const float w = __fmul_rn(jj < cw ? cwtT[j0 - tb + jj] : 0.f, sc);
+                const float xr = __fmul_rn(v[u][k + h].re, w);
+                const float xi = __fmul_rn(side == 0 ? v[u][k + h].im : -v[u][k + h].im, w);
+                slice3(xr, sx[0][h], sx[1][h], sx[2][h]);
+                slice3(xi, sy[0][h], sy[1][h], sy[2][h]);
+              }
+#pragma unroll
+              for (int t = 0; t < 3; ++t) {
+                px[t][k >> 1] = pack_bf16(sx[t][0], sx[t][1]);
+                py[t][k >> 1] = pack_bf16(sy[t][0], sy[t][1]);
+                pn[t][k >> 1] = px[t][k >> 1] ^ 0x80008000u;
+              }
+              pb[0][k >> 1] = pack_bf16(__fmul_rn(sx[2][0], 0.001953125f), __fmul_rn(sx[2][1], 0.001953125f));
+              pb[1][k >> 1] = pack_bf16(__fmul_rn(sy[2][0], 0.001953125f), __fmul_rn(sy[2][1], 0.001953125f));
+            }
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+              unsigned char* buf = sl0 + t * Sh::SLBYTES;
+              *reinterpret_cast<uint4*>(buf + swz(r, g)) = make_uint4(px[t][0], px[t][1], px[t][2], px[t][3]);
+              *reinterpret_cast<uint4*>(buf + swz(mp + r, g)) = make_uint4(py[t][0], py[t][1], py[t][2], py[t][3]);
+              *reinterpret_cast<uint4*>(buf + swz(2 * mp + r, g)) = make_uint4(pn[t][0], pn[t][1], pn[t][2], pn[t][3]);
+            }
+            *reinterpret_cast<uint4*>(bsl + swz(r, g)) = make_uint4(pb[0][0], pb[0][1], pb[0][2], pb[0][3]);
+            *reinterpret_cast<uint4*>(bsl + swz(mp + r, g)) = make_uint4(pb[1][0], pb[1][1], pb[1][2], pb[1][3]);
+          }
+          fence_async_smem();
+          mbar_arrive(&full[s]);
+          // the next chunk's loads (a new table segment waits for every producer)
+          const int jn = j0 + kGramChunk;
+          if (jn < N) {
+            if (jn >= tb + kTableCols) {
+              tb = jn;
+              load_table(tb);
+            }
+            load_chunk(jn, min(kGramChunk, min(N, jn < wend ? wend : jn + kGramWindow) - jn), tb, v);
+          }
+        }
+      }
+      if (ok) named_bar_sync(kBarProd, kPipeProd);  // rsc and the table are read before the next pair rewrites them
+    }
+  } else if (warp == kPipeMmaWarp) {
+    // ================================================================ MMA issue
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
+      uint32_t cc = 0, wc = 0;  // chunks and windows consumed
+      bool ok = true;
+      for (int ci = blockIdx.x; ci < ncodes && ok; ci += gridDim.x) {
+        const uint32_t code = codes[ci];
+        const PipePair q = pipe_pair(args[code >> kCodeProbShift], code, NP);
+        if (!q.run) continue;
+        for (int w0 = 0; w0 < q.N && ok; w0 += kGramWindow, ++wc) {
+          const int wend = min(q.N, w0 + kGramWindow);
+          const uint32_t aset = wc & 1u;
+          ok = wait(&accempty[aset], ((wc >> 1) & 1u) ^ 1u);  // the epilogue has read this set's last window
+          tc_fence_after_sync();
+          for (int j0 = w0; j0 < wend && ok; j0 += kGramChunk, ++cc) {
+            const uint32_t s = cc & 1u;
+            ok = wait(&full[s], (cc >> 1) & 1u);
+            if (!ok) break;
+            tc_fence_after_sync();
+            const uint32_t base = sbase + s * Sh::STAGE;
+            const bool first = j0 == w0;
+            const int pa[6] = {0, 0, 0, 1, 1, 2};
+            const int pbx[6] = {0, 1, 2, 1, 2, 3};  // 3 = slice 3 times 2^-9
+            const int pacc[6] = {0, 1, 2, 3, 4, 4};
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+              for (int x = 0; x < 6; ++x) {
+                const uint32_t ao = base + (uint32_t)pa[x] * Sh::SLBYTES + 32u * ks;
+                const uint32_t bo = base + (uint32_t)pbx[x] * Sh::SLBYTES + 32u * ks;
+                const uint32_t dt = tbase + aset * Sh::SETCOLS + (uint32_t)(pacc[x] * NP);
+                const bool acc0 = !(first && ks == 0 && x != 5);
+                mma_bf16(dt, desc_kmajor_sw128(ao), desc_kmajor_sw128(bo), idesc, acc0);
+                mma_bf16(dt, desc_kmajor_sw128(ao + (uint32_t)q.mp * 128u), desc_kmajor_sw128(bo + (uint32_t)q.mp * 128u),
+                         idesc, true);
+              }
+            }
+            mma_commit(&empty[s]);
+            if (j0 + kGramChunk >= wend) mma_commit(&accfull[aset]);
+          }
+        }
+      }
+      // every MMA issued has completed before the tensor memory is released
+      mma_commit(&drain);
+      mbar_wait(&drain, 0, kWaitPolls);
+    }
+  } else {
+    // ================================================================ epilogue
+    const int q4 = warp & 3;
+    const int L = q4 * 32 + lane;  // TMEM lane of this thread
+    const int et = tid - kPipeEpi0 * 32;  // 0..127
+    const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
+    uint32_t wc = 0;
+    bool ok = true;
+    for (int ci = blockIdx.x; ci < ncodes && ok; ci += gridDim.x) {
+      const uint32_t code = codes[ci];
+      const GramArgs& a = args[code >> kCodeProbShift];
+      const PipePair q = pipe_pair(a, code, NP);
+      float4* Hout = a.H + a.hoff[q.side][q.pid];
+      const int m = q.m, mp = q.mp;
+      if (!q.run) {
+        if (m > NP || (q.N > kGramWindow && a.voff[q.side][q.pid] < 0)) {
+          if (et == 0) atomicOr(a.status, kStatusTooLarge);
+        } else {
+          for (int i = et; i < mp * mp; i += 128) Hout[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        continue;
+      }
+      const int64_t voff = a.voff[q.side][q.pid];
+      long long* Vg = voff >= 0 ? a.V + voff : nullptr;
+      if (et < m) erexp[et] = __float_as_int(Hout[et].x);
+      named_bar_sync(kBarEpi, 128);
+      for (int w0 = 0; w0 < q.N && ok; w0 += kGramWindow, ++wc) {
+        const bool last = w0 + kGramWindow >= q.N;
+        const uint32_t aset = wc & 1u;
+        ok = named_bar_and(kBarEpi, 128, et == 0 ? wait(&accfull[aset], (wc >> 1) & 1u) : true);
+        if (!ok) break;
+        tc_fence_after_sync();
+#pragma unroll 1
+        for (int cb = 0; cb < NP; cb += 16) {
+          float p11[16], p12[16], p13[16], p22[16], plo[16];
+          const uint32_t tc = tbase + lane_base + aset * Sh::SETCOLS + cb;
+          tmem_ld16(tc + 0 * NP, p11);
+          tmem_ld16(tc + 1 * NP, p12);
+          tmem_ld16(tc + 2 * NP, p13);
+          tmem_ld16(tc + 3 * NP, p22);
+          tmem_ld16(tc + 4 * NP, plo);
+          tmem_ld_wait();
+          if (L < 2 * mp) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int j = cb + i;
+              if (j >= mp) break;
+              long long x = (long long)__float2int_rn(p11[i]) * (1LL << 31) +
+                            (long long)__float2int_rn(p12[i]) * (1LL << 24) +
+                            (long long)__float2int_rn(p13[i]) * (1LL << 16) +
+                            (long long)__float2int_rn(p22[i]) * (1LL << 15) + (long long)__float2int_rn(plo[i] * 256.f);
+              if (Vg) {
+                const int64_t gi = (int64_t)j * (2 * mp) + L;
+                if (w0 > 0) x += Vg[gi];
+                if (!last) Vg[gi] = x;
+              }
+              if (last) Vs[(int64_t)L * (mp + 1) + j] = x;
+            }
+          }
+        }
+        tc_fence_before_sync();
+        mbar_arrive(&accempty[aset]);
+      }
+      if (!ok) break;
+      named_bar_sync(kBarEpi, 128);  // the last window's sums are in Vs
+      bool bad = false;
+      for (int i = 0; i < m; ++i) bad = bad || erexp[i] == kBadRow;
+      if (bad) {  // non-finite entries: reported, H of this pair left as zero
+        if (et == 0) atomicOr(a.status, kStatusNaN);
+        for (int i = et; i < mp * mp; i += 128) Hout[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        for (int idx = et; idx < m * m; idx += 128) {
+          const int i = idx % m, j = idx / m;
+          const int64_t ls = mp + 1;
+          const long long re = Vs[(int64_t)i * ls + j] + Vs[(int64_t)j * ls + i];
+          const long long im = Vs[(int64_t)(mp + i) * ls + j] - Vs[(int64_t)(mp + j) * ls + i];
+          const int ex = erexp[i] + erexp[j] - 12 - 32;
+          const float2 hr = ll_to_df(re, ex), hi = ll_to_df(im, ex);
+          Hout[i + (int64_t)j * mp] = make_float4(hr.x, hr.y, hi.x, hi.y);
+        }
+      }
+      named_bar_sync(kBarEpi, 128);  // Vs and erexp read before the next pair's last window
+    }
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicOr(args[0].status, kStatusTimeout);
+  if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
 template <int NP>
 bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t st) {
   using Sh = GramShape<NP>;
@@ -629,10 +1004,33 @@ bool prof_read_gram(unsigned long long* out10) {
 #endif
 }
 
+// the pipelined kernel: one CTA per SM
+template <int NP>
+bool launch_pipe(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t st) {
+  using Sh = PipeShape<NP>;
+  auto kern = gram_pipe_kernel<NP>;
+  int dev = 0, maxopt = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&maxopt, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      Sh::SMEM > (uint32_t)maxopt ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int grid = std::min(n, nsm);
+#ifdef DH2_PROFILE
+  std::fprintf(stderr, "dh2 gram_pipe<%d>: %d pairs, grid %d, %u B shared\n", NP, n, grid, Sh::SMEM);
+#endif
+  gram_scales_kernel<<<(n + 7) / 8, 256, 0, st>>>(args, codes, n);
+  kern<<<grid, kPipeThreads, Sh::SMEM, st>>>(args, codes, n);
+  return true;
+}
+
 bool launch_gram(const GramArgs* args_dev, const uint32_t* codes, int n, int maxm, cudaStream_t st) {
   if (n <= 0) return true;
-  if (maxm <= 32) return launch_np<32>(args_dev, codes, n, st);
-  if (maxm <= 48) return launch_np<48>(args_dev, codes, n, st);
+  if (maxm <= 32) return launch_pipe<32>(args_dev, codes, n, st);
+  if (maxm <= 48) return launch_pipe<48>(args_dev, codes, n, st);
   if (maxm <= 64) return launch_np<64>(args_dev, codes, n, st);
   return false;
 }
