@@ -567,24 +567,24 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
 // One CTA per SM, 13 warps in three roles that walk the same schedule (the
 // launch list's pairs, their windows of kGramWindow columns, their chunks of
 // kGramChunk columns), so that no work description passes between them:
-//   warps 0-7   producers: load a chunk of A, slice it into one of two
+//   warps 0-11  producers: load a chunk of A, slice it into one of two
 //               shared-memory stages, arrive on full[s];
-//   warp 8      one thread issues the chunk's 48 MMAs into one of two
+//   warp 12     one thread issues the chunk's 48 MMAs into one of two
 //               accumulator sets of tensor memory (one set per window,
 //               alternating), then commits to empty[s] (the stage may be
 //               refilled) and, after a window's last chunk, to accfull[a];
-//   warps 9-12  epilogue: reads a finished window's accumulators (warp w the
+//   warps 13-16 epilogue: reads a finished window's accumulators (warp w the
 //               TMEM lanes 32 (w % 4) ..), adds it to the pair's window sums,
 //               arrives on accempty[a], and after a pair's last window forms
 //               H = V + V^* in double-float.
-// Loading and slicing of chunk c + 1 run while the tensor cores work on chunk
-// c, and a pair's window sums and H while the next pair's chunks are sliced
-// and multiplied.  Every wait is bounded: a wait that runs out sets the CTA's
+// Chunks c + 1 and c + 2 are being loaded while chunk c is sliced, slicing
+// runs while the tensor cores work on the chunk before, and a pair's window
+// sums and H while the next pair's chunks are sliced and multiplied.  Every wait is bounded: a wait that runs out sets the CTA's
 // abort flag and every role leaves its schedule at its next wait.
-constexpr int kPipeProd = 256;                // producer threads (warps 0-7)
-constexpr int kPipeMmaWarp = 8;
-constexpr int kPipeEpi0 = 9;                  // first epilogue warp
-constexpr int kPipeThreads = 13 * 32;
+constexpr int kPipeProd = 384;                // producer threads (warps 0-11): one item each, m <= 48
+constexpr int kPipeMmaWarp = 12;
+constexpr int kPipeEpi0 = 13;                 // first epilogue warp
+constexpr int kPipeThreads = 17 * 32;
 constexpr uint32_t kBarProd = 1, kBarEpi = 2;  // named barriers of the producers, of the epilogue
 
 template <int NP>
@@ -620,12 +620,12 @@ template <int NP>
 __global__ void __launch_bounds__(kPipeThreads, 1)
     gram_pipe_kernel(const GramArgs* __restrict__ args, const uint32_t* __restrict__ codes, int ncodes) {
   using Sh = PipeShape<NP>;
-  constexpr int U = (64 * 8 + kPipeProd - 1) / kPipeProd;
+  static_assert(NP * 8 <= kPipeProd, "one item per producer thread");
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   long long* Vs = reinterpret_cast<long long*>(smem + 2 * Sh::STAGE);
-  __shared__ int cgcT[kTableCols];
-  __shared__ float cwtT[kTableCols];
+  __shared__ int cgcT[2 * kTableCols];   // two segments of the pair's column table: G index
+  __shared__ float cwtT[2 * kTableCols];  // and weight 1/omega_b of each column
   __shared__ float rsc[64];
   __shared__ int erexp[64];
   __shared__ __align__(8) uint64_t full[2], empty[2], accfull[2], accempty[2], drain;
@@ -669,6 +669,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 
   if (warp < kPipeProd / 32) {
     // ================================================================ producers
+    // one (row, 8-column group) item per thread and chunk; the entries of
+    // chunks c + 1 and c + 2 are in flight while chunk c is sliced.  The
+    // column table is held in two segment buffers of kTableCols columns
+    // (segment k in buffer k % 2), so that a chunk's weights are still there
+    // when it is sliced after the next segment has been loaded.
     uint32_t cc = 0;  // chunks produced
     bool ok = true;   // the same in every producer thread (decided by thread 0, spread by a barrier)
     for (int ci = blockIdx.x; ci < ncodes && ok; ci += gridDim.x) {
@@ -684,120 +689,120 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       const int64_t ld = a.ld;
       const float4* Hin = a.H + a.hoff[side][q.pid];
       const int nitem = m * 8;
-      auto load_table = [&](int tb) {
-        named_bar_sync(kBarProd, kPipeProd);  // no producer still reads the previous segment
-        for (int jj = tid; jj < kTableCols && tb + jj < N; jj += kPipeProd) {
-          cgcT[jj] = gcol[tb + jj];
-          cwtT[jj] = colw[tb + jj];
+      const int r = tid % m, g = tid / m;  // this thread's item
+      const bool live = tid < nitem;
+      const int nch = (N + kGramChunk - 1) / kGramChunk;
+      int seg_loaded = 0;  // segments 0 .. seg_loaded - 1 have been loaded (the last two are held)
+      auto load_table = [&](int sg) {
+        named_bar_sync(kBarProd, kPipeProd);  // no producer still reads segment sg - 2 (its buffer)
+        const int t0 = sg * kTableCols, b = (sg & 1) * kTableCols;
+        for (int jj = tid; jj < kTableCols && t0 + jj < N; jj += kPipeProd) {
+          cgcT[b + jj] = gcol[t0 + jj];
+          cwtT[b + jj] = colw[t0 + jj];
         }
         named_bar_sync(kBarProd, kPipeProd);
       };
-      auto load_chunk = [&](int j0, int cw, int tb, C2<float> (&v)[U][8]) {
+      // entries of this thread's item of chunk jc (zero past the pair)
+      auto load_chunk = [&](int jc, C2<float> (&v)[8]) {
+        const int j0 = jc * kGramChunk;
+        if (j0 >= N) return;
+        const int sg = j0 / kTableCols;
+        if (sg >= seg_loaded) {  // chunks run in order: the next segment
+          load_table(sg);
+          seg_loaded = sg + 1;
+        }
+        const int cw = min(kGramChunk, N - j0);
+        const int* cg = cgcT + ((sg & 1) * kTableCols + j0 - sg * kTableCols + 8 * g);
+        bool vec = false;
+        int64_t e0 = 0;
+        if (side == 1 && live && 8 * g + 7 < cw) {
+          const int gc0 = cg[0];
+          e0 = (int64_t)(r0 + r) * ld + gc0;
+          vec = (e0 & 1) == 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int qi = tid + kPipeProd * u;
-          const int r = qi % m, g = qi / m;
-          bool vec = false;
-          int64_t e0 = 0;
-          if (side == 1 && qi < nitem && 8 * g + 7 < cw) {
-            const int* cg = cgcT + (j0 - tb + 8 * g);
-            const int gc0 = cg[0];
-            e0 = (int64_t)(r0 + r) * ld + gc0;
-            vec = (e0 & 1) == 0;
+          for (int k = 1; k < 8; ++k) vec = vec && cg[k] == gc0 + k;
+        }
+        if (vec) {
+          const float4* src = reinterpret_cast<const float4*>(G + e0);
 #pragma unroll
-            for (int k = 1; k < 8; ++k) vec = vec && cg[k] == gc0 + k;
+          for (int k = 0; k < 4; ++k) {
+            const float4 x = src[k];
+            v[2 * k] = C2<float>{x.x, x.y};
+            v[2 * k + 1] = C2<float>{x.z, x.w};
           }
-          if (vec) {
-            const float4* src = reinterpret_cast<const float4*>(G + e0);
+        } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const float4 x = src[k];
-              v[u][2 * k] = C2<float>{x.x, x.y};
-              v[u][2 * k + 1] = C2<float>{x.z, x.w};
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-              const int jj = 8 * g + k;
-              v[u][k] = C2<float>{0.f, 0.f};
-              if (qi < nitem && jj < cw) {
-                const int gc = cgcT[j0 - tb + jj];
-                const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
-                v[u][k] = G[e];
-              }
+          for (int k = 0; k < 8; ++k) {
+            const int jj = 8 * g + k;
+            v[k] = C2<float>{0.f, 0.f};
+            if (live && jj < cw) {
+              const int gc = cg[k];
+              const int64_t e = side == 0 ? (int64_t)gc * ld + r0 + r : (int64_t)(r0 + r) * ld + gc;
+              v[k] = G[e];
             }
           }
         }
       };
-      int tb = 0;
-      load_table(0);
-      C2<float> v[U][8];
-      load_chunk(0, min(kGramChunk, N), 0, v);
+      C2<float> vA[8], vB[8];
+      load_chunk(0, vA);
+      load_chunk(1, vB);
       if (tid < m) {
         const int e = __float_as_int(Hin[tid].x);  // row scale from gram_scales_kernel (kBadRow: see the epilogue)
         rsc[tid] = ldexpf(1.f, 6 - (e == kBadRow ? 0 : e));
       }
       named_bar_sync(kBarProd, kPipeProd);
-      for (int w0 = 0; w0 < N && ok; w0 += kGramWindow) {
-        const int wend = min(N, w0 + kGramWindow);
-        for (int j0 = w0; j0 < wend; j0 += kGramChunk, ++cc) {
-          const int cw = min(kGramChunk, wend - j0);
-          const int s = (int)(cc & 1u);
-          // stage s is free once the MMAs of the chunk it held have completed
-          ok = named_bar_and(kBarProd, kPipeProd, tid == 0 ? wait(&empty[s], ((cc >> 1) & 1u) ^ 1u) : true);
-          if (!ok) break;
-          unsigned char* sl0 = smem + s * Sh::STAGE;
-          unsigned char* bsl = sl0 + 3 * Sh::SLBYTES;
+      const float sc = live ? rsc[r] : 0.f;
+      // slice chunk jc from v into its stage, then refill v with chunk jc + 2
+      auto produce = [&](int jc, C2<float> (&v)[8]) -> bool {
+        const uint32_t s = cc & 1u;
+        // stage s is free once the MMAs of the chunk it held have completed
+        if (!named_bar_and(kBarProd, kPipeProd, tid == 0 ? wait(&empty[s], ((cc >> 1) & 1u) ^ 1u) : true))
+          return false;
+        unsigned char* sl0 = smem + s * Sh::STAGE;
+        unsigned char* bsl = sl0 + 3 * Sh::SLBYTES;
+        const int j0 = jc * kGramChunk, cw = min(kGramChunk, N - j0), sg = j0 / kTableCols;
+        const float* cwp = cwtT + ((sg & 1) * kTableCols + j0 - sg * kTableCols + 8 * g);
+        if (live) {
+          uint32_t px[3][4], py[3][4], pn[3][4], pb[2][4];
 #pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const int qi = tid + kPipeProd * u;
-            if (qi >= nitem) continue;
-            const int r = qi % m, g = qi / m;
-            const float sc = rsc[r];
-            uint32_t px[3][4], py[3][4], pn[3][4], pb[2][4];
+          for (int k = 0; k < 8; k += 2) {
+            float sx[3][2], sy[3][2];
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-              float sx[3][2], sy[3][2];
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int jj = 8 * g + k + h;
-                const float w = __fmul_rn(jj < cw ? cwtT[j0 - tb + jj] : 0.f, sc);
-                const float xr = __fmul_rn(v[u][k + h].re, w);
-                const float xi = __fmul_rn(side == 0 ? v[u][k + h].im : -v[u][k + h].im, w);
-                slice3(xr, sx[0][h], sx[1][h], sx[2][h]);
-                slice3(xi, sy[0][h], sy[1][h], sy[2][h]);
-              }
-#pragma unroll
-              for (int t = 0; t < 3; ++t) {
-                px[t][k >> 1] = pack_bf16(sx[t][0], sx[t][1]);
-                py[t][k >> 1] = pack_bf16(sy[t][0], sy[t][1]);
-                pn[t][k >> 1] = px[t][k >> 1] ^ 0x80008000u;
-              }
-              pb[0][k >> 1] = pack_bf16(__fmul_rn(sx[2][0], 0.001953125f), __fmul_rn(sx[2][1], 0.001953125f));
-              pb[1][k >> 1] = pack_bf16(__fmul_rn(sy[2][0], 0.001953125f), __fmul_rn(sy[2][1], 0.001953125f));
+            for (int h = 0; h < 2; ++h) {
+              const float wt = __fmul_rn(8 * g + k + h < cw ? cwp[k + h] : 0.f, sc);  // exact: sc is a power of two
+              const float xr = __fmul_rn(v[k + h].re, wt);
+              const float xi = __fmul_rn(side == 0 ? v[k + h].im : -v[k + h].im, wt);
+              slice3(xr, sx[0][h], sx[1][h], sx[2][h]);
+              slice3(xi, sy[0][h], sy[1][h], sy[2][h]);
             }
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
-              unsigned char* buf = sl0 + t * Sh::SLBYTES;
-              *reinterpret_cast<uint4*>(buf + swz(r, g)) = make_uint4(px[t][0], px[t][1], px[t][2], px[t][3]);
-              *reinterpret_cast<uint4*>(buf + swz(mp + r, g)) = make_uint4(py[t][0], py[t][1], py[t][2], py[t][3]);
-              *reinterpret_cast<uint4*>(buf + swz(2 * mp + r, g)) = make_uint4(pn[t][0], pn[t][1], pn[t][2], pn[t][3]);
+              px[t][k >> 1] = pack_bf16(sx[t][0], sx[t][1]);
+              py[t][k >> 1] = pack_bf16(sy[t][0], sy[t][1]);
+              pn[t][k >> 1] = px[t][k >> 1] ^ 0x80008000u;
             }
-            *reinterpret_cast<uint4*>(bsl + swz(r, g)) = make_uint4(pb[0][0], pb[0][1], pb[0][2], pb[0][3]);
-            *reinterpret_cast<uint4*>(bsl + swz(mp + r, g)) = make_uint4(pb[1][0], pb[1][1], pb[1][2], pb[1][3]);
+            pb[0][k >> 1] = pack_bf16(__fmul_rn(sx[2][0], 0.001953125f), __fmul_rn(sx[2][1], 0.001953125f));
+            pb[1][k >> 1] = pack_bf16(__fmul_rn(sy[2][0], 0.001953125f), __fmul_rn(sy[2][1], 0.001953125f));
           }
-          fence_async_smem();
-          mbar_arrive(&full[s]);
-          // the next chunk's loads (a new table segment waits for every producer)
-          const int jn = j0 + kGramChunk;
-          if (jn < N) {
-            if (jn >= tb + kTableCols) {
-              tb = jn;
-              load_table(tb);
-            }
-            load_chunk(jn, min(kGramChunk, min(N, jn < wend ? wend : jn + kGramWindow) - jn), tb, v);
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            unsigned char* buf = sl0 + t * Sh::SLBYTES;
+            *reinterpret_cast<uint4*>(buf + swz(r, g)) = make_uint4(px[t][0], px[t][1], px[t][2], px[t][3]);
+            *reinterpret_cast<uint4*>(buf + swz(mp + r, g)) = make_uint4(py[t][0], py[t][1], py[t][2], py[t][3]);
+            *reinterpret_cast<uint4*>(buf + swz(2 * mp + r, g)) = make_uint4(pn[t][0], pn[t][1], pn[t][2], pn[t][3]);
           }
+          *reinterpret_cast<uint4*>(bsl + swz(r, g)) = make_uint4(pb[0][0], pb[0][1], pb[0][2], pb[0][3]);
+          *reinterpret_cast<uint4*>(bsl + swz(mp + r, g)) = make_uint4(pb[1][0], pb[1][1], pb[1][2], pb[1][3]);
         }
+        fence_async_smem();
+        mbar_arrive(&full[s]);
+        ++cc;
+        load_chunk(jc + 2, v);
+        return true;
+      };
+      for (int jc = 0; jc < nch && ok; jc += 2) {
+        ok = produce(jc, vA);
+        if (ok && jc + 1 < nch) ok = produce(jc + 1, vB);
       }
       if (ok) named_bar_sync(kBarProd, kPipeProd);  // rsc and the table are read before the next pair rewrites them
     }
@@ -881,18 +886,18 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         if (!ok) break;
         tc_fence_after_sync();
 #pragma unroll 1
-        for (int cb = 0; cb < NP; cb += 16) {
-          float p11[16], p12[16], p13[16], p22[16], plo[16];
+        for (int cb = 0; cb < mp; cb += 8) {
+          float p11[8], p12[8], p13[8], p22[8], plo[8];
           const uint32_t tc = tbase + lane_base + aset * Sh::SETCOLS + cb;
-          tmem_ld16(tc + 0 * NP, p11);
-          tmem_ld16(tc + 1 * NP, p12);
-          tmem_ld16(tc + 2 * NP, p13);
-          tmem_ld16(tc + 3 * NP, p22);
-          tmem_ld16(tc + 4 * NP, plo);
+          tmem_ld8(tc + 0 * NP, p11);
+          tmem_ld8(tc + 1 * NP, p12);
+          tmem_ld8(tc + 2 * NP, p13);
+          tmem_ld8(tc + 3 * NP, p22);
+          tmem_ld8(tc + 4 * NP, plo);
           tmem_ld_wait();
           if (L < 2 * mp) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
+            for (int i = 0; i < 8; ++i) {
               const int j = cb + i;
               if (j >= mp) break;
               long long x = (long long)__float2int_rn(p11[i]) * (1LL << 31) +
