@@ -1163,7 +1163,16 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     prof_read_pair(pr);
     const double np = pr[5] ? (double)pr[5] : 1.0;
     const double ns = pr[12] ? (double)pr[12] : 1.0;
-    unsigned long long gq[10];
+    unsigned long long gq[22];
+    if (prof_read_gram(gq) && gq[10]) {
+      const double pp = (double)gq[10];
+      std::fprintf(stderr,
+                   "dh2 gram pipeline profile: %llu pairs, %.2f chunks/pair; cycles/pair: producers wait %.0f, slice "
+                   "%.0f, loads %.0f; MMA thread wait full %.0f, wait accumulators %.0f, issue %.0f; epilogue wait %.0f, "
+                   "flush %.0f, H %.0f\n",
+                   gq[10], gq[11] / pp, gq[12] / pp, gq[13] / pp, gq[14] / pp, gq[15] / pp, gq[16] / pp, gq[17] / pp,
+                   gq[18] / pp, gq[19] / pp, gq[20] / pp);
+    }
     if (prof_read_gram(gq) && gq[0]) {
       const double gp = (double)gq[0];
       std::fprintf(stderr,

@@ -53,6 +53,11 @@ using namespace sm100;
 // scales, table loads, issuing chunk loads, waits for MMA batches, slicing,
 // issuing MMAs, window flushes, H output
 __device__ unsigned long long g_gprof[10];
+// the pipelined form: pairs, chunks; producer thread 0: cycles waiting for a
+// free stage (with the barrier), slicing, issuing loads (with table
+// segments); MMA thread: waiting for a full stage, for a free accumulator set,
+// issuing; epilogue thread 0: waiting for a window, flushing it, forming H
+__device__ unsigned long long g_pprof[12];
 #define GP_T(v) v = clock64()
 #define GP_ON 1
 #else
@@ -676,11 +681,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     // when it is sliced after the next segment has been loaded.
     uint32_t cc = 0;  // chunks produced
     bool ok = true;   // the same in every producer thread (decided by thread 0, spread by a barrier)
+#if GP_ON
+    long long pw = 0, psl = 0, pld = 0, npair = 0;
+#endif
     for (int ci = blockIdx.x; ci < ncodes && ok; ci += gridDim.x) {
       const uint32_t code = codes[ci];
       const GramArgs& a = args[code >> kCodeProbShift];
       const PipePair q = pipe_pair(a, code, NP);
       if (!q.run) continue;
+#if GP_ON
+      ++npair;
+#endif
       const int m = q.m, N = q.N, mp = q.mp, side = q.side, r0 = q.r0;
       const int64_t cmo = a.cmoff[side][q.pid];
       const int32_t* gcol = a.gcol[side] + cmo;
@@ -706,6 +717,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       auto load_chunk = [&](int jc, C2<float> (&v)[8]) {
         const int j0 = jc * kGramChunk;
         if (j0 >= N) return;
+#if GP_ON
+        const long long t0 = clock64();
+#endif
         const int sg = j0 / kTableCols;
         if (sg >= seg_loaded) {  // chunks run in order: the next segment
           load_table(sg);
@@ -742,6 +756,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
             }
           }
         }
+#if GP_ON
+        pld += clock64() - t0;
+#endif
       };
       C2<float> vA[8], vB[8];
       load_chunk(0, vA);
@@ -755,9 +772,16 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       // slice chunk jc from v into its stage, then refill v with chunk jc + 2
       auto produce = [&](int jc, C2<float> (&v)[8]) -> bool {
         const uint32_t s = cc & 1u;
+#if GP_ON
+        const long long t0 = clock64();
+#endif
         // stage s is free once the MMAs of the chunk it held have completed
         if (!named_bar_and(kBarProd, kPipeProd, tid == 0 ? wait(&empty[s], ((cc >> 1) & 1u) ^ 1u) : true))
           return false;
+#if GP_ON
+        const long long t1 = clock64();
+        pw += t1 - t0;
+#endif
         unsigned char* sl0 = smem + s * Sh::STAGE;
         unsigned char* bsl = sl0 + 3 * Sh::SLBYTES;
         const int j0 = jc * kGramChunk, cw = min(kGramChunk, N - j0), sg = j0 / kTableCols;
@@ -796,6 +820,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         }
         fence_async_smem();
         mbar_arrive(&full[s]);
+#if GP_ON
+        psl += clock64() - t1;
+#endif
         ++cc;
         load_chunk(jc + 2, v);
         return true;
@@ -806,12 +833,24 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       }
       if (ok) named_bar_sync(kBarProd, kPipeProd);  // rsc and the table are read before the next pair rewrites them
     }
+#if GP_ON
+    if (tid == 0) {
+      atomicAdd(&g_pprof[0], (unsigned long long)npair);
+      atomicAdd(&g_pprof[1], (unsigned long long)cc);
+      atomicAdd(&g_pprof[2], (unsigned long long)pw);
+      atomicAdd(&g_pprof[3], (unsigned long long)psl);
+      atomicAdd(&g_pprof[4], (unsigned long long)pld);
+    }
+#endif
   } else if (warp == kPipeMmaWarp) {
     // ================================================================ MMA issue
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(128, NP);
       uint32_t cc = 0, wc = 0;  // chunks and windows consumed
       bool ok = true;
+#if GP_ON
+      long long mwf = 0, mwa = 0, mis = 0;
+#endif
       for (int ci = blockIdx.x; ci < ncodes && ok; ci += gridDim.x) {
         const uint32_t code = codes[ci];
         const PipePair q = pipe_pair(args[code >> kCodeProbShift], code, NP);
@@ -819,12 +858,25 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         for (int w0 = 0; w0 < q.N && ok; w0 += kGramWindow, ++wc) {
           const int wend = min(q.N, w0 + kGramWindow);
           const uint32_t aset = wc & 1u;
+#if GP_ON
+          long long t0 = clock64();
+#endif
           ok = wait(&accempty[aset], ((wc >> 1) & 1u) ^ 1u);  // the epilogue has read this set's last window
+#if GP_ON
+          mwa += clock64() - t0;
+#endif
           tc_fence_after_sync();
           for (int j0 = w0; j0 < wend && ok; j0 += kGramChunk, ++cc) {
             const uint32_t s = cc & 1u;
+#if GP_ON
+            long long t1 = clock64();
+#endif
             ok = wait(&full[s], (cc >> 1) & 1u);
             if (!ok) break;
+#if GP_ON
+            long long t2 = clock64();
+            mwf += t2 - t1;
+#endif
             tc_fence_after_sync();
             const uint32_t base = sbase + s * Sh::STAGE;
             const bool first = j0 == w0;
@@ -846,9 +898,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
             }
             mma_commit(&empty[s]);
             if (j0 + kGramChunk >= wend) mma_commit(&accfull[aset]);
+#if GP_ON
+            mis += clock64() - t2;
+#endif
           }
         }
       }
+#if GP_ON
+      atomicAdd(&g_pprof[5], (unsigned long long)mwf);
+      atomicAdd(&g_pprof[6], (unsigned long long)mwa);
+      atomicAdd(&g_pprof[7], (unsigned long long)mis);
+#endif
       // every MMA issued has completed before the tensor memory is released
       mma_commit(&drain);
       mbar_wait(&drain, 0, kWaitPolls);
@@ -861,6 +921,9 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
     const uint32_t lane_base = (uint32_t)(q4 * 32) << 16;
     uint32_t wc = 0;
     bool ok = true;
+#if GP_ON
+    long long ew = 0, efl = 0, eh = 0;
+#endif
     for (int ci = blockIdx.x; ci < ncodes && ok; ci += gridDim.x) {
       const uint32_t code = codes[ci];
       const GramArgs& a = args[code >> kCodeProbShift];
@@ -882,8 +945,15 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       for (int w0 = 0; w0 < q.N && ok; w0 += kGramWindow, ++wc) {
         const bool last = w0 + kGramWindow >= q.N;
         const uint32_t aset = wc & 1u;
+#if GP_ON
+        long long t0 = clock64();
+#endif
         ok = named_bar_and(kBarEpi, 128, et == 0 ? wait(&accfull[aset], (wc >> 1) & 1u) : true);
         if (!ok) break;
+#if GP_ON
+        long long t1 = clock64();
+        ew += t1 - t0;
+#endif
         tc_fence_after_sync();
 #pragma unroll 1
         for (int cb = 0; cb < mp; cb += 8) {
@@ -915,8 +985,14 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         }
         tc_fence_before_sync();
         mbar_arrive(&accempty[aset]);
+#if GP_ON
+        efl += clock64() - t1;
+#endif
       }
       if (!ok) break;
+#if GP_ON
+      long long t2 = clock64();
+#endif
       named_bar_sync(kBarEpi, 128);  // the last window's sums are in Vs
       bool bad = false;
       for (int i = 0; i < m; ++i) bad = bad || erexp[i] == kBadRow;
@@ -935,7 +1011,17 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
         }
       }
       named_bar_sync(kBarEpi, 128);  // Vs and erexp read before the next pair's last window
+#if GP_ON
+      eh += clock64() - t2;
+#endif
     }
+#if GP_ON
+    if (et == 0) {
+      atomicAdd(&g_pprof[8], (unsigned long long)ew);
+      atomicAdd(&g_pprof[9], (unsigned long long)efl);
+      atomicAdd(&g_pprof[10], (unsigned long long)eh);
+    }
+#endif
   }
   tc_fence_before_sync();
   __syncthreads();
@@ -994,17 +1080,19 @@ bool launch_np(const GramArgs* args, const uint32_t* codes, int n, cudaStream_t 
 
 void prof_reset_gram() {
 #ifdef DH2_PROFILE
-  unsigned long long z[10] = {};
-  cudaMemcpyToSymbol(g_gprof, z, sizeof(z));
+  unsigned long long z[12] = {};
+  cudaMemcpyToSymbol(g_gprof, z, 10 * sizeof(unsigned long long));
+  cudaMemcpyToSymbol(g_pprof, z, sizeof(z));
 #endif
 }
 
-bool prof_read_gram(unsigned long long* out10) {
+bool prof_read_gram(unsigned long long* out22) {
 #ifdef DH2_PROFILE
-  cudaMemcpyFromSymbol(out10, g_gprof, 10 * sizeof(unsigned long long));
+  cudaMemcpyFromSymbol(out22, g_gprof, 10 * sizeof(unsigned long long));
+  cudaMemcpyFromSymbol(out22 + 10, g_pprof, 12 * sizeof(unsigned long long));
   return true;
 #else
-  (void)out10;
+  (void)out22;
   return false;
 #endif
 }

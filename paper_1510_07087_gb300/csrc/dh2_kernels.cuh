@@ -162,8 +162,9 @@ bool launch_gram(const GramArgs* args_dev, const uint32_t* codes, int n, int max
 // Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 17 values.
 void prof_reset_pair();
 bool prof_read_pair(unsigned long long* out17);
-// Phase cycle counters of the Gram kernel (only with -DDH2_PROFILE); 10 values.
+// Phase cycle counters of the Gram kernels (only with -DDH2_PROFILE): 10
+// values of the one-stage form, then 12 of the pipelined form.
 void prof_reset_gram();
-bool prof_read_gram(unsigned long long* out10);
+bool prof_read_gram(unsigned long long* out22);
 
 }  // namespace dh2
