@@ -239,6 +239,35 @@ dh2_status dh2_compress_kernel(const dh2_tree* tree, const double* pts_xyz, doub
 dh2_status dh2_compress_kernel_dlp(const dh2_tree* tree, const double* pts_xyz, const double* normals_xyz,
                                    double kappa, const dh2_compress_params* params, void* stream,
                                    dh2_matrix** out);
+/* ---------------------------------------------------------------- captured schedule
+ * The compression of one problem, or of nprob independent problems as by
+ * dh2_compress_batched, prepared once and captured into a CUDA graph: the
+ * representation(s) are allocated, the launch lists and argument blocks
+ * uploaded and the kernel sequence (block norms and nearfield, leaf factors
+ * and R, the level steps with their capacity launches, expansion, projection)
+ * recorded without running it.  dh2_plan_run replays the whole sequence with
+ * one graph launch on new matrices of the same shapes and leading dimensions;
+ * no allocation, upload of a launch list or host synchronisation happens in
+ * it.  The representation is the same as dh2_compress / dh2_compress_batched
+ * would produce for those matrices.  G, ld, dtype, params: as for
+ * dh2_compress_batched (device matrices only; G gives the first inputs).
+ * The plan owns its matrices (dh2_plan_matrix lends them; they stay valid
+ * until dh2_plan_free and are rewritten by every run).  Errors: EINVAL,
+ * ENOMEM, ECUDA, EUNSUPPORTED (a class beyond the device's shared memory; the
+ * debug and profile builds, which synchronise inside the schedule).  A run's
+ * device status (timeout, non-convergence, non-finite input) is returned by
+ * dh2_plan_wait, which synchronises the stream.  Runs on one plan are
+ * stream-ordered: do not run one plan on two streams at once.  The paper has
+ * no counterpart (scheduling). */
+typedef struct dh2_plan dh2_plan;
+dh2_status dh2_plan_create(int32_t nprob, const dh2_tree* const* trees, const void* const* G, const int64_t* ld,
+                           dh2_dtype dtype, const dh2_compress_params* params, void* stream, dh2_plan** out);
+/* G: nprob device matrices, or NULL for those of the previous run. */
+dh2_status dh2_plan_run(dh2_plan* P, const void* const* G, void* stream);
+dh2_status dh2_plan_wait(dh2_plan* P, void* stream);
+dh2_status dh2_plan_matrix(const dh2_plan* P, int32_t i, dh2_matrix** M);
+void dh2_plan_free(dh2_plan* P);
+
 void dh2_matrix_free(dh2_matrix* M);
 
 /* y = G~ x for the compressed matrix (Section 4: forward transformation,

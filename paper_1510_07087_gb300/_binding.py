@@ -108,6 +108,12 @@ SIGNATURES = [
     ("dh2_compress_kernel_dlp", c_int32, [c_void_p, c_void_p, c_void_p, c_double, POINTER(CompressParams),
                                           c_void_p, POINTER(c_void_p)]),
     ("dh2_matrix_free", None, [c_void_p]),
+    ("dh2_plan_create", c_int32, [c_int32, c_void_p, c_void_p, c_void_p, c_int32, POINTER(CompressParams), c_void_p,
+                                  POINTER(c_void_p)]),
+    ("dh2_plan_run", c_int32, [c_void_p, c_void_p, c_void_p]),
+    ("dh2_plan_wait", c_int32, [c_void_p, c_void_p]),
+    ("dh2_plan_matrix", c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
+    ("dh2_plan_free", None, [c_void_p]),
     ("dh2_matvec", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_matvec_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_matvec_adjoint", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
@@ -271,16 +277,17 @@ def _colmajor_ld(G) -> int:
 class Matrix:
     """Owner of a dh2_matrix handle (device-resident DH^2 representation)."""
 
-    def __init__(self, handle: int, tree: Tree, mode: int, G):
+    def __init__(self, handle: int, tree: Tree, mode: int, G, owner=None):
         self.handle = c_void_p(handle)
         self.tree = tree
         self.mode = mode
         self._G = G  # keeps a viewed nearfield alive
+        self._owner = owner  # a Plan that owns the handle (None: this object owns it)
 
     def __del__(self):
-        if getattr(self, "handle", None) and self.handle.value:
+        if self._owner is None and getattr(self, "handle", None) and self.handle.value:
             _lib().dh2_matrix_free(self.handle)
-            self.handle = c_void_p()
+        self.handle = c_void_p()
 
     def ranks(self, side: int) -> np.ndarray:
         out = np.empty(self.tree.stats().npairs[side], dtype=np.int32)
@@ -419,6 +426,68 @@ def dh2_compress_batched(trees, Gs, eps: float = 1e-4, zeta: float = 2.0 / 3.0, 
     _check(_lib().dh2_compress_batched(n, th, gp, lds, dt, byref(p), c_void_p(_stream_handle(stream)), outs),
            "dh2_compress_batched")
     return [Matrix(outs[i], trees[i], mode, Gs[i]) for i in range(n)]
+
+
+class Plan:
+    """Owner of a dh2_plan handle: the compression of one or several problems captured once into a CUDA
+    graph (include/dh2.h, dh2_plan_create) and replayed by run() on new matrices of the same shapes."""
+
+    def __init__(self, trees, Gs, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,
+                 mode: int | None = None, nearfield: int = 0, max_sweeps: int = 0, stream=None):
+        n = len(trees)
+        if n != len(Gs) or n == 0:
+            raise ValueError("need one matrix per tree")
+        dt = _dtype_code(Gs[0])
+        if any(_dtype_code(g) != dt for g in Gs):
+            raise TypeError("all matrices must have the same dtype")
+        if mode is None:
+            mode = MODE_FP32 if dt == DH2_C64 else MODE_FP64
+        self.handle = c_void_p()
+        self.trees = list(trees)
+        self.mode = mode
+        self.lds = [_colmajor_ld(g) for g in Gs]
+        self._dt = dt
+        th = (c_void_p * n)(*[t.handle for t in trees])
+        gp = (c_void_p * n)(*[g.data_ptr() for g in Gs])
+        lds = (c_int64 * n)(*self.lds)
+        p = _params(eps, zeta, err_mode, mode, nearfield, max_sweeps)
+        h = c_void_p()
+        _check(_lib().dh2_plan_create(n, th, gp, lds, dt, byref(p), c_void_p(_stream_handle(stream)), byref(h)),
+               "dh2_plan_create")
+        self.handle = h
+        self._Gs = list(Gs)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib().dh2_plan_free(self.handle)
+            self.handle = c_void_p()
+
+    def run(self, Gs=None, stream=None) -> None:
+        """Replay the captured schedule on Gs (same dtypes, shapes and leading dimensions), or on the
+        matrices of the previous run; stream-ordered, no host synchronisation."""
+        if Gs is None:
+            gp = None
+        else:
+            if len(Gs) != len(self.trees):
+                raise ValueError("need one matrix per tree")
+            for g, ld in zip(Gs, self.lds):
+                if _dtype_code(g) != self._dt or _colmajor_ld(g) != ld:
+                    raise ValueError("a plan runs on matrices of its own dtype and leading dimension")
+            self._Gs = list(Gs)
+            gp = (c_void_p * len(Gs))(*[g.data_ptr() for g in Gs])
+        _check(_lib().dh2_plan_run(self.handle, gp, c_void_p(_stream_handle(stream))), "dh2_plan_run")
+
+    def wait(self, stream=None) -> None:
+        """Synchronise the stream and raise the last run's device status, if any."""
+        _check(_lib().dh2_plan_wait(self.handle, c_void_p(_stream_handle(stream))), "dh2_plan_wait")
+
+    def matrices(self) -> list:
+        out = []
+        for i, t in enumerate(self.trees):
+            h = c_void_p()
+            _check(_lib().dh2_plan_matrix(self.handle, i, byref(h)), "dh2_plan_matrix")
+            out.append(Matrix(h.value, t, self.mode, self._Gs[i], owner=self))
+        return out
 
 
 def dh2_compress_kernel(tree: Tree, points: np.ndarray, kappa: float, diag: float, eps: float = 1e-4,

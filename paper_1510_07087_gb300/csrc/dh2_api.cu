@@ -699,12 +699,27 @@ struct HostStage {
   const PanelPlan* plan;
 };
 
+// A compression captured into a CUDA graph (dh2_plan): the graph, the scratch
+// it works in, and a function that writes new matrix pointers into the
+// device copies of the kernels' argument blocks before a replay.
+struct PlanState {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* scratch = nullptr;
+  bool ok_launch = true;
+  std::function<cudaError_t(const void* const* G, cudaStream_t st)> set_inputs;
+};
+
 // The compression of one or several independent problems: each phase is one
 // launch over every problem (block norms, leaf factors, one launch per level
 // for the non-leaf steps), then expansion and projection per problem.
 template <typename T>
 dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params& cp, cudaStream_t st,
-                        const HostStage* hs = nullptr) {
+                        const HostStage* hs = nullptr, PlanState* plan = nullptr) {
+#if defined(DH2_CHECK) || defined(DH2_PROFILE)
+  if (plan) return DH2_EUNSUPPORTED;  // these builds synchronise inside the schedule
+#endif
+  if (plan && hs) return DH2_EINVAL;
   bool any_gen = false;  // entries generated in the kernels (matrix-free mode)
   for (const dh2_matrix* M : Ms) any_gen = any_gen || M->gen != 0;
   const int nprob = (int)Ms.size();
@@ -987,7 +1002,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
   }
   cudaEvent_t ev[7] = {};
-  for (int i = 0; i < 7 && ce == cudaSuccess; ++i) ce = cudaEventCreate(&ev[i]);
+  for (int i = 0; i < 7 && ce == cudaSuccess && !plan; ++i) ce = cudaEventCreate(&ev[i]);
+  auto rec = [&](int i) {  // phase boundaries (not in a captured schedule)
+    if (!plan) cudaEventRecord(ev[i], st);
+  };
   if (ce != cudaSuccess) {
     cudaGetLastError();
     for (cudaEvent_t e : ev)
@@ -1019,7 +1037,17 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     check_set_limits_ops(lim);
   }
 #endif
-  cudaEventRecord(ev[0], st);
+  if (plan) {
+    // everything from here to the projection becomes the graph; each replay
+    // starts by clearing the status words
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeAsync(scratch, st);
+      return DH2_ECUDA;
+    }
+    for (dh2_matrix* M : Ms) cudaMemsetAsync(M->status, 0, sizeof(uint32_t), st);
+  }
+  rec(0);
   bool ok_launch = true;  // false once a launch needed more shared memory than the device has
   int nlaunch = 0;  // kernels launched by this compression (counted where they are issued)
   int32_t kcl[DH2_KC_COUNT] = {};  // the same, by kernel class
@@ -1120,8 +1148,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       counted(DH2_KC_NORMS, true);
     }
     DH2_PHASE_SYNC("panels");
-    cudaEventRecord(ev[1], st);
-    cudaEventRecord(ev[2], st);
+    rec(1);
+    rec(2);
     for (cudaEvent_t e : pev)
       if (e) cudaEventDestroy(e);
     if (cs) cudaStreamDestroy(cs);
@@ -1131,12 +1159,12 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     colw_side(kSideRow);
     colw_side(kSideCol);
     DH2_PHASE_SYNC("norms_near");
-    cudaEventRecord(ev[1], st);
+    rec(1);
 #ifdef DH2_PROFILE
     prof_reset_pair();
     prof_reset_gram();
 #endif
-    if (mixed) {
+    if (mixed && !plan) {
       kev_ok = true;
       for (int i = 0; i < 3 * kLeafClasses && kev_ok; ++i)
         kev_ok = cudaEventCreate(&kev[i]) == cudaSuccess;
@@ -1145,7 +1173,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int c = 0; c < kLeafClasses; ++c)
       leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c,
                   kev_ok && cls_begin[c + 1] > cls_begin[c]);
-    cudaEventRecord(ev[2], st);
+    rec(2);
     // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
     for (int c = 0; c < kLeafClasses; ++c) {
       const int64_t nt = tile_cls_begin[c + 1] - tile_cls_begin[c];
@@ -1157,7 +1185,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
   }
 #ifdef DH2_PROFILE
-  {
+  if (!plan) {
     cudaStreamSynchronize(st);
     unsigned long long pr[17];
     prof_read_pair(pr);
@@ -1192,7 +1220,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   }
 #endif
   DH2_PHASE_SYNC("leaf pairs");
-  cudaEventRecord(ev[3], st);
+  rec(3);
   {
     // the class split needs the sons' ranks, known only on the device: each
     // class is launched at the level's capacity and its CTAs past the class's
@@ -1222,7 +1250,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       DH2_PHASE_SYNC("non-leaf pairs");
     }
   }
-  cudaEventRecord(ev[4], st);
+  rec(4);
   for (dh2_matrix* M : Ms) {
     Tree& tr = M->tree->tr;
     Tree::Dev* D = tr.dev;
@@ -1236,7 +1264,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       DH2_PHASE_SYNC("expand");
     }
   }
-  cudaEventRecord(ev[5], st);
+  rec(5);
   for (dh2_matrix* M : Ms) {
     Tree& tr = M->tree->tr;
     Tree::Dev* D = tr.dev;
@@ -1256,7 +1284,44 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     counted(DH2_KC_PROJECT, D->nadm > 0);
     DH2_PHASE_SYNC("project");
   }
-  cudaEventRecord(ev[6], st);
+  rec(6);
+  if (plan) {
+    cudaGraph_t g = nullptr;
+    const cudaError_t e0 = cudaStreamEndCapture(st, &g);
+    cudaError_t e1 = e0;
+    if (e0 == cudaSuccess) e1 = cudaGraphInstantiate(&plan->exec, g, 0);
+    if (e0 != cudaSuccess || e1 != cudaSuccess) {
+      cudaGetLastError();
+      if (g) cudaGraphDestroy(g);
+      plan->exec = nullptr;
+      cudaFreeAsync(scratch, st);
+      return DH2_ECUDA;
+    }
+    plan->graph = g;
+    plan->scratch = scratch;
+    plan->ok_launch = ok_launch;
+    // new inputs: the matrix pointers in the host copies of the argument
+    // blocks, then those blocks to the device (before the graph runs)
+    plan->set_inputs = [pas, nas, gas, d_pa, d_na, d_ga, nprob, mixed](const void* const* G,
+                                                                     cudaStream_t s2) mutable -> cudaError_t {
+      for (int i = 0; i < nprob; ++i) {
+        pas[i].G = (const C2<T>*)G[i];
+        nas[i].G = (const C2<T>*)G[i];
+        if (mixed) gas[i].G = (const C2<float>*)G[i];
+      }
+      cudaError_t e = cudaMemcpyAsync(d_pa, pas.data(), sizeof(PairArgs<T>) * nprob, cudaMemcpyHostToDevice, s2);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_na, nas.data(), sizeof(NormsArgs<T>) * nprob, cudaMemcpyHostToDevice, s2);
+      if (e == cudaSuccess && mixed)
+        e = cudaMemcpyAsync(d_ga, gas.data(), sizeof(GramArgs) * nprob, cudaMemcpyHostToDevice, s2);
+      return e;
+    };
+    for (dh2_matrix* M : Ms) {
+      M->launches = nlaunch;
+      std::memcpy(M->class_launches, kcl, sizeof(kcl));
+    }
+    return DH2_OK;
+  }
   cudaFreeAsync(scratch, st);
   std::vector<uint32_t> status(nprob, 0);
   cudaError_t e1 = cudaSuccess;
@@ -1758,6 +1823,106 @@ dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, con
   }
   for (int i = 0; i < nprob; ++i) out[i] = Ms[i];
   return DH2_OK;
+}
+
+struct dh2_plan {
+  std::vector<dh2_matrix*> Ms;
+  std::vector<const void*> G;  // the matrices of the last run
+  PlanState ps;
+  cudaStream_t stream = nullptr;  // the stream the plan was made on (for the release)
+};
+
+dh2_status dh2_plan_create(int32_t nprob, const dh2_tree* const* trees, const void* const* G, const int64_t* ld,
+                           dh2_dtype dtype, const dh2_compress_params* params, void* stream, dh2_plan** out) {
+  if (!out || nprob < 1) return DH2_EINVAL;
+  *out = nullptr;
+  if (nprob > kMaxBatch || !trees || !G || !ld || !params) return DH2_EINVAL;
+  if (nprob > 1 && (params->rank_override[0] || params->rank_override[1])) return DH2_EINVAL;
+  dh2_plan* P = new (std::nothrow) dh2_plan;
+  if (!P) return DH2_ENOMEM;
+  P->stream = (cudaStream_t)stream;
+  for (int i = 0; i < nprob; ++i) {
+    dh2_matrix* M = nullptr;
+    const dh2_status s = G[i] ? prepare_matrix(trees[i], G[i], dtype, ld[i], nullptr, 0.0, 0.0, params, stream, &M)
+                              : DH2_EINVAL;
+    if (s != DH2_OK) {
+      for (dh2_matrix* m : P->Ms) matrix_release(m);
+      delete P;
+      return s;
+    }
+    P->Ms.push_back(M);
+    P->G.push_back(G[i]);
+  }
+  const dh2_status s = mode_f32(params->mode)
+                           ? run_compress<float>(P->Ms, *params, (cudaStream_t)stream, nullptr, &P->ps)
+                           : run_compress<double>(P->Ms, *params, (cudaStream_t)stream, nullptr, &P->ps);
+  if (s == DH2_OK && !P->ps.ok_launch) {
+    dh2_plan_free(P);
+    return DH2_EUNSUPPORTED;
+  }
+  if (s != DH2_OK) {
+    for (dh2_matrix* m : P->Ms) matrix_release(m);
+    delete P;
+    return s;
+  }
+  *out = P;
+  return DH2_OK;
+}
+
+dh2_status dh2_plan_run(dh2_plan* P, const void* const* G, void* stream) {
+  if (!P || !P->ps.exec) return DH2_EINVAL;
+  const int n = (int)P->Ms.size();
+  if (G)
+    for (int i = 0; i < n; ++i) {
+      if (!G[i]) return DH2_EINVAL;
+      P->G[i] = G[i];
+    }
+  for (int i = 0; i < n; ++i) P->Ms[i]->G = P->G[i];  // view-mode nearfield, products and errors read it
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = P->ps.set_inputs(P->G.data(), st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(P->ps.exec, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return DH2_ECUDA;
+  }
+  return DH2_OK;
+}
+
+dh2_status dh2_plan_wait(dh2_plan* P, void* stream) {
+  if (!P) return DH2_EINVAL;
+  const int n = (int)P->Ms.size();
+  std::vector<uint32_t> status(n, 0);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(&status[i], P->Ms[i]->status, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    cudaGetLastError();
+    return DH2_ECUDA;
+  }
+  uint32_t all = 0;
+  for (uint32_t v : status) all |= v;
+  if (all & kStatusTimeout) return DH2_ETIMEOUT;
+  if (all & kStatusTooLarge) return DH2_EUNSUPPORTED;
+  if (all & (kStatusNoConv | kStatusNaN)) return DH2_ENOCONV;
+  return DH2_OK;
+}
+
+dh2_status dh2_plan_matrix(const dh2_plan* P, int32_t i, dh2_matrix** M) {
+  if (!P || !M || i < 0 || i >= (int32_t)P->Ms.size()) return DH2_EINVAL;
+  *M = P->Ms[i];
+  return DH2_OK;
+}
+
+void dh2_plan_free(dh2_plan* P) {
+  if (!P) return;
+  if (P->ps.exec) cudaGraphExecDestroy(P->ps.exec);
+  if (P->ps.graph) cudaGraphDestroy(P->ps.graph);
+  if (P->ps.scratch) cudaFreeAsync(P->ps.scratch, P->stream);
+  for (dh2_matrix* m : P->Ms) matrix_release(m);
+  cudaGetLastError();
+  delete P;
 }
 
 void dh2_matrix_free(dh2_matrix* M) { matrix_release(M); }

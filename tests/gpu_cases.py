@@ -54,7 +54,7 @@ class Case:
     """One compression of a seeded Helmholtz (or given) matrix on the GPU and by the oracle."""
 
     def __init__(self, n, kappa, leaf, eps, mode, eta1=2 * math.sqrt(2), eta2=1.0, G=None, dir_rule=0,
-                 nearfield=0, pts=None):
+                 nearfield=0, pts=None, compress=True):
         D = dev()
         self.D = D
         pts = fibonacci_sphere(n) if pts is None else pts
@@ -69,7 +69,17 @@ class Case:
         dt = torch.complex128 if mode == D.MODE_FP64 else torch.complex64
         self.Gd = colmajor(self.G, dt)
         self.mode = mode
-        self.M = D.dh2_compress(self.T, self.Gd, eps=eps, mode=mode, nearfield=nearfield)
+        w = O.block_weights(self.tr, O.block_norms(self.tr, self.G), self.cp.zeta)
+        self.w = w
+        self.V = O.compress(self.tr, self.G, self.cp, "row", w)
+        self.W = O.compress(self.tr, self.G, self.cp, "col", w)
+        if compress:
+            self.attach(D.dh2_compress(self.T, self.Gd, eps=eps, mode=mode, nearfield=nearfield))
+
+    def attach(self, M):
+        """Take M (a compression of this case's tree and matrix) as the GPU result: its ranks, and the
+        oracle re-run at them."""
+        self.M = M
         self.launches = self.M.class_launches()
         self.rank = {}
         self.pid = {}
@@ -79,10 +89,7 @@ class Case:
             self.rank[side] = {(int(pr["cluster"][p]), int(pr["dir"][p])): int(rk[p]) for p in range(len(rk))}
             for p in range(len(rk)):
                 self.pid[(side, int(pr["cluster"][p]), int(pr["dir"][p]))] = p
-        w = O.block_weights(self.tr, O.block_norms(self.tr, self.G), self.cp.zeta)
-        self.w = w
-        self.V = O.compress(self.tr, self.G, self.cp, "row", w)
-        self.W = O.compress(self.tr, self.G, self.cp, "col", w)
+        w = self.w
         self.Vg = O.compress(self.tr, self.G, self.cp, "row", w, rank_override=self.rank[0])
         self.Wg = O.compress(self.tr, self.G, self.cp, "col", w, rank_override=self.rank[1])
         self.Sg = O.project(self.tr, self.G, self.Vg, self.Wg)
