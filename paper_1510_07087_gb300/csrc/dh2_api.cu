@@ -1829,7 +1829,7 @@ struct dh2_plan {
   std::vector<dh2_matrix*> Ms;
   std::vector<const void*> G;  // the matrices of the last run
   PlanState ps;
-  cudaStream_t stream = nullptr;  // the stream the plan was made on (for the release)
+  cudaStream_t stream = nullptr;  // the library's stream the schedule was prepared and captured on
 };
 
 dh2_status dh2_plan_create(int32_t nprob, const dh2_tree* const* trees, const void* const* G, const int64_t* ld,
@@ -1840,7 +1840,14 @@ dh2_status dh2_plan_create(int32_t nprob, const dh2_tree* const* trees, const vo
   if (nprob > 1 && (params->rank_override[0] || params->rank_override[1])) return DH2_EINVAL;
   dh2_plan* P = new (std::nothrow) dh2_plan;
   if (!P) return DH2_ENOMEM;
-  P->stream = (cudaStream_t)stream;
+  // the capture runs on a stream of the library's own (the caller's may be the
+  // legacy default stream, which cannot be captured); the caller's stream is
+  // synchronised once the representations are allocated on it
+  if (cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete P;
+    return DH2_ECUDA;
+  }
   for (int i = 0; i < nprob; ++i) {
     dh2_matrix* M = nullptr;
     const dh2_status s = G[i] ? prepare_matrix(trees[i], G[i], dtype, ld[i], nullptr, 0.0, 0.0, params, stream, &M)
@@ -1853,16 +1860,15 @@ dh2_status dh2_plan_create(int32_t nprob, const dh2_tree* const* trees, const vo
     P->Ms.push_back(M);
     P->G.push_back(G[i]);
   }
-  const dh2_status s = mode_f32(params->mode)
-                           ? run_compress<float>(P->Ms, *params, (cudaStream_t)stream, nullptr, &P->ps)
-                           : run_compress<double>(P->Ms, *params, (cudaStream_t)stream, nullptr, &P->ps);
-  if (s == DH2_OK && !P->ps.ok_launch) {
-    dh2_plan_free(P);
-    return DH2_EUNSUPPORTED;
-  }
+  dh2_status s = cudaStreamSynchronize((cudaStream_t)stream) == cudaSuccess ? DH2_OK : DH2_ECUDA;
+  if (s == DH2_OK)
+    s = mode_f32(params->mode) ? run_compress<float>(P->Ms, *params, P->stream, nullptr, &P->ps)
+                               : run_compress<double>(P->Ms, *params, P->stream, nullptr, &P->ps);
+  if (s == DH2_OK && cudaStreamSynchronize(P->stream) != cudaSuccess) s = DH2_ECUDA;  // uploads done
+  if (s == DH2_OK && !P->ps.ok_launch) s = DH2_EUNSUPPORTED;
   if (s != DH2_OK) {
-    for (dh2_matrix* m : P->Ms) matrix_release(m);
-    delete P;
+    cudaGetLastError();
+    dh2_plan_free(P);
     return s;
   }
   *out = P;
@@ -1917,10 +1923,16 @@ dh2_status dh2_plan_matrix(const dh2_plan* P, int32_t i, dh2_matrix** M) {
 
 void dh2_plan_free(dh2_plan* P) {
   if (!P) return;
+  // replays may still run on the caller's streams: the device finishes first
+  cudaDeviceSynchronize();
   if (P->ps.exec) cudaGraphExecDestroy(P->ps.exec);
   if (P->ps.graph) cudaGraphDestroy(P->ps.graph);
   if (P->ps.scratch) cudaFreeAsync(P->ps.scratch, P->stream);
   for (dh2_matrix* m : P->Ms) matrix_release(m);
+  if (P->stream) {
+    cudaStreamSynchronize(P->stream);
+    cudaStreamDestroy(P->stream);
+  }
   cudaGetLastError();
   delete P;
 }
@@ -2082,25 +2094,13 @@ dh2_status run_error_spectral(dh2_matrix* M, const void* Gref, dh2_dtype rdt, in
     if (rdt == DH2_C128 && Gref) launch_gemv<double>((const C2<double>*)Gref, ldr, gen, n, trans, x, y, st);
     else launch_gemv<float>((const C2<float>*)Gref, ldr, gen, n, trans, x, y, st);
   };
-  std::vector<C2<double>> h(n);
-  auto start = [&]() -> dh2_status {  // seeded start vector, unit norm
-    uint64_t z = 0x9E3779B97F4A7C15ull;
-    double s2 = 0;
-    for (int64_t i = 0; i < n; ++i) {
-      z ^= z << 13;
-      z ^= z >> 7;
-      z ^= z << 17;
-      const double re = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
-      z ^= z << 13;
-      z ^= z >> 7;
-      z ^= z << 17;
-      const double im = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
-      h[i] = C2<double>{re, im};
-      s2 += re * re + im * im;
-    }
-    const double sc = 1.0 / std::sqrt(s2);
-    for (auto& e : h) e = C2<double>{e.re * sc, e.im * sc};
-    DH2_CUDA_TRY(cudaMemcpyAsync(v, h.data(), sizeof(C2<double>) * n, cudaMemcpyHostToDevice, st));
+  double* d_n2 = M->acc + 2;  // |w|^2 of the current iteration (device)
+  // seeded start vector of unit norm, on the device
+  auto start = [&]() -> dh2_status {
+    launch_seed_vector(v, n, 0x9E3779B97F4A7C15ull, st);
+    DH2_CUDA_TRY(cudaMemsetAsync(d_n2, 0, sizeof(double), st));
+    launch_norm2(v, n, d_n2, st);
+    launch_normalize(v, v, n, d_n2, st);
     return DH2_OK;
   };
   // lambda_max(A^* A) for A = G_ref - G~ (err) or A = G_ref; w = A^* A v, v <- w / |w|
@@ -2123,16 +2123,15 @@ dh2_status run_error_spectral(dh2_matrix* M, const void* Gref, dh2_dtype rdt, in
         if (s != DH2_OK) return s;
         launch_sub<T>(w, yt, n, st);
       }
-      DH2_CUDA_TRY(cudaMemcpyAsync(h.data(), w, sizeof(C2<double>) * n, cudaMemcpyDeviceToHost, st));
+      DH2_CUDA_TRY(cudaMemsetAsync(d_n2, 0, sizeof(double), st));
+      launch_norm2(w, n, d_n2, st);
+      launch_normalize(v, w, n, d_n2, st);
+      double s2 = 0.0;
+      DH2_CUDA_TRY(cudaMemcpyAsync(&s2, d_n2, sizeof(double), cudaMemcpyDeviceToHost, st));
       DH2_CUDA_TRY(cudaStreamSynchronize(st));
-      double s2 = 0;
-      for (const auto& e : h) s2 += e.re * e.re + e.im * e.im;
       const double nw = std::sqrt(s2);  // |A^* A v| with |v| = 1
       *lam = nw;
       if (!(nw > 0.0)) return DH2_OK;
-      const double sc = 1.0 / nw;
-      for (auto& e : h) e = C2<double>{e.re * sc, e.im * sc};
-      DH2_CUDA_TRY(cudaMemcpyAsync(v, h.data(), sizeof(C2<double>) * n, cudaMemcpyHostToDevice, st));
       if (it > 2 && std::fabs(nw - prev) <= 1e-6 * nw) break;
       prev = nw;
     }

@@ -703,6 +703,40 @@ __global__ void sub_kernel(C2<double>* __restrict__ u, const C2<T>* __restrict__
     u[i] = C2<double>{u[i].re - (double)t[i].re, u[i].im - (double)t[i].im};
 }
 
+// |v|^2 summed into *acc (zeroed by the caller)
+__global__ void norm2_kernel(const C2<double>* __restrict__ v, int64_t n, double* __restrict__ acc) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += v[i].re * v[i].re + v[i].im * v[i].im;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
+}
+
+// v = w / sqrt(*n2) (v may be w); nothing when *n2 is not positive
+__global__ void normalize_kernel(C2<double>* __restrict__ v, const C2<double>* w, int64_t n,
+                                 const double* __restrict__ n2) {
+  const double t = *n2;
+  if (!(t > 0.0)) return;
+  const double sc = rsqrt(t);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v[i] = C2<double>{w[i].re * sc, w[i].im * sc};
+}
+
+// a seeded start vector: entry i from two splitmix64 draws of (seed, i), each in [-1/2, 1/2)
+__global__ void seed_vector_kernel(C2<double>* __restrict__ v, int64_t n, uint64_t seed) {
+  auto mix = [](uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = mix(seed ^ (2 * (uint64_t)i)), b = mix(seed ^ (2 * (uint64_t)i + 1));
+    v[i] = C2<double>{(double)(a >> 11) * (1.0 / 9007199254740992.0) - 0.5,
+                      (double)(b >> 11) * (1.0 / 9007199254740992.0) - 0.5};
+  }
+}
+
 }  // namespace
 
 void check_set_limits_ops(const CheckLimits& l) {
@@ -795,6 +829,16 @@ template <typename T>
 void launch_to_type(const C2<double>* v, C2<T>* o, int64_t n, cudaStream_t st) {
   if (n > 0) to_type_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, o, n);
 }
+void launch_norm2(const C2<double>* v, int64_t n, double* acc, cudaStream_t st) {
+  if (n > 0) norm2_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 4), 256, 0, st>>>(v, n, acc);
+}
+void launch_normalize(C2<double>* v, const C2<double>* w, int64_t n, const double* n2, cudaStream_t st) {
+  if (n > 0) normalize_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, w, n, n2);
+}
+void launch_seed_vector(C2<double>* v, int64_t n, uint64_t seed, cudaStream_t st) {
+  if (n > 0) seed_vector_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, n, seed);
+}
+
 template <typename T>
 void launch_sub(C2<double>* u, const C2<T>* t, int64_t n, cudaStream_t st) {
   if (n > 0) sub_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(u, t, n);

@@ -158,6 +158,10 @@ template <typename T>
 void launch_closed_form(const ErrArgs<T>& a, const double* bnorm2, int nblocks, double* acc, cudaStream_t st);
 // o = (T) v; u -= t  (vectors of n complex entries)
 template <typename T> void launch_to_type(const C2<double>* v, C2<T>* o, int64_t n, cudaStream_t st);
+// *acc += |v|^2; v = w / sqrt(*n2) (device scalar; v may be w); a seeded vector with entries in [-1/2, 1/2)^2
+void launch_norm2(const C2<double>* v, int64_t n, double* acc, cudaStream_t st);
+void launch_normalize(C2<double>* v, const C2<double>* w, int64_t n, const double* n2, cudaStream_t st);
+void launch_seed_vector(C2<double>* v, int64_t n, uint64_t seed, cudaStream_t st);
 template <typename T> void launch_sub(C2<double>* u, const C2<T>* t, int64_t n, cudaStream_t st);
 
 }  // namespace dh2
