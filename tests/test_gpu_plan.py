@@ -83,7 +83,8 @@ def test_plan_replays_on_new_matrices():
     M1 = D.dh2_compress(T, Gd1, eps=1e-4)
     _same(P.matrices()[0], M1, T)
     # a matrix of another leading dimension is refused before anything runs
-    wide = torch.zeros((2050, 2048), dtype=torch.complex64, device="cuda").t()[:, :2048]  # ld 2050
+    wide = torch.zeros((2048, 2050), dtype=torch.complex64, device="cuda").t()[:2048]  # column-major, ld 2050
+    assert wide.stride() == (1, 2050)
     with pytest.raises(ValueError):
         P.run([wide])
 
