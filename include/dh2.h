@@ -336,7 +336,7 @@ enum {
 dh2_status dh2_error(const dh2_matrix* M, const void* G_ref, dh2_dtype ref_dtype, int64_t ld, int32_t which,
                      void* stream, double* rel_err);
 
-/* Ranks of the used pairs of one side (host, npairs entries). */
+/* Ranks of the used pairs of one side (host, npairs entries; may be NULL when the side has no pair). */
 dh2_status dh2_matrix_ranks(const dh2_matrix* M, int32_t side, int32_t* ranks);
 /* Singular values resolved individually for one pair (host, up to `cap`
  * doubles, sorted descending); *count receives how many were resolved.  The

@@ -2222,8 +2222,10 @@ dh2_status dh2_error(const dh2_matrix* Mc, const void* G_ref, dh2_dtype ref_dtyp
 }
 
 dh2_status dh2_matrix_ranks(const dh2_matrix* M, int32_t side, int32_t* ranks) {
-  if (!M || !ranks || (side != 0 && side != 1)) return DH2_EINVAL;
+  if (!M || (side != 0 && side != 1)) return DH2_EINVAL;
   const int64_t np = M->tree->tr.dev->npairs[side];
+  if (np == 0) return DH2_OK;  // no pairs on this side (no admissible block): nothing to write
+  if (!ranks) return DH2_EINVAL;
   DH2_CUDA_TRY(cudaMemcpyAsync(ranks, M->rank[side], 4 * np, cudaMemcpyDeviceToHost, M->stream));
   DH2_CUDA_TRY(cudaStreamSynchronize(M->stream));
   return DH2_OK;
