@@ -745,7 +745,9 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   const uint32_t* d_norm = nullptr;
   std::vector<const uint32_t*> d_nl(maxdepth + 1, nullptr);
   std::vector<int64_t> n_nl(maxdepth + 1, 0);
-  int64_t n_leaf = 0, n_norm = 0;
+  int64_t n_leaf = 0, n_norm = 0, n_norm_adm = 0;
+  const uint32_t* d_norm_adm = nullptr;   // the admissible blocks' codes
+  const uint32_t* d_norm_near = nullptr;  // the nearfield blocks' codes
   // R tiles (code << 32 | first column) in the order of the codes
   const uint64_t* d_ltiles = nullptr;
   std::vector<const uint64_t*> d_nltiles(maxdepth + 1, nullptr);
@@ -779,7 +781,14 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         for (int sd = 0; sd < 2; ++sd)
           for (int64_t p : tr.side[sd].nonleaf_by_level[l])
             nl_codes[l].push_back(((uint32_t)i << kCodeProbShift) | ((uint32_t)sd << kCodeSideShift) | (uint32_t)p);
-      for (size_t b = 0; b < tr.blocks.size(); ++b) norm_codes.push_back(((uint32_t)i << 26) | (uint32_t)b);
+      for (size_t b = 0; b < tr.blocks.size(); ++b)
+        if (tr.blocks[b].adm) norm_codes.push_back(((uint32_t)i << 26) | (uint32_t)b);
+    }
+    n_norm_adm = (int64_t)norm_codes.size();  // admissible blocks first, then the nearfield blocks
+    for (int i = 0; i < nprob; ++i) {
+      const Tree& tr = Ms[i]->tree->tr;
+      for (size_t b = 0; b < tr.blocks.size(); ++b)
+        if (!tr.blocks[b].adm) norm_codes.push_back(((uint32_t)i << 26) | (uint32_t)b);
     }
     std::stable_sort(lc.begin(), lc.end(), [](const LC& a, const LC& b) {
       return a.cls != b.cls ? a.cls < b.cls : a.cost > b.cost;
@@ -951,6 +960,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     n_leaf = (int64_t)leaf_codes.size();
     d_norm = up(norm_codes);
     n_norm = (int64_t)norm_codes.size();
+    d_norm_adm = d_norm;
+    d_norm_near = d_norm + n_norm_adm;
     for (int l = 0; l <= maxdepth; ++l) {
       d_nl[l] = up(nl_codes[l]);
       n_nl[l] = (int64_t)nl_codes[l].size();
@@ -977,6 +988,9 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     for (int c = 0; c <= kLeafClasses; ++c) tile_cls_begin[c] = D->leaf_tile_class_begin[c];
     d_norm = nullptr;
     n_norm = (int64_t)tr.blocks.size();
+    n_norm_adm = D->nadm;
+    d_norm_adm = (const uint32_t*)D->adm_list;  // block ids of problem 0: the codes themselves
+    d_norm_near = (const uint32_t*)D->inadm_list;
     for (int l = 0; l <= tr.depth; ++l) {
       d_nl[l] = D->codes + D->nl_code_begin[l];
       n_nl[l] = D->nl_code_count[l];
@@ -1037,11 +1051,41 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     check_set_limits_ops(lim);
   }
 #endif
+  // mixed mode, dense input, nearfield copied: the copies depend on G alone and
+  // run on a low-priority side stream under the leaf work (the Gram kernels
+  // hold one CTA per SM and leave threads and registers free), joined before
+  // the end of the schedule
+  cudaStream_t sst = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool split_near = mixed && !any_gen && !hs && cp.nearfield == 0 && n_norm > n_norm_adm;
+  if (split_near) {
+    int lo = 0, hi = 0;
+    split_near = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+                 cudaStreamCreateWithPriority(&sst, cudaStreamNonBlocking, lo) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) == cudaSuccess;
+    if (!split_near) {  // everything on the one stream
+      cudaGetLastError();
+      if (sst) cudaStreamDestroy(sst);
+      if (ev_fork) cudaEventDestroy(ev_fork);
+      if (ev_join) cudaEventDestroy(ev_join);
+      sst = nullptr;
+      ev_fork = ev_join = nullptr;
+    }
+  }
+  auto release_side = [&]() {
+    if (sst) cudaStreamDestroy(sst);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    sst = nullptr;
+    ev_fork = ev_join = nullptr;
+  };
   if (plan) {
     // everything from here to the projection becomes the graph; each replay
     // starts by clearing the status words
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
+      release_side();
       cudaFreeAsync(scratch, st);
       return DH2_ECUDA;
     }
@@ -1154,8 +1198,18 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       if (e) cudaEventDestroy(e);
     if (cs) cudaStreamDestroy(cs);
   } else {
-    launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
-    counted(DH2_KC_NORMS, n_norm > 0);
+    if (split_near) {
+      cudaEventRecord(ev_fork, st);
+      cudaStreamWaitEvent(sst, ev_fork, 0);
+      launch_norms_near<T>(d_na, d_norm_near, (int)(n_norm - n_norm_adm), sst);
+      counted(DH2_KC_NORMS, true);
+      cudaEventRecord(ev_join, sst);
+      launch_norms_near<T>(d_na, d_norm_adm, (int)n_norm_adm, st);
+      counted(DH2_KC_NORMS, n_norm_adm > 0);
+    } else {
+      launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
+      counted(DH2_KC_NORMS, n_norm > 0);
+    }
     colw_side(kSideRow);
     colw_side(kSideCol);
     DH2_PHASE_SYNC("norms_near");
@@ -1284,10 +1338,12 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     counted(DH2_KC_PROJECT, D->nadm > 0);
     DH2_PHASE_SYNC("project");
   }
+  if (split_near) cudaStreamWaitEvent(st, ev_join, 0);  // the nearfield copies are part of the result
   rec(6);
   if (plan) {
     cudaGraph_t g = nullptr;
     const cudaError_t e0 = cudaStreamEndCapture(st, &g);
+    release_side();
     cudaError_t e1 = e0;
     if (e0 == cudaSuccess) e1 = cudaGraphInstantiate(&plan->exec, g, 0);
     if (e0 != cudaSuccess || e1 != cudaSuccess) {
@@ -1322,6 +1378,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
     return DH2_OK;
   }
+  release_side();  // the work already enqueued on the side stream still runs
   cudaFreeAsync(scratch, st);
   std::vector<uint32_t> status(nprob, 0);
   cudaError_t e1 = cudaSuccess;

@@ -83,3 +83,20 @@ def test_batched_rejects_mixed_dtypes():
     Gs[1] = Gs[1].to(torch.complex64)
     with pytest.raises(TypeError):
         D.dh2_compress_batched(trees[:2], Gs[:2])
+
+
+def test_batched_mixed_equals_single():
+    """The mixed mode's batch (row scales, tensor-core Gram matrices, factor launches over all
+    problems; the nearfield copies on the side stream) equals each problem's own compression."""
+    D = _dev()
+    trees, Gs, Gh = _setup(D, torch.complex64)
+    mode = D.MODE_MIXED_BF16X3
+    Mb = D.dh2_compress_batched(trees, Gs, eps=1e-4, mode=mode)
+    for T, G, G64h, M in zip(trees, Gs, Gh, Mb):
+        Ms = D.dh2_compress(T, G, eps=1e-4, mode=mode)
+        for side in (0, 1):
+            assert np.array_equal(M.ranks(side), Ms.ranks(side))
+        assert M.storage() == Ms.storage()
+        G128 = torch.from_numpy(np.ascontiguousarray(G64h.T)).to("cuda").t()
+        eb, es = D.dh2_error(M, G128), D.dh2_error(Ms, G128)
+        assert eb <= 1e-4 and abs(eb - es) <= 1e-12 * es
