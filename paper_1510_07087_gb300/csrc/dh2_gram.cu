@@ -880,6 +880,16 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
             tc_fence_after_sync();
             const uint32_t base = sbase + s * Sh::STAGE;
             const bool first = j0 == w0;
+            // the stage's operand descriptors, formed once per chunk: slices 1-3
+            // and the scaled copy of slice 3, at rows 0 and mp; a K step adds 32
+            // bytes (2 units of 16) to the start address field
+            uint64_t d0[4], d1[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+              d0[x] = desc_kmajor_sw128(base + (uint32_t)x * Sh::SLBYTES);
+              d1[x] = desc_kmajor_sw128(base + (uint32_t)x * Sh::SLBYTES + (uint32_t)q.mp * 128u);
+            }
+            const uint32_t dt0 = tbase + aset * Sh::SETCOLS;
             const int pa[6] = {0, 0, 0, 1, 1, 2};
             const int pbx[6] = {0, 1, 2, 1, 2, 3};  // 3 = slice 3 times 2^-9
             const int pacc[6] = {0, 1, 2, 3, 4, 4};
@@ -887,13 +897,11 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
             for (int ks = 0; ks < 4; ++ks) {
 #pragma unroll
               for (int x = 0; x < 6; ++x) {
-                const uint32_t ao = base + (uint32_t)pa[x] * Sh::SLBYTES + 32u * ks;
-                const uint32_t bo = base + (uint32_t)pbx[x] * Sh::SLBYTES + 32u * ks;
-                const uint32_t dt = tbase + aset * Sh::SETCOLS + (uint32_t)(pacc[x] * NP);
+                const uint64_t ko = (uint64_t)(2 * ks);
+                const uint32_t dt = dt0 + (uint32_t)(pacc[x] * NP);
                 const bool acc0 = !(first && ks == 0 && x != 5);
-                mma_bf16(dt, desc_kmajor_sw128(ao), desc_kmajor_sw128(bo), idesc, acc0);
-                mma_bf16(dt, desc_kmajor_sw128(ao + (uint32_t)q.mp * 128u), desc_kmajor_sw128(bo + (uint32_t)q.mp * 128u),
-                         idesc, true);
+                mma_bf16(dt, d0[pa[x]] + ko, d0[pbx[x]] + ko, idesc, acc0);
+                mma_bf16(dt, d1[pa[x]] + ko, d1[pbx[x]] + ko, idesc, true);
               }
             }
             mma_commit(&empty[s]);

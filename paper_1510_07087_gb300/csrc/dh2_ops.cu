@@ -124,7 +124,13 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
           rm = fmaxf(rm, v);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-          if (lane == 0 && j0 + u < ms) cmx[j0 + u] = rs == 0 ? v : fmaxf(cmx[j0 + u], v);
+          // the first row slab stores the column maximum, later slabs merge
+          // into it without waiting for a read (non-negative floats order as
+          // their bit patterns)
+          if (lane == 0 && j0 + u < ms) {
+            if (rs == 0) cmx[j0 + u] = v;
+            else atomicMax(reinterpret_cast<int*>(cmx + j0 + u), __float_as_int(v));
+          }
         }
       }
       if (r < mt) rmx[r] = rm;
