@@ -1199,13 +1199,15 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     if (cs) cudaStreamDestroy(cs);
   } else {
     if (split_near) {
+      // the admissible blocks first (weights, row scales), then the copies on
+      // the side stream, beside the leaf work that follows on this stream
+      launch_norms_near<T>(d_na, d_norm_adm, (int)n_norm_adm, st);
+      counted(DH2_KC_NORMS, n_norm_adm > 0);
       cudaEventRecord(ev_fork, st);
       cudaStreamWaitEvent(sst, ev_fork, 0);
       launch_norms_near<T>(d_na, d_norm_near, (int)(n_norm - n_norm_adm), sst);
       counted(DH2_KC_NORMS, true);
       cudaEventRecord(ev_join, sst);
-      launch_norms_near<T>(d_na, d_norm_adm, (int)n_norm_adm, st);
-      counted(DH2_KC_NORMS, n_norm_adm > 0);
     } else {
       launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
       counted(DH2_KC_NORMS, n_norm > 0);
