@@ -890,19 +890,25 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
               d1[x] = desc_kmajor_sw128(base + (uint32_t)x * Sh::SLBYTES + (uint32_t)q.mp * 128u);
             }
             const uint32_t dt0 = tbase + aset * Sh::SETCOLS;
-            const int pa[6] = {0, 0, 0, 1, 1, 2};
-            const int pbx[6] = {0, 1, 2, 1, 2, 3};  // 3 = slice 3 times 2^-9
-            const int pacc[6] = {0, 1, 2, 3, 4, 4};
+            // products in an order where no two consecutive MMAs write the same
+            // accumulator: (1,1), (2,2), (1,2), (2,3), (1,3), (3,3)/512, first on
+            // rows 0 (X' columns) then on rows mp (Y' columns)
+            const int pa[6] = {0, 1, 0, 1, 0, 2};
+            const int pbx[6] = {0, 1, 1, 2, 2, 3};  // 3 = slice 3 times 2^-9
+            const int pacc[6] = {0, 3, 1, 4, 2, 4};
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t ko = (uint64_t)(2 * ks);
 #pragma unroll
               for (int x = 0; x < 6; ++x) {
-                const uint64_t ko = (uint64_t)(2 * ks);
-                const uint32_t dt = dt0 + (uint32_t)(pacc[x] * NP);
+                // the window's first MMA into an accumulator overwrites it ((3,3)
+                // follows (2,3) into the same one)
                 const bool acc0 = !(first && ks == 0 && x != 5);
-                mma_bf16(dt, d0[pa[x]] + ko, d0[pbx[x]] + ko, idesc, acc0);
-                mma_bf16(dt, d1[pa[x]] + ko, d1[pbx[x]] + ko, idesc, true);
+                mma_bf16(dt0 + (uint32_t)(pacc[x] * NP), d0[pa[x]] + ko, d0[pbx[x]] + ko, idesc, acc0);
               }
+#pragma unroll
+              for (int x = 0; x < 6; ++x)
+                mma_bf16(dt0 + (uint32_t)(pacc[x] * NP), d1[pa[x]] + ko, d1[pbx[x]] + ko, idesc, true);
             }
             mma_commit(&empty[s]);
             if (j0 + kGramChunk >= wend) mma_commit(&accfull[aset]);
