@@ -55,6 +55,9 @@ struct Tree::Dev {
   int32_t *bt, *bs, *badm, *bpair[2], *boff_row;
   int64_t *near_off, *Soff, *bmax_off;
   int32_t *adm_list, *inadm_list;
+  int64_t* norm_pieces;  // admissible blocks' norms pass: b << 32 | 32-row slab << 16 | column group
+  int64_t* norm_pbegin;  // per admissible block (adm_list order) its first piece; nadm + 1 entries
+  int64_t nnorm_pieces = 0;
   // matvec lists (row side; the column side's serve the adjoint product)
   int64_t *own_ptr, *par_ptr;
   int32_t *own_blk, *par_pair, *par_son;
@@ -341,6 +344,20 @@ dh2_status upload_tree(Tree& tr) {
   add64(std::move(noff), &D->near_off);
   add64(std::move(soffs), &D->Soff);
   add64(std::move(mxoff), &D->bmax_off);
+  {
+    std::vector<int64_t> pcs, pbeg;
+    for (int32_t b : adm) {
+      pbeg.push_back((int64_t)pcs.size());
+      const Block& B = tr.blocks[b];
+      const int64_t nsl = ((int64_t)tr.size[B.t] + 31) / 32, ngr = ((int64_t)tr.size[B.s] + kNormCols - 1) / kNormCols;
+      for (int64_t sl = 0; sl < nsl; ++sl)
+        for (int64_t g = 0; g < ngr; ++g) pcs.push_back((int64_t)(((uint64_t)b << 32) | ((uint64_t)sl << 16) | (uint64_t)g));
+    }
+    pbeg.push_back((int64_t)pcs.size());
+    D->nnorm_pieces = (int64_t)pcs.size();
+    add64(std::move(pcs), &D->norm_pieces);
+    add64(std::move(pbeg), &D->norm_pbegin);
+  }
   add32(std::move(adm), &D->adm_list);
   add32(std::move(inadm), &D->inadm_list);
   // matvec lists: own blocks and father pairs per pair, row side (the
@@ -748,6 +765,11 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   int64_t n_leaf = 0, n_norm = 0, n_norm_adm = 0;
   const uint32_t* d_norm_adm = nullptr;   // the admissible blocks' codes
   const uint32_t* d_norm_near = nullptr;  // the nearfield blocks' codes
+  const uint64_t* d_pieces = nullptr;     // the admissible blocks' norms pass in pieces
+  const int64_t* d_pbegin = nullptr;      // per admissible code its first piece
+  int64_t n_pieces = 0;
+  std::vector<uint64_t> pieces;
+  std::vector<int64_t> pbegin;
   // R tiles (code << 32 | first column) in the order of the codes
   const uint64_t* d_ltiles = nullptr;
   std::vector<const uint64_t*> d_nltiles(maxdepth + 1, nullptr);
@@ -790,6 +812,16 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       for (size_t b = 0; b < tr.blocks.size(); ++b)
         if (!tr.blocks[b].adm) norm_codes.push_back(((uint32_t)i << 26) | (uint32_t)b);
     }
+    for (int64_t q = 0; q < n_norm_adm; ++q) {
+      pbegin.push_back((int64_t)pieces.size());
+      const uint32_t code = norm_codes[q];
+      const Tree& tr = Ms[code >> 26]->tree->tr;
+      const Block& B = tr.blocks[code & ((1u << 26) - 1u)];
+      const uint64_t nsl = ((uint64_t)tr.size[B.t] + 31) / 32, ngr = ((uint64_t)tr.size[B.s] + kNormCols - 1) / kNormCols;
+      for (uint64_t sl = 0; sl < nsl; ++sl)
+        for (uint64_t g = 0; g < ngr; ++g) pieces.push_back(((uint64_t)code << 32) | (sl << 16) | g);
+    }
+    pbegin.push_back((int64_t)pieces.size());
     std::stable_sort(lc.begin(), lc.end(), [](const LC& a, const LC& b) {
       return a.cls != b.cls ? a.cls < b.cls : a.cost > b.cost;
     });
@@ -813,7 +845,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
     tile_cls_begin[kLeafClasses] = (int64_t)leaf_tiles.size();
     for (int l = 0; l <= maxdepth; ++l) tiles_of(nl_codes[l], nl_tiles[l]);
-    codes_bytes = align256(4 * leaf_codes.size()) + align256(4 * norm_codes.size()) + align256(8 * leaf_tiles.size());
+    codes_bytes = align256(4 * leaf_codes.size()) + align256(4 * norm_codes.size()) + align256(8 * leaf_tiles.size()) +
+                  align256(8 * pieces.size()) + align256(8 * pbegin.size());
     for (int l = 0; l <= maxdepth; ++l)
       codes_bytes += align256(4 * nl_codes[l].size()) + align256(8 * nl_tiles[l].size());
   }
@@ -879,14 +912,19 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   if (nprob == 1)
     for (int sd = 0; sd < 2; ++sd)
       if (cp.rank_override[sd]) ovr_bytes += align256(4 * (size_t)Ms[0]->tree->tr.dev->npairs[sd]);
+  // the norms pass's partial sums, one per piece
+  int64_t n_pieces_all = nprob > 1 ? (int64_t)pieces.size() : Ms[0]->tree->tr.dev->nnorm_pieces;
+  const size_t part_bytes = align256(8 * (size_t)std::max<int64_t>(n_pieces_all, 1));
   void* scratch = nullptr;
-  if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + gram_bytes + ovr_bytes + 256,
+  if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + gram_bytes + ovr_bytes +
+                                     part_bytes + 256,
                        st) != cudaSuccess) {
     cudaGetLastError();
     return DH2_ENOMEM;
   }
   char* const gram_base = (char*)scratch + args_bytes + codes_bytes + cls_bytes + host_bytes;
   char* const ovr_base = gram_base + gram_bytes;
+  double* const d_partial = (double*)(ovr_base + ovr_bytes);
   cudaError_t ce_ovr = cudaSuccess;
   if (ovr_bytes) {
     char* op = ovr_base;
@@ -974,6 +1012,15 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     };
     d_ltiles = up64(leaf_tiles);
     n_ltiles = (int64_t)leaf_tiles.size();
+    d_pieces = up64(pieces);
+    n_pieces = (int64_t)pieces.size();
+    {
+      int64_t* d = (int64_t*)sp;
+      if (!pbegin.empty() && ce == cudaSuccess)
+        ce = cudaMemcpyAsync(d, pbegin.data(), 8 * pbegin.size(), cudaMemcpyHostToDevice, st);
+      sp += align256(8 * pbegin.size());
+      d_pbegin = d;
+    }
     for (int l = 0; l <= maxdepth; ++l) {
       d_nltiles[l] = up64(nl_tiles[l]);
       n_nltiles[l] = (int64_t)nl_tiles[l].size();
@@ -991,6 +1038,9 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     n_norm_adm = D->nadm;
     d_norm_adm = (const uint32_t*)D->adm_list;  // block ids of problem 0: the codes themselves
     d_norm_near = (const uint32_t*)D->inadm_list;
+    d_pieces = (const uint64_t*)D->norm_pieces;
+    d_pbegin = D->norm_pbegin;
+    n_pieces = D->nnorm_pieces;
     for (int l = 0; l <= tr.depth; ++l) {
       d_nl[l] = D->codes + D->nl_code_begin[l];
       n_nl[l] = D->nl_code_count[l];
@@ -1198,16 +1248,31 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       if (e) cudaEventDestroy(e);
     if (cs) cudaStreamDestroy(cs);
   } else {
-    if (split_near) {
-      // the admissible blocks first (weights, row scales), then the copies on
-      // the side stream, beside the leaf work that follows on this stream
-      launch_norms_near<T>(d_na, d_norm_adm, (int)n_norm_adm, st);
+    if (!any_gen) {
+      // stored G: the admissible blocks in pieces of 32 rows by kNormCols
+      // columns (sums and maxima merged atomically into zeroed buffers, then
+      // the weights), then the nearfield copies -- on the side stream beside
+      // the leaf work in the mixed mode
+      for (int i = 0; i < nprob; ++i)
+        if (nas[i].bmax)
+          cudaMemsetAsync(nas[i].bmax, 0, sizeof(float) * (size_t)Ms[i]->tree->tr.dev->bmax_elems, st);
+      launch_norms_adm<T>(d_na, d_pieces, n_pieces, d_norm_adm, d_pbegin, n_norm_adm, d_partial, st);
+      counted(DH2_KC_NORMS, n_pieces > 0);
       counted(DH2_KC_NORMS, n_norm_adm > 0);
-      cudaEventRecord(ev_fork, st);
-      cudaStreamWaitEvent(sst, ev_fork, 0);
-      launch_norms_near<T>(d_na, d_norm_near, (int)(n_norm - n_norm_adm), sst);
-      counted(DH2_KC_NORMS, true);
-      cudaEventRecord(ev_join, sst);
+      const int64_t n_near = n_norm - n_norm_adm;
+      if (n_near > 0 && cp.nearfield == 0) {
+        cudaStream_t cst = st;
+        if (split_near) {
+          cudaEventRecord(ev_fork, st);
+          cudaStreamWaitEvent(sst, ev_fork, 0);
+          cst = sst;
+        }
+        launch_norms_near<T>(d_na, d_norm_near, (int)n_near, cst);
+        counted(DH2_KC_NORMS, true);
+        if (split_near) cudaEventRecord(ev_join, sst);
+      } else if (split_near) {
+        cudaEventRecord(ev_join, st);  // nothing on the side stream: the join is immediate
+      }
     } else {
       launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
       counted(DH2_KC_NORMS, n_norm > 0);

@@ -28,6 +28,7 @@ constexpr int kCodeProbShift = 26;
 constexpr uint32_t kCodePairMask = (1u << 25) - 1u;
 constexpr int kMaxBatch = 64;
 constexpr int kRTile = 32;  // columns per tile of the R = Q^* A kernel
+constexpr int kNormCols = 64;  // columns of a piece of the admissible blocks' norms pass (by 32 rows)
 
 // Device status bits (OR-ed by kernels into one word).
 constexpr uint32_t kStatusNoConv = 1u;

@@ -709,6 +709,79 @@ __global__ void sub_kernel(C2<double>* __restrict__ u, const C2<T>* __restrict__
     u[i] = C2<double>{u[i].re - (double)t[i].re, u[i].im - (double)t[i].im};
 }
 
+// Admissible blocks of a stored G in pieces of one 32-row slab by kNormCols
+// columns, one warp per piece (piece = code << 32 | slab << 16 | column
+// group), so that no block's size sets the kernel's tail: the piece's sum of
+// squares goes to partial[piece]; in the mixed modes its rows' and columns'
+// largest |re|, |im| are merged into the block's maxima (zeroed before) by
+// atomic maxima (non-negative floats order as their bit patterns).
+// norms_finish_kernel adds a block's pieces in their order (the result does
+// not depend on the order in which pieces run) and forms the weights.
+template <typename T>
+__global__ void __launch_bounds__(256) norms_adm_kernel(const NormsArgs<T>* __restrict__ args,
+                                                        const uint64_t* __restrict__ pieces, int64_t n,
+                                                        double* __restrict__ partial) {
+  const int64_t w = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const uint64_t pc = pieces[w];
+  const uint32_t code = (uint32_t)(pc >> 32);
+  const int slab = (int)((pc >> 16) & 0xFFFFu), grp = (int)(pc & 0xFFFFu);
+  const NormsArgs<T>& a = args[code >> 26];
+  const int b = (int)(code & ((1u << 26) - 1u));
+  const int t = a.bt[b], s = a.bs[b];
+  const int mt = a.csize[t], ms = a.csize[s];
+  const int64_t t0 = a.cstart[t], s0 = a.cstart[s];
+  const int r = slab * 32 + lane;
+  const int c0 = grp * kNormCols, c1 = min(ms, c0 + kNormCols);
+  float* rmx = a.bmax ? a.bmax + a.bmax_off[b] : nullptr;
+  float* cmx = rmx ? rmx + mt : nullptr;
+  T acc = T(0);
+  float rm = 0.f;
+  for (int j0 = c0; j0 < c1; j0 += 8) {
+    C2<T> g[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      g[u] = czero<T>();
+      if (r < mt && j0 + u < c1) {
+        const int64_t gi = (s0 + j0 + u) * a.ld + t0 + r;
+        if (DH2_IN(gi, c_lim.G, 24, b)) g[u] = a.G[gi];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      acc += g[u].re * g[u].re + g[u].im * g[u].im;
+      if (cmx) {
+        float v = fmaxf(fabsf((float)g[u].re), fabsf((float)g[u].im));
+        rm = fmaxf(rm, v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0 && j0 + u < c1) atomicMax(reinterpret_cast<int*>(cmx + j0 + u), __float_as_int(v));
+      }
+    }
+  }
+  if (rmx && r < mt) atomicMax(reinterpret_cast<int*>(rmx + r), __float_as_int(rm));
+  const double tot = warp_sum((double)acc);
+  if (lane == 0) partial[w] = tot;
+}
+
+// the admissible blocks' |G_b|_F^2 (their pieces pbegin[i] .. pbegin[i+1] - 1
+// added in order) and weights 1/omega_b
+template <typename T>
+__global__ void norms_finish_kernel(const NormsArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes,
+                                    const int64_t* __restrict__ pbegin, const double* __restrict__ partial,
+                                    int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t code = codes[i];
+  const NormsArgs<T>& a = args[code >> 26];
+  const int b = (int)(code & ((1u << 26) - 1u));
+  double tot = 0.0;
+  for (int64_t q = pbegin[i]; q < pbegin[i + 1]; ++q) tot += partial[q];
+  if (a.bnorm2 && DH2_IN(b, c_lim.nblocks, 25, b)) a.bnorm2[b] = tot;
+  a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[a.bt[b]]]) : 1.0;
+}
+
 // |v|^2 summed into *acc (zeroed by the caller)
 __global__ void norm2_kernel(const C2<double>* __restrict__ v, int64_t n, double* __restrict__ acc) {
   double s = 0.0;
@@ -835,6 +908,14 @@ template <typename T>
 void launch_to_type(const C2<double>* v, C2<T>* o, int64_t n, cudaStream_t st) {
   if (n > 0) to_type_kernel<T><<<(int)std::min<int64_t>((n + 255) / 256, 152 * 8), 256, 0, st>>>(v, o, n);
 }
+template <typename T>
+void launch_norms_adm(const NormsArgs<T>* args_dev, const uint64_t* pieces, int64_t npieces, const uint32_t* codes,
+                      const int64_t* pbegin, int64_t nblocks, double* partial, cudaStream_t st) {
+  if (npieces > 0) norms_adm_kernel<T><<<(int)((npieces + 7) / 8), 256, 0, st>>>(args_dev, pieces, npieces, partial);
+  if (nblocks > 0)
+    norms_finish_kernel<T><<<(int)((nblocks + 255) / 256), 256, 0, st>>>(args_dev, codes, pbegin, partial, nblocks);
+}
+
 void launch_norm2(const C2<double>* v, int64_t n, double* acc, cudaStream_t st) {
   if (n > 0) norm2_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 4), 256, 0, st>>>(v, n, acc);
 }
@@ -912,6 +993,8 @@ void launch_colw(const int32_t* gblk, const double* invw, T* colw, int64_t n, cu
                                       int64_t, cudaStream_t);                                              \
   template void launch_closed_form<T>(const ErrArgs<T>&, const double*, int, double*, cudaStream_t);            \
   template void launch_to_type<T>(const C2<double>*, C2<T>*, int64_t, cudaStream_t);                       \
+  template void launch_norms_adm<T>(const NormsArgs<T>*, const uint64_t*, int64_t, const uint32_t*, const int64_t*, \
+                                    int64_t, double*, cudaStream_t);                                           \
   template void launch_sub<T>(C2<double>*, const C2<T>*, int64_t, cudaStream_t);
 
 DH2_INST(float)

@@ -122,6 +122,14 @@ void launch_colw(const int32_t* gblk, const double* invw, T* colw, int64_t n, cu
 // codes: (problem << 26) | block for a batch, or NULL for blocks 0..n-1 of args_dev[0]
 template <typename T>
 void launch_norms_near(const NormsArgs<T>* args_dev, const uint32_t* codes, int n, cudaStream_t st);
+// admissible blocks of a stored G in pieces (code << 32 | 32-row slab << 16 |
+// kNormCols-column group; block i's pieces are pbegin[i] .. pbegin[i+1] - 1):
+// partial sums per piece (scratch `partial`, npieces doubles), in the mixed modes
+// the row/column maxima (zeroed before) merged atomically, then bnorm2 and the
+// weights of the nblocks codes
+template <typename T>
+void launch_norms_adm(const NormsArgs<T>* args_dev, const uint64_t* pieces, int64_t npieces, const uint32_t* codes,
+                      const int64_t* pbegin, int64_t nblocks, double* partial, cudaStream_t st);
 template <typename T> void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream_t st);
 template <typename T> void launch_project(const ProjArgs<T>& a, int nadm, cudaStream_t st);
 template <typename T>
