@@ -1267,7 +1267,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
           cudaStreamWaitEvent(sst, ev_fork, 0);
           cst = sst;
         }
-        launch_norms_near<T>(d_na, d_norm_near, (int)n_near, cst);
+        if (split_near) launch_near_copy<T>(d_na, d_norm_near, n_near, cst);  // beside the leaf work
+        else launch_norms_near<T>(d_na, d_norm_near, (int)n_near, cst);
         counted(DH2_KC_NORMS, true);
         if (split_near) cudaEventRecord(ev_join, sst);
       } else if (split_near) {
