@@ -1107,6 +1107,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // the end of the schedule
   cudaStream_t sst = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool copy_pending = false;  // the nearfield copies wait for the leaf factors' launch
   bool split_near = mixed && !any_gen && !hs && cp.nearfield == 0 && n_norm > n_norm_adm;
   if (split_near) {
     int lo = 0, hi = 0;
@@ -1161,23 +1162,29 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // modes the tensor-core Gram matrices and their pivoted Cholesky
   // events around the Gram and factor launches of each class (mixed modes,
   // device input): the leaf phase split into its two kernels
-  cudaEvent_t kev[3 * kLeafClasses] = {};
+  cudaEvent_t kev[4 * kLeafClasses] = {};
   bool kev_ok = false;
-  auto leaf_factor = [&](const uint32_t* codes, int n, int c, bool timed) {
+  // stage (mixed modes): 1 the Gram matrices, 2 their factors, 3 both
+  auto leaf_factor = [&](const uint32_t* codes, int n, int c, bool timed, int stage = 3) {
     if (n <= 0) return;
     const int P = even_up(std::max(2, cls_maxm[c]));
     if constexpr (sizeof(T) == 4) {
       if (mixed) {
-        if (timed) cudaEventRecord(kev[3 * c], st);
-        ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);  // row scales, then the Gram matrices
-        counted(DH2_KC_GRAM_SCALES, true);
-        counted(DH2_KC_LEAF_GRAM + c, true);
-        if (timed) cudaEventRecord(kev[3 * c + 1], st);
-        // pivoted Cholesky, then Jacobi, rank and Q
-        ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);
-        counted(DH2_KC_LEAF_FACTOR + c, true);
-        counted(DH2_KC_LEAF_JACOBI + c, true);
-        if (timed) cudaEventRecord(kev[3 * c + 2], st);
+        if (stage & 1) {
+          if (timed) cudaEventRecord(kev[4 * c], st);
+          ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);  // row scales, then the Gram matrices
+          counted(DH2_KC_GRAM_SCALES, true);
+          counted(DH2_KC_LEAF_GRAM + c, true);
+          if (timed) cudaEventRecord(kev[4 * c + 1], st);
+        }
+        if (stage & 2) {
+          // pivoted Cholesky, then Jacobi, rank and Q
+          if (timed) cudaEventRecord(kev[4 * c + 2], st);
+          ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);
+          counted(DH2_KC_LEAF_FACTOR + c, true);
+          counted(DH2_KC_LEAF_JACOBI + c, true);
+          if (timed) cudaEventRecord(kev[4 * c + 3], st);
+        }
         return;
       }
     }
@@ -1260,19 +1267,11 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       counted(DH2_KC_NORMS, n_pieces > 0);
       counted(DH2_KC_NORMS, n_norm_adm > 0);
       const int64_t n_near = n_norm - n_norm_adm;
-      if (n_near > 0 && cp.nearfield == 0) {
-        cudaStream_t cst = st;
-        if (split_near) {
-          cudaEventRecord(ev_fork, st);
-          cudaStreamWaitEvent(sst, ev_fork, 0);
-          cst = sst;
-        }
-        if (split_near) launch_near_copy<T>(d_na, d_norm_near, n_near, cst);  // beside the leaf work
-        else launch_norms_near<T>(d_na, d_norm_near, (int)n_near, cst);
+      if (split_near) {
+        copy_pending = true;  // launched beside the leaf factors
+      } else if (n_near > 0 && cp.nearfield == 0) {
+        launch_norms_near<T>(d_na, d_norm_near, (int)n_near, st);
         counted(DH2_KC_NORMS, true);
-        if (split_near) cudaEventRecord(ev_join, sst);
-      } else if (split_near) {
-        cudaEventRecord(ev_join, st);  // nothing on the side stream: the join is immediate
       }
     } else {
       launch_norms_near<T>(d_na, d_norm, (int)n_norm, st);
@@ -1288,13 +1287,27 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
 #endif
     if (mixed && !plan) {
       kev_ok = true;
-      for (int i = 0; i < 3 * kLeafClasses && kev_ok; ++i)
+      for (int i = 0; i < 4 * kLeafClasses && kev_ok; ++i)
         kev_ok = cudaEventCreate(&kev[i]) == cudaSuccess;
       if (!kev_ok) cudaGetLastError();  // no split timing; the compression itself goes on
     }
+    // mixed modes: every class's Gram matrices first, then the factors, with
+    // the nearfield copies forked beside the factors (not beside the Gram
+    // kernels, which they slow)
     for (int c = 0; c < kLeafClasses; ++c)
       leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c,
-                  kev_ok && cls_begin[c + 1] > cls_begin[c]);
+                  kev_ok && cls_begin[c + 1] > cls_begin[c], mixed ? 1 : 3);
+    if (copy_pending) {
+      cudaEventRecord(ev_fork, st);
+      cudaStreamWaitEvent(sst, ev_fork, 0);
+      launch_near_copy<T>(d_na, d_norm_near, n_norm - n_norm_adm, sst);
+      counted(DH2_KC_NORMS, true);
+      cudaEventRecord(ev_join, sst);
+    }
+    if (mixed)
+      for (int c = 0; c < kLeafClasses; ++c)
+        leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c,
+                    kev_ok && cls_begin[c + 1] > cls_begin[c], 2);
     rec(2);
     // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
     for (int c = 0; c < kLeafClasses; ++c) {
@@ -1460,8 +1473,8 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   float split[2] = {0, 0};
   for (int c = 0; c < kLeafClasses; ++c) {
     float a = 0, b = 0;
-    if (kev_ok && cls_begin[c + 1] > cls_begin[c] && cudaEventElapsedTime(&a, kev[3 * c], kev[3 * c + 1]) == cudaSuccess &&
-        cudaEventElapsedTime(&b, kev[3 * c + 1], kev[3 * c + 2]) == cudaSuccess) {
+    if (kev_ok && cls_begin[c + 1] > cls_begin[c] && cudaEventElapsedTime(&a, kev[4 * c], kev[4 * c + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, kev[4 * c + 2], kev[4 * c + 3]) == cudaSuccess) {
       split[0] += a;
       split[1] += b;
     }
