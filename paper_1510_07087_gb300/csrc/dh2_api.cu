@@ -1101,42 +1101,11 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     check_set_limits_ops(lim);
   }
 #endif
-  // mixed mode, dense input, nearfield copied: the copies depend on G alone and
-  // run on a low-priority side stream under the leaf work (the Gram kernels
-  // hold one CTA per SM and leave threads and registers free), joined before
-  // the end of the schedule
-  cudaStream_t sst = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  bool copy_pending = false;  // the nearfield copies wait for the leaf factors' launch
-  bool split_near = mixed && !any_gen && !hs && cp.nearfield == 0 && n_norm > n_norm_adm;
-  if (split_near) {
-    int lo = 0, hi = 0;
-    split_near = cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
-                 cudaStreamCreateWithPriority(&sst, cudaStreamNonBlocking, lo) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-                 cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) == cudaSuccess;
-    if (!split_near) {  // everything on the one stream
-      cudaGetLastError();
-      if (sst) cudaStreamDestroy(sst);
-      if (ev_fork) cudaEventDestroy(ev_fork);
-      if (ev_join) cudaEventDestroy(ev_join);
-      sst = nullptr;
-      ev_fork = ev_join = nullptr;
-    }
-  }
-  auto release_side = [&]() {
-    if (sst) cudaStreamDestroy(sst);
-    if (ev_fork) cudaEventDestroy(ev_fork);
-    if (ev_join) cudaEventDestroy(ev_join);
-    sst = nullptr;
-    ev_fork = ev_join = nullptr;
-  };
   if (plan) {
     // everything from here to the projection becomes the graph; each replay
     // starts by clearing the status words
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
-      release_side();
       cudaFreeAsync(scratch, st);
       return DH2_ECUDA;
     }
@@ -1164,27 +1133,22 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // device input): the leaf phase split into its two kernels
   cudaEvent_t kev[4 * kLeafClasses] = {};
   bool kev_ok = false;
-  // stage (mixed modes): 1 the Gram matrices, 2 their factors, 3 both
-  auto leaf_factor = [&](const uint32_t* codes, int n, int c, bool timed, int stage = 3) {
+  auto leaf_factor = [&](const uint32_t* codes, int n, int c, bool timed) {
     if (n <= 0) return;
     const int P = even_up(std::max(2, cls_maxm[c]));
     if constexpr (sizeof(T) == 4) {
       if (mixed) {
-        if (stage & 1) {
-          if (timed) cudaEventRecord(kev[4 * c], st);
-          ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);  // row scales, then the Gram matrices
-          counted(DH2_KC_GRAM_SCALES, true);
-          counted(DH2_KC_LEAF_GRAM + c, true);
-          if (timed) cudaEventRecord(kev[4 * c + 1], st);
-        }
-        if (stage & 2) {
-          // pivoted Cholesky, then Jacobi, rank and Q
-          if (timed) cudaEventRecord(kev[4 * c + 2], st);
-          ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);
-          counted(DH2_KC_LEAF_FACTOR + c, true);
-          counted(DH2_KC_LEAF_JACOBI + c, true);
-          if (timed) cudaEventRecord(kev[4 * c + 3], st);
-        }
+        if (timed) cudaEventRecord(kev[4 * c], st);
+        ok_launch &= launch_gram(d_ga, codes, n, cls_maxm[c], st);  // row scales, then the Gram matrices
+        counted(DH2_KC_GRAM_SCALES, true);
+        counted(DH2_KC_LEAF_GRAM + c, true);
+        if (timed) cudaEventRecord(kev[4 * c + 1], st);
+        // pivoted Cholesky, then Jacobi, rank and Q
+        if (timed) cudaEventRecord(kev[4 * c + 2], st);
+        ok_launch &= launch_pair_kernel_gram(reinterpret_cast<const PairArgs<float>*>(d_pa), codes, n, P, st);
+        counted(DH2_KC_LEAF_FACTOR + c, true);
+        counted(DH2_KC_LEAF_JACOBI + c, true);
+        if (timed) cudaEventRecord(kev[4 * c + 3], st);
         return;
       }
     }
@@ -1257,9 +1221,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   } else {
     if (!any_gen) {
       // stored G: the admissible blocks in pieces of 32 rows by kNormCols
-      // columns (sums and maxima merged atomically into zeroed buffers, then
-      // the weights), then the nearfield copies -- on the side stream beside
-      // the leaf work in the mixed mode
+      // columns (maxima merged atomically into zeroed buffers, sums per piece,
+      // then the weights), then the nearfield copies.  (The copies on a second
+      // stream beside the leaf work slowed the kernels beside them by more than
+      // their own time: measured, not kept.)
       for (int i = 0; i < nprob; ++i)
         if (nas[i].bmax)
           cudaMemsetAsync(nas[i].bmax, 0, sizeof(float) * (size_t)Ms[i]->tree->tr.dev->bmax_elems, st);
@@ -1267,9 +1232,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       counted(DH2_KC_NORMS, n_pieces > 0);
       counted(DH2_KC_NORMS, n_norm_adm > 0);
       const int64_t n_near = n_norm - n_norm_adm;
-      if (split_near) {
-        copy_pending = true;  // launched beside the leaf factors
-      } else if (n_near > 0 && cp.nearfield == 0) {
+      if (n_near > 0 && cp.nearfield == 0) {
         launch_norms_near<T>(d_na, d_norm_near, (int)n_near, st);
         counted(DH2_KC_NORMS, true);
       }
@@ -1291,23 +1254,9 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         kev_ok = cudaEventCreate(&kev[i]) == cudaSuccess;
       if (!kev_ok) cudaGetLastError();  // no split timing; the compression itself goes on
     }
-    // mixed modes: every class's Gram matrices first, then the factors, with
-    // the nearfield copies forked beside the factors (not beside the Gram
-    // kernels, which they slow)
     for (int c = 0; c < kLeafClasses; ++c)
       leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c,
-                  kev_ok && cls_begin[c + 1] > cls_begin[c], mixed ? 1 : 3);
-    if (copy_pending) {
-      cudaEventRecord(ev_fork, st);
-      cudaStreamWaitEvent(sst, ev_fork, 0);
-      launch_near_copy<T>(d_na, d_norm_near, n_norm - n_norm_adm, sst);
-      counted(DH2_KC_NORMS, true);
-      cudaEventRecord(ev_join, sst);
-    }
-    if (mixed)
-      for (int c = 0; c < kLeafClasses; ++c)
-        leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c,
-                    kev_ok && cls_begin[c + 1] > cls_begin[c], 2);
+                  kev_ok && cls_begin[c + 1] > cls_begin[c]);
     rec(2);
     // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
     for (int c = 0; c < kLeafClasses; ++c) {
@@ -1419,12 +1368,10 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     counted(DH2_KC_PROJECT, D->nadm > 0);
     DH2_PHASE_SYNC("project");
   }
-  if (split_near) cudaStreamWaitEvent(st, ev_join, 0);  // the nearfield copies are part of the result
   rec(6);
   if (plan) {
     cudaGraph_t g = nullptr;
     const cudaError_t e0 = cudaStreamEndCapture(st, &g);
-    release_side();
     cudaError_t e1 = e0;
     if (e0 == cudaSuccess) e1 = cudaGraphInstantiate(&plan->exec, g, 0);
     if (e0 != cudaSuccess || e1 != cudaSuccess) {
@@ -1459,7 +1406,6 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
     }
     return DH2_OK;
   }
-  release_side();  // the work already enqueued on the side stream still runs
   cudaFreeAsync(scratch, st);
   std::vector<uint32_t> status(nprob, 0);
   cudaError_t e1 = cudaSuccess;

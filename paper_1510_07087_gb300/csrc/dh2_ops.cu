@@ -782,45 +782,6 @@ __global__ void norms_finish_kernel(const NormsArgs<T>* __restrict__ args, const
   a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[a.bt[b]]]) : 1.0;
 }
 
-// Nearfield copies of a stored G, persistent and small: one CTA of 4 warps per
-// SM, warps striding over the inadmissible blocks, 16 entries per lane in
-// flight, so that it runs beside the leaf work (a Gram CTA still fits on
-// every SM) instead of filling the GPU with one warp per block.
-template <typename T>
-__global__ void __launch_bounds__(128) near_copy_kernel(const NormsArgs<T>* __restrict__ args,
-                                                        const uint32_t* __restrict__ codes, int64_t n) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-  for (int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < n; w += nw) {
-    const uint32_t code = codes[w];
-    const NormsArgs<T>& a = args[code >> 26];
-    const int b = (int)(code & ((1u << 26) - 1u));
-    const int t = a.bt[b], s = a.bs[b];
-    const int mt = a.csize[t], ms = a.csize[s];
-    const int64_t t0 = a.cstart[t], s0 = a.cstart[s];
-    const int total = mt * ms;
-    C2<T>* out = a.near + a.near_off[b];
-    for (int e0 = 0; e0 < total; e0 += 32 * 16) {
-      C2<T> g[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = e0 + lane + 32 * u;
-        g[u] = czero<T>();
-        if (e < total) {
-          const int r = e % mt, j = e / mt;
-          const int64_t gi = (s0 + j) * a.ld + t0 + r;
-          if (DH2_IN(gi, c_lim.G, 26, b)) g[u] = a.G[gi];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int e = e0 + lane + 32 * u;
-        if (e < total && DH2_IN(a.near_off[b] + e, c_lim.near, 27, b)) out[e] = g[u];
-      }
-    }
-  }
-}
-
 // |v|^2 summed into *acc (zeroed by the caller)
 __global__ void norm2_kernel(const C2<double>* __restrict__ v, int64_t n, double* __restrict__ acc) {
   double s = 0.0;
@@ -955,14 +916,6 @@ void launch_norms_adm(const NormsArgs<T>* args_dev, const uint64_t* pieces, int6
     norms_finish_kernel<T><<<(int)((nblocks + 255) / 256), 256, 0, st>>>(args_dev, codes, pbegin, partial, nblocks);
 }
 
-template <typename T>
-void launch_near_copy(const NormsArgs<T>* args_dev, const uint32_t* codes, int64_t n, cudaStream_t st) {
-  int dev = 0, nsm = 152;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    cudaGetLastError();
-  if (n > 0) near_copy_kernel<T><<<(int)std::min<int64_t>(nsm, (n + 3) / 4), 128, 0, st>>>(args_dev, codes, n);
-}
-
 void launch_norm2(const C2<double>* v, int64_t n, double* acc, cudaStream_t st) {
   if (n > 0) norm2_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 4), 256, 0, st>>>(v, n, acc);
 }
@@ -1042,7 +995,6 @@ void launch_colw(const int32_t* gblk, const double* invw, T* colw, int64_t n, cu
   template void launch_to_type<T>(const C2<double>*, C2<T>*, int64_t, cudaStream_t);                       \
   template void launch_norms_adm<T>(const NormsArgs<T>*, const uint64_t*, int64_t, const uint32_t*, const int64_t*, \
                                     int64_t, double*, cudaStream_t);                                           \
-  template void launch_near_copy<T>(const NormsArgs<T>*, const uint32_t*, int64_t, cudaStream_t);      \
   template void launch_sub<T>(C2<double>*, const C2<T>*, int64_t, cudaStream_t);
 
 DH2_INST(float)

@@ -130,9 +130,6 @@ void launch_norms_near(const NormsArgs<T>* args_dev, const uint32_t* codes, int 
 template <typename T>
 void launch_norms_adm(const NormsArgs<T>* args_dev, const uint64_t* pieces, int64_t npieces, const uint32_t* codes,
                       const int64_t* pbegin, int64_t nblocks, double* partial, cudaStream_t st);
-// nearfield copies of the listed (inadmissible) blocks of a stored G: one small CTA per SM
-template <typename T>
-void launch_near_copy(const NormsArgs<T>* args_dev, const uint32_t* codes, int64_t n, cudaStream_t st);
 template <typename T> void launch_expand(const SideView<T>& S, const int32_t* pairs, int n, cudaStream_t st);
 template <typename T> void launch_project(const ProjArgs<T>& a, int nadm, cudaStream_t st);
 template <typename T>
