@@ -44,7 +44,7 @@ struct Tree::Dev {
   int32_t *cluster[2], *leaf[2], *start[2], *m[2], *ncols[2], *son[2], *sonoff[2], *level[2], *kcap[2],
       *rowcap[2];
   int64_t *cmoff[2], *Roff[2], *Qoff[2], *Xoff[2], *hoff[2];
-  int64_t *gram_off[2], *gram_voff[2];  // mixed modes: leaf Gram matrix offsets, window sums (-1: none)
+  int64_t* gram_off[2];  // mixed modes: leaf Gram matrix offsets
   int32_t *gcol[2], *gblk[2];
   int64_t* seg_dst[2];  // column-map segments (expanded into gcol/gblk on upload)
   int64_t* seg_begin[2];  // per pair: first segment
@@ -70,7 +70,7 @@ struct Tree::Dev {
   // host-side sizes
   int64_t npairs[2] = {0, 0}, nleaf[2] = {0, 0};
   int64_t R_elems[2] = {0, 0}, Q_elems[2] = {0, 0}, X_elems[2] = {0, 0}, h_elems[2] = {0, 0};
-  int64_t gram_elems = 0, gram_velems = 0;  // both sides together
+  int64_t gram_elems = 0;  // both sides together
   int64_t S_elems = 0, near_elems = 0, bmax_elems = 0;
   int64_t nadm = 0, ninadm = 0;
   int64_t nleaf_codes = 0;
@@ -210,7 +210,7 @@ dh2_status upload_tree(Tree& tr) {
     D->npairs[sd] = np;
     std::vector<int32_t> cl(np), lf(np), st(np), mm(np), nco(np), son(2 * np, -1), soff(2 * np, 0), lv(np),
         kc(np), rc(np), io(np);
-    std::vector<int64_t> cmo(np), ro(np), qo(np), xo(np, 0), ho(np), go(np, 0), gvo(np, -1);
+    std::vector<int64_t> cmo(np), ro(np), qo(np), xo(np, 0), ho(np), go(np, 0);
     int64_t R_e = 0, Q_e = 0, X_e = 0, h_e = 0;
     for (int64_t p = 0; p < np; ++p) {  // sons before fathers (level descending)
       const Pair& P = S.pairs[p];
@@ -225,13 +225,9 @@ dh2_status upload_tree(Tree& tr) {
       if (P.leaf) {
         rc[p] = tr.size[P.cluster];
         kc[p] = (int32_t)std::min<int64_t>(rc[p], P.ncols);
-        const int64_t mpd = (rc[p] + 7) & ~7;  // Gram matrix: mp x mp, window sums 2 mp x mp
+        const int64_t mpd = (rc[p] + 7) & ~7;  // Gram matrix: mp x mp
         go[p] = D->gram_elems;
         D->gram_elems += mpd * mpd;
-        if (P.ncols > kGramWindow) {
-          gvo[p] = D->gram_velems;
-          D->gram_velems += 2 * mpd * mpd;  // 2 mp lanes x mp columns, column-major
-        }
       } else {
         for (int j = 0; j < 2; ++j) {
           son[2 * p + j] = (int32_t)P.son_pair[j];
@@ -294,7 +290,6 @@ dh2_status upload_tree(Tree& tr) {
     add64(std::move(xo), &D->Xoff[sd]);
     add64(std::move(ho), &D->hoff[sd]);
     add64(std::move(go), &D->gram_off[sd]);
-    add64(std::move(gvo), &D->gram_voff[sd]);
     // column maps: allocated here, expanded from the segments after the upload
     bufs.push_back({nullptr, 4 * (size_t)S.nleafcols, (void**)&D->gcol[sd]});
     bufs.push_back({nullptr, 4 * (size_t)S.nleafcols, (void**)&D->gblk[sd]});
@@ -891,7 +886,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // mixed modes: the leaf Gram matrices (double-float, mp x mp per leaf pair)
   // and the window sums of the pairs with more than one window, per problem
   const bool mixed = mode_mixed(cp.mode);
-  std::vector<size_t> gram_h_off(nprob, 0), gram_l_off(nprob, 0), gram_v_off(nprob, 0), gram_m_off(nprob, 0);
+  std::vector<size_t> gram_h_off(nprob, 0), gram_l_off(nprob, 0), gram_m_off(nprob, 0);
   size_t gram_bytes = 0;
   if (mixed) {
     gram_bytes = align256(sizeof(GramArgs) * nprob);
@@ -901,8 +896,6 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       if (!Ms[i]->gram) gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);  // else kept by the matrix
       gram_l_off[i] = gram_bytes;  // Cholesky factors: over H, or beside the kept Gram matrices
       if (Ms[i]->gram) gram_bytes += align256(sizeof(float4) * (size_t)D->gram_elems);
-      gram_v_off[i] = gram_bytes;
-      gram_bytes += align256(sizeof(long long) * (size_t)D->gram_velems);
       gram_m_off[i] = gram_bytes;
       gram_bytes += align256(sizeof(float) * (size_t)D->bmax_elems);
     }
@@ -956,7 +949,6 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         g.gcol[sd] = D->gcol[sd];
         g.colw[sd] = (const float*)M->colw[sd];
         g.hoff[sd] = D->gram_off[sd];
-        g.voff[sd] = D->gram_voff[sd];
         g.seg_begin[sd] = D->seg_begin[sd];
         g.seg_blk[sd] = D->seg_blk[sd];
       }
@@ -971,7 +963,6 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       g.G = (const C2<float>*)M->G;
       g.ld = M->ld;
       g.H = Hbuf;
-      g.V = (long long*)(gram_base + gram_v_off[i]);
       g.status = M->status;
       g.spin_limit = (uint32_t)std::min<int64_t>(std::max<int64_t>(cp.spin_limit, 0), (int64_t)UINT32_MAX);
     }

@@ -124,7 +124,8 @@ struct GramShape {
   static constexpr uint32_t BBYTES = BROWS * 128u;
   static constexpr int NACC = 5;
   static constexpr uint32_t TCOLS = NACC * NP <= 256 ? 256u : 512u;
-  static constexpr uint32_t SMEM = 1024 + 3 * SLBYTES + BBYTES;
+  static constexpr uint32_t VSBYTES = 2 * MPMAX * (MPMAX + 1) * 8;  // the pair's window sums, 2 mp rows of mp + 1
+  static constexpr uint32_t SMEM = 1024 + 3 * SLBYTES + BBYTES + VSBYTES;
 };
 
 constexpr int kBadRow = 0x7fffffff;  // row-scale marker of a non-finite entry
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sl0 = smem;
   unsigned char* bsl = smem + 3 * Sh::SLBYTES;  // slice 3 times 2^-9, rows [X; Y] (B operand of (3,3))
-  long long* Vs = reinterpret_cast<long long*>(smem);  // after the last MMA: V, 2 mp x mp, row stride mp + 1
+  long long* Vs = reinterpret_cast<long long*>(smem + 3 * Sh::SLBYTES + Sh::BBYTES);  // V, 2 mp x mp, row stride mp + 1
   __shared__ int cgcT[kTableCols];  // column table of the pair: G index of each column
   __shared__ float cwtT[kTableCols]; // and its weight 1/omega_b
   __shared__ float rsc[64];
@@ -254,9 +255,7 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
     const int mp = (m + 7) & ~7;
     float4* Hout = a.H + a.hoff[side][pid];
     st_ptr = a.status;
-    const int64_t voff = a.voff[side][pid];
-    long long* Vg = voff >= 0 ? a.V + voff : nullptr;
-    if (m > NP || (N > kGramWindow && !Vg)) {  // not for this launch: reported, nothing written
+    if (m > NP) {  // not for this launch: reported, nothing written
       if (tid == 0) atomicOr(a.status, kStatusTooLarge);
       continue;
     }
@@ -493,10 +492,9 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
         timed_out = true;
         break;
       }
-      // window done: V = P11 2^31 + P12 2^24 + P13 2^16 + P22 2^15 + low 2^8 per lane (row of [Re; Im]);
-      // every P is an integer below 2^24 held exactly in FP32.  Partial sums of
-      // long rows go to global memory column by column (lanes contiguous).
-      const bool last = wend >= N;
+      // window done: V += P11 2^31 + P12 2^24 + P13 2^16 + P22 2^15 + low 2^8 per lane (row of [Re; Im]);
+      // every P is an integer below 2^24 held exactly in FP32.  The sums of
+      // the pair's windows stay in shared memory (each entry owned by one thread).
 #if GP_ON
       GP_T(ga);
 #endif
@@ -521,12 +519,8 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
                           (long long)__float2int_rn(p12[i]) * (1LL << 24) +
                           (long long)__float2int_rn(p13[i]) * (1LL << 16) +
                           (long long)__float2int_rn(p22[i]) * (1LL << 15) + (long long)__float2int_rn(plo[i] * 256.f);
-            if (Vg) {
-              const int64_t gi = (int64_t)j * (2 * mp) + L;
-              if (w0 > 0) x += Vg[gi];
-              if (!last) Vg[gi] = x;
-            }
-            if (last) Vs[(int64_t)L * (mp + 1) + j] = x;  // padded rows: no shared-memory bank conflicts
+            long long* vp = Vs + (int64_t)L * (mp + 1) + j;  // padded rows: no shared-memory bank conflicts
+            *vp = w0 > 0 ? *vp + x : x;
           }
         }
       }
@@ -550,7 +544,7 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
       const float2 hr = ll_to_df(re, ex), hi = ll_to_df(im, ex);
       Hout[i + (int64_t)j * mp] = make_float4(hr.x, hr.y, hi.x, hi.y);
     }
-    __syncthreads();  // Vs (over the slice buffers) read before the next pair's slices
+    __syncthreads();  // Vs read before the next pair's first window
 #if GP_ON
     gp[9] += clock64() - ga;
 #endif
@@ -569,7 +563,7 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
 }
 
 // ---------------------------------------------------------------- pipelined form (leaves of <= 48 rows)
-// One CTA per SM, 13 warps in three roles that walk the same schedule (the
+// One CTA per SM, 17 warps in three roles that walk the same schedule (the
 // launch list's pairs, their windows of kGramWindow columns, their chunks of
 // kGramChunk columns), so that no work description passes between them:
 //   warps 0-11  producers: load a chunk of A, slice it into one of two
@@ -579,13 +573,14 @@ __global__ void __launch_bounds__(kGramThreads, GramShape<NP>::TCOLS == 512 ? 1 
 //               alternating), then commits to empty[s] (the stage may be
 //               refilled) and, after a window's last chunk, to accfull[a];
 //   warps 13-16 epilogue: reads a finished window's accumulators (warp w the
-//               TMEM lanes 32 (w % 4) ..), adds it to the pair's window sums,
-//               arrives on accempty[a], and after a pair's last window forms
-//               H = V + V^* in double-float.
+//               TMEM lanes 32 (w % 4) ..), adds it to the pair's window sums
+//               in shared memory, arrives on accempty[a], and after a pair's
+//               last window forms H = V + V^* in double-float.
 // Chunks c + 1 and c + 2 are being loaded while chunk c is sliced, slicing
 // runs while the tensor cores work on the chunk before, and a pair's window
-// sums and H while the next pair's chunks are sliced and multiplied.  Every wait is bounded: a wait that runs out sets the CTA's
-// abort flag and every role leaves its schedule at its next wait.
+// sums and H while the next pair's chunks are sliced and multiplied.  Every
+// wait is bounded: a wait that runs out sets the CTA's abort flag and every
+// role leaves its schedule at its next wait.
 constexpr int kPipeProd = 384;                // producer threads (warps 0-11): one item each, m <= 48
 constexpr int kPipeMmaWarp = 12;
 constexpr int kPipeEpi0 = 13;                 // first epilogue warp
@@ -597,7 +592,7 @@ struct PipeShape {
   static constexpr uint32_t SLBYTES = (NP + 128) * 128u;  // one slice: rows [X; Y; -X], MMA reads [0,128), [mp, mp+128)
   static constexpr uint32_t BBYTES = (2 * NP + 16) * 128u;  // slice 3 times 2^-9, rows [X; Y]
   static constexpr uint32_t STAGE = 3 * SLBYTES + BBYTES;
-  static constexpr uint32_t VSBYTES = 2 * NP * (NP + 1) * 8;  // last window's sums, 2 mp rows of mp + 1
+  static constexpr uint32_t VSBYTES = 2 * NP * (NP + 1) * 8;  // the pair's window sums, 2 mp rows of mp + 1
   static constexpr uint32_t SMEM = 1024 + 2 * STAGE + VSBYTES;
   static constexpr uint32_t SETCOLS = 5 * NP;  // accumulators of one set
   static_assert(STAGE % 1024 == 0 && 2 * SETCOLS <= 512, "stages on 1 KiB, two sets in 512 columns");
@@ -616,8 +611,7 @@ __device__ __forceinline__ PipePair pipe_pair(const GramArgs& a, uint32_t code, 
   q.N = a.ncols[q.side][q.pid];
   q.r0 = a.start[q.side][q.pid];
   q.mp = (q.m + 7) & ~7;
-  const bool fits = q.m <= np && (q.N <= kGramWindow || a.voff[q.side][q.pid] >= 0);
-  q.run = fits && q.m > 0 && q.N > 0;
+  q.run = q.m <= np && q.m > 0 && q.N > 0;
   return q;
 }
 
@@ -945,19 +939,16 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
       float4* Hout = a.H + a.hoff[q.side][q.pid];
       const int m = q.m, mp = q.mp;
       if (!q.run) {
-        if (m > NP || (q.N > kGramWindow && a.voff[q.side][q.pid] < 0)) {
+        if (m > NP) {
           if (et == 0) atomicOr(a.status, kStatusTooLarge);
         } else {
           for (int i = et; i < mp * mp; i += 128) Hout[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         continue;
       }
-      const int64_t voff = a.voff[q.side][q.pid];
-      long long* Vg = voff >= 0 ? a.V + voff : nullptr;
       if (et < m) erexp[et] = __float_as_int(Hout[et].x);
       named_bar_sync(kBarEpi, 128);
       for (int w0 = 0; w0 < q.N && ok; w0 += kGramWindow, ++wc) {
-        const bool last = w0 + kGramWindow >= q.N;
         const uint32_t aset = wc & 1u;
 #if GP_ON
         long long t0 = clock64();
@@ -988,12 +979,8 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
                             (long long)__float2int_rn(p12[i]) * (1LL << 24) +
                             (long long)__float2int_rn(p13[i]) * (1LL << 16) +
                             (long long)__float2int_rn(p22[i]) * (1LL << 15) + (long long)__float2int_rn(plo[i] * 256.f);
-              if (Vg) {
-                const int64_t gi = (int64_t)j * (2 * mp) + L;
-                if (w0 > 0) x += Vg[gi];
-                if (!last) Vg[gi] = x;
-              }
-              if (last) Vs[(int64_t)L * (mp + 1) + j] = x;
+              long long* vp = Vs + (int64_t)L * (mp + 1) + j;  // the pair's sums, owned by this thread
+              *vp = w0 > 0 ? *vp + x : x;
             }
           }
         }
@@ -1007,7 +994,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
 #if GP_ON
       long long t2 = clock64();
 #endif
-      named_bar_sync(kBarEpi, 128);  // the last window's sums are in Vs
+      named_bar_sync(kBarEpi, 128);  // the pair's sums are in Vs
       bool bad = false;
       for (int i = 0; i < m; ++i) bad = bad || erexp[i] == kBadRow;
       if (bad) {  // non-finite entries: reported, H of this pair left as zero
@@ -1024,7 +1011,7 @@ __global__ void __launch_bounds__(kPipeThreads, 1)
           Hout[i + (int64_t)j * mp] = make_float4(hr.x, hr.y, hi.x, hi.y);
         }
       }
-      named_bar_sync(kBarEpi, 128);  // Vs and erexp read before the next pair's last window
+      named_bar_sync(kBarEpi, 128);  // Vs and erexp read before the next pair's first window
 #if GP_ON
       eh += clock64() - t2;
 #endif

@@ -135,7 +135,6 @@ struct GramArgs {
   const int32_t* gcol[2];    // leaf column map: index of G's other dimension
   const float* colw[2];      // leaf column map: weight 1/omega of the column's block
   const int64_t* hoff[2];    // per pair: first entry of its Gram in H (mp x mp, mp = m rounded up to 8)
-  const int64_t* voff[2];    // per pair: first entry of its window sums in V, -1 if one window suffices
   const int64_t* seg_begin[2];  // per pair: its blocks of F_tc as a range of column-map segments
   const int32_t* seg_blk[2];    // per segment: block id
   const int32_t* bt;         // per block: row cluster
@@ -148,7 +147,6 @@ struct GramArgs {
   const C2<float>* G;
   int64_t ld;
   float4* H;                 // Gram matrices: (re hi, re lo, im hi, im lo) double-float, column-major, ld mp
-  long long* V;              // window sums of pairs with more than one window
   uint32_t* status;
   uint32_t spin_limit;       // polls of a wait for a tensor-core batch (0: default)
 };

@@ -87,7 +87,7 @@ def test_batched_rejects_mixed_dtypes():
 
 def test_batched_mixed_equals_single():
     """The mixed mode's batch (row scales, tensor-core Gram matrices, factor launches over all
-    problems; the nearfield copies on the side stream) equals each problem's own compression."""
+    problems) equals each problem's own compression."""
     D = _dev()
     trees, Gs, Gh = _setup(D, torch.complex64)
     mode = D.MODE_MIXED_BF16X3
