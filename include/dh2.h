@@ -67,9 +67,10 @@ typedef enum { DH2_C64 = 0, DH2_C128 = 1 } dh2_dtype;
  *        rank-revealing step is a pivoted Cholesky of it in double-float
  *        arithmetic, followed by the same FP32 Jacobi, FP64 tail sums, R, level
  *        steps and projection as FP32.  Leaves of at most 64 rows, dense G
- *        only (not the matrix-free entry points).  Meant for eps down to
- *        about 1e-5: at eps = 1e-6 the three slices no longer resolve the
- *        tail sums (use FP32 there). */
+ *        only (not the matrix-free entry points).  For eps >= 1e-5: below
+ *        that the squared singular values are no longer resolved to the tail
+ *        sums' precision, and the call (unless keep_gram is set) runs the
+ *        FP32 mode's leaf step instead; its result is then the FP32 mode's. */
 typedef enum { DH2_MODE_FP64 = 0, DH2_MODE_FP32 = 1, DH2_MODE_MIXED_BF16X3 = 2 } dh2_mode;
 
 /* Tree parameters (Section 3; Section 7 for the paper's values).
@@ -267,6 +268,55 @@ dh2_status dh2_plan_run(dh2_plan* P, const void* const* G, void* stream);
 dh2_status dh2_plan_wait(dh2_plan* P, void* stream);
 dh2_status dh2_plan_matrix(const dh2_plan* P, int32_t i, dh2_matrix** M);
 void dh2_plan_free(dh2_plan* P);
+
+/* ---------------------------------------------------------------- autotuning
+ * Launch choices of the compression that change its time, not its steps
+ * (Section 6's procedure is the same under every choice).  One table per
+ * process, read by each later compression when it prepares its launches (a
+ * plan keeps the choices it was captured with).
+ *  jacobi_tpp[c]   : most threads per column pair of a Jacobi round, factor
+ *                    class c (rows <= 32, <= 40, <= 48, <= 64, more): 4, 8,
+ *                    16 or 32 (default 32).  Changes the summation order of
+ *                    the rotation sums, so results move by rounding only.
+ *  jacobi_narrow[c]: mixed mode, leaf classes 0..3: threads per CTA of the
+ *                    Jacobi launch, 0 = 4 x rows, 1 = about 2 x rows
+ *                    (default), 2 = about 1 x rows (a multiple of 32), at the
+ *                    same threads per SM.  Changes the rounding as above.
+ *  rq_ctas_per_sm  : resident CTAs per SM of the persistent leaf R kernel,
+ *                    1..4 within its occupancy limit, 0 = that limit
+ *                    (default).  Changes no result.
+ * dh2_tuning_set returns DH2_EINVAL (table unchanged) for a value outside
+ * these sets. */
+typedef struct {
+  int32_t jacobi_tpp[5];
+  int32_t jacobi_narrow[4];
+  int32_t rq_ctas_per_sm;
+  int32_t reserved[2];
+} dh2_tuning;
+dh2_status dh2_tuning_get(dh2_tuning* out);
+dh2_status dh2_tuning_set(const dh2_tuning* tuning);
+/* One timed candidate of dh2_autotune: knob 0 = rq_ctas_per_sm, 1 =
+ * jacobi_narrow[cls], 2 = jacobi_tpp[cls]; ms = median device time of the
+ * phase the knob acts on (leaf R, or leaf factors) over the repetitions. */
+typedef struct {
+  int32_t knob;
+  int32_t cls;
+  int32_t value;
+  float ms;
+} dh2_tune_record;
+/* Autotune the table on one problem: compresses (tree, G) with `params`
+ * under each candidate of each knob in turn (coordinate descent: the R grid,
+ * then per factor class the narrow Jacobi launch and the Jacobi width; a
+ * class with no pairs in the problem is skipped), `reps` calls per candidate
+ * (1..15), keeps the fastest value of each knob, installs the result and
+ * returns it in `out`.  records: NULL, or room for `cap` records, of which
+ * *nrec are written (every candidate timed, in order; NULL nrec allowed when
+ * records is NULL).  The matrices it makes are freed before it returns.
+ * Errors: those of dh2_compress (the table is then left as it was), EINVAL
+ * for reps outside 1..15. */
+dh2_status dh2_autotune(const dh2_tree* tree, const void* G, dh2_dtype dtype, int64_t ld,
+                        const dh2_compress_params* params, void* stream, int32_t reps, dh2_tuning* out,
+                        dh2_tune_record* records, int32_t cap, int32_t* nrec);
 
 void dh2_matrix_free(dh2_matrix* M);
 

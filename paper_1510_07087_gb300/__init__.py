@@ -8,5 +8,6 @@ from ._binding import (  # noqa: F401
     KC_CLASSIFY, KC_COLW, KC_COUNT, KC_EXPAND, KC_GRAM_SCALES, KC_LEAF_JACOBI, KC_LEAF_FACTOR, KC_LEAF_GRAM, KC_LEAF_R, KC_LEVEL_FACTOR, KC_LEVEL_R, KC_NORMS,
     KC_PROJECT,
     DH2Error, Plan, ERR_FRO_BLOCKWISE, ERR_FRO_CLOSED, ERR_SPECTRAL, Matrix, Tree,
+    autotune, set_tuning, tuning,
     dh2_compress, dh2_compress_batched, dh2_compress_host, dh2_compress_kernel, dh2_compress_kernel_dlp, dh2_debug_fail_alloc, dh2_error, dh2_matvec_adjoint, dh2_matvec, dh2_matvec_noalloc, dh2_tree_build, dh2_version, exported_symbols,
 )

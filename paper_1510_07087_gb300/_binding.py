@@ -76,6 +76,23 @@ class TreeStats(ctypes.Structure):
                 ("max_leaf", c_int32), ("ndirs_max", c_int32)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("jacobi_tpp", c_int32 * 5), ("jacobi_narrow", c_int32 * 4), ("rq_ctas_per_sm", c_int32),
+                ("reserved", c_int32 * 2)]
+
+
+class TuneRecord(ctypes.Structure):
+    _fields_ = [("knob", c_int32), ("cls", c_int32), ("value", c_int32), ("ms", ctypes.c_float)]
+
+
+TUNE_KNOBS = ("rq_ctas_per_sm", "jacobi_narrow", "jacobi_tpp")
+
+
+def _tuning_dict(t: Tuning) -> dict:
+    return {"jacobi_tpp": list(t.jacobi_tpp), "jacobi_narrow": list(t.jacobi_narrow),
+            "rq_ctas_per_sm": int(t.rq_ctas_per_sm)}
+
+
 class DH2Error(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -114,6 +131,10 @@ SIGNATURES = [
     ("dh2_plan_wait", c_int32, [c_void_p, c_void_p]),
     ("dh2_plan_matrix", c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
     ("dh2_plan_free", None, [c_void_p]),
+    ("dh2_tuning_get", c_int32, [POINTER(Tuning)]),
+    ("dh2_tuning_set", c_int32, [POINTER(Tuning)]),
+    ("dh2_autotune", c_int32, [c_void_p, c_void_p, c_int32, c_int64, POINTER(CompressParams), c_void_p, c_int32,
+                               POINTER(Tuning), c_void_p, c_int32, POINTER(c_int32)]),
     ("dh2_matvec", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_matvec_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     ("dh2_matvec_adjoint", c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
@@ -388,6 +409,44 @@ def dh2_compress(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_
     _check(_lib().dh2_compress(tree.handle, c_void_p(G.data_ptr()), dt, ld, byref(p),
                                c_void_p(_stream_handle(stream)), byref(h)), "dh2_compress")
     return Matrix(h.value, tree, mode, G)
+
+
+def tuning() -> dict:
+    """The process's tuning table (dh2_tuning_get)."""
+    t = Tuning()
+    _check(_lib().dh2_tuning_get(byref(t)), "dh2_tuning_get")
+    return _tuning_dict(t)
+
+
+def set_tuning(d: dict) -> None:
+    """Install a tuning table (dh2_tuning_set); keys as returned by tuning()."""
+    t = Tuning()
+    for c, v in enumerate(d["jacobi_tpp"]):
+        t.jacobi_tpp[c] = int(v)
+    for c, v in enumerate(d["jacobi_narrow"]):
+        t.jacobi_narrow[c] = int(v)
+    t.rq_ctas_per_sm = int(d["rq_ctas_per_sm"])
+    _check(_lib().dh2_tuning_set(byref(t)), "dh2_tuning_set")
+
+
+def autotune(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,
+             mode: int | None = None, nearfield: int = 0, reps: int = 3, stream=None):
+    """dh2_autotune on one problem: returns (installed table, timed candidates as
+    [{"knob", "cls", "value", "ms"}])."""
+    dt = _dtype_code(G)
+    if mode is None:
+        mode = MODE_FP32 if dt == DH2_C64 else MODE_FP64
+    p = _params(eps, zeta, err_mode, mode, nearfield, 0)
+    t = Tuning()
+    cap = 64
+    recs = (TuneRecord * cap)()
+    nrec = c_int32(0)
+    _check(_lib().dh2_autotune(tree.handle, c_void_p(G.data_ptr()), dt, _colmajor_ld(G), byref(p),
+                               c_void_p(_stream_handle(stream)), int(reps), byref(t), ctypes.cast(recs, c_void_p),
+                               cap, byref(nrec)), "dh2_autotune")
+    log = [{"knob": TUNE_KNOBS[r.knob], "cls": int(r.cls), "value": int(r.value), "ms": float(r.ms)}
+           for r in recs[:nrec.value]]
+    return _tuning_dict(t), log
 
 
 def dh2_compress_host(tree: Tree, G, eps: float = 1e-4, zeta: float = 2.0 / 3.0, err_mode: int = 0,

@@ -35,6 +35,38 @@ inline bool mode_f32(int mode) { return mode != DH2_MODE_FP64; }  // complex64 d
 inline bool mode_mixed(int mode) { return mode == DH2_MODE_MIXED_BF16X3; }
 inline int leaf_class(int m) { return m <= 32 ? 0 : m <= 40 ? 1 : m <= 48 ? 2 : m <= 64 ? 3 : 4; }
 
+// The process's tuning table (dh2_tuning_set, dh2_autotune): read once by each
+// compression when it prepares its launches.
+std::mutex g_tune_mu;
+TuneTable g_tune = {{32, 32, 32, 32, 32}, {1, 1, 1, 1}, 0};
+TuneTable tune_current() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune;
+}
+bool tune_valid(const dh2_tuning& t) {
+  for (int c = 0; c < 5; ++c) {
+    const int v = t.jacobi_tpp[c];
+    if (v != 4 && v != 8 && v != 16 && v != 32) return false;
+  }
+  for (int c = 0; c < 4; ++c)
+    if (t.jacobi_narrow[c] < 0 || t.jacobi_narrow[c] > 2) return false;
+  return t.rq_ctas_per_sm >= 0 && t.rq_ctas_per_sm <= 4;
+}
+TuneTable to_table(const dh2_tuning& t) {
+  TuneTable x{};
+  for (int c = 0; c < 5; ++c) x.jacobi_tpp[c] = t.jacobi_tpp[c];
+  for (int c = 0; c < 4; ++c) x.jacobi_narrow[c] = t.jacobi_narrow[c];
+  x.rq_ctas_per_sm = t.rq_ctas_per_sm;
+  return x;
+}
+dh2_tuning from_table(const TuneTable& x) {
+  dh2_tuning t{};
+  for (int c = 0; c < 5; ++c) t.jacobi_tpp[c] = x.jacobi_tpp[c];
+  for (int c = 0; c < 4; ++c) t.jacobi_narrow[c] = x.jacobi_narrow[c];
+  t.rq_ctas_per_sm = x.rq_ctas_per_sm;
+  return t;
+}
+
 // Device copy of a tree's work lists (one arena, uploaded on first use).
 struct Tree::Dev {
   void* arena = nullptr;
@@ -587,6 +619,8 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
     pa.rank_ovr[sd] = nullptr;  // set by run_compress when ranks are given
   }
   pa.max_sweeps = cp.max_sweeps > 0 ? cp.max_sweeps : 30;
+  const TuneTable tt = tune_current();
+  for (int c = 0; c < 5; ++c) pa.jacobi_tpp[c] = tt.jacobi_tpp[c];
   pa.status = M->status;
   pa.pts = M->pts;
   pa.nrm = M->nrm;
@@ -1778,11 +1812,27 @@ dh2_status prepare_matrix(const dh2_tree* Tc, const void* G, dh2_dtype dtype, in
   return DH2_OK;
 }
 
+// The mixed mode's leaf step squares the singular values: the slices'
+// backward error (2^-23 of a row's largest entry) and the double-float Gram
+// matrix resolve sigma^2 to about 2^-46 of the leaf matrix's squared norm,
+// which reaches the tail sums of the rank rule once eps falls below ~1e-5.
+// There (unless the Gram matrices are asked for) the leaves take the FP32
+// streamed LQ, which works on the leaf matrix itself.
+constexpr double kMixedMinEps = 1e-5;
+dh2_compress_params leaf_path(const dh2_compress_params& p) {
+  dh2_compress_params q = p;
+  if (mode_mixed(p.mode) && p.eps < kMixedMinEps && !p.keep_gram) q.mode = DH2_MODE_FP32;
+  return q;
+}
+
 dh2_status compress_impl(const dh2_tree* Tc, const void* G, dh2_dtype dtype, int64_t ld, const double* pts_host,
                          double kappa, double diag, const dh2_compress_params* params, void* stream,
                          dh2_matrix** out, const double* nrm_host = nullptr) {
   if (!out) return DH2_EINVAL;
   *out = nullptr;  // stays NULL on every failure below
+  if (!params) return DH2_EINVAL;
+  const dh2_compress_params qp = leaf_path(*params);
+  params = &qp;
   dh2_matrix* M = nullptr;
   dh2_status s = prepare_matrix(Tc, G, dtype, ld, pts_host, kappa, diag, params, stream, &M, nrm_host);
   if (s != DH2_OK) return s;
@@ -1815,6 +1865,8 @@ dh2_status dh2_compress_host(const dh2_tree* Tc, const void* G_host, dh2_dtype d
   if (out) *out = nullptr;
   if (!Tc || !G_host || !params || !out || params->nearfield != 0) return DH2_EINVAL;
   if (dtype != DH2_C64 && dtype != DH2_C128) return DH2_EINVAL;
+  const dh2_compress_params qp = leaf_path(*params);
+  params = &qp;
   const int64_t n = Tc->tr.n;
   if (ld < n) return DH2_EINVAL;
   const size_t elem = dtype == DH2_C64 ? 8 : 16;
@@ -1879,6 +1931,8 @@ dh2_status dh2_compress_batched(int32_t nprob, const dh2_tree* const* trees, con
   for (int i = 0; i < nprob; ++i) out[i] = nullptr;
   if (nprob > kMaxBatch || !trees || !G || !ld || !params) return DH2_EINVAL;
   if (nprob > 1 && (params->rank_override[0] || params->rank_override[1])) return DH2_EINVAL;  // one problem's ranks
+  const dh2_compress_params qp = leaf_path(*params);
+  params = &qp;
   std::vector<dh2_matrix*> Ms;
   for (int i = 0; i < nprob; ++i) {
     dh2_matrix* M = nullptr;
@@ -1913,6 +1967,8 @@ dh2_status dh2_plan_create(int32_t nprob, const dh2_tree* const* trees, const vo
   *out = nullptr;
   if (nprob > kMaxBatch || !trees || !G || !ld || !params) return DH2_EINVAL;
   if (nprob > 1 && (params->rank_override[0] || params->rank_override[1])) return DH2_EINVAL;
+  const dh2_compress_params qp = leaf_path(*params);
+  params = &qp;
   dh2_plan* P = new (std::nothrow) dh2_plan;
   if (!P) return DH2_ENOMEM;
   // the capture runs on a stream of the library's own (the caller's may be the
@@ -2010,6 +2066,94 @@ void dh2_plan_free(dh2_plan* P) {
   }
   cudaGetLastError();
   delete P;
+}
+
+dh2_status dh2_tuning_get(dh2_tuning* out) {
+  if (!out) return DH2_EINVAL;
+  *out = from_table(tune_current());
+  return DH2_OK;
+}
+
+dh2_status dh2_tuning_set(const dh2_tuning* t) {
+  if (!t || !tune_valid(*t)) return DH2_EINVAL;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune = to_table(*t);
+  return DH2_OK;
+}
+
+dh2_status dh2_autotune(const dh2_tree* T, const void* G, dh2_dtype dtype, int64_t ld,
+                        const dh2_compress_params* params, void* stream, int32_t reps, dh2_tuning* out,
+                        dh2_tune_record* records, int32_t cap, int32_t* nrec) {
+  if (nrec) *nrec = 0;
+  if (!T || !G || !params || !out || reps < 1 || reps > 15 || (records && (cap < 0 || !nrec))) return DH2_EINVAL;
+  const TuneTable saved = tune_current();
+  const bool mixed = mode_mixed(leaf_path(*params).mode);
+  // factor classes with leaf pairs in this problem
+  bool has[5] = {false, false, false, false, false};
+  for (int sd = 0; sd < 2; ++sd)
+    for (int64_t p : T->tr.side[sd].leaf_pairs) has[leaf_class(T->tr.size[T->tr.side[sd].pairs[p].cluster])] = true;
+  auto install = [&](const TuneTable& x) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = x;
+  };
+  int nr = 0;
+  // median over reps of the device time of the phases the knob acts on
+  auto timed = [&](const TuneTable& x, int knob, int cls, int value, float* med) -> dh2_status {
+    install(x);
+    std::vector<float> t;
+    for (int r = 0; r < reps; ++r) {
+      dh2_matrix* M = nullptr;
+      const dh2_status s = dh2_compress(T, G, dtype, ld, params, stream, &M);
+      if (s != DH2_OK) return s;
+      t.push_back(knob == 0 ? M->phase_ms[2] : (mixed ? M->leaf_split_ms[1] : M->phase_ms[1]) + M->phase_ms[3]);
+      dh2_matrix_free(M);
+    }
+    std::sort(t.begin(), t.end());
+    *med = t[t.size() / 2];
+    if (records && nr < cap) records[nr++] = dh2_tune_record{knob, cls, value, *med};
+    return DH2_OK;
+  };
+  // one knob: every candidate from the current best table, keep the fastest
+  TuneTable best = saved;
+  auto descend = [&](int knob, int cls, const int* cand, int ncand, int32_t* field_of_best) -> dh2_status {
+    float tbest = 0.f;
+    int vbest = *field_of_best;
+    for (int i = 0; i < ncand; ++i) {
+      TuneTable x = best;
+      int32_t* f = knob == 0 ? &x.rq_ctas_per_sm : knob == 1 ? &x.jacobi_narrow[cls] : &x.jacobi_tpp[cls];
+      *f = cand[i];
+      float ms = 0.f;
+      const dh2_status s = timed(x, knob, cls, cand[i], &ms);
+      if (s != DH2_OK) return s;
+      if (i == 0 || ms < tbest) {
+        tbest = ms;
+        vbest = cand[i];
+      }
+    }
+    *field_of_best = vbest;
+    return DH2_OK;
+  };
+  dh2_status s = DH2_OK;
+  {
+    dh2_matrix* M = nullptr;  // untimed first call: uploads and first-use allocations
+    s = dh2_compress(T, G, dtype, ld, params, stream, &M);
+    if (s == DH2_OK) dh2_matrix_free(M);
+  }
+  static const int kRq[3] = {0, 1, 2}, kNarrow[3] = {0, 1, 2}, kTpp[3] = {32, 16, 8};
+  if (s == DH2_OK) s = descend(0, 0, kRq, 3, &best.rq_ctas_per_sm);
+  for (int c = 0; c < 5 && s == DH2_OK; ++c) {
+    if (!has[c]) continue;
+    if (mixed && c < 4) s = descend(1, c, kNarrow, 3, &best.jacobi_narrow[c]);
+    if (s == DH2_OK) s = descend(2, c, kTpp, 3, &best.jacobi_tpp[c]);
+  }
+  if (nrec) *nrec = nr;
+  if (s != DH2_OK) {
+    install(saved);
+    return s;
+  }
+  install(best);
+  *out = from_table(best);
+  return DH2_OK;
 }
 
 void dh2_matrix_free(dh2_matrix* M) { matrix_release(M); }

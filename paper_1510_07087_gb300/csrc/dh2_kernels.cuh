@@ -14,6 +14,19 @@ struct __align__(2 * sizeof(T)) C2 {
 
 // Arguments of the per-pair factorisation kernel (one CTA per (cluster,
 // direction) pair).  Index [side] selects the row (0) or column (1) basis.
+// Launch choices the autotuner sets (the public dh2_tuning, validated): one
+// table per process, read when a compression prepares its launches.
+struct TuneTable {
+  int32_t jacobi_tpp[5];     // factor classes (<= 32, 40, 48, 64 rows, more): most threads per Jacobi column pair
+  int32_t jacobi_narrow[4];  // mixed mode leaf classes: Jacobi CTAs of ~4 (0), ~2 (1) or ~1 (2) x rows threads
+  int32_t rq_ctas_per_sm;    // leaf R kernel: resident CTAs per SM (0: its occupancy limit)
+};
+TuneTable tune_current();
+// factor class of a pair kernel compiled for P_T rows
+__host__ __device__ constexpr int factor_class(int P_T) {
+  return P_T <= 32 ? 0 : P_T <= 40 ? 1 : P_T <= 48 ? 2 : P_T <= 64 ? 3 : 4;
+}
+
 template <typename T>
 struct PairArgs {
   const int32_t* start[2];            // first row index of the pair's cluster
@@ -43,6 +56,7 @@ struct PairArgs {
   const int64_t* hoff[2];             // mixed modes: per pair, first entry of its Gram matrix in H
   const int32_t* rank_ovr[2];         // per pair a rank replacing the truncation rule (< 0: the rule), or NULL
   int32_t max_sweeps;
+  int32_t jacobi_tpp[5];              // per factor class: most threads per Jacobi column pair (TuneTable)
   uint32_t* status;
   // matrix-free mode: entries generated from points (permuted order, 3 doubles
   // each) and, for the double layer, their normals (NULL for the single layer)

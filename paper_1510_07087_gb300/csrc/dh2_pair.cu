@@ -543,9 +543,6 @@ __device__ void gram_cholesky(const PairArgs<T>& a, int side, int pid, int p, in
 #ifndef DH2_LQT
 #define DH2_LQT 8  // threads per row in the streamed LQ (4 or 8)
 #endif
-#ifndef DH2_JACOBI_TPP
-#define DH2_JACOBI_TPP 32  // most threads per column pair in the Jacobi step (4..32)
-#endif
 // Steps 2-4 of a pair (Jacobi on the K leading columns of L in shared memory,
 // the rank from the tail sums, Q), shared by pair_kernel and
 // gram_jacobi_kernel.
@@ -559,12 +556,13 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
   __shared__ int sh_k;
   (void)t_b;
   // ---------------------------------------------------------------- 2. Jacobi
-  // one column pair per group of tpp threads (as many as the pe/2 pairs of a
-  // round allow, 4..32); round-robin ordering over pe columns
+  // one column pair per group of tpp threads (at most the tuning table's
+  // width for this class, fewer where the pe/2 pairs of a round need more
+  // groups; 4..32); round-robin ordering over pe columns
   const int pe = K + (K & 1);
   const T tol = T(p) * Eps<T>::u;
   constexpr int JH = (P_T / 2 + NT / 4 - 1) / (NT / 4);  // pairs per group at most
-  int tpp = DH2_JACOBI_TPP;
+  int tpp = a.jacobi_tpp[factor_class(P_T)];
   while (tpp > 4 && tpp * (pe / 2) > NT) tpp >>= 1;
   const int jng = NT / tpp;
   const int jg = tid / tpp, jl = tid & (tpp - 1);
@@ -1305,8 +1303,8 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
 // from its singular-value record.  Only L is held in shared memory, so that
 // more pairs run side by side than in the Cholesky, whose shared memory holds
 // all of H.
-template <int P_T, int NT>
-__global__ void __launch_bounds__(NT, 2048 / NT - 4)
+template <int P_T, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     gram_jacobi_kernel(const PairArgs<float>* __restrict__ args, const uint32_t* __restrict__ codes, const int P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int LDL = P + 1;
@@ -1786,6 +1784,8 @@ bool launch_rq_leaf(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+  const int cap = tune_current().rq_ctas_per_sm;  // the tuning table's choice, within the occupancy limit
+  if (cap > 0 && cap < per_sm) per_sm = cap;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)std::max(1, nsm) * std::max(1, per_sm));
   kern<<<grid, 128, smem, st>>>(args, tiles, (int64_t)ntiles, P);
   return true;
@@ -1827,23 +1827,42 @@ bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
   return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st, count);
 }
 
-template <int P_T, int NT>
+// The Jacobi launch of a class: NT = 4 x rows threads per CTA, or (the
+// tuning table's narrow choices) NTN, a multiple of 32 near 2 x rows, or NTM
+// near 1 x rows, with the same threads per SM (about twice or four times the
+// CTAs, so more pairs at once; at most 32 CTAs per SM).
+template <int P_T, int NT, int NTN, int NTM>
 bool launch_gram_factor(const PairArgs<float>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
+  static_assert(NT % 32 == 0 && NTN % 32 == 0 && NTM % 32 == 0 && NTM >= P_T,
+                "whole warps (the Jacobi reductions run converged), one thread per column of the rank step");
   if (!launch_one<float, P_T, false, NT, true>(args, codes, nblocks, P, st)) return false;
   const size_t smem = (((size_t)P * (P + 1) * sizeof(C2<float>) + 15) & ~(size_t)15) + (size_t)P * sizeof(double) +
                       (size_t)P * sizeof(int);
-  auto kern = gram_jacobi_kernel<P_T, NT>;
-  if (!set_smem(kern, smem)) return false;
-  kern<<<nblocks, NT, smem, st>>>(args, codes, P);
+  constexpr int MINB = 2048 / NT - 4;
+  const int narrow = tune_current().jacobi_narrow[factor_class(P_T)];
+  if (narrow == 2) {
+    constexpr int MB = NT * MINB / NTM < 32 ? NT * MINB / NTM : 32;
+    auto kern = gram_jacobi_kernel<P_T, NTM, MB>;
+    if (!set_smem(kern, smem)) return false;
+    kern<<<nblocks, NTM, smem, st>>>(args, codes, P);
+  } else if (narrow == 1) {
+    auto kern = gram_jacobi_kernel<P_T, NTN, NT * MINB / NTN>;
+    if (!set_smem(kern, smem)) return false;
+    kern<<<nblocks, NTN, smem, st>>>(args, codes, P);
+  } else {
+    auto kern = gram_jacobi_kernel<P_T, NT, MINB>;
+    if (!set_smem(kern, smem)) return false;
+    kern<<<nblocks, NT, smem, st>>>(args, codes, P);
+  }
   return true;
 }
 
 bool launch_pair_kernel_gram(const PairArgs<float>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st) {
   if (nblocks <= 0) return true;
-  if (P <= 32) return launch_gram_factor<32, 128>(args, codes, nblocks, P, st);
-  if (P <= 40) return launch_gram_factor<40, 160>(args, codes, nblocks, P, st);
-  if (P <= 48) return launch_gram_factor<48, 192>(args, codes, nblocks, P, st);
-  if (P <= 64) return launch_gram_factor<64, 256>(args, codes, nblocks, P, st);
+  if (P <= 32) return launch_gram_factor<32, 128, 64, 32>(args, codes, nblocks, P, st);
+  if (P <= 40) return launch_gram_factor<40, 160, 96, 64>(args, codes, nblocks, P, st);
+  if (P <= 48) return launch_gram_factor<48, 192, 96, 64>(args, codes, nblocks, P, st);
+  if (P <= 64) return launch_gram_factor<64, 256, 128, 64>(args, codes, nblocks, P, st);
   return false;
 }
 

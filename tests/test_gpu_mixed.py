@@ -150,6 +150,27 @@ def test_mixed_paper_parameters():
     check_reduced(c, max_bad_frac=0.01, max_diff=1)
 
 
+def test_mixed_below_1e5_takes_the_fp32_leaf_step():
+    """The Gram path squares the singular values, so below eps = 1e-5 it no longer resolves the
+    tail sums: there the mixed mode runs the FP32 mode's leaf step (its ranks and storage are the
+    FP32 mode's), unless keep_gram asks for the Gram matrices; at 1e-5 it keeps the Gram path."""
+    D = dev()
+    pts = fibonacci_sphere(4096)
+    T = D.dh2_tree_build(pts, 32, 12.0)
+    G = helmholtz_matrix(pts, 12.0)[np.ix_(T.perm(), T.perm())]
+    Gd = colmajor(G, torch.complex64)
+    Mm = D.dh2_compress(T, Gd, eps=1e-5, mode=D.MODE_MIXED_BF16X3)
+    assert Mm.leaf_split_ms()[0] > 0  # the Gram launches ran
+    Mm = D.dh2_compress(T, Gd, eps=1e-6, mode=D.MODE_MIXED_BF16X3)
+    Mf = D.dh2_compress(T, Gd, eps=1e-6, mode=D.MODE_FP32)
+    assert Mm.leaf_split_ms()[0] == 0
+    for side in (0, 1):
+        assert np.array_equal(Mm.ranks(side), Mf.ranks(side))
+    assert Mm.storage() == Mf.storage()
+    Mk = D.dh2_compress(T, Gd, eps=1e-6, mode=D.MODE_MIXED_BF16X3, keep_gram=1)
+    assert Mk.leaf_split_ms()[0] > 0
+
+
 def test_mixed_wait_bound_reports_timeout():
     D = dev()
     from paper_1510_07087_gb300 import _binding as B

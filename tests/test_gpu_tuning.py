@@ -1,0 +1,86 @@
+"""The autotuner and its table (dh2_autotune, dh2_tuning_set/get).
+
+  * dh2_autotune times every candidate of each knob (the R grid, then per leaf
+    class the narrow Jacobi launch and the Jacobi width), installs the fastest
+    value of each and returns the installed table and the timed candidates;
+  * the R grid changes no result (bit-identical products);
+  * under other Jacobi widths and launch shapes (which change the rounding
+    order of the rotation sums only) the FP64 mode still meets the FP64 parity
+    criteria against the oracle and the mixed mode its reduced-precision ones.
+"""
+import numpy as np
+import pytest
+
+from gpu_cases import Case, check_fp64, check_reduced, colmajor, dev
+from synth import helmholtz_matrix, random_ellipsoid
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(autouse=True)
+def _restore_table():
+    D = dev()
+    saved = D.tuning()
+    yield
+    D.set_tuning(saved)
+
+
+def _leaf64_problem(n=4096, kappa=12.0):
+    D = dev()
+    pts = random_ellipsoid(n)
+    T = D.dh2_tree_build(pts, 64, kappa)
+    G = helmholtz_matrix(pts, kappa)[np.ix_(T.perm(), T.perm())]
+    return T, G, colmajor(G, torch.complex64)
+
+
+def test_autotune_installs_the_fastest_candidates():
+    D = dev()
+    T, _, Gd = _leaf64_problem()
+    table, log = D.autotune(T, Gd, eps=1e-4, mode=D.MODE_MIXED_BF16X3, reps=3)
+    assert D.tuning() == table
+    assert all(r["ms"] > 0 for r in log)
+    rq = [r for r in log if r["knob"] == "rq_ctas_per_sm"]
+    assert [r["value"] for r in rq] == [0, 1, 2]
+    assert table["rq_ctas_per_sm"] == min(rq, key=lambda r: r["ms"])["value"]
+    classes = sorted({r["cls"] for r in log if r["knob"] == "jacobi_tpp"})
+    assert classes, log  # a leaf-64 tree has leaves in several classes
+    for c in classes:
+        nar = [r for r in log if r["knob"] == "jacobi_narrow" and r["cls"] == c]
+        tpp = [r for r in log if r["knob"] == "jacobi_tpp" and r["cls"] == c]
+        assert [r["value"] for r in nar] == [0, 1, 2] and [r["value"] for r in tpp] == [32, 16, 8]
+        assert table["jacobi_narrow"][c] == min(nar, key=lambda r: r["ms"])["value"]
+        assert table["jacobi_tpp"][c] == min(tpp, key=lambda r: r["ms"])["value"]
+    print("autotuned table:", table)
+
+
+def test_r_grid_changes_no_result():
+    """The persistent R kernel's CTAs per SM only change which CTA takes a tile: the ranks, the
+    stored bases and every coupling matrix S_b (formed from R) are bit-identical."""
+    D = dev()
+    T, _, Gd = _leaf64_problem(2048, 8.0)
+    adm = np.flatnonzero(T.blocks()[:, 2] == 1)
+    rng = np.random.default_rng(9)
+    sample = rng.choice(adm, min(60, len(adm)), replace=False)
+    res = []
+    for rq in (0, 1, 2):
+        t = D.tuning()
+        t["rq_ctas_per_sm"] = rq
+        D.set_tuning(t)
+        M = D.dh2_compress(T, Gd, eps=1e-4, mode=D.MODE_MIXED_BF16X3)
+        res.append(([M.ranks(0), M.ranks(1)], [M.coupling(int(b)) for b in sample],
+                    [M.pair_basis(s, p) for s in (0, 1) for p in range(0, len(M.ranks(s)), 97)]))
+    for r, S, V in res[1:]:
+        assert all(np.array_equal(a, b) for a, b in zip(r, res[0][0]))
+        assert all(np.array_equal(a, b) for a, b in zip(S, res[0][1]))
+        assert all(np.array_equal(a, b) for a, b in zip(V, res[0][2]))
+
+
+@pytest.mark.parametrize("tpp,narrow", [(8, 2), (16, 0)])
+def test_other_jacobi_choices_keep_parity(tpp, narrow):
+    D = dev()
+    D.set_tuning({"jacobi_tpp": [tpp] * 5, "jacobi_narrow": [narrow] * 4, "rq_ctas_per_sm": 1})
+    check_fp64(Case(2048, 6.0, 64, 1e-4, D.MODE_FP64, pts=random_ellipsoid(2048)))
+    c = Case(4096, 12.0, 64, 1e-4, D.MODE_MIXED_BF16X3, pts=random_ellipsoid(4096))
+    check_reduced(c, max_bad_frac=0.01, max_diff=1)

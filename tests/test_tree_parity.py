@@ -108,6 +108,39 @@ def test_invalid_arguments_rejected():
         b.dh2_tree_build(bad, 16, 4.0)
 
 
+def test_tuning_table_set_get_and_validation():
+    """dh2_tuning_set installs a table that dh2_tuning_get returns; a value outside a knob's set
+    (a Jacobi width that is not a power of two up to 32, a narrow choice outside 0..2, more than 4
+    R CTAs per SM) is refused with DH2_EINVAL and leaves the table as it was; dh2_autotune checks
+    its arguments before any device work."""
+    b = _lib_or_skip()
+    saved = b.tuning()
+    try:
+        t = {"jacobi_tpp": [32, 16, 8, 4, 32], "jacobi_narrow": [1, 0, 1, 0], "rq_ctas_per_sm": 2}
+        b.set_tuning(t)
+        assert b.tuning() == t
+        for bad in ({"jacobi_tpp": [32, 12, 8, 4, 32]}, {"jacobi_tpp": [64, 16, 8, 4, 32]},
+                    {"jacobi_narrow": [3, 0, 0, 0]}, {"rq_ctas_per_sm": 5}, {"rq_ctas_per_sm": -1}):
+            with pytest.raises(b.DH2Error) as ei:
+                b.set_tuning({**t, **bad})
+            assert ei.value.status == 1
+            assert b.tuning() == t
+        lib = b._lib()
+        T = b.dh2_tree_build(fibonacci_sphere(64), 16, 4.0)
+        p = b.CompressParams(1e-4, 2.0 / 3.0, 0, b.MODE_FP32, 0, 0)
+        out = b.Tuning()
+        nrec = b.c_int32(7)
+        for reps in (0, 16):  # outside 1..15
+            assert lib.dh2_autotune(T.handle, b.c_void_p(1), b.DH2_C64, 64, b.byref(p), None, reps, b.byref(out),
+                                    None, 0, b.byref(nrec)) == 1
+            assert nrec.value == 0
+        assert lib.dh2_autotune(T.handle, None, b.DH2_C64, 64, b.byref(p), None, 3, b.byref(out), None, 0,
+                                None) == 1
+        assert b.tuning() == t
+    finally:
+        b.set_tuning(saved)
+
+
 def test_host_input_arguments_rejected_before_any_device_work():
     """dh2_compress_host checks its arguments on the host first: view mode (the staging buffer
     is reused), ld < n, an unknown dtype and null pointers return DH2_EINVAL with no handle."""
