@@ -282,22 +282,28 @@ void dh2_plan_free(dh2_plan* P);
  *                    Jacobi launch, 0 = 4 x rows, 1 = about 2 x rows
  *                    (default), 2 = about 1 x rows (a multiple of 32), at the
  *                    same threads per SM.  Changes the rounding as above.
- *  rq_ctas_per_sm  : resident CTAs per SM of the persistent leaf R kernel,
- *                    1..4 within its occupancy limit, 0 = that limit
- *                    (default).  Changes no result.
+ *  rq_ctas_per_sm  : resident CTAs per SM of the persistent leaf R kernel
+ *                    of the FP32 pipes, 1..4 within its occupancy limit, 0 =
+ *                    that limit (default).  Changes no result.
+ *  rq_tensor       : mixed mode: 1 = the leaf R on the tensor cores (bf16
+ *                    slices, FP32 accumulation), 0 = on the FP32 pipes
+ *                    (default, measured faster).  The two agree to FP32
+ *                    rounding.
  * dh2_tuning_set returns DH2_EINVAL (table unchanged) for a value outside
  * these sets. */
 typedef struct {
   int32_t jacobi_tpp[5];
   int32_t jacobi_narrow[4];
   int32_t rq_ctas_per_sm;
-  int32_t reserved[2];
+  int32_t rq_tensor;
+  int32_t reserved;
 } dh2_tuning;
 dh2_status dh2_tuning_get(dh2_tuning* out);
 dh2_status dh2_tuning_set(const dh2_tuning* tuning);
 /* One timed candidate of dh2_autotune: knob 0 = rq_ctas_per_sm, 1 =
- * jacobi_narrow[cls], 2 = jacobi_tpp[cls]; ms = median device time of the
- * phase the knob acts on (leaf R, or leaf factors) over the repetitions. */
+ * jacobi_narrow[cls], 2 = jacobi_tpp[cls], 3 = rq_tensor; ms = median device
+ * time of the phase the knob acts on (leaf R, or leaf factors) over the
+ * repetitions. */
 typedef struct {
   int32_t knob;
   int32_t cls;
@@ -305,8 +311,9 @@ typedef struct {
   float ms;
 } dh2_tune_record;
 /* Autotune the table on one problem: compresses (tree, G) with `params`
- * under each candidate of each knob in turn (coordinate descent: the R grid,
- * then per factor class the narrow Jacobi launch and the Jacobi width; a
+ * under each candidate of each knob in turn (coordinate descent: in the
+ * mixed mode the R kernel, then the R grid, then per factor class the
+ * Jacobi launch width and the threads per column pair; a
  * class with no pairs in the problem is skipped), `reps` calls per candidate
  * (1..15), keeps the fastest value of each knob, installs the result and
  * returns it in `out`.  records: NULL, or room for `cap` records, of which
@@ -454,6 +461,7 @@ enum {
   DH2_KC_LEAF_GRAM = 20,    /* + leaf row class 0..3: tensor-core Gram matrices (MIXED_BF16X3)   */
   DH2_KC_GRAM_SCALES = 24,  /* row scales of the leaf Gram matrices (MIXED_BF16X3)               */
   DH2_KC_LEAF_JACOBI = 25,  /* + leaf row class 0..3: Jacobi, rank and Q after the Cholesky (MIXED) */
+  DH2_KC_LEAF_R_TC = 29,    /* leaf R_tc = Q_tc^* G^omega_tc on the tensor cores, all classes (MIXED) */
   DH2_KC_COUNT = 32
 };
 /* Launches of the last compression that produced M, by kernel class

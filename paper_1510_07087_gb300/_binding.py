@@ -36,6 +36,7 @@ KC_PROJECT = 19
 KC_LEAF_GRAM = 20
 KC_GRAM_SCALES = 24
 KC_LEAF_JACOBI = 25
+KC_LEAF_R_TC = 29
 KC_GRAM_SCALES = 24
 KC_COUNT = 32
 
@@ -78,19 +79,19 @@ class TreeStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("jacobi_tpp", c_int32 * 5), ("jacobi_narrow", c_int32 * 4), ("rq_ctas_per_sm", c_int32),
-                ("reserved", c_int32 * 2)]
+                ("rq_tensor", c_int32), ("reserved", c_int32)]
 
 
 class TuneRecord(ctypes.Structure):
     _fields_ = [("knob", c_int32), ("cls", c_int32), ("value", c_int32), ("ms", ctypes.c_float)]
 
 
-TUNE_KNOBS = ("rq_ctas_per_sm", "jacobi_narrow", "jacobi_tpp")
+TUNE_KNOBS = ("rq_ctas_per_sm", "jacobi_narrow", "jacobi_tpp", "rq_tensor")
 
 
 def _tuning_dict(t: Tuning) -> dict:
     return {"jacobi_tpp": list(t.jacobi_tpp), "jacobi_narrow": list(t.jacobi_narrow),
-            "rq_ctas_per_sm": int(t.rq_ctas_per_sm)}
+            "rq_ctas_per_sm": int(t.rq_ctas_per_sm), "rq_tensor": int(t.rq_tensor)}
 
 
 class DH2Error(RuntimeError):
@@ -426,6 +427,7 @@ def set_tuning(d: dict) -> None:
     for c, v in enumerate(d["jacobi_narrow"]):
         t.jacobi_narrow[c] = int(v)
     t.rq_ctas_per_sm = int(d["rq_ctas_per_sm"])
+    t.rq_tensor = int(d.get("rq_tensor", 0))
     _check(_lib().dh2_tuning_set(byref(t)), "dh2_tuning_set")
 
 

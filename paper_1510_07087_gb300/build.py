@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdh2.so")
 
 HOST_SOURCES = ["dh2_tree.cpp"]
-CUDA_SOURCES = ["dh2_pair.cu", "dh2_gram.cu", "dh2_ops.cu", "dh2_api.cu"]
+CUDA_SOURCES = ["dh2_pair.cu", "dh2_gram.cu", "dh2_rq_tc.cu", "dh2_ops.cu", "dh2_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -9,6 +9,7 @@
 #include <functional>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include <cstdio>
@@ -38,7 +39,7 @@ inline int leaf_class(int m) { return m <= 32 ? 0 : m <= 40 ? 1 : m <= 48 ? 2 : 
 // The process's tuning table (dh2_tuning_set, dh2_autotune): read once by each
 // compression when it prepares its launches.
 std::mutex g_tune_mu;
-TuneTable g_tune = {{32, 32, 32, 32, 32}, {1, 1, 1, 1}, 0};
+TuneTable g_tune = {{32, 32, 32, 32, 32}, {1, 1, 1, 1}, 0, 0};
 TuneTable tune_current() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   return g_tune;
@@ -50,13 +51,14 @@ bool tune_valid(const dh2_tuning& t) {
   }
   for (int c = 0; c < 4; ++c)
     if (t.jacobi_narrow[c] < 0 || t.jacobi_narrow[c] > 2) return false;
-  return t.rq_ctas_per_sm >= 0 && t.rq_ctas_per_sm <= 4;
+  return t.rq_ctas_per_sm >= 0 && t.rq_ctas_per_sm <= 4 && (t.rq_tensor == 0 || t.rq_tensor == 1);
 }
 TuneTable to_table(const dh2_tuning& t) {
   TuneTable x{};
   for (int c = 0; c < 5; ++c) x.jacobi_tpp[c] = t.jacobi_tpp[c];
   for (int c = 0; c < 4; ++c) x.jacobi_narrow[c] = t.jacobi_narrow[c];
   x.rq_ctas_per_sm = t.rq_ctas_per_sm;
+  x.rq_tensor = t.rq_tensor;
   return x;
 }
 dh2_tuning from_table(const TuneTable& x) {
@@ -64,6 +66,7 @@ dh2_tuning from_table(const TuneTable& x) {
   for (int c = 0; c < 5; ++c) t.jacobi_tpp[c] = x.jacobi_tpp[c];
   for (int c = 0; c < 4; ++c) t.jacobi_narrow[c] = x.jacobi_narrow[c];
   t.rq_ctas_per_sm = x.rq_ctas_per_sm;
+  t.rq_tensor = x.rq_tensor;
   return t;
 }
 
@@ -1283,8 +1286,18 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       leaf_factor(d_leaf + cls_begin[c], (int)(cls_begin[c + 1] - cls_begin[c]), c,
                   kev_ok && cls_begin[c + 1] > cls_begin[c]);
     rec(2);
-    // R of the leaf pairs, one launch per size class (shared memory sized by the class's rows)
-    for (int c = 0; c < kLeafClasses; ++c) {
+    // R of the leaf pairs: in the mixed mode one tensor-core launch over every
+    // class's tiles; otherwise one launch per size class (shared memory sized by
+    // the class's rows)
+    const bool rq_tc = mixed && tune_current().rq_tensor != 0;
+    if (rq_tc && tile_cls_begin[kLeafClasses] > 0) {
+      if constexpr (std::is_same<T, float>::value) {
+        const uint32_t sl = (uint32_t)std::min<int64_t>(std::max<int64_t>(cp.spin_limit, 0), (int64_t)UINT32_MAX);
+        ok_launch &= launch_rq_tc(d_pa, d_ltiles, tile_cls_begin[kLeafClasses], sl, st);
+        counted(DH2_KC_LEAF_R_TC, true);
+      }
+    }
+    for (int c = 0; c < kLeafClasses && !rq_tc; ++c) {
       const int64_t nt = tile_cls_begin[c + 1] - tile_cls_begin[c];
       if (nt > 0) {
         ok_launch &= launch_rq_kernel<T>(d_pa, d_ltiles + tile_cls_begin[c], (int)nt, even_up(std::max(2, cls_maxm[c])), false,
@@ -2105,7 +2118,8 @@ dh2_status dh2_autotune(const dh2_tree* T, const void* G, dh2_dtype dtype, int64
       dh2_matrix* M = nullptr;
       const dh2_status s = dh2_compress(T, G, dtype, ld, params, stream, &M);
       if (s != DH2_OK) return s;
-      t.push_back(knob == 0 ? M->phase_ms[2] : (mixed ? M->leaf_split_ms[1] : M->phase_ms[1]) + M->phase_ms[3]);
+      t.push_back(knob == 0 || knob == 3 ? M->phase_ms[2]
+                                         : (mixed ? M->leaf_split_ms[1] : M->phase_ms[1]) + M->phase_ms[3]);
       dh2_matrix_free(M);
     }
     std::sort(t.begin(), t.end());
@@ -2120,7 +2134,10 @@ dh2_status dh2_autotune(const dh2_tree* T, const void* G, dh2_dtype dtype, int64
     int vbest = *field_of_best;
     for (int i = 0; i < ncand; ++i) {
       TuneTable x = best;
-      int32_t* f = knob == 0 ? &x.rq_ctas_per_sm : knob == 1 ? &x.jacobi_narrow[cls] : &x.jacobi_tpp[cls];
+      int32_t* f = knob == 0   ? &x.rq_ctas_per_sm
+                   : knob == 1 ? &x.jacobi_narrow[cls]
+                   : knob == 2 ? &x.jacobi_tpp[cls]
+                               : &x.rq_tensor;
       *f = cand[i];
       float ms = 0.f;
       const dh2_status s = timed(x, knob, cls, cand[i], &ms);
@@ -2139,7 +2156,8 @@ dh2_status dh2_autotune(const dh2_tree* T, const void* G, dh2_dtype dtype, int64
     s = dh2_compress(T, G, dtype, ld, params, stream, &M);
     if (s == DH2_OK) dh2_matrix_free(M);
   }
-  static const int kRq[3] = {0, 1, 2}, kNarrow[3] = {0, 1, 2}, kTpp[3] = {32, 16, 8};
+  static const int kRq[3] = {0, 1, 2}, kNarrow[3] = {0, 1, 2}, kTpp[3] = {32, 16, 8}, kTensor[2] = {0, 1};
+  if (s == DH2_OK && mixed) s = descend(3, 0, kTensor, 2, &best.rq_tensor);
   if (s == DH2_OK) s = descend(0, 0, kRq, 3, &best.rq_ctas_per_sm);
   for (int c = 0; c < 5 && s == DH2_OK; ++c) {
     if (!has[c]) continue;

@@ -20,6 +20,7 @@ struct TuneTable {
   int32_t jacobi_tpp[5];     // factor classes (<= 32, 40, 48, 64 rows, more): most threads per Jacobi column pair
   int32_t jacobi_narrow[4];  // mixed mode leaf classes: Jacobi CTAs of ~4 (0), ~2 (1) or ~1 (2) x rows threads
   int32_t rq_ctas_per_sm;    // leaf R kernel: resident CTAs per SM (0: its occupancy limit)
+  int32_t rq_tensor;         // mixed mode: leaf R on the tensor cores (1) or the FP32 pipes (0)
 };
 TuneTable tune_current();
 // factor class of a pair kernel compiled for P_T rows
@@ -170,6 +171,12 @@ constexpr int kGramWindow = 448;
 // H = A A^* for the leaf pairs of a launch list (leaves of at most maxm <= 64
 // rows) on the tensor cores; false if the launch cannot run.
 bool launch_gram(const GramArgs* args_dev, const uint32_t* codes, int n, int maxm, cudaStream_t st);
+
+// R = Q^* A of the mixed mode's leaf pairs on the tensor cores, over a list of
+// R tiles of kRTile columns (all leaf classes; a 128-column tile starts at
+// every entry whose first column is a multiple of 128); false if it cannot run.
+bool launch_rq_tc(const PairArgs<float>* args_dev, const uint64_t* tiles, int64_t ntiles, uint32_t spin_limit,
+                  cudaStream_t st);
 
 // Phase cycle counters of the pair kernel (only with -DDH2_PROFILE); 17 values.
 void prof_reset_pair();

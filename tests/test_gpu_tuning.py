@@ -41,6 +41,9 @@ def test_autotune_installs_the_fastest_candidates():
     table, log = D.autotune(T, Gd, eps=1e-4, mode=D.MODE_MIXED_BF16X3, reps=3)
     assert D.tuning() == table
     assert all(r["ms"] > 0 for r in log)
+    ten = [r for r in log if r["knob"] == "rq_tensor"]
+    assert [r["value"] for r in ten] == [0, 1]
+    assert table["rq_tensor"] == min(ten, key=lambda r: r["ms"])["value"]
     rq = [r for r in log if r["knob"] == "rq_ctas_per_sm"]
     assert [r["value"] for r in rq] == [0, 1, 2]
     assert table["rq_ctas_per_sm"] == min(rq, key=lambda r: r["ms"])["value"]
@@ -67,6 +70,7 @@ def test_r_grid_changes_no_result():
     for rq in (0, 1, 2):
         t = D.tuning()
         t["rq_ctas_per_sm"] = rq
+        t["rq_tensor"] = 0  # the grid of the FP32-pipe R kernel
         D.set_tuning(t)
         M = D.dh2_compress(T, Gd, eps=1e-4, mode=D.MODE_MIXED_BF16X3)
         res.append(([M.ranks(0), M.ranks(1)], [M.coupling(int(b)) for b in sample],
@@ -77,10 +81,41 @@ def test_r_grid_changes_no_result():
         assert all(np.array_equal(a, b) for a, b in zip(V, res[0][2]))
 
 
-@pytest.mark.parametrize("tpp,narrow", [(8, 2), (16, 0)])
-def test_other_jacobi_choices_keep_parity(tpp, narrow):
+@pytest.mark.parametrize("tpp,narrow,tensor", [(8, 2, 1), (16, 0, 0)])
+def test_other_choices_keep_parity(tpp, narrow, tensor):
     D = dev()
-    D.set_tuning({"jacobi_tpp": [tpp] * 5, "jacobi_narrow": [narrow] * 4, "rq_ctas_per_sm": 1})
+    D.set_tuning({"jacobi_tpp": [tpp] * 5, "jacobi_narrow": [narrow] * 4, "rq_ctas_per_sm": 1,
+                  "rq_tensor": tensor})
     check_fp64(Case(2048, 6.0, 64, 1e-4, D.MODE_FP64, pts=random_ellipsoid(2048)))
     c = Case(4096, 12.0, 64, 1e-4, D.MODE_MIXED_BF16X3, pts=random_ellipsoid(4096))
     check_reduced(c, max_bad_frac=0.01, max_diff=1)
+
+
+def test_tensor_core_r_agrees_with_the_fp32_pipes():
+    """The mixed mode's leaf R on the tensor cores (three bf16 slices per operand, six products,
+    FP32 accumulation) and on the FP32 pipes agree to FP32 rounding: the leaf ranks (which R does
+    not enter) are equal, the level ranks equal outside near-ties, and the coupling matrices agree
+    to 1e-4 of their norm."""
+    D = dev()
+    T, _, Gd = _leaf64_problem()
+    adm = np.flatnonzero(T.blocks()[:, 2] == 1)
+    sample = np.random.default_rng(4).choice(adm, min(80, len(adm)), replace=False)
+    out = []
+    for tensor in (0, 1):
+        t = D.tuning()
+        t["rq_tensor"] = tensor
+        D.set_tuning(t)
+        M = D.dh2_compress(T, Gd, eps=1e-4, mode=D.MODE_MIXED_BF16X3)
+        assert M.class_launches()[D.KC_LEAF_R_TC] == tensor
+        out.append((M, [M.ranks(0), M.ranks(1)], [M.coupling(int(b)) for b in sample]))
+    (M0, r0, S0), (M1, r1, S1) = out
+    for side in (0, 1):
+        leaf = T.pairs(side)["leaf"].astype(bool)
+        assert np.array_equal(r0[side][leaf], r1[side][leaf])
+        assert np.mean(r0[side] != r1[side]) <= 0.005
+    checked = 0
+    for a, b in zip(S0, S1):
+        if a.shape == b.shape and a.size:
+            assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(a)
+            checked += 1
+    assert checked >= len(sample) // 2
