@@ -748,16 +748,34 @@ __global__ void __launch_bounds__(256) norms_adm_kernel(const NormsArgs<T>* __re
         if (DH2_IN(gi, c_lim.G, 24, b)) g[u] = a.G[gi];
       }
     }
+    float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       acc += g[u].re * g[u].re + g[u].im * g[u].im;
-      if (cmx) {
-        float v = fmaxf(fabsf((float)g[u].re), fabsf((float)g[u].im));
-        rm = fmaxf(rm, v);
+      v[u] = fmaxf(fabsf((float)g[u].re), fabsf((float)g[u].im));
+      rm = fmaxf(rm, v[u]);
+    }
+    if (cmx) {
+      // the 8 columns' maxima over the warp's 32 rows in 9 shuffles: each
+      // exchange halves the columns a lane holds (xor 16, 8, 4), then xor 2, 1;
+      // lane l ends with column ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1)
+      const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+      float w4[4], w2[2];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0 && j0 + u < c1) atomicMax(reinterpret_cast<int*>(cmx + j0 + u), __float_as_int(v));
+      for (int i = 0; i < 4; ++i) {
+        const float keep = b4 ? v[4 + i] : v[i], give = b4 ? v[i] : v[4 + i];
+        w4[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, give, 16));
       }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float keep = b3 ? w4[2 + i] : w4[i], give = b3 ? w4[i] : w4[2 + i];
+        w2[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, give, 8));
+      }
+      float w1 = fmaxf(b2 ? w2[1] : w2[0], __shfl_xor_sync(0xffffffffu, b2 ? w2[0] : w2[1], 4));
+      w1 = fmaxf(w1, __shfl_xor_sync(0xffffffffu, w1, 2));
+      w1 = fmaxf(w1, __shfl_xor_sync(0xffffffffu, w1, 1));
+      const int u = (int)b4 * 4 + (int)b3 * 2 + (int)b2;
+      if ((lane & 3) == 0 && j0 + u < c1) atomicMax(reinterpret_cast<int*>(cmx + j0 + u), __float_as_int(w1));
     }
   }
   if (rmx && r < mt) atomicMax(reinterpret_cast<int*>(rmx + r), __float_as_int(rm));
