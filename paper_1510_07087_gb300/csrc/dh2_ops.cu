@@ -54,6 +54,45 @@ __device__ __forceinline__ const C2<T>* xbasis(const SideView<T>& S, int pid) {
 }
 
 // ---------------------------------------------------------------- norms / nearfield
+// acc + |g|^2 with a fixed rounding sequence (no contraction left to the
+// compiler), so that every kernel summing a piece gets the same bits
+__device__ __forceinline__ float sq_add(float acc, C2<float> g) {
+  return __fadd_rn(acc, __fmaf_rn(g.re, g.re, __fmul_rn(g.im, g.im)));
+}
+__device__ __forceinline__ double sq_add(double acc, C2<double> g) {
+  return __dadd_rn(acc, __fma_rn(g.re, g.re, __dmul_rn(g.im, g.im)));
+}
+
+// |G_b|_F^2 of an admissible block as the admissible blocks' pass forms it:
+// pieces of 32 rows by kNormCols columns in slab-major order, each a warp sum
+// (in double) of per-lane sums over the piece's columns in order, added in
+// piece order; one warp.
+template <typename T>
+__device__ double block_norm2_pieces(const NormsArgs<T>& a, int b, int64_t t0, int64_t s0, int mt, int ms, int lane) {
+  double tot = 0.0;
+  for (int sl = 0; sl * 32 < mt; ++sl) {
+    const int r = sl * 32 + lane;
+    for (int c0 = 0; c0 < ms; c0 += kNormCols) {
+      const int c1 = min(ms, c0 + kNormCols);
+      T acc = T(0);
+      for (int j0 = c0; j0 < c1; j0 += 8) {
+        C2<T> g[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          g[u] = czero<T>();
+          if (r < mt && j0 + u < c1) {
+            const int64_t gi = (s0 + j0 + u) * a.ld + t0 + r;
+            if (DH2_IN(gi, c_lim.G, 20, b)) g[u] = a.G[gi];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = sq_add(acc, g[u]);
+      }
+      tot += warp_sum((double)acc);
+    }
+  }
+  return tot;
+}
 // One warp per block of the block tree: |G_b|_F for an admissible block
 // (weight omega_b = |G_b|_F zeta^-level(t), Remark "Error control"); a copy of
 // G_b into the nearfield buffer for an inadmissible one.  Each warp walks the
@@ -103,7 +142,6 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
     // is a warp reduction, merged over the row slabs by lane 0.
     float* rmx = a.bmax + a.bmax_off[b];
     float* cmx = rmx + mt;
-    T acc = T(0);
     for (int rs = 0; rs < mt; rs += 32) {
       const int r = rs + lane;
       float rm = 0.f;
@@ -119,7 +157,6 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          acc += g[u].re * g[u].re + g[u].im * g[u].im;
           float v = fmaxf(fabsf((float)g[u].re), fabsf((float)g[u].im));
           rm = fmaxf(rm, v);
 #pragma unroll
@@ -135,33 +172,12 @@ __global__ void __launch_bounds__(256) norms_near_kernel(const NormsArgs<T>* __r
       }
       if (r < mt) rmx[r] = rm;
     }
-    const double tot = warp_sum((double)acc);
+    const double tot = block_norm2_pieces(a, b, t0, s0, mt, ms, lane);
     if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
       a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
     if (lane == 0 && a.bnorm2) a.bnorm2[b] = tot;
   } else if (a.badm[b]) {
-    T acc[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] = T(0);
-    for (int e0 = 0; e0 < total; e0 += 256) {
-      C2<T> g[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + lane + 32 * u;
-        g[u] = czero<T>();
-        if (e < total) {
-          const int r = e % mt, j = e / mt;
-          const int64_t gi = (s0 + j) * a.ld + t0 + r;
-          if (DH2_IN(gi, c_lim.G, 20, b)) g[u] = a.G[gi];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] += g[u].re * g[u].re + g[u].im * g[u].im;
-    }
-    double tot = 0.0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) tot += (double)acc[u];
-    tot = warp_sum(tot);
+    const double tot = block_norm2_pieces(a, b, t0, s0, mt, ms, lane);
     if (lane == 0 && DH2_IN(b, c_lim.nblocks, 23, b))
       a.invw[b] = tot > 0.0 ? 1.0 / (sqrt(tot) * a.zpow[a.clevel[t]]) : 1.0;
     if (lane == 0 && a.bnorm2) a.bnorm2[b] = tot;
@@ -751,7 +767,7 @@ __global__ void __launch_bounds__(256) norms_adm_kernel(const NormsArgs<T>* __re
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      acc += g[u].re * g[u].re + g[u].im * g[u].im;
+      acc = sq_add(acc, g[u]);
       v[u] = fmaxf(fabsf((float)g[u].re), fabsf((float)g[u].im));
       rm = fmaxf(rm, v[u]);
     }
