@@ -510,7 +510,12 @@ def run_gpu(args):
         Tp = D.dh2_tree_build(pts, args.leaf, args.kappa, 20.0, 5.0)
         Pp = pts[Tp.perm()]
         Gp = workload_matrix(args, Pp, None, h, cdt, dev)
+        tuning_p = None
+        headline_table = D.tuning()
+        if not args.no_autotune:  # this problem's own launch choices (the level steps' segment width above all)
+            tuning_p, _ = D.autotune(Tp, Gp, eps=args.eps, mode=mode, nearfield=args.nearfield, reps=1)
         msp, php, spp, Mp = _timed_compress(D, Tp, Gp, mode, args, 3, 2)
+        D.set_tuning(headline_table)
         rp = [Mp.ranks(0), Mp.ranks(1)]
         errp = None
         if not args.skip_error:
@@ -523,7 +528,7 @@ def run_gpu(args):
             "adm_fraction": Tp.stats().adm_fraction, "rel_err_vs_fp64": errp,
             "k_max": int(max(rp[0].max(initial=0), rp[1].max(initial=0))),
             "phases_ms": [float(v) for v in php], "leaf_split_ms": [float(v) for v in spp], "steps": 3, "warmup": 2,
-            "step_roofline_frac": in_bytes / (_peaks()[0]["hbm_gbs"] * 1e9) * 1e3 / msp}
+            "step_roofline_frac": in_bytes / (_peaks()[0]["hbm_gbs"] * 1e9) * 1e3 / msp, "tuning": tuning_p}
         del Mp
     peaks, src = _peaks()
     adm_bytes = elem * st.adm_fraction * args.n * args.n

@@ -289,6 +289,13 @@ void dh2_plan_free(dh2_plan* P);
  *                    slices, FP32 accumulation), 0 = on the FP32 pipes
  *                    (default, measured faster).  The two agree to FP32
  *                    rounding.
+ *  level_seg_cols  : non-leaf pairs with more than 2 x level_seg_cols
+ *                    columns are factored in column segments of that width
+ *                    (each segment's LQ factor L_i by its own CTA, then the
+ *                    pair's factor from [L_1 ... L_S], which has the same
+ *                    singular values and left singular vectors); 0 = never
+ *                    split, else a multiple of 64 from 256 to 8192 (default
+ *                    1024).  Changes the rounding only.
  * dh2_tuning_set returns DH2_EINVAL (table unchanged) for a value outside
  * these sets. */
 typedef struct {
@@ -296,14 +303,14 @@ typedef struct {
   int32_t jacobi_narrow[4];
   int32_t rq_ctas_per_sm;
   int32_t rq_tensor;
-  int32_t reserved;
+  int32_t level_seg_cols;
 } dh2_tuning;
 dh2_status dh2_tuning_get(dh2_tuning* out);
 dh2_status dh2_tuning_set(const dh2_tuning* tuning);
 /* One timed candidate of dh2_autotune: knob 0 = rq_ctas_per_sm, 1 =
- * jacobi_narrow[cls], 2 = jacobi_tpp[cls], 3 = rq_tensor; ms = median device
- * time of the phase the knob acts on (leaf R, or leaf factors) over the
- * repetitions. */
+ * jacobi_narrow[cls], 2 = jacobi_tpp[cls], 3 = rq_tensor, 4 = level_seg_cols;
+ * ms = median device time of the phase the knob acts on (leaf R, level
+ * steps, or leaf factors) over the repetitions. */
 typedef struct {
   int32_t knob;
   int32_t cls;
@@ -312,7 +319,8 @@ typedef struct {
 } dh2_tune_record;
 /* Autotune the table on one problem: compresses (tree, G) with `params`
  * under each candidate of each knob in turn (coordinate descent: in the
- * mixed mode the R kernel, then the R grid, then per factor class the
+ * mixed mode the R kernel, then the R grid, the level steps' segment width
+ * (if a non-leaf pair has more than 1024 columns), then per factor class the
  * Jacobi launch width and the threads per column pair; a
  * class with no pairs in the problem is skipped), `reps` calls per candidate
  * (1..15), keeps the fastest value of each knob, installs the result and

@@ -79,19 +79,20 @@ class TreeStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("jacobi_tpp", c_int32 * 5), ("jacobi_narrow", c_int32 * 4), ("rq_ctas_per_sm", c_int32),
-                ("rq_tensor", c_int32), ("reserved", c_int32)]
+                ("rq_tensor", c_int32), ("level_seg_cols", c_int32)]
 
 
 class TuneRecord(ctypes.Structure):
     _fields_ = [("knob", c_int32), ("cls", c_int32), ("value", c_int32), ("ms", ctypes.c_float)]
 
 
-TUNE_KNOBS = ("rq_ctas_per_sm", "jacobi_narrow", "jacobi_tpp", "rq_tensor")
+TUNE_KNOBS = ("rq_ctas_per_sm", "jacobi_narrow", "jacobi_tpp", "rq_tensor", "level_seg_cols")
 
 
 def _tuning_dict(t: Tuning) -> dict:
     return {"jacobi_tpp": list(t.jacobi_tpp), "jacobi_narrow": list(t.jacobi_narrow),
-            "rq_ctas_per_sm": int(t.rq_ctas_per_sm), "rq_tensor": int(t.rq_tensor)}
+            "rq_ctas_per_sm": int(t.rq_ctas_per_sm), "rq_tensor": int(t.rq_tensor),
+            "level_seg_cols": int(t.level_seg_cols)}
 
 
 class DH2Error(RuntimeError):
@@ -428,6 +429,7 @@ def set_tuning(d: dict) -> None:
         t.jacobi_narrow[c] = int(v)
     t.rq_ctas_per_sm = int(d["rq_ctas_per_sm"])
     t.rq_tensor = int(d.get("rq_tensor", 0))
+    t.level_seg_cols = int(d.get("level_seg_cols", 1024))
     _check(_lib().dh2_tuning_set(byref(t)), "dh2_tuning_set")
 
 

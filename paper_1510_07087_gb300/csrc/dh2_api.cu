@@ -39,7 +39,7 @@ inline int leaf_class(int m) { return m <= 32 ? 0 : m <= 40 ? 1 : m <= 48 ? 2 : 
 // The process's tuning table (dh2_tuning_set, dh2_autotune): read once by each
 // compression when it prepares its launches.
 std::mutex g_tune_mu;
-TuneTable g_tune = {{32, 32, 32, 32, 32}, {1, 1, 1, 1}, 0, 0};
+TuneTable g_tune = {{32, 32, 32, 32, 32}, {1, 1, 1, 1}, 0, 0, 1024};
 TuneTable tune_current() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   return g_tune;
@@ -51,7 +51,8 @@ bool tune_valid(const dh2_tuning& t) {
   }
   for (int c = 0; c < 4; ++c)
     if (t.jacobi_narrow[c] < 0 || t.jacobi_narrow[c] > 2) return false;
-  return t.rq_ctas_per_sm >= 0 && t.rq_ctas_per_sm <= 4 && (t.rq_tensor == 0 || t.rq_tensor == 1);
+  return t.rq_ctas_per_sm >= 0 && t.rq_ctas_per_sm <= 4 && (t.rq_tensor == 0 || t.rq_tensor == 1) &&
+         (t.level_seg_cols == 0 || (t.level_seg_cols >= 256 && t.level_seg_cols <= 8192 && t.level_seg_cols % 64 == 0));
 }
 TuneTable to_table(const dh2_tuning& t) {
   TuneTable x{};
@@ -59,6 +60,7 @@ TuneTable to_table(const dh2_tuning& t) {
   for (int c = 0; c < 4; ++c) x.jacobi_narrow[c] = t.jacobi_narrow[c];
   x.rq_ctas_per_sm = t.rq_ctas_per_sm;
   x.rq_tensor = t.rq_tensor;
+  x.level_seg_cols = t.level_seg_cols;
   return x;
 }
 dh2_tuning from_table(const TuneTable& x) {
@@ -67,6 +69,7 @@ dh2_tuning from_table(const TuneTable& x) {
   for (int c = 0; c < 4; ++c) t.jacobi_narrow[c] = x.jacobi_narrow[c];
   t.rq_ctas_per_sm = x.rq_ctas_per_sm;
   t.rq_tensor = x.rq_tensor;
+  t.level_seg_cols = x.level_seg_cols;
   return t;
 }
 
@@ -624,6 +627,9 @@ void fill_args(dh2_matrix* M, const dh2_compress_params& cp, PairArgs<T>& pa, No
   pa.max_sweeps = cp.max_sweeps > 0 ? cp.max_sweeps : 30;
   const TuneTable tt = tune_current();
   for (int c = 0; c < 5; ++c) pa.jacobi_tpp[c] = tt.jacobi_tpp[c];
+  pa.seg_off[0] = pa.seg_off[1] = nullptr;  // set by run_compress when wide pairs are split
+  pa.seg_buf = nullptr;
+  pa.seg_cols = 0;
   pa.status = M->status;
   pa.pts = M->pts;
   pa.nrm = M->nrm;
@@ -945,9 +951,42 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
   // the norms pass's partial sums, one per piece
   int64_t n_pieces_all = nprob > 1 ? (int64_t)pieces.size() : Ms[0]->tree->tr.dev->nnorm_pieces;
   const size_t part_bytes = align256(8 * (size_t)std::max<int64_t>(n_pieces_all, 1));
+  // non-leaf pairs wider than twice the tuning table's segment width are
+  // factored by column segments: per level the segment entries (code << 32 |
+  // segment), per problem and side each pair's slot in the segment buffer
+  // (p x p per segment, p at most the pair's row capacity)
+  const int seg_cols = tune_current().level_seg_cols;
+  std::vector<std::vector<uint64_t>> seg_lists(maxdepth + 1);
+  std::vector<std::vector<int64_t>> seg_off_h((size_t)nprob * 2);
+  int64_t seg_elems = 0;
+  if (seg_cols > 0)
+    for (int i = 0; i < nprob; ++i) {
+      const Tree& tr = Ms[i]->tree->tr;
+      const Tree::Dev* D = tr.dev;
+      for (int sd = 0; sd < 2; ++sd) {
+        std::vector<int64_t>& so = seg_off_h[(size_t)i * 2 + sd];
+        so.assign(tr.side[sd].pairs.size(), -1);
+        for (int l = tr.depth; l >= 0; --l)
+          for (int64_t p : tr.side[sd].nonleaf_by_level[l]) {
+            const int64_t nc = tr.side[sd].pairs[p].ncols;
+            if (nc <= 2 * (int64_t)seg_cols) continue;
+            const int64_t nseg = (nc + seg_cols - 1) / seg_cols, rc = D->rowcap_h[sd][p];
+            so[p] = seg_elems;
+            seg_elems += nseg * rc * rc;
+            const uint32_t code = ((uint32_t)i << kCodeProbShift) | ((uint32_t)sd << kCodeSideShift) | (uint32_t)p;
+            for (int64_t s = 0; s < nseg; ++s) seg_lists[l].push_back(((uint64_t)code << 32) | (uint64_t)s);
+          }
+      }
+    }
+  size_t seg_bytes = 0;
+  if (seg_elems > 0) {
+    seg_bytes += align256(sizeof(C2<T>) * (size_t)seg_elems);
+    for (const auto& v : seg_off_h) seg_bytes += align256(8 * std::max<size_t>(v.size(), 1));
+    for (const auto& v : seg_lists) seg_bytes += 5 * align256(8 * v.size()) + align256(16);  // list, 4 classes, counts
+  }
   void* scratch = nullptr;
   if (dev_malloc_async(&scratch, args_bytes + codes_bytes + cls_bytes + host_bytes + gram_bytes + ovr_bytes +
-                                     part_bytes + 256,
+                                     part_bytes + seg_bytes + 256,
                        st) != cudaSuccess) {
     cudaGetLastError();
     return DH2_ENOMEM;
@@ -966,6 +1005,37 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
         pas[0].rank_ovr[sd] = (const int32_t*)op;
         op += align256(4 * (size_t)np);
       }
+  }
+  // the segment buffer, slots, lists and class lists
+  std::vector<const uint64_t*> d_seg(maxdepth + 1, nullptr);
+  std::vector<uint64_t*> d_seg_cls(maxdepth + 1, nullptr);
+  std::vector<int*> d_seg_cnt(maxdepth + 1, nullptr);
+  if (seg_elems > 0) {
+    char* sp2 = (char*)d_partial + part_bytes;
+    C2<T>* seg_buf = (C2<T>*)sp2;
+    sp2 += align256(sizeof(C2<T>) * (size_t)seg_elems);
+    for (int i = 0; i < nprob; ++i) {
+      pas[i].seg_buf = seg_buf;
+      pas[i].seg_cols = seg_cols;
+      for (int sd = 0; sd < 2; ++sd) {
+        const std::vector<int64_t>& v = seg_off_h[(size_t)i * 2 + sd];
+        if (!v.empty() && ce_ovr == cudaSuccess)
+          ce_ovr = cudaMemcpyAsync(sp2, v.data(), 8 * v.size(), cudaMemcpyHostToDevice, st);
+        pas[i].seg_off[sd] = v.empty() ? nullptr : (const int64_t*)sp2;
+        sp2 += align256(8 * std::max<size_t>(v.size(), 1));
+      }
+    }
+    for (int l = 0; l <= maxdepth; ++l) {
+      const std::vector<uint64_t>& v = seg_lists[l];
+      if (!v.empty() && ce_ovr == cudaSuccess)
+        ce_ovr = cudaMemcpyAsync(sp2, v.data(), 8 * v.size(), cudaMemcpyHostToDevice, st);
+      d_seg[l] = (const uint64_t*)sp2;
+      sp2 += align256(8 * v.size());
+      d_seg_cls[l] = (uint64_t*)sp2;
+      sp2 += 4 * align256(8 * v.size());
+      d_seg_cnt[l] = (int*)sp2;
+      sp2 += align256(16);
+    }
   }
   GramArgs* d_ga = (GramArgs*)gram_base;
   std::vector<GramArgs> gas;
@@ -1124,6 +1194,7 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       lim.near = std::max<int64_t>(lim.near, M->nearfield_copy ? D->near_elems : 0);
       lim.nblocks = std::max<int64_t>(lim.nblocks, (int64_t)tr.blocks.size());
     }
+    lim.seg = seg_elems;
     cudaStreamSynchronize(st);
     check_set_limits_pair(lim);
     check_set_limits_ops(lim);
@@ -1361,6 +1432,22 @@ dh2_status run_compress(std::vector<dh2_matrix*>& Ms, const dh2_compress_params&
       launch_classify<T>(d_pa, d_nl[l], n, d_cls, d_cnt, st);
       counted(DH2_KC_CLASSIFY, true);
       const int Pc[4] = {32, 48, 64, P_level[l]};
+      // wide pairs: their column segments' factors first, by row class
+      const int nsg = (int)seg_lists[l].size();
+      if (nsg > 0) {
+        if (cudaMemsetAsync(d_seg_cnt[l], 0, 4 * sizeof(int), st) != cudaSuccess) {
+          cudaGetLastError();
+          ok_launch = false;
+        }
+        launch_classify_seg<T>(d_pa, d_seg[l], nsg, d_seg_cls[l], d_seg_cnt[l], st);
+        counted(DH2_KC_CLASSIFY, true);
+        for (int c = 0; c < 4; ++c) {
+          if (c > 0 && Pc[c - 1] >= P_level[l]) break;
+          ok_launch &= launch_pair_kernel<T>(d_pa, nullptr, nsg, std::min(Pc[c], std::max(P_level[l], 2)), true, st,
+                                             d_seg_cnt[l] + c, d_seg_cls[l] + (int64_t)c * nsg);
+          counted(DH2_KC_LEVEL_FACTOR + c, true);
+        }
+      }
       for (int c = 0; c < 4; ++c) {
         if (c > 0 && Pc[c - 1] >= P_level[l]) break;  // no pair of this level has more rows
         ok_launch &= launch_pair_kernel<T>(d_pa, d_cls + (int64_t)c * n, n, std::min(Pc[c], std::max(P_level[l], 2)),
@@ -2119,6 +2206,7 @@ dh2_status dh2_autotune(const dh2_tree* T, const void* G, dh2_dtype dtype, int64
       const dh2_status s = dh2_compress(T, G, dtype, ld, params, stream, &M);
       if (s != DH2_OK) return s;
       t.push_back(knob == 0 || knob == 3 ? M->phase_ms[2]
+                  : knob == 4            ? M->phase_ms[3]
                                          : (mixed ? M->leaf_split_ms[1] : M->phase_ms[1]) + M->phase_ms[3]);
       dh2_matrix_free(M);
     }
@@ -2137,7 +2225,8 @@ dh2_status dh2_autotune(const dh2_tree* T, const void* G, dh2_dtype dtype, int64
       int32_t* f = knob == 0   ? &x.rq_ctas_per_sm
                    : knob == 1 ? &x.jacobi_narrow[cls]
                    : knob == 2 ? &x.jacobi_tpp[cls]
-                               : &x.rq_tensor;
+                   : knob == 3 ? &x.rq_tensor
+                               : &x.level_seg_cols;
       *f = cand[i];
       float ms = 0.f;
       const dh2_status s = timed(x, knob, cls, cand[i], &ms);
@@ -2159,6 +2248,12 @@ dh2_status dh2_autotune(const dh2_tree* T, const void* G, dh2_dtype dtype, int64
   static const int kRq[3] = {0, 1, 2}, kNarrow[3] = {0, 1, 2}, kTpp[3] = {32, 16, 8}, kTensor[2] = {0, 1};
   if (s == DH2_OK && mixed) s = descend(3, 0, kTensor, 2, &best.rq_tensor);
   if (s == DH2_OK) s = descend(0, 0, kRq, 3, &best.rq_ctas_per_sm);
+  // the level steps' column segments, if the problem has non-leaf pairs wide enough to split
+  bool wide = false;
+  for (int sd = 0; sd < 2; ++sd)
+    for (const Pair& P : T->tr.side[sd].pairs) wide = wide || (!P.leaf && P.ncols > 2 * 512);
+  static const int kSeg[4] = {1024, 0, 512, 2048};
+  if (s == DH2_OK && wide) s = descend(4, 0, kSeg, 4, &best.level_seg_cols);
   for (int c = 0; c < 5 && s == DH2_OK; ++c) {
     if (!has[c]) continue;
     if (mixed && c < 4) s = descend(1, c, kNarrow, 3, &best.jacobi_narrow[c]);

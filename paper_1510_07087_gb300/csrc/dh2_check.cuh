@@ -8,7 +8,7 @@
 namespace dh2 {
 
 struct CheckLimits {
-  int64_t G, R[2], Q[2], X[2], S, near, nblocks, npairs[2], ncol[2];
+  int64_t G, R[2], Q[2], X[2], S, near, nblocks, npairs[2], ncol[2], seg;
 };
 
 struct CheckRecord {

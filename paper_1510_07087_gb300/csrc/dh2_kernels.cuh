@@ -21,6 +21,7 @@ struct TuneTable {
   int32_t jacobi_narrow[4];  // mixed mode leaf classes: Jacobi CTAs of ~4 (0), ~2 (1) or ~1 (2) x rows threads
   int32_t rq_ctas_per_sm;    // leaf R kernel: resident CTAs per SM (0: its occupancy limit)
   int32_t rq_tensor;         // mixed mode: leaf R on the tensor cores (1) or the FP32 pipes (0)
+  int32_t level_seg_cols;    // non-leaf pairs wider than twice this: factored by column segments (0: never)
 };
 TuneTable tune_current();
 // factor class of a pair kernel compiled for P_T rows
@@ -58,6 +59,12 @@ struct PairArgs {
   const int32_t* rank_ovr[2];         // per pair a rank replacing the truncation rule (< 0: the rule), or NULL
   int32_t max_sweeps;
   int32_t jacobi_tpp[5];              // per factor class: most threads per Jacobi column pair (TuneTable)
+  // non-leaf pairs factored by column segments: per pair the first entry of
+  // its segments' factors in seg_buf (p x p each, ld p, one after the other),
+  // -1 if not split; seg_cols columns per segment
+  const int64_t* seg_off[2];
+  C2<T>* seg_buf;
+  int32_t seg_cols;
   uint32_t* status;
   // matrix-free mode: entries generated from points (permuted order, 3 doubles
   // each) and, for the double layer, their normals (NULL for the single layer)
@@ -115,10 +122,13 @@ __device__ __forceinline__ C2<T> kernel_entry(const double* pts, const double* n
 // `count` (device int) the launch is sized at capacity nblocks and CTAs at or
 // past *count return at once, so a list whose length is known only on the
 // device needs no read-back.  Returns false, launching nothing, if the shared
-// memory the launch needs exceeds the device's per-block limit.
+// memory the launch needs exceeds the device's per-block limit.  With `segs`
+// (non-leaf pairs only; codes unused) each CTA takes an entry code << 32 |
+// segment and forms that column segment's LQ factor into the pair's slot of
+// the segment buffer.
 template <typename T>
 bool launch_pair_kernel(const PairArgs<T>* args_dev, const uint32_t* codes, int nblocks, int P, bool from_r,
-                        cudaStream_t st, const int* count = nullptr);
+                        cudaStream_t st, const int* count = nullptr, const uint64_t* segs = nullptr);
 
 // The leaf factorisation of the mixed modes: the pair kernel with steps 1
 // and 1b replaced by the pivoted Cholesky of the leaf's Gram matrix H
@@ -139,6 +149,10 @@ bool launch_rq_kernel(const PairArgs<T>* args_dev, const uint64_t* tiles, int nt
 template <typename T>
 void launch_classify(const PairArgs<T>* args_dev, const uint32_t* codes, int n, uint32_t* out, int* counts,
                      cudaStream_t st);
+// the same for segment entries (code << 32 | segment)
+template <typename T>
+void launch_classify_seg(const PairArgs<T>* args_dev, const uint64_t* segs, int n, uint64_t* out, int* counts,
+                         cudaStream_t st);
 
 // Arguments of the leaf Gram kernel of the mixed modes (one per problem).
 // Index [side] selects the row (0) or column (1) basis.

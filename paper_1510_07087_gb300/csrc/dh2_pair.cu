@@ -187,6 +187,7 @@ struct Source {
   const C2<T>* R1;
   int64_t roff0, roff1;
   int k1, off0, off1, ld0, ld1;
+  bool segsrc = false;  // R0 is the segments' factors [L_1 ... L_S] (bounds of the segment buffer)
 
   // leaf: global column index and weight 1/omega_b of column j of F_tc
   __device__ __forceinline__ void colinfo(int j, int& gc, T& w) const {
@@ -207,7 +208,7 @@ struct Source {
   __device__ __forceinline__ const C2<T>* sons_ptr(int r, int j) const {
     if (r < k1) {
       const int64_t e = (int64_t)(off0 + j) * ld0 + r;
-      if (!DH2_IN(roff0 + e, c_lim.R[side], 1, pid)) return nullptr;
+      if (!DH2_IN(roff0 + e, segsrc ? c_lim.seg : c_lim.R[side], 1, pid)) return nullptr;
       return R0 + e;
     }
     const int64_t e = (int64_t)(off1 + j) * ld1 + (r - k1);
@@ -238,7 +239,7 @@ struct Source {
     if (FROM_R) {
       if (r < k1) {
         const int64_t e = (int64_t)(off0 + j) * ld0 + r;
-        if (!DH2_IN(roff0 + e, c_lim.R[side], 1, pid)) return czero<T>();
+        if (!DH2_IN(roff0 + e, segsrc ? c_lim.seg : c_lim.R[side], 1, pid)) return czero<T>();
         return R0[e];
       }
       const int64_t e = (int64_t)(off1 + j) * ld1 + (r - k1);
@@ -760,7 +761,7 @@ constexpr int pair_min_blocks() {
 template <typename T, int P_T, bool FROM_R, int NT, bool GRAM = false>
 __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P,
-                const int* __restrict__ count) {
+                const int* __restrict__ count, const uint64_t* __restrict__ segs) {
   constexpr int LPR = NT / P_T;      // threads per row in the pivoted LQ (rows in place)
   constexpr int LQT = DH2_LQT;       // threads per row in the streamed LQ
   constexpr int GPW = 32 / LQT;      // rows per warp and per block of rows
@@ -802,13 +803,16 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (count && (int)blockIdx.x >= *count) return;  // launched at capacity: slots past the list's length
-  const uint32_t code = codes[blockIdx.x];
+  // segs: entries (code << 32 | segment) of non-leaf pairs factored by column
+  // segments; this CTA forms one segment's LQ factor only
+  const uint32_t code = segs ? (uint32_t)(segs[blockIdx.x] >> 32) : codes[blockIdx.x];
+  const int seg = segs ? (int)(uint32_t)segs[blockIdx.x] : -1;
   const int prob = (int)(code >> kCodeProbShift);
   const int side = (int)((code >> kCodeSideShift) & 1u);
   const int pid = (int)(code & kCodePairMask);
   const PairArgs<T>& a = args[prob];
   if (!DH2_IN(pid, c_lim.npairs[side], 9, pid)) return;
-  const int N = a.ncols[side][pid];
+  int N = a.ncols[side][pid];
   const int kcap = a.kcap[side][pid];
   const int lvl = a.level[side][pid];
 
@@ -842,6 +846,35 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     src.kappa = a.kappa;
     src.diag = a.diag;
     src.gen = a.gen;
+  }
+  // column segments of a wide non-leaf pair (Section 6's Ghat_tc = [L_1 Q_1,
+  // ..., L_S Q_S] has the singular values and left singular vectors of
+  // [L_1 ... L_S]): a segment CTA factors its columns; the pair's own CTA
+  // then factors the segments' factors instead of Ghat_tc
+  C2<T>* seg_out = nullptr;
+  if (FROM_R) {
+    const int64_t so = a.seg_off[side] ? a.seg_off[side][pid] : -1;
+    if (seg >= 0) {
+      if (so < 0 || p > P || p > P_T || p == 0) return;  // reported by the pair's own CTA
+      const int c0 = seg * a.seg_cols;
+      N = min(a.seg_cols, N - c0);
+      src.off0 += c0;
+      src.off1 += c0;
+      seg_out = a.seg_buf + so + (int64_t)seg * p * p;
+      if (N <= 0) {
+        for (int i = tid; i < p * p; i += NT) seg_out[i] = czero<T>();
+        return;
+      }
+    } else if (so >= 0 && p > 0) {
+      const int nseg = (N + a.seg_cols - 1) / a.seg_cols;
+      src.R0 = a.seg_buf + so;
+      src.roff0 = so;
+      src.k1 = p;
+      src.ld0 = p;
+      src.off0 = 0;
+      src.segsrc = true;
+      N = nseg * p;
+    }
   }
   int32_t* rank_out = a.rank[side] + pid;
   double* sig_out = a.sig[side] + (int64_t)pid * kSigStride;
@@ -1141,6 +1174,11 @@ __global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
     atomicAdd(&g_prof[16], (unsigned long long)pq_c);
   }
 #endif
+
+  if (seg_out) {  // a segment: its factor L (p x p, ld p) for the pair's CTA
+    for (int i = tid; i < p * p; i += NT) seg_out[i] = Lm[(i / p) * LDL + i % p];
+    return;
+  }
 
   // ---------------------------------------------------------------- 1b. pivoted LQ of L
   // Rank-revealing step: L Omega' = L' by Householder reflections from the
@@ -1690,7 +1728,7 @@ bool set_smem(K kern, size_t smem) {
 
 template <typename T, int P_T, bool FROM_R, int NT, bool GRAM = false>
 bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, cudaStream_t st,
-                const int* count = nullptr) {
+                const int* count = nullptr, const uint64_t* segs = nullptr) {
   constexpr int C = 16 * (NT / P_T);
   constexpr int XTRA = GRAM ? 0 : C;
   const int LDL = P + 1;
@@ -1705,7 +1743,7 @@ bool launch_one(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int
     if (solo[0] == '1' && smem < 120 * 1024) smem = 120 * 1024;
 #endif
   if (!set_smem(kern, smem)) return false;
-  kern<<<nblocks, NT, smem, st>>>(args, codes, P, count);
+  kern<<<nblocks, NT, smem, st>>>(args, codes, P, count, segs);
   return true;
 }
 
@@ -1765,6 +1803,22 @@ __global__ void classify_kernel(const PairArgs<T>* __restrict__ args, const uint
   out[(int64_t)cls * n + atomicAdd(&counts[cls], 1)] = code;
 }
 
+// the same classes for the segment entries (code << 32 | segment) of wide pairs
+template <typename T>
+__global__ void classify_seg_kernel(const PairArgs<T>* __restrict__ args, const uint64_t* __restrict__ segs, int n,
+                                    uint64_t* __restrict__ out, int* __restrict__ counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t e = segs[i];
+  const uint32_t code = (uint32_t)(e >> 32);
+  const PairArgs<T>& a = args[code >> kCodeProbShift];
+  const int side = (int)((code >> kCodeSideShift) & 1u);
+  const int pid = (int)(code & kCodePairMask);
+  const int p = a.rank[side][a.son[side][2 * pid]] + a.rank[side][a.son[side][2 * pid + 1]];
+  const int cls = p <= 32 ? 0 : p <= 48 ? 1 : p <= 64 ? 2 : 3;
+  out[(int64_t)cls * n + atomicAdd(&counts[cls], 1)] = e;
+}
+
 template <typename T, bool FROM_R>
 bool launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
   const size_t smem = (size_t)(32 + 2 + kRTile + 2) * P * sizeof(C2<T>);  // row-major Q block and A tile
@@ -1804,6 +1858,14 @@ void launch_classify(const PairArgs<T>* args, const uint32_t* codes, int n, uint
                      cudaStream_t st) {
   if (n > 0) classify_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(args, codes, n, out, counts);
 }
+template <typename T>
+void launch_classify_seg(const PairArgs<T>* args, const uint64_t* segs, int n, uint64_t* out, int* counts,
+                         cudaStream_t st) {
+  if (n > 0) classify_seg_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(args, segs, n, out, counts);
+}
+template void launch_classify_seg<float>(const PairArgs<float>*, const uint64_t*, int, uint64_t*, int*, cudaStream_t);
+template void launch_classify_seg<double>(const PairArgs<double>*, const uint64_t*, int, uint64_t*, int*,
+                                          cudaStream_t);
 template void launch_classify<float>(const PairArgs<float>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
 template void launch_classify<double>(const PairArgs<double>*, const uint32_t*, int, uint32_t*, int*, cudaStream_t);
 
@@ -1812,7 +1874,7 @@ template bool launch_rq_kernel<double>(const PairArgs<double>*, const uint64_t*,
 
 template <typename T>
 bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblocks, int P, bool from_r,
-                        cudaStream_t st, const int* count) {
+                        cudaStream_t st, const int* count, const uint64_t* segs) {
   if (nblocks <= 0) return true;
   if (!from_r) {
     if (P <= 32) return launch_one<T, 32, false, 128>(args, codes, nblocks, P, st, count);
@@ -1821,10 +1883,10 @@ bool launch_pair_kernel(const PairArgs<T>* args, const uint32_t* codes, int nblo
     if (P <= 64) return launch_one<T, 64, false, 256>(args, codes, nblocks, P, st, count);
     return launch_one<T, 128, false, 256>(args, codes, nblocks, P, st, count);
   }
-  if (P <= 32) return launch_one<T, 32, true, 128>(args, codes, nblocks, P, st, count);
-  if (P <= 48) return launch_one<T, 48, true, 192>(args, codes, nblocks, P, st, count);
-  if (P <= 64) return launch_one<T, 64, true, 256>(args, codes, nblocks, P, st, count);
-  return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st, count);
+  if (P <= 32) return launch_one<T, 32, true, 128>(args, codes, nblocks, P, st, count, segs);
+  if (P <= 48) return launch_one<T, 48, true, 192>(args, codes, nblocks, P, st, count, segs);
+  if (P <= 64) return launch_one<T, 64, true, 256>(args, codes, nblocks, P, st, count, segs);
+  return launch_one<T, 128, true, 256>(args, codes, nblocks, P, st, count, segs);
 }
 
 // The Jacobi launch of a class: NT = 4 x rows threads per CTA, or (the
@@ -1867,8 +1929,8 @@ bool launch_pair_kernel_gram(const PairArgs<float>* args, const uint32_t* codes,
 }
 
 template bool launch_pair_kernel<float>(const PairArgs<float>*, const uint32_t*, int, int, bool, cudaStream_t,
-                                        const int*);
+                                        const int*, const uint64_t*);
 template bool launch_pair_kernel<double>(const PairArgs<double>*, const uint32_t*, int, int, bool, cudaStream_t,
-                                         const int*);
+                                         const int*, const uint64_t*);
 
 }  // namespace dh2

@@ -119,3 +119,32 @@ def test_tensor_core_r_agrees_with_the_fp32_pipes():
             assert np.linalg.norm(a - b) <= 1e-4 * np.linalg.norm(a)
             checked += 1
     assert checked >= len(sample) // 2
+
+
+@pytest.mark.parametrize("kind", ["fp64", "mixed"])
+def test_wide_level_pairs_by_column_segments(kind):
+    """Non-leaf pairs wider than twice level_seg_cols are factored by column segments (each
+    segment's LQ factor L_i, then the pair's factor from [L_1 ... L_S]): with segments of 256
+    columns the paper's parameters (eta1 = 20, eta2 = 5) split pairs on several levels, and the
+    FP64 mode still meets the FP64 parity criteria against the oracle (ranks outside ties,
+    products to 1e-11), the mixed mode its reduced-precision ones."""
+    D = dev()
+    t = D.tuning()
+    t["level_seg_cols"] = 0
+    D.set_tuning(t)
+    mode = D.MODE_FP64 if kind == "fp64" else D.MODE_MIXED_BF16X3
+    n, kappa, leaf = (2048, 8.0, 16) if kind == "fp64" else (4096, 12.0, 32)
+    c = Case(n, kappa, leaf, 1e-4, mode, eta1=20.0, eta2=5.0, compress=False)
+    plain = D.dh2_compress(c.T, c.Gd, eps=1e-4, mode=mode).class_launches()
+    t["level_seg_cols"] = 256
+    D.set_tuning(t)
+    M = D.dh2_compress(c.T, c.Gd, eps=1e-4, mode=mode)
+    split = M.class_launches()
+    assert split[D.KC_CLASSIFY] > plain[D.KC_CLASSIFY]  # levels with segment launches
+    pr = [c.T.pairs(s) for s in (0, 1)]
+    assert max(int(p["ncols"][~p["leaf"].astype(bool)].max(initial=0)) for p in pr) > 512
+    c.attach(M)
+    if kind == "fp64":
+        check_fp64(c)
+    else:
+        check_reduced(c, max_bad_frac=0.01, max_diff=1)

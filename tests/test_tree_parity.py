@@ -111,18 +111,20 @@ def test_invalid_arguments_rejected():
 def test_tuning_table_set_get_and_validation():
     """dh2_tuning_set installs a table that dh2_tuning_get returns; a value outside a knob's set
     (a Jacobi width that is not a power of two up to 32, a narrow choice outside 0..2, more than 4
-    R CTAs per SM, an R kernel choice other than 0/1) is refused with DH2_EINVAL and leaves the
+    R CTAs per SM, an R kernel choice other than 0/1, a segment width that is not 0 or a multiple of
+    64 in 256..8192) is refused with DH2_EINVAL and leaves the
     table as it was; dh2_autotune checks its arguments before any device work."""
     b = _lib_or_skip()
     saved = b.tuning()
     try:
         t = {"jacobi_tpp": [32, 16, 8, 4, 32], "jacobi_narrow": [1, 0, 1, 0], "rq_ctas_per_sm": 2,
-             "rq_tensor": 0}
+             "rq_tensor": 0, "level_seg_cols": 512}
         b.set_tuning(t)
         assert b.tuning() == t
         for bad in ({"jacobi_tpp": [32, 12, 8, 4, 32]}, {"jacobi_tpp": [64, 16, 8, 4, 32]},
                     {"jacobi_narrow": [3, 0, 0, 0]}, {"rq_ctas_per_sm": 5}, {"rq_ctas_per_sm": -1},
-                    {"rq_tensor": 2}):
+                    {"rq_tensor": 2}, {"level_seg_cols": 100}, {"level_seg_cols": 1000},
+                    {"level_seg_cols": 16384}):
             with pytest.raises(b.DH2Error) as ei:
                 b.set_tuning({**t, **bad})
             assert ei.value.status == 1
