@@ -754,16 +754,21 @@ __global__ void __launch_bounds__(256) norms_adm_kernel(const NormsArgs<T>* __re
   float* cmx = rmx ? rmx + mt : nullptr;
   T acc = T(0);
   float rm = 0.f;
-  for (int j0 = c0; j0 < c1; j0 += 8) {
-    C2<T> g[8];
+  // 8 columns at a time, the next 8 in flight while these are summed
+  auto load8 = [&](int j0, C2<T> (&d)[8]) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      g[u] = czero<T>();
+      d[u] = czero<T>();
       if (r < mt && j0 + u < c1) {
         const int64_t gi = (s0 + j0 + u) * a.ld + t0 + r;
-        if (DH2_IN(gi, c_lim.G, 24, b)) g[u] = a.G[gi];
+        if (DH2_IN(gi, c_lim.G, 24, b)) d[u] = a.G[gi];
       }
     }
+  };
+  C2<T> g[8], gn[8];
+  load8(c0, g);
+  for (int j0 = c0; j0 < c1; j0 += 8) {
+    if (j0 + 8 < c1) load8(j0 + 8, gn);
     float v[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -793,6 +798,8 @@ __global__ void __launch_bounds__(256) norms_adm_kernel(const NormsArgs<T>* __re
       const int u = (int)b4 * 4 + (int)b3 * 2 + (int)b2;
       if ((lane & 3) == 0 && j0 + u < c1) atomicMax(reinterpret_cast<int*>(cmx + j0 + u), __float_as_int(w1));
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) g[u] = gn[u];
   }
   if (rmx && r < mt) atomicMax(reinterpret_cast<int*>(rmx + r), __float_as_int(rm));
   const double tot = warp_sum((double)acc);
