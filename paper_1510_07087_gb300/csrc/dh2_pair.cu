@@ -1590,7 +1590,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
     rq_leaf_kernel(const PairArgs<T>* __restrict__ args, const uint64_t* __restrict__ tiles, const int64_t ntiles,
                    const int P) {
   constexpr int NT = 128;
-  constexpr int QB = 32;
+  constexpr int QB = 16;  // ranks per pass (leaf ranks are mostly below 16): a smaller Q stage, more CTAs per SM
   constexpr int TW = kRTile;
   constexpr int LQ = QB + 2, LA = TW + 2;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1830,7 +1830,7 @@ bool launch_rq(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P
 
 template <typename T>
 bool launch_rq_leaf(const PairArgs<T>* args, const uint64_t* tiles, int ntiles, int P, cudaStream_t st) {
-  constexpr int QB = 32, LQ = QB + 2, LA = kRTile + 2;
+  constexpr int QB = 16, LQ = QB + 2, LA = kRTile + 2;
   const size_t smem = 2 * (size_t)(LQ + LA) * P * sizeof(C2<T>);  // two stages of Q block and A tile
   auto kern = rq_leaf_kernel<T>;
   if (!set_smem(kern, smem)) return false;
