@@ -24,6 +24,7 @@
 // recursion) for all pairs of the launch at once.
 #include <cfloat>
 #include <cstdlib>
+#include <type_traits>
 
 #include "dh2_check.cuh"
 #include "dh2_internal.h"
@@ -78,6 +79,17 @@ __device__ __forceinline__ C2<T> cmacc(C2<T> acc, C2<T> a, C2<T> b) {
   acc.re = fma(a.im, b.im, acc.re);
   acc.im = fma(a.im, b.re, acc.im);
   acc.im = fma(-a.re, b.im, acc.im);
+  return acc;
+}
+// acc + a b, with the same fused multiply-adds in the same order as
+// cmacc(acc, a, conj(b)) (the negations are exact), so either form of a
+// product gives the same bits
+template <typename T>
+__device__ __forceinline__ C2<T> cmac_nc(C2<T> acc, C2<T> a, C2<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.im, b.re, acc.im);
+  acc.im = fma(a.re, b.im, acc.im);
   return acc;
 }
 template <typename T>
@@ -749,6 +761,26 @@ __device__ __forceinline__ void jacobi_rank_q(const PairArgs<T>& a, int side, in
   DH2_PROF_ADD(2, t_d - t_c);
 }
 
+// CTAs per SM of the pivoted Cholesky of a Gram matrix (pair_kernel with
+// GRAM): its shared memory is H alone (P x P double-float complex), so the
+// register file sets the limit for the classes up to 48 rows.  8 / 7 / 5 CTAs
+// (64 / 56 / 64 registers, no spills) against the 6 / 5 / 4 of the LQ pair
+// kernel: the Cholesky waits on a barrier per pivot step, and more pairs per
+// SM fill those waits (measured: factor phase 4.50 -> 4.19 ms at n = 32768)
+#ifndef DH2_GRAM_MINB128
+#define DH2_GRAM_MINB128 8
+#endif
+#ifndef DH2_GRAM_MINB160
+#define DH2_GRAM_MINB160 7
+#endif
+#ifndef DH2_GRAM_MINB192
+#define DH2_GRAM_MINB192 5
+#endif
+template <int NT>
+constexpr int gram_min_blocks() {
+  return NT >= 256 ? 3 : NT >= 192 ? DH2_GRAM_MINB192 : NT >= 160 ? DH2_GRAM_MINB160 : DH2_GRAM_MINB128;
+}
+
 template <int NT, typename T>
 constexpr int pair_min_blocks() {
   return sizeof(T) == 4 ? (NT >= 256   ? DH2_PAIR_MINB
@@ -759,7 +791,7 @@ constexpr int pair_min_blocks() {
 }
 
 template <typename T, int P_T, bool FROM_R, int NT, bool GRAM = false>
-__global__ void __launch_bounds__(NT, (pair_min_blocks<NT, T>()))
+__global__ void __launch_bounds__(NT, (GRAM ? gram_min_blocks<NT>() : pair_min_blocks<NT, T>()))
     pair_kernel(const PairArgs<T>* __restrict__ args, const uint32_t* __restrict__ codes, const int P,
                 const int* __restrict__ count, const uint64_t* __restrict__ segs) {
   constexpr int LPR = NT / P_T;      // threads per row in the pivoted LQ (rows in place)
@@ -1585,8 +1617,11 @@ __device__ __forceinline__ RqLeafTile<T> rq_leaf_tile(const PairArgs<T>* __restr
 // one before.  The weight 1/omega_b and the conjugation of G^* are applied to
 // the outputs: for the row basis R = w sum_r conj(Q) G, for the column basis
 // R = w conj(sum_r Q G') with G' the stored entries of G.
+#ifndef DH2_RQ_MINB
+#define DH2_RQ_MINB 3  // FP32 leaf R kernel: register cap for this many CTAs per SM
+#endif
 template <typename T>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? DH2_RQ_MINB : 2)
     rq_leaf_kernel(const PairArgs<T>* __restrict__ args, const uint64_t* __restrict__ tiles, const int64_t ntiles,
                    const int P) {
   constexpr int NT = 128;
@@ -1649,21 +1684,32 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 3 : 2)
     const T sg = x.side == 0 ? T(1) : T(-1);  // conj(Q) for the row basis, Q for the column basis
     for (int u = tid; u < nqt * njt; u += NT) {
       const int q0 = 2 * (u % nqt), jb = 2 * (u / nqt);
-      const C2<T>* qp = Qs + q0;
-      const C2<T>* ap = As + jb;
       C2<T> c00 = czero<T>(), c01 = czero<T>(), c10 = czero<T>(), c11 = czero<T>();
+      // the row loop once per basis (no sign multiply per entry of Q): the
+      // products with conj(Q) (row basis) or Q (column basis)
+      auto rows = [&](auto conj_q) {
+        const C2<T>* qp = Qs + q0;
+        const C2<T>* ap = As + jb;
 #pragma unroll 2
-      for (int r = 0; r < x.p; ++r, qp += LQ, ap += LA) {
-        C2<T> x0, x1, y0, y1;
-        load_c2x2(qp, x0, x1);
-        load_c2x2(ap, y0, y1);
-        x0.im *= sg;
-        x1.im *= sg;
-        c00 = cmacc(c00, y0, x0);
-        c01 = cmacc(c01, y1, x0);
-        c10 = cmacc(c10, y0, x1);
-        c11 = cmacc(c11, y1, x1);
-      }
+        for (int r = 0; r < x.p; ++r, qp += LQ, ap += LA) {
+          C2<T> x0, x1, y0, y1;
+          load_c2x2(qp, x0, x1);
+          load_c2x2(ap, y0, y1);
+          if constexpr (decltype(conj_q)::value) {
+            c00 = cmacc(c00, y0, x0);
+            c01 = cmacc(c01, y1, x0);
+            c10 = cmacc(c10, y0, x1);
+            c11 = cmacc(c11, y1, x1);
+          } else {
+            c00 = cmac_nc(c00, y0, x0);
+            c01 = cmac_nc(c01, y1, x0);
+            c10 = cmac_nc(c10, y0, x1);
+            c11 = cmac_nc(c11, y1, x1);
+          }
+        }
+      };
+      if (x.side == 0) rows(std::true_type{});
+      else rows(std::false_type{});
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
         const int qq = q0 + (d >> 1), jj = jb + (d & 1);
