@@ -50,7 +50,11 @@ FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # together) at n=32768, kappa=32, leaf 64, from an ncu capture summarised under
 # profiles/; valid only for the kernel sources it was measured on (sha1 of
 # csrc/dh2_gram.cu + csrc/dh2_pair.cu).
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    # gram_pipe_kernel<32>, <48> x2, gram_kernel<64>: one compression at n=32768 (ncu
+    # dram__bytes_read.sum 5865124864 + dram__bytes_write.sum 1023523072)
+    ("gram", "mixed"): {"sha1": "08165f8f3a8361e22036447170b4b073d3e7364a", "bytes": 6888647936},
+}
 
 
 def _peaks():
