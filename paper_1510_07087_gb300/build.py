@@ -41,9 +41,10 @@ def build(verbose: bool = False) -> str:
     extra = ["-DDH2_CHECK"] if os.environ.get("DH2_CHECK") == "1" else []
     if os.environ.get("DH2_PROFILE") == "1":
         extra.append("-DDH2_PROFILE")
-    # tuning macros of the pair kernel (defaults in csrc/dh2_pair.cu)
+    # build-time tuning macros (defaults in csrc/dh2_pair.cu and csrc/dh2_ops.cu)
     for name in ("DH2_PAIR_MINB", "DH2_PAIR_MINB192", "DH2_PAIR_MINB160", "DH2_PAIR_MINB128", "DH2_LQT", "DH2_HOST_PANELS",
-                 "DH2_GRAM_MINB128", "DH2_GRAM_MINB160", "DH2_GRAM_MINB192", "DH2_RQ_MINB"):
+                 "DH2_GRAM_MINB128", "DH2_GRAM_MINB160", "DH2_GRAM_MINB192", "DH2_RQ_MINB",
+                 "DH2_PROJ_MINB"):
         if os.environ.get(name):
             extra.append(f"-D{name}={int(os.environ[name])}")
     for src in CUDA_SOURCES:

@@ -255,8 +255,26 @@ __device__ __forceinline__ C2<T> cmac(C2<T> acc, C2<T> x, C2<T> y) {  // acc + x
   return acc;
 }
 
+namespace {
+// global -> shared copy of BYTES (4, 8 or 16; both addresses aligned to it)
+// without a register round trip, and the wait for this thread's copies
+template <int BYTES>
+__device__ __forceinline__ void proj_cp_async(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src),
+               "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void proj_cp_async_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+}  // namespace
+
+#ifndef DH2_PROJ_MINB
+#define DH2_PROJ_MINB 5  // FP32 projection: register cap for this many CTAs per SM (96 registers, no spills)
+#endif
 template <typename T>
-__global__ void __launch_bounds__(128) project_kernel(ProjArgs<T> a, int nadm) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? DH2_PROJ_MINB : 1) project_kernel(ProjArgs<T> a, int nadm) {
   constexpr int KS = 32;
   constexpr int JC = sizeof(T) == 4 ? 16 : 8;
   __shared__ C2<T> sR[4][KS * JC];  // R chunk: kt x jc, column-major, ld KS
@@ -296,17 +314,29 @@ __global__ void __launch_bounds__(128) project_kernel(ProjArgs<T> a, int nadm) {
       for (int j0 = 0; j0 < ms; j0 += JC) {
         const int jc = min(JC, ms - j0);
         __syncwarp();
-        if (lane < kt)
-          for (int jj = 0; jj < jc; ++jj) {
+        // the chunk's entries by asynchronous copies with fixed trip counts,
+        // all in flight together (one load latency per chunk, not one per
+        // entry): R rows q < kt (lane q) of columns j0 + jj, jj < jc; W rows
+        // j0 + jj (lane % JC) of columns c < ks
+#pragma unroll
+        for (int jj = 0; jj < JC; ++jj)
+          if (lane < kt && jj < jc) {
             const int64_t ri = lane + (int64_t)(j0 + jj) * ldr;
-            r_s[lane + jj * KS] = DH2_IN(rbase + ri, c_lim.R[0], 40, b) ? R[ri] : czero<T>();
+            if (DH2_IN(rbase + ri, c_lim.R[0], 40, b)) proj_cp_async<sizeof(C2<T>)>(r_s + lane + jj * KS, R + ri);
+            else r_s[lane + jj * KS] = czero<T>();
           }
-        for (int idx = lane; idx < jc * ks; idx += 32) {
-          const int jj = idx % jc, c = idx / jc;
-          const int64_t wi = (j0 + jj) + (int64_t)c * ms;
-          const bool ok = wleaf ? DH2_IN(wbase + wi, c_lim.Q[1], 41, b) : DH2_IN(wbase + wi, c_lim.X[1], 42, b);
-          w_s[jj + c * JC] = ok ? W[wi] : czero<T>();
+        constexpr int WU = KS * JC / 32;  // W entries per lane
+#pragma unroll
+        for (int u = 0; u < WU; ++u) {
+          const int jj = lane % JC, c = u * (32 / JC) + lane / JC;
+          if (jj < jc && c < ks) {
+            const int64_t wi = (j0 + jj) + (int64_t)c * ms;
+            const bool ok = wleaf ? DH2_IN(wbase + wi, c_lim.Q[1], 41, b) : DH2_IN(wbase + wi, c_lim.X[1], 42, b);
+            if (ok) proj_cp_async<sizeof(C2<T>)>(w_s + jj + c * JC, W + wi);
+            else w_s[jj + c * JC] = czero<T>();
+          }
         }
+        proj_cp_async_wait();
         __syncwarp();
         if (act)
           for (int jj = 0; jj < jc; ++jj) {
