@@ -21,6 +21,11 @@ LIB = os.path.join(HERE, "libdh2.so")
 HOST_SOURCES = ["dh2_tree.cpp"]
 CUDA_SOURCES = ["dh2_pair.cu", "dh2_gram.cu", "dh2_rq_tc.cu", "dh2_ops.cu", "dh2_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# build-time tuning macros, read from the environment (integers; the defaults,
+# the measured best, sit beside each #ifndef in csrc/)
+TUNING_MACROS = ("DH2_PAIR_MINB", "DH2_PAIR_MINB192", "DH2_PAIR_MINB160", "DH2_PAIR_MINB128", "DH2_LQT",
+                 "DH2_HOST_PANELS", "DH2_GRAM_MINB128", "DH2_GRAM_MINB160", "DH2_GRAM_MINB192", "DH2_RQ_MINB",
+                 "DH2_PROJ_MINB")
 
 
 def _nvcc() -> str:
@@ -41,10 +46,7 @@ def build(verbose: bool = False) -> str:
     extra = ["-DDH2_CHECK"] if os.environ.get("DH2_CHECK") == "1" else []
     if os.environ.get("DH2_PROFILE") == "1":
         extra.append("-DDH2_PROFILE")
-    # build-time tuning macros (defaults in csrc/dh2_pair.cu and csrc/dh2_ops.cu)
-    for name in ("DH2_PAIR_MINB", "DH2_PAIR_MINB192", "DH2_PAIR_MINB160", "DH2_PAIR_MINB128", "DH2_LQT", "DH2_HOST_PANELS",
-                 "DH2_GRAM_MINB128", "DH2_GRAM_MINB160", "DH2_GRAM_MINB192", "DH2_RQ_MINB",
-                 "DH2_PROJ_MINB"):
+    for name in TUNING_MACROS:
         if os.environ.get(name):
             extra.append(f"-D{name}={int(os.environ[name])}")
     for src in CUDA_SOURCES:

@@ -199,3 +199,17 @@ def test_host_input_panels(kind, n, kappa, leaf, eta1, eta2, rule):
                 assert row_panel[p] == (int(s_last[bl].max()) if len(bl) else 0)
             else:
                 assert row_panel[p] == -1
+
+
+def test_build_reads_every_tuning_macro():
+    """Every integer macro with a default behind an #ifndef in the CUDA and C++ sources is one the
+    build reads from the environment, and the build reads no other: a tuning choice cannot be set
+    by a name that the sources ignore, nor exist without a way to set it."""
+    from paper_1510_07087_gb300 import build as B
+    found = set()
+    for f in sorted(os.listdir(B.CSRC)):
+        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
+            src = open(os.path.join(B.CSRC, f)).read()
+            found |= set(re.findall(r"^#ifndef (DH2_\w+)\s*\n#define \1 -?\d+\b", src, re.M))
+    assert found, "no tuning macros parsed"
+    assert found == set(B.TUNING_MACROS)
