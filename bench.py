@@ -339,9 +339,58 @@ def _alg_flops(T, ranks):
     return fac, rq
 
 
-def _timed_compress(D, T, G, mode, args, steps, warmup, clk=None):
+def dist_init(world: int) -> None:
+    """Replicas under torchrun (one process per GPU, each compressing its own copy of the workload):
+    a process group for the barriers around the timed regions and the maximum over ranks of their
+    times; no collective on the data path (the problems are independent)."""
+    import torch
+    import torch.distributed as dist
+
+    if world > 1 and not dist.is_initialized():
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
+def _replicas() -> bool:
+    import torch.distributed as dist
+
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+
+
+def barrier() -> None:
+    """All ranks (a no-op on one process)."""
+    if _replicas():
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def replica_max(ms: float) -> float:
+    """The largest of the ranks' values (the timed region's milliseconds); the value itself on one
+    process."""
+    if not _replicas():
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    on_gpu = dist.get_backend() == "nccl"
+    t = torch.tensor([ms], dtype=torch.float64,
+                     device=torch.device("cuda", torch.cuda.current_device()) if on_gpu else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_replica: float, world: int, ms: float) -> float:
+    """Input GB/s of the whole job: every replica's bytes over the slowest replica's time."""
+    return world * bytes_per_replica / (ms * 1e-3) / 1e9
+
+
+def _timed_compress(D, T, G, mode, args, steps, warmup, clk=None, replicas=False):
     """Mean ms per dh2_compress over `steps` calls (CUDA events on the launching stream) and the
-    per-phase and leaf-split means from the library's own events; returns the last matrix too."""
+    per-phase and leaf-split means from the library's own events; returns the last matrix too.
+    With `replicas` the timed region is bracketed by barriers of all ranks and the time is the
+    largest over them."""
     import torch
 
     stream = torch.cuda.current_stream()
@@ -356,6 +405,8 @@ def _timed_compress(D, T, G, mode, args, steps, warmup, clk=None):
         clk.__enter__()
     try:
         torch.cuda.synchronize()
+        if replicas:
+            barrier()
         ev0.record(stream)
         for _ in range(steps):
             M = D.dh2_compress(T, G, eps=args.eps, mode=mode, nearfield=args.nearfield)
@@ -364,11 +415,16 @@ def _timed_compress(D, T, G, mode, args, steps, warmup, clk=None):
             del M
         ev1.record(stream)
         torch.cuda.synchronize()
+        if replicas:
+            barrier()
     finally:
         if clk is not None:
             clk.__exit__(None, None, None)
+    ms = ev0.elapsed_time(ev1) / steps
+    if replicas:
+        ms = replica_max(ms)
     M = D.dh2_compress(T, G, eps=args.eps, mode=mode, nearfield=args.nearfield)
-    return ev0.elapsed_time(ev1) / steps, phases / steps, split / steps, M
+    return ms, phases / steps, split / steps, M
 
 
 def _rank_hist(a, b):
@@ -383,8 +439,11 @@ def run_gpu(args):
     import paper_1510_07087_gb300 as D
     from synth import mean_nn_distance
 
-    dev = torch.device("cuda", 0)
+    # one GPU per rank (replicas under torchrun); cuda:0 on one process
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    lead = int(os.environ.get("RANK", "0")) == 0
     pts, nrm = workload_points(args)
     h = mean_nn_distance(pts)
     T = D.dh2_tree_build(pts, args.leaf, args.kappa, args.eta1, args.eta2)
@@ -406,7 +465,8 @@ def run_gpu(args):
         tuning = {"table": table, "candidates": log, "reps": 3,
                   "objective": "median device ms of the phase each knob acts on"}
     clk = ClockSampler(torch.cuda.current_device())
-    ms, phases, split, M = _timed_compress(D, T, Gd, mode, args, args.steps, args.warmup, clk)
+    ms, phases, split, M = _timed_compress(D, T, Gd, mode, args, args.steps, args.warmup, clk,
+                                           replicas=world > 1)
     ranks = [M.ranks(0), M.ranks(1)]
     storage = M.storage()
     # matrix-vector product with the compressed matrix (Section 4), one right-hand side
@@ -422,10 +482,10 @@ def run_gpu(args):
     m1.record(stream)
     torch.cuda.synchronize()
     matvec_ms = m0.elapsed_time(m1) / 10
-    # error against the FP64 matrix (complex128, built the same way)
+    # error against the FP64 matrix (complex128, built the same way); with replicas on rank 0 only
     rel_err = None
     secondary = {}
-    if args.mode != "fp64" and not args.skip_error:
+    if args.mode != "fp64" and not args.skip_error and lead:
         G128 = workload_matrix(args, P, Nrm, h, torch.complex128, dev)
         rel_err = D.dh2_error(M, G128)
         if not args.skip_secondary:
@@ -466,6 +526,8 @@ def run_gpu(args):
             for it in range(args.warmup + args.steps):
                 if it == args.warmup:
                     torch.cuda.synchronize()
+                    if world > 1:
+                        barrier()
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
@@ -476,7 +538,9 @@ def run_gpu(args):
                 del Me
             e1.record(stream)
             torch.cuda.synchronize()
-            return e0.elapsed_time(e1) / args.steps
+            if world > 1:
+                barrier()
+            return replica_max(e0.elapsed_time(e1) / args.steps) if world > 1 else e0.elapsed_time(e1) / args.steps
 
         seq = None
         if args.nearfield == 0:
@@ -496,17 +560,19 @@ def run_gpu(args):
 
         seq_ms = timed(copy_then_compress, "seq")
         h2d_ms = sum(a.elapsed_time(b) for a, b in h2d_ev) / len(h2d_ev)
-        seq = {"ms_per_step": seq_ms, "value": in_bytes / (seq_ms * 1e-3) / 1e9, "h2d_ms": h2d_ms,
+        seq = {"ms_per_step": seq_ms, "value": whole_job_gbs(in_bytes, world, seq_ms), "h2d_ms": h2d_ms,
                "h2d_gbs": in_bytes / (h2d_ms * 1e-3) / 1e9}
         if args.nearfield != 0:
             e2e_ms = seq_ms  # view mode: the host-input call copies into a buffer the matrix cannot keep
-        e2e = {"value": in_bytes / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": e2e_ms,
+        e2e = {"value": whole_job_gbs(in_bytes, world, e2e_ms), "unit": "GB/s", "ms_per_step": e2e_ms,
                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h,
                "api": "dh2_compress_host" if args.nearfield == 0 else "H2D copy + dh2_compress",
                # host path phases: [panel copies with the leaf work overlapped, 0, 0, level steps,
                # expansion, projection]
                "phases_ms": last_phases.get("host"), "copy_then_compress": seq}
         del Gh, Gdev
+    if not lead:
+        return None  # replicas: the other ranks' part ends with the timed regions
     if not args.skip_secondary and args.kernel == "slp" and args.eta1 != 20.0:
         # the paper's parameter set (Section 7: eta1 = 20, eta2 = 5) on the same points: many coarse
         # admissible blocks, long column lists per pair
@@ -586,8 +652,8 @@ def run_gpu(args):
     launches = M.launch_count()  # kernels the library launched for the last compression
     line = {
         "metric": "compression wall time & input GB/s at n=32768, kappa=32, eps=1e-4; rel. error vs FP64",
-        "value": in_bytes / (ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "replicas only",
+        "value": whole_job_gbs(in_bytes, world, ms), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "c64/f32 (f64 tail sums)", "fp64": "c128/f64",
                                        "mixed": "c64/bf16x3-tc/f32 (f64 tail sums)"}[args.mode],
         "data": "synthetic (Fibonacci sphere, Helmholtz collocation)", "config": workload(args),
@@ -599,7 +665,7 @@ def run_gpu(args):
         "matvec_ms": matvec_ms,
         "mem_per_n_kib_c128": storage["total"] * 16 / 1024 / args.n,
         "adm_fraction": st.adm_fraction, "e2e": e2e, "secondary": secondary or None,
-        "clocks": clk.summary(), "gpu_launches": launches * args.steps, "launches_per_step": launches,
+        "clocks": clk.summary(), "gpu_launches": launches * args.steps * world, "launches_per_step": launches,
         "tuning": tuning,
     }
     return line
@@ -899,7 +965,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 # the wall time of each bounded sample step; value is the extrapolated whole-compression rate
                 "ms_per_step": 1e3 * statistics.mean(walls), "extrapolated": True,
-                "higher_is_better": True, "scaling": "replicas only", "vs_baseline": None, "dtype": "c128/f64",
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128/f64",
                 "data": "synthetic", "config": workload(args),
                 "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
                                  "sample": desc, "threads": "BLAS/OpenMP fixed to 1"},
@@ -910,7 +976,10 @@ def main():
         if rank == 0:
             {"small": sweep_small, "cube": sweep_cube, "surfaces": sweep_surfaces}[args.sweep](args)
         return
+    dist_init(world)
     line = run_gpu(args)
+    if line is None:
+        return
     line["n_gpus"] = world
     if not args.skip_cpu and rank == 0:
         est, desc, _ = oracle_baseline(args, budget_s=args.cpu_budget)
