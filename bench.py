@@ -339,7 +339,7 @@ def _alg_flops(T, ranks):
     return fac, rq
 
 
-def dist_init(world: int) -> None:
+def dist_init(world: int, backend: str | None = None) -> None:
     """Replicas under torchrun (one process per GPU, each compressing its own copy of the workload):
     a process group for the barriers around the timed regions and the maximum over ranks of their
     times; no collective on the data path (the problems are independent)."""
@@ -347,9 +347,11 @@ def dist_init(world: int) -> None:
     import torch.distributed as dist
 
     if world > 1 and not dist.is_initialized():
-        if torch.cuda.is_available():
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group(backend)
 
 
 def _replicas() -> bool:

@@ -26,7 +26,7 @@ def _rank(rank: int, world: int, port: int, out) -> None:
     import bench
     import torch.distributed as dist
 
-    bench.dist_init(world)
+    bench.dist_init(world, backend="gloo")  # host-side test, with or without a GPU
     try:
         assert dist.get_backend() == "gloo"
         bench.barrier()
